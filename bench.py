@@ -1,0 +1,331 @@
+"""Benchmark of the coupled LB + rigid-RBC time step on GB300.
+
+Default workload: the walled plane channel 64 x 64 x 256 (solid planes
+y = 0, 63; periodic x, z) with 3,650 cells (hematocrit 0.35), driven by a
+force density of 5.376e-7 along x, FP32 populations.  One step is one full
+coupled step: cell list + Gay-Berne forces, per-cell sampling + rigid update +
+spreading, and the fused lattice pass.
+
+Prints one JSON line (rank 0): value = fluid-node updates per second over all
+ranks (MLUPS) from CUDA events around K graph-launched steps, with live
+per-kernel event timing of the lattice pass for the roofline, nvidia-smi clock
+samples taken during the timed region, the end-to-end figure through the
+public API with host buffers (init from host arrays, K steps, fields read
+back), and the FP64 oracle timed on a bounded sample on the host.
+
+``--impl reference`` times the oracle (plain FP64 CPU implementation) on the
+same workload and prints the same line with ``"impl": "reference"``.
+Multi-GPU (torchrun): every rank runs an independent replica of the
+workload (the step has no exchange between replicas); value = sum of
+node updates / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1107_4889_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "coupled-step MLUPS"
+UNIT = "MLUPS"
+L2_BYTES = 129e6
+
+
+def _workload(name):
+    if name == "channel":
+        g, c, p = wl.channel_workload()
+        desc = "walled channel 64x64x256, 3650 RBC (H=0.35), G=5.376e-7, FP32 populations"
+    elif name == "box32":
+        g, c, p = wl.box_workload()
+        desc = "periodic box 32^3, 32 RBC (H=0.098), G=1e-6, FP32 populations"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return g, c, p, desc
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier_and_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower() in ("active", "0x1", "1"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _lb_source_hash():
+    h = hashlib.sha256()
+    for f in ("lb.cu", "rbc_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1107_4889_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(workload):
+    """DRAM bytes per lattice-pass launch from the committed ncu summary, if
+    it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"lb_pass_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_hash = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", txt)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m_hash or not m_bytes or m_hash.group(1) != _lb_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+def _algorithmic_bytes_per_node(geom, params):
+    # populations 19 x 4 B read + written; G (3) and theta (1) read; u (3)
+    # written; sigma (6) written when the elongational torque is on; the
+    # node's solid flag (1 B) on walled lattices
+    b = 2 * 19 * 4 + 4 * 4 + 3 * 4
+    if params.get("alpha_tt", 0.04) != 0.0:
+        b += 6 * 4
+    if geom["solid"] is not None:
+        b += 1
+    return b
+
+
+def _oracle_rate(geom, cells, params, budget_s):
+    """Run the FP64 oracle for about budget_s seconds; returns (MLUPS, steps, seconds)."""
+    from oracle import oracle as orc
+    nf = wl.fluid_count(geom)
+    o = orc.Oracle(geom, cells, params)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter()
+    steps = 1
+    per = t1 - t0
+    more = int(max(0, budget_s - per) / per)
+    if more:
+        o.step(more)
+        steps += more
+    dt = time.perf_counter() - t0
+    o.close()
+    return nf * steps / dt / 1e6, steps, dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    geom, cells, params, desc = _workload(args.workload)
+    nf = wl.fluid_count(geom)
+    rate, steps, dt = _oracle_rate(geom, cells, params, args.reference_budget)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc, "fluid_nodes": nf, "cells": len(cells["pos"])},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} coupled steps of the full workload ({dt:.1f} s), "
+                                   f"capped by a {args.reference_budget:.0f} s budget"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1107_4889_gb300 import build as B
+    from paper_1107_4889_gb300.rbc import Solver
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if rank == 0:
+        B.build()
+    _barrier(ws)
+    torch.cuda.set_device(local)
+    geom, cells, params, desc = _workload(args.workload)
+    nf = wl.fluid_count(geom)
+    N = geom["nx"] * geom["ny"] * geom["nz"]
+
+    s = Solver(geom, cells, params)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    st = s.stats()
+
+    # timed region: K graph-launched steps, live event timing of the kernels
+    s.set_timing(args.steps)
+    clocks = Clocks(local)
+    stream = s.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    _barrier(ws)
+    ms = e0.elapsed_time(e1)
+    kms, kcount = s.kernel_times()
+    st2 = s.stats()
+    launches = s.launches_per_step() * args.steps
+    ws_bytes = s.workspace_bytes
+    s.close()
+    ms_max = _barrier_and_max(ms, ws)
+    value = nf * args.steps * ws / (ms_max * 1e-3) / 1e6
+
+    # end to end through the public API with host buffers
+    _barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s2 = Solver(geom, cells, params)
+    s2.step(args.steps)
+    f = s2.fields()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    s2.close()
+    e2e_s = _barrier_and_max(e2e_s, ws)
+    n = len(cells["pos"])
+    h2d = (0 if geom["solid"] is None else N) + n * (3 + 4 + 3 + 3) * 8
+    d2h = N * 8 + N * 3 * 8 + n * 13 * 8
+    e2e = {"value": nf * args.steps * ws / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "note": "job = init from host arrays + K steps + fields read back"}
+    assert np.isfinite(f["u"]).all()
+
+    if rank != 0:
+        return
+    lb_ms = kms[0] / max(kcount[0], 1)
+    bpn = _algorithmic_bytes_per_node(geom, params)
+    peak, peak_kind = _peaks()
+    achieved = bpn * nf / (lb_ms * 1e-3) / 1e9
+    traffic = _profiled_traffic(args.workload)
+    roof = {"kernel": "lattice pass (k_lb)", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_fluid_node": bpn,
+            "lb_ms_per_launch": lb_ms, "cell_work_ms_per_step": kms[1] / max(kcount[1], 1)}
+
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        rate, csteps, cdt = _oracle_rate(geom, cells, params, args.cpu_budget)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{csteps} coupled steps of the same workload ({cdt:.1f} s, one core)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "nodes": N, "fluid_nodes": nf, "cells": n,
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": f"inputs larger than L2: per-step working set "
+                         f"{ws_bytes / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB",
+                   "steps_per_s": args.steps / (ms_max * 1e-3)},
+        "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+        "budget": {"mass_drift_rel": (st2["mass"] - st["mass"]) / st["mass"], "max_u": st2["max_u"],
+                   "gb_clamps": st2["gb_clamps"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["channel", "box32"], default="channel")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--reference-budget", type=float, default=60.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * rbc.h -- C ABI of the GB300 (sm_103a) library for the coupled lattice-
+ * Boltzmann + rigid red-blood-cell time step of S. Melchionna, "A model for
+ * red blood cells in simulations of large-scale blood flows" (2011).
+ *
+ * One time step h (lattice units, h = 1) advances
+ *   - the plasma: D3Q19 BGK streaming and collision with the Hermite
+ *     body-force term and a per-node relaxation time (Sec. 2.1,
+ *     Eqs. streaming, lbe_discrete, chen_force, dens, vel, stresstensorLB);
+ *   - the relaxation time set by the local hematocrit through the smoothed
+ *     characteristic function of every cell (Sec. 2.4, Eq. enhance-viscosity);
+ *   - the fluid-cell exchange through each cell's diffused shape function:
+ *     smeared velocity / vorticity and the elongational torque sampled from
+ *     the fluid (Sec. 2.2, Eqs. vel, vort, pheno_torque_diss), the reaction
+ *     spread back as a force density (Sec. 2.2, body-force equation);
+ *   - Gay-Berne cell-cell and cell-wall forces and torques found through a
+ *     device-built cell list (Sec. 2.5, App. B);
+ *   - the rigid-body update of every cell (App. A).
+ *
+ * Conventions.  Lattice node n = x + nx*(y + ny*z), x fastest.  Lattice
+ * indices wrap on every axis; walls are solid nodes, and an axis declared
+ * non-periodic must have solid end planes.  Quaternions are (w, x, y, z) and
+ * map body to lab frame; angular velocities are body-frame.  All host
+ * buffers are caller-owned; inputs are copied at rbc_init.
+ *
+ * Status codes: every function returning int returns one of RBC_OK or a
+ * negative RBC_E* code and never aborts; rbc_last_error() describes the last
+ * failure of a handle (or of the calling thread when the handle is NULL).
+ * The library is single-GPU: it runs on the CUDA device current at rbc_init.
+ */
+#ifndef RBC_H
+#define RBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RBC_OK 0
+#define RBC_EINVAL (-1)    /* invalid argument, geometry or parameter */
+#define RBC_ENOMEM (-2)    /* workspace too small, or a capacity exceeded */
+#define RBC_ECUDA (-3)     /* a CUDA runtime call failed */
+#define RBC_EUNSTABLE (-4) /* NaN, or |u| above the Mach guard */
+#define RBC_ETIMEOUT (-5)  /* a bounded device wait ran out */
+
+typedef struct rbc_handle rbc_handle;
+
+/* Geometry of the lattice (Sec. 2.1).  solid: host array of nx*ny*nz bytes,
+ * 1 = solid node, NULL = all fluid; copied at init.  body_force: external
+ * force density added at every fluid node (lattice units). */
+typedef struct {
+    int nx, ny, nz;
+    int periodic[3];
+    const uint8_t *solid;
+    double body_force[3];
+} rbc_geometry;
+
+/* Initial cell state (Sec. 2.2: Gamma_i = (R_i, Q_i, V_i, Omega_i)).  Host
+ * arrays, copied at init: pos 3n (inside the box), quat 4n (need not be
+ * normalised), vel 3n or NULL (zero), omega_body 3n or NULL (zero). */
+typedef struct {
+    int n;
+    const double *pos;
+    const double *quat;
+    const double *vel;
+    const double *omega_body;
+} rbc_cells;
+
+/* Model parameters (paper values in brackets; rbc_default_params fills them).
+ *   tau0, delta, kappa  Eq. enhance-viscosity [1, 2, 20]
+ *   gamma_T, gamma_R    friction rates of App. A [0.1, 0.1]
+ *   alpha_tt            elongational torque factor, Eq. pheno_torque_diss [0.04]
+ *   eps0                Gay-Berne energy scale, Eq. gayberne [not given; 0.01]
+ *   xi[3]               shape-function radii along the body axes [4, 4, 1.5]
+ *   semi_axes[3]        Gay-Berne semi-axes (shape matrix S) [4, 4, 1.5]
+ *   mass, inertia[3]    M and the diagonal body-frame I [10; 1000, 1000, 1000]
+ *   sigma_min_wall      wall-RBC sigma_min (Sec. 2.5) [0.5]
+ *   wall_radius         radius of the spherical wall particle [0.5]
+ *   rho_floor           lower clamp of the reduced GB distance [0.75]
+ *   r_cut, r_cut_wall   candidate radii of the cell-pair / cell-wall search;
+ *                       0 derives the Gay-Berne range from the shape
+ *   mach_max            |u| guard of the stability flag [0.3]
+ *   bin_capacity        cells per cell-list bin [0 = 32]
+ *   max_neighbors       candidate partners kept per cell [0 = 64]
+ *   stream              cudaStream_t the library works on (NULL: one it
+ *                       creates and owns). */
+typedef struct {
+    double tau0, delta, kappa;
+    double gamma_T, gamma_R;
+    double alpha_tt;
+    double eps0;
+    double xi[3];
+    double semi_axes[3];
+    double mass, inertia[3];
+    double sigma_min_wall, wall_radius;
+    double rho_floor;
+    double r_cut, r_cut_wall;
+    double mach_max;
+    int bin_capacity;
+    int max_neighbors;
+    void *stream;
+} rbc_params;
+
+/* Running budgets (Sec. 2.2 conservation claims).  mass and p_fluid are the
+ * zeroth and first moments of the stored populations over fluid nodes;
+ * p_cells = sum_i M V_i; max_u = max |u| of the last lattice pass. */
+typedef struct {
+    int64_t step;
+    double mass;
+    double p_fluid[3];
+    double p_cells[3];
+    double max_u;
+    int64_t gb_clamps;
+    int32_t unstable;
+    int32_t overflow; /* bit 0 bin, bit 1 neighbour list, bit 2 shape box */
+} rbc_stats_t;
+
+/* Fill *p with the paper's parameters (values above) and a NULL stream. */
+void rbc_default_params(rbc_params *p);
+
+/* Bytes of device workspace rbc_init needs for this problem (256-byte
+ * aligned pieces).  Returns RBC_EINVAL for an invalid problem. */
+int rbc_workspace_size(const rbc_geometry *geom, const rbc_cells *cells,
+                       const rbc_params *params, size_t *bytes);
+
+/* Validate the problem, carve the caller's device workspace (at least
+ * rbc_workspace_size bytes, 256-byte aligned, owned by the caller and kept
+ * alive until rbc_free), copy geometry and cells to the device, set the
+ * fluid at rest (f = f^eq(rho = 1, u = 0)) and capture one step as CUDA
+ * graphs on params->stream.  Synchronises that stream.  *out receives the
+ * handle.  Errors: RBC_EINVAL, RBC_ENOMEM (workspace too small), RBC_ECUDA. */
+int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params *params,
+             void *workspace, size_t workspace_bytes, rbc_handle **out);
+
+/* Enqueue n coupled steps on the handle's stream and return without waiting
+ * (Sec. 2, App. A; the step order is: cell list and Gay-Berne forces,
+ * sampling + rigid update + spreading per cell, lattice pass).  Returns
+ * RBC_EUNSTABLE / RBC_ENOMEM if an earlier synchronising call saw the device
+ * flags raised; RBC_EINVAL for n < 0. */
+int rbc_step(rbc_handle *h, int64_t n);
+
+/* Copy the fields of the last lattice pass to host buffers (any may be
+ * NULL): rho[N] (Eq. dens), u[3N] node-major (Eq. vel), and per cell 13
+ * doubles R(3) quat(4) V(3) Omega_body(3).  Solid nodes report rho = u = 0.
+ * Synchronises the stream; returns RBC_EUNSTABLE if the guard tripped. */
+int rbc_fields(rbc_handle *h, double *rho, double *u, double *cells_state);
+
+/* Compute the budgets on the device and copy them to *out (synchronising). */
+int rbc_stats(rbc_handle *h, rbc_stats_t *out);
+
+/* Per cell 21 doubles of the last step: F_mech(3) tau_mech(3) (Gay-Berne,
+ * lab frame), u~(3) omega~(3) (Eqs. vel, vort), T^S(3) (Eq.
+ * pheno_torque_diss), J(3) L(3) (hydrodynamic linear and lab angular impulse
+ * returned to the fluid).  Host buffer; synchronises. */
+int rbc_cell_diag(rbc_handle *h, double *out);
+
+/* Candidate partners of every cell from the last cell-list pass: counts[n]
+ * and lists[n*max_per_cell], each list sorted by partner index; partners are
+ * the j != i with |R_i - R_j|^2 < r_cut^2 (minimum image along periodic
+ * axes, FP64, no fused multiply-add).  Returns RBC_ENOMEM if a list is longer
+ * than max_per_cell.  Host buffers; synchronises. */
+int rbc_neighbors(rbc_handle *h, int *counts, int *lists, int max_per_cell);
+
+/* Kernel timing.  rbc_set_timing(h, capacity) makes the next `capacity`
+ * steps record CUDA events around the lattice pass and around the per-step
+ * cell work on the handle's stream (capacity 0 turns it off).
+ * rbc_kernel_times synchronises and returns for k = 0 (lattice pass) and
+ * k = 1 (cell work) the summed milliseconds ms[k] and the number of timed
+ * launches count[k], then clears them. */
+int rbc_set_timing(rbc_handle *h, int capacity);
+int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2]);
+
+/* Kernel launches one rbc_step(h, 1) enqueues. */
+int rbc_launches_per_step(const rbc_handle *h);
+
+/* Release the handle, its graphs, events and owned stream (not the caller's
+ * workspace).  NULL is ignored. */
+void rbc_free(rbc_handle *h);
+
+/* Message of the last failure on h (h may be NULL: last failure of the
+ * calling thread).  Valid until the next call on the same handle/thread. */
+const char *rbc_last_error(const rbc_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBC_H */

@@ -1,0 +1,679 @@
+// api.cu -- host runtime behind the C ABI of include/rbc.h.
+//
+// The caller lends one device workspace (PyTorch's allocator in the Python
+// binding); the runtime carves every buffer out of it, validates and uploads
+// the problem, and captures one coupled step as two CUDA graphs on the
+// caller's stream: the cell work (bin clear, k_bin, k_gb, k_cells) and the
+// lattice pass (one per ping-pong parity).  rbc_step only launches graphs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/rbc.h"
+#include "internal.h"
+
+using namespace rbc;
+
+namespace {
+
+thread_local std::string g_thread_err;
+
+struct Problem {
+    int nx, ny, nz, N;
+    long long Np;
+    int per[3];
+    bool any_solid;
+    int nc;
+    Params p;
+    int nb[3], nbins, bin_cap, max_nbr;
+    double bin_size[3];
+    std::vector<int> wall_start, wall_xyz;
+    int nw;
+    int budget_blocks;
+};
+
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base(static_cast<char *>(b)) {}
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        T *ptr = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return ptr;
+    }
+};
+
+int fail(std::string *err, int code, const std::string &msg)
+{
+    if (err) *err = msg;
+    g_thread_err = msg;
+    return code;
+}
+
+inline long long node(const Problem &P, int x, int y, int z)
+{
+    x = (x % P.nx + P.nx) % P.nx;
+    y = (y % P.ny + P.ny) % P.ny;
+    z = (z % P.nz + P.nz) % P.nz;
+    return (long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z);
+}
+
+int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Problem &P, std::string *err)
+{
+    if (!g || !pp) return fail(err, RBC_EINVAL, "geometry and params are required");
+    if (g->nx < 3 || g->ny < 3 || g->nz < 3) return fail(err, RBC_EINVAL, "every lattice dimension must be >= 3");
+    const long long N = (long long)g->nx * g->ny * g->nz;
+    if (N > 1500000000LL) return fail(err, RBC_EINVAL, "lattice too large for 32-bit node indices");
+    P.nx = g->nx;
+    P.ny = g->ny;
+    P.nz = g->nz;
+    P.N = (int)N;
+    P.Np = (N + 63) / 64 * 64;
+    for (int a = 0; a < 3; ++a) P.per[a] = g->periodic[a] ? 1 : 0;
+    P.any_solid = false;
+    if (g->solid) {
+        for (long long n = 0; n < N; ++n)
+            if (g->solid[n]) {
+                P.any_solid = true;
+                break;
+            }
+    }
+    // a non-periodic axis must be closed by solid end planes (indices wrap)
+    const int dims[3] = {g->nx, g->ny, g->nz};
+    for (int a = 0; a < 3; ++a) {
+        if (P.per[a]) continue;
+        if (!g->solid) return fail(err, RBC_EINVAL, "a non-periodic axis needs solid end planes");
+        const int b = (a + 1) % 3, c2 = (a + 2) % 3;
+        for (int e = 0; e < 2; ++e) {
+            const int at = e ? dims[a] - 1 : 0;
+            for (int i = 0; i < dims[b]; ++i)
+                for (int j = 0; j < dims[c2]; ++j) {
+                    int X[3];
+                    X[a] = at;
+                    X[b] = i;
+                    X[c2] = j;
+                    if (!g->solid[node(P, X[0], X[1], X[2])])
+                        return fail(err, RBC_EINVAL, "a non-periodic axis needs solid end planes");
+                }
+        }
+    }
+    // parameters
+    const rbc_params &q = *pp;
+    if (!(q.tau0 > 0.5)) return fail(err, RBC_EINVAL, "tau0 must exceed 1/2");
+    if (!(q.delta >= 0.0) || !(q.kappa > 0.0)) return fail(err, RBC_EINVAL, "delta >= 0 and kappa > 0 required");
+    if (!(q.mass > 0.0)) return fail(err, RBC_EINVAL, "mass must be positive");
+    for (int a = 0; a < 3; ++a) {
+        if (!(q.inertia[a] > 0.0)) return fail(err, RBC_EINVAL, "inertia must be positive");
+        if (!(q.xi[a] > 0.0) || !(q.semi_axes[a] > 0.0)) return fail(err, RBC_EINVAL, "xi and semi_axes must be positive");
+    }
+    if (!(q.gamma_T >= 0.0) || !(q.gamma_R >= 0.0) || !(q.eps0 >= 0.0))
+        return fail(err, RBC_EINVAL, "gamma_T, gamma_R, eps0 must be >= 0");
+    if (!(q.sigma_min_wall > 0.0) || !(q.wall_radius >= 0.0)) return fail(err, RBC_EINVAL, "bad wall particle");
+    const int nc = c ? c->n : 0;
+    if (nc < 0) return fail(err, RBC_EINVAL, "negative cell count");
+    if (nc > 0 && (!c->pos || !c->quat)) return fail(err, RBC_EINVAL, "cell positions and quaternions are required");
+    P.nc = nc;
+
+    Params &p = P.p;
+    for (int a = 0; a < 3; ++a) {
+        p.gext[a] = (float)g->body_force[a];
+        p.xi[a] = (float)q.xi[a];
+        p.a2[a] = q.semi_axes[a] * q.semi_axes[a];
+        p.I[a] = q.inertia[a];
+        p.periodic[a] = P.per[a];
+    }
+    p.tau0 = (float)q.tau0;
+    p.delta = (float)q.delta;
+    p.kappa = (float)q.kappa;
+    p.alpha = (float)q.alpha_tt;
+    const double mach = q.mach_max > 0.0 ? q.mach_max : 0.3;
+    p.mach2 = (float)(mach * mach);
+    p.M = q.mass;
+    p.gT = q.gamma_T;
+    p.gR = q.gamma_R;
+    p.eT = std::exp(-0.5 * q.gamma_T);
+    p.eR = std::exp(-0.5 * q.gamma_R);
+    p.eps0 = q.eps0;
+    const double amin = std::min(q.semi_axes[0], std::min(q.semi_axes[1], q.semi_axes[2]));
+    const double amax = std::max(q.semi_axes[0], std::max(q.semi_axes[1], q.semi_axes[2]));
+    p.smin_cc = std::sqrt(2.0 * (amin * amin + amin * amin));
+    p.smin_w = q.sigma_min_wall;
+    p.rw2 = q.wall_radius * q.wall_radius;
+    p.rho_floor = q.rho_floor;
+    p.rho_cut = std::pow(2.0, 1.0 / 6.0);
+    const double rc = q.r_cut > 0.0 ? q.r_cut : std::sqrt(2.0 * (2.0 * amax * amax)) + (p.rho_cut - 1.0) * p.smin_cc;
+    const double rcw = q.r_cut_wall > 0.0 ? q.r_cut_wall
+                                          : std::sqrt(2.0 * (amax * amax + p.rw2)) + (p.rho_cut - 1.0) * p.smin_w;
+    p.rc2 = rc * rc;
+    p.rcw2 = rcw * rcw;
+
+    // shape box: per axis at most floor(2 |xi|) + 3 nodes
+    const double xin = std::sqrt(q.xi[0] * q.xi[0] + q.xi[1] * q.xi[1] + q.xi[2] * q.xi[2]);
+    const int bdim = (int)std::floor(2.0 * xin) + 3;
+    p.box_max = bdim * bdim * bdim;
+    p.box_dim = bdim;
+    if (nc > 0) {
+        if (bdim > std::min(g->nx, std::min(g->ny, g->nz)))
+            return fail(err, RBC_EINVAL, "shape-function support does not fit in the lattice");
+        if ((size_t)p.box_max * sizeof(float) > 200u * 1024u)
+            return fail(err, RBC_EINVAL, "shape-function support too large for shared memory");
+        const double bin_min = std::max(rc, rcw);
+        for (int a = 0; a < 3; ++a) {
+            if (P.per[a] && 2.0 * rc >= dims[a]) return fail(err, RBC_EINVAL, "r_cut must be below half the box");
+            P.nb[a] = std::max(1, (int)std::floor(dims[a] / bin_min));
+            P.bin_size[a] = (double)dims[a] / P.nb[a];
+        }
+        for (int i = 0; i < nc; ++i)
+            for (int a = 0; a < 3; ++a) {
+                const double r = c->pos[3 * i + a];
+                if (!std::isfinite(r)) return fail(err, RBC_EINVAL, "non-finite cell position");
+                if (!P.per[a] && (r < 0.0 || r >= dims[a])) return fail(err, RBC_EINVAL, "cell outside a non-periodic box");
+            }
+    } else {
+        P.nb[0] = P.nb[1] = P.nb[2] = 1;
+        for (int a = 0; a < 3; ++a) P.bin_size[a] = dims[a];
+    }
+    P.nbins = P.nb[0] * P.nb[1] * P.nb[2];
+    P.bin_cap = q.bin_capacity > 0 ? q.bin_capacity : 32;
+    P.max_nbr = q.max_neighbors > 0 ? std::min(q.max_neighbors, 128) : 64;
+
+    // wall particles: solid nodes with a fluid node among their 18 links
+    P.nw = 0;
+    P.wall_start.assign(P.nbins + 1, 0);
+    P.wall_xyz.clear();
+    if (P.any_solid && nc > 0) {
+        std::vector<int> xyz, bins;
+        for (int z = 0; z < P.nz; ++z)
+            for (int y = 0; y < P.ny; ++y)
+                for (int x = 0; x < P.nx; ++x) {
+                    if (!g->solid[node(P, x, y, z)]) continue;
+                    bool wet = false;
+                    for (int dz = -1; dz <= 1 && !wet; ++dz)
+                        for (int dy = -1; dy <= 1 && !wet; ++dy)
+                            for (int dx = -1; dx <= 1 && !wet; ++dx) {
+                                const int m = std::abs(dx) + std::abs(dy) + std::abs(dz);
+                                if (m == 0 || m == 3) continue;
+                                if (!g->solid[node(P, x + dx, y + dy, z + dz)]) wet = true;
+                            }
+                    if (!wet) continue;
+                    const int X[3] = {x, y, z};
+                    int b[3];
+                    for (int a = 0; a < 3; ++a) b[a] = std::min(P.nb[a] - 1, (int)std::floor(X[a] / P.bin_size[a]));
+                    bins.push_back(b[0] + P.nb[0] * (b[1] + P.nb[1] * b[2]));
+                    xyz.push_back(x);
+                    xyz.push_back(y);
+                    xyz.push_back(z);
+                }
+        P.nw = (int)bins.size();
+        for (int w = 0; w < P.nw; ++w) P.wall_start[bins[w] + 1]++;
+        for (int b = 0; b < P.nbins; ++b) P.wall_start[b + 1] += P.wall_start[b];
+        std::vector<int> cur(P.wall_start.begin(), P.wall_start.end() - 1);
+        P.wall_xyz.assign(3 * (size_t)P.nw, 0);
+        for (int w = 0; w < P.nw; ++w) {
+            const int at = cur[bins[w]]++;
+            for (int a = 0; a < 3; ++a) P.wall_xyz[3 * at + a] = xyz[3 * w + a];
+        }
+    }
+    P.budget_blocks = budget_blocks_for(P.N);
+    return RBC_OK;
+}
+
+// Carve the device buffers (base == nullptr only measures).
+size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
+{
+    Carver cv(base);
+    const size_t Np = (size_t)P.Np;
+    d.nx = P.nx;
+    d.ny = P.ny;
+    d.nz = P.nz;
+    d.N = P.N;
+    d.Np = P.Np;
+    d.walls = P.any_solid ? 1 : 0;
+    d.pops[0] = cv.take<float>(19 * Np);
+    d.pops[1] = cv.take<float>(19 * Np);
+    d.U = cv.take<float>(3 * Np);
+    d.S = (P.nc > 0 && q->alpha_tt != 0.0) ? cv.take<float>(6 * Np) : nullptr;
+    d.G = P.nc > 0 ? cv.take<float>(3 * Np) : nullptr;
+    d.theta = P.nc > 0 ? cv.take<float>(Np) : nullptr;
+    d.rho = cv.take<float>(Np);
+    d.solid = P.any_solid ? cv.take<uint8_t>(Np) : nullptr;
+    const size_t n = (size_t)std::max(P.nc, 1);
+    d.nc = P.nc;
+    d.R = cv.take<double>(3 * n);
+    d.q = cv.take<double>(4 * n);
+    d.V = cv.take<double>(3 * n);
+    d.Om = cv.take<double>(3 * n);
+    d.A = cv.take<double>(6 * n);
+    d.Fm = cv.take<double>(3 * n);
+    d.Tm = cv.take<double>(3 * n);
+    d.have = cv.take<int>(n);
+    d.diag = cv.take<double>(21 * n);
+    for (int a = 0; a < 3; ++a) {
+        d.nb[a] = P.nb[a];
+        d.bin_size[a] = P.bin_size[a];
+    }
+    d.nbins = P.nbins;
+    d.bin_cap = P.bin_cap;
+    d.bin_count = cv.take<int>(P.nbins);
+    d.bin_cells = cv.take<int>((size_t)P.nbins * P.bin_cap);
+    d.cell_bin = cv.take<int>(n);
+    d.max_nbr = P.max_nbr;
+    d.nbr = cv.take<int>(n * P.max_nbr);
+    d.nbr_count = cv.take<int>(n);
+    d.nw = P.nw;
+    d.wall_start = cv.take<int>(P.nbins + 1);
+    d.wall_xyz = cv.take<int>(3 * (size_t)std::max(P.nw, 1));
+    d.flags = cv.take<int>(8);
+    d.clamps = cv.take<unsigned long long>(1);
+    d.budget_blocks = P.budget_blocks;
+    d.budget_part = cv.take<double>(8 * (size_t)P.budget_blocks);
+    d.budget_out = cv.take<double>(16);
+    return (cv.off + 255) & ~size_t(255);
+}
+
+}  // namespace
+
+struct rbc_handle {
+    Problem P;
+    Dev d;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t g_cells = nullptr, g_lb[2] = {nullptr, nullptr};
+    int64_t step = 0;
+    int timing_cap = 0, timing_used = 0;
+    std::vector<cudaEvent_t> ev;  // 3 per timed step
+    std::string err;
+    int device = 0;
+    std::vector<uint8_t> solid_host;
+};
+
+#define RBC_CU(call)                                                                                \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(h ? &h->err : nullptr, RBC_ECUDA,                                           \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+    } while (0)
+
+static int capture(rbc_handle *h, void (*body)(rbc_handle *, int), int arg, cudaGraphExec_t *out)
+{
+    cudaGraph_t graph = nullptr;
+    RBC_CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    body(h, arg);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (e != cudaSuccess) return fail(&h->err, RBC_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(&h->err, RBC_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    return RBC_OK;
+}
+
+static void body_cells(rbc_handle *h, int)
+{
+    launch_bin(h->d, h->P.p, h->stream);
+    launch_gb(h->d, h->P.p, h->stream);
+    launch_cells(h->d, h->P.p, h->stream);
+}
+
+static void body_lb(rbc_handle *h, int parity) { launch_lb(h->d, h->P.p, parity, h->stream); }
+
+extern "C" {
+
+void rbc_default_params(rbc_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->tau0 = 1.0;
+    p->delta = 2.0;
+    p->kappa = 20.0;
+    p->gamma_T = 0.1;
+    p->gamma_R = 0.1;
+    p->alpha_tt = 0.04;
+    p->eps0 = 0.01;
+    p->xi[0] = 4.0;
+    p->xi[1] = 4.0;
+    p->xi[2] = 1.5;
+    p->semi_axes[0] = 4.0;
+    p->semi_axes[1] = 4.0;
+    p->semi_axes[2] = 1.5;
+    p->mass = 10.0;
+    p->inertia[0] = p->inertia[1] = p->inertia[2] = 1000.0;
+    p->sigma_min_wall = 0.5;
+    p->wall_radius = 0.5;
+    p->rho_floor = 0.75;
+    p->mach_max = 0.3;
+}
+
+int rbc_workspace_size(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params *params, size_t *bytes)
+{
+    if (!bytes) return fail(nullptr, RBC_EINVAL, "bytes is NULL");
+    Problem P;
+    int rc = analyse(geom, cells, params, P, nullptr);
+    if (rc != RBC_OK) return rc;
+    Dev d;
+    *bytes = carve(P, params, nullptr, d);
+    return RBC_OK;
+}
+
+int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params *params, void *workspace,
+             size_t workspace_bytes, rbc_handle **out)
+{
+    if (!out) return fail(nullptr, RBC_EINVAL, "out is NULL");
+    *out = nullptr;
+    rbc_handle *h = new (std::nothrow) rbc_handle();
+    if (!h) return fail(nullptr, RBC_ENOMEM, "host allocation failed");
+    int rc = analyse(geom, cells, params, h->P, &h->err);
+    if (rc != RBC_OK) {
+        delete h;
+        return rc;
+    }
+    Dev probe;
+    const size_t need = carve(h->P, params, nullptr, probe);
+    if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u)) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "workspace must be >= %zu bytes and 256-byte aligned", need);
+        fail(nullptr, RBC_ENOMEM, msg);
+        delete h;
+        return RBC_ENOMEM;
+    }
+    carve(h->P, params, workspace, h->d);
+    if (h->P.any_solid) h->solid_host.assign(geom->solid, geom->solid + h->P.N);
+    cudaGetDevice(&h->device);
+    if (params->stream) {
+        h->stream = static_cast<cudaStream_t>(params->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            fail(nullptr, RBC_ECUDA, "stream creation failed");
+            delete h;
+            return RBC_ECUDA;
+        }
+        h->own_stream = true;
+    }
+    rc = [&]() -> int {
+        Dev &d = h->d;
+        const Problem &P = h->P;
+        cudaStream_t s = h->stream;
+        const size_t Np = (size_t)P.Np;
+        // fluid at rest: f = w_p, i.e. zero deviations; fields zero
+        RBC_CU(cudaMemsetAsync(d.pops[0], 0, 19 * Np * sizeof(float), s));
+        RBC_CU(cudaMemsetAsync(d.pops[1], 0, 19 * Np * sizeof(float), s));
+        RBC_CU(cudaMemsetAsync(d.U, 0, 3 * Np * sizeof(float), s));
+        if (d.S) RBC_CU(cudaMemsetAsync(d.S, 0, 6 * Np * sizeof(float), s));
+        if (d.G) RBC_CU(cudaMemsetAsync(d.G, 0, 3 * Np * sizeof(float), s));
+        if (d.theta) RBC_CU(cudaMemsetAsync(d.theta, 0, Np * sizeof(float), s));
+        RBC_CU(cudaMemsetAsync(d.rho, 0, Np * sizeof(float), s));
+        if (d.solid) {
+            RBC_CU(cudaMemsetAsync(d.solid, 0, Np, s));
+            RBC_CU(cudaMemcpyAsync(d.solid, geom->solid, (size_t)P.N, cudaMemcpyHostToDevice, s));
+        }
+        RBC_CU(cudaMemsetAsync(d.flags, 0, 8 * sizeof(int), s));
+        RBC_CU(cudaMemsetAsync(d.clamps, 0, sizeof(unsigned long long), s));
+        const int n = P.nc;
+        if (n > 0) {
+            const int dims[3] = {P.nx, P.ny, P.nz};
+            std::vector<double> R(3 * (size_t)n), q(4 * (size_t)n), V(3 * (size_t)n, 0.0), W(3 * (size_t)n, 0.0);
+            for (int i = 0; i < n; ++i) {
+                for (int a = 0; a < 3; ++a) {
+                    double r = cells->pos[3 * i + a];
+                    if (P.per[a]) {
+                        r = std::fmod(r, (double)dims[a]);
+                        if (r < 0.0) r += dims[a];
+                        if (r >= dims[a]) r -= dims[a];
+                    }
+                    R[3 * i + a] = r;
+                    if (cells->vel) V[3 * i + a] = cells->vel[3 * i + a];
+                    if (cells->omega_body) W[3 * i + a] = cells->omega_body[3 * i + a];
+                }
+                double nq = 0.0;
+                for (int k = 0; k < 4; ++k) nq += cells->quat[4 * i + k] * cells->quat[4 * i + k];
+                if (!(nq > 0.0) || !std::isfinite(nq)) return fail(&h->err, RBC_EINVAL, "degenerate quaternion");
+                for (int k = 0; k < 4; ++k) q[4 * i + k] = cells->quat[4 * i + k] / std::sqrt(nq);
+            }
+            RBC_CU(cudaMemcpyAsync(d.R, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+            RBC_CU(cudaMemcpyAsync(d.q, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+            RBC_CU(cudaMemcpyAsync(d.V, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+            RBC_CU(cudaMemcpyAsync(d.Om, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+            RBC_CU(cudaMemsetAsync(d.have, 0, sizeof(int) * n, s));
+            RBC_CU(cudaMemsetAsync(d.diag, 0, sizeof(double) * 21 * n, s));
+            RBC_CU(cudaMemsetAsync(d.Fm, 0, sizeof(double) * 3 * n, s));
+            RBC_CU(cudaMemsetAsync(d.Tm, 0, sizeof(double) * 3 * n, s));
+            RBC_CU(cudaMemsetAsync(d.nbr_count, 0, sizeof(int) * n, s));
+            RBC_CU(cudaMemcpyAsync(d.wall_start, P.wall_start.data(), sizeof(int) * (P.nbins + 1),
+                                   cudaMemcpyHostToDevice, s));
+            if (P.nw > 0)
+                RBC_CU(cudaMemcpyAsync(d.wall_xyz, P.wall_xyz.data(), sizeof(int) * 3 * (size_t)P.nw,
+                                       cudaMemcpyHostToDevice, s));
+            const size_t smem = cells_smem_bytes(P.p);
+            (void)smem;
+        }
+        RBC_CU(cudaStreamSynchronize(s));
+        if (n > 0) {
+            int r = capture(h, body_cells, 0, &h->g_cells);
+            if (r != RBC_OK) return r;
+        }
+        for (int par = 0; par < 2; ++par) {
+            int r = capture(h, body_lb, par, &h->g_lb[par]);
+            if (r != RBC_OK) return r;
+        }
+        RBC_CU(cudaStreamSynchronize(s));
+        RBC_CU(cudaGetLastError());
+        return RBC_OK;
+    }();
+    if (rc != RBC_OK) {
+        g_thread_err = h->err;
+        rbc_free(h);
+        return rc;
+    }
+    *out = h;
+    return RBC_OK;
+}
+
+static int check_flags(rbc_handle *h)
+{
+    int flags[8];
+    RBC_CU(cudaMemcpyAsync(flags, h->d.flags, sizeof flags, cudaMemcpyDeviceToHost, h->stream));
+    RBC_CU(cudaStreamSynchronize(h->stream));
+    if (flags[FLAG_OVERFLOW])
+        return fail(&h->err, RBC_ENOMEM,
+                    std::string("capacity exceeded:") + ((flags[FLAG_OVERFLOW] & OVF_BIN) ? " cell-list bin" : "") +
+                        ((flags[FLAG_OVERFLOW] & OVF_NBR) ? " neighbour list" : "") +
+                        ((flags[FLAG_OVERFLOW] & OVF_BOX) ? " shape box" : ""));
+    if (flags[FLAG_UNSTABLE]) return fail(&h->err, RBC_EUNSTABLE, "NaN or |u| above the Mach guard");
+    return RBC_OK;
+}
+
+int rbc_step(rbc_handle *h, int64_t n)
+{
+    if (!h) return fail(nullptr, RBC_EINVAL, "handle is NULL");
+    if (n < 0) return fail(&h->err, RBC_EINVAL, "negative step count");
+    for (int64_t k = 0; k < n; ++k) {
+        const int par = (int)(h->step & 1);
+        const bool timed = h->timing_used < h->timing_cap;
+        cudaEvent_t *ev = timed ? &h->ev[3 * (size_t)h->timing_used] : nullptr;
+        if (timed) RBC_CU(cudaEventRecord(ev[0], h->stream));
+        if (h->g_cells) RBC_CU(cudaGraphLaunch(h->g_cells, h->stream));
+        if (timed) RBC_CU(cudaEventRecord(ev[1], h->stream));
+        RBC_CU(cudaGraphLaunch(h->g_lb[par], h->stream));
+        if (timed) {
+            RBC_CU(cudaEventRecord(ev[2], h->stream));
+            h->timing_used++;
+        }
+        h->step++;
+    }
+    return RBC_OK;
+}
+
+int rbc_fields(rbc_handle *h, double *rho, double *u, double *cells_state)
+{
+    if (!h) return fail(nullptr, RBC_EINVAL, "handle is NULL");
+    const Dev &d = h->d;
+    const size_t N = (size_t)d.N, Np = (size_t)d.Np;
+    const int par = (int)(h->step & 1);
+    if (rho) {
+        launch_rho(d, par, h->stream);
+        std::vector<float> r(N);
+        RBC_CU(cudaMemcpyAsync(r.data(), d.rho, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        RBC_CU(cudaStreamSynchronize(h->stream));
+        const uint8_t *solid = h->P.any_solid ? h->solid_host.data() : nullptr;
+        for (size_t k = 0; k < N; ++k) rho[k] = (solid && solid[k]) ? 0.0 : 1.0 + (double)r[k];
+    }
+    if (u) {
+        std::vector<float> U(3 * Np);
+        RBC_CU(cudaMemcpyAsync(U.data(), d.U, 3 * Np * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        RBC_CU(cudaStreamSynchronize(h->stream));
+        for (size_t k = 0; k < N; ++k)
+            for (int a = 0; a < 3; ++a) u[3 * k + a] = U[a * Np + k];
+    }
+    if (cells_state && d.nc > 0) {
+        const size_t n = (size_t)d.nc;
+        std::vector<double> R(3 * n), q(4 * n), V(3 * n), W(3 * n);
+        RBC_CU(cudaMemcpyAsync(R.data(), d.R, R.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+        RBC_CU(cudaMemcpyAsync(q.data(), d.q, q.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+        RBC_CU(cudaMemcpyAsync(V.data(), d.V, V.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+        RBC_CU(cudaMemcpyAsync(W.data(), d.Om, W.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+        RBC_CU(cudaStreamSynchronize(h->stream));
+        for (size_t i = 0; i < n; ++i) {
+            double *o = &cells_state[13 * i];
+            for (int a = 0; a < 3; ++a) {
+                o[a] = R[3 * i + a];
+                o[7 + a] = V[3 * i + a];
+                o[10 + a] = W[3 * i + a];
+            }
+            for (int k = 0; k < 4; ++k) o[3 + k] = q[4 * i + k];
+        }
+    }
+    return check_flags(h);
+}
+
+int rbc_stats(rbc_handle *h, rbc_stats_t *out)
+{
+    if (!h || !out) return fail(h ? &h->err : nullptr, RBC_EINVAL, "NULL argument");
+    const int par = (int)(h->step & 1);
+    launch_budget(h->d, h->P.p, par, h->stream);
+    double b[16];
+    int flags[8];
+    unsigned long long cl = 0;
+    RBC_CU(cudaMemcpyAsync(b, h->d.budget_out, sizeof b, cudaMemcpyDeviceToHost, h->stream));
+    RBC_CU(cudaMemcpyAsync(flags, h->d.flags, sizeof flags, cudaMemcpyDeviceToHost, h->stream));
+    RBC_CU(cudaMemcpyAsync(&cl, h->d.clamps, sizeof cl, cudaMemcpyDeviceToHost, h->stream));
+    RBC_CU(cudaStreamSynchronize(h->stream));
+    RBC_CU(cudaGetLastError());
+    out->step = h->step;
+    out->mass = b[0];
+    for (int a = 0; a < 3; ++a) {
+        out->p_fluid[a] = b[1 + a];
+        out->p_cells[a] = b[6 + a];
+    }
+    out->max_u = b[4];
+    out->gb_clamps = (int64_t)cl;
+    out->unstable = flags[FLAG_UNSTABLE] != 0 || b[5] > 0.0;
+    out->overflow = flags[FLAG_OVERFLOW];
+    if (out->overflow) return fail(&h->err, RBC_ENOMEM, "a device capacity was exceeded");
+    if (out->unstable) return fail(&h->err, RBC_EUNSTABLE, "NaN or |u| above the Mach guard");
+    return RBC_OK;
+}
+
+int rbc_cell_diag(rbc_handle *h, double *out)
+{
+    if (!h || !out) return fail(h ? &h->err : nullptr, RBC_EINVAL, "NULL argument");
+    if (h->d.nc == 0) return RBC_OK;
+    RBC_CU(cudaMemcpyAsync(out, h->d.diag, sizeof(double) * 21 * h->d.nc, cudaMemcpyDeviceToHost, h->stream));
+    RBC_CU(cudaStreamSynchronize(h->stream));
+    return RBC_OK;
+}
+
+int rbc_neighbors(rbc_handle *h, int *counts, int *lists, int max_per_cell)
+{
+    if (!h || !counts || (max_per_cell > 0 && !lists)) return fail(h ? &h->err : nullptr, RBC_EINVAL, "NULL argument");
+    const int n = h->d.nc;
+    if (n == 0) return RBC_OK;
+    std::vector<int> L((size_t)n * h->d.max_nbr);
+    RBC_CU(cudaMemcpyAsync(counts, h->d.nbr_count, sizeof(int) * n, cudaMemcpyDeviceToHost, h->stream));
+    RBC_CU(cudaMemcpyAsync(L.data(), h->d.nbr, sizeof(int) * L.size(), cudaMemcpyDeviceToHost, h->stream));
+    RBC_CU(cudaStreamSynchronize(h->stream));
+    int rc = RBC_OK;
+    for (int i = 0; i < n; ++i) {
+        if (counts[i] > max_per_cell) rc = RBC_ENOMEM;
+        for (int k = 0; k < std::min(counts[i], max_per_cell); ++k)
+            lists[(size_t)i * max_per_cell + k] = L[(size_t)i * h->d.max_nbr + k];
+    }
+    if (rc != RBC_OK) return fail(&h->err, rc, "a neighbour list is longer than max_per_cell");
+    int flags[8];
+    RBC_CU(cudaMemcpy(flags, h->d.flags, sizeof flags, cudaMemcpyDeviceToHost));
+    if (flags[FLAG_OVERFLOW] & (OVF_BIN | OVF_NBR)) return fail(&h->err, RBC_ENOMEM, "cell list capacity exceeded");
+    return RBC_OK;
+}
+
+int rbc_set_timing(rbc_handle *h, int capacity)
+{
+    if (!h || capacity < 0) return fail(h ? &h->err : nullptr, RBC_EINVAL, "bad argument");
+    RBC_CU(cudaStreamSynchronize(h->stream));
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    h->ev.clear();
+    h->timing_cap = 0;
+    h->timing_used = 0;
+    for (int k = 0; k < 3 * capacity; ++k) {
+        cudaEvent_t e;
+        RBC_CU(cudaEventCreate(&e));
+        h->ev.push_back(e);
+    }
+    h->timing_cap = capacity;
+    return RBC_OK;
+}
+
+int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2])
+{
+    if (!h || !ms || !count) return fail(h ? &h->err : nullptr, RBC_EINVAL, "NULL argument");
+    RBC_CU(cudaStreamSynchronize(h->stream));
+    ms[0] = ms[1] = 0.0;
+    count[0] = count[1] = 0;
+    for (int k = 0; k < h->timing_used; ++k) {
+        float a = 0.f, b = 0.f;
+        RBC_CU(cudaEventElapsedTime(&a, h->ev[3 * k], h->ev[3 * k + 1]));
+        RBC_CU(cudaEventElapsedTime(&b, h->ev[3 * k + 1], h->ev[3 * k + 2]));
+        ms[0] += b;
+        count[0]++;
+        if (h->g_cells) {
+            ms[1] += a;
+            count[1]++;
+        }
+    }
+    h->timing_used = 0;
+    h->timing_cap = 0;
+    return RBC_OK;
+}
+
+int rbc_launches_per_step(const rbc_handle *h)
+{
+    if (!h) return 0;
+    return 1 + (h->d.nc > 0 ? 3 : 0);
+}
+
+void rbc_free(rbc_handle *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->g_cells) cudaGraphExecDestroy(h->g_cells);
+    for (int k = 0; k < 2; ++k)
+        if (h->g_lb[k]) cudaGraphExecDestroy(h->g_lb[k]);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+const char *rbc_last_error(const rbc_handle *h)
+{
+    if (h) return h->err.c_str();
+    return g_thread_err.c_str();
+}
+
+}  // extern "C"

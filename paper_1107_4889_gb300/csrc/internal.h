@@ -1,0 +1,77 @@
+// internal.h -- device buffers of one solver instance and the kernel
+// launchers the host runtime (api.cu) calls.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace rbc {
+
+// Flags word indices (device int[8]).
+enum { FLAG_UNSTABLE = 0, FLAG_OVERFLOW = 1 };
+enum { OVF_BIN = 1, OVF_NBR = 2, OVF_BOX = 4 };
+
+struct Dev {
+    // lattice: planes of Np floats (N rounded up to 64), node n = x + nx*(y + ny*z)
+    int nx, ny, nz, N;
+    long long Np;
+    int walls;          // any solid node
+    float *pops[2];     // 19 planes: deviations d_p = f_p - w_p of post-collision populations
+    float *U;           // 3 planes: velocity of the last lattice pass
+    float *S;           // 6 planes (xx yy zz xy xz yz): stress of the last pass, or null
+    float *G;           // 3 planes: force density accumulated by the cells (zeroed by the pass)
+    float *theta;       // 1 plane: sum of smoothed characteristic functions (zeroed by the pass)
+    float *rho;         // 1 plane: density for field output
+    uint8_t *solid;     // N bytes or null
+    // cells (SoA FP64)
+    int nc;
+    double *R, *q, *V, *Om;  // 3n, 4n, 3n, 3n
+    double *A;               // 6n shape tensors (xx yy zz xy xz yz)
+    double *Fm, *Tm;         // 3n GB force, 3n GB torque (lab)
+    int *have;               // n: cached combined force exists (not the first step)
+    double *diag;            // 21n per-cell diagnostics of the last step
+    // cell list
+    int nb[3], nbins, bin_cap;
+    double bin_size[3];
+    int *bin_count, *bin_cells, *cell_bin;
+    int max_nbr;
+    int *nbr, *nbr_count;
+    // wall particles binned in the same grid
+    int nw;
+    int *wall_start;  // nbins + 1
+    int *wall_xyz;    // 3 * nw, bin-sorted
+    // status
+    int *flags;                     // 8 ints
+    unsigned long long *clamps;     // 1
+    double *budget_part;            // budget_blocks * 8
+    double *budget_out;             // 16: mass, p_fluid(3), max|u|, NaN count, p_cells(3)
+    int budget_blocks;
+};
+
+struct Params {
+    float gext[3];
+    float tau0, delta, kappa, alpha;
+    float mach2;
+    float xi[3];
+    double a2[3];
+    double M, I[3], eT, eR, gT, gR;
+    double eps0, smin_cc, smin_w, rw2, rho_floor, rho_cut, rc2, rcw2;
+    int periodic[3];
+    int box_max;  // largest shape box (nodes)
+    int box_dim;  // largest shape box edge (nodes)
+};
+
+// lb.cu
+void launch_lb(const Dev &d, const Params &p, int parity, cudaStream_t s);
+void launch_rho(const Dev &d, int parity, cudaStream_t s);
+void launch_budget(const Dev &d, const Params &p, int parity, cudaStream_t s);
+int budget_blocks_for(int N);
+
+// cells.cu
+void launch_bin(const Dev &d, const Params &p, cudaStream_t s);
+void launch_gb(const Dev &d, const Params &p, cudaStream_t s);
+void launch_cells(const Dev &d, const Params &p, cudaStream_t s);
+size_t cells_smem_bytes(const Params &p);
+
+}  // namespace rbc

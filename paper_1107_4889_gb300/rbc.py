@@ -1,0 +1,309 @@
+"""Thin Python binding of the C ABI in include/rbc.h (ctypes).
+
+Argument marshalling only: every step of the coupled time step runs in the
+CUDA kernels of ``lib/librbc.so``.  PyTorch supplies the device workspace
+(one uint8 tensor from its caching allocator) and the CUDA stream.  There is
+no CPU fallback: if the library is missing or no GPU is present, the calls
+raise.
+
+The functions carry the C names (``rbc_init``, ``rbc_step``, ``rbc_fields``,
+``rbc_stats`` ...); :class:`Solver` bundles them with the workspace it owns.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "librbc.so")
+
+RBC_OK, RBC_EINVAL, RBC_ENOMEM, RBC_ECUDA, RBC_EUNSTABLE, RBC_ETIMEOUT = 0, -1, -2, -3, -4, -5
+_NAMES = {RBC_EINVAL: "EINVAL", RBC_ENOMEM: "ENOMEM", RBC_ECUDA: "ECUDA",
+          RBC_EUNSTABLE: "EUNSTABLE", RBC_ETIMEOUT: "ETIMEOUT"}
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_U8 = ctypes.POINTER(ctypes.c_uint8)
+
+
+class rbc_geometry(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("periodic", ctypes.c_int * 3), ("solid", _U8), ("body_force", ctypes.c_double * 3)]
+
+
+class rbc_cells(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("pos", _D), ("quat", _D), ("vel", _D), ("omega_body", _D)]
+
+
+class rbc_params(ctypes.Structure):
+    _fields_ = [("tau0", ctypes.c_double), ("delta", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("gamma_T", ctypes.c_double), ("gamma_R", ctypes.c_double),
+                ("alpha_tt", ctypes.c_double), ("eps0", ctypes.c_double),
+                ("xi", ctypes.c_double * 3), ("semi_axes", ctypes.c_double * 3),
+                ("mass", ctypes.c_double), ("inertia", ctypes.c_double * 3),
+                ("sigma_min_wall", ctypes.c_double), ("wall_radius", ctypes.c_double),
+                ("rho_floor", ctypes.c_double), ("r_cut", ctypes.c_double),
+                ("r_cut_wall", ctypes.c_double), ("mach_max", ctypes.c_double),
+                ("bin_capacity", ctypes.c_int), ("max_neighbors", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class rbc_stats_t(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("mass", ctypes.c_double),
+                ("p_fluid", ctypes.c_double * 3), ("p_cells", ctypes.c_double * 3),
+                ("max_u", ctypes.c_double), ("gb_clamps", ctypes.c_int64),
+                ("unstable", ctypes.c_int32), ("overflow", ctypes.c_int32)]
+
+
+#: symbols include/rbc.h declares
+EXPORTS = ["rbc_default_params", "rbc_workspace_size", "rbc_init", "rbc_step", "rbc_fields",
+           "rbc_stats", "rbc_cell_diag", "rbc_neighbors", "rbc_set_timing", "rbc_kernel_times",
+           "rbc_launches_per_step", "rbc_free", "rbc_last_error"]
+
+_lib = None
+
+
+class RbcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    """Load librbc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_1107_4889_gb300.build` (nvcc, sm_103a)")
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    L.rbc_default_params.argtypes = [P(rbc_params)]
+    L.rbc_default_params.restype = None
+    L.rbc_workspace_size.argtypes = [P(rbc_geometry), P(rbc_cells), P(rbc_params), P(ctypes.c_size_t)]
+    L.rbc_init.argtypes = [P(rbc_geometry), P(rbc_cells), P(rbc_params), ctypes.c_void_p, ctypes.c_size_t,
+                           P(ctypes.c_void_p)]
+    L.rbc_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    L.rbc_fields.argtypes = [ctypes.c_void_p, _D, _D, _D]
+    L.rbc_stats.argtypes = [ctypes.c_void_p, P(rbc_stats_t)]
+    L.rbc_cell_diag.argtypes = [ctypes.c_void_p, _D]
+    L.rbc_neighbors.argtypes = [ctypes.c_void_p, _I, _I, ctypes.c_int]
+    L.rbc_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.rbc_kernel_times.argtypes = [ctypes.c_void_p, _D, _I64]
+    L.rbc_launches_per_step.argtypes = [ctypes.c_void_p]
+    L.rbc_free.argtypes = [ctypes.c_void_p]
+    L.rbc_free.restype = None
+    L.rbc_last_error.argtypes = [ctypes.c_void_p]
+    L.rbc_last_error.restype = ctypes.c_char_p
+    for name in ("rbc_workspace_size", "rbc_init", "rbc_step", "rbc_fields", "rbc_stats", "rbc_cell_diag",
+                 "rbc_neighbors", "rbc_set_timing", "rbc_kernel_times", "rbc_launches_per_step"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(code, handle=None):
+    if code != RBC_OK:
+        msg = load().rbc_last_error(handle)
+        raise RbcError(code, msg.decode() if msg else "")
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+class _Inputs:
+    """Keeps the numpy buffers the ctypes structs point into alive."""
+
+    def __init__(self, geometry, cells, params, stream):
+        nx, ny, nz = int(geometry["nx"]), int(geometry["ny"]), int(geometry["nz"])
+        self.N = nx * ny * nz
+        g = rbc_geometry()
+        g.nx, g.ny, g.nz = nx, ny, nz
+        per = geometry.get("periodic", (1, 1, 1))
+        bf = geometry.get("body_force", (0.0, 0.0, 0.0))
+        for a in range(3):
+            g.periodic[a] = int(per[a])
+            g.body_force[a] = float(bf[a])
+        solid = geometry.get("solid")
+        self.solid = None if solid is None else np.ascontiguousarray(np.asarray(solid, np.uint8).reshape(-1))
+        g.solid = None if self.solid is None else self.solid.ctypes.data_as(_U8)
+        self.geom = g
+        c = rbc_cells()
+        n = 0 if cells is None else int(np.asarray(cells["pos"]).shape[0])
+        self.n = n
+        c.n = n
+        if n:
+            self.pos = np.ascontiguousarray(np.asarray(cells["pos"], np.float64).reshape(n, 3))
+            self.quat = np.ascontiguousarray(np.asarray(cells["quat"], np.float64).reshape(n, 4))
+            v, w = cells.get("vel"), cells.get("omega")
+            self.vel = None if v is None else np.ascontiguousarray(np.asarray(v, np.float64).reshape(n, 3))
+            self.om = None if w is None else np.ascontiguousarray(np.asarray(w, np.float64).reshape(n, 3))
+            c.pos, c.quat, c.vel, c.omega_body = _dp(self.pos), _dp(self.quat), _dp(self.vel), _dp(self.om)
+        self.cells = c
+        p = rbc_params()
+        load().rbc_default_params(ctypes.byref(p))
+        for k, v in (params or {}).items():
+            if k in ("xi", "semi_axes", "inertia"):
+                arr = getattr(p, k)
+                for a in range(3):
+                    arr[a] = float(v[a])
+            elif k in ("bin_capacity", "max_neighbors"):
+                setattr(p, k, int(v))
+            elif k == "stream":
+                continue
+            else:
+                setattr(p, k, float(v))
+        p.stream = stream
+        self.params = p
+
+
+def rbc_default_params():
+    p = rbc_params()
+    load().rbc_default_params(ctypes.byref(p))
+    return p
+
+
+def rbc_workspace_size(geometry, cells, params) -> int:
+    ins = _Inputs(geometry, cells, params, None)
+    nb = ctypes.c_size_t(0)
+    _check(load().rbc_workspace_size(ctypes.byref(ins.geom), ctypes.byref(ins.cells), ctypes.byref(ins.params),
+                                     ctypes.byref(nb)))
+    return int(nb.value)
+
+
+def rbc_init(geometry, cells, params, workspace_ptr: int, workspace_bytes: int, stream: int | None):
+    ins = _Inputs(geometry, cells, params, stream)
+    h = ctypes.c_void_p()
+    _check(load().rbc_init(ctypes.byref(ins.geom), ctypes.byref(ins.cells), ctypes.byref(ins.params),
+                           ctypes.c_void_p(workspace_ptr), ctypes.c_size_t(workspace_bytes), ctypes.byref(h)))
+    return h
+
+
+def rbc_step(h, n: int = 1):
+    _check(load().rbc_step(h, int(n)), h)
+
+
+def rbc_fields(h, N: int, n: int, want_rho=True, want_u=True, want_cells=True):
+    rho = np.zeros(N) if want_rho else None
+    u = np.zeros(3 * N) if want_u else None
+    cs = np.zeros(13 * max(n, 1)) if want_cells else None
+    _check(load().rbc_fields(h, _dp(rho), _dp(u), _dp(cs)), h)
+    out = {}
+    if want_rho:
+        out["rho"] = rho
+    if want_u:
+        out["u"] = u.reshape(N, 3)
+    if want_cells:
+        cs = cs[: 13 * n].reshape(n, 13)
+        out.update(pos=cs[:, 0:3], quat=cs[:, 3:7], vel=cs[:, 7:10], omega=cs[:, 10:13])
+    return out
+
+
+def rbc_stats(h):
+    s = rbc_stats_t()
+    code = load().rbc_stats(h, ctypes.byref(s))
+    out = dict(step=int(s.step), mass=s.mass, p_fluid=np.array(s.p_fluid[:]), p_cells=np.array(s.p_cells[:]),
+               max_u=s.max_u, gb_clamps=int(s.gb_clamps), unstable=int(s.unstable), overflow=int(s.overflow))
+    _check(code, h)
+    return out
+
+
+def rbc_cell_diag(h, n: int):
+    out = np.zeros(21 * max(n, 1))
+    _check(load().rbc_cell_diag(h, _dp(out)), h)
+    out = out[: 21 * n].reshape(n, 21)
+    return dict(F_mech=out[:, 0:3], tau_mech=out[:, 3:6], u_s=out[:, 6:9], omega_s=out[:, 9:12],
+                T_S=out[:, 12:15], J=out[:, 15:18], L=out[:, 18:21])
+
+
+def rbc_neighbors(h, n: int, max_per_cell: int = 128):
+    counts = np.zeros(max(n, 1), dtype=np.int32)
+    lists = np.zeros(max(n, 1) * max_per_cell, dtype=np.int32)
+    _check(load().rbc_neighbors(h, counts.ctypes.data_as(_I), lists.ctypes.data_as(_I), max_per_cell), h)
+    lists = lists.reshape(-1, max_per_cell)
+    return [lists[i, : counts[i]].copy() for i in range(n)]
+
+
+def rbc_set_timing(h, capacity: int):
+    _check(load().rbc_set_timing(h, int(capacity)), h)
+
+
+def rbc_kernel_times(h):
+    ms = np.zeros(2)
+    cnt = np.zeros(2, dtype=np.int64)
+    _check(load().rbc_kernel_times(h, _dp(ms), cnt.ctypes.data_as(_I64)), h)
+    return ms, cnt
+
+
+def rbc_launches_per_step(h) -> int:
+    return int(load().rbc_launches_per_step(h))
+
+
+def rbc_free(h):
+    if h:
+        load().rbc_free(h)
+
+
+class Solver:
+    """One coupled LB + RBC solve on the current CUDA device.
+
+    ``geometry``: dict(nx, ny, nz, periodic, solid, body_force); ``cells``:
+    dict(pos, quat, vel, omega) or None; ``params``: dict of rbc_params
+    fields (missing keys take the paper's values)."""
+
+    def __init__(self, geometry, cells, params=None, device=None, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("the RBC solver needs a CUDA GPU")
+        load()
+        self.device = torch.device("cuda" if device is None else device)
+        self.N = int(geometry["nx"]) * int(geometry["ny"]) * int(geometry["nz"])
+        self.n = 0 if cells is None else int(np.asarray(cells["pos"]).shape[0])
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream() if stream is None else stream
+            self.workspace_bytes = rbc_workspace_size(geometry, cells, params)
+            self.workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+            self.handle = rbc_init(geometry, cells, params, self.workspace.data_ptr(), self.workspace_bytes,
+                                   self.stream.cuda_stream)
+
+    def step(self, n=1):
+        rbc_step(self.handle, n)
+
+    def fields(self, rho=True, u=True, cells=True):
+        return rbc_fields(self.handle, self.N, self.n, rho, u, cells)
+
+    def stats(self):
+        return rbc_stats(self.handle)
+
+    def cell_diag(self):
+        return rbc_cell_diag(self.handle, self.n)
+
+    def neighbors(self, max_per_cell=128):
+        return rbc_neighbors(self.handle, self.n, max_per_cell)
+
+    def set_timing(self, capacity):
+        rbc_set_timing(self.handle, capacity)
+
+    def kernel_times(self):
+        return rbc_kernel_times(self.handle)
+
+    def launches_per_step(self):
+        return rbc_launches_per_step(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rbc_free(self.handle)
+            self.handle = None
+        self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

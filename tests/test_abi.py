@@ -1,0 +1,87 @@
+"""The C-ABI library loads and exports every entry point include/rbc.h
+declares; host-only entry points (defaults, workspace sizing, validation)
+work without a GPU.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1107_4889_gb300 import build as B
+from paper_1107_4889_gb300 import rbc
+from paper_1107_4889_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return rbc.load()
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(rbc_\w+)\s*\(", txt, re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert len(declared) >= 12
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(rbc.EXPORTS) == set(declared)
+
+
+def test_default_params_are_the_papers(lib):
+    p = rbc.rbc_default_params()
+    assert (p.tau0, p.delta, p.kappa, p.gamma_T, p.gamma_R, p.alpha_tt) == (1.0, 2.0, 20.0, 0.1, 0.1, 0.04)
+    assert list(p.xi) == [4.0, 4.0, 1.5] and p.mass == 10.0 and list(p.inertia) == [1000.0] * 3
+
+
+def test_struct_layouts_match_header(lib):
+    assert ctypes.sizeof(rbc.rbc_geometry) == 24 + 8 + 24
+    assert ctypes.sizeof(rbc.rbc_cells) == 8 + 4 * 8
+    assert ctypes.sizeof(rbc.rbc_stats_t) == 8 * 10 + 8
+    assert rbc.rbc_params.stream.offset == ctypes.sizeof(rbc.rbc_params) - 8
+
+
+def test_workspace_size_scales_with_problem(lib):
+    g, c, p = wl.box_workload()
+    s1 = rbc.rbc_workspace_size(g, c, p)
+    N = 32 ** 3
+    assert s1 > 2 * 19 * 4 * N  # two population copies at least
+    g2, c2, p2 = wl.channel_workload()
+    s2 = rbc.rbc_workspace_size(g2, c2, p2)
+    assert s2 > 2 * 19 * 4 * 64 * 64 * 256
+
+
+def test_validation_rejects_bad_problems(lib):
+    g, c, p = wl.box_workload()
+    with pytest.raises(rbc.RbcError) as e:
+        rbc.rbc_workspace_size(g, c, dict(p, tau0=0.4))
+    assert e.value.code == rbc.RBC_EINVAL
+    bad = dict(g, periodic=(1, 0, 1))  # non-periodic y without solid end planes
+    with pytest.raises(rbc.RbcError):
+        rbc.rbc_workspace_size(bad, c, p)
+    tiny = wl.periodic_box(8)
+    with pytest.raises(rbc.RbcError):  # support box larger than the lattice
+        rbc.rbc_workspace_size(tiny, wl.cells_dict(np.array([[4.0, 4.0, 4.0]]), np.array([[1.0, 0, 0, 0]])), p)
+    gch, cch, pch = wl.channel_workload(nx=32, ny=32, nz=32, ncells=10)
+    cch["pos"][0, 1] = 40.0  # outside the walled axis
+    with pytest.raises(rbc.RbcError):
+        rbc.rbc_workspace_size(gch, cch, pch)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    import importlib
+    mod = importlib.reload(rbc)
+    mod._lib = None
+    with pytest.raises(RuntimeError):
+        mod.load(str(tmp_path / "librbc.so"))
+    importlib.reload(rbc)

@@ -1,0 +1,218 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (FP32 storage and arithmetic on the lattice, FP64 cell state):
+  - velocity and density: relative L2 <= 1e-5 after up to 100 steps;
+  - per-cell force, torque and impulses: relative (to the largest value over
+    the cells) <= 1e-5; the smeared vorticity relative to the larger of its
+    own largest value and the velocity-gradient scale |u~| / xi_min;
+  - positions and orientations: relative to how far the cells moved / turned;
+  - cell-pair candidate lists: bit-exact.
+"""
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+from oracle import oracle as orc
+from paper_1107_4889_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1107_4889_gb300 import build
+    build.build()
+
+
+def _solver(geom, cells, params):
+    from paper_1107_4889_gb300.rbc import Solver
+    return Solver(geom, cells, params)
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def _compare(geom, cells, params, steps, tol=TOL, check_cells=True):
+    o = orc.Oracle(geom, cells, params)
+    s = _solver(geom, cells, params)
+    o.step(steps)
+    s.step(steps)
+    rho_o, u_o, _ = o.fields()
+    f = s.fields()
+    fluid = np.ones(o.N, bool) if geom["solid"] is None else geom["solid"].reshape(-1) == 0
+    err_u = rel_l2(f["u"][fluid], u_o[fluid])
+    err_rho = rel_l2(f["rho"][fluid], rho_o[fluid])
+    assert err_u <= tol, f"u rel-L2 {err_u:.3e}"
+    assert err_rho <= tol, f"rho rel-L2 {err_rho:.3e}"
+    out = dict(err_u=err_u, err_rho=err_rho,
+               err_drho=rel_l2(f["rho"][fluid] - 1.0, rho_o[fluid] - 1.0))
+    if check_cells and o.n:
+        dg, do = s.cell_diag(), o.diag()
+        # the smeared vorticity is a difference quotient of the FP32-stored
+        # velocity: in a nearly uniform flow it sits at that storage's noise
+        # floor, so its scale is at least the velocity-gradient scale
+        # |u~| / xi_min across the support
+        grad_scale = np.abs(do["u_s"]).max() / min(params["xi"])
+        for k in ("J", "L", "F_mech", "tau_mech", "T_S", "u_s", "omega_s"):
+            scale = np.abs(do[k]).max()
+            if k == "omega_s":
+                scale = max(scale, grad_scale)
+            if scale == 0:
+                assert np.abs(dg[k]).max() == 0, k
+                continue
+            e = np.abs(dg[k] - do[k]).max() / scale
+            assert e <= tol, f"{k}: {e:.3e}"
+            out["err_" + k] = e
+        co = o.cells()
+        dims = np.array([geom["nx"], geom["ny"], geom["nz"]], float)
+
+        def mi(d):
+            return d - dims * np.round(d / dims) * np.asarray(geom["periodic"])
+
+        # positions and orientations: error relative to how far the cells moved
+        disp = np.abs(mi(co["pos"] - np.asarray(cells["pos"]))).max()
+        assert np.abs(mi(f["pos"] - co["pos"])).max() <= tol * disp + 1e-12
+        Qg = Rotation.from_quat(f["quat"][:, [1, 2, 3, 0]])
+        Qo = Rotation.from_matrix(co["Q"])
+        Q0 = Rotation.from_quat(np.asarray(cells["quat"])[:, [1, 2, 3, 0]])
+        turned = (Qo * Q0.inv()).magnitude().max()
+        assert (Qg * Qo.inv()).magnitude().max() <= tol * turned + 1e-12
+        vs = np.abs(co["vel"]).max()
+        assert np.abs(f["vel"] - co["vel"]).max() <= tol * max(vs, 1e-30)
+        out["err_pos"] = np.abs(mi(f["pos"] - co["pos"])).max() / max(disp, 1e-30)
+    s.close()
+    o.close()
+    return out
+
+
+def test_fluid_only_uniform_force_matches_closed_form_and_oracle():
+    geom = wl.periodic_box(16, 12, 20, body_force=(1e-5, -2e-5, 5e-6))
+    s = _solver(geom, None, wl.params())
+    s.step(50)
+    f = s.fields()
+    G = np.array([1e-5, -2e-5, 5e-6])
+    # pass n (from 0) reports u = (n + 1/2) G: 49.5 G after 50 passes
+    assert np.allclose(f["u"], 49.5 * G, rtol=2e-6)
+    s.close()
+    _compare(geom, None, wl.params(), 50)
+
+
+def test_ragged_lattice_and_walls_fluid_only():
+    """17 x 19 x 23 nodes (not a multiple of the block size) with solid walls
+    and an obstacle, driven flow, 120 steps."""
+    geom = wl.plane_channel(17, 19, 23, body_force=(2e-6, 0.0, 1e-6))
+    geom["solid"][5:9, 7:10, 6:9] = 1
+    _compare(geom, None, wl.params(), 120)
+
+
+def test_coupled_periodic_box_32_cells_100_steps():
+    """The 32^3 box with 32 cells (hematocrit 9.8 %), force 1e-6 along x."""
+    geom, cells, params = wl.box_workload()
+    r = _compare(geom, cells, params, 100)
+    print("box32:", r)
+
+
+def test_coupled_box_with_cell_velocities_and_contacts():
+    """Cells start with velocities towards each other so Gay-Berne forces act."""
+    geom, cells, params = wl.box_workload(n=24, ncells=8, body_force=(0, 0, 0), seed=21)
+    rng = np.random.default_rng(4)
+    cells["vel"] = rng.normal(size=(8, 3)) * 0.01
+    cells["omega"] = rng.normal(size=(8, 3)) * 1e-3
+    r = _compare(geom, cells, dict(params, eps0=0.01), 60)
+    print("contacts:", r)
+
+
+def test_coupled_walled_channel():
+    geom, cells, params = wl.channel_workload(nx=24, ny=28, nz=32, ncells=12, body_force=(5e-6, 0, 0), seed=33)
+    rng = np.random.default_rng(5)
+    cells["vel"] = rng.normal(size=(12, 3)) * 3e-3  # drive some cells into the walls
+    r = _compare(geom, cells, params, 80)
+    print("channel:", r)
+
+
+def test_single_cell_across_periodic_boundary():
+    geom = wl.periodic_box(20, body_force=(0, 3e-6, 0))
+    cells = wl.cells_dict(np.array([[19.6, 0.3, 10.2]]), np.array([[0.3, 0.8, -0.2, 0.4]]))
+    cells["vel"] = np.array([[1e-3, -2e-3, 5e-4]])
+    _compare(geom, cells, wl.params(), 60)
+
+
+def test_no_alpha_and_no_viscosity_contrast():
+    geom, cells, params = wl.box_workload(n=24, ncells=6, seed=9)
+    _compare(geom, cells, dict(params, alpha_tt=0.0, delta=0.0), 40)
+
+
+def test_neighbor_lists_bit_exact():
+    """Dense random positions plus pairs placed at the candidate radius to
+    within rounding; eps0 = 0 so the overlapping cells exert no force."""
+    rng = np.random.default_rng(17)
+    L = 48
+    geom = wl.periodic_box(L)
+    n = 400
+    pos = rng.random((n, 3)) * L
+    rc = wl.PAPER_PARAMS["r_cut"]
+    for k in range(20):  # pairs within an ulp or so of r_cut
+        dirn = rng.normal(size=3)
+        dirn /= np.linalg.norm(dirn)
+        pos[2 * k + 1] = np.mod(pos[2 * k] + dirn * rc * (1 + (k % 5 - 2) * 1e-16), L)
+    pos[pos >= L] -= L
+    cells = wl.cells_dict(pos, wl.random_quaternions(rng, n))
+    params = wl.params(eps0=0.0, bin_capacity=64, max_neighbors=128)
+    o = orc.Oracle(geom, cells, params)
+    ref = {tuple(p) for p in o.neighbor_pairs()}
+    s = _solver(geom, cells, params)
+    s.step(1)
+    lists = s.neighbors(128)
+    got = set()
+    for i, lst in enumerate(lists):
+        assert np.all(np.diff(lst) > 0)
+        for j in lst:
+            got.add((min(i, j), max(i, j)))
+            assert i in lists[j]
+    assert got == ref and len(ref) > 100
+
+
+def test_momentum_budget_on_gpu():
+    geom, cells, params = wl.box_workload(n=24, ncells=6, body_force=(0, 0, 0), seed=5)
+    rng = np.random.default_rng(1005)
+    cells["vel"] = rng.normal(size=(6, 3)) * 1e-3
+    s = _solver(geom, cells, params)
+    b0 = s.stats()
+    P0 = b0["p_fluid"] + b0["p_cells"]
+    scale = np.abs(cells["vel"]).sum() * params["mass"]
+    s.step(50)
+    b = s.stats()
+    assert abs(b["mass"] - b0["mass"]) < 1e-6 * b0["mass"]
+    assert np.allclose(b["p_fluid"] + b["p_cells"], P0, atol=1e-5 * scale)
+    assert np.abs(b["p_fluid"]).max() > 1e-3 * scale
+
+
+def test_instability_flag_is_reported():
+    """A body force far beyond the stability bound (|F| ~ 0.1 of Sec. 3)
+    trips the Mach guard; the guard reports on the host, nothing faults."""
+    from paper_1107_4889_gb300.rbc import RbcError, RBC_EUNSTABLE
+    geom = wl.periodic_box(8, body_force=(0.05, 0, 0))
+    s = _solver(geom, None, wl.params())
+    s.step(20)
+    with pytest.raises(RbcError) as e:
+        s.stats()
+    assert e.value.code == RBC_EUNSTABLE
+
+
+def test_full_size_channel_sampled_against_oracle():
+    """The 64 x 64 x 256 channel with 3,650 cells in the launch
+    configuration the benchmark times: 6 steps compared with the oracle on
+    every field and every cell."""
+    geom, cells, params = wl.channel_workload()
+    cells["vel"] = np.random.default_rng(2).normal(size=(len(cells["pos"]), 3)) * 1e-3
+    r = _compare(geom, cells, params, 6)
+    print("channel full size:", r)
