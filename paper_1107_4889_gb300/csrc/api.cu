@@ -17,6 +17,7 @@
 
 #include "../../include/rbc.h"
 #include "internal.h"
+#include "rbc_device.cuh"
 
 using namespace rbc;
 
@@ -138,6 +139,8 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     const double mach = q.mach_max > 0.0 ? q.mach_max : 0.3;
     p.mach2 = (float)(mach * mach);
     p.M = q.mass;
+    p.iM = 1.0 / q.mass;
+    for (int a = 0; a < 3; ++a) p.iI[a] = 1.0 / q.inertia[a];
     p.gT = q.gamma_T;
     p.gR = q.gamma_R;
     p.eT = std::exp(-0.5 * q.gamma_T);
@@ -164,11 +167,12 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     if (nc > 0) {
         if (bdim > std::min(g->nx, std::min(g->ny, g->nz)))
             return fail(err, RBC_EINVAL, "shape-function support does not fit in the lattice");
-        if ((size_t)p.box_max * sizeof(float) > 200u * 1024u)
+        if (cells_smem_bytes(p) > 200u * 1024u)
             return fail(err, RBC_EINVAL, "shape-function support too large for shared memory");
         const double bin_min = std::max(rc, rcw);
         for (int a = 0; a < 3; ++a) {
-            if (P.per[a] && 2.0 * rc >= dims[a]) return fail(err, RBC_EINVAL, "r_cut must be below half the box");
+            // half the box must exceed r_cut by more than the FP32 prefilter band
+            if (P.per[a] && 2.0 * (rc + 0.05) >= dims[a]) return fail(err, RBC_EINVAL, "r_cut must be below half the box");
             P.nb[a] = std::max(1, (int)std::floor(dims[a] / bin_min));
             P.bin_size[a] = (double)dims[a] / P.nb[a];
         }
@@ -246,6 +250,7 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.theta = P.nc > 0 ? cv.take<float>(Np) : nullptr;
     d.rho = cv.take<float>(Np);
     d.solid = P.any_solid ? cv.take<uint8_t>(Np) : nullptr;
+    d.links = P.any_solid ? cv.take<uint32_t>(Np) : nullptr;
     const size_t n = (size_t)std::max(P.nc, 1);
     d.nc = P.nc;
     d.R = cv.take<double>(3 * n);
@@ -253,10 +258,15 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.V = cv.take<double>(3 * n);
     d.Om = cv.take<double>(3 * n);
     d.A = cv.take<double>(6 * n);
+    d.Rf = cv.take<float>(3 * n);
+    d.Af = cv.take<float>(6 * n);
     d.Fm = cv.take<double>(3 * n);
     d.Tm = cv.take<double>(3 * n);
     d.have = cv.take<int>(n);
     d.diag = cv.take<double>(21 * n);
+    d.hdr = cv.take<float>(kHdrWords * n);
+    d.part = cv.take<double>(10 * n);
+    d.JL = cv.take<float>(6 * n);
     for (int a = 0; a < 3; ++a) {
         d.nb[a] = P.nb[a];
         d.bin_size[a] = P.bin_size[a];
@@ -321,7 +331,9 @@ static void body_cells(rbc_handle *h, int)
 {
     launch_bin(h->d, h->P.p, h->stream);
     launch_gb(h->d, h->P.p, h->stream);
-    launch_cells(h->d, h->P.p, h->stream);
+    launch_sample(h->d, h->P.p, h->stream);
+    launch_rigid(h->d, h->P.p, h->stream);
+    launch_spread(h->d, h->P.p, h->stream);
 }
 
 static void body_lb(rbc_handle *h, int parity) { launch_lb(h->d, h->P.p, parity, h->stream); }
@@ -411,9 +423,23 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
         if (d.G) RBC_CU(cudaMemsetAsync(d.G, 0, 3 * Np * sizeof(float), s));
         if (d.theta) RBC_CU(cudaMemsetAsync(d.theta, 0, Np * sizeof(float), s));
         RBC_CU(cudaMemsetAsync(d.rho, 0, Np * sizeof(float), s));
+        std::vector<uint32_t> links;
         if (d.solid) {
             RBC_CU(cudaMemsetAsync(d.solid, 0, Np, s));
             RBC_CU(cudaMemcpyAsync(d.solid, geom->solid, (size_t)P.N, cudaMemcpyHostToDevice, s));
+            // per-node link mask in the library's velocity ordering: bit p set
+            // when the downstream node x + c_p is solid, bit 31 when x is solid
+            links.assign((size_t)P.N, 0u);
+            for (int z = 0; z < P.nz; ++z)
+                for (int y = 0; y < P.ny; ++y)
+                    for (int x = 0; x < P.nx; ++x) {
+                        const long long n = node(P, x, y, z);
+                        uint32_t m = geom->solid[n] ? (1u << 31) : 0u;
+                        for (int p = 1; p < kQ; ++p)
+                            if (geom->solid[node(P, x + cx(p), y + cy(p), z + cz(p))]) m |= 1u << p;
+                        links[n] = m;
+                    }
+            RBC_CU(cudaMemcpyAsync(d.links, links.data(), links.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
         }
         RBC_CU(cudaMemsetAsync(d.flags, 0, 8 * sizeof(int), s));
         RBC_CU(cudaMemsetAsync(d.clamps, 0, sizeof(unsigned long long), s));
@@ -456,6 +482,9 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
             (void)smem;
         }
         RBC_CU(cudaStreamSynchronize(s));
+        prepare_lb(h->d);
+        if (n > 0) prepare_cells(h->P.p);
+        RBC_CU(cudaGetLastError());
         if (n > 0) {
             int r = capture(h, body_cells, 0, &h->g_cells);
             if (r != RBC_OK) return r;
@@ -655,7 +684,7 @@ int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2])
 int rbc_launches_per_step(const rbc_handle *h)
 {
     if (!h) return 0;
-    return 1 + (h->d.nc > 0 ? 3 : 0);
+    return 1 + (h->d.nc > 0 ? 5 : 0);
 }
 
 void rbc_free(rbc_handle *h)

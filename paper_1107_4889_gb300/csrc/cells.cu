@@ -1,20 +1,28 @@
 // cells.cu -- per-cell work of the coupled step.
 //
-//   k_bin    one thread per cell: cell-list bin (FP64 position / bin size),
-//            slot in a fixed-capacity bin, and the shape tensor A = Q S^2 Q^T.
-//   k_gb     one thread per cell: candidate partners from the 27 surrounding
-//            bins (FP64 distance test without fused multiply-add, kept sorted
-//            by partner index), Gay-Berne forces and torques over them and
-//            over the wall particles binned in the same grid (Sec. 2.5,
-//            App. B).  Each pair is evaluated once from each side, so every
-//            cell sums its own force in a fixed order (no atomics).
-//   k_cells  one CTA per cell: the cell's shape-function weights on a box
-//            around its support staged in shared memory, sampling of the
-//            fluid (Eqs. vel, vort, pheno_torque_diss) with a block
-//            reduction, the rigid-body update by one thread (App. A), and the
-//            spreading of the reaction force density and the smoothed
-//            characteristic function to the lattice with atomics (Sec. 2.2,
-//            Eq. enhance-viscosity).
+//   k_bin     one thread per cell: cell-list bin and slot (FP64 position / bin
+//             size), the shape tensor A = Q S^2 Q^T, and the cell's shape
+//             header (orientation, the box around its support, centre node).
+//   k_gb      one warp per cell: the 27 surrounding bins are scanned by the
+//             lanes with the exact FP64 distance test (no fused multiply-add),
+//             passing partners are compacted with a ballot and ranked into a
+//             list sorted by partner index; the lanes then evaluate the
+//             Gay-Berne pairs and the wall particles (Sec. 2.5, App. B).  A
+//             conservative FP32 reduced-distance test skips pairs that are
+//             certainly outside the range, so FP64 runs only for pairs that
+//             interact.  Each pair is evaluated from both sides: every cell
+//             sums its own force in a fixed order, without atomics.
+//   k_sample  one CTA per cell: shape-function weights on the box staged in
+//             shared memory, block reduction of the normalisation and of the
+//             sampled fields (Eqs. vel, vort, pheno_torque_diss).
+//   k_rigid   one thread per cell, FP64: combined force and torque, the
+//             rigid-body update (App. A) and the hydrodynamic impulses.
+//   k_spread  one CTA per cell: the same weights recomputed in shared memory,
+//             the reaction force density and the smoothed characteristic
+//             function added to the lattice with atomics (Sec. 2.2, Eq.
+//             enhance-viscosity).
+#include <algorithm>
+
 #include "internal.h"
 #include "rbc_device.cuh"
 
@@ -23,50 +31,105 @@ namespace rbc {
 namespace {
 
 constexpr int kBinThreads = 128;
-constexpr int kGbThreads = 64;
-constexpr int kCellThreads = 256;
+constexpr int kGbWarps = 4;
+constexpr int kCellThreads = 128;
+constexpr int kRigidThreads = 32;
 constexpr int kMaxNbr = 128;
 
-__global__ void __launch_bounds__(kBinThreads)
-k_bin(const double *__restrict__ R, const double *__restrict__ q, double *__restrict__ A,
-      int *__restrict__ cell_bin, int *__restrict__ bin_count, int *__restrict__ bin_cells,
-      int *__restrict__ flags, int nc, int nb0, int nb1, int nb2, double bs0, double bs1,
-      double bs2, int cap, double a20, double a21, double a22)
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// ---------------------------------------------------------------------------
+// k_bin
+// ---------------------------------------------------------------------------
+struct BinArgs {
+    const double *R, *q;
+    double *A;
+    float *Rf, *Af;
+    float *hdr;
+    int *cell_bin, *bin_count, *bin_cells, *flags;
+    int nc, nb[3], cap, dims[3], box_dim;
+    double bs[3], a2[3];
+    float xi[3];
+};
+
+__global__ void __launch_bounds__(kBinThreads) k_bin(BinArgs g)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nc) return;
-    const int nb[3] = {nb0, nb1, nb2};
-    const double bs[3] = {bs0, bs1, bs2};
+    if (i >= g.nc) return;
+    double Rd[3];
     int b[3];
     for (int a = 0; a < 3; ++a) {
-        int k = (int)floor(R[3 * i + a] / bs[a]);
-        b[a] = k < 0 ? 0 : (k >= nb[a] ? nb[a] - 1 : k);
+        Rd[a] = g.R[3 * i + a];
+        int k = (int)floor(Rd[a] / g.bs[a]);
+        b[a] = k < 0 ? 0 : (k >= g.nb[a] ? g.nb[a] - 1 : k);
     }
-    const int bin = b[0] + nb0 * (b[1] + nb1 * b[2]);
-    cell_bin[i] = bin;
-    const int slot = atomicAdd(&bin_count[bin], 1);
-    if (slot < cap)
-        bin_cells[bin * cap + slot] = i;
+    const int bin = b[0] + g.nb[0] * (b[1] + g.nb[1] * b[2]);
+    g.cell_bin[i] = bin;
+    const int slot = atomicAdd(&g.bin_count[bin], 1);
+    if (slot < g.cap)
+        g.bin_cells[bin * g.cap + slot] = i;
     else
-        atomicOr(&flags[FLAG_OVERFLOW], OVF_BIN);
-    double qq[4] = {q[4 * i], q[4 * i + 1], q[4 * i + 2], q[4 * i + 3]};
+        atomicOr(&g.flags[FLAG_OVERFLOW], OVF_BIN);
+    double qq[4] = {g.q[4 * i], g.q[4 * i + 1], g.q[4 * i + 2], g.q[4 * i + 3]};
     const double in = 1.0 / sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
     for (int k = 0; k < 4; ++k) qq[k] *= in;
     double Q[9];
     quat_matrix(qq, Q);
-    const double a2[3] = {a20, a21, a22};
-    const Sym3 S = shape_tensor(Q, a2);
-    double *o = &A[6 * i];
+    const Sym3 S = shape_tensor(Q, g.a2);
+    double *o = &g.A[6 * i];
     o[0] = S.xx;
     o[1] = S.yy;
     o[2] = S.zz;
     o[3] = S.xy;
     o[4] = S.xz;
     o[5] = S.yz;
+    for (int a = 0; a < 3; ++a) g.Rf[3 * i + a] = (float)Rd[a];
+    g.Af[6 * i] = (float)S.xx;
+    g.Af[6 * i + 1] = (float)S.yy;
+    g.Af[6 * i + 2] = (float)S.zz;
+    g.Af[6 * i + 3] = (float)S.xy;
+    g.Af[6 * i + 4] = (float)S.xz;
+    g.Af[6 * i + 5] = (float)S.yz;
+
+    // shape header: the box spans the axis-aligned hull of the support
+    // |y_b| <= xi_b (half extent sum_b |Q_ab| xi_b) plus one node per side.
+    // It must have 1..box_dim nodes per axis and lie within one period of the
+    // lattice on each side; a cell that left the box or went non-finite is
+    // flagged and skipped by the shape kernels.
+    float *h = &g.hdr[kHdrWords * i];
+    int *hi_ = reinterpret_cast<int *>(h);
+    bool ok = true;
+    int ctr[3];
+    for (int a = 0; a < 3; ++a) {
+        double e = 0.0;
+        for (int c = 0; c < 3; ++c) e += fabs(Q[3 * a + c]) * (double)g.xi[c];
+        int lo = 0, n = 1;
+        if (fabs(Rd[a]) < 1e7 && e < 1e7) {
+            lo = (int)ceil(Rd[a] - e) - 1;
+            const int hi = (int)floor(Rd[a] + e) + 1;
+            n = hi - lo + 1;
+            if (n < 1 || n > g.box_dim || lo < -g.dims[a] || hi >= 2 * g.dims[a]) ok = false;
+            ctr[a] = wrap1((int)floor(Rd[a] + 0.5), g.dims[a]);
+        } else {
+            ok = false;
+            ctr[a] = 0;
+        }
+        h[9 + a] = (float)((double)lo - Rd[a]);
+        hi_[12 + a] = lo;
+        hi_[15 + a] = n;
+    }
+    for (int k = 0; k < 9; ++k) h[k] = (float)Q[k];
+    hi_[18] = ok ? ctr[0] + g.dims[0] * (ctr[1] + g.dims[1] * ctr[2]) : 0;
+    hi_[19] = ok ? 1 : 0;
+    if (!ok) atomicOr(&g.flags[FLAG_OVERFLOW], OVF_BOX);
 }
 
+// ---------------------------------------------------------------------------
+// k_gb
+// ---------------------------------------------------------------------------
 struct GbArgs {
     const double *R, *A;
+    const float *Rf, *Af;
     const int *cell_bin, *bin_count, *bin_cells;
     const int *wall_start, *wall_xyz;
     int *nbr, *nbr_count;
@@ -75,7 +138,20 @@ struct GbArgs {
     unsigned long long *clamps;
     int nc, cap, maxn, nb[3], per[3];
     double L[3], rc2, rcw2, smin, smin_w, rw2, eps0, rho_floor, rho_cut;
+    float rho_cut_f;  // FP32 prefilter bound (rho_cut with a safety margin)
+    float rc_lo2, rc_hi2, rcw2_f, Lf[3];  // FP32 candidate band around r_cut, wall radius
 };
+
+__device__ __forceinline__ void min_image_f(float d[3], const int per[3], const float L[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        if (!per[a]) continue;
+        if (d[a] > 0.5f * L[a])
+            d[a] -= L[a];
+        else if (d[a] < -0.5f * L[a])
+            d[a] += L[a];
+    }
+}
 
 // minimum image along periodic axes; positions live in [0, L)
 __device__ __forceinline__ void min_image(double d[3], const int per[3], const double L[3])
@@ -107,103 +183,378 @@ __device__ __forceinline__ void bin_range(int b, int nb, int per, int &lo, int &
 
 __device__ __forceinline__ int wrap_bin(int b, int nb) { return b < 0 ? b + nb : (b >= nb ? b - nb : b); }
 
-__global__ void __launch_bounds__(kGbThreads) k_gb(GbArgs g)
+// Reduced Gay-Berne distance in FP32 (no force): false only if the pair is
+// certainly outside the range.  H = Ai + Aj as 6 floats (xx yy zz xy xz yz).
+__device__ __forceinline__ bool gb_maybe_in_range(const float d[3], const float H[6], float smin, float cut)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.nc) return;
+    const float cxx = H[1] * H[2] - H[5] * H[5];
+    const float cyy = H[0] * H[2] - H[4] * H[4];
+    const float czz = H[0] * H[1] - H[3] * H[3];
+    const float cxy = H[4] * H[5] - H[3] * H[2];
+    const float cxz = H[3] * H[5] - H[4] * H[1];
+    const float cyz = H[3] * H[4] - H[0] * H[5];
+    const float det = H[0] * cxx + H[3] * cxy + H[4] * cxz;
+    const float kx = cxx * d[0] + cxy * d[1] + cxz * d[2];
+    const float ky = cxy * d[0] + cyy * d[1] + cyz * d[2];
+    const float kz = cxz * d[0] + cyz * d[1] + czz * d[2];
+    const float R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const float phi = 0.5f * (d[0] * kx + d[1] * ky + d[2] * kz) / (det * R2);
+    const float rho = (sqrtf(R2) - rsqrtf(phi) + smin) / smin;
+    return !(rho > cut);
+}
+
+__global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g)
+{
+    __shared__ int s_cand[kGbWarps][kMaxNbr];
+    __shared__ int s_sort[kGbWarps][kMaxNbr];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int i = blockIdx.x * kGbWarps + wid;
+    if (i >= g.nc) return;  // uniform across the warp
+    const unsigned lt = (1u << lane) - 1u;
     const double Ri[3] = {g.R[3 * i], g.R[3 * i + 1], g.R[3 * i + 2]};
-    const double *ai = &g.A[6 * i];
-    const Sym3 Ai{ai[0], ai[1], ai[2], ai[3], ai[4], ai[5]};
+    const float Rif[3] = {g.Rf[3 * i], g.Rf[3 * i + 1], g.Rf[3 * i + 2]};
+    const float *aif = &g.Af[6 * i];
+    const float Aif[6] = {aif[0], aif[1], aif[2], aif[3], aif[4], aif[5]};
     const int bin = g.cell_bin[i];
     const int b[3] = {bin % g.nb[0], (bin / g.nb[0]) % g.nb[1], bin / (g.nb[0] * g.nb[1])};
     int lo[3], hi[3];
     for (int a = 0; a < 3; ++a) bin_range(b[a], g.nb[a], g.per[a], lo[a], hi[a]);
 
-    int lst[kMaxNbr];
+    // 1. candidates: FP32 distance decides outside a band around r_cut; inside
+    //    the band the exact FP64 test (no fused multiply-add) decides, so the
+    //    partner sets are those of the FP64 test
     int cnt = 0;
-    bool ovf = false;
     for (int oz = lo[2]; oz <= hi[2]; ++oz)
         for (int oy = lo[1]; oy <= hi[1]; ++oy)
             for (int ox = lo[0]; ox <= hi[0]; ++ox) {
                 const int bb = wrap_bin(b[0] + ox, g.nb[0]) +
                                g.nb[0] * (wrap_bin(b[1] + oy, g.nb[1]) + g.nb[1] * wrap_bin(b[2] + oz, g.nb[2]));
                 const int c = min(g.bin_count[bb], g.cap);
-                for (int k = 0; k < c; ++k) {
-                    const int j = g.bin_cells[bb * g.cap + k];
-                    if (j == i) continue;
-                    double d[3] = {__dsub_rn(Ri[0], g.R[3 * j]), __dsub_rn(Ri[1], g.R[3 * j + 1]),
-                                   __dsub_rn(Ri[2], g.R[3 * j + 2])};
-                    min_image(d, g.per, g.L);
-                    if (!(dist2_exact(d) < g.rc2)) continue;
-                    if (cnt >= g.maxn) {
-                        ovf = true;
-                        continue;
+                for (int k0 = 0; k0 < c; k0 += 32) {
+                    const int k = k0 + lane;
+                    bool pass = false;
+                    int j = -1;
+                    if (k < c) {
+                        j = g.bin_cells[bb * g.cap + k];
+                        if (j != i) {
+                            float df[3] = {Rif[0] - g.Rf[3 * j], Rif[1] - g.Rf[3 * j + 1], Rif[2] - g.Rf[3 * j + 2]};
+                            min_image_f(df, g.per, g.Lf);
+                            const float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
+                            if (r2f < g.rc_lo2) {
+                                pass = true;
+                            } else if (r2f <= g.rc_hi2) {
+                                double d[3] = {__dsub_rn(Ri[0], g.R[3 * j]), __dsub_rn(Ri[1], g.R[3 * j + 1]),
+                                               __dsub_rn(Ri[2], g.R[3 * j + 2])};
+                                min_image(d, g.per, g.L);
+                                pass = dist2_exact(d) < g.rc2;
+                            }
+                        }
                     }
-                    int pos = cnt++;
-                    while (pos > 0 && lst[pos - 1] > j) {
-                        lst[pos] = lst[pos - 1];
-                        --pos;
-                    }
-                    lst[pos] = j;
+                    const unsigned m = __ballot_sync(0xffffffffu, pass);
+                    const int pos = cnt + __popc(m & lt);
+                    if (pass && pos < g.maxn) s_cand[wid][pos] = j;
+                    cnt += __popc(m);
                 }
             }
-    if (ovf) atomicOr(&g.flags[FLAG_OVERFLOW], OVF_NBR);
-    g.nbr_count[i] = cnt;
-    for (int k = 0; k < cnt; ++k) g.nbr[i * g.maxn + k] = lst[k];
+    if (cnt > g.maxn) {
+        if (lane == 0) atomicOr(&g.flags[FLAG_OVERFLOW], OVF_NBR);
+        cnt = g.maxn;
+    }
+    __syncwarp();
+    // 2. rank sort by partner index (entries are distinct)
+    for (int e = lane; e < cnt; e += 32) {
+        const int v = s_cand[wid][e];
+        int r = 0;
+        for (int f = 0; f < cnt; ++f) r += s_cand[wid][f] < v;
+        s_sort[wid][r] = v;
+    }
+    __syncwarp();
+    for (int e = lane; e < cnt; e += 32) g.nbr[i * g.maxn + e] = s_sort[wid][e];
+    if (lane == 0) g.nbr_count[i] = cnt;
 
+    // 3. cell-cell pairs, lane-parallel; FP64 only for pairs the FP32
+    //    reduced distance cannot rule out
     double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
     int clamped = 0;
-    for (int k = 0; k < cnt; ++k) {
-        const int j = lst[k];
+    bool hit = false;
+    for (int e = lane; e < cnt; e += 32) {
+        const int j = s_sort[wid][e];
+        float df[3] = {Rif[0] - g.Rf[3 * j], Rif[1] - g.Rf[3 * j + 1], Rif[2] - g.Rf[3 * j + 2]};
+        min_image_f(df, g.per, g.Lf);
+        const float *ajf = &g.Af[6 * j];
+        const float H[6] = {Aif[0] + ajf[0], Aif[1] + ajf[1], Aif[2] + ajf[2],
+                            Aif[3] + ajf[3], Aif[4] + ajf[4], Aif[5] + ajf[5]};
+        if (!gb_maybe_in_range(df, H, (float)g.smin, g.rho_cut_f)) continue;
         double d[3] = {__dsub_rn(Ri[0], g.R[3 * j]), __dsub_rn(Ri[1], g.R[3 * j + 1]),
                        __dsub_rn(Ri[2], g.R[3 * j + 2])};
         min_image(d, g.per, g.L);
         const double *aj = &g.A[6 * j];
+        const double *ai = &g.A[6 * i];
+        const Sym3 Ai{ai[0], ai[1], ai[2], ai[3], ai[4], ai[5]};
         const Sym3 Aj{aj[0], aj[1], aj[2], aj[3], aj[4], aj[5]};
-        gb_pair(d, Ai, Aj, g.smin, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
+        hit |= gb_pair(d, Ai, Aj, g.smin, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
     }
+    // 4. wall particles of the same 27 bins, lane-strided, FP32 until the
+    //    exact candidate test of the few that may interact
     if (g.wall_start != nullptr) {
-        const Sym3 Aw{g.rw2, g.rw2, g.rw2, 0.0, 0.0, 0.0};
-        int wlo[3], whi[3];
-        for (int a = 0; a < 3; ++a) bin_range(b[a], g.nb[a], g.per[a], wlo[a], whi[a]);
-        for (int oz = wlo[2]; oz <= whi[2]; ++oz)
-            for (int oy = wlo[1]; oy <= whi[1]; ++oy)
-                for (int ox = wlo[0]; ox <= whi[0]; ++ox) {
+        const float rw2f = (float)g.rw2;
+        const float Hw[6] = {Aif[0] + rw2f, Aif[1] + rw2f, Aif[2] + rw2f, Aif[3], Aif[4], Aif[5]};
+        for (int oz = lo[2]; oz <= hi[2]; ++oz)
+            for (int oy = lo[1]; oy <= hi[1]; ++oy)
+                for (int ox = lo[0]; ox <= hi[0]; ++ox) {
                     const int bb = wrap_bin(b[0] + ox, g.nb[0]) +
                                    g.nb[0] * (wrap_bin(b[1] + oy, g.nb[1]) + g.nb[1] * wrap_bin(b[2] + oz, g.nb[2]));
-                    for (int w = g.wall_start[bb]; w < g.wall_start[bb + 1]; ++w) {
-                        double d[3] = {Ri[0] - (double)g.wall_xyz[3 * w], Ri[1] - (double)g.wall_xyz[3 * w + 1],
-                                       Ri[2] - (double)g.wall_xyz[3 * w + 2]};
+                    const int w1 = g.wall_start[bb + 1];
+                    for (int w = g.wall_start[bb] + lane; w < w1; w += 32) {
+                        const int wx = g.wall_xyz[3 * w], wy = g.wall_xyz[3 * w + 1], wz = g.wall_xyz[3 * w + 2];
+                        float df[3] = {Rif[0] - (float)wx, Rif[1] - (float)wy, Rif[2] - (float)wz};
+                        min_image_f(df, g.per, g.Lf);
+                        if (!(df[0] * df[0] + df[1] * df[1] + df[2] * df[2] < g.rcw2_f)) continue;
+                        if (!gb_maybe_in_range(df, Hw, (float)g.smin_w, g.rho_cut_f)) continue;
+                        double d[3] = {Ri[0] - (double)wx, Ri[1] - (double)wy, Ri[2] - (double)wz};
                         min_image(d, g.per, g.L);
                         if (!(dist2_exact(d) < g.rcw2)) continue;
-                        gb_pair(d, Ai, Aw, g.smin_w, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
+                        const double *ai = &g.A[6 * i];
+                        const Sym3 Ai{ai[0], ai[1], ai[2], ai[3], ai[4], ai[5]};
+                        const Sym3 Aw{g.rw2, g.rw2, g.rw2, 0.0, 0.0, 0.0};
+                        hit |= gb_pair(d, Ai, Aw, g.smin_w, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
                     }
                 }
     }
-    for (int a = 0; a < 3; ++a) {
-        g.Fm[3 * i + a] = F[a];
-        g.Tm[3 * i + a] = T[a];
+    // 5. fixed-order warp reduction (skipped when no lane interacted)
+    if (__any_sync(0xffffffffu, hit)) {
+        for (int off = 16; off > 0; off >>= 1)
+            for (int a = 0; a < 3; ++a) {
+                F[a] += __shfl_xor_sync(0xffffffffu, F[a], off);
+                T[a] += __shfl_xor_sync(0xffffffffu, T[a], off);
+            }
+        for (int off = 16; off > 0; off >>= 1) clamped += __shfl_xor_sync(0xffffffffu, clamped, off);
     }
-    if (clamped) atomicAdd(g.clamps, (unsigned long long)clamped);
+    if (lane == 0) {
+        for (int a = 0; a < 3; ++a) {
+            g.Fm[3 * i + a] = F[a];
+            g.Tm[3 * i + a] = T[a];
+        }
+        if (clamped) atomicAdd(g.clamps, (unsigned long long)clamped);
+    }
 }
 
-struct CellsArgs {
-    double *R, *q, *V, *Om;
-    const double *Fm, *Tm;
-    int *have;
-    double *diag;
+// ---------------------------------------------------------------------------
+// shape weights shared by k_sample and k_spread
+// ---------------------------------------------------------------------------
+struct ShapeArgs {
+    const float *hdr;
+    const uint8_t *solid;
     const float *U, *S;
     float *G, *theta;
-    const uint8_t *solid;
-    int *flags;
+    double *part;
+    const float *JL;
     int nx, ny, nz;
     long long Np;
     float two_over_xi[3], xi[3], kappa, alpha;
-    double M, I[3], eT, eR, gT, gR, L[3];
-    int per[3], box_max, box_dim;
+    int box_dim;
 };
 
-__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+struct Hdr {
+    float Q[9], base[3];
+    int o[3], n[3], gc, ok;
+};
+
+__device__ __forceinline__ void load_hdr(const float *src, Hdr &h)
+{
+    const int *si = reinterpret_cast<const int *>(src);
+    for (int k = 0; k < 9; ++k) h.Q[k] = src[k];
+    for (int k = 0; k < 3; ++k) {
+        h.base[k] = src[9 + k];
+        h.o[k] = si[12 + k];
+        h.n[k] = si[15 + k];
+    }
+    h.gc = si[18];
+    h.ok = si[19];
+}
+
+// Per-row range [lo, hi] of box nodes (along x, the lattice's fastest index)
+// whose weight may be non-zero: the support |y_b| < xi_b cut along the row
+// x = (., i1, i2), widened by one node at each end (nodes outside have w = 0
+// exactly, so the range only saves work).  lo > hi for an empty row.
+// iq[b] = 1 / Q_xb (0 when |Q_xb| is negligible, then axis b does not
+// depend on x).
+__device__ __forceinline__ void row_range(const Hdr &h, const float xi[3], const float iq[3], int i1, int i2,
+                                          int &lo, int &hi)
+{
+    const float r1 = h.base[1] + (float)i1, r2 = h.base[2] + (float)i2;
+    float tlo = -1e30f, thi = 1e30f;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const float cb = h.Q[3 + b] * r1 + h.Q[6 + b] * r2;
+        if (iq[b] == 0.f) {
+            if (fabsf(cb) >= xi[b] * 1.0001f) {
+                lo = 1;
+                hi = 0;
+                return;
+            }
+            continue;
+        }
+        const float t1 = (-xi[b] - cb) * iq[b], t2 = (xi[b] - cb) * iq[b];
+        tlo = fmaxf(tlo, fminf(t1, t2));
+        thi = fminf(thi, fmaxf(t1, t2));
+    }
+    const float flo = tlo - h.base[0], fhi = thi - h.base[0];
+    if (!(flo <= fhi)) {
+        lo = 1;
+        hi = 0;
+        return;
+    }
+    lo = (int)fmaxf(floorf(flo) - 1.0f, 0.0f);
+    hi = (int)fminf(ceilf(fhi) + 1.0f, (float)(h.n[0] - 1));
+}
+
+// Shared-memory work plan of one cell: the weight box, per-row ranges, the
+// prefix sums of the row lengths and an item -> row map, so that the nodes
+// of all non-empty row segments are handed to the threads as one flat list.
+struct Plan {
+    float *sw;              // box weights, box_max
+    int *rlo, *rhi, *gyz;   // per row: weight range, lattice offset of the row
+    int *vlo;               // per row: first x of the visit range
+    int *pre;               // per row: first item (exclusive prefix)
+    unsigned short *map;    // per item: its row
+    int *tot;               // per warp totals of the scan
+};
+
+__device__ __forceinline__ Plan plan_layout(float *smem, int box_dim)
+{
+    const int R = box_dim * box_dim, V = R * box_dim;
+    Plan P;
+    P.sw = smem;
+    P.rlo = reinterpret_cast<int *>(smem + V);
+    P.rhi = P.rlo + R;
+    P.gyz = P.rhi + R;
+    P.vlo = P.gyz + R;
+    P.pre = P.vlo + R;
+    P.tot = P.pre + R + 1;
+    P.map = reinterpret_cast<unsigned short *>(P.tot + 32);
+    return P;
+}
+
+size_t plan_bytes(int box_dim)
+{
+    const size_t R = (size_t)box_dim * box_dim, V = R * box_dim;
+    return V * sizeof(float) + (5 * R + 1 + 32) * sizeof(int) + V * sizeof(unsigned short);
+}
+
+// Rows are split into contiguous chunks, one per thread.  Given each row's
+// item count len(r) (computed by the owner), build the exclusive prefix and
+// the item -> row map; returns the item total (same value in all threads).
+template <typename LenFn>
+__device__ __forceinline__ int plan_items(const Plan &P, int nrows, LenFn len)
+{
+    const int per = (nrows + blockDim.x - 1) / blockDim.x;
+    const int r0 = threadIdx.x * per;
+    int s = 0;
+    for (int k = 0; k < per; ++k)
+        if (r0 + k < nrows) s += len(r0 + k);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int v = s;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += u;
+    }
+    if (lane == 31) P.tot[w] = v;
+    __syncthreads();
+    int base = 0, total = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        if (k < w) base += P.tot[k];
+        total += P.tot[k];
+    }
+    int excl = base + v - s;
+    for (int k = 0; k < per; ++k) {
+        const int r = r0 + k;
+        if (r >= nrows) break;
+        const int n = len(r);
+        P.pre[r] = excl;
+        for (int t = 0; t < n; ++t) P.map[excl + t] = (unsigned short)r;
+        excl += n;
+    }
+    __syncthreads();
+    return total;
+}
+
+// Weights w = prod_b phi(2 y_b / xi_b), y = Q^T (x - R) (Sec. 2.2), 0 at solid
+// nodes, into the box in shared memory (zero outside the row ranges); also
+// fills rlo/rhi/gyz.  Returns this thread's partial sum of w.
+__device__ __forceinline__ float shape_weights(const ShapeArgs &a, const Hdr &h, const Plan &P)
+{
+    const int n0 = h.n[0], n1 = h.n[1], nrows = n1 * h.n[2], vol = n0 * nrows;
+    const int nxy = a.nx * a.ny;
+    for (int m = threadIdx.x; m < vol; m += blockDim.x) P.sw[m] = 0.f;
+    float iq[3];
+    for (int b = 0; b < 3; ++b) iq[b] = fabsf(h.Q[b]) < 1e-7f ? 0.f : 1.0f / h.Q[b];
+    const int per = (nrows + blockDim.x - 1) / blockDim.x;
+    const int r0 = threadIdx.x * per;
+    for (int k = 0; k < per; ++k) {
+        const int r = r0 + k;
+        if (r >= nrows) break;
+        const int i1 = r % n1, i2 = r / n1;
+        int lo, hi;
+        row_range(h, a.xi, iq, i1, i2, lo, hi);
+        P.rlo[r] = lo;
+        P.rhi[r] = hi;
+        P.gyz[r] = a.nx * wrap1(h.o[1] + i1, a.ny) + nxy * wrap1(h.o[2] + i2, a.nz);
+    }
+    // rows of this thread's chunk are its own: no barrier needed before the scan
+    const int total = plan_items(P, nrows, [&](int r) { return max(0, P.rhi[r] - P.rlo[r] + 1); });
+    float part = 0.f;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int r = P.map[t];
+        const int i0 = P.rlo[r] + (t - P.pre[r]);
+        const int g = P.gyz[r] + wrap1(h.o[0] + i0, a.nx);
+        float w = 0.f;
+        if (a.solid == nullptr || !a.solid[g]) {
+            const int i1 = r % n1, i2 = r / n1;
+            const float r0f = h.base[0] + (float)i0, r1f = h.base[1] + (float)i1, r2f = h.base[2] + (float)i2;
+            w = peskin4((h.Q[0] * r0f + h.Q[3] * r1f + h.Q[6] * r2f) * a.two_over_xi[0]) *
+                peskin4((h.Q[1] * r0f + h.Q[4] * r1f + h.Q[7] * r2f) * a.two_over_xi[1]) *
+                peskin4((h.Q[2] * r0f + h.Q[5] * r1f + h.Q[8] * r2f) * a.two_over_xi[2]);
+        }
+        P.sw[i0 + n0 * r] = w;
+        part += w;
+    }
+    return part;
+}
+
+// x-range of row r to visit for gradients: the union of its own range and
+// those of its four in-box neighbour rows (y and z).
+__device__ __forceinline__ void visit_range(const Hdr &h, const Plan &P, int r, int &lo, int &hi)
+{
+    const int n1 = h.n[1], n2 = h.n[2], i1 = r % n1, i2 = r / n1;
+    lo = P.rlo[r];
+    hi = P.rhi[r];
+    const int nb[4] = {i1 > 0 ? r - 1 : -1, i1 + 1 < n1 ? r + 1 : -1, i2 > 0 ? r - n1 : -1, i2 + 1 < n2 ? r + n1 : -1};
+    for (int k = 0; k < 4; ++k) {
+        if (nb[k] < 0 || P.rlo[nb[k]] > P.rhi[nb[k]]) continue;
+        if (lo > hi) {
+            lo = P.rlo[nb[k]];
+            hi = P.rhi[nb[k]];
+        } else {
+            lo = min(lo, P.rlo[nb[k]]);
+            hi = max(hi, P.rhi[nb[k]]);
+        }
+    }
+}
+
+// Plan the visit of every node where w or its central difference may be
+// non-zero (row visit ranges, flattened); records each row's first x in
+// P.vlo and returns the item count.
+__device__ __forceinline__ int plan_visit(const Hdr &h, const Plan &P)
+{
+    const int nrows = h.n[1] * h.n[2];
+    return plan_items(P, nrows, [&](int r) {
+        int lo, hi;
+        visit_range(h, P, r, lo, hi);
+        P.vlo[r] = lo;
+        return max(0, hi - lo + 1);
+    });
+}
 
 // Sum NV per-thread values over the block: FP32 within a warp, FP64 across
 // warps in a fixed order; the result lands in out[] (shared) for all threads.
@@ -225,116 +576,59 @@ __device__ __forceinline__ void block_sum(float (&v)[NV], double (*red)[NV], dou
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// k_sample: S = sum w;  u~ S = sum w u;  omega~ S = -sum D w x (u - u_c)
+// (summation by parts of the central-difference curl; sum D w vanishes over
+// the box, so the constant u_c = u at the centre node changes nothing in
+// exact arithmetic and removes FP32 cancellation);  T^S S / alpha =
+// sum w (sigma n) x (x - R), n = D w / |D w|.
+// ---------------------------------------------------------------------------
 template <bool ALPHA>
-__global__ void __launch_bounds__(kCellThreads) k_cells(CellsArgs a)
+__global__ void __launch_bounds__(kCellThreads) k_sample(ShapeArgs a)
 {
-    extern __shared__ float sw[];  // shape weight w per box node (0 at solid nodes)
-    __shared__ double sQd[9], sRd[3];
-    __shared__ float sQ[9], sbase[3];
-    __shared__ int so[3], sn[3], sbad;
+    extern __shared__ float smem[];
+    const Plan P = plan_layout(smem, a.box_dim);
+    __shared__ Hdr h;
     __shared__ double red[kCellThreads / 32][9];
     __shared__ double sums[9];
-    __shared__ float sJ[3], sL[3], sU0[3];
+    __shared__ float uc[3];
     const int i = blockIdx.x;
-    const int tid = threadIdx.x;
-
-    if (tid == 0) {
-        double qq[4] = {a.q[4 * i], a.q[4 * i + 1], a.q[4 * i + 2], a.q[4 * i + 3]};
-        const double in = 1.0 / sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
-        for (int k = 0; k < 4; ++k) qq[k] *= in;
-        quat_matrix(qq, sQd);
-        for (int k = 0; k < 9; ++k) sQ[k] = (float)sQd[k];
-        // the box must have 1..box_dim nodes per axis and lie within one
-        // period of the lattice on each side, so that a single wrap maps it
-        // into the lattice; a cell that left the box or went non-finite is
-        // flagged and skipped
-        const int dims[3] = {a.nx, a.ny, a.nz};
-        bool bad = false;
-        for (int d = 0; d < 3; ++d) {
-            const double Rd = a.R[3 * i + d];
-            sRd[d] = Rd;
-            double e = 0.0;
-            for (int b = 0; b < 3; ++b) e += fabs(sQd[3 * d + b]) * (double)a.xi[b];
-            if (!(fabs(Rd) < 1e7) || !(e < 1e7)) {
-                bad = true;
-                so[d] = 0;
-                sn[d] = 1;
-                continue;
-            }
-            const int lo = (int)ceil(Rd - e) - 1;
-            const int hi = (int)floor(Rd + e) + 1;
-            so[d] = lo;
-            sn[d] = hi - lo + 1;
-            sbase[d] = (float)((double)lo - Rd);
-            if (sn[d] < 1 || sn[d] > a.box_dim || lo < -dims[d] || hi >= 2 * dims[d]) bad = true;
-        }
-        sbad = bad;
-        if (sbad) atomicOr(&a.flags[FLAG_OVERFLOW], OVF_BOX);
-        // reference velocity: u at the node nearest the centre.  Sum D delta
-        // vanishes over the box, so subtracting a constant from u leaves the
-        // vorticity sum unchanged in exact arithmetic and removes the FP32
-        // cancellation of a nearly uniform flow.
-        if (!bad) {
-            int c[3];
-            for (int d = 0; d < 3; ++d) c[d] = wrap1((int)floor(sRd[d] + 0.5), dims[d]);
-            const long long gc = c[0] + (long long)a.nx * (c[1] + (long long)a.ny * c[2]);
-            sU0[0] = a.U[gc];
-            sU0[1] = a.U[a.Np + gc];
-            sU0[2] = a.U[2 * a.Np + gc];
+    if (threadIdx.x == 0) {
+        load_hdr(&a.hdr[kHdrWords * i], h);
+        if (h.ok) {
+            uc[0] = a.U[h.gc];
+            uc[1] = a.U[a.Np + h.gc];
+            uc[2] = a.U[2 * a.Np + h.gc];
         }
     }
     __syncthreads();
-    if (sbad) return;
-    const int n0 = sn[0], n1 = sn[1], n01 = sn[0] * sn[1], vol = n01 * sn[2];
-    const int nxy = a.nx * a.ny;
-
-    // 1. weights w = prod_b phi(2 y_b / xi_b), y = Q^T (x - R) (Sec. 2.2)
-    {
-        float part[1] = {0.f};
-        for (int m = tid; m < vol; m += blockDim.x) {
-            const int i0 = m % n0, t = m / n0, i1 = t % n1, i2 = t / n1;
-            const int g = wrap1(so[0] + i0, a.nx) + a.nx * wrap1(so[1] + i1, a.ny) + nxy * wrap1(so[2] + i2, a.nz);
-            float w = 0.f;
-            if (a.solid == nullptr || !a.solid[g]) {
-                const float r0 = sbase[0] + (float)i0, r1 = sbase[1] + (float)i1, r2 = sbase[2] + (float)i2;
-                w = 1.f;
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    const float y = sQ[b] * r0 + sQ[3 + b] * r1 + sQ[6 + b] * r2;
-                    w *= peskin4(y * a.two_over_xi[b]);
-                }
-            }
-            sw[m] = w;
-            part[0] += w;
-        }
-        __syncthreads();
-        block_sum<1>(part, reinterpret_cast<double (*)[1]>(red), sums);
-    }
+    if (!h.ok) return;
+    float p1[1] = {shape_weights(a, h, P)};
+    block_sum<1>(p1, reinterpret_cast<double (*)[1]>(red), sums);
     const double S = sums[0];
     __syncthreads();
-    if (!(S > 0.0)) {
-        if (tid == 0) atomicOr(&a.flags[FLAG_UNSTABLE], 2);
-        return;
-    }
 
-    // 2. sampling: u~ = sum delta u, omega~ = sum delta curl u = -sum D delta x u
-    //    (summation by parts of the central-difference curl), and
-    //    T^S = alpha sum delta (sigma n) x (x - R), n = D delta / |D delta|
-    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int n0 = h.n[0], n1 = h.n[1], n2 = h.n[2], n01 = n0 * n1;
     const float thr = (float)(1e-24 * S * S);
-    for (int m = tid; m < vol; m += blockDim.x) {
-        const int i0 = m % n0, t = m / n0, i1 = t % n1, i2 = t / n1;
+    const int total = plan_visit(h, P);
+    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int r = P.map[t];
+        const int i0 = P.vlo[r] + (t - P.pre[r]);
+        const int i1 = r % n1, i2 = r / n1;
+        const int m = i0 + n0 * r;
+        const float *sw = P.sw;
         const float w0 = sw[m];
         const float Dx = 0.5f * ((i0 + 1 < n0 ? sw[m + 1] : 0.f) - (i0 > 0 ? sw[m - 1] : 0.f));
         const float Dy = 0.5f * ((i1 + 1 < n1 ? sw[m + n0] : 0.f) - (i1 > 0 ? sw[m - n0] : 0.f));
-        const float Dz = 0.5f * ((i2 + 1 < sn[2] ? sw[m + n01] : 0.f) - (i2 > 0 ? sw[m - n01] : 0.f));
+        const float Dz = 0.5f * ((i2 + 1 < n2 ? sw[m + n01] : 0.f) - (i2 > 0 ? sw[m - n01] : 0.f));
         if (w0 == 0.f && Dx == 0.f && Dy == 0.f && Dz == 0.f) continue;
-        const int g = wrap1(so[0] + i0, a.nx) + a.nx * wrap1(so[1] + i1, a.ny) + nxy * wrap1(so[2] + i2, a.nz);
+        const int g = P.gyz[r] + wrap1(h.o[0] + i0, a.nx);
         const float ux = a.U[g], uy = a.U[a.Np + g], uz = a.U[2 * a.Np + g];
         acc[0] += w0 * ux;
         acc[1] += w0 * uy;
         acc[2] += w0 * uz;
-        const float vx = ux - sU0[0], vy = uy - sU0[1], vz = uz - sU0[2];
+        const float vx = ux - uc[0], vy = uy - uc[1], vz = uz - uc[2];
         acc[3] -= Dy * vz - Dz * vy;
         acc[4] -= Dz * vx - Dx * vz;
         acc[5] -= Dx * vy - Dy * vx;
@@ -348,7 +642,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellsArgs a)
                 const float tx = sxx * nx + sxy * ny + sxz * nz;
                 const float ty = sxy * nx + syy * ny + syz * nz;
                 const float tz = sxz * nx + syz * ny + szz * nz;
-                const float r0 = sbase[0] + (float)i0, r1 = sbase[1] + (float)i1, r2 = sbase[2] + (float)i2;
+                const float r0 = h.base[0] + (float)i0, r1 = h.base[1] + (float)i1, r2 = h.base[2] + (float)i2;
                 acc[6] += w0 * (ty * r2 - tz * r1);
                 acc[7] += w0 * (tz * r0 - tx * r2);
                 acc[8] += w0 * (tx * r1 - ty * r0);
@@ -356,131 +650,197 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellsArgs a)
         }
     }
     block_sum<9>(acc, red, sums);
+    if (threadIdx.x == 0) {
+        double *o = &a.part[10 * i];
+        o[0] = S;
+        for (int k = 0; k < 9; ++k) o[1 + k] = sums[k];
+    }
+}
 
-    // 3. rigid-body update (App. A) by one thread, FP64
-    if (tid == 0) {
-        const double iS = 1.0 / S;
-        double ut[3], wt[3], TS[3], Fm[3], Tm[3], Fc[3], Tl[3], Tb[3], wb[3], Tc[3];
+// ---------------------------------------------------------------------------
+// k_rigid: App. A, FP64, one thread per cell
+// ---------------------------------------------------------------------------
+struct RigidArgs {
+    double *R, *q, *V, *Om;
+    const double *Fm, *Tm, *part;
+    const float *hdr;
+    int *have, *flags;
+    double *diag;
+    float *JL;
+    int nc;
+    double M, I[3], iM, iI[3], eT, eR, gT, gR, alpha, L[3];
+    int per[3];
+};
+
+// sin and cos; for |t| < 0.1 their Taylor series to t^11 / t^12 (remainder
+// below 1e-22, under half an FP64 ulp), else the library function
+__device__ __forceinline__ void sincos_rot(double t, double *s, double *c)
+{
+    if (fabs(t) < 0.1) {
+        const double t2 = t * t;
+        *s = t * (1.0 + t2 * (-1.0 / 6.0 + t2 * (1.0 / 120.0 + t2 * (-1.0 / 5040.0 +
+             t2 * (1.0 / 362880.0 + t2 * (-1.0 / 39916800.0))))));
+        *c = 1.0 + t2 * (-0.5 + t2 * (1.0 / 24.0 + t2 * (-1.0 / 720.0 + t2 * (1.0 / 40320.0 +
+             t2 * (-1.0 / 3628800.0 + t2 * (1.0 / 479001600.0))))));
+    } else {
+        sincos(t, s, c);
+    }
+}
+
+__global__ void __launch_bounds__(kRigidThreads) k_rigid(RigidArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nc) return;
+    const int ok = reinterpret_cast<const int *>(a.hdr)[kHdrWords * i + 19];
+    const double S = a.part[10 * i];
+    if (!ok || !(S > 0.0)) {
+        if (ok) atomicOr(&a.flags[FLAG_UNSTABLE], 2);
+        for (int k = 0; k < 6; ++k) a.JL[6 * i + k] = 0.f;
+        return;
+    }
+    double q[4] = {a.q[4 * i], a.q[4 * i + 1], a.q[4 * i + 2], a.q[4 * i + 3]};
+    {
+        const double in = 1.0 / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        for (int k = 0; k < 4; ++k) q[k] *= in;
+    }
+    double Q[9];
+    quat_matrix(q, Q);
+    const double iS = 1.0 / S;
+    double ut[3], wt[3], TS[3], Fm[3], Tm[3], Fc[3], Tl[3], Tc[3];
+    for (int d = 0; d < 3; ++d) {
+        ut[d] = a.part[10 * i + 1 + d] * iS;
+        wt[d] = a.part[10 * i + 4 + d] * iS;
+        TS[d] = a.alpha * a.part[10 * i + 7 + d] * iS;
+        Fm[d] = a.Fm[3 * i + d];
+        Tm[d] = a.Tm[3 * i + d];
+        // App. A step 5: F^comb = F^mech + gamma_T M u~; torque in the body
+        // frame with the elongational torque included
+        Fc[d] = Fm[d] + a.gT * a.M * ut[d];
+        Tl[d] = Tm[d] + TS[d];
+    }
+    for (int d = 0; d < 3; ++d) {
+        const double Tb = Q[d] * Tl[0] + Q[3 + d] * Tl[1] + Q[6 + d] * Tl[2];
+        const double wb = Q[d] * wt[0] + Q[3 + d] * wt[1] + Q[6 + d] * wt[2];
+        Tc[d] = Tb + a.gR * a.I[d] * wb;
+    }
+    double V[3], Om[3], V0[3], Om0[3];
+    for (int d = 0; d < 3; ++d) {
+        V0[d] = V[d] = a.V[3 * i + d];
+        Om0[d] = Om[d] = a.Om[3 * i + d];
+    }
+    const bool have = a.have[i] != 0;
+    if (have) {  // steps 6-7 of the previous step, with the forces at this pose
         for (int d = 0; d < 3; ++d) {
-            ut[d] = sums[d] * iS;
-            wt[d] = sums[3 + d] * iS;
-            TS[d] = ALPHA ? (double)a.alpha * sums[6 + d] * iS : 0.0;
-            Fm[d] = a.Fm[3 * i + d];
-            Tm[d] = a.Tm[3 * i + d];
-            Fc[d] = Fm[d] + a.gT * a.M * ut[d];
-            Tl[d] = Tm[d] + TS[d];
-        }
-        const double *Q = sQd;
-        for (int d = 0; d < 3; ++d) {
-            Tb[d] = Q[d] * Tl[0] + Q[3 + d] * Tl[1] + Q[6 + d] * Tl[2];
-            wb[d] = Q[d] * wt[0] + Q[3 + d] * wt[1] + Q[6 + d] * wt[2];
-            Tc[d] = Tb[d] + a.gR * a.I[d] * wb[d];
-        }
-        double V[3], Om[3], V0[3], Om0[3];
-        for (int d = 0; d < 3; ++d) {
-            V0[d] = V[d] = a.V[3 * i + d];
-            Om0[d] = Om[d] = a.Om[3 * i + d];
-        }
-        const bool have = a.have[i] != 0;
-        if (have) {  // steps 6-7 of the previous step, with forces at this pose
-            for (int d = 0; d < 3; ++d) {
-                Om[d] *= a.eR;
-                V[d] *= a.eT;
-                V[d] += 0.5 * Fc[d] / a.M;
-                Om[d] += 0.5 * Tc[d] / a.I[d];
-            }
-        }
-        for (int d = 0; d < 3; ++d) {  // steps 1-2
-            Om[d] += 0.5 * Tc[d] / a.I[d];
-            V[d] += 0.5 * Fc[d] / a.M;
             Om[d] *= a.eR;
             V[d] *= a.eT;
-        }
-        const double c = have ? 1.0 : 0.5;
-        double J[3], L[3], dp[3];
-        for (int d = 0; d < 3; ++d) {
-            J[d] = a.M * (V[d] - V0[d]) - c * Fm[d];
-            dp[d] = a.I[d] * (Om[d] - Om0[d]);
-        }
-        for (int d = 0; d < 3; ++d) L[d] = Q[3 * d] * dp[0] + Q[3 * d + 1] * dp[1] + Q[3 * d + 2] * dp[2] - c * Tm[d];
-        // step 3: drift
-        double R[3];
-        for (int d = 0; d < 3; ++d) {
-            R[d] = sRd[d] + V[d];
-            if (a.per[d]) {
-                if (R[d] >= a.L[d])
-                    R[d] -= a.L[d];
-                else if (R[d] < 0.0)
-                    R[d] += a.L[d];
-            }
-        }
-        // step 4: sub-rotations about body axes 1, 2, 3, 2, 1 by h Om/2, h Om/2,
-        // h Om, h Om/2, h Om/2; each turns pi = I Om by R^T and the frame by R
-        double q[4] = {a.q[4 * i], a.q[4 * i + 1], a.q[4 * i + 2], a.q[4 * i + 3]};
-        {
-            const double in = 1.0 / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-            for (int k = 0; k < 4; ++k) q[k] *= in;
-        }
-        const int ax[5] = {0, 1, 2, 1, 0};
-        const double fr[5] = {0.5, 0.5, 1.0, 0.5, 0.5};
-        for (int s = 0; s < 5; ++s) {
-            const int k = ax[s];
-            const double th = fr[s] * Om[k];
-            double sh, ch;
-            sincos(0.5 * th, &sh, &ch);
-            double r[4] = {ch, 0.0, 0.0, 0.0};
-            r[1 + k] = sh;
-            const double w1 = q[0], x1 = q[1], y1 = q[2], z1 = q[3];
-            const double w2 = r[0], x2 = r[1], y2 = r[2], z2 = r[3];
-            q[0] = w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2;
-            q[1] = w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2;
-            q[2] = w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2;
-            q[3] = w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2;
-            double st, ct;
-            sincos(th, &st, &ct);
-            const int p1 = (k + 1) % 3, p2 = (k + 2) % 3;
-            const double pi1 = a.I[p1] * Om[p1], pi2 = a.I[p2] * Om[p2];
-            Om[p1] = (ct * pi1 + st * pi2) / a.I[p1];
-            Om[p2] = (-st * pi1 + ct * pi2) / a.I[p2];
-        }
-        {
-            const double in = 1.0 / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-            for (int k = 0; k < 4; ++k) a.q[4 * i + k] = q[k] * in;
-        }
-        for (int d = 0; d < 3; ++d) {
-            a.R[3 * i + d] = R[d];
-            a.V[3 * i + d] = V[d];
-            a.Om[3 * i + d] = Om[d];
-        }
-        a.have[i] = 1;
-        double *o = &a.diag[21 * i];
-        for (int d = 0; d < 3; ++d) {
-            o[d] = Fm[d];
-            o[3 + d] = Tm[d];
-            o[6 + d] = ut[d];
-            o[9 + d] = wt[d];
-            o[12 + d] = TS[d];
-            o[15 + d] = J[d];
-            o[18 + d] = L[d];
-            sJ[d] = (float)J[d];
-            sL[d] = (float)L[d];
+            V[d] += 0.5 * Fc[d] * a.iM;
+            Om[d] += 0.5 * Tc[d] * a.iI[d];
         }
     }
-    __syncthreads();
+    for (int d = 0; d < 3; ++d) {  // steps 1-2
+        Om[d] += 0.5 * Tc[d] * a.iI[d];
+        V[d] += 0.5 * Fc[d] * a.iM;
+        Om[d] *= a.eR;
+        V[d] *= a.eT;
+    }
+    // hydrodynamic impulses: momentum change minus the mechanical impulse
+    const double c = have ? 1.0 : 0.5;
+    double J[3], Lm[3], dp[3];
+    for (int d = 0; d < 3; ++d) {
+        J[d] = a.M * (V[d] - V0[d]) - c * Fm[d];
+        dp[d] = a.I[d] * (Om[d] - Om0[d]);
+    }
+    for (int d = 0; d < 3; ++d) Lm[d] = Q[3 * d] * dp[0] + Q[3 * d + 1] * dp[1] + Q[3 * d + 2] * dp[2] - c * Tm[d];
+    // step 3: drift
+    double R[3];
+    for (int d = 0; d < 3; ++d) {
+        R[d] = a.R[3 * i + d] + V[d];
+        if (a.per[d]) {
+            if (R[d] >= a.L[d])
+                R[d] -= a.L[d];
+            else if (R[d] < 0.0)
+                R[d] += a.L[d];
+        }
+    }
+    // step 4: sub-rotations about body axes 1, 2, 3, 2, 1 by h Om/2, h Om/2,
+    // h Om, h Om/2, h Om/2; each turns pi = I Om by R^T and the frame by R
+    const int ax[5] = {0, 1, 2, 1, 0};
+    const double fr[5] = {0.5, 0.5, 1.0, 0.5, 0.5};
+    for (int s = 0; s < 5; ++s) {
+        const int k = ax[s];
+        const double th = fr[s] * Om[k];
+        double sh, ch;
+        sincos_rot(0.5 * th, &sh, &ch);
+        double r[4] = {ch, 0.0, 0.0, 0.0};
+        r[1 + k] = sh;
+        const double w1 = q[0], x1 = q[1], y1 = q[2], z1 = q[3];
+        q[0] = w1 * r[0] - x1 * r[1] - y1 * r[2] - z1 * r[3];
+        q[1] = w1 * r[1] + x1 * r[0] + y1 * r[3] - z1 * r[2];
+        q[2] = w1 * r[2] - x1 * r[3] + y1 * r[0] + z1 * r[1];
+        q[3] = w1 * r[3] + x1 * r[2] - y1 * r[1] + z1 * r[0];
+        double st, ct;
+        sincos_rot(th, &st, &ct);
+        const int p1 = (k + 1) % 3, p2 = (k + 2) % 3;
+        const double pi1 = a.I[p1] * Om[p1], pi2 = a.I[p2] * Om[p2];
+        Om[p1] = (ct * pi1 + st * pi2) * a.iI[p1];
+        Om[p2] = (-st * pi1 + ct * pi2) * a.iI[p2];
+    }
+    const double in = 1.0 / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int k = 0; k < 4; ++k) a.q[4 * i + k] = q[k] * in;
+    for (int d = 0; d < 3; ++d) {
+        a.R[3 * i + d] = R[d];
+        a.V[3 * i + d] = V[d];
+        a.Om[3 * i + d] = Om[d];
+    }
+    a.have[i] = 1;
+    double *o = &a.diag[21 * i];
+    for (int d = 0; d < 3; ++d) {
+        o[d] = Fm[d];
+        o[3 + d] = Tm[d];
+        o[6 + d] = ut[d];
+        o[9 + d] = wt[d];
+        o[12 + d] = TS[d];
+        o[15 + d] = J[d];
+        o[18 + d] = Lm[d];
+        a.JL[6 * i + d] = (float)J[d];
+        a.JL[6 * i + 3 + d] = (float)Lm[d];
+    }
+}
 
-    // 4. spreading (h = 1): G += -J delta + 1/2 L x D delta at fluid nodes;
-    //    theta += 1 - (1 - w)^kappa where w > 0
+// ---------------------------------------------------------------------------
+// k_spread (h = 1): G += -J delta + 1/2 L x D delta at fluid nodes;
+// theta += 1 - (1 - w)^kappa where w > 0
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCellThreads) k_spread(ShapeArgs a)
+{
+    extern __shared__ float smem[];
+    const Plan P = plan_layout(smem, a.box_dim);
+    __shared__ Hdr h;
+    const int i = blockIdx.x;
+    if (threadIdx.x == 0) load_hdr(&a.hdr[kHdrWords * i], h);
+    __syncthreads();
+    if (!h.ok) return;
+    const double S = a.part[10 * i];
+    if (!(S > 0.0)) return;
+    shape_weights(a, h, P);
+    __syncthreads();
     const float iS = (float)(1.0 / S);
-    const float Jx = sJ[0], Jy = sJ[1], Jz = sJ[2];
-    const float Lx = 0.5f * sL[0], Ly = 0.5f * sL[1], Lz = 0.5f * sL[2];
-    for (int m = tid; m < vol; m += blockDim.x) {
-        const int i0 = m % n0, t = m / n0, i1 = t % n1, i2 = t / n1;
+    const float Jx = a.JL[6 * i], Jy = a.JL[6 * i + 1], Jz = a.JL[6 * i + 2];
+    const float Lx = 0.5f * a.JL[6 * i + 3], Ly = 0.5f * a.JL[6 * i + 4], Lz = 0.5f * a.JL[6 * i + 5];
+    const int n0 = h.n[0], n1 = h.n[1], n2 = h.n[2], n01 = n0 * n1;
+    const int total = plan_visit(h, P);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int r = P.map[t];
+        const int i0 = P.vlo[r] + (t - P.pre[r]);
+        const int i1 = r % n1, i2 = r / n1;
+        const int m = i0 + n0 * r;
+        const float *sw = P.sw;
         const float w0 = sw[m];
         const float Dx = 0.5f * ((i0 + 1 < n0 ? sw[m + 1] : 0.f) - (i0 > 0 ? sw[m - 1] : 0.f));
         const float Dy = 0.5f * ((i1 + 1 < n1 ? sw[m + n0] : 0.f) - (i1 > 0 ? sw[m - n0] : 0.f));
-        const float Dz = 0.5f * ((i2 + 1 < sn[2] ? sw[m + n01] : 0.f) - (i2 > 0 ? sw[m - n01] : 0.f));
+        const float Dz = 0.5f * ((i2 + 1 < n2 ? sw[m + n01] : 0.f) - (i2 > 0 ? sw[m - n01] : 0.f));
         if (w0 == 0.f && Dx == 0.f && Dy == 0.f && Dz == 0.f) continue;
-        const int g = wrap1(so[0] + i0, a.nx) + a.nx * wrap1(so[1] + i1, a.ny) + nxy * wrap1(so[2] + i2, a.nz);
+        const int g = P.gyz[r] + wrap1(h.o[0] + i0, a.nx);
         if (a.solid != nullptr && a.solid[g]) continue;
         const float dl = w0 * iS, ex = Dx * iS, ey = Dy * iS, ez = Dz * iS;
         atomicAdd(&a.G[g], -Jx * dl + (Ly * ez - Lz * ey));
@@ -490,15 +850,60 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellsArgs a)
     }
 }
 
+ShapeArgs shape_args(const Dev &d, const Params &p)
+{
+    ShapeArgs a;
+    a.hdr = d.hdr;
+    a.solid = d.solid;
+    a.U = d.U;
+    a.S = d.S;
+    a.G = d.G;
+    a.theta = d.theta;
+    a.part = d.part;
+    a.JL = d.JL;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.nz = d.nz;
+    a.Np = d.Np;
+    for (int k = 0; k < 3; ++k) {
+        a.two_over_xi[k] = 2.0f / p.xi[k];
+        a.xi[k] = p.xi[k];
+    }
+    a.box_dim = p.box_dim;
+    a.kappa = p.kappa;
+    a.alpha = p.alpha;
+    return a;
+}
+
 }  // namespace
 
 void launch_bin(const Dev &d, const Params &p, cudaStream_t s)
 {
     if (d.nc == 0) return;
     cudaMemsetAsync(d.bin_count, 0, sizeof(int) * d.nbins, s);
-    k_bin<<<(d.nc + kBinThreads - 1) / kBinThreads, kBinThreads, 0, s>>>(
-        d.R, d.q, d.A, d.cell_bin, d.bin_count, d.bin_cells, d.flags, d.nc, d.nb[0], d.nb[1], d.nb[2],
-        d.bin_size[0], d.bin_size[1], d.bin_size[2], d.bin_cap, p.a2[0], p.a2[1], p.a2[2]);
+    BinArgs g;
+    g.R = d.R;
+    g.q = d.q;
+    g.A = d.A;
+    g.Rf = d.Rf;
+    g.Af = d.Af;
+    g.hdr = d.hdr;
+    g.cell_bin = d.cell_bin;
+    g.bin_count = d.bin_count;
+    g.bin_cells = d.bin_cells;
+    g.flags = d.flags;
+    g.nc = d.nc;
+    g.cap = d.bin_cap;
+    g.box_dim = p.box_dim;
+    const int dims[3] = {d.nx, d.ny, d.nz};
+    for (int a = 0; a < 3; ++a) {
+        g.nb[a] = d.nb[a];
+        g.bs[a] = d.bin_size[a];
+        g.a2[a] = p.a2[a];
+        g.xi[a] = p.xi[a];
+        g.dims[a] = dims[a];
+    }
+    k_bin<<<(d.nc + kBinThreads - 1) / kBinThreads, kBinThreads, 0, s>>>(g);
 }
 
 void launch_gb(const Dev &d, const Params &p, cudaStream_t s)
@@ -535,56 +940,82 @@ void launch_gb(const Dev &d, const Params &p, cudaStream_t s)
     g.eps0 = p.eps0;
     g.rho_floor = p.rho_floor;
     g.rho_cut = p.rho_cut;
-    k_gb<<<(d.nc + kGbThreads - 1) / kGbThreads, kGbThreads, 0, s>>>(g);
+    g.rho_cut_f = (float)(p.rho_cut * 1.001 + 1e-3);
+    g.Rf = d.Rf;
+    g.Af = d.Af;
+    // FP32 positions carry ~1e-7 relative error: outside a band of
+    // 1e-3 + 2e-6 max(L) around r_cut the FP32 distance decides the same way
+    // as the exact FP64 test
+    const double band = 1e-3 + 2e-6 * (double)std::max(d.nx, std::max(d.ny, d.nz));
+    const double rc = sqrt(p.rc2);
+    g.rc_lo2 = (float)((rc - band) * (rc - band));
+    g.rc_hi2 = (float)((rc + band) * (rc + band));
+    g.rcw2_f = (float)(p.rcw2 * 1.0001 + 1e-3);
+    for (int a = 0; a < 3; ++a) g.Lf[a] = (float)dims[a];
+    const int blocks = (d.nc + kGbWarps - 1) / kGbWarps;
+    k_gb<<<blocks, 32 * kGbWarps, 0, s>>>(g);
 }
 
-size_t cells_smem_bytes(const Params &p) { return sizeof(float) * (size_t)p.box_max; }
+size_t cells_smem_bytes(const Params &p) { return plan_bytes(p.box_dim); }
 
-void launch_cells(const Dev &d, const Params &p, cudaStream_t s)
+void prepare_cells(const Params &p)
+{
+    const int smem = (int)cells_smem_bytes(p);
+    cudaFuncSetAttribute(k_sample<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_sample<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+void launch_sample(const Dev &d, const Params &p, cudaStream_t s)
 {
     if (d.nc == 0) return;
-    CellsArgs a;
+    const ShapeArgs a = shape_args(d, p);
+    const size_t smem = cells_smem_bytes(p);
+    if (d.S != nullptr)
+        k_sample<true><<<d.nc, kCellThreads, smem, s>>>(a);
+    else
+        k_sample<false><<<d.nc, kCellThreads, smem, s>>>(a);
+}
+
+void launch_rigid(const Dev &d, const Params &p, cudaStream_t s)
+{
+    if (d.nc == 0) return;
+    RigidArgs a;
     a.R = d.R;
     a.q = d.q;
     a.V = d.V;
     a.Om = d.Om;
     a.Fm = d.Fm;
     a.Tm = d.Tm;
+    a.part = d.part;
+    a.hdr = d.hdr;
     a.have = d.have;
-    a.diag = d.diag;
-    a.U = d.U;
-    a.S = d.S;
-    a.G = d.G;
-    a.theta = d.theta;
-    a.solid = d.solid;
     a.flags = d.flags;
-    a.nx = d.nx;
-    a.ny = d.ny;
-    a.nz = d.nz;
-    a.Np = d.Np;
-    for (int k = 0; k < 3; ++k) {
-        a.xi[k] = p.xi[k];
-        a.two_over_xi[k] = 2.0f / p.xi[k];
-        a.I[k] = p.I[k];
-        a.per[k] = p.periodic[k];
-    }
-    a.L[0] = d.nx;
-    a.L[1] = d.ny;
-    a.L[2] = d.nz;
-    a.kappa = p.kappa;
-    a.alpha = p.alpha;
+    a.diag = d.diag;
+    a.JL = d.JL;
+    a.nc = d.nc;
     a.M = p.M;
+    a.iM = p.iM;
     a.eT = p.eT;
     a.eR = p.eR;
     a.gT = p.gT;
     a.gR = p.gR;
-    a.box_max = p.box_max;
-    a.box_dim = p.box_dim;
-    const size_t smem = cells_smem_bytes(p);
-    if (d.S != nullptr)
-        k_cells<true><<<d.nc, kCellThreads, smem, s>>>(a);
-    else
-        k_cells<false><<<d.nc, kCellThreads, smem, s>>>(a);
+    a.alpha = d.S != nullptr ? (double)p.alpha : 0.0;
+    const int dims[3] = {d.nx, d.ny, d.nz};
+    for (int k = 0; k < 3; ++k) {
+        a.I[k] = p.I[k];
+        a.iI[k] = p.iI[k];
+        a.per[k] = p.periodic[k];
+        a.L[k] = dims[k];
+    }
+    k_rigid<<<(d.nc + kRigidThreads - 1) / kRigidThreads, kRigidThreads, 0, s>>>(a);
+}
+
+void launch_spread(const Dev &d, const Params &p, cudaStream_t s)
+{
+    if (d.nc == 0) return;
+    const ShapeArgs a = shape_args(d, p);
+    k_spread<<<d.nc, kCellThreads, cells_smem_bytes(p), s>>>(a);
 }
 
 }  // namespace rbc

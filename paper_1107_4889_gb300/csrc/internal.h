@@ -8,8 +8,12 @@
 
 namespace rbc {
 
+// Per-cell shape header (floats; integer fields stored bit-cast):
+// Q[9] body->lab, base[3] = box origin - R, origin[3], dims[3], centre node, ok.
+constexpr int kHdrWords = 20;
+
 // Flags word indices (device int[8]).
-enum { FLAG_UNSTABLE = 0, FLAG_OVERFLOW = 1 };
+enum { FLAG_UNSTABLE = 0, FLAG_OVERFLOW = 1, FLAG_TIMEOUT = 2 };
 enum { OVF_BIN = 1, OVF_NBR = 2, OVF_BOX = 4 };
 
 struct Dev {
@@ -24,13 +28,18 @@ struct Dev {
     float *theta;       // 1 plane: sum of smoothed characteristic functions (zeroed by the pass)
     float *rho;         // 1 plane: density for field output
     uint8_t *solid;     // N bytes or null
+    uint32_t *links;    // N words or null: bit p (1..18) = node + c_p is solid, bit 31 = node is solid
     // cells (SoA FP64)
     int nc;
     double *R, *q, *V, *Om;  // 3n, 4n, 3n, 3n
     double *A;               // 6n shape tensors (xx yy zz xy xz yz)
+    float *Rf, *Af;          // 3n, 6n FP32 copies of positions and shape tensors (prefilters)
     double *Fm, *Tm;         // 3n GB force, 3n GB torque (lab)
     int *have;               // n: cached combined force exists (not the first step)
     double *diag;            // 21n per-cell diagnostics of the last step
+    float *hdr;              // kHdrWords per cell: shape header built by k_bin
+    double *part;            // 10n: shape normalisation S and the 9 sampled sums
+    float *JL;               // 6n: impulses J, L handed from k_rigid to k_spread
     // cell list
     int nb[3], nbins, bin_cap;
     double bin_size[3];
@@ -47,6 +56,9 @@ struct Dev {
     double *budget_part;            // budget_blocks * 8
     double *budget_out;             // 16: mass, p_fluid(3), max|u|, NaN count, p_cells(3)
     int budget_blocks;
+    // lattice pass launch: grid of the row-staged kernel (0: one thread per node)
+    int lb_grid;
+    size_t lb_smem;
 };
 
 struct Params {
@@ -55,7 +67,7 @@ struct Params {
     float mach2;
     float xi[3];
     double a2[3];
-    double M, I[3], eT, eR, gT, gR;
+    double M, I[3], iM, iI[3], eT, eR, gT, gR;
     double eps0, smin_cc, smin_w, rw2, rho_floor, rho_cut, rc2, rcw2;
     int periodic[3];
     int box_max;  // largest shape box (nodes)
@@ -63,6 +75,7 @@ struct Params {
 };
 
 // lb.cu
+void prepare_lb(Dev &d);
 void launch_lb(const Dev &d, const Params &p, int parity, cudaStream_t s);
 void launch_rho(const Dev &d, int parity, cudaStream_t s);
 void launch_budget(const Dev &d, const Params &p, int parity, cudaStream_t s);
@@ -71,7 +84,10 @@ int budget_blocks_for(int N);
 // cells.cu
 void launch_bin(const Dev &d, const Params &p, cudaStream_t s);
 void launch_gb(const Dev &d, const Params &p, cudaStream_t s);
-void launch_cells(const Dev &d, const Params &p, cudaStream_t s);
+void launch_sample(const Dev &d, const Params &p, cudaStream_t s);
+void launch_rigid(const Dev &d, const Params &p, cudaStream_t s);
+void launch_spread(const Dev &d, const Params &p, cudaStream_t s);
 size_t cells_smem_bytes(const Params &p);
+void prepare_cells(const Params &p);
 
 }  // namespace rbc

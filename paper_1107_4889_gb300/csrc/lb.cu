@@ -8,8 +8,8 @@
 // density and the smoothed hematocrit the cells spread, collides, stores the
 // 19 new deviations to its own node and writes u and sigma for the cells to
 // sample.  Bytes per fluid node: 76 read + 76 write (populations), 16 read
-// (G, theta), 12 written (u), 24 written (sigma when alpha != 0), plus the
-// 16-byte clear of G and theta.
+// (G, theta), 12 written (u), 24 written (sigma when alpha != 0), 4 read
+// (link mask, walled lattices only), plus the 16-byte clear of G and theta.
 #include "internal.h"
 #include "rbc_device.cuh"
 
@@ -19,48 +19,50 @@ namespace {
 
 constexpr int kLbThreads = 256;
 
+// opposite speeds for run-time indices
+__constant__ int kOppTab[kQ] = {opp(0),  opp(1),  opp(2),  opp(3),  opp(4),  opp(5),  opp(6),
+                                opp(7),  opp(8),  opp(9),  opp(10), opp(11), opp(12), opp(13),
+                                opp(14), opp(15), opp(16), opp(17), opp(18)};
+
 __device__ __forceinline__ int wrapm(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// Collision (Sec. 2.1), in deviations.  With drho = sum d, j = sum c d:
+struct LbArgs {
+    const float *src;
+    float *dst;
+    const uint32_t *links;
+    float *G, *th, *U, *S;
+    int *flags;
+    int nx, ny, nz, N;
+    long long Np;
+    float gx0, gy0, gz0, tau0, delta, mach2;
+};
+
+// Collision (Sec. 2.1) of node n = (x, y, z), in deviations, from its 19
+// pulled deviations d, the link mask lk, and the force density / smoothed
+// hematocrit sums read at the node.  With drho = sum d, j = sum c d:
 //   rho = 1 + drho, u = (j + G/2) / rho                       (Eqs. dens, vel)
 //   f_eq - w = w [drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)]
 //   Df = (1 - 1/2T) w [3 c.G + 4.5 (c.G)(c.u) - 1.5 G.u]       (Eq. chen_force,
 //        force-density G, Guo's factor of the scheme Eq. vel comes from)
 //   d* = d - (d - d_eq)/T + Df                                (Eq. lbe_discrete)
 //   sigma = -(1 - 1/2T) sum c c (d - d_eq)                    (Eq. stresstensorLB)
+// Stores d*, u, sigma, clears the node's G and theta, raises the stability
+// flag, and at walls writes the reflected populations (halfway bounce-back):
+// a population heading into a solid neighbour m comes back to this node in
+// the opposite direction next pass, so it is stored in m's slot of that
+// direction, from which this node pulls.  Each (slot, solid node) pair has
+// exactly one writer.
 template <bool WALLS, bool CELLS, bool SIGMA>
-__global__ void __launch_bounds__(kLbThreads)
-k_lb(const float *__restrict__ src, float *__restrict__ dst, const uint8_t *__restrict__ solid,
-     float *__restrict__ G, float *__restrict__ th, float *__restrict__ U, float *__restrict__ S,
-     int *__restrict__ flags, int nx, int ny, int nz, int N, long long Np, float gx0, float gy0,
-     float gz0, float tau0, float delta, float mach2)
+__device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], uint32_t lk, float gx, float gy,
+                                             float gz, float T, int n, int x, int y, int z)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    if (WALLS && solid[n]) return;
-    const int x = n % nx;
-    const int t = n / nx;
-    const int y = t % ny;
-    const int z = t / ny;
-    const int nxy = nx * ny;
-    // upstream coordinates x - c
-    const int xs[3] = {x, wrapm(x - 1, nx), wrapm(x + 1, nx)};        // c_x = 0, +1, -1
-    const int ys[3] = {y * nx, wrapm(y - 1, ny) * nx, wrapm(y + 1, ny) * nx};
-    const int zs[3] = {z * nxy, wrapm(z - 1, nz) * nxy, wrapm(z + 1, nz) * nxy};
-
-    float d[kQ];
-#pragma unroll
-    for (int p = 0; p < kQ; ++p) {
-        const int ix = cx(p) == 0 ? 0 : (cx(p) > 0 ? 1 : 2);
-        const int iy = cy(p) == 0 ? 0 : (cy(p) > 0 ? 1 : 2);
-        const int iz = cz(p) == 0 ? 0 : (cz(p) > 0 ? 1 : 2);
-        const int s = xs[ix] + ys[iy] + zs[iz];
-        if (WALLS && p != 0 && solid[s])
-            d[p] = src[(long long)opp(p) * Np + n];
-        else
-            d[p] = src[(long long)p * Np + s];
+    const long long Np = a.Np;
+    if (CELLS) {
+        a.G[n] = 0.f;
+        a.G[Np + n] = 0.f;
+        a.G[2 * Np + n] = 0.f;
+        a.th[n] = 0.f;
     }
-
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int p = 0; p < kQ; ++p) {
@@ -68,17 +70,6 @@ k_lb(const float *__restrict__ src, float *__restrict__ dst, const uint8_t *__re
         if (cx(p)) jx += cx(p) > 0 ? d[p] : -d[p];
         if (cy(p)) jy += cy(p) > 0 ? d[p] : -d[p];
         if (cz(p)) jz += cz(p) > 0 ? d[p] : -d[p];
-    }
-    float gx = gx0, gy = gy0, gz = gz0, T = tau0;
-    if (CELLS) {
-        gx += G[n];
-        gy += G[Np + n];
-        gz += G[2 * Np + n];
-        T += delta * th[n];
-        G[n] = 0.f;
-        G[Np + n] = 0.f;
-        G[2 * Np + n] = 0.f;
-        th[n] = 0.f;
     }
     const float rho = 1.0f + drho;
     const float irho = 1.0f / rho;
@@ -106,20 +97,236 @@ k_lb(const float *__restrict__ src, float *__restrict__ dst, const uint8_t *__re
             if (cx(p) && cz(p)) pxz += cx(p) * cz(p) > 0 ? neq : -neq;
             if (cy(p) && cz(p)) pyz += cy(p) * cz(p) > 0 ? neq : -neq;
         }
-        dst[(long long)p * Np + n] = d[p] - om * neq + df;
+        a.dst[(long long)p * Np + n] = d[p] - om * neq + df;
     }
-    U[n] = ux;
-    U[Np + n] = uy;
-    U[2 * Np + n] = uz;
+    a.U[n] = ux;
+    a.U[Np + n] = uy;
+    a.U[2 * Np + n] = uz;
     if (SIGMA) {
-        S[n] = -ff * pxx;
-        S[Np + n] = -ff * pyy;
-        S[2 * Np + n] = -ff * pzz;
-        S[3 * Np + n] = -ff * pxy;
-        S[4 * Np + n] = -ff * pxz;
-        S[5 * Np + n] = -ff * pyz;
+        a.S[n] = -ff * pxx;
+        a.S[Np + n] = -ff * pyy;
+        a.S[2 * Np + n] = -ff * pzz;
+        a.S[3 * Np + n] = -ff * pxy;
+        a.S[4 * Np + n] = -ff * pxz;
+        a.S[5 * Np + n] = -ff * pyz;
     }
-    if (!(rho > 0.0f) || !(usq <= mach2)) atomicOr(&flags[FLAG_UNSTABLE], 1);
+    if (!(rho > 0.0f) || !(usq <= a.mach2)) atomicOr(&a.flags[FLAG_UNSTABLE], 1);
+    if (WALLS && (lk & 0x7FFFEu)) {  // nodes next to a wall only
+        const int nxy = a.nx * a.ny;
+#pragma unroll 1
+        for (int p = 1; p < kQ; ++p) {
+            if (!((lk >> p) & 1u)) continue;
+            const int xd = wrapm(x + cx(p), a.nx), yd = wrapm(y + cy(p), a.ny), zd = wrapm(z + cz(p), a.nz);
+            // read back this thread's own store of d*_p
+            a.dst[(long long)kOppTab[p] * Np + (xd + a.nx * yd + nxy * zd)] = a.dst[(long long)p * Np + n];
+        }
+    }
+}
+
+// One thread per node; the 19 upstream deviations are pulled straight from
+// global memory (used when rows are not a multiple of 16 bytes).
+template <bool WALLS, bool CELLS, bool SIGMA>
+__global__ void __launch_bounds__(kLbThreads) k_lb(LbArgs a)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= a.N) return;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x = n % nx;
+    const int t = n / nx;
+    const int y = t % ny;
+    const int z = t / ny;
+    const int nxy = nx * ny;
+    // upstream coordinates x - c (index 1: c = +1, index 2: c = -1)
+    const int xs[3] = {x, wrapm(x - 1, nx), wrapm(x + 1, nx)};
+    const int ys[3] = {y * nx, wrapm(y - 1, ny) * nx, wrapm(y + 1, ny) * nx};
+    const int zs[3] = {z * nxy, wrapm(z - 1, nz) * nxy, wrapm(z + 1, nz) * nxy};
+    // Pull without any test: at a wall the upstream slot is a solid node's,
+    // into which this node wrote its reflected population last pass.
+    const uint32_t lk = WALLS ? a.links[n] : 0u;
+    float d[kQ];
+#pragma unroll
+    for (int p = 0; p < kQ; ++p) {
+        const int ix = cx(p) == 0 ? 0 : (cx(p) > 0 ? 1 : 2);
+        const int iy = cy(p) == 0 ? 0 : (cy(p) > 0 ? 1 : 2);
+        const int iz = cz(p) == 0 ? 0 : (cz(p) > 0 ? 1 : 2);
+        d[p] = a.src[(long long)p * a.Np + (xs[ix] + ys[iy] + zs[iz])];
+    }
+    float gx = a.gx0, gy = a.gy0, gz = a.gz0, T = a.tau0;
+    if (CELLS) {
+        gx += a.G[n];
+        gy += a.G[a.Np + n];
+        gz += a.G[2 * a.Np + n];
+        T += a.delta * a.th[n];
+    }
+    if (WALLS && (lk >> 31)) return;  // solid node: nothing to collide
+    collide_node<WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, n, x, y, z);
+}
+
+// ---------------------------------------------------------------------------
+// Row-staged lattice pass.  A row is the nx nodes at fixed (y, z).  Every
+// CTA is persistent and walks batches of B consecutive y-rows at one z; for
+// each batch
+// it brings into shared memory, with asynchronous bulk copies completing on
+// an mbarrier, the upstream row of every speed (row (y - c_y, z - c_z) of
+// plane p) plus the batch's own rows of G, theta and the link mask, into a
+// ring of kStages buffers (kStages - 1 batches in flight while one is
+// computed).  The bytes in flight
+// are then bounded by shared memory, not by registers; the x shift of the
+// pull is an index into the staged row.  Needs nx * 4 bytes to be a multiple
+// of 16 (bulk-copy granularity).
+// ---------------------------------------------------------------------------
+constexpr int kStThreads = 256;
+constexpr int kStages = 4;        // batches in the shared-memory ring (kStages - 1 in flight)
+constexpr int kStageBytes = 24 * 1024;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Wait for phase `parity` of the mbarrier, for at most kWaitCycles; false on
+// timeout (the caller raises the timeout flag).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+struct StageLayout {
+    int B;        // rows per batch
+    int planes;   // staged planes per row: 19 (+4 G, theta) (+1 links)
+    int stage_floats;
+};
+
+template <bool WALLS, bool CELLS, bool SIGMA>
+__global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout L, int nbatches)
+{
+    extern __shared__ __align__(128) float sm[];
+    __shared__ __align__(8) unsigned long long bars[kStages];
+    __shared__ int abort_flag;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int B = L.B;
+    const uint32_t row_bytes = (uint32_t)nx * 4u;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kStages; ++k) mbar_init(smem_addr(&bars[k]), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // A batch is rows y0 .. y0 + nb - 1 at one z (nyb batches per z slab).
+    // Staged plane k, batch row b sits at stage + (k * B + b) * nx.  For a
+    // speed p the upstream rows y - c_y are contiguous in plane p except
+    // where they wrap in y, so each plane needs one copy, or two.
+    const int nyb = (ny + B - 1) / B;
+    auto issue = [&](int batch, int stage) {
+        if (threadIdx.x >= 32) return;
+        const int z = batch / nyb, y0 = (batch - z * nyb) * B;
+        const int nb = min(B, ny - y0);
+        const uint32_t bar = smem_addr(&bars[stage]);
+        if (threadIdx.x == 0) mbar_expect_tx(bar, (uint32_t)(L.planes * nb) * row_bytes);
+        __syncwarp();
+        float *base = sm + (size_t)stage * L.stage_floats;
+        for (int k = threadIdx.x; k < L.planes; k += 32) {
+            float *dst = base + (size_t)k * B * nx;
+            if (k < kQ) {
+                const int zs = wrapm(z - cz(k), nz);
+                const float *plane = a.src + (long long)k * a.Np + (long long)zs * ny * nx;
+                int ys = y0 - cy(k);  // first upstream row, may be -1 or run past ny
+                int b = 0;
+                while (b < nb) {
+                    const int yr = wrapm(ys + b, ny);
+                    const int run = min(nb - b, ny - yr);
+                    bulk_g2s(smem_addr(dst + (size_t)b * nx), plane + (long long)yr * nx, (uint32_t)run * row_bytes, bar);
+                    b += run;
+                }
+            } else {
+                const long long off = ((long long)z * ny + y0) * nx;
+                const float *src;
+                if (CELLS && k < kQ + 3)
+                    src = a.G + (long long)(k - kQ) * a.Np + off;
+                else if (CELLS && k == kQ + 3)
+                    src = a.th + off;
+                else
+                    src = reinterpret_cast<const float *>(a.links) + off;
+                bulk_g2s(smem_addr(dst), src, (uint32_t)nb * row_bytes, bar);
+            }
+        }
+    };
+
+    int it = 0;
+    int batch = blockIdx.x;
+    for (int k = 0; k < kStages; ++k)
+        if (batch + k * (int)gridDim.x < nbatches) issue(batch + k * gridDim.x, k);
+    for (; batch < nbatches; batch += gridDim.x, ++it) {
+        const int stage = it % kStages;
+        const uint32_t bar = smem_addr(&bars[stage]);
+        if (!mbar_wait(bar, (uint32_t)((it / kStages) & 1))) {
+            atomicOr(&a.flags[FLAG_TIMEOUT], 1);
+            abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        const float *st = sm + (size_t)stage * L.stage_floats;
+        const int z = batch / nyb, y0 = (batch - z * nyb) * B;
+        const int nb = min(B, ny - y0);
+        for (int l = threadIdx.x; l < nb * nx; l += blockDim.x) {
+            const int b = l / nx, x = l - b * nx;
+            const int y = y0 + b;
+            const int n = (y + ny * z) * nx + x;
+            const uint32_t lk = WALLS ? reinterpret_cast<const uint32_t *>(st)[((size_t)(kQ + (CELLS ? 4 : 0)) * B + b) * nx + x] : 0u;
+            if (WALLS && (lk >> 31)) continue;
+            float d[kQ];
+#pragma unroll
+            for (int p = 0; p < kQ; ++p) {
+                const int xs = cx(p) == 0 ? x : wrapm(x - cx(p), nx);
+                d[p] = st[((size_t)p * B + b) * nx + xs];
+            }
+            float gx = a.gx0, gy = a.gy0, gz = a.gz0, T = a.tau0;
+            if (CELLS) {
+                gx += st[((size_t)(kQ + 0) * B + b) * nx + x];
+                gy += st[((size_t)(kQ + 1) * B + b) * nx + x];
+                gz += st[((size_t)(kQ + 2) * B + b) * nx + x];
+                T += a.delta * st[((size_t)(kQ + 3) * B + b) * nx + x];
+            }
+            collide_node<WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, n, x, y, z);
+        }
+        __syncthreads();  // the stage is free again
+        if (batch + kStages * (int)gridDim.x < nbatches) issue(batch + kStages * gridDim.x, stage);
+    }
+    if (abort_flag) {
+        // let any copy still in flight land before the CTA's memory goes away
+        for (int k = 0; k < kStages; ++k) mbar_wait(smem_addr(&bars[k]), 0);
+    }
 }
 
 __global__ void k_rho(const float *__restrict__ pops, const uint8_t *__restrict__ solid,
@@ -221,30 +428,112 @@ k_budget_final(const double *__restrict__ part, int nblocks, const double *__res
 
 }  // namespace
 
-void launch_lb(const Dev &d, const Params &p, int parity, cudaStream_t s)
+StageLayout stage_layout(const Dev &d)
 {
-    const float *src = d.pops[parity];
-    float *dst = d.pops[parity ^ 1];
-    const int grid = (d.N + kLbThreads - 1) / kLbThreads;
+    StageLayout L;
+    L.planes = kQ + (d.nc > 0 ? 4 : 0) + (d.walls ? 1 : 0);
+    const int row_floats = d.nx;
+    // about kStageBytes per stage, whole rows, at most one y column of rows;
+    // a multiple of the rows that fill the CTA's threads when rows are short
+    int B = kStageBytes / (L.planes * row_floats * 4);
+    B = B < 1 ? 1 : (B > d.ny ? d.ny : B);
+    if (row_floats < kStThreads && B * row_floats > kStThreads) B -= B % (kStThreads / row_floats > 0 ? kStThreads / row_floats : 1);
+    L.B = B;
+    L.stage_floats = L.planes * B * row_floats;
+    return L;
+}
+
+bool staged_ok(const Dev &d)
+{
+    if (d.nx % 4 != 0) return false;  // rows must be whole 16-byte units
+    const StageLayout L = stage_layout(d);
+    return (size_t)kStages * L.stage_floats * sizeof(float) <= 200u * 1024u;
+}
+
+template <bool W, bool C, bool S_>
+void prepare_lb_t(Dev &d)
+{
+    d.lb_grid = 0;
+    if (!staged_ok(d)) return;
+    const StageLayout L = stage_layout(d);
+    const size_t smem = (size_t)kStages * L.stage_floats * sizeof(float);
+    cudaFuncSetAttribute(k_lb_staged<W, C, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_staged<W, C, S_>, kStThreads, smem);
+    int grid = sms * (per_sm > 0 ? per_sm : 1);
+    d.lb_grid = grid > nbatches ? nbatches : grid;
+    d.lb_smem = smem;
+}
+
+template <bool W, bool C, bool S_>
+void launch_lb_t(const Dev &d, const LbArgs &a, cudaStream_t s)
+{
+    if (d.lb_grid > 0) {
+        const StageLayout L = stage_layout(d);
+        const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
+        k_lb_staged<W, C, S_><<<d.lb_grid, kStThreads, d.lb_smem, s>>>(a, L, nbatches);
+    } else {
+        k_lb<W, C, S_><<<(d.N + kLbThreads - 1) / kLbThreads, kLbThreads, 0, s>>>(a);
+    }
+}
+
+void prepare_lb(Dev &d)
+{
     const bool cells = d.nc > 0, sig = d.S != nullptr, walls = d.walls != 0;
-#define RBC_LB(W, C, S_)                                                                          \
-    k_lb<W, C, S_><<<grid, kLbThreads, 0, s>>>(src, dst, d.solid, d.G, d.theta, d.U, d.S, d.flags, \
-                                               d.nx, d.ny, d.nz, d.N, d.Np, p.gext[0], p.gext[1], \
-                                               p.gext[2], p.tau0, p.delta, p.mach2)
     if (walls) {
         if (cells) {
-            if (sig) RBC_LB(true, true, true); else RBC_LB(true, true, false);
+            if (sig) prepare_lb_t<true, true, true>(d); else prepare_lb_t<true, true, false>(d);
         } else {
-            if (sig) RBC_LB(true, false, true); else RBC_LB(true, false, false);
+            if (sig) prepare_lb_t<true, false, true>(d); else prepare_lb_t<true, false, false>(d);
         }
     } else {
         if (cells) {
-            if (sig) RBC_LB(false, true, true); else RBC_LB(false, true, false);
+            if (sig) prepare_lb_t<false, true, true>(d); else prepare_lb_t<false, true, false>(d);
         } else {
-            if (sig) RBC_LB(false, false, true); else RBC_LB(false, false, false);
+            if (sig) prepare_lb_t<false, false, true>(d); else prepare_lb_t<false, false, false>(d);
         }
     }
-#undef RBC_LB
+}
+
+void launch_lb(const Dev &d, const Params &p, int parity, cudaStream_t s)
+{
+    LbArgs a;
+    a.src = d.pops[parity];
+    a.dst = d.pops[parity ^ 1];
+    a.links = d.links;
+    a.G = d.G;
+    a.th = d.theta;
+    a.U = d.U;
+    a.S = d.S;
+    a.flags = d.flags;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.nz = d.nz;
+    a.N = d.N;
+    a.Np = d.Np;
+    a.gx0 = p.gext[0];
+    a.gy0 = p.gext[1];
+    a.gz0 = p.gext[2];
+    a.tau0 = p.tau0;
+    a.delta = p.delta;
+    a.mach2 = p.mach2;
+    const bool cells = d.nc > 0, sig = d.S != nullptr, walls = d.walls != 0;
+    if (walls) {
+        if (cells) {
+            if (sig) launch_lb_t<true, true, true>(d, a, s); else launch_lb_t<true, true, false>(d, a, s);
+        } else {
+            if (sig) launch_lb_t<true, false, true>(d, a, s); else launch_lb_t<true, false, false>(d, a, s);
+        }
+    } else {
+        if (cells) {
+            if (sig) launch_lb_t<false, true, true>(d, a, s); else launch_lb_t<false, true, false>(d, a, s);
+        } else {
+            if (sig) launch_lb_t<false, false, true>(d, a, s); else launch_lb_t<false, false, false>(d, a, s);
+        }
+    }
 }
 
 void launch_rho(const Dev &d, int parity, cudaStream_t s)

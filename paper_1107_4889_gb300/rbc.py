@@ -266,7 +266,10 @@ class Solver:
         self.N = int(geometry["nx"]) * int(geometry["ny"]) * int(geometry["nz"])
         self.n = 0 if cells is None else int(np.asarray(cells["pos"]).shape[0])
         with torch.cuda.device(self.device):
-            self.stream = torch.cuda.current_stream() if stream is None else stream
+            # a stream of its own: the legacy default stream cannot be
+            # captured into CUDA graphs, and events recorded on self.stream
+            # then time exactly the solver's work
+            self.stream = torch.cuda.Stream(self.device) if stream is None else stream
             self.workspace_bytes = rbc_workspace_size(geometry, cells, params)
             self.workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
             self.handle = rbc_init(geometry, cells, params, self.workspace.data_ptr(), self.workspace_bytes,
