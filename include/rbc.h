@@ -175,6 +175,35 @@ int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2]);
 /* Kernel launches one rbc_step(h, 1) enqueues. */
 int rbc_launches_per_step(const rbc_handle *h);
 
+/* Size of the static device scratch of rbc_neighbors_noalloc, in ints
+ * (4 MiB). */
+#define RBC_NOALLOC_SCRATCH_INTS (1 << 20)
+
+/* Candidate-partner lists of n cells without any device allocation and
+ * without caller-provided scratch.  The paper has no counterpart: this is a
+ * convenience for callers that cannot call cudaMalloc -- code running where
+ * device memory is fully committed to buffers it does not own, or a host
+ * that forbids allocation outside its own pool -- and so cannot lend the
+ * workspace rbc_init needs.  It builds the lists rbc_neighbors reports after
+ * a step: partners j != i with |R_i - R_j|^2 < r_cut^2 (minimum image along
+ * periodic axes, FP64, no fused multiply-add), each list sorted by index.
+ *   pos           device, 3n doubles, inside [0, n_axis) on every axis
+ *   nx, ny, nz    box; periodic[3] host flags
+ *   counts        device, n ints (out); lists device, n * max_per_cell ints
+ *   max_per_cell  1..128; stream: cudaStream_t (NULL: legacy default)
+ * Its scratch (an overflow flag, bin counts and 32 slots per bin of a grid
+ * of bins no smaller than r_cut) is a static device array of
+ * RBC_NOALLOC_SCRATCH_INTS ints that every GPU loading the library holds
+ * until the process exits; boxes whose grid needs more return RBC_EINVAL.
+ * All calls share that array, so calls that overlap on the GPU race and
+ * must be serialised.  The first call on a device looks up the array's
+ * address (cudaGetSymbolAddress) with that device current: make it before
+ * any stream capture.  Synchronises the stream; RBC_ENOMEM when a bin holds
+ * more than 32 cells or a list exceeds max_per_cell; rbc_last_error(NULL)
+ * describes failures. */
+int rbc_neighbors_noalloc(const double *pos, int n, int nx, int ny, int nz, const int periodic[3],
+                          double r_cut, int *counts, int *lists, int max_per_cell, void *stream);
+
 /* Release the handle, its graphs, events and owned stream (not the caller's
  * workspace).  NULL is ignored. */
 void rbc_free(rbc_handle *h);

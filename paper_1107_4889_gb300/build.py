@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "librbc.so")
-SOURCES = ["api.cu", "lb.cu", "cells.cu"]
+SOURCES = ["api.cu", "lb.cu", "cells.cu", "noalloc.cu"]
 HEADERS = ["internal.h", "rbc_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

@@ -292,6 +292,11 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
 
 }  // namespace
 
+namespace rbc {
+// lets other translation units report through rbc_last_error(NULL)
+void set_thread_error(const std::string &msg) { g_thread_err = msg; }
+}  // namespace rbc
+
 struct rbc_handle {
     Problem P;
     Dev d;

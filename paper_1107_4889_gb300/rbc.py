@@ -61,7 +61,7 @@ class rbc_stats_t(ctypes.Structure):
 #: symbols include/rbc.h declares
 EXPORTS = ["rbc_default_params", "rbc_workspace_size", "rbc_init", "rbc_step", "rbc_fields",
            "rbc_stats", "rbc_cell_diag", "rbc_neighbors", "rbc_set_timing", "rbc_kernel_times",
-           "rbc_launches_per_step", "rbc_free", "rbc_last_error"]
+           "rbc_launches_per_step", "rbc_neighbors_noalloc", "rbc_free", "rbc_last_error"]
 
 _lib = None
 
@@ -95,6 +95,10 @@ def load(path: str = LIB_PATH):
     L.rbc_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.rbc_kernel_times.argtypes = [ctypes.c_void_p, _D, _I64]
     L.rbc_launches_per_step.argtypes = [ctypes.c_void_p]
+    L.rbc_neighbors_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        _I, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p]
+    L.rbc_neighbors_noalloc.restype = ctypes.c_int
     L.rbc_free.argtypes = [ctypes.c_void_p]
     L.rbc_free.restype = None
     L.rbc_last_error.argtypes = [ctypes.c_void_p]
@@ -242,6 +246,17 @@ def rbc_kernel_times(h):
 
 def rbc_launches_per_step(h) -> int:
     return int(load().rbc_launches_per_step(h))
+
+
+def rbc_neighbors_noalloc(pos_ptr: int, n: int, dims, periodic, r_cut: float, counts_ptr: int, lists_ptr: int,
+                          max_per_cell: int, stream: int | None):
+    """Candidate-partner lists without device allocation (device pointers in
+    and out; see include/rbc.h).  For callers that cannot allocate device
+    memory: the scratch is a static device array inside the library."""
+    per = (ctypes.c_int * 3)(*[int(p) for p in periodic])
+    _check(load().rbc_neighbors_noalloc(ctypes.c_void_p(pos_ptr), int(n), int(dims[0]), int(dims[1]), int(dims[2]),
+                                        per, float(r_cut), ctypes.c_void_p(counts_ptr), ctypes.c_void_p(lists_ptr),
+                                        int(max_per_cell), ctypes.c_void_p(stream)))
 
 
 def rbc_free(h):
