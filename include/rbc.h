@@ -128,15 +128,18 @@ int rbc_workspace_size(const rbc_geometry *geom, const rbc_cells *cells,
 /* Validate the problem, carve the caller's device workspace (at least
  * rbc_workspace_size bytes, 256-byte aligned, owned by the caller and kept
  * alive until rbc_free), copy geometry and cells to the device, set the
- * fluid at rest (f = f^eq(rho = 1, u = 0)) and capture one step as CUDA
- * graphs on params->stream.  Synchronises that stream.  *out receives the
+ * fluid at rest (f = f^eq(rho = 1, u = 0)), capture one step as CUDA graphs
+ * on params->stream and build the cell list and Gay-Berne forces of the
+ * initial poses.  Synchronises that stream.  *out receives the
  * handle.  Errors: RBC_EINVAL, RBC_ENOMEM (workspace too small), RBC_ECUDA. */
 int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params *params,
              void *workspace, size_t workspace_bytes, rbc_handle **out);
 
 /* Enqueue n coupled steps on the handle's stream and return without waiting
- * (Sec. 2, App. A; the step order is: cell list and Gay-Berne forces,
- * sampling + rigid update + spreading per cell, lattice pass).  Returns
+ * (Sec. 2, App. A).  One step: sampling, rigid update and spreading per cell
+ * at the current poses (whose cell list and Gay-Berne forces are already
+ * known), then the lattice pass, while the cell list and Gay-Berne forces of
+ * the new poses are computed alongside it for the next step.  Returns
  * RBC_EUNSTABLE / RBC_ENOMEM if an earlier synchronising call saw the device
  * flags raised; RBC_EINVAL for n < 0. */
 int rbc_step(rbc_handle *h, int64_t n);
@@ -156,7 +159,8 @@ int rbc_stats(rbc_handle *h, rbc_stats_t *out);
  * returned to the fluid).  Host buffer; synchronises. */
 int rbc_cell_diag(rbc_handle *h, double *out);
 
-/* Candidate partners of every cell from the last cell-list pass: counts[n]
+/* Candidate partners of every cell at its current pose (the cell list is
+ * rebuilt at rbc_init and at the end of every step): counts[n]
  * and lists[n*max_per_cell], each list sorted by partner index; partners are
  * the j != i with |R_i - R_j|^2 < r_cut^2 (minimum image along periodic
  * axes, FP64, no fused multiply-add).  Returns RBC_ENOMEM if a list is longer
@@ -164,11 +168,13 @@ int rbc_cell_diag(rbc_handle *h, double *out);
 int rbc_neighbors(rbc_handle *h, int *counts, int *lists, int max_per_cell);
 
 /* Kernel timing.  rbc_set_timing(h, capacity) makes the next `capacity`
- * steps record CUDA events around the lattice pass and around the per-step
- * cell work on the handle's stream (capacity 0 turns it off).
- * rbc_kernel_times synchronises and returns for k = 0 (lattice pass) and
- * k = 1 (cell work) the summed milliseconds ms[k] and the number of timed
- * launches count[k], then clears them. */
+ * steps record CUDA events inside the step graph on the handle's stream:
+ * before sampling, after spreading and after the lattice pass (capacity 0
+ * turns it off).  rbc_kernel_times synchronises and returns for k = 0 (the
+ * lattice pass, which runs alongside the next step's cell list and
+ * Gay-Berne forces) and k = 1 (sampling, rigid update and spreading) the
+ * summed milliseconds ms[k] and the number of timed launches count[k], then
+ * clears them. */
 int rbc_set_timing(rbc_handle *h, int capacity);
 int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2]);
 

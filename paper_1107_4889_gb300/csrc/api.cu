@@ -34,6 +34,8 @@ struct Problem {
     Params p;
     int nb[3], nbins, bin_cap, max_nbr;
     double bin_size[3];
+    int wnb[3], nwbins;
+    double wbin_size[3];
     std::vector<int> wall_start, wall_xyz;
     int nw;
     int budget_blocks;
@@ -187,12 +189,19 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
         for (int a = 0; a < 3; ++a) P.bin_size[a] = dims[a];
     }
     P.nbins = P.nb[0] * P.nb[1] * P.nb[2];
+    // wall-particle grid: bins no smaller than the wall candidate radius
+    // (plus the FP32 prefilter's margin)
+    for (int a = 0; a < 3; ++a) {
+        P.wnb[a] = std::max(1, (int)std::floor(dims[a] / (rcw + 0.01)));
+        P.wbin_size[a] = (double)dims[a] / P.wnb[a];
+    }
+    P.nwbins = P.wnb[0] * P.wnb[1] * P.wnb[2];
     P.bin_cap = q.bin_capacity > 0 ? q.bin_capacity : 32;
     P.max_nbr = q.max_neighbors > 0 ? std::min(q.max_neighbors, 128) : 64;
 
     // wall particles: solid nodes with a fluid node among their 18 links
     P.nw = 0;
-    P.wall_start.assign(P.nbins + 1, 0);
+    P.wall_start.assign(P.nwbins + 1, 0);
     P.wall_xyz.clear();
     if (P.any_solid && nc > 0) {
         std::vector<int> xyz, bins;
@@ -211,15 +220,16 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
                     if (!wet) continue;
                     const int X[3] = {x, y, z};
                     int b[3];
-                    for (int a = 0; a < 3; ++a) b[a] = std::min(P.nb[a] - 1, (int)std::floor(X[a] / P.bin_size[a]));
-                    bins.push_back(b[0] + P.nb[0] * (b[1] + P.nb[1] * b[2]));
+                    for (int a = 0; a < 3; ++a)
+                        b[a] = std::min(P.wnb[a] - 1, (int)std::floor(X[a] / P.wbin_size[a]));
+                    bins.push_back(b[0] + P.wnb[0] * (b[1] + P.wnb[1] * b[2]));
                     xyz.push_back(x);
                     xyz.push_back(y);
                     xyz.push_back(z);
                 }
         P.nw = (int)bins.size();
         for (int w = 0; w < P.nw; ++w) P.wall_start[bins[w] + 1]++;
-        for (int b = 0; b < P.nbins; ++b) P.wall_start[b + 1] += P.wall_start[b];
+        for (int b = 0; b < P.nwbins; ++b) P.wall_start[b + 1] += P.wall_start[b];
         std::vector<int> cur(P.wall_start.begin(), P.wall_start.end() - 1);
         P.wall_xyz.assign(3 * (size_t)P.nw, 0);
         for (int w = 0; w < P.nw; ++w) {
@@ -280,7 +290,12 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.nbr = cv.take<int>(n * P.max_nbr);
     d.nbr_count = cv.take<int>(n);
     d.nw = P.nw;
-    d.wall_start = cv.take<int>(P.nbins + 1);
+    for (int a = 0; a < 3; ++a) {
+        d.wnb[a] = P.wnb[a];
+        d.wbin_size[a] = P.wbin_size[a];
+    }
+    d.nwbins = P.nwbins;
+    d.wall_start = cv.take<int>(P.nwbins + 1);
     d.wall_xyz = cv.take<int>(3 * (size_t)std::max(P.nw, 1));
     d.flags = cv.take<int>(8);
     d.clamps = cv.take<unsigned long long>(1);
@@ -300,12 +315,19 @@ void set_thread_error(const std::string &msg) { g_thread_err = msg; }
 struct rbc_handle {
     Problem P;
     Dev d;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr, side = nullptr;
     bool own_stream = false;
-    cudaGraphExec_t g_cells = nullptr, g_lb[2] = {nullptr, nullptr};
+    // g_pro: cell list + Gay-Berne of the initial poses (run once at init);
+    // g_step[parity]: sample -> rigid -> spread, then the lattice pass on
+    // the main stream alongside the next step's cell list + Gay-Berne on the
+    // side stream (they touch disjoint data), joined at the end
+    cudaGraphExec_t g_pro = nullptr, g_step[2] = {nullptr, nullptr};
+    cudaGraph_t src[3] = {nullptr, nullptr, nullptr};  // kept: exec updates name their nodes
+    cudaGraphNode_t ev_node[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    cudaEvent_t ev_dummy[3] = {nullptr, nullptr, nullptr}, fork_ev = nullptr, join_ev = nullptr;
     int64_t step = 0;
     int timing_cap = 0, timing_used = 0;
-    std::vector<cudaEvent_t> ev;  // 3 per timed step
+    std::vector<cudaEvent_t> ev;  // 3 per timed step: before sample, after spread, after the lattice pass
     std::string err;
     int device = 0;
     std::vector<uint8_t> solid_host;
@@ -319,29 +341,66 @@ struct rbc_handle {
                         std::string(#call) + ": " + cudaGetErrorString(e_));                        \
     } while (0)
 
-static int capture(rbc_handle *h, void (*body)(rbc_handle *, int), int arg, cudaGraphExec_t *out)
+static int capture(rbc_handle *h, void (*body)(rbc_handle *, int), int arg, cudaGraphExec_t *out,
+                   cudaGraphNode_t *ev_nodes, cudaGraph_t *keep)
 {
     cudaGraph_t graph = nullptr;
     RBC_CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     body(h, arg);
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     if (e != cudaSuccess) return fail(&h->err, RBC_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    if (ev_nodes) {
+        // find the event-record nodes of the three timing points
+        size_t count = 0;
+        cudaGraphGetNodes(graph, nullptr, &count);
+        std::vector<cudaGraphNode_t> nodes(count);
+        cudaGraphGetNodes(graph, nodes.data(), &count);
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t evr;
+            if (cudaGraphEventRecordNodeGetEvent(nd, &evr) != cudaSuccess) continue;
+            for (int k = 0; k < 3; ++k)
+                if (evr == h->ev_dummy[k]) ev_nodes[k] = nd;
+        }
+    }
     e = cudaGraphInstantiate(out, graph, 0);
-    cudaGraphDestroy(graph);
+    *keep = graph;
     if (e != cudaSuccess) return fail(&h->err, RBC_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    if (ev_nodes && (!ev_nodes[0] || !ev_nodes[1] || !ev_nodes[2]))
+        return fail(&h->err, RBC_ECUDA, "timing nodes not found in the step graph");
     return RBC_OK;
 }
 
-static void body_cells(rbc_handle *h, int)
+static void body_prologue(rbc_handle *h, int)
 {
     launch_bin(h->d, h->P.p, h->stream);
     launch_gb(h->d, h->P.p, h->stream);
-    launch_sample(h->d, h->P.p, h->stream);
-    launch_rigid(h->d, h->P.p, h->stream);
-    launch_spread(h->d, h->P.p, h->stream);
 }
 
-static void body_lb(rbc_handle *h, int parity) { launch_lb(h->d, h->P.p, parity, h->stream); }
+static void body_step(rbc_handle *h, int parity)
+{
+    const bool cells = h->d.nc > 0;
+    cudaEventRecordWithFlags(h->ev_dummy[0], h->stream, cudaEventRecordExternal);
+    if (cells) {
+        launch_sample(h->d, h->P.p, h->stream);
+        launch_rigid(h->d, h->P.p, h->stream);
+        launch_spread(h->d, h->P.p, h->stream);
+    }
+    cudaEventRecordWithFlags(h->ev_dummy[1], h->stream, cudaEventRecordExternal);
+    if (cells) {
+        cudaEventRecord(h->fork_ev, h->stream);
+        cudaStreamWaitEvent(h->side, h->fork_ev, 0);
+    }
+    launch_lb(h->d, h->P.p, parity, h->stream);
+    cudaEventRecordWithFlags(h->ev_dummy[2], h->stream, cudaEventRecordExternal);
+    if (cells) {
+        launch_bin(h->d, h->P.p, h->side);
+        launch_gb(h->d, h->P.p, h->side);
+        cudaEventRecord(h->join_ev, h->side);
+        cudaStreamWaitEvent(h->stream, h->join_ev, 0);
+    }
+}
 
 extern "C" {
 
@@ -478,7 +537,7 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
             RBC_CU(cudaMemsetAsync(d.Fm, 0, sizeof(double) * 3 * n, s));
             RBC_CU(cudaMemsetAsync(d.Tm, 0, sizeof(double) * 3 * n, s));
             RBC_CU(cudaMemsetAsync(d.nbr_count, 0, sizeof(int) * n, s));
-            RBC_CU(cudaMemcpyAsync(d.wall_start, P.wall_start.data(), sizeof(int) * (P.nbins + 1),
+            RBC_CU(cudaMemcpyAsync(d.wall_start, P.wall_start.data(), sizeof(int) * (P.nwbins + 1),
                                    cudaMemcpyHostToDevice, s));
             if (P.nw > 0)
                 RBC_CU(cudaMemcpyAsync(d.wall_xyz, P.wall_xyz.data(), sizeof(int) * 3 * (size_t)P.nw,
@@ -490,14 +549,20 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
         prepare_lb(h->d);
         if (n > 0) prepare_cells(h->P.p);
         RBC_CU(cudaGetLastError());
+        RBC_CU(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        RBC_CU(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+        RBC_CU(cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
+        for (int k = 0; k < 3; ++k) RBC_CU(cudaEventCreate(&h->ev_dummy[k]));
         if (n > 0) {
-            int r = capture(h, body_cells, 0, &h->g_cells);
+            int r = capture(h, body_prologue, 0, &h->g_pro, nullptr, &h->src[2]);
             if (r != RBC_OK) return r;
         }
         for (int par = 0; par < 2; ++par) {
-            int r = capture(h, body_lb, par, &h->g_lb[par]);
+            int r = capture(h, body_step, par, &h->g_step[par], h->ev_node[par], &h->src[par]);
             if (r != RBC_OK) return r;
         }
+        // cell list and Gay-Berne forces of the initial poses
+        if (h->g_pro) RBC_CU(cudaGraphLaunch(h->g_pro, s));
         RBC_CU(cudaStreamSynchronize(s));
         RBC_CU(cudaGetLastError());
         return RBC_OK;
@@ -532,15 +597,13 @@ int rbc_step(rbc_handle *h, int64_t n)
     for (int64_t k = 0; k < n; ++k) {
         const int par = (int)(h->step & 1);
         const bool timed = h->timing_used < h->timing_cap;
-        cudaEvent_t *ev = timed ? &h->ev[3 * (size_t)h->timing_used] : nullptr;
-        if (timed) RBC_CU(cudaEventRecord(ev[0], h->stream));
-        if (h->g_cells) RBC_CU(cudaGraphLaunch(h->g_cells, h->stream));
-        if (timed) RBC_CU(cudaEventRecord(ev[1], h->stream));
-        RBC_CU(cudaGraphLaunch(h->g_lb[par], h->stream));
-        if (timed) {
-            RBC_CU(cudaEventRecord(ev[2], h->stream));
-            h->timing_used++;
-        }
+        // each timed launch records into its own three events
+        for (int e = 0; e < 3; ++e)
+            RBC_CU(cudaGraphExecEventRecordNodeSetEvent(h->g_step[par], h->ev_node[par][e],
+                                                        timed ? h->ev[3 * (size_t)h->timing_used + e]
+                                                              : h->ev_dummy[e]));
+        RBC_CU(cudaGraphLaunch(h->g_step[par], h->stream));
+        if (timed) h->timing_used++;
         h->step++;
     }
     return RBC_OK;
@@ -676,7 +739,7 @@ int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2])
         RBC_CU(cudaEventElapsedTime(&b, h->ev[3 * k + 1], h->ev[3 * k + 2]));
         ms[0] += b;
         count[0]++;
-        if (h->g_cells) {
+        if (h->d.nc > 0) {
             ms[1] += a;
             count[1]++;
         }
@@ -689,17 +752,27 @@ int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2])
 int rbc_launches_per_step(const rbc_handle *h)
 {
     if (!h) return 0;
-    return 1 + (h->d.nc > 0 ? 5 : 0);
+    return 1 + (h->d.nc > 0 ? 5 : 0);  // bin-count clear is a memset node
 }
 
 void rbc_free(rbc_handle *h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    if (h->g_cells) cudaGraphExecDestroy(h->g_cells);
+    if (h->g_pro) cudaGraphExecDestroy(h->g_pro);
     for (int k = 0; k < 2; ++k)
-        if (h->g_lb[k]) cudaGraphExecDestroy(h->g_lb[k]);
+        if (h->g_step[k]) cudaGraphExecDestroy(h->g_step[k]);
+    for (int k = 0; k < 3; ++k)
+        if (h->src[k]) cudaGraphDestroy(h->src[k]);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    for (int k = 0; k < 3; ++k)
+        if (h->ev_dummy[k]) cudaEventDestroy(h->ev_dummy[k]);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }

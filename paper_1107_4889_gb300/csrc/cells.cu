@@ -30,7 +30,7 @@ namespace rbc {
 
 namespace {
 
-constexpr int kBinThreads = 128;
+constexpr int kBinThreads = 32;  // FP64-bound: spread the warps over all SMs
 constexpr int kGbWarps = 4;
 constexpr int kCellThreads = 128;
 constexpr int kRigidThreads = 32;
@@ -140,6 +140,8 @@ struct GbArgs {
     double L[3], rc2, rcw2, smin, smin_w, rw2, eps0, rho_floor, rho_cut;
     float rho_cut_f;  // FP32 prefilter bound (rho_cut with a safety margin)
     float rc_lo2, rc_hi2, rcw2_f, Lf[3];  // FP32 candidate band around r_cut, wall radius
+    int wnb[3];                           // wall-particle grid
+    float wbs[3];
 };
 
 __device__ __forceinline__ void min_image_f(float d[3], const int per[3], const float L[3])
@@ -207,6 +209,7 @@ __global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g)
 {
     __shared__ int s_cand[kGbWarps][kMaxNbr];
     __shared__ int s_sort[kGbWarps][kMaxNbr];
+    __shared__ int s_pre[kGbWarps][32], s_key[kGbWarps][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int i = blockIdx.x * kGbWarps + wid;
     if (i >= g.nc) return;  // uniform across the warp
@@ -220,42 +223,62 @@ __global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g)
     int lo[3], hi[3];
     for (int a = 0; a < 3; ++a) bin_range(b[a], g.nb[a], g.per[a], lo[a], hi[a]);
 
-    // 1. candidates: FP32 distance decides outside a band around r_cut; inside
-    //    the band the exact FP64 test (no fused multiply-add) decides, so the
-    //    partner sets are those of the FP64 test
+    // 1. candidates.  The lanes read the counts of the (up to 27) neighbour
+    //    bins at once and prefix-sum them, so the candidates are visited 32
+    //    at a time.  The FP32 distance decides outside a band around r_cut;
+    //    inside the band the exact FP64 test (no fused multiply-add)
+    //    decides, so the partner sets are those of the FP64 test.
+    const int bx = hi[0] - lo[0] + 1, by = hi[1] - lo[1] + 1, nbn = bx * by * (hi[2] - lo[2] + 1);
     int cnt = 0;
-    for (int oz = lo[2]; oz <= hi[2]; ++oz)
-        for (int oy = lo[1]; oy <= hi[1]; ++oy)
-            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
-                const int bb = wrap_bin(b[0] + ox, g.nb[0]) +
-                               g.nb[0] * (wrap_bin(b[1] + oy, g.nb[1]) + g.nb[1] * wrap_bin(b[2] + oz, g.nb[2]));
-                const int c = min(g.bin_count[bb], g.cap);
-                for (int k0 = 0; k0 < c; k0 += 32) {
-                    const int k = k0 + lane;
-                    bool pass = false;
-                    int j = -1;
-                    if (k < c) {
-                        j = g.bin_cells[bb * g.cap + k];
-                        if (j != i) {
-                            float df[3] = {Rif[0] - g.Rf[3 * j], Rif[1] - g.Rf[3 * j + 1], Rif[2] - g.Rf[3 * j + 2]};
-                            min_image_f(df, g.per, g.Lf);
-                            const float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
-                            if (r2f < g.rc_lo2) {
-                                pass = true;
-                            } else if (r2f <= g.rc_hi2) {
-                                double d[3] = {__dsub_rn(Ri[0], g.R[3 * j]), __dsub_rn(Ri[1], g.R[3 * j + 1]),
-                                               __dsub_rn(Ri[2], g.R[3 * j + 2])};
-                                min_image(d, g.per, g.L);
-                                pass = dist2_exact(d) < g.rc2;
-                            }
-                        }
+    {
+        int my_bb = 0, my_c = 0;
+        if (lane < nbn) {
+            const int ox = lo[0] + lane % bx, oy = lo[1] + (lane / bx) % by, oz = lo[2] + lane / (bx * by);
+            my_bb = wrap_bin(b[0] + ox, g.nb[0]) +
+                    g.nb[0] * (wrap_bin(b[1] + oy, g.nb[1]) + g.nb[1] * wrap_bin(b[2] + oz, g.nb[2]));
+            my_c = min(g.bin_count[my_bb], g.cap);
+        }
+        int incl = my_c;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        s_pre[wid][lane] = incl - my_c;
+        s_key[wid][lane] = my_bb;
+        __syncwarp();
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            bool pass = false;
+            int j = -1;
+            if (t < total) {
+                int k0 = 0, k1 = nbn - 1;  // last bin whose first candidate is <= t
+                while (k0 < k1) {
+                    const int mid = (k0 + k1 + 1) >> 1;
+                    if (s_pre[wid][mid] <= t) k0 = mid; else k1 = mid - 1;
+                }
+                j = g.bin_cells[s_key[wid][k0] * g.cap + (t - s_pre[wid][k0])];
+                if (j != i) {
+                    float df[3] = {Rif[0] - g.Rf[3 * j], Rif[1] - g.Rf[3 * j + 1], Rif[2] - g.Rf[3 * j + 2]};
+                    min_image_f(df, g.per, g.Lf);
+                    const float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
+                    if (r2f < g.rc_lo2) {
+                        pass = true;
+                    } else if (r2f <= g.rc_hi2) {
+                        double d[3] = {__dsub_rn(Ri[0], g.R[3 * j]), __dsub_rn(Ri[1], g.R[3 * j + 1]),
+                                       __dsub_rn(Ri[2], g.R[3 * j + 2])};
+                        min_image(d, g.per, g.L);
+                        pass = dist2_exact(d) < g.rc2;
                     }
-                    const unsigned m = __ballot_sync(0xffffffffu, pass);
-                    const int pos = cnt + __popc(m & lt);
-                    if (pass && pos < g.maxn) s_cand[wid][pos] = j;
-                    cnt += __popc(m);
                 }
             }
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            const int pos = cnt + __popc(m & lt);
+            if (pass && pos < g.maxn) s_cand[wid][pos] = j;
+            cnt += __popc(m);
+        }
+        __syncwarp();
+    }
     if (cnt > g.maxn) {
         if (lane == 0) atomicOr(&g.flags[FLAG_OVERFLOW], OVF_NBR);
         cnt = g.maxn;
@@ -294,32 +317,57 @@ __global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g)
         const Sym3 Aj{aj[0], aj[1], aj[2], aj[3], aj[4], aj[5]};
         hit |= gb_pair(d, Ai, Aj, g.smin, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
     }
-    // 4. wall particles of the same 27 bins, lane-strided, FP32 until the
-    //    exact candidate test of the few that may interact
+    // 4. wall particles of the 27 wall bins around the cell (a grid of its
+    //    own, bins no smaller than the wall radius), flattened like the
+    //    candidates; FP32 until the exact test of the few that may interact
     if (g.wall_start != nullptr) {
         const float rw2f = (float)g.rw2;
         const float Hw[6] = {Aif[0] + rw2f, Aif[1] + rw2f, Aif[2] + rw2f, Aif[3], Aif[4], Aif[5]};
-        for (int oz = lo[2]; oz <= hi[2]; ++oz)
-            for (int oy = lo[1]; oy <= hi[1]; ++oy)
-                for (int ox = lo[0]; ox <= hi[0]; ++ox) {
-                    const int bb = wrap_bin(b[0] + ox, g.nb[0]) +
-                                   g.nb[0] * (wrap_bin(b[1] + oy, g.nb[1]) + g.nb[1] * wrap_bin(b[2] + oz, g.nb[2]));
-                    const int w1 = g.wall_start[bb + 1];
-                    for (int w = g.wall_start[bb] + lane; w < w1; w += 32) {
-                        const int wx = g.wall_xyz[3 * w], wy = g.wall_xyz[3 * w + 1], wz = g.wall_xyz[3 * w + 2];
-                        float df[3] = {Rif[0] - (float)wx, Rif[1] - (float)wy, Rif[2] - (float)wz};
-                        min_image_f(df, g.per, g.Lf);
-                        if (!(df[0] * df[0] + df[1] * df[1] + df[2] * df[2] < g.rcw2_f)) continue;
-                        if (!gb_maybe_in_range(df, Hw, (float)g.smin_w, g.rho_cut_f)) continue;
-                        double d[3] = {Ri[0] - (double)wx, Ri[1] - (double)wy, Ri[2] - (double)wz};
-                        min_image(d, g.per, g.L);
-                        if (!(dist2_exact(d) < g.rcw2)) continue;
-                        const double *ai = &g.A[6 * i];
-                        const Sym3 Ai{ai[0], ai[1], ai[2], ai[3], ai[4], ai[5]};
-                        const Sym3 Aw{g.rw2, g.rw2, g.rw2, 0.0, 0.0, 0.0};
-                        hit |= gb_pair(d, Ai, Aw, g.smin_w, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
-                    }
-                }
+        int wb[3], wlo[3], whi[3];
+        for (int a = 0; a < 3; ++a) {
+            const int k = (int)floorf(Rif[a] / g.wbs[a]);
+            wb[a] = k < 0 ? 0 : (k >= g.wnb[a] ? g.wnb[a] - 1 : k);
+            bin_range(wb[a], g.wnb[a], g.per[a], wlo[a], whi[a]);
+        }
+        const int wx = whi[0] - wlo[0] + 1, wy = whi[1] - wlo[1] + 1, nwn = wx * wy * (whi[2] - wlo[2] + 1);
+        int my_start = 0, my_c = 0;
+        if (lane < nwn) {
+            const int ox = wlo[0] + lane % wx, oy = wlo[1] + (lane / wx) % wy, oz = wlo[2] + lane / (wx * wy);
+            const int bb = wrap_bin(wb[0] + ox, g.wnb[0]) +
+                           g.wnb[0] * (wrap_bin(wb[1] + oy, g.wnb[1]) + g.wnb[1] * wrap_bin(wb[2] + oz, g.wnb[2]));
+            my_start = g.wall_start[bb];
+            my_c = g.wall_start[bb + 1] - my_start;
+        }
+        int incl = my_c;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+        s_pre[wid][lane] = incl - my_c;
+        s_key[wid][lane] = my_start;
+        __syncwarp();
+        for (int t = lane; t < total; t += 32) {
+            int k0 = 0, k1 = nwn - 1;
+            while (k0 < k1) {
+                const int mid = (k0 + k1 + 1) >> 1;
+                if (s_pre[wid][mid] <= t) k0 = mid; else k1 = mid - 1;
+            }
+            const int w = s_key[wid][k0] + (t - s_pre[wid][k0]);
+            const int wxp = g.wall_xyz[3 * w], wyp = g.wall_xyz[3 * w + 1], wzp = g.wall_xyz[3 * w + 2];
+            float df[3] = {Rif[0] - (float)wxp, Rif[1] - (float)wyp, Rif[2] - (float)wzp};
+            min_image_f(df, g.per, g.Lf);
+            if (!(df[0] * df[0] + df[1] * df[1] + df[2] * df[2] < g.rcw2_f)) continue;
+            if (!gb_maybe_in_range(df, Hw, (float)g.smin_w, g.rho_cut_f)) continue;
+            double d[3] = {Ri[0] - (double)wxp, Ri[1] - (double)wyp, Ri[2] - (double)wzp};
+            min_image(d, g.per, g.L);
+            if (!(dist2_exact(d) < g.rcw2)) continue;
+            const double *ai = &g.A[6 * i];
+            const Sym3 Ai{ai[0], ai[1], ai[2], ai[3], ai[4], ai[5]};
+            const Sym3 Aw{g.rw2, g.rw2, g.rw2, 0.0, 0.0, 0.0};
+            hit |= gb_pair(d, Ai, Aw, g.smin_w, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
+        }
     }
     // 5. fixed-order warp reduction (skipped when no lane interacted)
     if (__any_sync(0xffffffffu, hit)) {
@@ -374,11 +422,10 @@ __device__ __forceinline__ void load_hdr(const float *src, Hdr &h)
 }
 
 // Per-row range [lo, hi] of box nodes (along x, the lattice's fastest index)
-// whose weight may be non-zero: the support |y_b| < xi_b cut along the row
-// x = (., i1, i2), widened by one node at each end (nodes outside have w = 0
+// inside the support |y_b| < xi_b of the row x = (., i1, i2); the interval is
+// widened by 1e-3 against rounding (nodes outside the support have w = 0
 // exactly, so the range only saves work).  lo > hi for an empty row.
-// iq[b] = 1 / Q_xb (0 when |Q_xb| is negligible, then axis b does not
-// depend on x).
+// iq[b] = 1 / Q_xb (0 when |Q_xb| is negligible: axis b does not depend on x).
 __device__ __forceinline__ void row_range(const Hdr &h, const float xi[3], const float iq[3], int i1, int i2,
                                           int &lo, int &hi)
 {
@@ -405,41 +452,54 @@ __device__ __forceinline__ void row_range(const Hdr &h, const float xi[3], const
         hi = 0;
         return;
     }
-    lo = (int)fmaxf(floorf(flo) - 1.0f, 0.0f);
-    hi = (int)fminf(ceilf(fhi) + 1.0f, (float)(h.n[0] - 1));
+    lo = (int)fmaxf(ceilf(flo - 1e-3f), 0.0f);
+    hi = (int)fminf(floorf(fhi + 1e-3f), (float)(h.n[0] - 1));
 }
 
-// Shared-memory work plan of one cell: the weight box, per-row ranges, the
-// prefix sums of the row lengths and an item -> row map, so that the nodes
-// of all non-empty row segments are handed to the threads as one flat list.
+// Shared-memory work plan of one cell.  The weights live in a box padded
+// with one zero node on every side, so neighbour reads need no bounds test;
+// per row (i1, i2) the plan keeps the weight range, the visit range start,
+// the row's lattice offset and coordinates; items (one per node to process)
+// are the flattened row segments, found through the exclusive prefix of the
+// row lengths and an item -> row map.
 struct Plan {
-    float *sw;              // box weights, box_max
-    int *rlo, *rhi, *gyz;   // per row: weight range, lattice offset of the row
-    int *vlo;               // per row: first x of the visit range
-    int *pre;               // per row: first item (exclusive prefix)
-    unsigned short *map;    // per item: its row
-    int *tot;               // per warp totals of the scan
+    float *sw;                    // padded box: (n0 + 2)(n1 + 2)(n2 + 2)
+    int *rlo, *rhi, *vlo, *gyz;   // per row
+    int *rc;                      // per row: i1 | i2 << 16
+    int *pre;                     // per row: first item
+    unsigned short *map;          // per item: its row
+    int *tot;                     // per warp totals of the scan
+    int sx, sxy;                  // padded strides
 };
 
-__device__ __forceinline__ Plan plan_layout(float *smem, int box_dim)
+__device__ __forceinline__ Plan plan_layout(float *smem, int box_dim, const Hdr &h)
 {
-    const int R = box_dim * box_dim, V = R * box_dim;
+    const int R = box_dim * box_dim, V = R * box_dim, Vp = (box_dim + 2) * (box_dim + 2) * (box_dim + 2);
     Plan P;
     P.sw = smem;
-    P.rlo = reinterpret_cast<int *>(smem + V);
+    P.rlo = reinterpret_cast<int *>(smem + Vp);
     P.rhi = P.rlo + R;
-    P.gyz = P.rhi + R;
-    P.vlo = P.gyz + R;
-    P.pre = P.vlo + R;
+    P.vlo = P.rhi + R;
+    P.gyz = P.vlo + R;
+    P.rc = P.gyz + R;
+    P.pre = P.rc + R;
     P.tot = P.pre + R + 1;
     P.map = reinterpret_cast<unsigned short *>(P.tot + 32);
+    (void)V;
+    P.sx = h.n[0] + 2;
+    P.sxy = (h.n[0] + 2) * (h.n[1] + 2);
     return P;
 }
 
 size_t plan_bytes(int box_dim)
 {
-    const size_t R = (size_t)box_dim * box_dim, V = R * box_dim;
-    return V * sizeof(float) + (5 * R + 1 + 32) * sizeof(int) + V * sizeof(unsigned short);
+    const size_t R = (size_t)box_dim * box_dim, V = R * box_dim, Vp = (size_t)(box_dim + 2) * (box_dim + 2) * (box_dim + 2);
+    return Vp * sizeof(float) + (6 * R + 1 + 32) * sizeof(int) + V * sizeof(unsigned short);
+}
+
+__device__ __forceinline__ int pidx(const Plan &P, int i0, int i1, int i2)
+{
+    return (i0 + 1) + P.sx * (i1 + 1) + P.sxy * (i2 + 1);
 }
 
 // Rows are split into contiguous chunks, one per thread.  Given each row's
@@ -480,13 +540,14 @@ __device__ __forceinline__ int plan_items(const Plan &P, int nrows, LenFn len)
 }
 
 // Weights w = prod_b phi(2 y_b / xi_b), y = Q^T (x - R) (Sec. 2.2), 0 at solid
-// nodes, into the box in shared memory (zero outside the row ranges); also
-// fills rlo/rhi/gyz.  Returns this thread's partial sum of w.
+// nodes, into the padded box (zero elsewhere); also fills the per-row plan.
+// Returns this thread's partial sum of w.
 __device__ __forceinline__ float shape_weights(const ShapeArgs &a, const Hdr &h, const Plan &P)
 {
-    const int n0 = h.n[0], n1 = h.n[1], nrows = n1 * h.n[2], vol = n0 * nrows;
+    const int n1 = h.n[1], nrows = n1 * h.n[2];
+    const int vp = P.sxy * (h.n[2] + 2);
     const int nxy = a.nx * a.ny;
-    for (int m = threadIdx.x; m < vol; m += blockDim.x) P.sw[m] = 0.f;
+    for (int m = threadIdx.x; m < vp; m += blockDim.x) P.sw[m] = 0.f;
     float iq[3];
     for (int b = 0; b < 3; ++b) iq[b] = fabsf(h.Q[b]) < 1e-7f ? 0.f : 1.0f / h.Q[b];
     const int per = (nrows + blockDim.x - 1) / blockDim.x;
@@ -499,77 +560,75 @@ __device__ __forceinline__ float shape_weights(const ShapeArgs &a, const Hdr &h,
         row_range(h, a.xi, iq, i1, i2, lo, hi);
         P.rlo[r] = lo;
         P.rhi[r] = hi;
+        P.rc[r] = i1 | (i2 << 16);
         P.gyz[r] = a.nx * wrap1(h.o[1] + i1, a.ny) + nxy * wrap1(h.o[2] + i2, a.nz);
     }
-    // rows of this thread's chunk are its own: no barrier needed before the scan
+    // the zero fill must land before the weights; rows of this thread's
+    // chunk are its own, so the scan needs no barrier before it
+    __syncthreads();
     const int total = plan_items(P, nrows, [&](int r) { return max(0, P.rhi[r] - P.rlo[r] + 1); });
     float part = 0.f;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int r = P.map[t];
         const int i0 = P.rlo[r] + (t - P.pre[r]);
+        const int i1 = P.rc[r] & 0xFFFF, i2 = P.rc[r] >> 16;
         const int g = P.gyz[r] + wrap1(h.o[0] + i0, a.nx);
         float w = 0.f;
         if (a.solid == nullptr || !a.solid[g]) {
-            const int i1 = r % n1, i2 = r / n1;
             const float r0f = h.base[0] + (float)i0, r1f = h.base[1] + (float)i1, r2f = h.base[2] + (float)i2;
             w = peskin4((h.Q[0] * r0f + h.Q[3] * r1f + h.Q[6] * r2f) * a.two_over_xi[0]) *
                 peskin4((h.Q[1] * r0f + h.Q[4] * r1f + h.Q[7] * r2f) * a.two_over_xi[1]) *
                 peskin4((h.Q[2] * r0f + h.Q[5] * r1f + h.Q[8] * r2f) * a.two_over_xi[2]);
         }
-        P.sw[i0 + n0 * r] = w;
+        P.sw[pidx(P, i0, i1, i2)] = w;
         part += w;
     }
     return part;
 }
 
-// x-range of row r to visit for gradients: the union of its own range and
-// those of its four in-box neighbour rows (y and z).
-__device__ __forceinline__ void visit_range(const Hdr &h, const Plan &P, int r, int &lo, int &hi)
+// Plan the visit of every node where w or its central difference may be
+// non-zero: per row its own weight range widened by one node (x neighbours)
+// joined with the weight ranges of its four neighbour rows (y, z
+// neighbours).  Records each row's first x in P.vlo; returns the item count.
+__device__ __forceinline__ int plan_visit(const Hdr &h, const Plan &P)
 {
-    const int n1 = h.n[1], n2 = h.n[2], i1 = r % n1, i2 = r / n1;
-    lo = P.rlo[r];
-    hi = P.rhi[r];
-    const int nb[4] = {i1 > 0 ? r - 1 : -1, i1 + 1 < n1 ? r + 1 : -1, i2 > 0 ? r - n1 : -1, i2 + 1 < n2 ? r + n1 : -1};
-    for (int k = 0; k < 4; ++k) {
-        if (nb[k] < 0 || P.rlo[nb[k]] > P.rhi[nb[k]]) continue;
-        if (lo > hi) {
-            lo = P.rlo[nb[k]];
-            hi = P.rhi[nb[k]];
-        } else {
+    const int n0 = h.n[0], n1 = h.n[1], n2 = h.n[2], nrows = n1 * n2;
+    return plan_items(P, nrows, [&](int r) {
+        const int i1 = r % n1, i2 = r / n1;
+        int lo = P.rlo[r] - 1, hi = P.rhi[r] + 1;
+        if (P.rlo[r] > P.rhi[r]) {
+            lo = 1 << 20;
+            hi = -1;
+        }
+        const int nb[4] = {i1 > 0 ? r - 1 : -1, i1 + 1 < n1 ? r + 1 : -1, i2 > 0 ? r - n1 : -1,
+                           i2 + 1 < n2 ? r + n1 : -1};
+        for (int k = 0; k < 4; ++k) {
+            if (nb[k] < 0 || P.rlo[nb[k]] > P.rhi[nb[k]]) continue;
             lo = min(lo, P.rlo[nb[k]]);
             hi = max(hi, P.rhi[nb[k]]);
         }
-    }
-}
-
-// Plan the visit of every node where w or its central difference may be
-// non-zero (row visit ranges, flattened); records each row's first x in
-// P.vlo and returns the item count.
-__device__ __forceinline__ int plan_visit(const Hdr &h, const Plan &P)
-{
-    const int nrows = h.n[1] * h.n[2];
-    return plan_items(P, nrows, [&](int r) {
-        int lo, hi;
-        visit_range(h, P, r, lo, hi);
+        lo = max(lo, 0);
+        hi = min(hi, n0 - 1);
         P.vlo[r] = lo;
         return max(0, hi - lo + 1);
     });
 }
 
-// Sum NV per-thread values over the block: FP32 within a warp, FP64 across
-// warps in a fixed order; the result lands in out[] (shared) for all threads.
+// Sum NV per-thread values over the block in a fixed order (FP32: FP64 runs
+// at a small fraction of the FP32 rate on this part); the result lands in
+// out[] (shared) for all threads.
 template <int NV>
-__device__ __forceinline__ void block_sum(float (&v)[NV], double (*red)[NV], double *out)
+__device__ __forceinline__ void block_sum(float (&v)[NV], float (*red)[NV], float *out)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k)
         for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
     if (lane == 0)
-        for (int k = 0; k < NV; ++k) red[warp][k] = (double)v[k];
+        for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
     __syncthreads();
     if (threadIdx.x < NV) {
-        double s = 0.0;
+        float s = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
         out[threadIdx.x] = s;
     }
@@ -587,10 +646,9 @@ template <bool ALPHA>
 __global__ void __launch_bounds__(kCellThreads) k_sample(ShapeArgs a)
 {
     extern __shared__ float smem[];
-    const Plan P = plan_layout(smem, a.box_dim);
     __shared__ Hdr h;
-    __shared__ double red[kCellThreads / 32][9];
-    __shared__ double sums[9];
+    __shared__ float red[kCellThreads / 32][9];
+    __shared__ float sums[9];
     __shared__ float uc[3];
     const int i = blockIdx.x;
     if (threadIdx.x == 0) {
@@ -603,25 +661,26 @@ __global__ void __launch_bounds__(kCellThreads) k_sample(ShapeArgs a)
     }
     __syncthreads();
     if (!h.ok) return;
+    const Plan P = plan_layout(smem, a.box_dim, h);
     float p1[1] = {shape_weights(a, h, P)};
-    block_sum<1>(p1, reinterpret_cast<double (*)[1]>(red), sums);
-    const double S = sums[0];
+    block_sum<1>(p1, reinterpret_cast<float (*)[1]>(red), sums);
+    const float S = sums[0];
     __syncthreads();
 
-    const int n0 = h.n[0], n1 = h.n[1], n2 = h.n[2], n01 = n0 * n1;
-    const float thr = (float)(1e-24 * S * S);
+    const int sx = P.sx, sxy = P.sxy;
+    const float thr = 1e-24f * S * S;
     const int total = plan_visit(h, P);
     float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int r = P.map[t];
         const int i0 = P.vlo[r] + (t - P.pre[r]);
-        const int i1 = r % n1, i2 = r / n1;
-        const int m = i0 + n0 * r;
+        const int i1 = P.rc[r] & 0xFFFF, i2 = P.rc[r] >> 16;
+        const int m = pidx(P, i0, i1, i2);
         const float *sw = P.sw;
         const float w0 = sw[m];
-        const float Dx = 0.5f * ((i0 + 1 < n0 ? sw[m + 1] : 0.f) - (i0 > 0 ? sw[m - 1] : 0.f));
-        const float Dy = 0.5f * ((i1 + 1 < n1 ? sw[m + n0] : 0.f) - (i1 > 0 ? sw[m - n0] : 0.f));
-        const float Dz = 0.5f * ((i2 + 1 < n2 ? sw[m + n01] : 0.f) - (i2 > 0 ? sw[m - n01] : 0.f));
+        const float Dx = 0.5f * (sw[m + 1] - sw[m - 1]);
+        const float Dy = 0.5f * (sw[m + sx] - sw[m - sx]);
+        const float Dz = 0.5f * (sw[m + sxy] - sw[m - sxy]);
         if (w0 == 0.f && Dx == 0.f && Dy == 0.f && Dz == 0.f) continue;
         const int g = P.gyz[r] + wrap1(h.o[0] + i0, a.nx);
         const float ux = a.U[g], uy = a.U[a.Np + g], uz = a.U[2 * a.Np + g];
@@ -638,9 +697,9 @@ __global__ void __launch_bounds__(kCellThreads) k_sample(ShapeArgs a)
                 const float inv = rsqrtf(nd2);
                 const float nx = Dx * inv, ny = Dy * inv, nz = Dz * inv;
                 const float sxx = a.S[g], syy = a.S[a.Np + g], szz = a.S[2 * a.Np + g];
-                const float sxy = a.S[3 * a.Np + g], sxz = a.S[4 * a.Np + g], syz = a.S[5 * a.Np + g];
-                const float tx = sxx * nx + sxy * ny + sxz * nz;
-                const float ty = sxy * nx + syy * ny + syz * nz;
+                const float sxy_ = a.S[3 * a.Np + g], sxz = a.S[4 * a.Np + g], syz = a.S[5 * a.Np + g];
+                const float tx = sxx * nx + sxy_ * ny + sxz * nz;
+                const float ty = sxy_ * nx + syy * ny + syz * nz;
                 const float tz = sxz * nx + syz * ny + szz * nz;
                 const float r0 = h.base[0] + (float)i0, r1 = h.base[1] + (float)i1, r2 = h.base[2] + (float)i2;
                 acc[6] += w0 * (ty * r2 - tz * r1);
@@ -652,8 +711,8 @@ __global__ void __launch_bounds__(kCellThreads) k_sample(ShapeArgs a)
     block_sum<9>(acc, red, sums);
     if (threadIdx.x == 0) {
         double *o = &a.part[10 * i];
-        o[0] = S;
-        for (int k = 0; k < 9; ++k) o[1 + k] = sums[k];
+        o[0] = (double)S;
+        for (int k = 0; k < 9; ++k) o[1 + k] = (double)sums[k];
     }
 }
 
@@ -814,31 +873,31 @@ __global__ void __launch_bounds__(kRigidThreads) k_rigid(RigidArgs a)
 __global__ void __launch_bounds__(kCellThreads) k_spread(ShapeArgs a)
 {
     extern __shared__ float smem[];
-    const Plan P = plan_layout(smem, a.box_dim);
     __shared__ Hdr h;
     const int i = blockIdx.x;
     if (threadIdx.x == 0) load_hdr(&a.hdr[kHdrWords * i], h);
     __syncthreads();
     if (!h.ok) return;
-    const double S = a.part[10 * i];
-    if (!(S > 0.0)) return;
+    const float S = (float)a.part[10 * i];
+    if (!(S > 0.f)) return;
+    const Plan P = plan_layout(smem, a.box_dim, h);
     shape_weights(a, h, P);
     __syncthreads();
-    const float iS = (float)(1.0 / S);
+    const float iS = 1.0f / S;
     const float Jx = a.JL[6 * i], Jy = a.JL[6 * i + 1], Jz = a.JL[6 * i + 2];
     const float Lx = 0.5f * a.JL[6 * i + 3], Ly = 0.5f * a.JL[6 * i + 4], Lz = 0.5f * a.JL[6 * i + 5];
-    const int n0 = h.n[0], n1 = h.n[1], n2 = h.n[2], n01 = n0 * n1;
+    const int sx = P.sx, sxy = P.sxy;
     const int total = plan_visit(h, P);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int r = P.map[t];
         const int i0 = P.vlo[r] + (t - P.pre[r]);
-        const int i1 = r % n1, i2 = r / n1;
-        const int m = i0 + n0 * r;
+        const int i1 = P.rc[r] & 0xFFFF, i2 = P.rc[r] >> 16;
+        const int m = pidx(P, i0, i1, i2);
         const float *sw = P.sw;
         const float w0 = sw[m];
-        const float Dx = 0.5f * ((i0 + 1 < n0 ? sw[m + 1] : 0.f) - (i0 > 0 ? sw[m - 1] : 0.f));
-        const float Dy = 0.5f * ((i1 + 1 < n1 ? sw[m + n0] : 0.f) - (i1 > 0 ? sw[m - n0] : 0.f));
-        const float Dz = 0.5f * ((i2 + 1 < n2 ? sw[m + n01] : 0.f) - (i2 > 0 ? sw[m - n01] : 0.f));
+        const float Dx = 0.5f * (sw[m + 1] - sw[m - 1]);
+        const float Dy = 0.5f * (sw[m + sx] - sw[m - sx]);
+        const float Dz = 0.5f * (sw[m + sxy] - sw[m - sxy]);
         if (w0 == 0.f && Dx == 0.f && Dy == 0.f && Dz == 0.f) continue;
         const int g = P.gyz[r] + wrap1(h.o[0] + i0, a.nx);
         if (a.solid != nullptr && a.solid[g]) continue;
@@ -951,7 +1010,11 @@ void launch_gb(const Dev &d, const Params &p, cudaStream_t s)
     g.rc_lo2 = (float)((rc - band) * (rc - band));
     g.rc_hi2 = (float)((rc + band) * (rc + band));
     g.rcw2_f = (float)(p.rcw2 * 1.0001 + 1e-3);
-    for (int a = 0; a < 3; ++a) g.Lf[a] = (float)dims[a];
+    for (int a = 0; a < 3; ++a) {
+        g.Lf[a] = (float)dims[a];
+        g.wnb[a] = d.wnb[a];
+        g.wbs[a] = (float)d.wbin_size[a];
+    }
     const int blocks = (d.nc + kGbWarps - 1) / kGbWarps;
     k_gb<<<blocks, 32 * kGbWarps, 0, s>>>(g);
 }

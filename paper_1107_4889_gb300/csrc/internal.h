@@ -46,9 +46,10 @@ struct Dev {
     int *bin_count, *bin_cells, *cell_bin;
     int max_nbr;
     int *nbr, *nbr_count;
-    // wall particles binned in the same grid
-    int nw;
-    int *wall_start;  // nbins + 1
+    // wall particles, binned in a grid of their own (bins >= the wall radius)
+    int nw, wnb[3], nwbins;
+    double wbin_size[3];
+    int *wall_start;  // nwbins + 1
     int *wall_xyz;    // 3 * nw, bin-sorted
     // status
     int *flags;                     // 8 ints
