@@ -277,6 +277,10 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.hdr = cv.take<float>(kHdrWords * n);
     d.part = cv.take<double>(10 * n);
     d.JL = cv.take<float>(6 * n);
+    d.sp_cap = P.nc > 0 ? P.p.box_max : 1;
+    d.sp_idx = cv.take<int>(n * (size_t)d.sp_cap);
+    d.sp_val = cv.take<float4>(n * (size_t)d.sp_cap);
+    d.sp_cnt = cv.take<int>(n);
     for (int a = 0; a < 3; ++a) {
         d.nb[a] = P.nb[a];
         d.bin_size[a] = P.bin_size[a];

@@ -17,10 +17,10 @@
 //             sampled fields (Eqs. vel, vort, pheno_torque_diss).
 //   k_rigid   one thread per cell, FP64: combined force and torque, the
 //             rigid-body update (App. A) and the hydrodynamic impulses.
-//   k_spread  one CTA per cell: the same weights recomputed in shared memory,
-//             the reaction force density and the smoothed characteristic
-//             function added to the lattice with atomics (Sec. 2.2, Eq.
-//             enhance-viscosity).
+//   k_spread  one warp per cell: streams the list of (node, w, D w) that
+//             k_sample wrote for the cell and adds the reaction force density
+//             and the smoothed characteristic function to the lattice with
+//             atomics (Sec. 2.2, Eq. enhance-viscosity).
 #include <algorithm>
 
 #include "internal.h"
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g)
 }
 
 // ---------------------------------------------------------------------------
-// shape weights shared by k_sample and k_spread
+// shape weights of k_sample
 // ---------------------------------------------------------------------------
 struct ShapeArgs {
     const float *hdr;
@@ -397,6 +397,9 @@ struct ShapeArgs {
     float *G, *theta;
     double *part;
     const float *JL;
+    int *sp_idx, *sp_cnt, *flags;
+    float4 *sp_val;
+    int sp_cap;
     int nx, ny, nz;
     long long Np;
     float two_over_xi[3], xi[3], kappa, alpha;
@@ -650,8 +653,10 @@ __global__ void __launch_bounds__(kCellThreads) k_sample(ShapeArgs a)
     __shared__ float red[kCellThreads / 32][9];
     __shared__ float sums[9];
     __shared__ float uc[3];
+    __shared__ int s_nsp;
     const int i = blockIdx.x;
     if (threadIdx.x == 0) {
+        s_nsp = 0;
         load_hdr(&a.hdr[kHdrWords * i], h);
         if (h.ok) {
             uc[0] = a.U[h.gc];
@@ -671,18 +676,40 @@ __global__ void __launch_bounds__(kCellThreads) k_sample(ShapeArgs a)
     const float thr = 1e-24f * S * S;
     const int total = plan_visit(h, P);
     float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int r = P.map[t];
-        const int i0 = P.vlo[r] + (t - P.pre[r]);
-        const int i1 = P.rc[r] & 0xFFFF, i2 = P.rc[r] >> 16;
-        const int m = pidx(P, i0, i1, i2);
-        const float *sw = P.sw;
-        const float w0 = sw[m];
-        const float Dx = 0.5f * (sw[m + 1] - sw[m - 1]);
-        const float Dy = 0.5f * (sw[m + sx] - sw[m - sx]);
-        const float Dz = 0.5f * (sw[m + sxy] - sw[m - sxy]);
-        if (w0 == 0.f && Dx == 0.f && Dy == 0.f && Dz == 0.f) continue;
-        const int g = P.gyz[r] + wrap1(h.o[0] + i0, a.nx);
+    int *sp_idx = a.sp_idx + (size_t)i * a.sp_cap;
+    float4 *sp_val = a.sp_val + (size_t)i * a.sp_cap;
+    const int lane = threadIdx.x & 31;
+    for (int tb = 0; tb < total; tb += blockDim.x) {
+        const int t = tb + threadIdx.x;
+        int r = 0, i0 = 0, i1 = 0, i2 = 0, g = 0;
+        float w0 = 0.f, Dx = 0.f, Dy = 0.f, Dz = 0.f;
+        if (t < total) {
+            r = P.map[t];
+            i0 = P.vlo[r] + (t - P.pre[r]);
+            i1 = P.rc[r] & 0xFFFF;
+            i2 = P.rc[r] >> 16;
+            const int m = pidx(P, i0, i1, i2);
+            const float *sw = P.sw;
+            w0 = sw[m];
+            Dx = 0.5f * (sw[m + 1] - sw[m - 1]);
+            Dy = 0.5f * (sw[m + sx] - sw[m - sx]);
+            Dz = 0.5f * (sw[m + sxy] - sw[m - sxy]);
+            g = P.gyz[r] + wrap1(h.o[0] + i0, a.nx);
+        }
+        const bool live = w0 != 0.f || Dx != 0.f || Dy != 0.f || Dz != 0.f;
+        // append the node to the cell's spread list (warp-aggregated)
+        const unsigned mk = __ballot_sync(0xffffffffu, live);
+        int base = 0;
+        if (lane == 0 && mk) base = atomicAdd(&s_nsp, __popc(mk));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (live) {
+            const int pos = base + __popc(mk & ((1u << lane) - 1u));
+            if (pos < a.sp_cap) {
+                sp_idx[pos] = g;
+                sp_val[pos] = make_float4(w0, Dx, Dy, Dz);
+            }
+        }
+        if (!live) continue;
         const float ux = a.U[g], uy = a.U[a.Np + g], uz = a.U[2 * a.Np + g];
         acc[0] += w0 * ux;
         acc[1] += w0 * uy;
@@ -713,6 +740,8 @@ __global__ void __launch_bounds__(kCellThreads) k_sample(ShapeArgs a)
         double *o = &a.part[10 * i];
         o[0] = (double)S;
         for (int k = 0; k < 9; ++k) o[1 + k] = (double)sums[k];
+        a.sp_cnt[i] = min(s_nsp, a.sp_cap);
+        if (s_nsp > a.sp_cap) atomicOr(&a.flags[FLAG_OVERFLOW], OVF_BOX);
     }
 }
 
@@ -870,42 +899,32 @@ __global__ void __launch_bounds__(kRigidThreads) k_rigid(RigidArgs a)
 // k_spread (h = 1): G += -J delta + 1/2 L x D delta at fluid nodes;
 // theta += 1 - (1 - w)^kappa where w > 0
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kCellThreads) k_spread(ShapeArgs a)
+// k_spread (h = 1): over the cell's spread list,
+// G += -J delta + 1/2 L x D delta at fluid nodes (delta = w / S) and
+// theta += 1 - (1 - w)^kappa where w > 0.  One warp per cell.
+constexpr int kSpreadWarps = 4;
+
+__global__ void __launch_bounds__(32 * kSpreadWarps) k_spread(ShapeArgs a, int nc)
 {
-    extern __shared__ float smem[];
-    __shared__ Hdr h;
-    const int i = blockIdx.x;
-    if (threadIdx.x == 0) load_hdr(&a.hdr[kHdrWords * i], h);
-    __syncthreads();
-    if (!h.ok) return;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kSpreadWarps + (threadIdx.x >> 5);
+    if (i >= nc) return;
+    const int ok = reinterpret_cast<const int *>(a.hdr)[kHdrWords * i + 19];
     const float S = (float)a.part[10 * i];
-    if (!(S > 0.f)) return;
-    const Plan P = plan_layout(smem, a.box_dim, h);
-    shape_weights(a, h, P);
-    __syncthreads();
+    if (!ok || !(S > 0.f)) return;
     const float iS = 1.0f / S;
-    const float Jx = a.JL[6 * i], Jy = a.JL[6 * i + 1], Jz = a.JL[6 * i + 2];
-    const float Lx = 0.5f * a.JL[6 * i + 3], Ly = 0.5f * a.JL[6 * i + 4], Lz = 0.5f * a.JL[6 * i + 5];
-    const int sx = P.sx, sxy = P.sxy;
-    const int total = plan_visit(h, P);
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int r = P.map[t];
-        const int i0 = P.vlo[r] + (t - P.pre[r]);
-        const int i1 = P.rc[r] & 0xFFFF, i2 = P.rc[r] >> 16;
-        const int m = pidx(P, i0, i1, i2);
-        const float *sw = P.sw;
-        const float w0 = sw[m];
-        const float Dx = 0.5f * (sw[m + 1] - sw[m - 1]);
-        const float Dy = 0.5f * (sw[m + sx] - sw[m - sx]);
-        const float Dz = 0.5f * (sw[m + sxy] - sw[m - sxy]);
-        if (w0 == 0.f && Dx == 0.f && Dy == 0.f && Dz == 0.f) continue;
-        const int g = P.gyz[r] + wrap1(h.o[0] + i0, a.nx);
-        if (a.solid != nullptr && a.solid[g]) continue;
-        const float dl = w0 * iS, ex = Dx * iS, ey = Dy * iS, ez = Dz * iS;
-        atomicAdd(&a.G[g], -Jx * dl + (Ly * ez - Lz * ey));
-        atomicAdd(&a.G[a.Np + g], -Jy * dl + (Lz * ex - Lx * ez));
-        atomicAdd(&a.G[2 * a.Np + g], -Jz * dl + (Lx * ey - Ly * ex));
-        if (w0 > 0.f) atomicAdd(&a.theta[g], 1.0f - powf(1.0f - w0, a.kappa));
+    const float Jx = a.JL[6 * i] * iS, Jy = a.JL[6 * i + 1] * iS, Jz = a.JL[6 * i + 2] * iS;
+    const float Lx = 0.5f * a.JL[6 * i + 3] * iS, Ly = 0.5f * a.JL[6 * i + 4] * iS, Lz = 0.5f * a.JL[6 * i + 5] * iS;
+    const int n = a.sp_cnt[i];
+    const int *idx = a.sp_idx + (size_t)i * a.sp_cap;
+    const float4 *val = a.sp_val + (size_t)i * a.sp_cap;
+    for (int e = lane; e < n; e += 32) {
+        const int g = idx[e];
+        const float4 v = val[e];
+        atomicAdd(&a.G[g], -Jx * v.x + (Ly * v.w - Lz * v.z));
+        atomicAdd(&a.G[a.Np + g], -Jy * v.x + (Lz * v.y - Lx * v.w));
+        atomicAdd(&a.G[2 * a.Np + g], -Jz * v.x + (Lx * v.z - Ly * v.y));
+        if (v.x > 0.f) atomicAdd(&a.theta[g], 1.0f - powf(1.0f - v.x, a.kappa));
     }
 }
 
@@ -920,6 +939,11 @@ ShapeArgs shape_args(const Dev &d, const Params &p)
     a.theta = d.theta;
     a.part = d.part;
     a.JL = d.JL;
+    a.sp_idx = d.sp_idx;
+    a.sp_val = d.sp_val;
+    a.sp_cnt = d.sp_cnt;
+    a.sp_cap = d.sp_cap;
+    a.flags = d.flags;
     a.nx = d.nx;
     a.ny = d.ny;
     a.nz = d.nz;
@@ -1026,7 +1050,6 @@ void prepare_cells(const Params &p)
     const int smem = (int)cells_smem_bytes(p);
     cudaFuncSetAttribute(k_sample<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_sample<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 void launch_sample(const Dev &d, const Params &p, cudaStream_t s)
@@ -1078,7 +1101,7 @@ void launch_spread(const Dev &d, const Params &p, cudaStream_t s)
 {
     if (d.nc == 0) return;
     const ShapeArgs a = shape_args(d, p);
-    k_spread<<<d.nc, kCellThreads, cells_smem_bytes(p), s>>>(a);
+    k_spread<<<(d.nc + kSpreadWarps - 1) / kSpreadWarps, 32 * kSpreadWarps, 0, s>>>(a, d.nc);
 }
 
 }  // namespace rbc

@@ -40,6 +40,12 @@ struct Dev {
     float *hdr;              // kHdrWords per cell: shape header built by k_bin
     double *part;            // 10n: shape normalisation S and the 9 sampled sums
     float *JL;               // 6n: impulses J, L handed from k_rigid to k_spread
+    // spread lists written by k_sample: per cell up to sp_cap entries of
+    // (lattice node, w, dw/dx, dw/dy, dw/dz) where w or its gradient is non-zero
+    int sp_cap;
+    int *sp_idx;             // n * sp_cap
+    float4 *sp_val;          // n * sp_cap
+    int *sp_cnt;             // n
     // cell list
     int nb[3], nbins, bin_cap;
     double bin_size[3];
@@ -58,7 +64,7 @@ struct Dev {
     double *budget_out;             // 16: mass, p_fluid(3), max|u|, NaN count, p_cells(3)
     int budget_blocks;
     // lattice pass launch: grid of the row-staged kernel (0: one thread per node)
-    int lb_grid;
+    int lb_grid, lb_stages;
     size_t lb_smem;
 };
 

@@ -164,19 +164,24 @@ __global__ void __launch_bounds__(kLbThreads) k_lb(LbArgs a)
 
 // ---------------------------------------------------------------------------
 // Row-staged lattice pass.  A row is the nx nodes at fixed (y, z).  Every
-// CTA is persistent and walks batches of B consecutive y-rows at one z; for
-// each batch
-// it brings into shared memory, with asynchronous bulk copies completing on
-// an mbarrier, the upstream row of every speed (row (y - c_y, z - c_z) of
-// plane p) plus the batch's own rows of G, theta and the link mask, into a
-// ring of kStages buffers (kStages - 1 batches in flight while one is
-// computed).  The bytes in flight
-// are then bounded by shared memory, not by registers; the x shift of the
-// pull is an index into the staged row.  Needs nx * 4 bytes to be a multiple
-// of 16 (bulk-copy granularity).
+// CTA is persistent and walks batches of B consecutive y-rows at one z.  A
+// producer warp brings each batch into a ring of L.stages shared-memory
+// buffers with asynchronous bulk copies: the upstream row of every speed
+// (row (y - c_y, z - c_z) of plane p) plus the batch's own rows of G, theta
+// and the link mask.  The copies complete on the stage's "full" mbarrier;
+// the eight consumer warps wait on it, collide the batch, and each arrives
+// on the stage's "empty" mbarrier, which the producer waits on before it
+// refills the stage.  No CTA-wide barrier sits in the loop, so the copy
+// issue never stalls the collision.  The bytes in flight are bounded by
+// shared memory, not by registers; the x shift of the pull is an index into
+// the staged row.  Needs nx * 4 bytes to be a multiple of 16 (bulk-copy
+// granularity).  Every wait is bounded (kWaitCycles) and raises
+// FLAG_TIMEOUT; the producer then waits for its copies in flight before the
+// CTA exits.
 // ---------------------------------------------------------------------------
-constexpr int kStThreads = 256;
-constexpr int kStages = 4;        // batches in the shared-memory ring (kStages - 1 in flight)
+constexpr int kStConsumers = 256;                 // collision threads (8 warps)
+constexpr int kStThreads = kStConsumers + 32;     // + the producer warp
+constexpr int kMaxStages = 4;
 constexpr int kStageBytes = 24 * 1024;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bounded mbarrier waits
 
@@ -193,6 +198,11 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
@@ -225,107 +235,122 @@ struct StageLayout {
     int B;        // rows per batch
     int planes;   // staged planes per row: 19 (+4 G, theta) (+1 links)
     int stage_floats;
+    int stages;   // buffers in the ring (2 .. kMaxStages)
 };
 
 template <bool WALLS, bool CELLS, bool SIGMA>
 __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout L, int nbatches)
 {
     extern __shared__ __align__(128) float sm[];
-    __shared__ __align__(8) unsigned long long bars[kStages];
-    __shared__ int abort_flag;
+    __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages];
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int B = L.B;
-    const uint32_t row_bytes = (uint32_t)nx * 4u;
+    const int B = L.B, ns = L.stages;
+    const int nyb = (ny + B - 1) / B;
     if (threadIdx.x == 0) {
-        for (int k = 0; k < kStages; ++k) mbar_init(smem_addr(&bars[k]), 1);
-        abort_flag = 0;
+        for (int k = 0; k < ns; ++k) {
+            mbar_init(smem_addr(&full[k]), 1);
+            mbar_init(smem_addr(&empty[k]), kStConsumers / 32);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    // A batch is rows y0 .. y0 + nb - 1 at one z (nyb batches per z slab).
-    // Staged plane k, batch row b sits at stage + (k * B + b) * nx.  For a
-    // speed p the upstream rows y - c_y are contiguous in plane p except
-    // where they wrap in y, so each plane needs one copy, or two.
-    const int nyb = (ny + B - 1) / B;
-    auto issue = [&](int batch, int stage) {
-        if (threadIdx.x >= 32) return;
-        const int z = batch / nyb, y0 = (batch - z * nyb) * B;
-        const int nb = min(B, ny - y0);
-        const uint32_t bar = smem_addr(&bars[stage]);
-        if (threadIdx.x == 0) mbar_expect_tx(bar, (uint32_t)(L.planes * nb) * row_bytes);
-        __syncwarp();
-        float *base = sm + (size_t)stage * L.stage_floats;
-        for (int k = threadIdx.x; k < L.planes; k += 32) {
-            float *dst = base + (size_t)k * B * nx;
-            if (k < kQ) {
-                const int zs = wrapm(z - cz(k), nz);
-                const float *plane = a.src + (long long)k * a.Np + (long long)zs * ny * nx;
-                int ys = y0 - cy(k);  // first upstream row, may be -1 or run past ny
-                int b = 0;
-                while (b < nb) {
-                    const int yr = wrapm(ys + b, ny);
-                    const int run = min(nb - b, ny - yr);
-                    bulk_g2s(smem_addr(dst + (size_t)b * nx), plane + (long long)yr * nx, (uint32_t)run * row_bytes, bar);
-                    b += run;
+    if (threadIdx.x >= kStConsumers) {
+        // Producer warp.  A batch is rows y0 .. y0 + nb - 1 at one z.  Staged
+        // plane k, batch row b sits at stage + (k * B + b) * nx.  For a speed
+        // p the upstream rows y - c_y are contiguous in plane p except where
+        // they wrap in y, so each plane needs one copy, or two.
+        const int lane = threadIdx.x - kStConsumers;
+        const uint32_t row_bytes = (uint32_t)nx * 4u;
+        int it = 0;
+        bool ok = true;
+        for (int batch = blockIdx.x; batch < nbatches; batch += gridDim.x, ++it) {
+            const int stage = it % ns;
+            if (it >= ns && !mbar_wait(smem_addr(&empty[stage]), (uint32_t)((it / ns - 1) & 1))) {
+                if (lane == 0) atomicOr(&a.flags[FLAG_TIMEOUT], 1);
+                ok = false;
+                break;
+            }
+            const int z = batch / nyb, y0 = (batch - z * nyb) * B;
+            const int nb = min(B, ny - y0);
+            const uint32_t bar = smem_addr(&full[stage]);
+            if (lane == 0) mbar_expect_tx(bar, (uint32_t)(L.planes * nb) * row_bytes);
+            __syncwarp();
+            float *base = sm + (size_t)stage * L.stage_floats;
+            for (int k = lane; k < L.planes; k += 32) {
+                float *dst = base + (size_t)k * B * nx;
+                if (k < kQ) {
+                    const int zs = wrapm(z - cz(k), nz);
+                    const float *plane = a.src + (long long)k * a.Np + (long long)zs * ny * nx;
+                    const int ys = y0 - cy(k);  // first upstream row, may be -1 or run past ny
+                    int b = 0;
+                    while (b < nb) {
+                        const int yr = wrapm(ys + b, ny);
+                        const int run = min(nb - b, ny - yr);
+                        bulk_g2s(smem_addr(dst + (size_t)b * nx), plane + (long long)yr * nx,
+                                 (uint32_t)run * row_bytes, bar);
+                        b += run;
+                    }
+                } else {
+                    const long long off = ((long long)z * ny + y0) * nx;
+                    const float *src;
+                    if (CELLS && k < kQ + 3)
+                        src = a.G + (long long)(k - kQ) * a.Np + off;
+                    else if (CELLS && k == kQ + 3)
+                        src = a.th + off;
+                    else
+                        src = reinterpret_cast<const float *>(a.links) + off;
+                    bulk_g2s(smem_addr(dst), src, (uint32_t)nb * row_bytes, bar);
                 }
-            } else {
-                const long long off = ((long long)z * ny + y0) * nx;
-                const float *src;
-                if (CELLS && k < kQ + 3)
-                    src = a.G + (long long)(k - kQ) * a.Np + off;
-                else if (CELLS && k == kQ + 3)
-                    src = a.th + off;
-                else
-                    src = reinterpret_cast<const float *>(a.links) + off;
-                bulk_g2s(smem_addr(dst), src, (uint32_t)nb * row_bytes, bar);
             }
         }
-    };
-
-    int it = 0;
-    int batch = blockIdx.x;
-    for (int k = 0; k < kStages; ++k)
-        if (batch + k * (int)gridDim.x < nbatches) issue(batch + k * gridDim.x, k);
-    for (; batch < nbatches; batch += gridDim.x, ++it) {
-        const int stage = it % kStages;
-        const uint32_t bar = smem_addr(&bars[stage]);
-        if (!mbar_wait(bar, (uint32_t)((it / kStages) & 1))) {
-            atomicOr(&a.flags[FLAG_TIMEOUT], 1);
-            abort_flag = 1;
+        if (!ok) {
+            // let the copies still in flight land before the CTA's memory goes away
+            for (int j = it > ns ? it - ns : 0; j < it; ++j)
+                mbar_wait(smem_addr(&full[j % ns]), (uint32_t)((j / ns) & 1));
         }
-        __syncthreads();
-        if (abort_flag) break;
+        return;
+    }
+
+    // consumer warps
+    const int lane = threadIdx.x & 31;
+    const int plane_stride = B * nx;
+    int it = 0;
+    for (int batch = blockIdx.x; batch < nbatches; batch += gridDim.x, ++it) {
+        const int stage = it % ns;
+        if (!mbar_wait(smem_addr(&full[stage]), (uint32_t)((it / ns) & 1))) {
+            if (lane == 0) atomicOr(&a.flags[FLAG_TIMEOUT], 1);
+            break;
+        }
         const float *st = sm + (size_t)stage * L.stage_floats;
         const int z = batch / nyb, y0 = (batch - z * nyb) * B;
         const int nb = min(B, ny - y0);
-        for (int l = threadIdx.x; l < nb * nx; l += blockDim.x) {
+        for (int l = threadIdx.x; l < nb * nx; l += kStConsumers) {
             const int b = l / nx, x = l - b * nx;
             const int y = y0 + b;
             const int n = (y + ny * z) * nx + x;
-            const uint32_t lk = WALLS ? reinterpret_cast<const uint32_t *>(st)[((size_t)(kQ + (CELLS ? 4 : 0)) * B + b) * nx + x] : 0u;
+            const float *row = st + (size_t)b * nx;
+            const uint32_t lk =
+                WALLS ? reinterpret_cast<const uint32_t *>(row)[(size_t)(kQ + (CELLS ? 4 : 0)) * plane_stride + x] : 0u;
             if (WALLS && (lk >> 31)) continue;
+            const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
             float d[kQ];
 #pragma unroll
             for (int p = 0; p < kQ; ++p) {
-                const int xs = cx(p) == 0 ? x : wrapm(x - cx(p), nx);
-                d[p] = st[((size_t)p * B + b) * nx + xs];
+                const int xs = cx(p) == 0 ? x : (cx(p) > 0 ? xm : xp);
+                d[p] = row[p * plane_stride + xs];
             }
             float gx = a.gx0, gy = a.gy0, gz = a.gz0, T = a.tau0;
             if (CELLS) {
-                gx += st[((size_t)(kQ + 0) * B + b) * nx + x];
-                gy += st[((size_t)(kQ + 1) * B + b) * nx + x];
-                gz += st[((size_t)(kQ + 2) * B + b) * nx + x];
-                T += a.delta * st[((size_t)(kQ + 3) * B + b) * nx + x];
+                gx += row[(kQ + 0) * plane_stride + x];
+                gy += row[(kQ + 1) * plane_stride + x];
+                gz += row[(kQ + 2) * plane_stride + x];
+                T += a.delta * row[(kQ + 3) * plane_stride + x];
             }
             collide_node<WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, n, x, y, z);
         }
-        __syncthreads();  // the stage is free again
-        if (batch + kStages * (int)gridDim.x < nbatches) issue(batch + kStages * gridDim.x, stage);
-    }
-    if (abort_flag) {
-        // let any copy still in flight land before the CTA's memory goes away
-        for (int k = 0; k < kStages; ++k) mbar_wait(smem_addr(&bars[k]), 0);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&empty[stage]));  // this warp is done with the stage
     }
 }
 
@@ -434,12 +459,14 @@ StageLayout stage_layout(const Dev &d)
     L.planes = kQ + (d.nc > 0 ? 4 : 0) + (d.walls ? 1 : 0);
     const int row_floats = d.nx;
     // about kStageBytes per stage, whole rows, at most one y column of rows;
-    // a multiple of the rows that fill the CTA's threads when rows are short
+    // a multiple of the rows that fill the consumer threads when rows are short
     int B = kStageBytes / (L.planes * row_floats * 4);
     B = B < 1 ? 1 : (B > d.ny ? d.ny : B);
-    if (row_floats < kStThreads && B * row_floats > kStThreads) B -= B % (kStThreads / row_floats > 0 ? kStThreads / row_floats : 1);
+    if (row_floats < kStConsumers && B * row_floats > kStConsumers)
+        B -= B % (kStConsumers / row_floats > 0 ? kStConsumers / row_floats : 1);
     L.B = B;
     L.stage_floats = L.planes * B * row_floats;
+    L.stages = kMaxStages;
     return L;
 }
 
@@ -447,32 +474,50 @@ bool staged_ok(const Dev &d)
 {
     if (d.nx % 4 != 0) return false;  // rows must be whole 16-byte units
     const StageLayout L = stage_layout(d);
-    return (size_t)kStages * L.stage_floats * sizeof(float) <= 200u * 1024u;
+    return 2u * L.stage_floats * sizeof(float) <= 200u * 1024u;
 }
 
+// Ring depth: among 2 .. kMaxStages stages (each depth fixes how many CTAs
+// fit on an SM), take the one whose last wave of batches leaves the fewest
+// idle CTA slots: time ~ ceil(batches / (SMs * k)) * k for k CTAs per SM;
+// ties go to the deeper ring.
 template <bool W, bool C, bool S_>
 void prepare_lb_t(Dev &d)
 {
     d.lb_grid = 0;
     if (!staged_ok(d)) return;
-    const StageLayout L = stage_layout(d);
-    const size_t smem = (size_t)kStages * L.stage_floats * sizeof(float);
-    cudaFuncSetAttribute(k_lb_staged<W, C, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    StageLayout L = stage_layout(d);
     const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_staged<W, C, S_>, kStThreads, smem);
-    int grid = sms * (per_sm > 0 ? per_sm : 1);
-    d.lb_grid = grid > nbatches ? nbatches : grid;
-    d.lb_smem = smem;
+    long long best_cost = -1;
+    for (int ns = kMaxStages; ns >= 2; --ns) {
+        const size_t smem = (size_t)ns * L.stage_floats * sizeof(float);
+        if (smem > 200u * 1024u) continue;
+        cudaFuncSetAttribute(k_lb_staged<W, C, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_staged<W, C, S_>, kStThreads, smem);
+        if (per_sm < 1) continue;
+        const long long slots = (long long)sms * per_sm;
+        const long long cost = ((nbatches + slots - 1) / slots) * per_sm;
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            d.lb_stages = ns;
+            d.lb_smem = smem;
+            d.lb_grid = (int)(slots > nbatches ? nbatches : slots);
+        }
+    }
+    if (d.lb_grid > 0)
+        cudaFuncSetAttribute(k_lb_staged<W, C, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.lb_smem);
 }
 
 template <bool W, bool C, bool S_>
 void launch_lb_t(const Dev &d, const LbArgs &a, cudaStream_t s)
 {
     if (d.lb_grid > 0) {
-        const StageLayout L = stage_layout(d);
+        StageLayout L = stage_layout(d);
+        L.stages = d.lb_stages;
         const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
         k_lb_staged<W, C, S_><<<d.lb_grid, kStThreads, d.lb_smem, s>>>(a, L, nbatches);
     } else {
