@@ -169,12 +169,12 @@ int rbc_neighbors(rbc_handle *h, int *counts, int *lists, int max_per_cell);
 
 /* Kernel timing.  rbc_set_timing(h, capacity) makes the next `capacity`
  * steps record CUDA events inside the step graph on the handle's stream:
- * before sampling, after spreading and after the lattice pass (capacity 0
- * turns it off).  rbc_kernel_times synchronises and returns for k = 0 (the
- * lattice pass, which runs alongside the next step's cell list and
- * Gay-Berne forces) and k = 1 (sampling, rigid update and spreading) the
- * summed milliseconds ms[k] and the number of timed launches count[k], then
- * clears them. */
+ * before and after the per-cell kernel and after the lattice pass (capacity
+ * 0 turns it off).  rbc_kernel_times synchronises and returns for k = 0 (the
+ * lattice pass, which runs alongside the next step's cell list, Gay-Berne
+ * forces and shape lists) and k = 1 (the per-cell kernel: sampling, rigid
+ * update and spreading) the summed milliseconds ms[k] and the number of
+ * timed launches count[k], then clears them. */
 int rbc_set_timing(rbc_handle *h, int capacity);
 int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2]);
 

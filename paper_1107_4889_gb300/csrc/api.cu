@@ -275,12 +275,13 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.have = cv.take<int>(n);
     d.diag = cv.take<double>(21 * n);
     d.hdr = cv.take<float>(kHdrWords * n);
-    d.part = cv.take<double>(10 * n);
-    d.JL = cv.take<float>(6 * n);
     d.sp_cap = P.nc > 0 ? P.p.box_max : 1;
-    d.sp_idx = cv.take<int>(n * (size_t)d.sp_cap);
-    d.sp_val = cv.take<float4>(n * (size_t)d.sp_cap);
-    d.sp_cnt = cv.take<int>(n);
+    for (int b = 0; b < 2; ++b) {
+        d.sp_idx[b] = cv.take<int2>(n * (size_t)d.sp_cap);
+        d.sp_val[b] = cv.take<float4>(n * (size_t)d.sp_cap);
+        d.sp_cnt[b] = cv.take<int>(n);
+        d.sp_S[b] = cv.take<float>(n);
+    }
     for (int a = 0; a < 3; ++a) {
         d.nb[a] = P.nb[a];
         d.bin_size[a] = P.bin_size[a];
@@ -319,19 +320,20 @@ void set_thread_error(const std::string &msg) { g_thread_err = msg; }
 struct rbc_handle {
     Problem P;
     Dev d;
-    cudaStream_t stream = nullptr, side = nullptr;
+    cudaStream_t stream = nullptr, side = nullptr, side2 = nullptr;
     bool own_stream = false;
     // g_pro: cell list + Gay-Berne of the initial poses (run once at init);
-    // g_step[parity]: sample -> rigid -> spread, then the lattice pass on
-    // the main stream alongside the next step's cell list + Gay-Berne on the
-    // side stream (they touch disjoint data), joined at the end
+    // g_step[parity]: the per-cell kernel, then the lattice pass on the main
+    // stream alongside the next step's cell list, Gay-Berne forces and shape
+    // lists on two side streams (they touch disjoint data), joined at the end
     cudaGraphExec_t g_pro = nullptr, g_step[2] = {nullptr, nullptr};
     cudaGraph_t src[3] = {nullptr, nullptr, nullptr};  // kept: exec updates name their nodes
     cudaGraphNode_t ev_node[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     cudaEvent_t ev_dummy[3] = {nullptr, nullptr, nullptr}, fork_ev = nullptr, join_ev = nullptr;
+    cudaEvent_t fork2_ev = nullptr, join2_ev = nullptr;
     int64_t step = 0;
     int timing_cap = 0, timing_used = 0;
-    std::vector<cudaEvent_t> ev;  // 3 per timed step: before sample, after spread, after the lattice pass
+    std::vector<cudaEvent_t> ev;  // 3 per timed step: before the cell kernel, after it, after the lattice pass
     std::string err;
     int device = 0;
     std::vector<uint8_t> solid_host;
@@ -376,21 +378,27 @@ static int capture(rbc_handle *h, void (*body)(rbc_handle *, int), int arg, cuda
     return RBC_OK;
 }
 
+// Cell list, Gay-Berne forces and shape lists of the initial poses (the
+// shape lists of step k live in buffer k & 1).
 static void body_prologue(rbc_handle *h, int)
 {
     launch_bin(h->d, h->P.p, h->stream);
     launch_gb(h->d, h->P.p, h->stream);
+    launch_weights(h->d, h->P.p, 0, h->stream);
 }
 
+// One coupled step.  Main stream: the per-cell kernel (sample the fields
+// with this pose's shape lists, the rigid update to the new poses, spread
+// the impulses with the same lists), then the lattice pass.  As soon as the
+// new poses exist, side streams build the next step's cell list, then its
+// Gay-Berne forces and (on a second side stream) its shape lists, into
+// buffer parity ^ 1; they read only the poses and write nothing the lattice
+// pass reads.  The step ends when all three streams have.
 static void body_step(rbc_handle *h, int parity)
 {
     const bool cells = h->d.nc > 0;
     cudaEventRecordWithFlags(h->ev_dummy[0], h->stream, cudaEventRecordExternal);
-    if (cells) {
-        launch_sample(h->d, h->P.p, h->stream);
-        launch_rigid(h->d, h->P.p, h->stream);
-        launch_spread(h->d, h->P.p, h->stream);
-    }
+    launch_cells(h->d, h->P.p, parity, h->stream);
     cudaEventRecordWithFlags(h->ev_dummy[1], h->stream, cudaEventRecordExternal);
     if (cells) {
         cudaEventRecord(h->fork_ev, h->stream);
@@ -400,9 +408,14 @@ static void body_step(rbc_handle *h, int parity)
     cudaEventRecordWithFlags(h->ev_dummy[2], h->stream, cudaEventRecordExternal);
     if (cells) {
         launch_bin(h->d, h->P.p, h->side);
+        cudaEventRecord(h->fork2_ev, h->side);
+        cudaStreamWaitEvent(h->side2, h->fork2_ev, 0);
         launch_gb(h->d, h->P.p, h->side);
+        launch_weights(h->d, h->P.p, parity ^ 1, h->side2);
         cudaEventRecord(h->join_ev, h->side);
+        cudaEventRecord(h->join2_ev, h->side2);
         cudaStreamWaitEvent(h->stream, h->join_ev, 0);
+        cudaStreamWaitEvent(h->stream, h->join2_ev, 0);
     }
 }
 
@@ -554,8 +567,11 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
         if (n > 0) prepare_cells(h->P.p);
         RBC_CU(cudaGetLastError());
         RBC_CU(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        RBC_CU(cudaStreamCreateWithFlags(&h->side2, cudaStreamNonBlocking));
         RBC_CU(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
         RBC_CU(cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
+        RBC_CU(cudaEventCreateWithFlags(&h->fork2_ev, cudaEventDisableTiming));
+        RBC_CU(cudaEventCreateWithFlags(&h->join2_ev, cudaEventDisableTiming));
         for (int k = 0; k < 3; ++k) RBC_CU(cudaEventCreate(&h->ev_dummy[k]));
         if (n > 0) {
             int r = capture(h, body_prologue, 0, &h->g_pro, nullptr, &h->src[2]);
@@ -756,7 +772,7 @@ int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2])
 int rbc_launches_per_step(const rbc_handle *h)
 {
     if (!h) return 0;
-    return 1 + (h->d.nc > 0 ? 5 : 0);  // bin-count clear is a memset node
+    return 1 + (h->d.nc > 0 ? 4 : 0);  // cells, bin, gb, weights; the bin-count clear is a memset node
 }
 
 void rbc_free(rbc_handle *h)
@@ -773,6 +789,12 @@ void rbc_free(rbc_handle *h)
         if (h->ev_dummy[k]) cudaEventDestroy(h->ev_dummy[k]);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->join_ev) cudaEventDestroy(h->join_ev);
+    if (h->fork2_ev) cudaEventDestroy(h->fork2_ev);
+    if (h->join2_ev) cudaEventDestroy(h->join2_ev);
+    if (h->side2) {
+        cudaStreamSynchronize(h->side2);
+        cudaStreamDestroy(h->side2);
+    }
     if (h->side) {
         cudaStreamSynchronize(h->side);
         cudaStreamDestroy(h->side);

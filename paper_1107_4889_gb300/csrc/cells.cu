@@ -12,15 +12,17 @@
 //             certainly outside the range, so FP64 runs only for pairs that
 //             interact.  Each pair is evaluated from both sides: every cell
 //             sums its own force in a fixed order, without atomics.
-//   k_sample  one CTA per cell: shape-function weights on the box staged in
-//             shared memory, block reduction of the normalisation and of the
-//             sampled fields (Eqs. vel, vort, pheno_torque_diss).
+//   k_weights one CTA per cell: shape-function weights on the box staged in
+//             shared memory, written out as the cell's shape list (node,
+//             w, D w) with the normalisation S; built for the next pose
+//             while the lattice pass runs.
+//   k_sample  one warp per cell: sampled fields over the shape list
+//             (Eqs. vel, vort, pheno_torque_diss).
 //   k_rigid   one thread per cell, FP64: combined force and torque, the
 //             rigid-body update (App. A) and the hydrodynamic impulses.
-//   k_spread  one warp per cell: streams the list of (node, w, D w) that
-//             k_sample wrote for the cell and adds the reaction force density
-//             and the smoothed characteristic function to the lattice with
-//             atomics (Sec. 2.2, Eq. enhance-viscosity).
+//   k_spread  one warp per cell: the reaction force density and the
+//             smoothed characteristic function added over the shape list
+//             with atomics (Sec. 2.2, Eq. enhance-viscosity).
 #include <algorithm>
 
 #include "internal.h"
@@ -33,7 +35,6 @@ namespace {
 constexpr int kBinThreads = 32;  // FP64-bound: spread the warps over all SMs
 constexpr int kGbWarps = 4;
 constexpr int kCellThreads = 128;
-constexpr int kRigidThreads = 32;
 constexpr int kMaxNbr = 128;
 
 __device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g)
 }
 
 // ---------------------------------------------------------------------------
-// shape weights of k_sample
+// shape weights of k_weights
 // ---------------------------------------------------------------------------
 struct ShapeArgs {
     const float *hdr;
@@ -397,8 +398,10 @@ struct ShapeArgs {
     float *G, *theta;
     double *part;
     const float *JL;
-    int *sp_idx, *sp_cnt, *flags;
+    int2 *sp_idx;
     float4 *sp_val;
+    int *sp_cnt, *flags;
+    float *sp_S;
     int sp_cap;
     int nx, ny, nz;
     long long Np;
@@ -639,52 +642,44 @@ __device__ __forceinline__ void block_sum(float (&v)[NV], float (*red)[NV], floa
 }
 
 // ---------------------------------------------------------------------------
-// k_sample: S = sum w;  u~ S = sum w u;  omega~ S = -sum D w x (u - u_c)
-// (summation by parts of the central-difference curl; sum D w vanishes over
-// the box, so the constant u_c = u at the centre node changes nothing in
-// exact arithmetic and removes FP32 cancellation);  T^S S / alpha =
-// sum w (sigma n) x (x - R), n = D w / |D w|.
+// k_weights: the shape list of one cell (CTA per cell): every box node where
+// w or its central difference D w is non-zero, with its lattice index, its
+// box coordinates (i0 | i1 << 10 | i2 << 20), w and D w, in visit order
+// (a block-wide ballot prefix keeps the order fixed from run to run), and
+// the normalisation S = sum w over fluid nodes (Sec. 2.2).
 // ---------------------------------------------------------------------------
-template <bool ALPHA>
-__global__ void __launch_bounds__(kCellThreads) k_sample(ShapeArgs a)
+__global__ void __launch_bounds__(kCellThreads) k_weights(ShapeArgs a)
 {
     extern __shared__ float smem[];
     __shared__ Hdr h;
-    __shared__ float red[kCellThreads / 32][9];
-    __shared__ float sums[9];
-    __shared__ float uc[3];
-    __shared__ int s_nsp;
+    __shared__ float red[kCellThreads / 32][1];
+    __shared__ float sums[1];
+    __shared__ int wcnt[kCellThreads / 32];
     const int i = blockIdx.x;
-    if (threadIdx.x == 0) {
-        s_nsp = 0;
-        load_hdr(&a.hdr[kHdrWords * i], h);
-        if (h.ok) {
-            uc[0] = a.U[h.gc];
-            uc[1] = a.U[a.Np + h.gc];
-            uc[2] = a.U[2 * a.Np + h.gc];
-        }
-    }
+    if (threadIdx.x == 0) load_hdr(&a.hdr[kHdrWords * i], h);
     __syncthreads();
-    if (!h.ok) return;
+    if (!h.ok) {
+        if (threadIdx.x == 0) {
+            a.sp_cnt[i] = 0;
+            a.sp_S[i] = 0.f;
+        }
+        return;
+    }
     const Plan P = plan_layout(smem, a.box_dim, h);
     float p1[1] = {shape_weights(a, h, P)};
-    block_sum<1>(p1, reinterpret_cast<float (*)[1]>(red), sums);
-    const float S = sums[0];
-    __syncthreads();
-
+    block_sum<1>(p1, red, sums);
     const int sx = P.sx, sxy = P.sxy;
-    const float thr = 1e-24f * S * S;
     const int total = plan_visit(h, P);
-    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int *sp_idx = a.sp_idx + (size_t)i * a.sp_cap;
+    int2 *sp_idx = a.sp_idx + (size_t)i * a.sp_cap;
     float4 *sp_val = a.sp_val + (size_t)i * a.sp_cap;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int run = 0;
     for (int tb = 0; tb < total; tb += blockDim.x) {
         const int t = tb + threadIdx.x;
-        int r = 0, i0 = 0, i1 = 0, i2 = 0, g = 0;
+        int i0 = 0, i1 = 0, i2 = 0, g = 0;
         float w0 = 0.f, Dx = 0.f, Dy = 0.f, Dz = 0.f;
         if (t < total) {
-            r = P.map[t];
+            const int r = P.map[t];
             i0 = P.vlo[r] + (t - P.pre[r]);
             i1 = P.rc[r] & 0xFFFF;
             i2 = P.rc[r] >> 16;
@@ -697,52 +692,116 @@ __global__ void __launch_bounds__(kCellThreads) k_sample(ShapeArgs a)
             g = P.gyz[r] + wrap1(h.o[0] + i0, a.nx);
         }
         const bool live = w0 != 0.f || Dx != 0.f || Dy != 0.f || Dz != 0.f;
-        // append the node to the cell's spread list (warp-aggregated)
         const unsigned mk = __ballot_sync(0xffffffffu, live);
-        int base = 0;
-        if (lane == 0 && mk) base = atomicAdd(&s_nsp, __popc(mk));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (live) {
-            const int pos = base + __popc(mk & ((1u << lane) - 1u));
-            if (pos < a.sp_cap) {
-                sp_idx[pos] = g;
-                sp_val[pos] = make_float4(w0, Dx, Dy, Dz);
-            }
+        if (lane == 0) wcnt[warp] = __popc(mk);
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int k = 0; k < nw; ++k) {
+            const int c = wcnt[k];
+            before += k < warp ? c : 0;
+            all += c;
         }
-        if (!live) continue;
-        const float ux = a.U[g], uy = a.U[a.Np + g], uz = a.U[2 * a.Np + g];
-        acc[0] += w0 * ux;
-        acc[1] += w0 * uy;
-        acc[2] += w0 * uz;
-        const float vx = ux - uc[0], vy = uy - uc[1], vz = uz - uc[2];
-        acc[3] -= Dy * vz - Dz * vy;
-        acc[4] -= Dz * vx - Dx * vz;
-        acc[5] -= Dx * vy - Dy * vx;
-        if (ALPHA && w0 > 0.f) {
-            const float nd2 = Dx * Dx + Dy * Dy + Dz * Dz;
-            if (nd2 > thr) {
-                const float inv = rsqrtf(nd2);
-                const float nx = Dx * inv, ny = Dy * inv, nz = Dz * inv;
-                const float sxx = a.S[g], syy = a.S[a.Np + g], szz = a.S[2 * a.Np + g];
-                const float sxy_ = a.S[3 * a.Np + g], sxz = a.S[4 * a.Np + g], syz = a.S[5 * a.Np + g];
-                const float tx = sxx * nx + sxy_ * ny + sxz * nz;
-                const float ty = sxy_ * nx + syy * ny + syz * nz;
-                const float tz = sxz * nx + syz * ny + szz * nz;
-                const float r0 = h.base[0] + (float)i0, r1 = h.base[1] + (float)i1, r2 = h.base[2] + (float)i2;
-                acc[6] += w0 * (ty * r2 - tz * r1);
-                acc[7] += w0 * (tz * r0 - tx * r2);
-                acc[8] += w0 * (tx * r1 - ty * r0);
-            }
+        const int pos = run + before + __popc(mk & ((1u << lane) - 1u));
+        if (live && pos < a.sp_cap) {
+            sp_idx[pos] = make_int2(g, i0 | (i1 << 10) | (i2 << 20));
+            sp_val[pos] = make_float4(w0, Dx, Dy, Dz);
         }
+        run += all;
+        __syncthreads();  // wcnt is reused
     }
-    block_sum<9>(acc, red, sums);
     if (threadIdx.x == 0) {
-        double *o = &a.part[10 * i];
-        o[0] = (double)S;
-        for (int k = 0; k < 9; ++k) o[1 + k] = (double)sums[k];
-        a.sp_cnt[i] = min(s_nsp, a.sp_cap);
-        if (s_nsp > a.sp_cap) atomicOr(&a.flags[FLAG_OVERFLOW], OVF_BOX);
+        a.sp_cnt[i] = min(run, a.sp_cap);
+        a.sp_S[i] = sums[0];
+        if (run > a.sp_cap) atomicOr(&a.flags[FLAG_OVERFLOW], OVF_BOX);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Sampling over the cell's shape list (one warp per cell):
+// S = sum w;  u~ S = sum w u;  omega~ S = -sum D w x (u - u_c)  (summation by
+// parts of the central-difference curl; sum D w vanishes over the box, so
+// the constant u_c = u at the centre node changes nothing in exact
+// arithmetic and removes FP32 cancellation);  T^S S / alpha =
+// sum w (sigma n) x (x - R), n = D w / |D w|  (Eqs. vel, vort,
+// pheno_torque_diss).  Lane partial sums, then a fixed shuffle tree: every
+// lane ends with the 9 sums.
+// ---------------------------------------------------------------------------
+constexpr int kCellWarps = 4;
+constexpr int kIlp = 4;  // list entries per lane in flight
+
+template <bool ALPHA>
+__device__ __forceinline__ void sample_sums(const ShapeArgs &a, int i, int n, float S, float (&acc)[9])
+{
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < 9; ++k) acc[k] = 0.f;
+    if (n == 0) return;
+    const float *hd = &a.hdr[kHdrWords * i];
+    const int gc = reinterpret_cast<const int *>(hd)[18];
+    const float uc0 = a.U[gc], uc1 = a.U[a.Np + gc], uc2 = a.U[2 * a.Np + gc];
+    const float b0 = hd[9], b1 = hd[10], b2 = hd[11];
+    const float thr = 1e-24f * S * S;
+    const int2 *idx = a.sp_idx + (size_t)i * a.sp_cap;
+    const float4 *val = a.sp_val + (size_t)i * a.sp_cap;
+    // kIlp independent entries per lane in flight: the list and U loads of
+    // all of them issue before any sum uses them
+    for (int e0 = lane; e0 < n; e0 += 32 * kIlp) {
+        int2 ix[kIlp];
+        float4 v[kIlp];
+        float u[kIlp][3];
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            const int e = e0 + 32 * j;
+            ix[j] = e < n ? idx[e] : make_int2(gc, 0);
+            v[j] = e < n ? val[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            const int g = ix[j].x;
+            u[j][0] = a.U[g];
+            u[j][1] = a.U[a.Np + g];
+            u[j][2] = a.U[2 * a.Np + g];
+        }
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            acc[0] += v[j].x * u[j][0];
+            acc[1] += v[j].x * u[j][1];
+            acc[2] += v[j].x * u[j][2];
+            const float vx = u[j][0] - uc0, vy = u[j][1] - uc1, vz = u[j][2] - uc2;
+            acc[3] -= v[j].z * vz - v[j].w * vy;
+            acc[4] -= v[j].w * vx - v[j].y * vz;
+            acc[5] -= v[j].y * vy - v[j].z * vx;
+        }
+        if (ALPHA) {
+            float sg[kIlp][6];
+            bool on[kIlp];
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) {
+                const int g = ix[j].x;
+                on[j] = v[j].x > 0.f && v[j].y * v[j].y + v[j].z * v[j].z + v[j].w * v[j].w > thr;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) sg[j][c] = on[j] ? a.S[c * a.Np + g] : 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) {
+                if (!on[j]) continue;
+                const float inv = rsqrtf(v[j].y * v[j].y + v[j].z * v[j].z + v[j].w * v[j].w);
+                const float nx = v[j].y * inv, ny = v[j].z * inv, nz = v[j].w * inv;
+                // sigma components: xx, yy, zz, xy, xz, yz
+                const float tx = sg[j][0] * nx + sg[j][3] * ny + sg[j][4] * nz;
+                const float ty = sg[j][3] * nx + sg[j][1] * ny + sg[j][5] * nz;
+                const float tz = sg[j][4] * nx + sg[j][5] * ny + sg[j][2] * nz;
+                const int pk = ix[j].y;
+                const float r0 = b0 + (float)(pk & 1023), r1 = b1 + (float)((pk >> 10) & 1023),
+                            r2 = b2 + (float)(pk >> 20);
+                acc[6] += v[j].x * (ty * r2 - tz * r1);
+                acc[7] += v[j].x * (tz * r0 - tx * r2);
+                acc[8] += v[j].x * (tx * r1 - ty * r0);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
 }
 
 // ---------------------------------------------------------------------------
@@ -750,185 +809,241 @@ __global__ void __launch_bounds__(kCellThreads) k_sample(ShapeArgs a)
 // ---------------------------------------------------------------------------
 struct RigidArgs {
     double *R, *q, *V, *Om;
-    const double *Fm, *Tm, *part;
+    const double *Fm, *Tm;
     const float *hdr;
     int *have, *flags;
     double *diag;
-    float *JL;
     int nc;
-    double M, I[3], iM, iI[3], eT, eR, gT, gR, alpha, L[3];
+    double L[3];
     int per[3];
+    // FP32 constants; aT[c] = eT^2 - 1 (c = 1: previous step closed here)
+    // or eT - 1 (c = 0: first step), aR likewise
+    float M, I[3], iM, iI[3], eT, eR, gT, gR, alpha, aT[2], aR[2];
 };
 
-// sin and cos; for |t| < 0.1 their Taylor series to t^11 / t^12 (remainder
-// below 1e-22, under half an FP64 ulp), else the library function
-__device__ __forceinline__ void sincos_rot(double t, double *s, double *c)
+__device__ __forceinline__ void quat_matrix_f(const float q[4], float Q[9])
 {
-    if (fabs(t) < 0.1) {
-        const double t2 = t * t;
-        *s = t * (1.0 + t2 * (-1.0 / 6.0 + t2 * (1.0 / 120.0 + t2 * (-1.0 / 5040.0 +
-             t2 * (1.0 / 362880.0 + t2 * (-1.0 / 39916800.0))))));
-        *c = 1.0 + t2 * (-0.5 + t2 * (1.0 / 24.0 + t2 * (-1.0 / 720.0 + t2 * (1.0 / 40320.0 +
-             t2 * (-1.0 / 3628800.0 + t2 * (1.0 / 479001600.0))))));
-    } else {
-        sincos(t, s, c);
-    }
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
+    Q[0] = 1.f - 2.f * (y * y + z * z);
+    Q[1] = 2.f * (x * y - w * z);
+    Q[2] = 2.f * (x * z + w * y);
+    Q[3] = 2.f * (x * y + w * z);
+    Q[4] = 1.f - 2.f * (x * x + z * z);
+    Q[5] = 2.f * (y * z - w * x);
+    Q[6] = 2.f * (x * z - w * y);
+    Q[7] = 2.f * (y * z + w * x);
+    Q[8] = 1.f - 2.f * (x * x + y * y);
 }
 
-__global__ void __launch_bounds__(kRigidThreads) k_rigid(RigidArgs a)
+// App. A for one cell, run by the cell's warp.  The state (R, q, V, Omega)
+// stays in FP64; the step's changes are computed in FP32 from forms without
+// cancellation and added to it once in FP64 (FP64 runs at a small fraction
+// of the FP32 rate on this part, so each FP64 value is handled by one lane:
+// lanes 0-2 R and V, 3-5 Omega, 6-9 q, 10-15 F^mech and T^mech; the FP32
+// work is the same in all lanes).  With b = 1 when the previous step is
+// closed here (b = 1/2 on the first step), aT = eT^2 - 1 (eT - 1) and
+// F^comb = F^mech + gamma_T M u~,
+// T^comb = Q^T (T^mech + T^S) + gamma_R I Q^T omega~:
+//   V'  - V0  = aT V0 + b eT F^comb / M                    (steps 6-7, 1-2)
+//   Om' - Om0 = aR Om0 + b eR T^comb / I
+//   J = M (V' - V0) - b F^mech
+//     = M aT V0 + b (eT - 1) F^mech + b eT gamma_T M u~
+//   L = Q I (Om' - Om0) - b T^mech
+//     = Q I (aR Om0 + b eR gamma_R Q^T omega~) + b ((eR - 1) T^mech + eR T^S)
+// The sub-rotations of step 4 (body axes 1, 2, 3, 2, 1 by h Om/2, h Om/2,
+// h Om, h Om/2, h Om/2) turn q by r = (cos t/2, sin t/2 e_k) and the
+// momenta pi = I Om about e_k by t; both are applied as increments,
+// q r - q = q (r - 1) with cos(t/2) - 1 = -sin^2(t/2) / (1 + cos(t/2)),
+// and cos t - 1 = -2 sin^2(t/2), sin t = 2 sin(t/2) cos(t/2).  The stored
+// q has unit norm (rbc_init normalises it, every step renormalises), so
+// |q + dq|^2 - 1 = e = 2 q.dq + dq.dq and the renormalised q is
+// (q + dq)(1 + s), s = -e/2 + 3e^2/8.
+// Returns false, with no update, when the cell has no valid shape box or
+// S = 0; J and L are then undefined.
+template <int N>
+__device__ __forceinline__ float pick(const float (&v)[N], int k)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.nc) return;
-    const int ok = reinterpret_cast<const int *>(a.hdr)[kHdrWords * i + 19];
-    const double S = a.part[10 * i];
-    if (!ok || !(S > 0.0)) {
-        if (ok) atomicOr(&a.flags[FLAG_UNSTABLE], 2);
-        for (int k = 0; k < 6; ++k) a.JL[6 * i + k] = 0.f;
-        return;
-    }
-    double q[4] = {a.q[4 * i], a.q[4 * i + 1], a.q[4 * i + 2], a.q[4 * i + 3]};
-    {
-        const double in = 1.0 / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-        for (int k = 0; k < 4; ++k) q[k] *= in;
-    }
-    double Q[9];
-    quat_matrix(q, Q);
-    const double iS = 1.0 / S;
-    double ut[3], wt[3], TS[3], Fm[3], Tm[3], Fc[3], Tl[3], Tc[3];
-    for (int d = 0; d < 3; ++d) {
-        ut[d] = a.part[10 * i + 1 + d] * iS;
-        wt[d] = a.part[10 * i + 4 + d] * iS;
-        TS[d] = a.alpha * a.part[10 * i + 7 + d] * iS;
-        Fm[d] = a.Fm[3 * i + d];
-        Tm[d] = a.Tm[3 * i + d];
-        // App. A step 5: F^comb = F^mech + gamma_T M u~; torque in the body
-        // frame with the elongational torque included
-        Fc[d] = Fm[d] + a.gT * a.M * ut[d];
-        Tl[d] = Tm[d] + TS[d];
-    }
-    for (int d = 0; d < 3; ++d) {
-        const double Tb = Q[d] * Tl[0] + Q[3 + d] * Tl[1] + Q[6 + d] * Tl[2];
-        const double wb = Q[d] * wt[0] + Q[3 + d] * wt[1] + Q[6 + d] * wt[2];
-        Tc[d] = Tb + a.gR * a.I[d] * wb;
-    }
-    double V[3], Om[3], V0[3], Om0[3];
-    for (int d = 0; d < 3; ++d) {
-        V0[d] = V[d] = a.V[3 * i + d];
-        Om0[d] = Om[d] = a.Om[3 * i + d];
-    }
-    const bool have = a.have[i] != 0;
-    if (have) {  // steps 6-7 of the previous step, with the forces at this pose
-        for (int d = 0; d < 3; ++d) {
-            Om[d] *= a.eR;
-            V[d] *= a.eT;
-            V[d] += 0.5 * Fc[d] * a.iM;
-            Om[d] += 0.5 * Tc[d] * a.iI[d];
-        }
-    }
-    for (int d = 0; d < 3; ++d) {  // steps 1-2
-        Om[d] += 0.5 * Tc[d] * a.iI[d];
-        V[d] += 0.5 * Fc[d] * a.iM;
-        Om[d] *= a.eR;
-        V[d] *= a.eT;
-    }
-    // hydrodynamic impulses: momentum change minus the mechanical impulse
-    const double c = have ? 1.0 : 0.5;
-    double J[3], Lm[3], dp[3];
-    for (int d = 0; d < 3; ++d) {
-        J[d] = a.M * (V[d] - V0[d]) - c * Fm[d];
-        dp[d] = a.I[d] * (Om[d] - Om0[d]);
-    }
-    for (int d = 0; d < 3; ++d) Lm[d] = Q[3 * d] * dp[0] + Q[3 * d + 1] * dp[1] + Q[3 * d + 2] * dp[2] - c * Tm[d];
-    // step 3: drift
-    double R[3];
-    for (int d = 0; d < 3; ++d) {
-        R[d] = a.R[3 * i + d] + V[d];
-        if (a.per[d]) {
-            if (R[d] >= a.L[d])
-                R[d] -= a.L[d];
-            else if (R[d] < 0.0)
-                R[d] += a.L[d];
-        }
-    }
-    // step 4: sub-rotations about body axes 1, 2, 3, 2, 1 by h Om/2, h Om/2,
-    // h Om, h Om/2, h Om/2; each turns pi = I Om by R^T and the frame by R
-    const int ax[5] = {0, 1, 2, 1, 0};
-    const double fr[5] = {0.5, 0.5, 1.0, 0.5, 0.5};
-    for (int s = 0; s < 5; ++s) {
-        const int k = ax[s];
-        const double th = fr[s] * Om[k];
-        double sh, ch;
-        sincos_rot(0.5 * th, &sh, &ch);
-        double r[4] = {ch, 0.0, 0.0, 0.0};
-        r[1 + k] = sh;
-        const double w1 = q[0], x1 = q[1], y1 = q[2], z1 = q[3];
-        q[0] = w1 * r[0] - x1 * r[1] - y1 * r[2] - z1 * r[3];
-        q[1] = w1 * r[1] + x1 * r[0] + y1 * r[3] - z1 * r[2];
-        q[2] = w1 * r[2] - x1 * r[3] + y1 * r[0] + z1 * r[1];
-        q[3] = w1 * r[3] + x1 * r[2] - y1 * r[1] + z1 * r[0];
-        double st, ct;
-        sincos_rot(th, &st, &ct);
-        const int p1 = (k + 1) % 3, p2 = (k + 2) % 3;
-        const double pi1 = a.I[p1] * Om[p1], pi2 = a.I[p2] * Om[p2];
-        Om[p1] = (ct * pi1 + st * pi2) * a.iI[p1];
-        Om[p2] = (-st * pi1 + ct * pi2) * a.iI[p2];
-    }
-    const double in = 1.0 / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    for (int k = 0; k < 4; ++k) a.q[4 * i + k] = q[k] * in;
-    for (int d = 0; d < 3; ++d) {
-        a.R[3 * i + d] = R[d];
-        a.V[3 * i + d] = V[d];
-        a.Om[3 * i + d] = Om[d];
-    }
-    a.have[i] = 1;
-    double *o = &a.diag[21 * i];
-    for (int d = 0; d < 3; ++d) {
-        o[d] = Fm[d];
-        o[3 + d] = Tm[d];
-        o[6 + d] = ut[d];
-        o[9 + d] = wt[d];
-        o[12 + d] = TS[d];
-        o[15 + d] = J[d];
-        o[18 + d] = Lm[d];
-        a.JL[6 * i + d] = (float)J[d];
-        a.JL[6 * i + 3 + d] = (float)Lm[d];
-    }
+    float r = v[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j) r = k == j ? v[j] : r;
+    return r;
 }
 
-// ---------------------------------------------------------------------------
-// k_spread (h = 1): G += -J delta + 1/2 L x D delta at fluid nodes;
-// theta += 1 - (1 - w)^kappa where w > 0
-// ---------------------------------------------------------------------------
-// k_spread (h = 1): over the cell's spread list,
-// G += -J delta + 1/2 L x D delta at fluid nodes (delta = w / S) and
-// theta += 1 - (1 - w)^kappa where w > 0.  One warp per cell.
-constexpr int kSpreadWarps = 4;
-
-__global__ void __launch_bounds__(32 * kSpreadWarps) k_spread(ShapeArgs a, int nc)
+__device__ __forceinline__ bool rigid_update(const RigidArgs &a, int i, float Sf, const float (&sums)[9],
+                                             float (&J)[3], float (&Lm)[3])
 {
     const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kSpreadWarps + (threadIdx.x >> 5);
-    if (i >= nc) return;
     const int ok = reinterpret_cast<const int *>(a.hdr)[kHdrWords * i + 19];
-    const float S = (float)a.part[10 * i];
-    if (!ok || !(S > 0.f)) return;
-    const float iS = 1.0f / S;
-    const float Jx = a.JL[6 * i] * iS, Jy = a.JL[6 * i + 1] * iS, Jz = a.JL[6 * i + 2] * iS;
-    const float Lx = 0.5f * a.JL[6 * i + 3] * iS, Ly = 0.5f * a.JL[6 * i + 4] * iS, Lz = 0.5f * a.JL[6 * i + 5] * iS;
+    if (!ok || !(Sf > 0.f)) {
+        if (ok && lane == 0) atomicOr(&a.flags[FLAG_UNSTABLE], 2);
+        return false;
+    }
+    double mine = 0.0, Rd = 0.0;
+    if (lane < 3) {
+        mine = a.V[3 * i + lane];
+        Rd = a.R[3 * i + lane];
+    } else if (lane < 6) {
+        mine = a.Om[3 * i + lane - 3];
+    } else if (lane < 10) {
+        mine = a.q[4 * i + lane - 6];
+    } else if (lane < 13) {
+        mine = a.Fm[3 * i + lane - 10];
+    } else if (lane < 16) {
+        mine = a.Tm[3 * i + lane - 13];
+    }
+    const float mf = (float)mine;
+    float V0[3], W0[3], qf[4], Fm[3], Tm[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        V0[d] = __shfl_sync(0xffffffffu, mf, d);
+        W0[d] = __shfl_sync(0xffffffffu, mf, 3 + d);
+        Fm[d] = __shfl_sync(0xffffffffu, mf, 10 + d);
+        Tm[d] = __shfl_sync(0xffffffffu, mf, 13 + d);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) qf[k] = __shfl_sync(0xffffffffu, mf, 6 + k);
+    float Q[9];
+    quat_matrix_f(qf, Q);
+    const float iS = 1.0f / Sf;
+    const int c = a.have[i] != 0 ? 1 : 0;
+    const float b = c ? 1.0f : 0.5f, aT = a.aT[c], aR = a.aR[c];
+    float ut[3], wt[3], TS[3], Tl[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        ut[d] = sums[d] * iS;
+        wt[d] = sums[3 + d] * iS;
+        TS[d] = a.alpha * sums[6 + d] * iS;
+        Tl[d] = Tm[d] + TS[d];
+    }
+    float dV[3], dW[3], Lb[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float Fc = Fm[d] + a.gT * a.M * ut[d];
+        const float Tb = Q[d] * Tl[0] + Q[3 + d] * Tl[1] + Q[6 + d] * Tl[2];
+        const float wb = Q[d] * wt[0] + Q[3 + d] * wt[1] + Q[6 + d] * wt[2];
+        const float Tc = Tb + a.gR * a.I[d] * wb;
+        dV[d] = aT * V0[d] + b * a.eT * Fc * a.iM;
+        dW[d] = aR * W0[d] + b * a.eR * Tc * a.iI[d];
+        J[d] = a.M * aT * V0[d] + b * (a.eT - 1.0f) * Fm[d] + b * a.eT * a.gT * a.M * ut[d];
+        Lb[d] = a.I[d] * (aR * W0[d] + b * a.eR * a.gR * wb);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        Lm[d] = Q[3 * d] * Lb[0] + Q[3 * d + 1] * Lb[1] + Q[3 * d + 2] * Lb[2] +
+                b * ((a.eR - 1.0f) * Tm[d] + a.eR * TS[d]);
+    // step 4 in increments: dq accumulates q r - q, dW the momentum turns
+    float Wf[3] = {W0[0] + dW[0], W0[1] + dW[1], W0[2] + dW[2]};
+    float dq[4] = {0.f, 0.f, 0.f, 0.f};
+    const int ax[5] = {0, 1, 2, 1, 0};
+    const float fr[5] = {0.5f, 0.5f, 1.0f, 0.5f, 0.5f};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int k = ax[s];
+        const float th = fr[s] * Wf[k];
+        float sh, ch;
+        sincosf(0.5f * th, &sh, &ch);
+        const float cm1 = -sh * sh / (1.0f + ch);
+        float r[4] = {cm1, 0.f, 0.f, 0.f};  // r - 1
+        r[1 + k] = sh;
+        const float w1 = qf[0] + dq[0], x1 = qf[1] + dq[1], y1 = qf[2] + dq[2], z1 = qf[3] + dq[3];
+        dq[0] += w1 * r[0] - x1 * r[1] - y1 * r[2] - z1 * r[3];
+        dq[1] += w1 * r[1] + x1 * r[0] + y1 * r[3] - z1 * r[2];
+        dq[2] += w1 * r[2] - x1 * r[3] + y1 * r[0] + z1 * r[1];
+        dq[3] += w1 * r[3] + x1 * r[2] - y1 * r[1] + z1 * r[0];
+        const float st = 2.0f * sh * ch, ctm1 = -2.0f * sh * sh;
+        const int p1 = (k + 1) % 3, p2 = (k + 2) % 3;
+        const float pi1 = a.I[p1] * Wf[p1], pi2 = a.I[p2] * Wf[p2];
+        const float d1 = (ctm1 * pi1 + st * pi2) * a.iI[p1];
+        const float d2 = (ctm1 * pi2 - st * pi1) * a.iI[p2];
+        Wf[p1] += d1;
+        Wf[p2] += d2;
+        dW[p1] += d1;
+        dW[p2] += d2;
+    }
+    // FP64 state, one value per lane
+    if (lane < 3) {
+        const double V = mine + (double)pick(dV, lane);
+        double R = Rd + V;  // step 3: drift
+        if (a.per[lane]) {
+            if (R >= a.L[lane])
+                R -= a.L[lane];
+            else if (R < 0.0)
+                R += a.L[lane];
+        }
+        a.V[3 * i + lane] = V;
+        a.R[3 * i + lane] = R;
+    } else if (lane < 6) {
+        a.Om[3 * i + lane - 3] = mine + (double)pick(dW, lane - 3);
+    } else if (lane < 10) {
+        const float e = 2.0f * (qf[0] * dq[0] + qf[1] * dq[1] + qf[2] * dq[2] + qf[3] * dq[3]) +
+                        (dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2] + dq[3] * dq[3]);
+        const float sc = e * (-0.5f + 0.375f * e);
+        const int k = lane - 6;
+        const float dk = pick(dq, k);
+        a.q[4 * i + k] = mine + (double)(dk + (pick(qf, k) + dk) * sc);
+    }
+    // diagnostics: F^mech, tau^mech (FP64 copies), u~, omega~, T^S, J, L
+    double *o = &a.diag[21 * i];
+    if (lane >= 10 && lane < 16) {
+        o[lane - 10] = mine;
+    } else if (lane >= 16 && lane < 31) {
+        const float v[15] = {ut[0], ut[1], ut[2], wt[0], wt[1], wt[2], TS[0], TS[1], TS[2],
+                             J[0],  J[1],  J[2],  Lm[0], Lm[1], Lm[2]};
+        o[6 + lane - 16] = (double)pick(v, lane - 16);
+    }
+    if (lane == 0) a.have[i] = 1;
+    return true;
+}
+
+
+// ---------------------------------------------------------------------------
+// k_cells: the per-cell part of the coupled step, one warp per cell.
+//   1. sample the fields over the cell's shape list (sample_sums);
+//   2. the rigid-body update and the hydrodynamic impulses J, L (App. A);
+//   3. spread (h = 1) over the same list: G += -J delta + 1/2 L x D delta
+//      (delta = w / S) and theta += 1 - (1 - w)^kappa where w > 0 (Sec.
+//      2.2, Eq. enhance-viscosity), with atomics.
+// A cell's spread writes only G and theta, which no sampling reads, so each
+// warp goes straight from its own update to its own spread.
+// ---------------------------------------------------------------------------
+template <bool ALPHA>
+__global__ void __launch_bounds__(32 * kCellWarps) k_cells(ShapeArgs a, RigidArgs ra, int nc)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kCellWarps + (threadIdx.x >> 5);
+    if (i >= nc) return;
     const int n = a.sp_cnt[i];
-    const int *idx = a.sp_idx + (size_t)i * a.sp_cap;
+    const float S = a.sp_S[i];
+    float sums[9];
+    sample_sums<ALPHA>(a, i, n, S, sums);
+    float J[3], L[3];
+    if (!rigid_update(ra, i, S, sums, J, L) || n == 0) return;
+    const float iS = 1.0f / S;
+    const float Jx = J[0] * iS, Jy = J[1] * iS, Jz = J[2] * iS;
+    const float Lx = 0.5f * L[0] * iS, Ly = 0.5f * L[1] * iS, Lz = 0.5f * L[2] * iS;
+    const int2 *idx = a.sp_idx + (size_t)i * a.sp_cap;
     const float4 *val = a.sp_val + (size_t)i * a.sp_cap;
-    for (int e = lane; e < n; e += 32) {
-        const int g = idx[e];
-        const float4 v = val[e];
-        atomicAdd(&a.G[g], -Jx * v.x + (Ly * v.w - Lz * v.z));
-        atomicAdd(&a.G[a.Np + g], -Jy * v.x + (Lz * v.y - Lx * v.w));
-        atomicAdd(&a.G[2 * a.Np + g], -Jz * v.x + (Lx * v.z - Ly * v.y));
-        if (v.x > 0.f) atomicAdd(&a.theta[g], 1.0f - powf(1.0f - v.x, a.kappa));
+    for (int e0 = lane; e0 < n; e0 += 32 * kIlp) {
+        int g[kIlp];
+        float4 v[kIlp];
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            const int e = e0 + 32 * j;
+            g[j] = e < n ? idx[e].x : -1;
+            v[j] = e < n ? val[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            if (g[j] < 0) continue;
+            atomicAdd(&a.G[g[j]], -Jx * v[j].x + (Ly * v[j].w - Lz * v[j].z));
+            atomicAdd(&a.G[a.Np + g[j]], -Jy * v[j].x + (Lz * v[j].y - Lx * v[j].w));
+            atomicAdd(&a.G[2 * a.Np + g[j]], -Jz * v[j].x + (Lx * v[j].z - Ly * v[j].y));
+            if (v[j].x > 0.f) atomicAdd(&a.theta[g[j]], 1.0f - powf(1.0f - v[j].x, a.kappa));
+        }
     }
 }
 
-ShapeArgs shape_args(const Dev &d, const Params &p)
+ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
 {
     ShapeArgs a;
     a.hdr = d.hdr;
@@ -937,11 +1052,10 @@ ShapeArgs shape_args(const Dev &d, const Params &p)
     a.S = d.S;
     a.G = d.G;
     a.theta = d.theta;
-    a.part = d.part;
-    a.JL = d.JL;
-    a.sp_idx = d.sp_idx;
-    a.sp_val = d.sp_val;
-    a.sp_cnt = d.sp_cnt;
+    a.sp_idx = d.sp_idx[buf];
+    a.sp_val = d.sp_val[buf];
+    a.sp_cnt = d.sp_cnt[buf];
+    a.sp_S = d.sp_S[buf];
     a.sp_cap = d.sp_cap;
     a.flags = d.flags;
     a.nx = d.nx;
@@ -1047,25 +1161,17 @@ size_t cells_smem_bytes(const Params &p) { return plan_bytes(p.box_dim); }
 
 void prepare_cells(const Params &p)
 {
-    const int smem = (int)cells_smem_bytes(p);
-    cudaFuncSetAttribute(k_sample<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_sample<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cells_smem_bytes(p));
 }
 
-void launch_sample(const Dev &d, const Params &p, cudaStream_t s)
+void launch_weights(const Dev &d, const Params &p, int buf, cudaStream_t s)
 {
     if (d.nc == 0) return;
-    const ShapeArgs a = shape_args(d, p);
-    const size_t smem = cells_smem_bytes(p);
-    if (d.S != nullptr)
-        k_sample<true><<<d.nc, kCellThreads, smem, s>>>(a);
-    else
-        k_sample<false><<<d.nc, kCellThreads, smem, s>>>(a);
+    k_weights<<<d.nc, kCellThreads, cells_smem_bytes(p), s>>>(shape_args(d, p, buf));
 }
 
-void launch_rigid(const Dev &d, const Params &p, cudaStream_t s)
+static RigidArgs rigid_args(const Dev &d, const Params &p)
 {
-    if (d.nc == 0) return;
     RigidArgs a;
     a.R = d.R;
     a.q = d.q;
@@ -1073,35 +1179,42 @@ void launch_rigid(const Dev &d, const Params &p, cudaStream_t s)
     a.Om = d.Om;
     a.Fm = d.Fm;
     a.Tm = d.Tm;
-    a.part = d.part;
     a.hdr = d.hdr;
     a.have = d.have;
     a.flags = d.flags;
     a.diag = d.diag;
-    a.JL = d.JL;
     a.nc = d.nc;
-    a.M = p.M;
-    a.iM = p.iM;
-    a.eT = p.eT;
-    a.eR = p.eR;
-    a.gT = p.gT;
-    a.gR = p.gR;
-    a.alpha = d.S != nullptr ? (double)p.alpha : 0.0;
+    a.M = (float)p.M;
+    a.iM = (float)p.iM;
+    a.eT = (float)p.eT;
+    a.eR = (float)p.eR;
+    a.gT = (float)p.gT;
+    a.gR = (float)p.gR;
+    a.aT[0] = (float)(p.eT - 1.0);
+    a.aT[1] = (float)((p.eT - 1.0) * (p.eT + 1.0));
+    a.aR[0] = (float)(p.eR - 1.0);
+    a.aR[1] = (float)((p.eR - 1.0) * (p.eR + 1.0));
+    a.alpha = d.S != nullptr ? p.alpha : 0.0f;
     const int dims[3] = {d.nx, d.ny, d.nz};
     for (int k = 0; k < 3; ++k) {
-        a.I[k] = p.I[k];
-        a.iI[k] = p.iI[k];
+        a.I[k] = (float)p.I[k];
+        a.iI[k] = (float)p.iI[k];
         a.per[k] = p.periodic[k];
         a.L[k] = dims[k];
     }
-    k_rigid<<<(d.nc + kRigidThreads - 1) / kRigidThreads, kRigidThreads, 0, s>>>(a);
+    return a;
 }
 
-void launch_spread(const Dev &d, const Params &p, cudaStream_t s)
+void launch_cells(const Dev &d, const Params &p, int buf, cudaStream_t s)
 {
     if (d.nc == 0) return;
-    const ShapeArgs a = shape_args(d, p);
-    k_spread<<<(d.nc + kSpreadWarps - 1) / kSpreadWarps, 32 * kSpreadWarps, 0, s>>>(a, d.nc);
+    const ShapeArgs a = shape_args(d, p, buf);
+    const RigidArgs r = rigid_args(d, p);
+    const int blocks = (d.nc + kCellWarps - 1) / kCellWarps;
+    if (d.S != nullptr)
+        k_cells<true><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc);
+    else
+        k_cells<false><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc);
 }
 
 }  // namespace rbc

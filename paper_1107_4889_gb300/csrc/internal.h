@@ -38,14 +38,15 @@ struct Dev {
     int *have;               // n: cached combined force exists (not the first step)
     double *diag;            // 21n per-cell diagnostics of the last step
     float *hdr;              // kHdrWords per cell: shape header built by k_bin
-    double *part;            // 10n: shape normalisation S and the 9 sampled sums
-    float *JL;               // 6n: impulses J, L handed from k_rigid to k_spread
-    // spread lists written by k_sample: per cell up to sp_cap entries of
-    // (lattice node, w, dw/dx, dw/dy, dw/dz) where w or its gradient is non-zero
+    // shape lists written by k_weights, two buffers (step parity): per cell
+    // up to sp_cap entries (lattice node, packed box coordinates) and
+    // (w, dw/dx, dw/dy, dw/dz) where w or its gradient is non-zero, their
+    // count and the normalisation S = sum w
     int sp_cap;
-    int *sp_idx;             // n * sp_cap
-    float4 *sp_val;          // n * sp_cap
-    int *sp_cnt;             // n
+    int2 *sp_idx[2];         // n * sp_cap
+    float4 *sp_val[2];       // n * sp_cap
+    int *sp_cnt[2];          // n
+    float *sp_S[2];          // n
     // cell list
     int nb[3], nbins, bin_cap;
     double bin_size[3];
@@ -91,9 +92,8 @@ int budget_blocks_for(int N);
 // cells.cu
 void launch_bin(const Dev &d, const Params &p, cudaStream_t s);
 void launch_gb(const Dev &d, const Params &p, cudaStream_t s);
-void launch_sample(const Dev &d, const Params &p, cudaStream_t s);
-void launch_rigid(const Dev &d, const Params &p, cudaStream_t s);
-void launch_spread(const Dev &d, const Params &p, cudaStream_t s);
+void launch_weights(const Dev &d, const Params &p, int buf, cudaStream_t s);
+void launch_cells(const Dev &d, const Params &p, int buf, cudaStream_t s);
 size_t cells_smem_bytes(const Params &p);
 void prepare_cells(const Params &p);
 

@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(kLbThreads) k_lb(LbArgs a)
 constexpr int kStConsumers = 256;                 // collision threads (8 warps)
 constexpr int kStThreads = kStConsumers + 32;     // + the producer warp
 constexpr int kMaxStages = 4;
+constexpr int kLbCtasWithCells = 2;
 constexpr int kStageBytes = 24 * 1024;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bounded mbarrier waits
 
@@ -480,7 +481,9 @@ bool staged_ok(const Dev &d)
 // Ring depth: among 2 .. kMaxStages stages (each depth fixes how many CTAs
 // fit on an SM), take the one whose last wave of batches leaves the fewest
 // idle CTA slots: time ~ ceil(batches / (SMs * k)) * k for k CTAs per SM;
-// ties go to the deeper ring.
+// ties go to the deeper ring.  With cells, at most kLbCtasWithCells CTAs per
+// SM: the next step's cell-list, Gay-Berne and shape-list kernels run
+// alongside the pass and need registers and shared memory on every SM.
 template <bool W, bool C, bool S_>
 void prepare_lb_t(Dev &d)
 {
@@ -498,6 +501,7 @@ void prepare_lb_t(Dev &d)
         cudaFuncSetAttribute(k_lb_staged<W, C, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_staged<W, C, S_>, kStThreads, smem);
+        if (d.nc > 0 && per_sm > kLbCtasWithCells) per_sm = kLbCtasWithCells;
         if (per_sm < 1) continue;
         const long long slots = (long long)sms * per_sm;
         const long long cost = ((nbatches + slots - 1) / slots) * per_sm;
