@@ -330,7 +330,7 @@ struct rbc_handle {
     cudaGraph_t src[3] = {nullptr, nullptr, nullptr};  // kept: exec updates name their nodes
     cudaGraphNode_t ev_node[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     cudaEvent_t ev_dummy[3] = {nullptr, nullptr, nullptr}, fork_ev = nullptr, join_ev = nullptr;
-    cudaEvent_t fork2_ev = nullptr, join2_ev = nullptr;
+    cudaEvent_t join2_ev = nullptr;
     int64_t step = 0;
     int timing_cap = 0, timing_used = 0;
     std::vector<cudaEvent_t> ev;  // 3 per timed step: before the cell kernel, after it, after the lattice pass
@@ -390,10 +390,10 @@ static void body_prologue(rbc_handle *h, int)
 // One coupled step.  Main stream: the per-cell kernel (sample the fields
 // with this pose's shape lists, the rigid update to the new poses, spread
 // the impulses with the same lists), then the lattice pass.  As soon as the
-// new poses exist, side streams build the next step's cell list, then its
-// Gay-Berne forces and (on a second side stream) its shape lists, into
-// buffer parity ^ 1; they read only the poses and write nothing the lattice
-// pass reads.  The step ends when all three streams have.
+// new poses exist, two side streams build the next step's cell list and
+// Gay-Berne forces, and its shape headers and shape lists (into buffer
+// parity ^ 1); they read only the poses and write nothing the lattice pass
+// reads.  The step ends when all three streams have.
 static void body_step(rbc_handle *h, int parity)
 {
     const bool cells = h->d.nc > 0;
@@ -403,15 +403,14 @@ static void body_step(rbc_handle *h, int parity)
     if (cells) {
         cudaEventRecord(h->fork_ev, h->stream);
         cudaStreamWaitEvent(h->side, h->fork_ev, 0);
+        cudaStreamWaitEvent(h->side2, h->fork_ev, 0);
     }
     launch_lb(h->d, h->P.p, parity, h->stream);
     cudaEventRecordWithFlags(h->ev_dummy[2], h->stream, cudaEventRecordExternal);
     if (cells) {
-        launch_bin(h->d, h->P.p, h->side);
-        cudaEventRecord(h->fork2_ev, h->side);
-        cudaStreamWaitEvent(h->side2, h->fork2_ev, 0);
-        launch_gb(h->d, h->P.p, h->side);
         launch_weights(h->d, h->P.p, parity ^ 1, h->side2);
+        launch_bin(h->d, h->P.p, h->side);
+        launch_gb(h->d, h->P.p, h->side);
         cudaEventRecord(h->join_ev, h->side);
         cudaEventRecord(h->join2_ev, h->side2);
         cudaStreamWaitEvent(h->stream, h->join_ev, 0);
@@ -570,7 +569,6 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
         RBC_CU(cudaStreamCreateWithFlags(&h->side2, cudaStreamNonBlocking));
         RBC_CU(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
         RBC_CU(cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
-        RBC_CU(cudaEventCreateWithFlags(&h->fork2_ev, cudaEventDisableTiming));
         RBC_CU(cudaEventCreateWithFlags(&h->join2_ev, cudaEventDisableTiming));
         for (int k = 0; k < 3; ++k) RBC_CU(cudaEventCreate(&h->ev_dummy[k]));
         if (n > 0) {
@@ -789,7 +787,6 @@ void rbc_free(rbc_handle *h)
         if (h->ev_dummy[k]) cudaEventDestroy(h->ev_dummy[k]);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->join_ev) cudaEventDestroy(h->join_ev);
-    if (h->fork2_ev) cudaEventDestroy(h->fork2_ev);
     if (h->join2_ev) cudaEventDestroy(h->join2_ev);
     if (h->side2) {
         cudaStreamSynchronize(h->side2);

@@ -1,8 +1,7 @@
 // cells.cu -- per-cell work of the coupled step.
 //
 //   k_bin     one thread per cell: cell-list bin and slot (FP64 position / bin
-//             size), the shape tensor A = Q S^2 Q^T, and the cell's shape
-//             header (orientation, the box around its support, centre node).
+//             size) and the shape tensor A = Q S^2 Q^T.
 //   k_gb      one warp per cell: the 27 surrounding bins are scanned by the
 //             lanes with the exact FP64 distance test (no fused multiply-add),
 //             passing partners are compacted with a ballot and ranked into a
@@ -12,17 +11,16 @@
 //             certainly outside the range, so FP64 runs only for pairs that
 //             interact.  Each pair is evaluated from both sides: every cell
 //             sums its own force in a fixed order, without atomics.
-//   k_weights one CTA per cell: shape-function weights on the box staged in
-//             shared memory, written out as the cell's shape list (node,
-//             w, D w) with the normalisation S; built for the next pose
-//             while the lattice pass runs.
-//   k_sample  one warp per cell: sampled fields over the shape list
-//             (Eqs. vel, vort, pheno_torque_diss).
-//   k_rigid   one thread per cell, FP64: combined force and torque, the
-//             rigid-body update (App. A) and the hydrodynamic impulses.
-//   k_spread  one warp per cell: the reaction force density and the
-//             smoothed characteristic function added over the shape list
-//             with atomics (Sec. 2.2, Eq. enhance-viscosity).
+//   k_weights one warp per cell: the cell's shape header and the shape-function
+//             weights on its box staged in shared memory, written out as
+//             the cell's shape list (node, w, D w) with the normalisation S;
+//             built for the next pose while the lattice pass runs.
+//   k_cells   one warp per cell: the fields sampled over the shape list
+//             (Eqs. vel, vort, pheno_torque_diss), the rigid-body update
+//             (App. A) with the hydrodynamic impulses, and the reaction
+//             force density and smoothed characteristic function added
+//             over the same list with atomics (Sec. 2.2, Eq.
+//             enhance-viscosity).
 #include <algorithm>
 
 #include "internal.h"
@@ -34,10 +32,33 @@ namespace {
 
 constexpr int kBinThreads = 32;  // FP64-bound: spread the warps over all SMs
 constexpr int kGbWarps = 4;
-constexpr int kCellThreads = 128;
 constexpr int kMaxNbr = 128;
 
 __device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+__device__ __forceinline__ void quat_matrix_f(const float q[4], float Q[9])
+{
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
+    Q[0] = 1.f - 2.f * (y * y + z * z);
+    Q[1] = 2.f * (x * y - w * z);
+    Q[2] = 2.f * (x * z + w * y);
+    Q[3] = 2.f * (x * y + w * z);
+    Q[4] = 1.f - 2.f * (x * x + z * z);
+    Q[5] = 2.f * (y * z - w * x);
+    Q[6] = 2.f * (x * z - w * y);
+    Q[7] = 2.f * (y * z + w * x);
+    Q[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// v[k] for a run-time k without local memory
+template <int N>
+__device__ __forceinline__ float pick(const float (&v)[N], int k)
+{
+    float r = v[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j) r = k == j ? v[j] : r;
+    return r;
+}
 
 // ---------------------------------------------------------------------------
 // k_bin
@@ -46,11 +67,9 @@ struct BinArgs {
     const double *R, *q;
     double *A;
     float *Rf, *Af;
-    float *hdr;
     int *cell_bin, *bin_count, *bin_cells, *flags;
-    int nc, nb[3], cap, dims[3], box_dim;
+    int nc, nb[3], cap;
     double bs[3], a2[3];
-    float xi[3];
 };
 
 __global__ void __launch_bounds__(kBinThreads) k_bin(BinArgs g)
@@ -92,37 +111,6 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(BinArgs g)
     g.Af[6 * i + 4] = (float)S.xz;
     g.Af[6 * i + 5] = (float)S.yz;
 
-    // shape header: the box spans the axis-aligned hull of the support
-    // |y_b| <= xi_b (half extent sum_b |Q_ab| xi_b) plus one node per side.
-    // It must have 1..box_dim nodes per axis and lie within one period of the
-    // lattice on each side; a cell that left the box or went non-finite is
-    // flagged and skipped by the shape kernels.
-    float *h = &g.hdr[kHdrWords * i];
-    int *hi_ = reinterpret_cast<int *>(h);
-    bool ok = true;
-    int ctr[3];
-    for (int a = 0; a < 3; ++a) {
-        double e = 0.0;
-        for (int c = 0; c < 3; ++c) e += fabs(Q[3 * a + c]) * (double)g.xi[c];
-        int lo = 0, n = 1;
-        if (fabs(Rd[a]) < 1e7 && e < 1e7) {
-            lo = (int)ceil(Rd[a] - e) - 1;
-            const int hi = (int)floor(Rd[a] + e) + 1;
-            n = hi - lo + 1;
-            if (n < 1 || n > g.box_dim || lo < -g.dims[a] || hi >= 2 * g.dims[a]) ok = false;
-            ctr[a] = wrap1((int)floor(Rd[a] + 0.5), g.dims[a]);
-        } else {
-            ok = false;
-            ctr[a] = 0;
-        }
-        h[9 + a] = (float)((double)lo - Rd[a]);
-        hi_[12 + a] = lo;
-        hi_[15 + a] = n;
-    }
-    for (int k = 0; k < 9; ++k) h[k] = (float)Q[k];
-    hi_[18] = ok ? ctr[0] + g.dims[0] * (ctr[1] + g.dims[1] * ctr[2]) : 0;
-    hi_[19] = ok ? 1 : 0;
-    if (!ok) atomicOr(&g.flags[FLAG_OVERFLOW], OVF_BOX);
 }
 
 // ---------------------------------------------------------------------------
@@ -389,15 +377,14 @@ __global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g)
 }
 
 // ---------------------------------------------------------------------------
-// shape weights of k_weights
+// Shape lists
 // ---------------------------------------------------------------------------
 struct ShapeArgs {
-    const float *hdr;
+    float *hdr;
+    const double *R, *q;
     const uint8_t *solid;
     const float *U, *S;
     float *G, *theta;
-    double *part;
-    const float *JL;
     int2 *sp_idx;
     float4 *sp_val;
     int *sp_cnt, *flags;
@@ -406,312 +393,152 @@ struct ShapeArgs {
     int nx, ny, nz;
     long long Np;
     float two_over_xi[3], xi[3], kappa, alpha;
-    int box_dim;
+    int box_dim, box_pad;  // box_pad = 3 box_dim^2: shared floats per warp of k_weights
 };
-
-struct Hdr {
-    float Q[9], base[3];
-    int o[3], n[3], gc, ok;
-};
-
-__device__ __forceinline__ void load_hdr(const float *src, Hdr &h)
-{
-    const int *si = reinterpret_cast<const int *>(src);
-    for (int k = 0; k < 9; ++k) h.Q[k] = src[k];
-    for (int k = 0; k < 3; ++k) {
-        h.base[k] = src[9 + k];
-        h.o[k] = si[12 + k];
-        h.n[k] = si[15 + k];
-    }
-    h.gc = si[18];
-    h.ok = si[19];
-}
-
-// Per-row range [lo, hi] of box nodes (along x, the lattice's fastest index)
-// inside the support |y_b| < xi_b of the row x = (., i1, i2); the interval is
-// widened by 1e-3 against rounding (nodes outside the support have w = 0
-// exactly, so the range only saves work).  lo > hi for an empty row.
-// iq[b] = 1 / Q_xb (0 when |Q_xb| is negligible: axis b does not depend on x).
-__device__ __forceinline__ void row_range(const Hdr &h, const float xi[3], const float iq[3], int i1, int i2,
-                                          int &lo, int &hi)
-{
-    const float r1 = h.base[1] + (float)i1, r2 = h.base[2] + (float)i2;
-    float tlo = -1e30f, thi = 1e30f;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        const float cb = h.Q[3 + b] * r1 + h.Q[6 + b] * r2;
-        if (iq[b] == 0.f) {
-            if (fabsf(cb) >= xi[b] * 1.0001f) {
-                lo = 1;
-                hi = 0;
-                return;
-            }
-            continue;
-        }
-        const float t1 = (-xi[b] - cb) * iq[b], t2 = (xi[b] - cb) * iq[b];
-        tlo = fmaxf(tlo, fminf(t1, t2));
-        thi = fminf(thi, fmaxf(t1, t2));
-    }
-    const float flo = tlo - h.base[0], fhi = thi - h.base[0];
-    if (!(flo <= fhi)) {
-        lo = 1;
-        hi = 0;
-        return;
-    }
-    lo = (int)fmaxf(ceilf(flo - 1e-3f), 0.0f);
-    hi = (int)fminf(floorf(fhi + 1e-3f), (float)(h.n[0] - 1));
-}
-
-// Shared-memory work plan of one cell.  The weights live in a box padded
-// with one zero node on every side, so neighbour reads need no bounds test;
-// per row (i1, i2) the plan keeps the weight range, the visit range start,
-// the row's lattice offset and coordinates; items (one per node to process)
-// are the flattened row segments, found through the exclusive prefix of the
-// row lengths and an item -> row map.
-struct Plan {
-    float *sw;                    // padded box: (n0 + 2)(n1 + 2)(n2 + 2)
-    int *rlo, *rhi, *vlo, *gyz;   // per row
-    int *rc;                      // per row: i1 | i2 << 16
-    int *pre;                     // per row: first item
-    unsigned short *map;          // per item: its row
-    int *tot;                     // per warp totals of the scan
-    int sx, sxy;                  // padded strides
-};
-
-__device__ __forceinline__ Plan plan_layout(float *smem, int box_dim, const Hdr &h)
-{
-    const int R = box_dim * box_dim, V = R * box_dim, Vp = (box_dim + 2) * (box_dim + 2) * (box_dim + 2);
-    Plan P;
-    P.sw = smem;
-    P.rlo = reinterpret_cast<int *>(smem + Vp);
-    P.rhi = P.rlo + R;
-    P.vlo = P.rhi + R;
-    P.gyz = P.vlo + R;
-    P.rc = P.gyz + R;
-    P.pre = P.rc + R;
-    P.tot = P.pre + R + 1;
-    P.map = reinterpret_cast<unsigned short *>(P.tot + 32);
-    (void)V;
-    P.sx = h.n[0] + 2;
-    P.sxy = (h.n[0] + 2) * (h.n[1] + 2);
-    return P;
-}
-
-size_t plan_bytes(int box_dim)
-{
-    const size_t R = (size_t)box_dim * box_dim, V = R * box_dim, Vp = (size_t)(box_dim + 2) * (box_dim + 2) * (box_dim + 2);
-    return Vp * sizeof(float) + (6 * R + 1 + 32) * sizeof(int) + V * sizeof(unsigned short);
-}
-
-__device__ __forceinline__ int pidx(const Plan &P, int i0, int i1, int i2)
-{
-    return (i0 + 1) + P.sx * (i1 + 1) + P.sxy * (i2 + 1);
-}
-
-// Rows are split into contiguous chunks, one per thread.  Given each row's
-// item count len(r) (computed by the owner), build the exclusive prefix and
-// the item -> row map; returns the item total (same value in all threads).
-template <typename LenFn>
-__device__ __forceinline__ int plan_items(const Plan &P, int nrows, LenFn len)
-{
-    const int per = (nrows + blockDim.x - 1) / blockDim.x;
-    const int r0 = threadIdx.x * per;
-    int s = 0;
-    for (int k = 0; k < per; ++k)
-        if (r0 + k < nrows) s += len(r0 + k);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int v = s;
-    for (int off = 1; off < 32; off <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, v, off);
-        if (lane >= off) v += u;
-    }
-    if (lane == 31) P.tot[w] = v;
-    __syncthreads();
-    int base = 0, total = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-        if (k < w) base += P.tot[k];
-        total += P.tot[k];
-    }
-    int excl = base + v - s;
-    for (int k = 0; k < per; ++k) {
-        const int r = r0 + k;
-        if (r >= nrows) break;
-        const int n = len(r);
-        P.pre[r] = excl;
-        for (int t = 0; t < n; ++t) P.map[excl + t] = (unsigned short)r;
-        excl += n;
-    }
-    __syncthreads();
-    return total;
-}
-
-// Weights w = prod_b phi(2 y_b / xi_b), y = Q^T (x - R) (Sec. 2.2), 0 at solid
-// nodes, into the padded box (zero elsewhere); also fills the per-row plan.
-// Returns this thread's partial sum of w.
-__device__ __forceinline__ float shape_weights(const ShapeArgs &a, const Hdr &h, const Plan &P)
-{
-    const int n1 = h.n[1], nrows = n1 * h.n[2];
-    const int vp = P.sxy * (h.n[2] + 2);
-    const int nxy = a.nx * a.ny;
-    for (int m = threadIdx.x; m < vp; m += blockDim.x) P.sw[m] = 0.f;
-    float iq[3];
-    for (int b = 0; b < 3; ++b) iq[b] = fabsf(h.Q[b]) < 1e-7f ? 0.f : 1.0f / h.Q[b];
-    const int per = (nrows + blockDim.x - 1) / blockDim.x;
-    const int r0 = threadIdx.x * per;
-    for (int k = 0; k < per; ++k) {
-        const int r = r0 + k;
-        if (r >= nrows) break;
-        const int i1 = r % n1, i2 = r / n1;
-        int lo, hi;
-        row_range(h, a.xi, iq, i1, i2, lo, hi);
-        P.rlo[r] = lo;
-        P.rhi[r] = hi;
-        P.rc[r] = i1 | (i2 << 16);
-        P.gyz[r] = a.nx * wrap1(h.o[1] + i1, a.ny) + nxy * wrap1(h.o[2] + i2, a.nz);
-    }
-    // the zero fill must land before the weights; rows of this thread's
-    // chunk are its own, so the scan needs no barrier before it
-    __syncthreads();
-    const int total = plan_items(P, nrows, [&](int r) { return max(0, P.rhi[r] - P.rlo[r] + 1); });
-    float part = 0.f;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int r = P.map[t];
-        const int i0 = P.rlo[r] + (t - P.pre[r]);
-        const int i1 = P.rc[r] & 0xFFFF, i2 = P.rc[r] >> 16;
-        const int g = P.gyz[r] + wrap1(h.o[0] + i0, a.nx);
-        float w = 0.f;
-        if (a.solid == nullptr || !a.solid[g]) {
-            const float r0f = h.base[0] + (float)i0, r1f = h.base[1] + (float)i1, r2f = h.base[2] + (float)i2;
-            w = peskin4((h.Q[0] * r0f + h.Q[3] * r1f + h.Q[6] * r2f) * a.two_over_xi[0]) *
-                peskin4((h.Q[1] * r0f + h.Q[4] * r1f + h.Q[7] * r2f) * a.two_over_xi[1]) *
-                peskin4((h.Q[2] * r0f + h.Q[5] * r1f + h.Q[8] * r2f) * a.two_over_xi[2]);
-        }
-        P.sw[pidx(P, i0, i1, i2)] = w;
-        part += w;
-    }
-    return part;
-}
-
-// Plan the visit of every node where w or its central difference may be
-// non-zero: per row its own weight range widened by one node (x neighbours)
-// joined with the weight ranges of its four neighbour rows (y, z
-// neighbours).  Records each row's first x in P.vlo; returns the item count.
-__device__ __forceinline__ int plan_visit(const Hdr &h, const Plan &P)
-{
-    const int n0 = h.n[0], n1 = h.n[1], n2 = h.n[2], nrows = n1 * n2;
-    return plan_items(P, nrows, [&](int r) {
-        const int i1 = r % n1, i2 = r / n1;
-        int lo = P.rlo[r] - 1, hi = P.rhi[r] + 1;
-        if (P.rlo[r] > P.rhi[r]) {
-            lo = 1 << 20;
-            hi = -1;
-        }
-        const int nb[4] = {i1 > 0 ? r - 1 : -1, i1 + 1 < n1 ? r + 1 : -1, i2 > 0 ? r - n1 : -1,
-                           i2 + 1 < n2 ? r + n1 : -1};
-        for (int k = 0; k < 4; ++k) {
-            if (nb[k] < 0 || P.rlo[nb[k]] > P.rhi[nb[k]]) continue;
-            lo = min(lo, P.rlo[nb[k]]);
-            hi = max(hi, P.rhi[nb[k]]);
-        }
-        lo = max(lo, 0);
-        hi = min(hi, n0 - 1);
-        P.vlo[r] = lo;
-        return max(0, hi - lo + 1);
-    });
-}
-
-// Sum NV per-thread values over the block in a fixed order (FP32: FP64 runs
-// at a small fraction of the FP32 rate on this part); the result lands in
-// out[] (shared) for all threads.
-template <int NV>
-__device__ __forceinline__ void block_sum(float (&v)[NV], float (*red)[NV], float *out)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k)
-        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
-    if (lane == 0)
-        for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
-    __syncthreads();
-    if (threadIdx.x < NV) {
-        float s = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-        out[threadIdx.x] = s;
-    }
-    __syncthreads();
-}
 
 // ---------------------------------------------------------------------------
-// k_weights: the shape list of one cell (CTA per cell): every box node where
-// w or its central difference D w is non-zero, with its lattice index, its
-// box coordinates (i0 | i1 << 10 | i2 << 20), w and D w, in visit order
-// (a block-wide ballot prefix keeps the order fixed from run to run), and
-// the normalisation S = sum w over fluid nodes (Sec. 2.2).
+// k_weights: shape header and shape list of one cell, one warp per cell.
+// Header: Q (FP32, from the unit quaternion), the box spanning the
+// axis-aligned hull of the support |y_b| <= xi_b (half extent
+// sum_b |Q_ab| xi_b) plus one node per side, its corner relative to R
+// (FP64 difference), the centre node and a validity flag.  The box must
+// have 1..box_dim nodes per axis and lie within one period of the lattice
+// on each side; a cell that left the box or went non-finite is flagged and
+// skipped by the per-cell kernel.  Nodes on the box faces lie outside the
+// support, so w = 0 there and D w = 0 outside the box.
+// Weights w = prod_b phi(2 y_b / xi_b), y = Q^T (x - R) (Sec. 2.2), 0 at
+// solid nodes, are evaluated one z-plane of the box at a time into a ring
+// of three planes in shared memory; plane z is visited once planes z - 1,
+// z, z + 1 are there.  The list holds every box node where w or its central
+// difference D w is non-zero, in lattice order (z, y, x), with its lattice
+// index, box coordinates (i0 | i1 << 10 | i2 << 20), w and D w; S is the sum
+// of w over fluid nodes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kCellThreads) k_weights(ShapeArgs a)
+constexpr int kWtWarps = 4;
+
+__global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc)
 {
     extern __shared__ float smem[];
-    __shared__ Hdr h;
-    __shared__ float red[kCellThreads / 32][1];
-    __shared__ float sums[1];
-    __shared__ int wcnt[kCellThreads / 32];
-    const int i = blockIdx.x;
-    if (threadIdx.x == 0) load_hdr(&a.hdr[kHdrWords * i], h);
-    __syncthreads();
-    if (!h.ok) {
-        if (threadIdx.x == 0) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * kWtWarps + warp;
+    if (i >= nc) return;
+    float *sw = smem + (size_t)warp * a.box_pad;
+    const float qm = lane < 4 ? (float)a.q[4 * i + lane] : 0.f;
+    float qf[4], Q[9];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) qf[k] = __shfl_sync(0xffffffffu, qm, k);
+    quat_matrix_f(qf, Q);
+    // the box along axis `lane` (lanes 0-2)
+    int lo = 0, n = 1, ctr = 0;
+    float base = 0.f;
+    bool okl = true;
+    if (lane < 3) {
+        const int dim = lane == 0 ? a.nx : (lane == 1 ? a.ny : a.nz);
+        const float q0 = lane == 0 ? Q[0] : (lane == 1 ? Q[3] : Q[6]);
+        const float q1 = lane == 0 ? Q[1] : (lane == 1 ? Q[4] : Q[7]);
+        const float q2 = lane == 0 ? Q[2] : (lane == 1 ? Q[5] : Q[8]);
+        const float e = fabsf(q0) * a.xi[0] + fabsf(q1) * a.xi[1] + fabsf(q2) * a.xi[2];
+        const double Rd = a.R[3 * i + lane];
+        if (fabs(Rd) < 1e7 && e < 1e7f) {
+            lo = (int)ceil(Rd - (double)e) - 1;
+            const int hi = (int)floor(Rd + (double)e) + 1;
+            n = hi - lo + 1;
+            okl = !(n < 1 || n > a.box_dim || lo < -dim || hi >= 2 * dim);
+            ctr = wrap1((int)floor(Rd + 0.5), dim);
+            base = (float)((double)lo - Rd);
+        } else {
+            okl = false;
+        }
+    }
+    const bool ok = __all_sync(0xffffffffu, okl);
+    int o[3], nn[3], cc[3];
+    float bs[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        o[ax] = __shfl_sync(0xffffffffu, lo, ax);
+        nn[ax] = __shfl_sync(0xffffffffu, n, ax);
+        cc[ax] = __shfl_sync(0xffffffffu, ctr, ax);
+        bs[ax] = __shfl_sync(0xffffffffu, base, ax);
+    }
+    float *h = &a.hdr[kHdrWords * i];
+    int *hi_ = reinterpret_cast<int *>(h);
+    if (!ok) {
+        if (lane == 0) {
+            hi_[18] = 0;
+            hi_[19] = 0;
             a.sp_cnt[i] = 0;
             a.sp_S[i] = 0.f;
+            atomicOr(&a.flags[FLAG_OVERFLOW], OVF_BOX);
         }
         return;
     }
-    const Plan P = plan_layout(smem, a.box_dim, h);
-    float p1[1] = {shape_weights(a, h, P)};
-    block_sum<1>(p1, red, sums);
-    const int sx = P.sx, sxy = P.sxy;
-    const int total = plan_visit(h, P);
+    const int n0 = nn[0], n1 = nn[1], n2 = nn[2], n01 = n0 * n1;
+    const float inv0 = 1.0f / (float)n0;
+    const int nxy = a.nx * a.ny;
+    const float t0 = a.two_over_xi[0], t1 = a.two_over_xi[1], t2 = a.two_over_xi[2];
+    float part = 0.f;
+    // w of box plane z into ring slot z % 3
+    auto eval_plane = [&](int z) {
+        float *dst = sw + (z % 3) * n01;
+        const float r2 = bs[2] + (float)z;
+        const float e0 = Q[6] * r2, e1 = Q[7] * r2, e2 = Q[8] * r2;
+        const int gz = nxy * wrap1(o[2] + z, a.nz);
+        for (int c = lane; c < n01; c += 32) {
+            const int i1 = (int)(((float)c + 0.5f) * inv0), i0 = c - i1 * n0;
+            const float r0 = bs[0] + (float)i0, r1 = bs[1] + (float)i1;
+            float w = peskin4((Q[0] * r0 + Q[3] * r1 + e0) * t0);
+            if (w != 0.f) w *= peskin4((Q[1] * r0 + Q[4] * r1 + e1) * t1);
+            if (w != 0.f) w *= peskin4((Q[2] * r0 + Q[5] * r1 + e2) * t2);
+            if (w != 0.f && a.solid != nullptr &&
+                a.solid[wrap1(o[0] + i0, a.nx) + a.nx * wrap1(o[1] + i1, a.ny) + gz])
+                w = 0.f;
+            dst[c] = w;
+            part += w;
+        }
+    };
     int2 *sp_idx = a.sp_idx + (size_t)i * a.sp_cap;
     float4 *sp_val = a.sp_val + (size_t)i * a.sp_cap;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int run = 0;
-    for (int tb = 0; tb < total; tb += blockDim.x) {
-        const int t = tb + threadIdx.x;
-        int i0 = 0, i1 = 0, i2 = 0, g = 0;
-        float w0 = 0.f, Dx = 0.f, Dy = 0.f, Dz = 0.f;
-        if (t < total) {
-            const int r = P.map[t];
-            i0 = P.vlo[r] + (t - P.pre[r]);
-            i1 = P.rc[r] & 0xFFFF;
-            i2 = P.rc[r] >> 16;
-            const int m = pidx(P, i0, i1, i2);
-            const float *sw = P.sw;
-            w0 = sw[m];
-            Dx = 0.5f * (sw[m + 1] - sw[m - 1]);
-            Dy = 0.5f * (sw[m + sx] - sw[m - sx]);
-            Dz = 0.5f * (sw[m + sxy] - sw[m - sxy]);
-            g = P.gyz[r] + wrap1(h.o[0] + i0, a.nx);
+    eval_plane(0);
+    for (int z = 0; z < n2; ++z) {
+        if (z + 1 < n2) eval_plane(z + 1);
+        __syncwarp();
+        const float *cur = sw + (z % 3) * n01;
+        const float *prv = sw + ((z + 2) % 3) * n01, *nxt = sw + ((z + 1) % 3) * n01;
+        const bool hzm = z > 0, hzp = z + 1 < n2;
+        const int gz = nxy * wrap1(o[2] + z, a.nz);
+        for (int cb = 0; cb < n01; cb += 32) {
+            const int c = cb + lane;
+            const bool col = c < n01;
+            const int i1 = col ? (int)(((float)c + 0.5f) * inv0) : 0, i0 = col ? c - i1 * n0 : 0;
+            const float w0 = col ? cur[c] : 0.f;
+            const float Dx = 0.5f * ((col && i0 + 1 < n0 ? cur[c + 1] : 0.f) - (col && i0 > 0 ? cur[c - 1] : 0.f));
+            const float Dy = 0.5f * ((col && i1 + 1 < n1 ? cur[c + n0] : 0.f) - (col && i1 > 0 ? cur[c - n0] : 0.f));
+            const float Dz = 0.5f * ((col && hzp ? nxt[c] : 0.f) - (col && hzm ? prv[c] : 0.f));
+            const bool live = w0 != 0.f || Dx != 0.f || Dy != 0.f || Dz != 0.f;
+            const unsigned mk = __ballot_sync(0xffffffffu, live);
+            const int pos = run + __popc(mk & ((1u << lane) - 1u));
+            if (live && pos < a.sp_cap) {
+                sp_idx[pos] = make_int2(wrap1(o[0] + i0, a.nx) + a.nx * wrap1(o[1] + i1, a.ny) + gz,
+                                        i0 | (i1 << 10) | (z << 20));
+                sp_val[pos] = make_float4(w0, Dx, Dy, Dz);
+            }
+            run += __popc(mk);
         }
-        const bool live = w0 != 0.f || Dx != 0.f || Dy != 0.f || Dz != 0.f;
-        const unsigned mk = __ballot_sync(0xffffffffu, live);
-        if (lane == 0) wcnt[warp] = __popc(mk);
-        __syncthreads();
-        int before = 0, all = 0;
-        for (int k = 0; k < nw; ++k) {
-            const int c = wcnt[k];
-            before += k < warp ? c : 0;
-            all += c;
-        }
-        const int pos = run + before + __popc(mk & ((1u << lane) - 1u));
-        if (live && pos < a.sp_cap) {
-            sp_idx[pos] = make_int2(g, i0 | (i1 << 10) | (i2 << 20));
-            sp_val[pos] = make_float4(w0, Dx, Dy, Dz);
-        }
-        run += all;
-        __syncthreads();  // wcnt is reused
+        __syncwarp();  // plane z - 1 is overwritten next
     }
-    if (threadIdx.x == 0) {
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if (lane == 0) {
+        for (int k = 0; k < 9; ++k) h[k] = Q[k];
+        for (int ax = 0; ax < 3; ++ax) {
+            h[9 + ax] = bs[ax];
+            hi_[12 + ax] = o[ax];
+            hi_[15 + ax] = nn[ax];
+        }
+        hi_[18] = cc[0] + a.nx * (cc[1] + a.ny * cc[2]);
+        hi_[19] = 1;
         a.sp_cnt[i] = min(run, a.sp_cap);
-        a.sp_S[i] = sums[0];
+        a.sp_S[i] = part;
         if (run > a.sp_cap) atomicOr(&a.flags[FLAG_OVERFLOW], OVF_BOX);
     }
 }
@@ -821,19 +648,6 @@ struct RigidArgs {
     float M, I[3], iM, iI[3], eT, eR, gT, gR, alpha, aT[2], aR[2];
 };
 
-__device__ __forceinline__ void quat_matrix_f(const float q[4], float Q[9])
-{
-    const float w = q[0], x = q[1], y = q[2], z = q[3];
-    Q[0] = 1.f - 2.f * (y * y + z * z);
-    Q[1] = 2.f * (x * y - w * z);
-    Q[2] = 2.f * (x * z + w * y);
-    Q[3] = 2.f * (x * y + w * z);
-    Q[4] = 1.f - 2.f * (x * x + z * z);
-    Q[5] = 2.f * (y * z - w * x);
-    Q[6] = 2.f * (x * z - w * y);
-    Q[7] = 2.f * (y * z + w * x);
-    Q[8] = 1.f - 2.f * (x * x + y * y);
-}
 
 // App. A for one cell, run by the cell's warp.  The state (R, q, V, Omega)
 // stays in FP64; the step's changes are computed in FP32 from forms without
@@ -860,14 +674,6 @@ __device__ __forceinline__ void quat_matrix_f(const float q[4], float Q[9])
 // (q + dq)(1 + s), s = -e/2 + 3e^2/8.
 // Returns false, with no update, when the cell has no valid shape box or
 // S = 0; J and L are then undefined.
-template <int N>
-__device__ __forceinline__ float pick(const float (&v)[N], int k)
-{
-    float r = v[0];
-#pragma unroll
-    for (int j = 1; j < N; ++j) r = k == j ? v[j] : r;
-    return r;
-}
 
 __device__ __forceinline__ bool rigid_update(const RigidArgs &a, int i, float Sf, const float (&sums)[9],
                                              float (&J)[3], float (&Lm)[3])
@@ -1047,6 +853,8 @@ ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
 {
     ShapeArgs a;
     a.hdr = d.hdr;
+    a.R = d.R;
+    a.q = d.q;
     a.solid = d.solid;
     a.U = d.U;
     a.S = d.S;
@@ -1067,6 +875,7 @@ ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
         a.xi[k] = p.xi[k];
     }
     a.box_dim = p.box_dim;
+    a.box_pad = 3 * p.box_dim * p.box_dim;
     a.kappa = p.kappa;
     a.alpha = p.alpha;
     return a;
@@ -1084,21 +893,16 @@ void launch_bin(const Dev &d, const Params &p, cudaStream_t s)
     g.A = d.A;
     g.Rf = d.Rf;
     g.Af = d.Af;
-    g.hdr = d.hdr;
     g.cell_bin = d.cell_bin;
     g.bin_count = d.bin_count;
     g.bin_cells = d.bin_cells;
     g.flags = d.flags;
     g.nc = d.nc;
     g.cap = d.bin_cap;
-    g.box_dim = p.box_dim;
-    const int dims[3] = {d.nx, d.ny, d.nz};
     for (int a = 0; a < 3; ++a) {
         g.nb[a] = d.nb[a];
         g.bs[a] = d.bin_size[a];
         g.a2[a] = p.a2[a];
-        g.xi[a] = p.xi[a];
-        g.dims[a] = dims[a];
     }
     k_bin<<<(d.nc + kBinThreads - 1) / kBinThreads, kBinThreads, 0, s>>>(g);
 }
@@ -1157,17 +961,22 @@ void launch_gb(const Dev &d, const Params &p, cudaStream_t s)
     k_gb<<<blocks, 32 * kGbWarps, 0, s>>>(g);
 }
 
-size_t cells_smem_bytes(const Params &p) { return plan_bytes(p.box_dim); }
+size_t cells_smem_bytes(const Params &p)
+{
+    return kWtWarps * 3 * (size_t)p.box_dim * p.box_dim * sizeof(float);
+}
 
 void prepare_cells(const Params &p)
 {
     cudaFuncSetAttribute(k_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cells_smem_bytes(p));
+    cudaFuncSetAttribute(k_weights, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 }
 
 void launch_weights(const Dev &d, const Params &p, int buf, cudaStream_t s)
 {
     if (d.nc == 0) return;
-    k_weights<<<d.nc, kCellThreads, cells_smem_bytes(p), s>>>(shape_args(d, p, buf));
+    k_weights<<<(d.nc + kWtWarps - 1) / kWtWarps, 32 * kWtWarps, cells_smem_bytes(p), s>>>(shape_args(d, p, buf),
+                                                                                         d.nc);
 }
 
 static RigidArgs rigid_args(const Dev &d, const Params &p)

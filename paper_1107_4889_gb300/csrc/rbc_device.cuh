@@ -69,12 +69,16 @@ static_assert(lattice_ok(), "D3Q19 velocity set");
 // Shape function factor (Sec. 2.2): Peskin's four-point kernel of r = 2|y|/xi
 // (support |y| <= xi; the printed branches are read as this kernel).
 // ---------------------------------------------------------------------------
+// Both radicands are >= 1 on their branch (1 + 4r - 4r^2 on [0, 1],
+// -7 + 12r - 4r^2 on [1, 2]), so sqrt(x) = x rsqrt(x) needs no special case.
 __device__ __forceinline__ float peskin4(float r)
 {
     r = fabsf(r);
-    if (r <= 1.0f) return 0.125f * (3.0f - 2.0f * r + sqrtf(1.0f + 4.0f * r - 4.0f * r * r));
-    if (r <= 2.0f) return 0.125f * (5.0f - 2.0f * r - sqrtf(-7.0f + 12.0f * r - 4.0f * r * r));
-    return 0.0f;
+    if (r >= 2.0f) return 0.0f;
+    const bool inner = r <= 1.0f;
+    const float x = inner ? 1.0f + 4.0f * r - 4.0f * r * r : -7.0f + 12.0f * r - 4.0f * r * r;
+    const float root = x * rsqrtf(x);
+    return 0.125f * (inner ? 3.0f - 2.0f * r + root : 5.0f - 2.0f * r - root);
 }
 
 // ---------------------------------------------------------------------------
