@@ -166,7 +166,14 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     const int bdim = (int)std::floor(2.0 * xin) + 3;
     p.box_max = bdim * bdim * bdim;
     p.box_dim = bdim;
+    // lattice points of a convex body K number at most vol(K + unit cube);
+    // the support (a parallelepiped of half-extents xi_b, its row ranges
+    // widened by 1e-3) plus the cube lies in the parallelepiped of
+    // half-extents xi_b + sqrt(3)/2 + 0.005
+    p.sup_cap = (int)std::floor((2.0 * q.xi[0] + std::sqrt(3.0) + 0.01) * (2.0 * q.xi[1] + std::sqrt(3.0) + 0.01) *
+                                (2.0 * q.xi[2] + std::sqrt(3.0) + 0.01)) + 1;
     if (nc > 0) {
+        if (bdim > 40) return fail(err, RBC_EINVAL, "shape-function support too large (more than 40 nodes per axis)");
         if (bdim > std::min(g->nx, std::min(g->ny, g->nz)))
             return fail(err, RBC_EINVAL, "shape-function support does not fit in the lattice");
         if (cells_smem_bytes(p) > 200u * 1024u)
@@ -303,6 +310,7 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.wall_start = cv.take<int>(P.nwbins + 1);
     d.wall_xyz = cv.take<int>(3 * (size_t)std::max(P.nw, 1));
     d.flags = cv.take<int>(8);
+    d.lb_work = cv.take<int>(2);
     d.clamps = cv.take<unsigned long long>(1);
     d.budget_blocks = P.budget_blocks;
     d.budget_part = cv.take<double>(8 * (size_t)P.budget_blocks);
@@ -370,7 +378,7 @@ static int capture(rbc_handle *h, void (*body)(rbc_handle *, int), int arg, cuda
                 if (evr == h->ev_dummy[k]) ev_nodes[k] = nd;
         }
     }
-    e = cudaGraphInstantiate(out, graph, 0);
+    e = cudaGraphInstantiate(out, graph, cudaGraphInstantiateFlagUseNodePriority);
     *keep = graph;
     if (e != cudaSuccess) return fail(&h->err, RBC_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
     if (ev_nodes && (!ev_nodes[0] || !ev_nodes[1] || !ev_nodes[2]))
@@ -522,6 +530,7 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
             RBC_CU(cudaMemcpyAsync(d.links, links.data(), links.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
         }
         RBC_CU(cudaMemsetAsync(d.flags, 0, 8 * sizeof(int), s));
+        RBC_CU(cudaMemsetAsync(d.lb_work, 0, 2 * sizeof(int), s));
         RBC_CU(cudaMemsetAsync(d.clamps, 0, sizeof(unsigned long long), s));
         const int n = P.nc;
         if (n > 0) {
@@ -565,6 +574,9 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
         prepare_lb(h->d);
         if (n > 0) prepare_cells(h->P.p);
         RBC_CU(cudaGetLastError());
+        int least = 0, greatest = 0;
+        RBC_CU(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        h->d.side_prio = greatest;
         RBC_CU(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
         RBC_CU(cudaStreamCreateWithFlags(&h->side2, cudaStreamNonBlocking));
         RBC_CU(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));

@@ -22,6 +22,7 @@
 //             over the same list with atomics (Sec. 2.2, Eq.
 //             enhance-viscosity).
 #include <algorithm>
+#include <utility>
 
 #include "internal.h"
 #include "rbc_device.cuh"
@@ -31,7 +32,8 @@ namespace rbc {
 namespace {
 
 constexpr int kBinThreads = 32;  // FP64-bound: spread the warps over all SMs
-constexpr int kGbWarps = 4;
+constexpr int kGbWarps = 8;   // cells per block of the Gay-Berne kernel
+constexpr int kGbQueue = 64;  // partners per cell (cells and wall particles) that may interact
 constexpr int kMaxNbr = 128;
 
 __device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
@@ -48,6 +50,26 @@ __device__ __forceinline__ void quat_matrix_f(const float q[4], float Q[9])
     Q[6] = 2.f * (x * z - w * y);
     Q[7] = 2.f * (y * z + w * x);
     Q[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Launch with a scheduling priority (the side-stream kernels of the step
+// take the device's highest, so that their blocks are dispatched ahead of
+// the persistent lattice pass that runs beside them).
+template <typename... Params, typename... Args>
+void launch_prio(void (*kernel)(Params...), int grid, int block, size_t smem, cudaStream_t s, int prio,
+                 Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = prio;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // v[k] for a run-time k without local memory
@@ -199,181 +221,230 @@ __global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g)
     __shared__ int s_cand[kGbWarps][kMaxNbr];
     __shared__ int s_sort[kGbWarps][kMaxNbr];
     __shared__ int s_pre[kGbWarps][32], s_key[kGbWarps][32];
+    __shared__ int s_q[kGbWarps][kGbQueue];  // partner j >= 0, or -1 - wall particle
+    __shared__ int s_qpre[kGbWarps + 1];
+    __shared__ double s_res[kGbWarps * kGbQueue][6];
+    __shared__ int s_clamped;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int i = blockIdx.x * kGbWarps + wid;
-    if (i >= g.nc) return;  // uniform across the warp
-    const unsigned lt = (1u << lane) - 1u;
-    const double Ri[3] = {g.R[3 * i], g.R[3 * i + 1], g.R[3 * i + 2]};
-    const float Rif[3] = {g.Rf[3 * i], g.Rf[3 * i + 1], g.Rf[3 * i + 2]};
-    const float *aif = &g.Af[6 * i];
-    const float Aif[6] = {aif[0], aif[1], aif[2], aif[3], aif[4], aif[5]};
-    const int bin = g.cell_bin[i];
-    const int b[3] = {bin % g.nb[0], (bin / g.nb[0]) % g.nb[1], bin / (g.nb[0] * g.nb[1])};
-    int lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) bin_range(b[a], g.nb[a], g.per[a], lo[a], hi[a]);
+    if (threadIdx.x == 0) s_clamped = 0;
+    int qn = 0;
+    if (i < g.nc) {  // uniform across the warp
+        const unsigned lt = (1u << lane) - 1u;
+        const double Ri[3] = {g.R[3 * i], g.R[3 * i + 1], g.R[3 * i + 2]};
+        const float Rif[3] = {g.Rf[3 * i], g.Rf[3 * i + 1], g.Rf[3 * i + 2]};
+        const float *aif = &g.Af[6 * i];
+        const float Aif[6] = {aif[0], aif[1], aif[2], aif[3], aif[4], aif[5]};
+        const int bin = g.cell_bin[i];
+        const int b[3] = {bin % g.nb[0], (bin / g.nb[0]) % g.nb[1], bin / (g.nb[0] * g.nb[1])};
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) bin_range(b[a], g.nb[a], g.per[a], lo[a], hi[a]);
 
-    // 1. candidates.  The lanes read the counts of the (up to 27) neighbour
-    //    bins at once and prefix-sum them, so the candidates are visited 32
-    //    at a time.  The FP32 distance decides outside a band around r_cut;
-    //    inside the band the exact FP64 test (no fused multiply-add)
-    //    decides, so the partner sets are those of the FP64 test.
-    const int bx = hi[0] - lo[0] + 1, by = hi[1] - lo[1] + 1, nbn = bx * by * (hi[2] - lo[2] + 1);
-    int cnt = 0;
-    {
-        int my_bb = 0, my_c = 0;
-        if (lane < nbn) {
-            const int ox = lo[0] + lane % bx, oy = lo[1] + (lane / bx) % by, oz = lo[2] + lane / (bx * by);
-            my_bb = wrap_bin(b[0] + ox, g.nb[0]) +
-                    g.nb[0] * (wrap_bin(b[1] + oy, g.nb[1]) + g.nb[1] * wrap_bin(b[2] + oz, g.nb[2]));
-            my_c = min(g.bin_count[my_bb], g.cap);
-        }
-        int incl = my_c;
-        for (int off = 1; off < 32; off <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += v;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        s_pre[wid][lane] = incl - my_c;
-        s_key[wid][lane] = my_bb;
-        __syncwarp();
-        for (int t0 = 0; t0 < total; t0 += 32) {
-            const int t = t0 + lane;
-            bool pass = false;
-            int j = -1;
-            if (t < total) {
-                int k0 = 0, k1 = nbn - 1;  // last bin whose first candidate is <= t
-                while (k0 < k1) {
-                    const int mid = (k0 + k1 + 1) >> 1;
-                    if (s_pre[wid][mid] <= t) k0 = mid; else k1 = mid - 1;
-                }
-                j = g.bin_cells[s_key[wid][k0] * g.cap + (t - s_pre[wid][k0])];
-                if (j != i) {
-                    float df[3] = {Rif[0] - g.Rf[3 * j], Rif[1] - g.Rf[3 * j + 1], Rif[2] - g.Rf[3 * j + 2]};
-                    min_image_f(df, g.per, g.Lf);
-                    const float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
-                    if (r2f < g.rc_lo2) {
-                        pass = true;
-                    } else if (r2f <= g.rc_hi2) {
-                        double d[3] = {__dsub_rn(Ri[0], g.R[3 * j]), __dsub_rn(Ri[1], g.R[3 * j + 1]),
-                                       __dsub_rn(Ri[2], g.R[3 * j + 2])};
-                        min_image(d, g.per, g.L);
-                        pass = dist2_exact(d) < g.rc2;
+        // 1. candidates.  The lanes read the counts of the (up to 27) neighbour
+        //    bins at once and prefix-sum them, so the candidates are visited 32
+        //    at a time.  The FP32 distance decides outside a band around r_cut;
+        //    inside the band the exact FP64 test (no fused multiply-add)
+        //    decides, so the partner sets are those of the FP64 test.
+        const int bx = hi[0] - lo[0] + 1, by = hi[1] - lo[1] + 1, nbn = bx * by * (hi[2] - lo[2] + 1);
+        int cnt = 0;
+        {
+            int my_bb = 0, my_c = 0;
+            if (lane < nbn) {
+                const int ox = lo[0] + lane % bx, oy = lo[1] + (lane / bx) % by, oz = lo[2] + lane / (bx * by);
+                my_bb = wrap_bin(b[0] + ox, g.nb[0]) +
+                        g.nb[0] * (wrap_bin(b[1] + oy, g.nb[1]) + g.nb[1] * wrap_bin(b[2] + oz, g.nb[2]));
+                my_c = min(g.bin_count[my_bb], g.cap);
+            }
+            int incl = my_c;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            s_pre[wid][lane] = incl - my_c;
+            s_key[wid][lane] = my_bb;
+            __syncwarp();
+            for (int t0 = 0; t0 < total; t0 += 32) {
+                const int t = t0 + lane;
+                bool pass = false;
+                int j = -1;
+                if (t < total) {
+                    int k0 = 0, k1 = nbn - 1;  // last bin whose first candidate is <= t
+                    while (k0 < k1) {
+                        const int mid = (k0 + k1 + 1) >> 1;
+                        if (s_pre[wid][mid] <= t) k0 = mid; else k1 = mid - 1;
+                    }
+                    j = g.bin_cells[s_key[wid][k0] * g.cap + (t - s_pre[wid][k0])];
+                    if (j != i) {
+                        float df[3] = {Rif[0] - g.Rf[3 * j], Rif[1] - g.Rf[3 * j + 1], Rif[2] - g.Rf[3 * j + 2]};
+                        min_image_f(df, g.per, g.Lf);
+                        const float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
+                        if (r2f < g.rc_lo2) {
+                            pass = true;
+                        } else if (r2f <= g.rc_hi2) {
+                            double d[3] = {__dsub_rn(Ri[0], g.R[3 * j]), __dsub_rn(Ri[1], g.R[3 * j + 1]),
+                                           __dsub_rn(Ri[2], g.R[3 * j + 2])};
+                            min_image(d, g.per, g.L);
+                            pass = dist2_exact(d) < g.rc2;
+                        }
                     }
                 }
+                const unsigned m = __ballot_sync(0xffffffffu, pass);
+                const int pos = cnt + __popc(m & lt);
+                if (pass && pos < g.maxn) s_cand[wid][pos] = j;
+                cnt += __popc(m);
+            }
+            __syncwarp();
+        }
+        if (cnt > g.maxn) {
+            if (lane == 0) atomicOr(&g.flags[FLAG_OVERFLOW], OVF_NBR);
+            cnt = g.maxn;
+        }
+        __syncwarp();
+        // 2. rank sort by partner index (entries are distinct)
+        for (int e = lane; e < cnt; e += 32) {
+            const int v = s_cand[wid][e];
+            int r = 0;
+            for (int f = 0; f < cnt; ++f) r += s_cand[wid][f] < v;
+            s_sort[wid][r] = v;
+        }
+        __syncwarp();
+        for (int e = lane; e < cnt; e += 32) g.nbr[i * g.maxn + e] = s_sort[wid][e];
+        if (lane == 0) g.nbr_count[i] = cnt;
+
+        // 3. the partners the FP32 reduced distance cannot rule out, in index
+        //    order, then the wall particles of the 27 wall bins around the
+        //    cell (a grid of its own, bins no smaller than the wall radius)
+        //    that pass the FP32 tests and the exact FP64 distance test
+        for (int e0 = 0; e0 < cnt; e0 += 32) {
+            const int e = e0 + lane;
+            bool pass = false;
+            int j = 0;
+            if (e < cnt) {
+                j = s_sort[wid][e];
+                float df[3] = {Rif[0] - g.Rf[3 * j], Rif[1] - g.Rf[3 * j + 1], Rif[2] - g.Rf[3 * j + 2]};
+                min_image_f(df, g.per, g.Lf);
+                const float *ajf = &g.Af[6 * j];
+                const float H[6] = {Aif[0] + ajf[0], Aif[1] + ajf[1], Aif[2] + ajf[2],
+                                    Aif[3] + ajf[3], Aif[4] + ajf[4], Aif[5] + ajf[5]};
+                pass = gb_maybe_in_range(df, H, (float)g.smin, g.rho_cut_f);
             }
             const unsigned m = __ballot_sync(0xffffffffu, pass);
-            const int pos = cnt + __popc(m & lt);
-            if (pass && pos < g.maxn) s_cand[wid][pos] = j;
-            cnt += __popc(m);
+            const int pos = qn + __popc(m & lt);
+            if (pass && pos < kGbQueue) s_q[wid][pos] = j;
+            qn += __popc(m);
         }
-        __syncwarp();
-    }
-    if (cnt > g.maxn) {
-        if (lane == 0) atomicOr(&g.flags[FLAG_OVERFLOW], OVF_NBR);
-        cnt = g.maxn;
-    }
-    __syncwarp();
-    // 2. rank sort by partner index (entries are distinct)
-    for (int e = lane; e < cnt; e += 32) {
-        const int v = s_cand[wid][e];
-        int r = 0;
-        for (int f = 0; f < cnt; ++f) r += s_cand[wid][f] < v;
-        s_sort[wid][r] = v;
-    }
-    __syncwarp();
-    for (int e = lane; e < cnt; e += 32) g.nbr[i * g.maxn + e] = s_sort[wid][e];
-    if (lane == 0) g.nbr_count[i] = cnt;
-
-    // 3. cell-cell pairs, lane-parallel; FP64 only for pairs the FP32
-    //    reduced distance cannot rule out
-    double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-    int clamped = 0;
-    bool hit = false;
-    for (int e = lane; e < cnt; e += 32) {
-        const int j = s_sort[wid][e];
-        float df[3] = {Rif[0] - g.Rf[3 * j], Rif[1] - g.Rf[3 * j + 1], Rif[2] - g.Rf[3 * j + 2]};
-        min_image_f(df, g.per, g.Lf);
-        const float *ajf = &g.Af[6 * j];
-        const float H[6] = {Aif[0] + ajf[0], Aif[1] + ajf[1], Aif[2] + ajf[2],
-                            Aif[3] + ajf[3], Aif[4] + ajf[4], Aif[5] + ajf[5]};
-        if (!gb_maybe_in_range(df, H, (float)g.smin, g.rho_cut_f)) continue;
-        double d[3] = {__dsub_rn(Ri[0], g.R[3 * j]), __dsub_rn(Ri[1], g.R[3 * j + 1]),
-                       __dsub_rn(Ri[2], g.R[3 * j + 2])};
-        min_image(d, g.per, g.L);
-        const double *aj = &g.A[6 * j];
-        const double *ai = &g.A[6 * i];
-        const Sym3 Ai{ai[0], ai[1], ai[2], ai[3], ai[4], ai[5]};
-        const Sym3 Aj{aj[0], aj[1], aj[2], aj[3], aj[4], aj[5]};
-        hit |= gb_pair(d, Ai, Aj, g.smin, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
-    }
-    // 4. wall particles of the 27 wall bins around the cell (a grid of its
-    //    own, bins no smaller than the wall radius), flattened like the
-    //    candidates; FP32 until the exact test of the few that may interact
-    if (g.wall_start != nullptr) {
-        const float rw2f = (float)g.rw2;
-        const float Hw[6] = {Aif[0] + rw2f, Aif[1] + rw2f, Aif[2] + rw2f, Aif[3], Aif[4], Aif[5]};
-        int wb[3], wlo[3], whi[3];
-        for (int a = 0; a < 3; ++a) {
-            const int k = (int)floorf(Rif[a] / g.wbs[a]);
-            wb[a] = k < 0 ? 0 : (k >= g.wnb[a] ? g.wnb[a] - 1 : k);
-            bin_range(wb[a], g.wnb[a], g.per[a], wlo[a], whi[a]);
-        }
-        const int wx = whi[0] - wlo[0] + 1, wy = whi[1] - wlo[1] + 1, nwn = wx * wy * (whi[2] - wlo[2] + 1);
-        int my_start = 0, my_c = 0;
-        if (lane < nwn) {
-            const int ox = wlo[0] + lane % wx, oy = wlo[1] + (lane / wx) % wy, oz = wlo[2] + lane / (wx * wy);
-            const int bb = wrap_bin(wb[0] + ox, g.wnb[0]) +
-                           g.wnb[0] * (wrap_bin(wb[1] + oy, g.wnb[1]) + g.wnb[1] * wrap_bin(wb[2] + oz, g.wnb[2]));
-            my_start = g.wall_start[bb];
-            my_c = g.wall_start[bb + 1] - my_start;
-        }
-        int incl = my_c;
-        for (int off = 1; off < 32; off <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += v;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        __syncwarp();
-        s_pre[wid][lane] = incl - my_c;
-        s_key[wid][lane] = my_start;
-        __syncwarp();
-        for (int t = lane; t < total; t += 32) {
-            int k0 = 0, k1 = nwn - 1;
-            while (k0 < k1) {
-                const int mid = (k0 + k1 + 1) >> 1;
-                if (s_pre[wid][mid] <= t) k0 = mid; else k1 = mid - 1;
-            }
-            const int w = s_key[wid][k0] + (t - s_pre[wid][k0]);
-            const int wxp = g.wall_xyz[3 * w], wyp = g.wall_xyz[3 * w + 1], wzp = g.wall_xyz[3 * w + 2];
-            float df[3] = {Rif[0] - (float)wxp, Rif[1] - (float)wyp, Rif[2] - (float)wzp};
-            min_image_f(df, g.per, g.Lf);
-            if (!(df[0] * df[0] + df[1] * df[1] + df[2] * df[2] < g.rcw2_f)) continue;
-            if (!gb_maybe_in_range(df, Hw, (float)g.smin_w, g.rho_cut_f)) continue;
-            double d[3] = {Ri[0] - (double)wxp, Ri[1] - (double)wyp, Ri[2] - (double)wzp};
-            min_image(d, g.per, g.L);
-            if (!(dist2_exact(d) < g.rcw2)) continue;
-            const double *ai = &g.A[6 * i];
-            const Sym3 Ai{ai[0], ai[1], ai[2], ai[3], ai[4], ai[5]};
-            const Sym3 Aw{g.rw2, g.rw2, g.rw2, 0.0, 0.0, 0.0};
-            hit |= gb_pair(d, Ai, Aw, g.smin_w, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
-        }
-    }
-    // 5. fixed-order warp reduction (skipped when no lane interacted)
-    if (__any_sync(0xffffffffu, hit)) {
-        for (int off = 16; off > 0; off >>= 1)
+        if (g.wall_start != nullptr) {
+            const float rw2f = (float)g.rw2;
+            const float Hw[6] = {Aif[0] + rw2f, Aif[1] + rw2f, Aif[2] + rw2f, Aif[3], Aif[4], Aif[5]};
+            int wb[3], wlo[3], whi[3];
             for (int a = 0; a < 3; ++a) {
-                F[a] += __shfl_xor_sync(0xffffffffu, F[a], off);
-                T[a] += __shfl_xor_sync(0xffffffffu, T[a], off);
+                const int k = (int)floorf(Rif[a] / g.wbs[a]);
+                wb[a] = k < 0 ? 0 : (k >= g.wnb[a] ? g.wnb[a] - 1 : k);
+                bin_range(wb[a], g.wnb[a], g.per[a], wlo[a], whi[a]);
             }
-        for (int off = 16; off > 0; off >>= 1) clamped += __shfl_xor_sync(0xffffffffu, clamped, off);
-    }
-    if (lane == 0) {
-        for (int a = 0; a < 3; ++a) {
-            g.Fm[3 * i + a] = F[a];
-            g.Tm[3 * i + a] = T[a];
+            const int wx = whi[0] - wlo[0] + 1, wy = whi[1] - wlo[1] + 1, nwn = wx * wy * (whi[2] - wlo[2] + 1);
+            int my_start = 0, my_c = 0;
+            if (lane < nwn) {
+                const int ox = wlo[0] + lane % wx, oy = wlo[1] + (lane / wx) % wy, oz = wlo[2] + lane / (wx * wy);
+                const int bb = wrap_bin(wb[0] + ox, g.wnb[0]) +
+                               g.wnb[0] * (wrap_bin(wb[1] + oy, g.wnb[1]) + g.wnb[1] * wrap_bin(wb[2] + oz, g.wnb[2]));
+                my_start = g.wall_start[bb];
+                my_c = g.wall_start[bb + 1] - my_start;
+            }
+            int incl = my_c;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            __syncwarp();
+            s_pre[wid][lane] = incl - my_c;
+            s_key[wid][lane] = my_start;
+            __syncwarp();
+            for (int t0 = 0; t0 < total; t0 += 32) {
+                const int t = t0 + lane;
+                bool pass = false;
+                int w = 0;
+                if (t < total) {
+                    int k0 = 0, k1 = nwn - 1;
+                    while (k0 < k1) {
+                        const int mid = (k0 + k1 + 1) >> 1;
+                        if (s_pre[wid][mid] <= t) k0 = mid; else k1 = mid - 1;
+                    }
+                    w = s_key[wid][k0] + (t - s_pre[wid][k0]);
+                    const int wxp = g.wall_xyz[3 * w], wyp = g.wall_xyz[3 * w + 1], wzp = g.wall_xyz[3 * w + 2];
+                    float df[3] = {Rif[0] - (float)wxp, Rif[1] - (float)wyp, Rif[2] - (float)wzp};
+                    min_image_f(df, g.per, g.Lf);
+                    if (df[0] * df[0] + df[1] * df[1] + df[2] * df[2] < g.rcw2_f &&
+                        gb_maybe_in_range(df, Hw, (float)g.smin_w, g.rho_cut_f)) {
+                        double d[3] = {Ri[0] - (double)wxp, Ri[1] - (double)wyp, Ri[2] - (double)wzp};
+                        min_image(d, g.per, g.L);
+                        pass = dist2_exact(d) < g.rcw2;
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, pass);
+                const int pos = qn + __popc(m & lt);
+                if (pass && pos < kGbQueue) s_q[wid][pos] = -1 - w;
+                qn += __popc(m);
+            }
         }
-        if (clamped) atomicAdd(g.clamps, (unsigned long long)clamped);
+        if (qn > kGbQueue) {
+            if (lane == 0) atomicOr(&g.flags[FLAG_OVERFLOW], OVF_NBR);
+            qn = kGbQueue;
+        }
     }
+    if (lane == 0) s_qpre[wid + 1] = qn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_qpre[0] = 0;
+        for (int c = 0; c < kGbWarps; ++c) s_qpre[c + 1] += s_qpre[c];
+    }
+    __syncthreads();
+    // 4. the block's queue, all lanes busy: one FP64 Gay-Berne pair each
+    //    (Sec. 2.5, App. B); cells and wall particles alike
+    const int P = s_qpre[kGbWarps];
+    for (int e = threadIdx.x; e < P; e += blockDim.x) {
+        int c = 0;
+        while (c + 1 < kGbWarps && s_qpre[c + 1] <= e) ++c;
+        const int ci = blockIdx.x * kGbWarps + c;
+        const int v = s_q[c][e - s_qpre[c]];
+        double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+        int clamped = 0;
+        const double *ai = &g.A[6 * ci];
+        const Sym3 Ai{ai[0], ai[1], ai[2], ai[3], ai[4], ai[5]};
+        if (v >= 0) {
+            double d[3] = {__dsub_rn(g.R[3 * ci], g.R[3 * v]), __dsub_rn(g.R[3 * ci + 1], g.R[3 * v + 1]),
+                           __dsub_rn(g.R[3 * ci + 2], g.R[3 * v + 2])};
+            min_image(d, g.per, g.L);
+            const double *aj = &g.A[6 * v];
+            const Sym3 Aj{aj[0], aj[1], aj[2], aj[3], aj[4], aj[5]};
+            gb_pair(d, Ai, Aj, g.smin, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
+        } else {
+            const int w = -1 - v;
+            double d[3] = {g.R[3 * ci] - (double)g.wall_xyz[3 * w], g.R[3 * ci + 1] - (double)g.wall_xyz[3 * w + 1],
+                           g.R[3 * ci + 2] - (double)g.wall_xyz[3 * w + 2]};
+            min_image(d, g.per, g.L);
+            const Sym3 Aw{g.rw2, g.rw2, g.rw2, 0.0, 0.0, 0.0};
+            gb_pair(d, Ai, Aw, g.smin_w, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
+        }
+        for (int a = 0; a < 3; ++a) {
+            s_res[e][a] = F[a];
+            s_res[e][3 + a] = T[a];
+        }
+        if (clamped) atomicAdd(&s_clamped, clamped);
+    }
+    __syncthreads();
+    // 5. every cell sums its own entries in queue order (deterministic)
+    if (i < g.nc && lane < 6) {
+        double acc = 0.0;
+        for (int e = s_qpre[wid]; e < s_qpre[wid + 1]; ++e) acc += s_res[e][lane];
+        if (lane < 3)
+            g.Fm[3 * i + lane] = acc;
+        else
+            g.Tm[3 * i + lane - 3] = acc;
+    }
+    if (threadIdx.x == 0 && s_clamped) atomicAdd(g.clamps, (unsigned long long)s_clamped);
 }
 
 // ---------------------------------------------------------------------------
@@ -393,7 +464,8 @@ struct ShapeArgs {
     int nx, ny, nz;
     long long Np;
     float two_over_xi[3], xi[3], kappa, alpha;
-    int box_dim, box_pad;  // box_pad = 3 box_dim^2: shared floats per warp of k_weights
+    int box_dim, sup_cap;
+    int box_pad;  // shared words per warp of k_weights: 2 box_dim^2 row words + sup_cap weights
 };
 
 // ---------------------------------------------------------------------------
@@ -404,17 +476,63 @@ struct ShapeArgs {
 // (FP64 difference), the centre node and a validity flag.  The box must
 // have 1..box_dim nodes per axis and lie within one period of the lattice
 // on each side; a cell that left the box or went non-finite is flagged and
-// skipped by the per-cell kernel.  Nodes on the box faces lie outside the
-// support, so w = 0 there and D w = 0 outside the box.
+// skipped by the per-cell kernel.
 // Weights w = prod_b phi(2 y_b / xi_b), y = Q^T (x - R) (Sec. 2.2), 0 at
-// solid nodes, are evaluated one z-plane of the box at a time into a ring
-// of three planes in shared memory; plane z is visited once planes z - 1,
-// z, z + 1 are there.  The list holds every box node where w or its central
-// difference D w is non-zero, in lattice order (z, y, x), with its lattice
-// index, box coordinates (i0 | i1 << 10 | i2 << 20), w and D w; S is the sum
-// of w over fluid nodes.
+// solid nodes, vanish outside the parallelepiped |y_b| < xi_b.  Per box row
+// (i1, i2) the kernel solves the three slab constraints for the row's
+// support interval along x (widened by 1e-3: nodes outside evaluate to 0),
+// evaluates w only there into a compact array, and visits per row the
+// union of its own support widened by one node and the supports of its
+// four neighbour rows: every node where w or its central difference D w can
+// be non-zero.  The list holds those where one is, in lattice order (z, y,
+// x), with the lattice index, box coordinates (i0 | i1 << 10 | i2 << 20), w
+// and D w; S is the sum of w over fluid nodes.
+// Shared memory per warp: row words (support lo | hi << 8 | first item
+// << 16), visit words (same layout) and the compact weights.
 // ---------------------------------------------------------------------------
 constexpr int kWtWarps = 4;
+
+// support interval [lo, hi] of box row (i1, i2) along x; lo > hi if empty
+__device__ __forceinline__ void support_row(const float Q[9], const float bs[3], const float t[3], int n0, int i1,
+                                            int i2, int &lo, int &hi)
+{
+    const float r1 = bs[1] + (float)i1, r2 = bs[2] + (float)i2;
+    float flo = -1e30f, fhi = 1e30f;
+    bool empty = false;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const float cb = Q[3 + b] * r1 + Q[6 + b] * r2;  // y_b without the x term
+        const float lim = 2.0f / t[b];                      // |y_b| < xi_b
+        if (fabsf(Q[b]) < 1e-7f) {
+            empty |= fabsf(cb) >= lim * 1.0001f;
+            continue;
+        }
+        const float iq = 1.0f / Q[b];
+        const float u1 = (-lim - cb) * iq, u2 = (lim - cb) * iq;
+        flo = fmaxf(flo, fminf(u1, u2));
+        fhi = fminf(fhi, fmaxf(u1, u2));
+    }
+    flo -= bs[0];
+    fhi -= bs[0];
+    if (empty || !(flo <= fhi)) {
+        lo = 1;
+        hi = 0;
+        return;
+    }
+    lo = (int)fmaxf(ceilf(flo - 1e-3f), 0.0f);
+    hi = (int)fminf(floorf(fhi + 1e-3f), (float)(n0 - 1));
+}
+
+// largest k in [0, n) with (words[k] >> 16) <= t (the item's row)
+__device__ __forceinline__ int find_row(const unsigned *words, int n, int t)
+{
+    int k0 = 0, k1 = n - 1;
+    while (k0 < k1) {
+        const int mid = (k0 + k1 + 1) >> 1;
+        if ((int)(words[mid] >> 16) <= t) k0 = mid; else k1 = mid - 1;
+    }
+    return k0;
+}
 
 __global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc)
 {
@@ -422,7 +540,10 @@ __global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = blockIdx.x * kWtWarps + warp;
     if (i >= nc) return;
-    float *sw = smem + (size_t)warp * a.box_pad;
+    const int rows_cap = a.box_dim * a.box_dim;
+    unsigned *srow = reinterpret_cast<unsigned *>(smem + (size_t)warp * a.box_pad);
+    unsigned *vrow = srow + rows_cap;
+    float *wc = reinterpret_cast<float *>(vrow + rows_cap);
     const float qm = lane < 4 ? (float)a.q[4 * i + lane] : 0.f;
     float qf[4], Q[9];
 #pragma unroll
@@ -450,7 +571,7 @@ __global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc)
             okl = false;
         }
     }
-    const bool ok = __all_sync(0xffffffffu, okl);
+    bool ok = __all_sync(0xffffffffu, okl);
     int o[3], nn[3], cc[3];
     float bs[3];
 #pragma unroll
@@ -459,6 +580,30 @@ __global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc)
         nn[ax] = __shfl_sync(0xffffffffu, n, ax);
         cc[ax] = __shfl_sync(0xffffffffu, ctr, ax);
         bs[ax] = __shfl_sync(0xffffffffu, base, ax);
+    }
+    const int n0 = nn[0], n1 = nn[1], n2 = nn[2], nrows = n1 * n2;
+    const float inv1 = 1.0f / (float)n1;
+    const float tq[3] = {a.two_over_xi[0], a.two_over_xi[1], a.two_over_xi[2]};
+    // 1. support interval and first item of every row
+    int stot = 0;
+    if (ok) {
+        for (int rb = 0; rb < nrows; rb += 32) {
+            const int r = rb + lane;
+            int slo = 1, shi = 0;
+            if (r < nrows) {
+                const int i2 = (int)(((float)r + 0.5f) * inv1), i1 = r - i2 * n1;
+                support_row(Q, bs, tq, n0, i1, i2, slo, shi);
+            }
+            const int len = slo <= shi ? shi - slo + 1 : 0;
+            int incl = len;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += v;
+            }
+            if (r < nrows) srow[r] = (slo <= shi ? (unsigned)(slo | (shi << 8)) : 0xFFu) | ((unsigned)(stot + incl - len) << 16);
+            stot += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (stot > a.sup_cap) ok = false;
     }
     float *h = &a.hdr[kHdrWords * i];
     int *hi_ = reinterpret_cast<int *>(h);
@@ -472,60 +617,95 @@ __global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc)
         }
         return;
     }
-    const int n0 = nn[0], n1 = nn[1], n2 = nn[2], n01 = n0 * n1;
-    const float inv0 = 1.0f / (float)n0;
-    const int nxy = a.nx * a.ny;
-    const float t0 = a.two_over_xi[0], t1 = a.two_over_xi[1], t2 = a.two_over_xi[2];
-    float part = 0.f;
-    // w of box plane z into ring slot z % 3
-    auto eval_plane = [&](int z) {
-        float *dst = sw + (z % 3) * n01;
-        const float r2 = bs[2] + (float)z;
-        const float e0 = Q[6] * r2, e1 = Q[7] * r2, e2 = Q[8] * r2;
-        const int gz = nxy * wrap1(o[2] + z, a.nz);
-        for (int c = lane; c < n01; c += 32) {
-            const int i1 = (int)(((float)c + 0.5f) * inv0), i0 = c - i1 * n0;
-            const float r0 = bs[0] + (float)i0, r1 = bs[1] + (float)i1;
-            float w = peskin4((Q[0] * r0 + Q[3] * r1 + e0) * t0);
-            if (w != 0.f) w *= peskin4((Q[1] * r0 + Q[4] * r1 + e1) * t1);
-            if (w != 0.f) w *= peskin4((Q[2] * r0 + Q[5] * r1 + e2) * t2);
-            if (w != 0.f && a.solid != nullptr &&
-                a.solid[wrap1(o[0] + i0, a.nx) + a.nx * wrap1(o[1] + i1, a.ny) + gz])
-                w = 0.f;
-            dst[c] = w;
-            part += w;
+    __syncwarp();
+    // 2. visit interval and first item of every row
+    int vtot = 0;
+    for (int rb = 0; rb < nrows; rb += 32) {
+        const int r = rb + lane;
+        int vlo = 1 << 20, vhi = -1;
+        if (r < nrows) {
+            const int i2 = (int)(((float)r + 0.5f) * inv1), i1 = r - i2 * n1;
+            const int own = (int)(srow[r] & 0xFFFFu);
+            if ((own & 0xFF) <= (own >> 8)) {
+                vlo = (own & 0xFF) - 1;
+                vhi = (own >> 8) + 1;
+            }
+            const int nb[4] = {i1 > 0 ? r - 1 : -1, i1 + 1 < n1 ? r + 1 : -1, i2 > 0 ? r - n1 : -1,
+                               i2 + 1 < n2 ? r + n1 : -1};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (nb[k] < 0) continue;
+                const int wk = (int)(srow[nb[k]] & 0xFFFFu);
+                if ((wk & 0xFF) > (wk >> 8)) continue;
+                vlo = min(vlo, wk & 0xFF);
+                vhi = max(vhi, wk >> 8);
+            }
+            vlo = max(vlo, 0);
+            vhi = min(vhi, n0 - 1);
         }
+        const int len = vlo <= vhi ? vhi - vlo + 1 : 0;
+        int incl = len;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (r < nrows) vrow[r] = (len > 0 ? (unsigned)(vlo | (vhi << 8)) : 0xFFu) | ((unsigned)(vtot + incl - len) << 16);
+        vtot += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    // 3. weights over the support items
+    const int nxy = a.nx * a.ny;
+    float part = 0.f;
+    for (int t = lane; t < stot; t += 32) {
+        const int r = find_row(srow, nrows, t);
+        const unsigned word = srow[r];
+        const int i0 = (int)(word & 0xFFu) + (t - (int)(word >> 16));
+        const int i2 = (int)(((float)r + 0.5f) * inv1), i1 = r - i2 * n1;
+        const float r0 = bs[0] + (float)i0, r1 = bs[1] + (float)i1, r2 = bs[2] + (float)i2;
+        float w = peskin4((Q[0] * r0 + Q[3] * r1 + Q[6] * r2) * tq[0]);
+        if (w != 0.f) w *= peskin4((Q[1] * r0 + Q[4] * r1 + Q[7] * r2) * tq[1]);
+        if (w != 0.f) w *= peskin4((Q[2] * r0 + Q[5] * r1 + Q[8] * r2) * tq[2]);
+        if (w != 0.f && a.solid != nullptr &&
+            a.solid[wrap1(o[0] + i0, a.nx) + a.nx * wrap1(o[1] + i1, a.ny) + nxy * wrap1(o[2] + i2, a.nz)])
+            w = 0.f;
+        wc[t] = w;
+        part += w;
+    }
+    __syncwarp();
+    // w at (x, row r) from the compact array; 0 outside the row's support
+    auto W = [&](int r, int x) -> float {
+        const unsigned word = srow[r];
+        const int slo = (int)(word & 0xFFu), shi = (int)((word >> 8) & 0xFFu);
+        return (x >= slo && x <= shi) ? wc[(int)(word >> 16) + x - slo] : 0.f;
     };
+    // 4. the visit items
     int2 *sp_idx = a.sp_idx + (size_t)i * a.sp_cap;
     float4 *sp_val = a.sp_val + (size_t)i * a.sp_cap;
     int run = 0;
-    eval_plane(0);
-    for (int z = 0; z < n2; ++z) {
-        if (z + 1 < n2) eval_plane(z + 1);
-        __syncwarp();
-        const float *cur = sw + (z % 3) * n01;
-        const float *prv = sw + ((z + 2) % 3) * n01, *nxt = sw + ((z + 1) % 3) * n01;
-        const bool hzm = z > 0, hzp = z + 1 < n2;
-        const int gz = nxy * wrap1(o[2] + z, a.nz);
-        for (int cb = 0; cb < n01; cb += 32) {
-            const int c = cb + lane;
-            const bool col = c < n01;
-            const int i1 = col ? (int)(((float)c + 0.5f) * inv0) : 0, i0 = col ? c - i1 * n0 : 0;
-            const float w0 = col ? cur[c] : 0.f;
-            const float Dx = 0.5f * ((col && i0 + 1 < n0 ? cur[c + 1] : 0.f) - (col && i0 > 0 ? cur[c - 1] : 0.f));
-            const float Dy = 0.5f * ((col && i1 + 1 < n1 ? cur[c + n0] : 0.f) - (col && i1 > 0 ? cur[c - n0] : 0.f));
-            const float Dz = 0.5f * ((col && hzp ? nxt[c] : 0.f) - (col && hzm ? prv[c] : 0.f));
-            const bool live = w0 != 0.f || Dx != 0.f || Dy != 0.f || Dz != 0.f;
-            const unsigned mk = __ballot_sync(0xffffffffu, live);
-            const int pos = run + __popc(mk & ((1u << lane) - 1u));
-            if (live && pos < a.sp_cap) {
-                sp_idx[pos] = make_int2(wrap1(o[0] + i0, a.nx) + a.nx * wrap1(o[1] + i1, a.ny) + gz,
-                                        i0 | (i1 << 10) | (z << 20));
-                sp_val[pos] = make_float4(w0, Dx, Dy, Dz);
-            }
-            run += __popc(mk);
+    for (int ub = 0; ub < vtot; ub += 32) {
+        const int u = ub + lane;
+        bool live = false;
+        float w0 = 0.f, Dx = 0.f, Dy = 0.f, Dz = 0.f;
+        int g = 0, pk = 0;
+        if (u < vtot) {
+            const int r = find_row(vrow, nrows, u);
+            const unsigned word = vrow[r];
+            const int i0 = (int)(word & 0xFFu) + (u - (int)(word >> 16));
+            const int i2 = (int)(((float)r + 0.5f) * inv1), i1 = r - i2 * n1;
+            w0 = W(r, i0);
+            Dx = 0.5f * (W(r, i0 + 1) - W(r, i0 - 1));
+            Dy = 0.5f * ((i1 + 1 < n1 ? W(r + 1, i0) : 0.f) - (i1 > 0 ? W(r - 1, i0) : 0.f));
+            Dz = 0.5f * ((i2 + 1 < n2 ? W(r + n1, i0) : 0.f) - (i2 > 0 ? W(r - n1, i0) : 0.f));
+            live = w0 != 0.f || Dx != 0.f || Dy != 0.f || Dz != 0.f;
+            g = wrap1(o[0] + i0, a.nx) + a.nx * wrap1(o[1] + i1, a.ny) + nxy * wrap1(o[2] + i2, a.nz);
+            pk = i0 | (i1 << 10) | (i2 << 20);
         }
-        __syncwarp();  // plane z - 1 is overwritten next
+        const unsigned mk = __ballot_sync(0xffffffffu, live);
+        const int pos = run + __popc(mk & ((1u << lane) - 1u));
+        if (live && pos < a.sp_cap) {
+            sp_idx[pos] = make_int2(g, pk);
+            sp_val[pos] = make_float4(w0, Dx, Dy, Dz);
+        }
+        run += __popc(mk);
     }
     for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
     if (lane == 0) {
@@ -875,7 +1055,8 @@ ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
         a.xi[k] = p.xi[k];
     }
     a.box_dim = p.box_dim;
-    a.box_pad = 3 * p.box_dim * p.box_dim;
+    a.box_pad = 2 * p.box_dim * p.box_dim + p.sup_cap;
+    a.sup_cap = p.sup_cap;
     a.kappa = p.kappa;
     a.alpha = p.alpha;
     return a;
@@ -904,7 +1085,7 @@ void launch_bin(const Dev &d, const Params &p, cudaStream_t s)
         g.bs[a] = d.bin_size[a];
         g.a2[a] = p.a2[a];
     }
-    k_bin<<<(d.nc + kBinThreads - 1) / kBinThreads, kBinThreads, 0, s>>>(g);
+    launch_prio(k_bin, (d.nc + kBinThreads - 1) / kBinThreads, kBinThreads, 0, s, d.side_prio, g);
 }
 
 void launch_gb(const Dev &d, const Params &p, cudaStream_t s)
@@ -958,12 +1139,12 @@ void launch_gb(const Dev &d, const Params &p, cudaStream_t s)
         g.wbs[a] = (float)d.wbin_size[a];
     }
     const int blocks = (d.nc + kGbWarps - 1) / kGbWarps;
-    k_gb<<<blocks, 32 * kGbWarps, 0, s>>>(g);
+    launch_prio(k_gb, blocks, 32 * kGbWarps, 0, s, d.side_prio, g);
 }
 
 size_t cells_smem_bytes(const Params &p)
 {
-    return kWtWarps * 3 * (size_t)p.box_dim * p.box_dim * sizeof(float);
+    return kWtWarps * (2 * (size_t)p.box_dim * p.box_dim + p.sup_cap) * sizeof(float);
 }
 
 void prepare_cells(const Params &p)
@@ -975,8 +1156,8 @@ void prepare_cells(const Params &p)
 void launch_weights(const Dev &d, const Params &p, int buf, cudaStream_t s)
 {
     if (d.nc == 0) return;
-    k_weights<<<(d.nc + kWtWarps - 1) / kWtWarps, 32 * kWtWarps, cells_smem_bytes(p), s>>>(shape_args(d, p, buf),
-                                                                                         d.nc);
+    launch_prio(k_weights, (d.nc + kWtWarps - 1) / kWtWarps, 32 * kWtWarps, cells_smem_bytes(p), s, d.side_prio,
+                shape_args(d, p, buf), d.nc);
 }
 
 static RigidArgs rigid_args(const Dev &d, const Params &p)

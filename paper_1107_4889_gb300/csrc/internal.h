@@ -66,6 +66,8 @@ struct Dev {
     int budget_blocks;
     // lattice pass launch: grid of the row-staged kernel (0: one thread per node)
     int lb_grid, lb_stages;
+    int *lb_work;  // lattice-pass batch counter and finished-CTA count (zero between launches)
+    int side_prio;  // launch priority of the side-stream kernels (the device's highest)
     size_t lb_smem;
 };
 
@@ -79,6 +81,7 @@ struct Params {
     double eps0, smin_cc, smin_w, rw2, rho_floor, rho_cut, rc2, rcw2;
     int periodic[3];
     int box_max;  // largest shape box (nodes)
+    int sup_cap;  // bound on the support nodes of one cell: prod_b (2 xi_b + sqrt 3 + 0.01)
     int box_dim;  // largest shape box edge (nodes)
 };
 

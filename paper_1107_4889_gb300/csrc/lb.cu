@@ -32,6 +32,7 @@ struct LbArgs {
     const uint32_t *links;
     float *G, *th, *U, *S;
     int *flags;
+    int *work;  // [0] next batch, [1] CTAs done; both zero at launch, reset by the last CTA
     int nx, ny, nz, N;
     long long Np;
     float gx0, gy0, gz0, tau0, delta, mach2;
@@ -164,8 +165,10 @@ __global__ void __launch_bounds__(kLbThreads) k_lb(LbArgs a)
 
 // ---------------------------------------------------------------------------
 // Row-staged lattice pass.  A row is the nx nodes at fixed (y, z).  Every
-// CTA is persistent and walks batches of B consecutive y-rows at one z.  A
-// producer warp brings each batch into a ring of L.stages shared-memory
+// CTA is persistent and claims batches of B consecutive y-rows at one z from
+// a global counter (CTAs that start late, behind other kernels on their SM,
+// take fewer).  A producer warp brings each batch into a ring of L.stages
+// shared-memory
 // buffers with asynchronous bulk copies: the upstream row of every speed
 // (row (y - c_y, z - c_z) of plane p) plus the batch's own rows of G, theta
 // and the link mask.  The copies complete on the stage's "full" mbarrier;
@@ -244,6 +247,7 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
 {
     extern __shared__ __align__(128) float sm[];
     __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages];
+    __shared__ int s_batch[kMaxStages];
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int B = L.B, ns = L.stages;
     const int nyb = (ny + B - 1) / B;
@@ -257,25 +261,42 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
     __syncthreads();
 
     if (threadIdx.x >= kStConsumers) {
-        // Producer warp.  A batch is rows y0 .. y0 + nb - 1 at one z.  Staged
+        // Producer warp.  Batches are claimed from a global counter, so a CTA
+        // that starts late (the SM was busy with another kernel) just does
+        // fewer of them.  A batch is rows y0 .. y0 + nb - 1 at one z.  Staged
         // plane k, batch row b sits at stage + (k * B + b) * nx.  For a speed
         // p the upstream rows y - c_y are contiguous in plane p except where
-        // they wrap in y, so each plane needs one copy, or two.
+        // they wrap in y, so each plane needs one copy, or two.  The batch id
+        // goes to s_batch[stage] before the arrive that the consumers'
+        // wait acquires; -1 tells them to stop.
         const int lane = threadIdx.x - kStConsumers;
         const uint32_t row_bytes = (uint32_t)nx * 4u;
         int it = 0;
         bool ok = true;
-        for (int batch = blockIdx.x; batch < nbatches; batch += gridDim.x, ++it) {
+        for (;; ++it) {
             const int stage = it % ns;
             if (it >= ns && !mbar_wait(smem_addr(&empty[stage]), (uint32_t)((it / ns - 1) & 1))) {
                 if (lane == 0) atomicOr(&a.flags[FLAG_TIMEOUT], 1);
                 ok = false;
                 break;
             }
+            int batch = 0;
+            if (lane == 0) batch = atomicAdd(&a.work[0], 1);
+            batch = __shfl_sync(0xffffffffu, batch, 0);
+            const uint32_t bar = smem_addr(&full[stage]);
+            if (batch >= nbatches) {
+                if (lane == 0) {
+                    s_batch[stage] = -1;
+                    mbar_arrive(bar);
+                }
+                break;
+            }
             const int z = batch / nyb, y0 = (batch - z * nyb) * B;
             const int nb = min(B, ny - y0);
-            const uint32_t bar = smem_addr(&full[stage]);
-            if (lane == 0) mbar_expect_tx(bar, (uint32_t)(L.planes * nb) * row_bytes);
+            if (lane == 0) {
+                s_batch[stage] = batch;
+                mbar_expect_tx(bar, (uint32_t)(L.planes * nb) * row_bytes);
+            }
             __syncwarp();
             float *base = sm + (size_t)stage * L.stage_floats;
             for (int k = lane; k < L.planes; k += 32) {
@@ -310,19 +331,26 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
             for (int j = it > ns ? it - ns : 0; j < it; ++j)
                 mbar_wait(smem_addr(&full[j % ns]), (uint32_t)((j / ns) & 1));
         }
+        // the last CTA out resets the counters for the next launch
+        if (lane == 0 && atomicAdd(&a.work[1], 1) == (int)gridDim.x - 1) {
+            a.work[0] = 0;
+            a.work[1] = 0;
+            __threadfence();
+        }
         return;
     }
 
     // consumer warps
     const int lane = threadIdx.x & 31;
     const int plane_stride = B * nx;
-    int it = 0;
-    for (int batch = blockIdx.x; batch < nbatches; batch += gridDim.x, ++it) {
+    for (int it = 0;; ++it) {
         const int stage = it % ns;
         if (!mbar_wait(smem_addr(&full[stage]), (uint32_t)((it / ns) & 1))) {
             if (lane == 0) atomicOr(&a.flags[FLAG_TIMEOUT], 1);
             break;
         }
+        const int batch = s_batch[stage];
+        if (batch < 0) break;
         const float *st = sm + (size_t)stage * L.stage_floats;
         const int z = batch / nyb, y0 = (batch - z * nyb) * B;
         const int nb = min(B, ny - y0);
@@ -558,6 +586,7 @@ void launch_lb(const Dev &d, const Params &p, int parity, cudaStream_t s)
     a.U = d.U;
     a.S = d.S;
     a.flags = d.flags;
+    a.work = d.lb_work;
     a.nx = d.nx;
     a.ny = d.ny;
     a.nz = d.nz;
