@@ -32,6 +32,7 @@
  *      (Eqs. dens, vel) and stress (Eq. stresstensorLB).
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -178,6 +179,163 @@ void orc_lb_pass(int nx, int ny, int nz, const unsigned char *solid, double *f,
         sigma[6 * n + 5] = fac * Pneq[1][2];
     }
     free(fs);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reduced-precision population storage                                      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The paper keeps the populations f_p at every node (Sec. 2.1) and says
+ * nothing about their storage format.  The reduced-precision variants store,
+ * after each collision, the deviation from the lattice weight scaled per
+ * direction,
+ *     s_p = (f_p - w_p) S / w_p,        f_p = w_p + s_p w_p / S,
+ * in a 16-bit floating-point format; the collision itself is done in full
+ * precision.  Dividing by w_p gives all directions the same range
+ * (s_p / S = f_p / w_p - 1).  For IEEE binary16 S = 2^10: its normal range
+ * then reaches down to |f_p / w_p - 1| = 2^-24 and its largest finite value
+ * 65504 up to |f_p / w_p - 1| < 64.  bfloat16 has the exponent range of FP32,
+ * so S = 1.  Scaling by a power of two is exact.
+ *
+ * Two roundings are offered.  Round to nearest (ties to even) is biased in a
+ * steady flow: the same node and direction round the same way step after
+ * step, and the errors add up to a spurious force (a walled channel at
+ * G = 1e-6 loses 2.5 % of its centre-line velocity with binary16, 15 % with
+ * bfloat16).  Stochastic rounding rounds up with probability equal to the
+ * fraction of the gap covered, so the error has zero mean; the random
+ * numbers come from Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
+ * random numbers: as easy as 1, 2, 3", SC 2011), keyed by a seed and counted
+ * by (node, step), six bits per stored value.
+ */
+double orc_storage_scale(int kind) { return kind == ORC_STORE_F16 ? 1024.0 : 1.0; }
+
+/* Format parameters: stored mantissa bits, smallest normal exponent, largest
+ * finite value. */
+static void format_of(int kind, int *mant, int *emin, double *vmax)
+{
+    if (kind == ORC_STORE_F16) {
+        *mant = 10;
+        *emin = -14;
+        *vmax = 65504.0;
+    } else {
+        *mant = 7;
+        *emin = -126;
+        *vmax = 3.3895313892515355e38;
+    }
+}
+
+/* Spacing of the format's values around |v| (gradual underflow below
+ * 2^emin). */
+static double quantum(double v, int mant, int emin)
+{
+    int e;
+    frexp(v, &e); /* |v| in [2^(e-1), 2^e) */
+    int lead = e - 1;
+    if (lead < emin) lead = emin;
+    return ldexp(1.0, lead - mant);
+}
+
+/* To nearest, ties to even (nearbyint in the default rounding mode),
+ * infinity past the largest finite value. */
+double orc_round_storage(int kind, double v)
+{
+    if (kind == ORC_STORE_EXACT || v == 0.0 || !isfinite(v)) return v;
+    int mant, emin;
+    double vmax;
+    format_of(kind, &mant, &emin, &vmax);
+    double q = quantum(v, mant, emin);
+    double r = nearbyint(v / q) * q;
+    if (fabs(r) > vmax) return copysign(INFINITY, v);
+    return r;
+}
+
+/* Stochastic rounding with `bits` random bits r: |v| lies between the format
+ * values a <= |v| < a + q; the result is a + q when
+ * (|v| - a)/q + (r + 1/2)/2^bits >= 1, else a, with the sign of v,
+ * saturated at the largest finite value. */
+double orc_round_storage_sr(int kind, double v, unsigned r, int bits)
+{
+    if (kind == ORC_STORE_EXACT || v == 0.0 || !isfinite(v)) return v;
+    int mant, emin;
+    double vmax;
+    format_of(kind, &mant, &emin, &vmax);
+    double m = fabs(v);
+    double q = quantum(m, mant, emin);
+    double t = m / q, fl = floor(t);
+    double thr = ((double)r + 0.5) / ldexp(1.0, bits);
+    double res = (t - fl + thr >= 1.0 ? fl + 1.0 : fl) * q;
+    if (res > vmax) res = vmax;
+    return copysign(res, v);
+}
+
+/* Philox4x32-10: ten rounds of the Philox S-box on a 128-bit counter with a
+ * 64-bit key bumped by the Weyl constants between rounds (Salmon et al.,
+ * Sec. 5). */
+void orc_philox4x32(const unsigned ctr_in[4], const unsigned key_in[2], unsigned out[4])
+{
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+    for (int i = 0; i < 4; i++) out[i] = c[i];
+}
+
+/* Random-bit slot of a speed: its rank when the 19 speeds are ordered by
+ * 9 (c_z + 1) + 3 (c_y + 1) + (c_x + 1), i.e. by (c_z, c_y, c_x). */
+static int speed_slot(int p)
+{
+    int key = 9 * (CV[p][2] + 1) + 3 * (CV[p][1] + 1) + (CV[p][0] + 1), rank = 0;
+    for (int q = 0; q < NQ; q++)
+        if (9 * (CV[q][2] + 1) + 3 * (CV[q][1] + 1) + (CV[q][0] + 1) < key) rank++;
+    return rank;
+}
+
+/* Six random bits of slot k at node n and step `step`: Philox4x32-10 of the
+ * counter (n, step low word, step high word, 0) under the key (seed low
+ * word, seed high word); slot k takes bits 6 (k mod 5) .. 6 (k mod 5) + 5 of
+ * output word k / 5. */
+unsigned orc_storage_bits(unsigned long long seed, long step, long n, int slot)
+{
+    unsigned ctr[4] = {(unsigned)n, (unsigned)((unsigned long long)step & 0xffffffffu),
+                       (unsigned)((unsigned long long)step >> 32), 0u};
+    unsigned key[2] = {(unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32)};
+    unsigned out[4];
+    orc_philox4x32(ctr, key, out);
+    return (out[slot / 5] >> (6 * (slot % 5))) & 63u;
+}
+
+/* Storage step of the reduced-precision variants on the post-collision
+ * populations of every fluid node. */
+static void store_populations(int kind, int stochastic, unsigned long long seed, long step, long N,
+                              const unsigned char *solid, double *f)
+{
+    if (kind == ORC_STORE_EXACT) return;
+    const double S = orc_storage_scale(kind);
+    for (int p = 0; p < NQ; p++) {
+        const double w = weight(p);
+        const int slot = speed_slot(p);
+        for (long n = 0; n < N; n++) {
+            if (is_solid(solid, n)) continue;
+            double x = (f[(long)p * N + n] - w) * S / w;
+            double sp = stochastic ? orc_round_storage_sr(kind, x, orc_storage_bits(seed, step, n, slot), 6)
+                                   : orc_round_storage(kind, x);
+            f[(long)p * N + n] = w + sp * w / S;
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -651,6 +809,8 @@ struct orc_state {
     int *have_cache;
     double *Fm, *Tm, *ut, *wt, *TS, *J, *L;
     long step, clamps;
+    int storage, stochastic;
+    unsigned long long seed;
 };
 
 static double *dalloc(long n) { return (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double)); }
@@ -684,6 +844,9 @@ orc_state *orc_create(const orc_config *c)
     s->rho_floor = c->rho_floor;
     s->rc = c->r_cut;
     s->rcw = c->r_cut_wall;
+    s->storage = c->storage;
+    s->stochastic = c->stochastic;
+    s->seed = c->seed;
 
     long N = s->N;
     s->f = dalloc(NQ * N);
@@ -935,11 +1098,28 @@ void orc_step(orc_state *s, long nsteps)
         free(sh);
         /* 7. lattice pass */
         orc_lb_pass(nx, ny, nz, s->solid, s->f, s->G, s->tau, s->rho, s->U, s->S);
+        /* 8. storage of the post-collision populations (reduced-precision
+         * variants only) */
+        store_populations(s->storage, s->stochastic, s->seed, s->step, N, s->solid, s->f);
         s->step++;
     }
 }
 
 long orc_step_count(const orc_state *s) { return s->step; }
+
+void orc_populations(const orc_state *s, double *f) { memcpy(f, s->f, sizeof(double) * NQ * (size_t)s->N); }
+
+void orc_set_populations(orc_state *s, const double *f)
+{
+    memcpy(s->f, f, sizeof(double) * NQ * (size_t)s->N);
+    for (long n = 0; n < s->N; n++)
+        for (int p = 0; p < NQ; p++) {
+            if (!is_solid(s->solid, n)) continue;
+            s->f[(long)p * s->N + n] = 0.0;
+        }
+    /* a prescribed state is stored by rounding to nearest */
+    store_populations(s->storage, 0, 0, 0, s->N, s->solid, s->f);
+}
 long orc_clamps(const orc_state *s) { return s->clamps; }
 
 void orc_fields(const orc_state *s, double *rho, double *u, double *sigma)

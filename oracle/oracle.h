@@ -41,7 +41,19 @@ typedef struct {
     double r_cut, r_cut_wall;     /* candidate radii of cell-cell / cell-wall pairs */
     int ncells;
     const double *pos, *quat, *vel, *omega;  /* 3n, 4n, 3n (or NULL), 3n body frame (or NULL) */
+    int storage;      /* population storage: ORC_STORE_EXACT, _F16 or _BF16 */
+    int stochastic;   /* 16-bit storage: 1 = stochastic rounding, 0 = to nearest */
+    unsigned long long seed;  /* key of the stochastic rounding's random numbers */
 } orc_config;
+
+/* Population storage of the reduced-precision variants: FP64 (exact), or the
+ * deviation from the lattice weight, scaled per direction, rounded to IEEE
+ * binary16 or to bfloat16 after every collision, to nearest
+ * (orc_round_storage) or stochastically (orc_round_storage_sr with six bits
+ * of orc_storage_bits per value). */
+#define ORC_STORE_EXACT 0
+#define ORC_STORE_F16 1
+#define ORC_STORE_BF16 2
 
 typedef struct orc_state orc_state;
 
@@ -97,6 +109,26 @@ void orc_rigid_open(double R[3], double Q[9], double V[3], double Om[3],
  * (NULL = 0) and relaxation-time field tau[N]; writes rho, u, sigma. */
 void orc_lb_pass(int nx, int ny, int nz, const unsigned char *solid, double *f,
                  const double *G, const double *tau, double *rho, double *u, double *sigma);
+/* Round v to the storage format `kind` (ORC_STORE_F16: IEEE binary16,
+ * ORC_STORE_BF16: bfloat16; to nearest, ties to even, overflow to infinity);
+ * ORC_STORE_EXACT returns v. */
+double orc_round_storage(int kind, double v);
+/* Stochastic rounding of v to `kind` with random integer r < 2^bits: up
+ * (away from zero) when the fraction of the gap covered plus (r + 1/2)/2^bits
+ * reaches 1; saturates at the largest finite value. */
+double orc_round_storage_sr(int kind, double v, unsigned r, int bits);
+/* Philox4x32-10 block function (counter, key -> 128 random bits). */
+void orc_philox4x32(const unsigned ctr[4], const unsigned key[2], unsigned out[4]);
+/* The six random bits of speed slot `slot` (rank of the speed ordered by
+ * (c_z, c_y, c_x)) at node n and step `step`. */
+unsigned orc_storage_bits(unsigned long long seed, long step, long n, int slot);
+/* Scale S of the stored deviation s_p = (f_p - w_p) S / w_p of `kind`. */
+double orc_storage_scale(int kind);
+/* Post-collision populations f[19*N] (solid nodes 0), direction-major. */
+void orc_populations(const orc_state *s, double *f);
+/* Replace the post-collision populations (then stored in the solver's
+ * format), e.g. to start from a prescribed flow. */
+void orc_set_populations(orc_state *s, const double *f);
 /* Velocities and weights in the order used above. */
 void orc_lattice(int *c, double *w);
 

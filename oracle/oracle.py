@@ -45,7 +45,13 @@ class _Config(ctypes.Structure):
         ("r_cut", ctypes.c_double), ("r_cut_wall", ctypes.c_double),
         ("ncells", ctypes.c_int),
         ("pos", _D), ("quat", _D), ("vel", _D), ("omega", _D),
+        ("storage", ctypes.c_int), ("stochastic", ctypes.c_int),
+        ("seed", ctypes.c_ulonglong),
     ]
+
+
+#: population storage of the reduced-precision variants (orc_round_storage)
+STORAGE = {"f64": 0, "f32": 0, "f16": 1, "bf16": 2}
 
 
 def build(force: bool = False) -> str:
@@ -98,6 +104,18 @@ def lib():
                                      ctypes.c_double, ctypes.c_double]
         L.orc_lb_pass.argtypes = [ctypes.c_int] * 3 + [_U8, _D, _D, _D, _D, _D, _D]
         L.orc_lattice.argtypes = [_I, _D]
+        L.orc_round_storage.restype = ctypes.c_double
+        L.orc_round_storage.argtypes = [ctypes.c_int, ctypes.c_double]
+        L.orc_round_storage_sr.restype = ctypes.c_double
+        L.orc_round_storage_sr.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_uint, ctypes.c_int]
+        L.orc_philox4x32.argtypes = [ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_uint),
+                                     ctypes.POINTER(ctypes.c_uint)]
+        L.orc_storage_bits.restype = ctypes.c_uint
+        L.orc_storage_bits.argtypes = [ctypes.c_ulonglong, ctypes.c_long, ctypes.c_long, ctypes.c_int]
+        L.orc_storage_scale.restype = ctypes.c_double
+        L.orc_storage_scale.argtypes = [ctypes.c_int]
+        L.orc_populations.argtypes = [ctypes.c_void_p, _D]
+        L.orc_set_populations.argtypes = [ctypes.c_void_p, _D]
         _lib = L
     return _lib
 
@@ -134,6 +152,38 @@ def lattice():
     w = np.zeros(19)
     lib().orc_lattice(c.ctypes.data_as(_I), _dp(w))
     return c, w
+
+
+def round_storage(kind, v):
+    """orc_round_storage elementwise: kind 'f16' or 'bf16' (or 'f64')."""
+    k = STORAGE[kind]
+    v = np.asarray(v, dtype=np.float64)
+    return np.array([lib().orc_round_storage(k, float(x)) for x in v.ravel()]).reshape(v.shape)
+
+
+def round_storage_sr(kind, v, r, bits=6):
+    """orc_round_storage_sr elementwise with random integers r (same shape)."""
+    k = STORAGE[kind]
+    v = np.asarray(v, dtype=np.float64)
+    r = np.broadcast_to(np.asarray(r, dtype=np.int64), v.shape)
+    return np.array([lib().orc_round_storage_sr(k, float(x), int(ri), int(bits))
+                     for x, ri in zip(v.ravel(), r.ravel())]).reshape(v.shape)
+
+
+def philox4x32(ctr, key):
+    c = (ctypes.c_uint * 4)(*[int(x) & 0xffffffff for x in ctr])
+    k = (ctypes.c_uint * 2)(*[int(x) & 0xffffffff for x in key])
+    o = (ctypes.c_uint * 4)()
+    lib().orc_philox4x32(c, k, o)
+    return [int(x) for x in o]
+
+
+def storage_bits(seed, step, n, slot):
+    return int(lib().orc_storage_bits(int(seed), int(step), int(n), int(slot)))
+
+
+def storage_scale(kind):
+    return float(lib().orc_storage_scale(STORAGE[kind]))
 
 
 def peskin(r):
@@ -231,9 +281,12 @@ def lb_pass(dims, solid, f, G, tau):
 class Oracle:
     """FP64 coupled solver.  ``geometry``: dict(nx, ny, nz, periodic, solid,
     body_force); ``cells``: dict(pos (n,3), quat (n,4), vel, omega);
-    ``params``: dict with the keys of orc_config."""
+    ``params``: dict with the keys of orc_config.  ``storage``: population
+    storage of the reduced-precision variants ('f64' exact, 'f16', 'bf16';
+    'f32' is taken as exact); ``stochastic``: stochastic rounding of the
+    16-bit store (else to nearest) keyed by ``seed``."""
 
-    def __init__(self, geometry, cells, params):
+    def __init__(self, geometry, cells, params, storage="f64", stochastic=True, seed=0):
         L = lib()
         nx, ny, nz = int(geometry["nx"]), int(geometry["ny"]), int(geometry["nz"])
         self.dims = (nx, ny, nz)
@@ -262,6 +315,9 @@ class Oracle:
         c.ncells = n
         c.pos, c.quat = _dp(self._pos), _dp(self._quat)
         c.vel, c.omega = _dp(self._vel), _dp(self._om)
+        c.storage = STORAGE[storage]
+        c.stochastic = 1 if stochastic else 0
+        c.seed = int(seed) & 0xffffffffffffffff
         self._cfg = c
         self._h = L.orc_create(ctypes.byref(c))
         if not self._h:
@@ -293,6 +349,16 @@ class Oracle:
         rho, u, s = np.zeros(self.N), np.zeros(3 * self.N), np.zeros(6 * self.N)
         lib().orc_fields(self._h, _dp(rho), _dp(u), _dp(s))
         return rho, u.reshape(self.N, 3), s.reshape(self.N, 6)
+
+    def populations(self):
+        """Post-collision populations f (19, N) in the oracle's speed order."""
+        f = np.zeros(19 * self.N)
+        lib().orc_populations(self._h, _dp(f))
+        return f.reshape(19, self.N)
+
+    def set_populations(self, f):
+        f = _f64(f, (19 * self.N,))
+        lib().orc_set_populations(self._h, _dp(f))
 
     def set_sampled_fields(self, u=None, sigma=None):
         u = _f64(u, (3 * self.N,)) if u is not None else None
