@@ -42,16 +42,29 @@ UNIT = "MLUPS"
 L2_BYTES = 129e6
 
 
-def _workload(name):
+PREC_NAME = {"f32": "FP32", "f16": "binary16 (stochastic rounding)", "bf16": "bfloat16 (stochastic rounding)"}
+
+
+def _workload(name, precision="f32"):
     if name == "channel":
         g, c, p = wl.channel_workload()
-        desc = "walled channel 64x64x256, 3650 RBC (H=0.35), G=5.376e-7, FP32 populations"
+        desc = "walled channel 64x64x256, 3650 RBC (H=0.35), G=5.376e-7"
     elif name == "box32":
         g, c, p = wl.box_workload()
-        desc = "periodic box 32^3, 32 RBC (H=0.098), G=1e-6, FP32 populations"
+        desc = "periodic box 32^3, 32 RBC (H=0.098), G=1e-6"
+    elif name in ("box256", "box128"):
+        L = int(name[3:])
+        g = wl.periodic_box(L, body_force=(1e-6, 0.0, 0.0))
+        c, p = None, wl.params()
+        desc = f"periodic box {L}^3, fluid only, G=1e-6"
+    elif name == "tube":
+        g, c, p = wl.tube_workload()
+        desc = (f"tube r=120 in 256^3, {len(c['pos'])} RBC (H={wl.tube_hematocrit(g, len(c['pos'])):.2f} "
+                f"of the lumen), G_z={g['body_force'][2]:.3e}")
     else:
         raise SystemExit(f"unknown workload {name}")
-    return g, c, p, desc
+    p = dict(p, precision=precision)
+    return g, c, p, f"{desc}, {PREC_NAME[precision]} populations"
 
 
 def _dist():
@@ -143,10 +156,12 @@ def _lb_source_hash():
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic(workload):
+def _profiled_traffic(workload, precision="f32"):
     """DRAM bytes per lattice-pass launch from the committed ncu summary, if
     it was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", f"lb_pass_{workload}.md")
+    if precision != "f32":
+        path = os.path.join(ROOT, "profiles", f"lb_pass_{workload}_{precision}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -157,13 +172,17 @@ def _profiled_traffic(workload):
     return float(m_bytes.group(1))
 
 
-def _algorithmic_bytes_per_node(geom, params):
-    # populations 19 x 4 B read + written; G (3) and theta (1) read; u (3)
-    # written; sigma (6) written when the elongational torque is on; the
-    # node's solid flag (1 B) on walled lattices
-    b = 2 * 19 * 4 + 4 * 4 + 3 * 4
-    if params.get("alpha_tt", 0.04) != 0.0:
-        b += 6 * 4
+def _algorithmic_bytes_per_node(geom, params, has_cells=True):
+    # populations 19 x e B read + written (e = 4 FP32, 2 for the 16-bit
+    # stores); u (3) written; with cells, G (3) and theta (1) read and sigma
+    # (6) written when the elongational torque is on; the node's solid flag
+    # (1 B) on walled lattices
+    e = 4 if params.get("precision", "f32") == "f32" else 2
+    b = 2 * 19 * e + 3 * 4
+    if has_cells:
+        b += 4 * 4
+        if params.get("alpha_tt", 0.04) != 0.0:
+            b += 6 * 4
     if geom["solid"] is not None:
         b += 1
     return b
@@ -192,14 +211,14 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    geom, cells, params, desc = _workload(args.workload)
+    geom, cells, params, desc = _workload(args.workload, args.precision)
     nf = wl.fluid_count(geom)
     rate, steps, dt = _oracle_rate(geom, cells, params, args.reference_budget)
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": desc, "fluid_nodes": nf, "cells": len(cells["pos"])},
+        "data": "synthetic", "config": {"workload": desc, "fluid_nodes": nf, "cells": 0 if cells is None else len(cells["pos"])},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{steps} coupled steps of the full workload ({dt:.1f} s), "
                                    f"capped by a {args.reference_budget:.0f} s budget"},
@@ -222,7 +241,9 @@ def run_ours(args):
         B.build()
     _barrier(ws)
     torch.cuda.set_device(local)
-    geom, cells, params, desc = _workload(args.workload)
+    geom, cells, params, desc = _workload(args.workload, args.precision)
+    if args.no_cells and cells is not None:
+        cells, desc = None, desc + ", cells removed"
     nf = wl.fluid_count(geom)
     N = geom["nx"] * geom["ny"] * geom["nz"]
 
@@ -266,7 +287,7 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     s2.close()
     e2e_s = _barrier_and_max(e2e_s, ws)
-    n = len(cells["pos"])
+    n = 0 if cells is None else len(cells["pos"])
     h2d = (0 if geom["solid"] is None else N) + n * (3 + 4 + 3 + 3) * 8
     d2h = N * 8 + N * 3 * 8 + n * 13 * 8
     e2e = {"value": nf * args.steps * ws / e2e_s / 1e6, "unit": UNIT,
@@ -277,10 +298,10 @@ def run_ours(args):
     if rank != 0:
         return
     lb_ms = kms[0] / max(kcount[0], 1)
-    bpn = _algorithmic_bytes_per_node(geom, params)
+    bpn = _algorithmic_bytes_per_node(geom, params, n > 0)
     peak, peak_kind = _peaks()
     achieved = bpn * nf / (lb_ms * 1e-3) / 1e9
-    traffic = _profiled_traffic(args.workload)
+    traffic = _profiled_traffic(args.workload, args.precision)
     roof = {"kernel": "lattice pass (k_lb)", "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_fluid_node": bpn,
@@ -295,7 +316,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "f32" else f"f32 ({args.precision} storage)", "data": "synthetic",
         "config": {"workload": desc, "nodes": N, "fluid_nodes": nf, "cells": n,
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": f"inputs larger than L2: per-step working set "
@@ -308,17 +330,117 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Batched serving of the request stream: solves/s and p50/p99
+    time-to-result of the binary16 request server (continuous batching,
+    Poisson arrivals at 0.8 of its measured capacity) against the plain FP32
+    single-instance path (the same requests one after another through
+    Solver), and the per-request work-rate (effective viscosity) error of
+    binary16 against FP32."""
+    import torch
+
+    from paper_1107_4889_gb300 import build as B
+    from paper_1107_4889_gb300.rbc import Server, Solver
+
+    B.build()
+    torch.cuda.set_device(0)
+    reqs16 = wl.serving_stream(args.serve_requests, precision="f16", step_scale=args.serve_step_scale)
+    n = len(reqs16)
+
+    def serve(reqs, arrivals=None):
+        srv = Server(int(args.serve_arena_gb * 2 ** 30), max_active=args.serve_slots, tick_steps=args.serve_tick)
+        torch.cuda.synchronize()
+        t0 = srv.clock()
+        order = list(range(len(reqs))) if arrivals is None else list(np.argsort(arrivals))
+        k, res = 0, []
+        while True:
+            now = srv.clock() - t0
+            while k < len(order) and (arrivals is None or arrivals[order[k]] <= now):
+                g, c, p, steps, info = reqs[order[k]]
+                srv.submit(g, c, p, steps, steps // 2, tag=int(order[k]))
+                k += 1
+            a, q = srv.poll()
+            res += srv.results()
+            if a == 0 and q == 0 and k == len(order):
+                break
+            if a == 0 and q == 0:
+                time.sleep(1e-4)
+        res += srv.results()
+        makespan = max(r["t_done"] for r in res) - t0
+        srv.close()
+        res.sort(key=lambda r: r["tag"])
+        return res, makespan
+
+    # plain FP32 single instance: the same requests, one after another
+    nseq = min(n, args.serve_baseline_requests)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p32 = []
+    for g, c, p, steps, info in reqs16[:nseq]:
+        s = Solver(g, c, dict(p, precision="f32"))
+        acc = []
+        for done in range(0, steps, args.serve_tick):
+            s.step(min(args.serve_tick, steps - done))
+            st = s.stats()
+            if done + args.serve_tick >= steps // 2:
+                acc.append(st["power"])
+        p32.append(float(np.mean(acc)))
+        s.close()
+    torch.cuda.synchronize()
+    seq_rate = nseq / (time.perf_counter() - t0)
+
+    # closed loop (all submitted at once): capacity of the batched server
+    res_cl, span_cl = serve(reqs16)
+    capacity = n / span_cl
+    # open loop: Poisson arrivals at 0.8 of capacity
+    rng = np.random.default_rng(wl.SEED_BASE + 40)
+    arrivals = np.cumsum(rng.exponential(1.0 / (0.8 * capacity), n))
+    res_ol, span_ol = serve(reqs16, arrivals)
+    ttr = np.array([r["t_done"] - r["t_submit"] for r in res_ol])
+    errs = [abs(res_cl[k]["mean_power"] / p32[k] - 1.0) for k in range(nseq)]
+    fluid = [wl.fluid_count(g) * steps for g, c, p, steps, i in reqs16]
+    line = {
+        "metric": "batched serving solves/s (binary16, continuous batching)", "value": capacity, "unit": "solves/s",
+        "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": f"{n} requests: boxes {list(wl.SERVING_BOXES)}, periodic (Kolmogorov drive) or walled "
+                               f"(uniform drive), hematocrit U[0.1,0.5] (slot-limited), shear rate logU[1e-5,1e-3], "
+                               f"steps U[2000,10000] x {args.serve_step_scale}",
+                   "slots": args.serve_slots, "tick_steps": args.serve_tick},
+        "fp32_single_instance": {"value": seq_rate, "unit": "solves/s", "requests": nseq},
+        "speedup_vs_fp32_single": capacity / seq_rate,
+        "mlups_batched": float(np.sum(fluid)) / span_cl / 1e6,
+        "open_loop": {"arrival_rate": 0.8 * capacity, "p50_s": float(np.percentile(ttr, 50)),
+                      "p99_s": float(np.percentile(ttr, 99)), "makespan_s": span_ol},
+        "viscosity_error_vs_fp32": {"max": float(np.max(errs)), "median": float(np.median(errs)),
+                                    "within_1pct": int(np.sum(np.array(errs) < 0.01)), "of": nseq},
+        "failed": int(sum(r["status"] != 0 for r in res_cl + res_ol)),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["channel", "box32"], default="channel")
+    ap.add_argument("--workload", choices=["channel", "box32", "tube", "box256", "box128"], default="channel")
+    ap.add_argument("--no-cells", action="store_true", help="drop the workload's cells (lattice pass alone)")
+    ap.add_argument("--precision", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--reference-budget", type=float, default=60.0)
+    ap.add_argument("--serve", action="store_true", help="batched-serving benchmark instead of the step benchmark")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-step-scale", type=float, default=0.1)
+    ap.add_argument("--serve-baseline-requests", type=int, default=60)
+    ap.add_argument("--serve-slots", type=int, default=48)
+    ap.add_argument("--serve-tick", type=int, default=100)
+    ap.add_argument("--serve-arena-gb", type=float, default=64.0)
     args = ap.parse_args()
+    if args.serve:
+        run_serve(args)
+        return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":

@@ -48,13 +48,16 @@ extern "C" {
 typedef struct rbc_handle rbc_handle;
 
 /* Geometry of the lattice (Sec. 2.1).  solid: host array of nx*ny*nz bytes,
- * 1 = solid node, NULL = all fluid; copied at init.  body_force: external
- * force density added at every fluid node (lattice units). */
+ * 1 = solid node, NULL = all fluid; copied at init.  The external force
+ * density at a fluid node (x, y, z) is body_force + body_force_wave *
+ * sin(2 pi y / ny) (lattice units): a uniform drive, plus the Kolmogorov
+ * profile that sustains a shear flow in a fully periodic box. */
 typedef struct {
     int nx, ny, nz;
     int periodic[3];
     const uint8_t *solid;
     double body_force[3];
+    double body_force_wave[3];
 } rbc_geometry;
 
 /* Initial cell state (Sec. 2.2: Gamma_i = (R_i, Q_i, V_i, Omega_i)).  Host
@@ -84,6 +87,21 @@ typedef struct {
  *   mach_max            |u| guard of the stability flag [0.3]
  *   bin_capacity        cells per cell-list bin [0 = 32]
  *   max_neighbors       candidate partners kept per cell [0 = 64]
+ *   precision           storage of the populations (the paper does not fix
+ *                       it; Sec. 2.1 keeps f_p per node): RBC_PREC_F32 keeps
+ *                       d_p = f_p - w_p in FP32; RBC_PREC_F16 / RBC_PREC_BF16
+ *                       keep s_p = d_p S / w_p in IEEE binary16 (S = 1024) /
+ *                       bfloat16 (S = 1), halving the population bytes; the
+ *                       collision arithmetic is FP32 in every case [F32]
+ *   rounding            16-bit stores: RBC_ROUND_STOCHASTIC rounds up with
+ *                       probability equal to the fraction of the gap covered
+ *                       (six random bits per value from Philox4x32-10, counter
+ *                       (node, pass, 0), key = seed), which keeps a steady
+ *                       flow unbiased; binary16 then stores values below its
+ *                       normal range (|f_p / w_p - 1| < 6e-8) as zero.
+ *                       RBC_ROUND_NEAREST (ties to even, IEEE) is biased by
+ *                       percents in slow steady flows [stochastic]
+ *   seed                key of the stochastic rounding [0]
  *   stream              cudaStream_t the library works on (NULL: one it
  *                       creates and owns). */
 typedef struct {
@@ -100,12 +118,24 @@ typedef struct {
     double mach_max;
     int bin_capacity;
     int max_neighbors;
+    int precision;
+    int rounding;
+    uint64_t seed;
     void *stream;
 } rbc_params;
 
+#define RBC_PREC_F32 0
+#define RBC_PREC_F16 1
+#define RBC_PREC_BF16 2
+#define RBC_ROUND_STOCHASTIC 0
+#define RBC_ROUND_NEAREST 1
+
 /* Running budgets (Sec. 2.2 conservation claims).  mass and p_fluid are the
  * zeroth and first moments of the stored populations over fluid nodes;
- * p_cells = sum_i M V_i; max_u = max |u| of the last lattice pass. */
+ * p_cells = sum_i M V_i; max_u = max |u| of the last lattice pass; power =
+ * sum over fluid nodes of G_ext(x) . u(x), the work rate of the external
+ * force on the velocity of the last pass (at a fixed drive it is inversely
+ * proportional to the effective viscosity of the suspension). */
 typedef struct {
     int64_t step;
     double mass;
@@ -115,6 +145,7 @@ typedef struct {
     int64_t gb_clamps;
     int32_t unstable;
     int32_t overflow; /* bit 0 bin, bit 1 neighbour list, bit 2 shape box */
+    double power;
 } rbc_stats_t;
 
 /* Fill *p with the paper's parameters (values above) and a NULL stream. */
@@ -125,7 +156,7 @@ void rbc_default_params(rbc_params *p);
 int rbc_workspace_size(const rbc_geometry *geom, const rbc_cells *cells,
                        const rbc_params *params, size_t *bytes);
 
-/* Validate the problem, carve the caller's device workspace (at least
+/* Validate the problem (at most 2^32 / 19 lattice nodes), carve the caller's device workspace (at least
  * rbc_workspace_size bytes, 256-byte aligned, owned by the caller and kept
  * alive until rbc_free), copy geometry and cells to the device, set the
  * fluid at rest (f = f^eq(rho = 1, u = 0)), capture one step as CUDA graphs
@@ -178,6 +209,23 @@ int rbc_neighbors(rbc_handle *h, int *counts, int *lists, int max_per_cell);
 int rbc_set_timing(rbc_handle *h, int capacity);
 int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2]);
 
+/* Autotuner of the lattice pass's launch shape (tiles per SM).  The
+ * row-staged pass is persistent: its grid is CTAs-per-SM x SMs, each CTA
+ * holding a ring of `stages` shared-memory buffers.  Without tuning the
+ * runtime picks the shape from a cost model (fewest idle CTA slots in the
+ * last wave; at most 2 CTAs per SM when cells run beside the pass).
+ * rbc_autotune times every shape that fits (ring depth 2..4 x 1..4 CTAs per
+ * SM) over steps_per_trial coupled steps after as many warm-up steps, keeps
+ * the fastest and re-captures the step graphs.  The trial steps are ordinary
+ * steps of the solve (the state advances).  Synchronises.  out may be NULL. */
+typedef struct {
+    int stages, ctas_per_sm;     /* chosen shape (0, 0: the one-thread-per-node pass, nothing to tune) */
+    double ms_per_step;          /* its time per coupled step */
+    double default_ms_per_step;  /* time per step of the cost model's shape */
+    int trials;                  /* shapes timed */
+} rbc_tune_report;
+int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out);
+
 /* Kernel launches one rbc_step(h, 1) enqueues. */
 int rbc_launches_per_step(const rbc_handle *h);
 
@@ -209,6 +257,75 @@ int rbc_launches_per_step(const rbc_handle *h);
  * describes failures. */
 int rbc_neighbors_noalloc(const double *pos, int n, int nx, int ny, int nz, const int periodic[3],
                           double r_cut, int *counts, int *lists, int max_per_cell, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Request server: continuous batching of independent solves.
+ *
+ * Not a step of the paper's method: it serves many rheology / vessel solves
+ * (the use Sec. 4 puts the model to) on one GPU.  Requests of different box
+ * sizes, hematocrits and drives are queued, admitted as device memory and
+ * slots free up, and advanced concurrently, each on its own stream in ticks
+ * of tick_steps steps captured as one CUDA graph (coupled steps followed by
+ * the budget reduction, which accumulates the time averages on the device).
+ * Device memory comes from one arena the caller lends: each admitted solve
+ * takes rbc_workspace_size bytes of it (first fit) and returns them when it
+ * finishes.  Results are the time-averaged budgets of each solve.
+ * ------------------------------------------------------------------------ */
+typedef struct rbc_server rbc_server;
+
+typedef struct {
+    rbc_geometry geom;     /* copied at submit */
+    rbc_cells cells;       /* copied at submit */
+    rbc_params params;     /* copied; params.stream is ignored (the server assigns one) */
+    int64_t steps;         /* coupled steps to run (>= 1) */
+    int64_t average_from;  /* samples (one per tick) at pass counts >= this are averaged */
+    uint64_t tag;          /* caller's identifier, returned in the result */
+} rbc_request;
+
+typedef struct {
+    uint64_t tag;
+    int32_t status;        /* RBC_OK or the error that ended the solve */
+    int32_t pad;
+    int64_t steps;         /* coupled steps run */
+    int64_t samples;       /* samples in the averages */
+    double mean_power;     /* time average of rbc_stats_t.power */
+    double mean_p_fluid[3];
+    double max_u;          /* largest max |u| over the samples */
+    double t_submit, t_admit, t_done;  /* server clock (s since rbc_server_create) */
+    uint64_t workspace_bytes;
+} rbc_result;
+
+/* Create a server on the current device.  arena: device memory (256-byte
+ * aligned, caller-owned, kept alive until rbc_server_free) that the solves'
+ * workspaces are carved from; max_active: solves advanced at once (1..256);
+ * tick_steps: steps per launched tick (even, 2..100000).  The server creates
+ * max_active streams. */
+int rbc_server_create(void *arena, size_t arena_bytes, int max_active, int tick_steps, rbc_server **out);
+
+/* Validate and queue a request (inputs copied).  RBC_EINVAL for an invalid
+ * problem, RBC_ENOMEM if its workspace exceeds the whole arena. */
+int rbc_server_submit(rbc_server *s, const rbc_request *r);
+
+/* One non-blocking round: retire finished ticks, finish solves that are
+ * done (their results become available), launch further ticks (at most two
+ * in flight per solve), and admit queued requests in arrival order while a
+ * slot and an arena block are free (requests that do not fit yet are passed
+ * over by later ones).  Admission runs rbc_init, which synchronises only the
+ * new solve's stream.  *active, *queued (may be NULL) receive the counts.
+ * Returns the first error of a server-level CUDA call; errors of one solve
+ * end that solve and go into its result. */
+int rbc_server_poll(rbc_server *s, int *active, int *queued);
+
+/* Move up to max finished results into out (oldest first); *n receives the
+ * number written. */
+int rbc_server_results(rbc_server *s, rbc_result *out, int max, int *n);
+
+/* Seconds on the server clock. */
+double rbc_server_clock(const rbc_server *s);
+
+/* Finish or abandon all work, release every solve, stream and event (not
+ * the arena).  NULL is ignored. */
+void rbc_server_free(rbc_server *s);
 
 /* Release the handle, its graphs, events and owned stream (not the caller's
  * workspace).  NULL is ignored. */

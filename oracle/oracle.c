@@ -32,6 +32,9 @@
  *      (Eqs. dens, vel) and stress (Eq. stresstensorLB).
  */
 #include <math.h>
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -253,7 +256,9 @@ double orc_round_storage(int kind, double v)
 /* Stochastic rounding with `bits` random bits r: |v| lies between the format
  * values a <= |v| < a + q; the result is a + q when
  * (|v| - a)/q + (r + 1/2)/2^bits >= 1, else a, with the sign of v,
- * saturated at the largest finite value. */
+ * saturated at the largest finite value.  binary16 stores values below its
+ * normal range (|v| < 2^-14, i.e. |f_p / w_p - 1| < 6e-8 after scaling) as
+ * zero. */
 double orc_round_storage_sr(int kind, double v, unsigned r, int bits)
 {
     if (kind == ORC_STORE_EXACT || v == 0.0 || !isfinite(v)) return v;
@@ -261,6 +266,7 @@ double orc_round_storage_sr(int kind, double v, unsigned r, int bits)
     double vmax;
     format_of(kind, &mant, &emin, &vmax);
     double m = fabs(v);
+    if (kind == ORC_STORE_F16 && m < ldexp(1.0, emin)) return 0.0;
     double q = quantum(m, mant, emin);
     double t = m / q, fl = floor(t);
     double thr = ((double)r + 0.5) / ldexp(1.0, bits);
@@ -798,7 +804,7 @@ struct orc_state {
     int nx, ny, nz, per[3];
     long N;
     unsigned char *solid;
-    double gext[3];
+    double gext[3], gwave[3];
     double tau0, delta, kappa, gT, gR, alpha, eps0, xi[3], a[3], M, I[3];
     double smin_w, r_w, rho_floor, rc, rcw;
     double *f, *rho, *U, *S, *G, *theta, *tau;
@@ -827,6 +833,7 @@ orc_state *orc_create(const orc_config *c)
     if (c->solid) memcpy(s->solid, c->solid, (size_t)s->N);
     for (int a = 0; a < 3; a++) {
         s->gext[a] = c->body_force[a];
+        s->gwave[a] = c->body_force_wave[a];
         s->xi[a] = c->xi[a];
         s->a[a] = c->semi_axes[a];
         s->I[a] = c->inertia[a];
@@ -1008,6 +1015,16 @@ static void QT_vec(const double Q[9], const double v[3], double r[3])
     for (int a = 0; a < 3; a++) r[a] = Q[0 * 3 + a] * v[0] + Q[1 * 3 + a] * v[1] + Q[2 * 3 + a] * v[2];
 }
 
+/* External force density at fluid node n: uniform part plus the
+ * Kolmogorov wave A sin(2 pi y / ny) (the driver of a shear flow in a
+ * periodic box, reading "G_ext on fluid nodes only"). */
+static void external_force(const orc_state *s, long n, double g[3])
+{
+    long y = (n / s->nx) % s->ny;
+    double sw = sin(2.0 * M_PI * (double)y / (double)s->ny);
+    for (int a = 0; a < 3; a++) g[a] = s->gext[a] + s->gwave[a] * sw;
+}
+
 void orc_step(orc_state *s, long nsteps)
 {
     const int nx = s->nx, ny = s->ny, nz = s->nz;
@@ -1090,7 +1107,9 @@ void orc_step(orc_state *s, long nsteps)
                 s->tau[n] = s->tau0;
                 continue;
             }
-            for (int a = 0; a < 3; a++) s->G[3 * n + a] += s->gext[a];
+            double gx[3];
+            external_force(s, n, gx);
+            for (int a = 0; a < 3; a++) s->G[3 * n + a] += gx[a];
             /* Eq. enhance-viscosity with h = 1 */
             s->tau[n] = s->tau0 + s->delta * H_STEP * s->theta[n];
         }
@@ -1179,11 +1198,19 @@ void orc_budget(const orc_state *s, double *out)
     }
     for (int i = 0; i < s->nc; i++)
         for (int a = 0; a < 3; a++) Pc[a] += s->M * s->V[3 * i + a];
+    double W = 0.0;
+    for (long n = 0; n < s->N; n++) {
+        if (s->solid[n]) continue;
+        double g[3];
+        external_force(s, n, g);
+        for (int a = 0; a < 3; a++) W += g[a] * s->U[3 * n + a];
+    }
     out[0] = m;
     for (int a = 0; a < 3; a++) {
         out[1 + a] = P[a];
         out[4 + a] = Pc[a];
     }
+    out[7] = W;
 }
 
 long orc_neighbor_pairs(const orc_state *s, int *pairs, long max)

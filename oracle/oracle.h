@@ -44,6 +44,7 @@ typedef struct {
     int storage;      /* population storage: ORC_STORE_EXACT, _F16 or _BF16 */
     int stochastic;   /* 16-bit storage: 1 = stochastic rounding, 0 = to nearest */
     unsigned long long seed;  /* key of the stochastic rounding's random numbers */
+    double body_force_wave[3];  /* amplitude of a force density A sin(2 pi y / ny) on fluid nodes */
 } orc_config;
 
 /* Population storage of the reduced-precision variants: FP64 (exact), or the
@@ -69,7 +70,9 @@ void orc_cells(const orc_state *s, double *out);
 /* Per cell 21 doubles of the last step: F_mech(3) tau_mech_lab(3) u~(3)
  * omega~(3) T^S(3) J(3) L(3). */
 void orc_diag(const orc_state *s, double *out);
-/* mass, P_fluid(3), P_cells(3) of the current state. */
+/* mass, P_fluid(3), P_cells(3) of the current state and the work rate of
+ * the external force, sum over fluid nodes of G_ext(x) . u(x) with u of the
+ * last lattice pass (8 doubles). */
 void orc_budget(const orc_state *s, double *out);
 long orc_clamps(const orc_state *s);
 /* Cell pairs i<j with |R_ij|^2 < r_cut^2 at the current positions, by brute

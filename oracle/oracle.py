@@ -47,6 +47,7 @@ class _Config(ctypes.Structure):
         ("pos", _D), ("quat", _D), ("vel", _D), ("omega", _D),
         ("storage", ctypes.c_int), ("stochastic", ctypes.c_int),
         ("seed", ctypes.c_ulonglong),
+        ("body_force_wave", ctypes.c_double * 3),
     ]
 
 
@@ -304,6 +305,7 @@ class Oracle:
         for a in range(3):
             c.periodic[a] = int(geometry.get("periodic", (1, 1, 1))[a])
             c.body_force[a] = float(geometry.get("body_force", (0.0, 0.0, 0.0))[a])
+            c.body_force_wave[a] = float(geometry.get("body_force_wave", (0.0, 0.0, 0.0))[a])
             c.xi[a] = float(params["xi"][a])
             c.semi_axes[a] = float(params["semi_axes"][a])
             c.inertia[a] = float(params["inertia"][a])
@@ -380,9 +382,9 @@ class Oracle:
                     T_S=out[:, 12:15], J=out[:, 15:18], L=out[:, 18:21])
 
     def budget(self):
-        out = np.zeros(7)
+        out = np.zeros(8)
         lib().orc_budget(self._h, _dp(out))
-        return dict(mass=out[0], p_fluid=out[1:4].copy(), p_cells=out[4:7].copy())
+        return dict(mass=out[0], p_fluid=out[1:4].copy(), p_cells=out[4:7].copy(), power=out[7])
 
     def neighbor_pairs(self):
         cap = max(16, self.n * 64)

@@ -16,10 +16,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "librbc.so")
-SOURCES = ["api.cu", "lb.cu", "cells.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "lb.cu", "cells.cu", "noalloc.cu", "serve.cu"]
 HEADERS = ["internal.h", "rbc_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-Xcompiler", "-pthread",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 
@@ -59,7 +59,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
                     raise RuntimeError(f"nvcc failed: {' '.join(j)}")
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+        r = subprocess.run([nvcc(), *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs],
+                           capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("nvcc link failed")

@@ -11,6 +11,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -31,6 +33,8 @@ struct Problem {
     int per[3];
     bool any_solid;
     int nc;
+    int prec, stochastic;
+    unsigned long long seed;
     Params p;
     int nb[3], nbins, bin_cap, max_nbr;
     double bin_size[3];
@@ -81,6 +85,8 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     P.nz = g->nz;
     P.N = (int)N;
     P.Np = (N + 63) / 64 * 64;
+    // the lattice pass addresses the 19 population planes with 32-bit offsets
+    if (19LL * P.Np >= (1LL << 32)) return fail(err, RBC_EINVAL, "lattice too large (19 * nodes must stay below 2^32)");
     for (int a = 0; a < 3; ++a) P.per[a] = g->periodic[a] ? 1 : 0;
     P.any_solid = false;
     if (g->solid) {
@@ -121,14 +127,26 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     if (!(q.gamma_T >= 0.0) || !(q.gamma_R >= 0.0) || !(q.eps0 >= 0.0))
         return fail(err, RBC_EINVAL, "gamma_T, gamma_R, eps0 must be >= 0");
     if (!(q.sigma_min_wall > 0.0) || !(q.wall_radius >= 0.0)) return fail(err, RBC_EINVAL, "bad wall particle");
+    if (q.precision < RBC_PREC_F32 || q.precision > RBC_PREC_BF16)
+        return fail(err, RBC_EINVAL, "precision must be RBC_PREC_F32, RBC_PREC_F16 or RBC_PREC_BF16");
+    if (q.rounding != RBC_ROUND_STOCHASTIC && q.rounding != RBC_ROUND_NEAREST)
+        return fail(err, RBC_EINVAL, "rounding must be RBC_ROUND_STOCHASTIC or RBC_ROUND_NEAREST");
+    P.prec = q.precision;
+    P.stochastic = q.rounding == RBC_ROUND_STOCHASTIC ? 1 : 0;
+    P.seed = (unsigned long long)q.seed;
     const int nc = c ? c->n : 0;
     if (nc < 0) return fail(err, RBC_EINVAL, "negative cell count");
     if (nc > 0 && (!c->pos || !c->quat)) return fail(err, RBC_EINVAL, "cell positions and quaternions are required");
     P.nc = nc;
 
     Params &p = P.p;
+    p.wave = 0;
     for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(g->body_force[a]) || !std::isfinite(g->body_force_wave[a]))
+            return fail(err, RBC_EINVAL, "non-finite body force");
         p.gext[a] = (float)g->body_force[a];
+        p.gwave[a] = (float)g->body_force_wave[a];
+        if (g->body_force_wave[a] != 0.0) p.wave = 1;
         p.xi[a] = (float)q.xi[a];
         p.a2[a] = q.semi_axes[a] * q.semi_axes[a];
         p.I[a] = q.inertia[a];
@@ -215,7 +233,7 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
         for (int z = 0; z < P.nz; ++z)
             for (int y = 0; y < P.ny; ++y)
                 for (int x = 0; x < P.nx; ++x) {
-                    if (!g->solid[node(P, x, y, z)]) continue;
+                    if (!g->solid[(long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z)]) continue;
                     bool wet = false;
                     for (int dz = -1; dz <= 1 && !wet; ++dz)
                         for (int dy = -1; dy <= 1 && !wet; ++dy)
@@ -259,8 +277,11 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.N = P.N;
     d.Np = P.Np;
     d.walls = P.any_solid ? 1 : 0;
-    d.pops[0] = cv.take<float>(19 * Np);
-    d.pops[1] = cv.take<float>(19 * Np);
+    d.prec = P.prec;
+    d.stochastic = P.stochastic;
+    d.seed = P.seed;
+    d.pops[0] = cv.take<uint8_t>(19 * Np * (size_t)pop_bytes(P.prec));
+    d.pops[1] = cv.take<uint8_t>(19 * Np * (size_t)pop_bytes(P.prec));
     d.U = cv.take<float>(3 * Np);
     d.S = (P.nc > 0 && q->alpha_tt != 0.0) ? cv.take<float>(6 * Np) : nullptr;
     d.G = P.nc > 0 ? cv.take<float>(3 * Np) : nullptr;
@@ -311,18 +332,33 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.wall_xyz = cv.take<int>(3 * (size_t)std::max(P.nw, 1));
     d.flags = cv.take<int>(8);
     d.lb_work = cv.take<int>(2);
+    d.lb_step = cv.take<unsigned long long>(1);
     d.clamps = cv.take<unsigned long long>(1);
     d.budget_blocks = P.budget_blocks;
     d.budget_part = cv.take<double>(8 * (size_t)P.budget_blocks);
     d.budget_out = cv.take<double>(16);
+    d.accum = cv.take<double>(8);
     return (cv.off + 255) & ~size_t(255);
 }
 
 }  // namespace
 
 namespace rbc {
+void raise_smem_limit(const void *func, int bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> limit;  // (device, kernel) -> limit set
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    int &cur = limit[std::make_pair(dev, func)];
+    if (bytes <= cur) return;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess) cur = bytes;
+}
+
 // lets other translation units report through rbc_last_error(NULL)
 void set_thread_error(const std::string &msg) { g_thread_err = msg; }
+void set_thread_error(const char *msg) { g_thread_err = msg; }
 }  // namespace rbc
 
 struct rbc_handle {
@@ -413,18 +449,59 @@ static void body_step(rbc_handle *h, int parity)
         cudaStreamWaitEvent(h->side, h->fork_ev, 0);
         cudaStreamWaitEvent(h->side2, h->fork_ev, 0);
     }
-    launch_lb(h->d, h->P.p, parity, h->stream);
-    cudaEventRecordWithFlags(h->ev_dummy[2], h->stream, cudaEventRecordExternal);
+    // the side kernels go into the graph first: their blocks are then
+    // dispatched before the persistent lattice pass fills the SMs
     if (cells) {
         launch_weights(h->d, h->P.p, parity ^ 1, h->side2);
         launch_bin(h->d, h->P.p, h->side);
         launch_gb(h->d, h->P.p, h->side);
+    }
+    launch_lb(h->d, h->P.p, parity, h->stream);
+    cudaEventRecordWithFlags(h->ev_dummy[2], h->stream, cudaEventRecordExternal);
+    if (cells) {
         cudaEventRecord(h->join_ev, h->side);
         cudaEventRecord(h->join2_ev, h->side2);
         cudaStreamWaitEvent(h->stream, h->join_ev, 0);
         cudaStreamWaitEvent(h->stream, h->join2_ev, 0);
     }
 }
+
+namespace rbc {
+
+// Serving: `steps` coupled steps from the handle's current step, then the
+// budget reduction, which adds to the handle's time-average sums once the
+// pass counter has reached average_from; captured as one graph (launched
+// on the handle's stream by the request server).
+static thread_local int g_tick_steps = 0;
+static thread_local long long g_tick_from = 0;
+static void body_ticks(rbc_handle *h, int start_parity)
+{
+    for (int k = 0; k < g_tick_steps; ++k) body_step(h, (start_parity + k) & 1);
+    launch_budget(h->d, h->P.p, (start_parity + g_tick_steps) & 1, h->stream, true, g_tick_from);
+}
+
+int capture_ticks(rbc_handle *h, int64_t steps, long long average_from, cudaGraphExec_t *out)
+{
+    if (steps <= 0 || steps > (1 << 20)) return fail(&h->err, RBC_EINVAL, "tick length out of range");
+    g_tick_steps = (int)steps;
+    g_tick_from = average_from;
+    cudaGraph_t keep = nullptr;
+    const int rc = capture(h, body_ticks, (int)(h->step & 1), out, nullptr, &keep);
+    if (keep) cudaGraphDestroy(keep);
+    return rc;
+}
+
+void advance_steps(rbc_handle *h, int64_t steps) { h->step += steps; }
+
+int read_accum(rbc_handle *h, double accum[8], int flags[8])
+{
+    RBC_CU(cudaMemcpyAsync(accum, h->d.accum, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    RBC_CU(cudaMemcpyAsync(flags, h->d.flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    RBC_CU(cudaStreamSynchronize(h->stream));
+    return RBC_OK;
+}
+
+}  // namespace rbc
 
 extern "C" {
 
@@ -504,8 +581,9 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
         cudaStream_t s = h->stream;
         const size_t Np = (size_t)P.Np;
         // fluid at rest: f = w_p, i.e. zero deviations; fields zero
-        RBC_CU(cudaMemsetAsync(d.pops[0], 0, 19 * Np * sizeof(float), s));
-        RBC_CU(cudaMemsetAsync(d.pops[1], 0, 19 * Np * sizeof(float), s));
+        // (zero bits are a zero deviation in every storage format)
+        RBC_CU(cudaMemsetAsync(d.pops[0], 0, 19 * Np * pop_bytes(d.prec), s));
+        RBC_CU(cudaMemsetAsync(d.pops[1], 0, 19 * Np * pop_bytes(d.prec), s));
         RBC_CU(cudaMemsetAsync(d.U, 0, 3 * Np * sizeof(float), s));
         if (d.S) RBC_CU(cudaMemsetAsync(d.S, 0, 6 * Np * sizeof(float), s));
         if (d.G) RBC_CU(cudaMemsetAsync(d.G, 0, 3 * Np * sizeof(float), s));
@@ -517,20 +595,23 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
             RBC_CU(cudaMemcpyAsync(d.solid, geom->solid, (size_t)P.N, cudaMemcpyHostToDevice, s));
             // per-node link mask in the library's velocity ordering: bit p set
             // when the downstream node x + c_p is solid, bit 31 when x is solid
+            // (set from the solid nodes: node m = s - c_p has x + c_p = s)
             links.assign((size_t)P.N, 0u);
             for (int z = 0; z < P.nz; ++z)
-                for (int y = 0; y < P.ny; ++y)
+                for (int y = 0; y < P.ny; ++y) {
+                    const long long row = (long long)P.nx * ((long long)y + (long long)P.ny * z);
                     for (int x = 0; x < P.nx; ++x) {
-                        const long long n = node(P, x, y, z);
-                        uint32_t m = geom->solid[n] ? (1u << 31) : 0u;
-                        for (int p = 1; p < kQ; ++p)
-                            if (geom->solid[node(P, x + cx(p), y + cy(p), z + cz(p))]) m |= 1u << p;
-                        links[n] = m;
+                        if (!geom->solid[row + x]) continue;
+                        links[row + x] |= 1u << 31;
+                        for (int p = 1; p < kQ; ++p) links[node(P, x - cx(p), y - cy(p), z - cz(p))] |= 1u << p;
                     }
+                }
             RBC_CU(cudaMemcpyAsync(d.links, links.data(), links.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
         }
         RBC_CU(cudaMemsetAsync(d.flags, 0, 8 * sizeof(int), s));
         RBC_CU(cudaMemsetAsync(d.lb_work, 0, 2 * sizeof(int), s));
+        RBC_CU(cudaMemsetAsync(d.lb_step, 0, sizeof(unsigned long long), s));
+        RBC_CU(cudaMemsetAsync(d.accum, 0, 8 * sizeof(double), s));
         RBC_CU(cudaMemsetAsync(d.clamps, 0, sizeof(unsigned long long), s));
         const int n = P.nc;
         if (n > 0) {
@@ -704,6 +785,7 @@ int rbc_stats(rbc_handle *h, rbc_stats_t *out)
     out->gb_clamps = (int64_t)cl;
     out->unstable = flags[FLAG_UNSTABLE] != 0 || b[5] > 0.0;
     out->overflow = flags[FLAG_OVERFLOW];
+    out->power = b[9];
     if (out->overflow) return fail(&h->err, RBC_ENOMEM, "a device capacity was exceeded");
     if (out->unstable) return fail(&h->err, RBC_EUNSTABLE, "NaN or |u| above the Mach guard");
     return RBC_OK;
@@ -777,6 +859,95 @@ int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2])
     h->timing_used = 0;
     h->timing_cap = 0;
     return RBC_OK;
+}
+
+// Re-capture both step graphs (after a change of launch shape).
+static int recapture_steps(rbc_handle *h)
+{
+    RBC_CU(cudaStreamSynchronize(h->stream));
+    for (int par = 0; par < 2; ++par) {
+        if (h->g_step[par]) cudaGraphExecDestroy(h->g_step[par]);
+        if (h->src[par]) cudaGraphDestroy(h->src[par]);
+        h->g_step[par] = nullptr;
+        h->src[par] = nullptr;
+        int r = capture(h, body_step, par, &h->g_step[par], h->ev_node[par], &h->src[par]);
+        if (r != RBC_OK) return r;
+    }
+    return RBC_OK;
+}
+
+// ms per coupled step over n steps after n warm-up steps (CUDA events on the
+// handle's stream).
+static int time_steps(rbc_handle *h, int n, double *ms)
+{
+    int rc = rbc_step(h, n);
+    if (rc != RBC_OK) return rc;
+    cudaEvent_t a, b;
+    RBC_CU(cudaEventCreate(&a));
+    RBC_CU(cudaEventCreate(&b));
+    cudaEventRecord(a, h->stream);
+    rc = rbc_step(h, n);
+    cudaEventRecord(b, h->stream);
+    cudaError_t e = cudaEventSynchronize(b);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return fail(&h->err, RBC_ECUDA, std::string("timing: ") + cudaGetErrorString(e));
+    *ms = (double)t / n;
+    return rc;
+}
+
+int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out)
+{
+    if (!h || steps_per_trial < 1) return fail(h ? &h->err : nullptr, RBC_EINVAL, "bad argument");
+    rbc_tune_report rep;
+    std::memset(&rep, 0, sizeof rep);
+    if (h->timing_used < h->timing_cap) return fail(&h->err, RBC_EINVAL, "kernel timing is active");
+    const int st0 = h->d.lb_stages, grid0 = h->d.lb_grid;
+    const size_t smem0 = h->d.lb_smem;
+    if (grid0 <= 0) {
+        int rc = time_steps(h, steps_per_trial, &rep.ms_per_step);
+        rep.default_ms_per_step = rep.ms_per_step;
+        if (out) *out = rep;
+        return rc;
+    }
+    int rc = time_steps(h, steps_per_trial, &rep.default_ms_per_step);
+    if (rc != RBC_OK) return rc;
+    int stages[16], ctas[16];
+    const int n = lb_shapes(h->d, stages, ctas, 16);
+    double best = rep.default_ms_per_step;
+    int best_k = -1;
+    for (int k = 0; k < n; ++k) {
+        set_lb_shape(h->d, stages[k], ctas[k]);
+        rc = recapture_steps(h);
+        double ms = 0.0;
+        if (rc == RBC_OK) rc = time_steps(h, steps_per_trial, &ms);
+        if (rc != RBC_OK) return rc;
+        rep.trials++;
+        if (ms < best) {
+            best = ms;
+            best_k = k;
+        }
+    }
+    if (best_k >= 0) {
+        set_lb_shape(h->d, stages[best_k], ctas[best_k]);
+        rep.stages = stages[best_k];
+        rep.ctas_per_sm = ctas[best_k];
+    } else {
+        h->d.lb_stages = st0;
+        h->d.lb_grid = grid0;
+        h->d.lb_smem = smem0;
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        rep.stages = st0;
+        rep.ctas_per_sm = (grid0 + sms - 1) / sms;
+    }
+    rep.ms_per_step = best;
+    rc = recapture_steps(h);
+    if (out) *out = rep;
+    return rc;
 }
 
 int rbc_launches_per_step(const rbc_handle *h)

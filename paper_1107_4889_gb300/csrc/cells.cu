@@ -1149,7 +1149,7 @@ size_t cells_smem_bytes(const Params &p)
 
 void prepare_cells(const Params &p)
 {
-    cudaFuncSetAttribute(k_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cells_smem_bytes(p));
+    raise_smem_limit((const void *)k_weights, (int)cells_smem_bytes(p));
     cudaFuncSetAttribute(k_weights, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 }
 

@@ -6,7 +6,11 @@
 #include <stddef.h>
 #include <stdint.h>
 
+struct rbc_handle;
+
 namespace rbc {
+
+using rbc_handle_t = ::rbc_handle;
 
 // Per-cell shape header (floats; integer fields stored bit-cast):
 // Q[9] body->lab, base[3] = box origin - R, origin[3], dims[3], centre node, ok.
@@ -16,12 +20,19 @@ constexpr int kHdrWords = 20;
 enum { FLAG_UNSTABLE = 0, FLAG_OVERFLOW = 1, FLAG_TIMEOUT = 2 };
 enum { OVF_BIN = 1, OVF_NBR = 2, OVF_BOX = 4 };
 
+// Population storage (values of rbc_params.precision).
+enum { PREC_F32 = 0, PREC_F16 = 1, PREC_BF16 = 2 };
+
 struct Dev {
     // lattice: planes of Np floats (N rounded up to 64), node n = x + nx*(y + ny*z)
     int nx, ny, nz, N;
     long long Np;
     int walls;          // any solid node
-    float *pops[2];     // 19 planes: deviations d_p = f_p - w_p of post-collision populations
+    // 19 planes of post-collision populations: FP32 deviations d_p = f_p - w_p
+    // (PREC_F32), or d_p / w_p scaled and rounded to binary16 / bfloat16
+    int prec, stochastic;
+    unsigned long long seed;  // key of the stochastic rounding's random numbers
+    void *pops[2];
     float *U;           // 3 planes: velocity of the last lattice pass
     float *S;           // 6 planes (xx yy zz xy xz yz): stress of the last pass, or null
     float *G;           // 3 planes: force density accumulated by the cells (zeroed by the pass)
@@ -62,17 +73,21 @@ struct Dev {
     int *flags;                     // 8 ints
     unsigned long long *clamps;     // 1
     double *budget_part;            // budget_blocks * 8
-    double *budget_out;             // 16: mass, p_fluid(3), max|u|, NaN count, p_cells(3)
+    double *budget_out;             // 16: mass, p_fluid(3), max|u|, NaN count, p_cells(3), work rate
+    double *accum;                  // 8: time-average sums of a served solve (k_budget_final)
     int budget_blocks;
     // lattice pass launch: grid of the row-staged kernel (0: one thread per node)
     int lb_grid, lb_stages;
     int *lb_work;  // lattice-pass batch counter and finished-CTA count (zero between launches)
+    unsigned long long *lb_step;  // lattice passes done (advanced by the pass itself)
     int side_prio;  // launch priority of the side-stream kernels (the device's highest)
     size_t lb_smem;
 };
 
 struct Params {
     float gext[3];
+    float gwave[3];  // amplitude of the force profile sin(2 pi y / ny)
+    int wave;        // gwave != 0
     float tau0, delta, kappa, alpha;
     float mach2;
     float xi[3];
@@ -85,11 +100,20 @@ struct Params {
     int box_dim;  // largest shape box edge (nodes)
 };
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (never
+// lowers it: solves of different shapes may launch the same kernel from
+// several threads).
+void raise_smem_limit(const void *func, int bytes);
+
 // lb.cu
+int pop_bytes(int prec);  // bytes of one stored population
 void prepare_lb(Dev &d);
+int lb_shapes(const Dev &d, int *stages, int *ctas_per_sm, int max);  // staged-pass shapes to try
+void set_lb_shape(Dev &d, int stages, int ctas_per_sm);
 void launch_lb(const Dev &d, const Params &p, int parity, cudaStream_t s);
 void launch_rho(const Dev &d, int parity, cudaStream_t s);
-void launch_budget(const Dev &d, const Params &p, int parity, cudaStream_t s);
+void launch_budget(const Dev &d, const Params &p, int parity, cudaStream_t s, bool accumulate = false,
+                   long long from = 0);
 int budget_blocks_for(int N);
 
 // cells.cu
@@ -99,5 +123,11 @@ void launch_weights(const Dev &d, const Params &p, int buf, cudaStream_t s);
 void launch_cells(const Dev &d, const Params &p, int buf, cudaStream_t s);
 size_t cells_smem_bytes(const Params &p);
 void prepare_cells(const Params &p);
+
+// api.cu, for the request server (serve.cu)
+int capture_ticks(rbc_handle_t *h, int64_t steps, long long average_from, cudaGraphExec_t *out);
+void advance_steps(rbc_handle_t *h, int64_t steps);
+int read_accum(rbc_handle_t *h, double accum[8], int flags[8]);
+void set_thread_error(const char *msg);
 
 }  // namespace rbc

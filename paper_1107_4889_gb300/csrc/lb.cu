@@ -1,15 +1,23 @@
 // lb.cu -- the fused D3Q19 lattice pass and the lattice reductions.
 //
-// One thread per lattice node.  Populations are stored as FP32 deviations
-// d_p = f_p - w_p from the lattice weights, one plane of Np floats per speed
-// (x fastest), ping-ponged between two buffers.  The pass pulls the 19
-// post-collision deviations of the previous pass from the upstream nodes
-// (halfway bounce-back from solid upstream nodes), reads and clears the force
-// density and the smoothed hematocrit the cells spread, collides, stores the
-// 19 new deviations to its own node and writes u and sigma for the cells to
-// sample.  Bytes per fluid node: 76 read + 76 write (populations), 16 read
-// (G, theta), 12 written (u), 24 written (sigma when alpha != 0), 4 read
-// (link mask, walled lattices only), plus the 16-byte clear of G and theta.
+// One thread per lattice node.  Populations are stored as deviations
+// d_p = f_p - w_p from the lattice weights, one plane of Np values per speed
+// (x fastest), ping-ponged between two buffers: FP32 d_p, or in 16 bits
+// (IEEE binary16 or bfloat16) the scaled deviation s_p = d_p S / w_p,
+// rounded stochastically (or to nearest) on store; the collision is FP32
+// either way.  The pass pulls the 19 post-collision values of the previous
+// pass from the upstream nodes (halfway bounce-back from solid upstream
+// nodes), reads and clears the force density and the smoothed hematocrit the
+// cells spread, collides, stores the 19 new values to its own node and
+// writes u and sigma for the cells to sample.  Bytes per fluid node with
+// populations of e bytes: 19 e read + 19 e write, 16 read (G, theta), 12
+// written (u), 24 written (sigma when alpha != 0), 4 read (link mask, walled
+// lattices only), plus the 16-byte clear of G and theta.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "internal.h"
 #include "rbc_device.cuh"
 
@@ -27,16 +35,139 @@ __constant__ int kOppTab[kQ] = {opp(0),  opp(1),  opp(2),  opp(3),  opp(4),  opp
 __device__ __forceinline__ int wrapm(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 struct LbArgs {
-    const float *src;
-    float *dst;
+    const void *src;  // populations of the previous pass (storage type St)
+    void *dst;
     const uint32_t *links;
     float *G, *th, *U, *S;
     int *flags;
-    int *work;  // [0] next batch, [1] CTAs done; both zero at launch, reset by the last CTA
+    int *work;                 // [0] next batch, [1] CTAs done; zero at launch, reset by the last CTA
+    unsigned long long *step;  // passes done: the counter of the rounding's random numbers
     int nx, ny, nz, N;
     long long Np;
     float gx0, gy0, gz0, tau0, delta, mach2;
+    float wx, wy, wz;  // amplitude of the external force profile sin(2 pi y / ny)
+    int wave;
+    uint32_t key0, key1;  // seed of the stochastic rounding
+    int stochastic;
 };
+
+// ---------------------------------------------------------------------------
+// Population storage.  FP32 keeps d_p itself.  The 16-bit formats keep
+// s_p = d_p S / w_p: dividing by w_p gives every speed the same range
+// (s_p / S = f_p / w_p - 1); binary16 takes S = 2^10, which keeps it out of
+// its subnormal range down to |f_p / w_p - 1| = 2^-24 and allows up to 64;
+// bfloat16 has FP32's exponent range and takes S = 1.
+//
+// Rounding to nearest is biased in a steady flow (a node and speed round the
+// same way step after step and the errors add up to a spurious force), so
+// by default the store rounds stochastically: up (away from zero) when the
+// fraction of the gap covered plus (r + 1/2)/64 reaches 1, for six random
+// bits r per value, saturating at the largest finite value.  The random
+// bits of a node come from one Philox4x32-10 block (Salmon, Moraes, Dror,
+// Shaw, SC 2011) with counter (node, pass low word, pass high word, 0) and
+// the seed as key; speed p takes bits 6 (k mod 5) .. + 5 of word k / 5,
+// k = rank of p when the speeds are ordered by (c_z, c_y, c_x).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int rnd_key(int p) { return 9 * (cz(p) + 1) + 3 * (cy(p) + 1) + (cx(p) + 1); }
+__host__ __device__ constexpr int rnd_slot(int p)
+{
+    int r = 0;
+    for (int q = 0; q < kQ; ++q) r += rnd_key(q) < rnd_key(p) ? 1 : 0;
+    return r;
+}
+__host__ __device__ constexpr float iwq(int p) { return c2(p) == 0 ? 3.0f : (c2(p) == 1 ? 18.0f : 36.0f); }
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+template <int P>
+__device__ __forceinline__ uint32_t rbits6(const uint4 &rb)
+{
+    constexpr int k = rnd_slot(P);
+    const uint32_t w = k / 5 == 0 ? rb.x : (k / 5 == 1 ? rb.y : (k / 5 == 2 ? rb.z : rb.w));
+    return (w >> (6 * (k % 5))) & 63u;
+}
+
+// binary16, stochastic: binary16 keeps 10 of FP32's 23 mantissa bits;
+// adding 128 r + 64 to the 13 dropped bits carries into the kept ones
+// exactly when the rounding goes up, and truncation (which saturates at
+// 65504) finishes it.  Values below binary16's normal range (|x| < 2^-14,
+// i.e. |f_p / w_p - 1| < 6e-8) are stored as zero.
+__device__ __forceinline__ __half sr_half(float x, uint32_t r)
+{
+    const uint32_t u = __float_as_uint(x), mag = u & 0x7fffffffu;
+    const __half h = __float2half_rz(__uint_as_float(u + (r << 7) + 64u));
+    return mag >= 0x38800000u ? h : __ushort_as_half((unsigned short)0);
+}
+
+// bfloat16, stochastic: 16 dropped bits, 1024 r + 512 added, then the high
+// half; finite inputs saturate at the largest finite value.
+__device__ __forceinline__ __nv_bfloat16 sr_bf16(float x, uint32_t r)
+{
+    const uint32_t u = __float_as_uint(x), sign = u & 0x80000000u, mag = u & 0x7fffffffu;
+    uint32_t y = mag + (r << 10) + 512u;
+    if (mag < 0x7f800000u) y = min(y, 0x7f7fffffu);
+    return __ushort_as_bfloat16((unsigned short)((sign | y) >> 16));
+}
+
+template <typename St>
+struct Pop;
+template <>
+struct Pop<float> {
+    static constexpr bool kRounds = false;
+    template <int P>
+    __device__ static __forceinline__ float get(float s) { return s; }
+    template <int P>
+    __device__ static __forceinline__ float put(float d, bool, const uint4 &) { return d; }
+};
+template <>
+struct Pop<__half> {
+    static constexpr bool kRounds = true;
+    static constexpr float kS = 1024.0f;
+    template <int P>
+    __device__ static __forceinline__ float get(__half s) { return __half2float(s) * (wq(P) * (1.0f / kS)); }
+    template <int P>
+    __device__ static __forceinline__ __half put(float d, bool sr, const uint4 &rb)
+    {
+        const float x = d * (kS * iwq(P));
+        return sr ? sr_half(x, rbits6<P>(rb)) : __float2half_rn(x);
+    }
+};
+template <>
+struct Pop<__nv_bfloat16> {
+    static constexpr bool kRounds = true;
+    template <int P>
+    __device__ static __forceinline__ float get(__nv_bfloat16 s) { return __bfloat162float(s) * wq(P); }
+    template <int P>
+    __device__ static __forceinline__ __nv_bfloat16 put(float d, bool sr, const uint4 &rb)
+    {
+        const float x = d * iwq(P);
+        return sr ? sr_bf16(x, rbits6<P>(rb)) : __float2bfloat16_rn(x);
+    }
+};
+
+// compile-time loop over the speeds (the storage conversions take p as a
+// template argument)
+template <int P, int End, typename F>
+__device__ __forceinline__ void for_speeds(F &&f)
+{
+    if constexpr (P < End) {
+        f(std::integral_constant<int, P>{});
+        for_speeds<P + 1, End>(f);
+    }
+}
 
 // Collision (Sec. 2.1) of node n = (x, y, z), in deviations, from its 19
 // pulled deviations d, the link mask lk, and the force density / smoothed
@@ -47,17 +178,22 @@ struct LbArgs {
 //        force-density G, Guo's factor of the scheme Eq. vel comes from)
 //   d* = d - (d - d_eq)/T + Df                                (Eq. lbe_discrete)
 //   sigma = -(1 - 1/2T) sum c c (d - d_eq)                    (Eq. stresstensorLB)
-// Stores d*, u, sigma, clears the node's G and theta, raises the stability
-// flag, and at walls writes the reflected populations (halfway bounce-back):
-// a population heading into a solid neighbour m comes back to this node in
-// the opposite direction next pass, so it is stored in m's slot of that
-// direction, from which this node pulls.  Each (slot, solid node) pair has
-// exactly one writer.
-template <bool WALLS, bool CELLS, bool SIGMA>
+// Stores d* (in the storage format; `step` counts the stochastic rounding's
+// random numbers), u, sigma, clears the node's G and theta, raises the
+// stability flag, and at walls writes the reflected populations (halfway
+// bounce-back): a population heading into a solid neighbour m comes back to
+// this node in the opposite direction next pass, so it is stored in m's slot
+// of that direction, from which this node pulls.  Each (slot, solid node)
+// pair has exactly one writer; opposite speeds share a weight, so the stored
+// value is copied as it is.
+template <typename St, bool WALLS, bool CELLS, bool SIGMA>
 __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], uint32_t lk, float gx, float gy,
-                                             float gz, float T, int n, int x, int y, int z)
+                                             float gz, float T, uint32_t n, int x, int y, int z,
+                                             unsigned long long step)
 {
-    const long long Np = a.Np;
+    // element offsets fit 32 bits: the host keeps 19 Np below 2^32
+    const uint32_t Np = (uint32_t)a.Np;
+    St *dst = static_cast<St *>(a.dst);
     if (CELLS) {
         a.G[n] = 0.f;
         a.G[Np + n] = 0.f;
@@ -78,28 +214,51 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
     const float uy = (jy + 0.5f * gy) * irho;
     const float uz = (jz + 0.5f * gz) * irho;
     const float om = 1.0f / T;
+    const float omc = 1.0f - om;
     const float ff = 1.0f - 0.5f * om;
     const float usq = ux * ux + uy * uy + uz * uz;
     const float gu = gx * ux + gy * uy + gz * uz;
+    const bool sr = Pop<St>::kRounds && a.stochastic != 0;
+    uint4 rb = make_uint4(0u, 0u, 0u, 0u);
+    if (sr) rb = philox4x32_10(make_uint4(n, (uint32_t)step, (uint32_t)(step >> 32), 0u), a.key0, a.key1);
+    // A speed p and its opposite q share |c.u|, |c.G| and the weight, so
+    //   d_eq(p, q) = A +- B,  A = w [drho + rho (4.5 (c.u)^2 - 1.5 u^2)],
+    //                         B = 3 w rho c.u,
+    //   Df(p, q)   = C +- D,  C = (1 - 1/2T) w [4.5 (c.G)(c.u) - 1.5 G.u],
+    //                         D = 3 (1 - 1/2T) w c.G,
+    //   d*         = (1 - 1/T) d + d_eq / T + Df,
+    // and the pair adds c c (d_p + d_q - 2A) to the stress.
     float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
-#pragma unroll
-    for (int p = 0; p < kQ; ++p) {
-        const float cu = float(cx(p)) * ux + float(cy(p)) * uy + float(cz(p)) * uz;
-        const float cg = float(cx(p)) * gx + float(cy(p)) * gy + float(cz(p)) * gz;
-        const float w = wq(p);
-        const float deq = w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
-        const float df = ff * w * (3.0f * cg + 4.5f * cg * cu - 1.5f * gu);
-        const float neq = d[p] - deq;
-        if (SIGMA) {
-            if (cx(p)) pxx += neq;
-            if (cy(p)) pyy += neq;
-            if (cz(p)) pzz += neq;
-            if (cx(p) && cy(p)) pxy += cx(p) * cy(p) > 0 ? neq : -neq;
-            if (cx(p) && cz(p)) pxz += cx(p) * cz(p) > 0 ? neq : -neq;
-            if (cy(p) && cz(p)) pyz += cy(p) * cz(p) > 0 ? neq : -neq;
+    for_speeds<0, kQ>([&](auto pc) {
+        constexpr int p = decltype(pc)::value;
+        constexpr int q = opp(p);
+        if constexpr (p == 0) {
+            const float A = wq(0) * (drho - 1.5f * rho * usq);
+            const float C = -1.5f * ff * wq(0) * gu;
+            dst[n] = Pop<St>::template put<0>(omc * d[0] + (om * A + C), sr, rb);
+        } else if constexpr (p < q) {
+            const float cu = float(cx(p)) * ux + float(cy(p)) * uy + float(cz(p)) * uz;
+            const float cg = float(cx(p)) * gx + float(cy(p)) * gy + float(cz(p)) * gz;
+            const float w = wq(p);
+            const float A = w * (drho + rho * (4.5f * cu * cu - 1.5f * usq));
+            const float B = (3.0f * w) * rho * cu;
+            const float fw = ff * w;
+            const float C = fw * (4.5f * cg * cu - 1.5f * gu);
+            const float D = 3.0f * fw * cg;
+            const float P = om * A + C, M = om * B + D;
+            dst[(uint32_t)p * Np + n] = Pop<St>::template put<p>(omc * d[p] + (P + M), sr, rb);
+            dst[(uint32_t)q * Np + n] = Pop<St>::template put<q>(omc * d[q] + (P - M), sr, rb);
+            if (SIGMA) {
+                const float ne = (d[p] + d[q]) - 2.0f * A;
+                if (cx(p)) pxx += ne;
+                if (cy(p)) pyy += ne;
+                if (cz(p)) pzz += ne;
+                if (cx(p) && cy(p)) pxy += cx(p) * cy(p) > 0 ? ne : -ne;
+                if (cx(p) && cz(p)) pxz += cx(p) * cz(p) > 0 ? ne : -ne;
+                if (cy(p) && cz(p)) pyz += cy(p) * cz(p) > 0 ? ne : -ne;
+            }
         }
-        a.dst[(long long)p * Np + n] = d[p] - om * neq + df;
-    }
+    });
     a.U[n] = ux;
     a.U[Np + n] = uy;
     a.U[2 * Np + n] = uz;
@@ -119,18 +278,30 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
             if (!((lk >> p) & 1u)) continue;
             const int xd = wrapm(x + cx(p), a.nx), yd = wrapm(y + cy(p), a.ny), zd = wrapm(z + cz(p), a.nz);
             // read back this thread's own store of d*_p
-            a.dst[(long long)kOppTab[p] * Np + (xd + a.nx * yd + nxy * zd)] = a.dst[(long long)p * Np + n];
+            dst[(uint32_t)kOppTab[p] * Np + (uint32_t)(xd + a.nx * yd + nxy * zd)] = dst[(uint32_t)p * Np + n];
         }
     }
 }
 
-// One thread per node; the 19 upstream deviations are pulled straight from
-// global memory (used when rows are not a multiple of 16 bytes).
-template <bool WALLS, bool CELLS, bool SIGMA>
-__global__ void __launch_bounds__(kLbThreads) k_lb(LbArgs a)
+// External force density at row y: the uniform drive plus the Kolmogorov
+// profile A sin(2 pi y / ny).
+__device__ __forceinline__ void external_force(const LbArgs &a, int y, float &gx, float &gy, float &gz)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= a.N) return;
+    gx = a.gx0;
+    gy = a.gy0;
+    gz = a.gz0;
+    if (a.wave) {
+        const float sw = sinpif(2.0f * (float)y / (float)a.ny);
+        gx += a.wx * sw;
+        gy += a.wy * sw;
+        gz += a.wz * sw;
+    }
+}
+
+template <typename St, bool WALLS, bool CELLS, bool SIGMA>
+__device__ __forceinline__ void lb_node(const LbArgs &a, int n, unsigned long long step)
+{
+    const St *src = static_cast<const St *>(a.src);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int x = n % nx;
     const int t = n / nx;
@@ -145,14 +316,15 @@ __global__ void __launch_bounds__(kLbThreads) k_lb(LbArgs a)
     // into which this node wrote its reflected population last pass.
     const uint32_t lk = WALLS ? a.links[n] : 0u;
     float d[kQ];
-#pragma unroll
-    for (int p = 0; p < kQ; ++p) {
-        const int ix = cx(p) == 0 ? 0 : (cx(p) > 0 ? 1 : 2);
-        const int iy = cy(p) == 0 ? 0 : (cy(p) > 0 ? 1 : 2);
-        const int iz = cz(p) == 0 ? 0 : (cz(p) > 0 ? 1 : 2);
-        d[p] = a.src[(long long)p * a.Np + (xs[ix] + ys[iy] + zs[iz])];
-    }
-    float gx = a.gx0, gy = a.gy0, gz = a.gz0, T = a.tau0;
+    for_speeds<0, kQ>([&](auto pc) {
+        constexpr int p = decltype(pc)::value;
+        constexpr int ix = cx(p) == 0 ? 0 : (cx(p) > 0 ? 1 : 2);
+        constexpr int iy = cy(p) == 0 ? 0 : (cy(p) > 0 ? 1 : 2);
+        constexpr int iz = cz(p) == 0 ? 0 : (cz(p) > 0 ? 1 : 2);
+        d[p] = Pop<St>::template get<p>(src[(uint32_t)p * (uint32_t)a.Np + (uint32_t)(xs[ix] + ys[iy] + zs[iz])]);
+    });
+    float gx, gy, gz, T = a.tau0;
+    external_force(a, y, gx, gy, gz);
     if (CELLS) {
         gx += a.G[n];
         gy += a.G[a.Np + n];
@@ -160,7 +332,28 @@ __global__ void __launch_bounds__(kLbThreads) k_lb(LbArgs a)
         T += a.delta * a.th[n];
     }
     if (WALLS && (lk >> 31)) return;  // solid node: nothing to collide
-    collide_node<WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, n, x, y, z);
+    collide_node<St, WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, (uint32_t)n, x, y, z, step);
+}
+
+template <typename St, bool WALLS, bool CELLS, bool SIGMA>
+__global__ void __launch_bounds__(kLbThreads) k_lb(LbArgs a)
+{
+    __shared__ unsigned long long s_step;
+    if (threadIdx.x == 0) s_step = *a.step;
+    __syncthreads();
+    const unsigned long long step = s_step;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < a.N) lb_node<St, WALLS, CELLS, SIGMA>(a, n, step);
+    // the last block out advances the pass counter
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&a.work[1], 1) == (int)gridDim.x - 1) {
+            a.work[1] = 0;
+            *a.step = step + 1;
+            __threadfence();
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -236,18 +429,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 }
 
 struct StageLayout {
-    int B;        // rows per batch
-    int planes;   // staged planes per row: 19 (+4 G, theta) (+1 links)
-    int stage_floats;
-    int stages;   // buffers in the ring (2 .. kMaxStages)
+    int B;           // rows per batch
+    int planes;      // staged planes per row: 19 populations (+4 G, theta) (+1 links)
+    int pop_bytes;   // bytes of the 19 population planes of a stage
+    int stage_bytes;
+    int stages;      // buffers in the ring (2 .. kMaxStages)
 };
 
-template <bool WALLS, bool CELLS, bool SIGMA>
+template <typename St, bool WALLS, bool CELLS, bool SIGMA>
 __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout L, int nbatches)
 {
-    extern __shared__ __align__(128) float sm[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages];
     __shared__ int s_batch[kMaxStages];
+    __shared__ unsigned long long s_step;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int B = L.B, ns = L.stages;
     const int nyb = (ny + B - 1) / B;
@@ -257,6 +452,7 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
             mbar_init(smem_addr(&empty[k]), kStConsumers / 32);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_step = *a.step;
     }
     __syncthreads();
 
@@ -264,13 +460,15 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
         // Producer warp.  Batches are claimed from a global counter, so a CTA
         // that starts late (the SM was busy with another kernel) just does
         // fewer of them.  A batch is rows y0 .. y0 + nb - 1 at one z.  Staged
-        // plane k, batch row b sits at stage + (k * B + b) * nx.  For a speed
-        // p the upstream rows y - c_y are contiguous in plane p except where
-        // they wrap in y, so each plane needs one copy, or two.  The batch id
-        // goes to s_batch[stage] before the arrive that the consumers'
-        // wait acquires; -1 tells them to stop.
+        // population plane k, batch row b sits at (k * B + b) * nx elements of
+        // the stage, the 4-byte planes after the 19 population planes.  For
+        // a speed p the upstream rows y - c_y are contiguous in plane p except
+        // where they wrap in y, so each plane needs one copy, or two.  The
+        // batch id goes to s_batch[stage] before the arrive that the
+        // consumers' wait acquires; -1 tells them to stop.
+        const St *src = static_cast<const St *>(a.src);
         const int lane = threadIdx.x - kStConsumers;
-        const uint32_t row_bytes = (uint32_t)nx * 4u;
+        const uint32_t prow_bytes = (uint32_t)nx * (uint32_t)sizeof(St), frow_bytes = (uint32_t)nx * 4u;
         int it = 0;
         bool ok = true;
         for (;; ++it) {
@@ -295,34 +493,37 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
             const int nb = min(B, ny - y0);
             if (lane == 0) {
                 s_batch[stage] = batch;
-                mbar_expect_tx(bar, (uint32_t)(L.planes * nb) * row_bytes);
+                mbar_expect_tx(bar, (uint32_t)(kQ * nb) * prow_bytes + (uint32_t)((L.planes - kQ) * nb) * frow_bytes);
             }
             __syncwarp();
-            float *base = sm + (size_t)stage * L.stage_floats;
+            unsigned char *base = smraw + (size_t)stage * L.stage_bytes;
+            St *pst = reinterpret_cast<St *>(base);
+            float *fst = reinterpret_cast<float *>(base + L.pop_bytes);
             for (int k = lane; k < L.planes; k += 32) {
-                float *dst = base + (size_t)k * B * nx;
                 if (k < kQ) {
+                    St *dst = pst + (size_t)k * B * nx;
                     const int zs = wrapm(z - cz(k), nz);
-                    const float *plane = a.src + (long long)k * a.Np + (long long)zs * ny * nx;
+                    const St *plane = src + (long long)k * a.Np + (long long)zs * ny * nx;
                     const int ys = y0 - cy(k);  // first upstream row, may be -1 or run past ny
                     int b = 0;
                     while (b < nb) {
                         const int yr = wrapm(ys + b, ny);
                         const int run = min(nb - b, ny - yr);
                         bulk_g2s(smem_addr(dst + (size_t)b * nx), plane + (long long)yr * nx,
-                                 (uint32_t)run * row_bytes, bar);
+                                 (uint32_t)run * prow_bytes, bar);
                         b += run;
                     }
                 } else {
+                    float *dst = fst + (size_t)(k - kQ) * B * nx;
                     const long long off = ((long long)z * ny + y0) * nx;
-                    const float *src;
+                    const float *fsrc;
                     if (CELLS && k < kQ + 3)
-                        src = a.G + (long long)(k - kQ) * a.Np + off;
+                        fsrc = a.G + (long long)(k - kQ) * a.Np + off;
                     else if (CELLS && k == kQ + 3)
-                        src = a.th + off;
+                        fsrc = a.th + off;
                     else
-                        src = reinterpret_cast<const float *>(a.links) + off;
-                    bulk_g2s(smem_addr(dst), src, (uint32_t)nb * row_bytes, bar);
+                        fsrc = reinterpret_cast<const float *>(a.links) + off;
+                    bulk_g2s(smem_addr(dst), fsrc, (uint32_t)nb * frow_bytes, bar);
                 }
             }
         }
@@ -331,18 +532,27 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
             for (int j = it > ns ? it - ns : 0; j < it; ++j)
                 mbar_wait(smem_addr(&full[j % ns]), (uint32_t)((j / ns) & 1));
         }
-        // the last CTA out resets the counters for the next launch
-        if (lane == 0 && atomicAdd(&a.work[1], 1) == (int)gridDim.x - 1) {
-            a.work[0] = 0;
-            a.work[1] = 0;
+        // the last CTA out resets the counters for the next launch and
+        // advances the pass counter (every CTA read it before its barrier)
+        if (lane == 0) {
             __threadfence();
+            if (atomicAdd(&a.work[1], 1) == (int)gridDim.x - 1) {
+                a.work[0] = 0;
+                a.work[1] = 0;
+                *a.step = s_step + 1;
+                __threadfence();
+            }
         }
         return;
     }
 
-    // consumer warps
+    // consumer warps: thread t takes batch nodes l = t, t + 256, ... as
+    // (row b, column x) = (l / nx, l % nx), advanced without a division
     const int lane = threadIdx.x & 31;
     const int plane_stride = B * nx;
+    const unsigned long long step = s_step;
+    const int x_first = threadIdx.x % nx, b_first = threadIdx.x / nx;
+    const int x_step = kStConsumers % nx, b_step = kStConsumers / nx;
     for (int it = 0;; ++it) {
         const int stage = it % ns;
         if (!mbar_wait(smem_addr(&full[stage]), (uint32_t)((it / ns) & 1))) {
@@ -351,39 +561,50 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
         }
         const int batch = s_batch[stage];
         if (batch < 0) break;
-        const float *st = sm + (size_t)stage * L.stage_floats;
+        const unsigned char *base = smraw + (size_t)stage * L.stage_bytes;
+        const St *pst = reinterpret_cast<const St *>(base);
+        const float *fst = reinterpret_cast<const float *>(base + L.pop_bytes);
         const int z = batch / nyb, y0 = (batch - z * nyb) * B;
         const int nb = min(B, ny - y0);
-        for (int l = threadIdx.x; l < nb * nx; l += kStConsumers) {
-            const int b = l / nx, x = l - b * nx;
+        for (int b = b_first, x = x_first; b < nb;) {
             const int y = y0 + b;
-            const int n = (y + ny * z) * nx + x;
-            const float *row = st + (size_t)b * nx;
+            const uint32_t n = (uint32_t)((y + ny * z) * nx + x);
+            const int bx = b, xx = x;
+            x += x_step;
+            b += b_step;
+            if (x >= nx) {
+                x -= nx;
+                ++b;
+            }
+            const St *prow = pst + (size_t)bx * nx;
+            const float *frow = fst + (size_t)bx * nx;
             const uint32_t lk =
-                WALLS ? reinterpret_cast<const uint32_t *>(row)[(size_t)(kQ + (CELLS ? 4 : 0)) * plane_stride + x] : 0u;
+                WALLS ? reinterpret_cast<const uint32_t *>(frow)[(size_t)(CELLS ? 4 : 0) * plane_stride + xx] : 0u;
             if (WALLS && (lk >> 31)) continue;
-            const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+            const int xm = xx == 0 ? nx - 1 : xx - 1, xp = xx == nx - 1 ? 0 : xx + 1;
             float d[kQ];
-#pragma unroll
-            for (int p = 0; p < kQ; ++p) {
-                const int xs = cx(p) == 0 ? x : (cx(p) > 0 ? xm : xp);
-                d[p] = row[p * plane_stride + xs];
-            }
-            float gx = a.gx0, gy = a.gy0, gz = a.gz0, T = a.tau0;
+            for_speeds<0, kQ>([&](auto pc) {
+                constexpr int p = decltype(pc)::value;
+                const int xs = cx(p) == 0 ? xx : (cx(p) > 0 ? xm : xp);
+                d[p] = Pop<St>::template get<p>(prow[p * plane_stride + xs]);
+            });
+            float gx, gy, gz, T = a.tau0;
+            external_force(a, y, gx, gy, gz);
             if (CELLS) {
-                gx += row[(kQ + 0) * plane_stride + x];
-                gy += row[(kQ + 1) * plane_stride + x];
-                gz += row[(kQ + 2) * plane_stride + x];
-                T += a.delta * row[(kQ + 3) * plane_stride + x];
+                gx += frow[0 * plane_stride + xx];
+                gy += frow[1 * plane_stride + xx];
+                gz += frow[2 * plane_stride + xx];
+                T += a.delta * frow[3 * plane_stride + xx];
             }
-            collide_node<WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, n, x, y, z);
+            collide_node<St, WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, n, xx, y, z, step);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&empty[stage]));  // this warp is done with the stage
     }
 }
 
-__global__ void k_rho(const float *__restrict__ pops, const uint8_t *__restrict__ solid,
+template <typename St>
+__global__ void k_rho(const void *__restrict__ pops_v, const uint8_t *__restrict__ solid,
                       float *__restrict__ rho, int N, long long Np)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -392,9 +613,12 @@ __global__ void k_rho(const float *__restrict__ pops, const uint8_t *__restrict_
         rho[n] = 0.f;
         return;
     }
+    const St *pops = static_cast<const St *>(pops_v);
     float s = 0.f;
-#pragma unroll
-    for (int p = 0; p < kQ; ++p) s += pops[(long long)p * Np + n];
+    for_speeds<0, kQ>([&](auto pc) {
+        constexpr int p = decltype(pc)::value;
+        s += Pop<St>::template get<p>(pops[(long long)p * Np + n]);
+    });
     rho[n] = s;  // rho - 1: the host adds 1 in FP64
 }
 
@@ -404,22 +628,29 @@ __global__ void k_rho(const float *__restrict__ pops, const uint8_t *__restrict_
 // partials in a fixed order and adds the cell momenta sum M V.
 constexpr int kBudThreads = 256;
 
+struct ForceArgs {
+    float g[3], w[3];
+    int nx, ny;
+};
+
+template <typename St>
 __global__ void __launch_bounds__(kBudThreads)
-k_budget_nodes(const float *__restrict__ pops, const float *__restrict__ U,
-               const uint8_t *__restrict__ solid, double *__restrict__ part, int N, long long Np)
+k_budget_nodes(const void *__restrict__ pops_v, const float *__restrict__ U,
+               const uint8_t *__restrict__ solid, double *__restrict__ part, int N, long long Np, ForceArgs fa)
 {
-    double m = 0.0, px = 0.0, py = 0.0, pz = 0.0, umax = 0.0, nan = 0.0;
+    const St *pops = static_cast<const St *>(pops_v);
+    double m = 0.0, px = 0.0, py = 0.0, pz = 0.0, umax = 0.0, nan = 0.0, work = 0.0;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
         if (solid && solid[n]) continue;
         float s = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-        for (int p = 0; p < kQ; ++p) {
-            const float v = pops[(long long)p * Np + n];
+        for_speeds<0, kQ>([&](auto pc) {
+            constexpr int p = decltype(pc)::value;
+            const float v = Pop<St>::template get<p>(pops[(long long)p * Np + n]);
             s += v;
             if (cx(p)) jx += cx(p) > 0 ? v : -v;
             if (cy(p)) jy += cy(p) > 0 ? v : -v;
             if (cz(p)) jz += cz(p) > 0 ? v : -v;
-        }
+        });
         m += 1.0 + (double)s;
         px += jx;
         py += jy;
@@ -428,18 +659,23 @@ k_budget_nodes(const float *__restrict__ pops, const float *__restrict__ U,
         const float u2 = ux * ux + uy * uy + uz * uz;
         if (!(u2 == u2) || !(s == s)) nan += 1.0;
         else if (u2 > umax) umax = u2;
+        // work rate of the external force (uniform + sin(2 pi y / ny) profile)
+        const double sw = sinpi(2.0 * (double)((n / fa.nx) % fa.ny) / (double)fa.ny);
+        work += ((double)fa.g[0] + (double)fa.w[0] * sw) * ux + ((double)fa.g[1] + (double)fa.w[1] * sw) * uy +
+                ((double)fa.g[2] + (double)fa.w[2] * sw) * uz;
     }
-    __shared__ double sh[6][kBudThreads];
+    __shared__ double sh[7][kBudThreads];
     sh[0][threadIdx.x] = m;
     sh[1][threadIdx.x] = px;
     sh[2][threadIdx.x] = py;
     sh[3][threadIdx.x] = pz;
     sh[4][threadIdx.x] = umax;
     sh[5][threadIdx.x] = nan;
+    sh[6][threadIdx.x] = work;
     __syncthreads();
     for (int w = kBudThreads / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) {
-            for (int k = 0; k < 6; ++k) {
+            for (int k = 0; k < 7; ++k) {
                 if (k == 4)
                     sh[k][threadIdx.x] = fmax(sh[k][threadIdx.x], sh[k][threadIdx.x + w]);
                 else
@@ -448,62 +684,110 @@ k_budget_nodes(const float *__restrict__ pops, const float *__restrict__ U,
         }
         __syncthreads();
     }
-    if (threadIdx.x < 6) part[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
+    if (threadIdx.x < 7) part[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// accum (optional, 8 doubles): time-average sums of a solve, added to when
+// the pass counter has reached `from`: work rate, sample count, p_fluid
+// (3), max |u| (a maximum), NaN count.
 __global__ void __launch_bounds__(kBudThreads)
 k_budget_final(const double *__restrict__ part, int nblocks, const double *__restrict__ V, int nc,
-               double M, double *__restrict__ out)
+               double M, double *__restrict__ out, double *__restrict__ accum,
+               const unsigned long long *__restrict__ step, long long from)
 {
-    __shared__ double sh[9][kBudThreads];
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    __shared__ double sh[10][kBudThreads];
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
         for (int k = 0; k < 6; ++k) {
             const double v = part[b * 8 + k];
             acc[k] = k == 4 ? fmax(acc[k], v) : acc[k] + v;
         }
+        acc[9] += part[b * 8 + 6];
     }
     for (int i = threadIdx.x; i < nc; i += blockDim.x)
         for (int a = 0; a < 3; ++a) acc[6 + a] += M * V[3 * i + a];
-    for (int k = 0; k < 9; ++k) sh[k][threadIdx.x] = acc[k];
+    for (int k = 0; k < 10; ++k) sh[k][threadIdx.x] = acc[k];
     __syncthreads();
     for (int w = kBudThreads / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w)
-            for (int k = 0; k < 9; ++k)
+            for (int k = 0; k < 10; ++k)
                 sh[k][threadIdx.x] = k == 4 ? fmax(sh[k][threadIdx.x], sh[k][threadIdx.x + w])
                                             : sh[k][threadIdx.x] + sh[k][threadIdx.x + w];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        // mass, p_fluid (3), max |u|, NaN count, p_cells (3)
-        for (int k = 0; k < 9; ++k) out[k] = k == 4 ? sqrt(sh[4][0]) : sh[k][0];
+        // mass, p_fluid (3), max |u|, NaN count, p_cells (3), work rate of the external force
+        for (int k = 0; k < 10; ++k) out[k] = k == 4 ? sqrt(sh[4][0]) : sh[k][0];
+        if (accum && (long long)*step >= from) {
+            accum[0] += out[9];
+            accum[1] += 1.0;
+            for (int a = 0; a < 3; ++a) accum[2 + a] += out[1 + a];
+            accum[5] = fmax(accum[5], out[4]);
+            accum[6] += out[5];
+        }
     }
 }
 
 }  // namespace
 
+int pop_bytes(int prec) { return prec == PREC_F32 ? 4 : 2; }
+
 StageLayout stage_layout(const Dev &d)
 {
     StageLayout L;
     L.planes = kQ + (d.nc > 0 ? 4 : 0) + (d.walls ? 1 : 0);
-    const int row_floats = d.nx;
+    const int es = pop_bytes(d.prec);
+    const int row_bytes = d.nx * (kQ * es + (L.planes - kQ) * 4);
     // about kStageBytes per stage, whole rows, at most one y column of rows;
     // a multiple of the rows that fill the consumer threads when rows are short
-    int B = kStageBytes / (L.planes * row_floats * 4);
+    int B = kStageBytes / row_bytes;
     B = B < 1 ? 1 : (B > d.ny ? d.ny : B);
-    if (row_floats < kStConsumers && B * row_floats > kStConsumers)
-        B -= B % (kStConsumers / row_floats > 0 ? kStConsumers / row_floats : 1);
+    if (d.nx < kStConsumers && B * d.nx > kStConsumers)
+        B -= B % (kStConsumers / d.nx > 0 ? kStConsumers / d.nx : 1);
     L.B = B;
-    L.stage_floats = L.planes * B * row_floats;
+    L.pop_bytes = kQ * B * d.nx * es;
+    L.stage_bytes = B * row_bytes;
     L.stages = kMaxStages;
     return L;
 }
 
 bool staged_ok(const Dev &d)
 {
-    if (d.nx % 4 != 0) return false;  // rows must be whole 16-byte units
+    if ((d.nx * pop_bytes(d.prec)) % 16 != 0) return false;  // rows must be whole 16-byte units
     const StageLayout L = stage_layout(d);
-    return 2u * L.stage_floats * sizeof(float) <= 200u * 1024u;
+    return 2u * (unsigned)L.stage_bytes <= 200u * 1024u;
+}
+
+// Calls op.run<St, WALLS, CELLS, SIGMA>() for the instance's storage type and
+// lattice.
+template <class Op, typename St>
+void dispatch_flags(const Dev &d, Op &op)
+{
+    const bool cells = d.nc > 0, sig = d.S != nullptr, walls = d.walls != 0;
+    if (walls) {
+        if (cells) {
+            if (sig) op.template run<St, true, true, true>(); else op.template run<St, true, true, false>();
+        } else {
+            if (sig) op.template run<St, true, false, true>(); else op.template run<St, true, false, false>();
+        }
+    } else {
+        if (cells) {
+            if (sig) op.template run<St, false, true, true>(); else op.template run<St, false, true, false>();
+        } else {
+            if (sig) op.template run<St, false, false, true>(); else op.template run<St, false, false, false>();
+        }
+    }
+}
+
+template <class Op>
+void dispatch(const Dev &d, Op &op)
+{
+    if (d.prec == PREC_F16)
+        dispatch_flags<Op, __half>(d, op);
+    else if (d.prec == PREC_BF16)
+        dispatch_flags<Op, __nv_bfloat16>(d, op);
+    else
+        dispatch_flags<Op, float>(d, op);
 }
 
 // Ring depth: among 2 .. kMaxStages stages (each depth fixes how many CTAs
@@ -512,67 +796,109 @@ bool staged_ok(const Dev &d)
 // ties go to the deeper ring.  With cells, at most kLbCtasWithCells CTAs per
 // SM: the next step's cell-list, Gay-Berne and shape-list kernels run
 // alongside the pass and need registers and shared memory on every SM.
-template <bool W, bool C, bool S_>
-void prepare_lb_t(Dev &d)
+struct PrepareOp {
+    Dev &d;
+    template <typename St, bool W, bool C, bool S_>
+    void run()
+    {
+        d.lb_grid = 0;
+        if (!staged_ok(d)) return;
+        StageLayout L = stage_layout(d);
+        const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        long long best_cost = -1;
+        raise_smem_limit((const void *)k_lb_staged<St, W, C, S_>, 200 * 1024);
+        for (int ns = kMaxStages; ns >= 2; --ns) {
+            const size_t smem = (size_t)ns * L.stage_bytes;
+            if (smem > 200u * 1024u) continue;
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_staged<St, W, C, S_>, kStThreads, smem);
+            if (d.nc > 0 && per_sm > kLbCtasWithCells) per_sm = kLbCtasWithCells;
+            if (per_sm < 1) continue;
+            const long long slots = (long long)sms * per_sm;
+            const long long cost = ((nbatches + slots - 1) / slots) * per_sm;
+            if (best_cost < 0 || cost < best_cost) {
+                best_cost = cost;
+                d.lb_stages = ns;
+                d.lb_smem = smem;
+                d.lb_grid = (int)(slots > nbatches ? nbatches : slots);
+            }
+        }
+    }
+};
+
+struct LaunchOp {
+    const Dev &d;
+    const LbArgs &a;
+    cudaStream_t s;
+    template <typename St, bool W, bool C, bool S_>
+    void run()
+    {
+        if (d.lb_grid > 0) {
+            StageLayout L = stage_layout(d);
+            L.stages = d.lb_stages;
+            const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
+            k_lb_staged<St, W, C, S_><<<d.lb_grid, kStThreads, d.lb_smem, s>>>(a, L, nbatches);
+        } else {
+            k_lb<St, W, C, S_><<<(d.N + kLbThreads - 1) / kLbThreads, kLbThreads, 0, s>>>(a);
+        }
+    }
+};
+
+void prepare_lb(Dev &d)
 {
-    d.lb_grid = 0;
-    if (!staged_ok(d)) return;
-    StageLayout L = stage_layout(d);
+    PrepareOp op{d};
+    dispatch(d, op);
+}
+
+// Launch shapes of the row-staged pass the autotuner tries: every ring depth
+// 2 .. kMaxStages whose stages fit, with 1 .. (what fits on an SM, at most
+// 4) CTAs per SM.
+struct ShapesOp {
+    const Dev &d;
+    int *stages, *ctas, max, n;
+    template <typename St, bool W, bool C, bool S_>
+    void run()
+    {
+        n = 0;
+        if (!staged_ok(d)) return;
+        const StageLayout L = stage_layout(d);
+        raise_smem_limit((const void *)k_lb_staged<St, W, C, S_>, 200 * 1024);
+        for (int ns = 2; ns <= kMaxStages; ++ns) {
+            const size_t smem = (size_t)ns * L.stage_bytes;
+            if (smem > 200u * 1024u) continue;
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_staged<St, W, C, S_>, kStThreads, smem);
+            for (int c = 1; c <= per_sm && c <= 4 && n < max; ++c) {
+                stages[n] = ns;
+                ctas[n] = c;
+                ++n;
+            }
+        }
+    }
+};
+
+int lb_shapes(const Dev &d, int *stages, int *ctas, int max)
+{
+    ShapesOp op{d, stages, ctas, max, 0};
+    dispatch(d, op);
+    return op.n;
+}
+
+void set_lb_shape(Dev &d, int stages, int ctas_per_sm)
+{
+    if (d.lb_grid <= 0) return;
+    const StageLayout L = stage_layout(d);
     const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long best_cost = -1;
-    for (int ns = kMaxStages; ns >= 2; --ns) {
-        const size_t smem = (size_t)ns * L.stage_floats * sizeof(float);
-        if (smem > 200u * 1024u) continue;
-        cudaFuncSetAttribute(k_lb_staged<W, C, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_staged<W, C, S_>, kStThreads, smem);
-        if (d.nc > 0 && per_sm > kLbCtasWithCells) per_sm = kLbCtasWithCells;
-        if (per_sm < 1) continue;
-        const long long slots = (long long)sms * per_sm;
-        const long long cost = ((nbatches + slots - 1) / slots) * per_sm;
-        if (best_cost < 0 || cost < best_cost) {
-            best_cost = cost;
-            d.lb_stages = ns;
-            d.lb_smem = smem;
-            d.lb_grid = (int)(slots > nbatches ? nbatches : slots);
-        }
-    }
-    if (d.lb_grid > 0)
-        cudaFuncSetAttribute(k_lb_staged<W, C, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.lb_smem);
-}
-
-template <bool W, bool C, bool S_>
-void launch_lb_t(const Dev &d, const LbArgs &a, cudaStream_t s)
-{
-    if (d.lb_grid > 0) {
-        StageLayout L = stage_layout(d);
-        L.stages = d.lb_stages;
-        const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
-        k_lb_staged<W, C, S_><<<d.lb_grid, kStThreads, d.lb_smem, s>>>(a, L, nbatches);
-    } else {
-        k_lb<W, C, S_><<<(d.N + kLbThreads - 1) / kLbThreads, kLbThreads, 0, s>>>(a);
-    }
-}
-
-void prepare_lb(Dev &d)
-{
-    const bool cells = d.nc > 0, sig = d.S != nullptr, walls = d.walls != 0;
-    if (walls) {
-        if (cells) {
-            if (sig) prepare_lb_t<true, true, true>(d); else prepare_lb_t<true, true, false>(d);
-        } else {
-            if (sig) prepare_lb_t<true, false, true>(d); else prepare_lb_t<true, false, false>(d);
-        }
-    } else {
-        if (cells) {
-            if (sig) prepare_lb_t<false, true, true>(d); else prepare_lb_t<false, true, false>(d);
-        } else {
-            if (sig) prepare_lb_t<false, false, true>(d); else prepare_lb_t<false, false, false>(d);
-        }
-    }
+    const long long slots = (long long)sms * ctas_per_sm;
+    d.lb_stages = stages;
+    d.lb_smem = (size_t)stages * L.stage_bytes;
+    d.lb_grid = (int)(slots > nbatches ? nbatches : slots);
 }
 
 void launch_lb(const Dev &d, const Params &p, int parity, cudaStream_t s)
@@ -587,6 +913,7 @@ void launch_lb(const Dev &d, const Params &p, int parity, cudaStream_t s)
     a.S = d.S;
     a.flags = d.flags;
     a.work = d.lb_work;
+    a.step = d.lb_step;
     a.nx = d.nx;
     a.ny = d.ny;
     a.nz = d.nz;
@@ -598,25 +925,26 @@ void launch_lb(const Dev &d, const Params &p, int parity, cudaStream_t s)
     a.tau0 = p.tau0;
     a.delta = p.delta;
     a.mach2 = p.mach2;
-    const bool cells = d.nc > 0, sig = d.S != nullptr, walls = d.walls != 0;
-    if (walls) {
-        if (cells) {
-            if (sig) launch_lb_t<true, true, true>(d, a, s); else launch_lb_t<true, true, false>(d, a, s);
-        } else {
-            if (sig) launch_lb_t<true, false, true>(d, a, s); else launch_lb_t<true, false, false>(d, a, s);
-        }
-    } else {
-        if (cells) {
-            if (sig) launch_lb_t<false, true, true>(d, a, s); else launch_lb_t<false, true, false>(d, a, s);
-        } else {
-            if (sig) launch_lb_t<false, false, true>(d, a, s); else launch_lb_t<false, false, false>(d, a, s);
-        }
-    }
+    a.wx = p.gwave[0];
+    a.wy = p.gwave[1];
+    a.wz = p.gwave[2];
+    a.wave = p.wave;
+    a.key0 = (uint32_t)(d.seed & 0xffffffffull);
+    a.key1 = (uint32_t)(d.seed >> 32);
+    a.stochastic = d.stochastic;
+    LaunchOp op{d, a, s};
+    dispatch(d, op);
 }
 
 void launch_rho(const Dev &d, int parity, cudaStream_t s)
 {
-    k_rho<<<(d.N + 255) / 256, 256, 0, s>>>(d.pops[parity], d.solid, d.rho, d.N, d.Np);
+    const int g = (d.N + 255) / 256;
+    if (d.prec == PREC_F16)
+        k_rho<__half><<<g, 256, 0, s>>>(d.pops[parity], d.solid, d.rho, d.N, d.Np);
+    else if (d.prec == PREC_BF16)
+        k_rho<__nv_bfloat16><<<g, 256, 0, s>>>(d.pops[parity], d.solid, d.rho, d.N, d.Np);
+    else
+        k_rho<float><<<g, 256, 0, s>>>(d.pops[parity], d.solid, d.rho, d.N, d.Np);
 }
 
 int budget_blocks_for(int N)
@@ -625,12 +953,26 @@ int budget_blocks_for(int N)
     return b < 1 ? 1 : (b > 4096 ? 4096 : b);
 }
 
-void launch_budget(const Dev &d, const Params &p, int parity, cudaStream_t s)
+void launch_budget(const Dev &d, const Params &p, int parity, cudaStream_t s, bool accumulate, long long from)
 {
-    k_budget_nodes<<<d.budget_blocks, kBudThreads, 0, s>>>(d.pops[parity], d.U, d.solid,
-                                                           d.budget_part, d.N, d.Np);
-    k_budget_final<<<1, kBudThreads, 0, s>>>(d.budget_part, d.budget_blocks, d.V, d.nc, p.M,
-                                             d.budget_out);
+    ForceArgs fa;
+    for (int k = 0; k < 3; ++k) {
+        fa.g[k] = p.gext[k];
+        fa.w[k] = p.gwave[k];
+    }
+    fa.nx = d.nx;
+    fa.ny = d.ny;
+    if (d.prec == PREC_F16)
+        k_budget_nodes<__half><<<d.budget_blocks, kBudThreads, 0, s>>>(d.pops[parity], d.U, d.solid,
+                                                                      d.budget_part, d.N, d.Np, fa);
+    else if (d.prec == PREC_BF16)
+        k_budget_nodes<__nv_bfloat16><<<d.budget_blocks, kBudThreads, 0, s>>>(d.pops[parity], d.U, d.solid,
+                                                                             d.budget_part, d.N, d.Np, fa);
+    else
+        k_budget_nodes<float><<<d.budget_blocks, kBudThreads, 0, s>>>(d.pops[parity], d.U, d.solid,
+                                                                     d.budget_part, d.N, d.Np, fa);
+    k_budget_final<<<1, kBudThreads, 0, s>>>(d.budget_part, d.budget_blocks, d.V, d.nc, p.M, d.budget_out,
+                                             accumulate ? d.accum : nullptr, d.lb_step, from);
 }
 
 }  // namespace rbc

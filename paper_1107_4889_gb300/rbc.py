@@ -31,7 +31,8 @@ _U8 = ctypes.POINTER(ctypes.c_uint8)
 
 class rbc_geometry(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
-                ("periodic", ctypes.c_int * 3), ("solid", _U8), ("body_force", ctypes.c_double * 3)]
+                ("periodic", ctypes.c_int * 3), ("solid", _U8), ("body_force", ctypes.c_double * 3),
+                ("body_force_wave", ctypes.c_double * 3)]
 
 
 class rbc_cells(ctypes.Structure):
@@ -48,20 +49,46 @@ class rbc_params(ctypes.Structure):
                 ("rho_floor", ctypes.c_double), ("r_cut", ctypes.c_double),
                 ("r_cut_wall", ctypes.c_double), ("mach_max", ctypes.c_double),
                 ("bin_capacity", ctypes.c_int), ("max_neighbors", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("precision", ctypes.c_int), ("rounding", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+
+
+#: rbc_params.precision / rounding values (include/rbc.h)
+PRECISION = {"f32": 0, "f16": 1, "bf16": 2}
+ROUNDING = {"stochastic": 0, "nearest": 1}
 
 
 class rbc_stats_t(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("mass", ctypes.c_double),
                 ("p_fluid", ctypes.c_double * 3), ("p_cells", ctypes.c_double * 3),
                 ("max_u", ctypes.c_double), ("gb_clamps", ctypes.c_int64),
-                ("unstable", ctypes.c_int32), ("overflow", ctypes.c_int32)]
+                ("unstable", ctypes.c_int32), ("overflow", ctypes.c_int32), ("power", ctypes.c_double)]
+
+
+class rbc_request(ctypes.Structure):
+    _fields_ = [("geom", rbc_geometry), ("cells", rbc_cells), ("params", rbc_params),
+                ("steps", ctypes.c_int64), ("average_from", ctypes.c_int64), ("tag", ctypes.c_uint64)]
+
+
+class rbc_result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("steps", ctypes.c_int64), ("samples", ctypes.c_int64), ("mean_power", ctypes.c_double),
+                ("mean_p_fluid", ctypes.c_double * 3), ("max_u", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_uint64)]
+
+
+class rbc_tune_report(ctypes.Structure):
+    _fields_ = [("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("ms_per_step", ctypes.c_double),
+                ("default_ms_per_step", ctypes.c_double), ("trials", ctypes.c_int)]
 
 
 #: symbols include/rbc.h declares
 EXPORTS = ["rbc_default_params", "rbc_workspace_size", "rbc_init", "rbc_step", "rbc_fields",
            "rbc_stats", "rbc_cell_diag", "rbc_neighbors", "rbc_set_timing", "rbc_kernel_times",
-           "rbc_launches_per_step", "rbc_neighbors_noalloc", "rbc_free", "rbc_last_error"]
+           "rbc_autotune", "rbc_launches_per_step", "rbc_neighbors_noalloc", "rbc_server_create", "rbc_server_submit",
+           "rbc_server_poll", "rbc_server_results", "rbc_server_clock", "rbc_server_free", "rbc_free",
+           "rbc_last_error"]
 
 _lib = None
 
@@ -95,10 +122,23 @@ def load(path: str = LIB_PATH):
     L.rbc_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.rbc_kernel_times.argtypes = [ctypes.c_void_p, _D, _I64]
     L.rbc_launches_per_step.argtypes = [ctypes.c_void_p]
+    L.rbc_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, P(rbc_tune_report)]
+    L.rbc_autotune.restype = ctypes.c_int
     L.rbc_neighbors_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         _I, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.c_void_p]
     L.rbc_neighbors_noalloc.restype = ctypes.c_int
+    L.rbc_server_create.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                    P(ctypes.c_void_p)]
+    L.rbc_server_submit.argtypes = [ctypes.c_void_p, P(rbc_request)]
+    L.rbc_server_poll.argtypes = [ctypes.c_void_p, _I, _I]
+    L.rbc_server_results.argtypes = [ctypes.c_void_p, P(rbc_result), ctypes.c_int, _I]
+    L.rbc_server_clock.argtypes = [ctypes.c_void_p]
+    L.rbc_server_clock.restype = ctypes.c_double
+    L.rbc_server_free.argtypes = [ctypes.c_void_p]
+    L.rbc_server_free.restype = None
+    for name in ("rbc_server_create", "rbc_server_submit", "rbc_server_poll", "rbc_server_results"):
+        getattr(L, name).restype = ctypes.c_int
     L.rbc_free.argtypes = [ctypes.c_void_p]
     L.rbc_free.restype = None
     L.rbc_last_error.argtypes = [ctypes.c_void_p]
@@ -130,9 +170,11 @@ class _Inputs:
         g.nx, g.ny, g.nz = nx, ny, nz
         per = geometry.get("periodic", (1, 1, 1))
         bf = geometry.get("body_force", (0.0, 0.0, 0.0))
+        bw = geometry.get("body_force_wave", (0.0, 0.0, 0.0))
         for a in range(3):
             g.periodic[a] = int(per[a])
             g.body_force[a] = float(bf[a])
+            g.body_force_wave[a] = float(bw[a])
         solid = geometry.get("solid")
         self.solid = None if solid is None else np.ascontiguousarray(np.asarray(solid, np.uint8).reshape(-1))
         g.solid = None if self.solid is None else self.solid.ctypes.data_as(_U8)
@@ -158,6 +200,12 @@ class _Inputs:
                     arr[a] = float(v[a])
             elif k in ("bin_capacity", "max_neighbors"):
                 setattr(p, k, int(v))
+            elif k == "precision":
+                p.precision = PRECISION[v] if isinstance(v, str) else int(v)
+            elif k == "rounding":
+                p.rounding = ROUNDING[v] if isinstance(v, str) else int(v)
+            elif k == "seed":
+                p.seed = int(v) & 0xffffffffffffffff
             elif k == "stream":
                 continue
             else:
@@ -212,7 +260,8 @@ def rbc_stats(h):
     s = rbc_stats_t()
     code = load().rbc_stats(h, ctypes.byref(s))
     out = dict(step=int(s.step), mass=s.mass, p_fluid=np.array(s.p_fluid[:]), p_cells=np.array(s.p_cells[:]),
-               max_u=s.max_u, gb_clamps=int(s.gb_clamps), unstable=int(s.unstable), overflow=int(s.overflow))
+               max_u=s.max_u, gb_clamps=int(s.gb_clamps), unstable=int(s.unstable), overflow=int(s.overflow),
+               power=s.power)
     _check(code, h)
     return out
 
@@ -242,6 +291,13 @@ def rbc_kernel_times(h):
     cnt = np.zeros(2, dtype=np.int64)
     _check(load().rbc_kernel_times(h, _dp(ms), cnt.ctypes.data_as(_I64)), h)
     return ms, cnt
+
+
+def rbc_autotune(h, steps_per_trial: int = 20):
+    r = rbc_tune_report()
+    _check(load().rbc_autotune(h, int(steps_per_trial), ctypes.byref(r)), h)
+    return dict(stages=r.stages, ctas_per_sm=r.ctas_per_sm, ms_per_step=r.ms_per_step,
+                default_ms_per_step=r.default_ms_per_step, trials=r.trials)
 
 
 def rbc_launches_per_step(h) -> int:
@@ -314,11 +370,119 @@ class Solver:
     def launches_per_step(self):
         return rbc_launches_per_step(self.handle)
 
+    def autotune(self, steps_per_trial=20):
+        return rbc_autotune(self.handle, steps_per_trial)
+
     def close(self):
         if getattr(self, "handle", None):
             rbc_free(self.handle)
             self.handle = None
         self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# request server
+# ---------------------------------------------------------------------------
+
+def rbc_server_create(arena_ptr: int, arena_bytes: int, max_active: int, tick_steps: int):
+    h = ctypes.c_void_p()
+    _check(load().rbc_server_create(ctypes.c_void_p(arena_ptr), ctypes.c_size_t(arena_bytes), int(max_active),
+                                    int(tick_steps), ctypes.byref(h)))
+    return h
+
+
+def rbc_server_submit(srv, geometry, cells, params, steps: int, average_from: int = 0, tag: int = 0):
+    ins = _Inputs(geometry, cells, params, None)
+    r = rbc_request()
+    r.geom, r.cells, r.params = ins.geom, ins.cells, ins.params
+    r.steps, r.average_from, r.tag = int(steps), int(average_from), int(tag)
+    _check(load().rbc_server_submit(srv, ctypes.byref(r)))  # inputs are copied by the server
+
+
+def rbc_server_poll(srv):
+    a, q = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().rbc_server_poll(srv, ctypes.byref(a), ctypes.byref(q)))
+    return a.value, q.value
+
+
+def rbc_server_results(srv, max_results: int = 256):
+    buf = (rbc_result * max_results)()
+    n = ctypes.c_int(0)
+    _check(load().rbc_server_results(srv, buf, max_results, ctypes.byref(n)))
+    out = []
+    for k in range(n.value):
+        r = buf[k]
+        out.append(dict(tag=int(r.tag), status=int(r.status), steps=int(r.steps), samples=int(r.samples),
+                        mean_power=r.mean_power, mean_p_fluid=np.array(r.mean_p_fluid[:]), max_u=r.max_u,
+                        t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done,
+                        workspace_bytes=int(r.workspace_bytes)))
+    return out
+
+
+def rbc_server_clock(srv) -> float:
+    return float(load().rbc_server_clock(srv))
+
+
+def rbc_server_free(srv):
+    if srv:
+        load().rbc_server_free(srv)
+
+
+class Server:
+    """Continuous-batching request server on the current CUDA device.
+
+    The arena (``arena_bytes`` of device memory from PyTorch's allocator) is
+    lent to the server, which carves each admitted solve's workspace from it.
+    ``submit`` queues a solve; ``poll`` advances the server one round (never
+    blocks); ``results`` drains finished solves."""
+
+    def __init__(self, arena_bytes, max_active=32, tick_steps=100, device=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("the RBC server needs a CUDA GPU")
+        load()
+        self.device = torch.device("cuda" if device is None else device)
+        with torch.cuda.device(self.device):
+            self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.device)
+            self.handle = rbc_server_create(self.arena.data_ptr(), int(arena_bytes), max_active, tick_steps)
+
+    def submit(self, geometry, cells, params, steps, average_from=0, tag=0):
+        rbc_server_submit(self.handle, geometry, cells, params, steps, average_from, tag)
+
+    def poll(self):
+        return rbc_server_poll(self.handle)
+
+    def results(self, max_results=256):
+        return rbc_server_results(self.handle, max_results)
+
+    def clock(self):
+        return rbc_server_clock(self.handle)
+
+    def drain(self, sleep_s=0.0):
+        """Poll until nothing is active or queued; returns all results."""
+        import time
+        out = []
+        while True:
+            a, q = self.poll()
+            out += self.results()
+            if a == 0 and q == 0:
+                break
+            if sleep_s:
+                time.sleep(sleep_s)
+        return out + self.results()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rbc_server_free(self.handle)
+            self.handle = None
+        self.arena = None
 
     def __del__(self):
         try:

@@ -47,11 +47,22 @@ def params(**overrides):
 # geometry
 # ---------------------------------------------------------------------------
 
-def periodic_box(nx, ny=None, nz=None, body_force=(0.0, 0.0, 0.0)):
+def periodic_box(nx, ny=None, nz=None, body_force=(0.0, 0.0, 0.0), body_force_wave=(0.0, 0.0, 0.0)):
+    """Fully periodic box; ``body_force_wave`` is the amplitude of a force
+    density profile A sin(2 pi y / ny) added to the uniform ``body_force``
+    (a Kolmogorov flow)."""
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     return dict(nx=nx, ny=ny, nz=nz, periodic=(1, 1, 1), solid=None,
-                body_force=tuple(float(b) for b in body_force))
+                body_force=tuple(float(b) for b in body_force),
+                body_force_wave=tuple(float(b) for b in body_force_wave))
+
+
+def kolmogorov_amplitude(ny, rate, nu=1.0 / 6.0):
+    """Amplitude A of the force A sin(k y), k = 2 pi / ny, whose steady plasma
+    flow u_x = A / (nu k^2) sin(k y) has the peak shear rate ``rate``."""
+    k = 2.0 * math.pi / ny
+    return nu * k * rate
 
 
 def plane_channel(nx, ny, nz, body_force=(0.0, 0.0, 0.0)):
@@ -224,32 +235,121 @@ def channel_workload(nx=64, ny=64, nz=256, ncells=3650, body_force=(5.376e-7, 0.
     return geom, cells_dict(pos, quat), params(**pover)
 
 
-def tube_workload(n=256, radius=120.0, ncells=51846, body_force=(0.0, 0.0, 0.0),
-                  seed=SEED_BASE + 3, wall_clearance=6.0, tilt_max_deg=5.0, **pover):
-    """Straight tube along z with cells in slots inside radius - clearance;
-    short axis along z (slot pitch >= 3.37), in-plane pitch >= 8.4."""
+def tube_workload(n=256, radius=120.0, ncells=51846, body_force=None, seed=SEED_BASE + 3,
+                  wall_clearance=6.0, pitch=8.3, zpitch=3.3, tilt_max_deg=1.5, **pover):
+    """Straight tube of the given radius along z in an n^3 box (periodic in
+    z) with cells in the slots of a lattice: hexagonal of pitch ``pitch`` in
+    the cross-section, inside radius - ``wall_clearance`` (the Gay-Berne
+    contact distance of a cell edge-on to a wall particle is 5.7), and
+    n / floor(n / zpitch) along z; short axis along z, a random spin about it
+    and a tilt of at most ``tilt_max_deg``.  Default: radius 120 in 256^3 (11,582,464
+    fluid nodes) with 51,846 cells, hematocrit 0.45 of the lumen, driven by
+    the axial force density 2 nu0 rate / radius that gives a wall shear rate
+    1e-4 per step in plain plasma (nu0 = 1/6), the periodic stand-in for a
+    pressure drop."""
     rng = np.random.default_rng(seed)
+    if body_force is None:
+        body_force = (0.0, 0.0, 2.0 * (1.0 / 6.0) * 1e-4 / radius)
     geom = tube(n, radius, body_force=body_force)
     c = (n - 1) / 2.0
     r_in = radius - wall_clearance
-    xs = slot_centres(n, 8.4, False, c - r_in, c + r_in)
-    zs = slot_centres(n, 3.37, True)
-    X, Y = np.meshgrid(xs, xs, indexing="ij")
-    inside = (X - c) ** 2 + (Y - c) ** 2 <= r_in * r_in
-    xy = np.stack([X[inside], Y[inside]], axis=1)
-    slots = np.concatenate([np.column_stack([np.repeat(xy, len(zs), axis=0),
-                                             np.tile(zs, len(xy))])])
+    dy = pitch * math.sqrt(3.0) / 2.0
+    xy = []
+    k = int(math.ceil(r_in / pitch)) + 1
+    for i, y in enumerate(np.arange(-r_in, r_in + 1e-9, dy)):
+        xs = np.arange(-k, k + 1) * pitch + 0.5 * pitch * (i % 2)  # odd rows shifted half a pitch
+        for x in xs[xs * xs + y * y <= r_in * r_in]:
+            xy.append((c + x, c + y))
+    xy = np.array(xy)
+    zs = slot_centres(n, zpitch, True)
+    slots = np.column_stack([np.repeat(xy, len(zs), axis=0), np.tile(zs, len(xy))])
     if ncells > len(slots):
         raise RuntimeError(f"{ncells} cells do not fit in {len(slots)} tube slots")
     pick = np.sort(rng.choice(len(slots), size=ncells, replace=False))
-    pos = slots[pick] + (rng.random((ncells, 3)) * 2.0 - 1.0) * np.array([0.04, 0.04, 0.05])
+    pos = slots[pick] + (rng.random((ncells, 3)) * 2.0 - 1.0) * np.array([0.04, 0.04, 0.03])
     pos = _wrap(pos, geom)
     base = np.array([1.0, 0.0, 0.0, 0.0])
     quat = tilted_quaternions(rng, ncells, base, math.radians(tilt_max_deg))
     return geom, cells_dict(pos, quat), params(**pover)
 
 
+def tube_hematocrit(geom, ncells, semi_axes=(4.0, 4.0, 1.5)):
+    """Cell volume fraction of the fluid nodes (the lumen)."""
+    a = semi_axes
+    return ncells * 4.0 / 3.0 * math.pi * a[0] * a[1] * a[2] / fluid_count(geom)
+
+
 def hematocrit(geom, ncells, semi_axes=(4.0, 4.0, 1.5)):
     V = geom["nx"] * geom["ny"] * geom["nz"]
     a = semi_axes
     return ncells * 4.0 / 3.0 * math.pi * a[0] * a[1] * a[2] / V
+
+
+# ---------------------------------------------------------------------------
+# request stream of the batched-serving workload
+# ---------------------------------------------------------------------------
+
+SERVING_BOXES = ((32, 32, 32), (48, 48, 48), (64, 64, 128), (96, 96, 96))
+
+
+def slot_lattice_cells(rng, geom, ncells, dense, wall_clearance=6.0, tilt_max_deg=None):
+    """Cells in the slots of a lattice, short axis along x: pitches (3.37,
+    8.4, 8.4) leave every pair out of the Gay-Berne range (tilt up to 5
+    degrees), (3.05, 8.05, 8.05) hold up to hematocrit 0.5 with neighbours
+    inside the range but not overlapping (tilt up to 0.5 degrees, which
+    moves a rim by 0.035 of the 0.05 gap).  Centres stay ``wall_clearance``
+    from solid y planes.  Returns as many cells as there are slots when
+    ``ncells`` is larger."""
+    if tilt_max_deg is None:
+        tilt_max_deg = 0.5 if dense else 5.0
+    px, pyz = (3.05, 8.05) if dense else (3.37, 8.4)
+    nx, ny, nz = geom["nx"], geom["ny"], geom["nz"]
+    xs = slot_centres(nx, px, True)
+    if geom["periodic"][1]:
+        ys = slot_centres(ny, pyz, True)
+    else:
+        ys = slot_centres(ny, pyz, False, wall_clearance, (ny - 1) - wall_clearance)
+    zs = slot_centres(nz, pyz, True)
+    n = min(ncells, len(xs) * len(ys) * len(zs))
+    pos = _wrap(place_slots(rng, (xs, ys, zs), n, (0.02, 0.02, 0.02)), geom)
+    base = axis_angle_quat([0.0, 1.0, 0.0], math.pi / 2.0)
+    quat = tilted_quaternions(rng, n, base, math.radians(tilt_max_deg))
+    return cells_dict(pos, quat)
+
+
+def serving_request(rng, box=None, walled=None, hematocrit=None, rate=None, steps=None,
+                    precision="f16", step_scale=1.0):
+    """One request of the serving stream: a periodic box driven by the
+    Kolmogorov force (peak shear rate ``rate``) or a walled channel along x
+    driven by a uniform force (wall shear rate ``rate``); hematocrit of the
+    fluid volume; 2,000-10,000 steps (times ``step_scale``).  Unset fields
+    are drawn: box from SERVING_BOXES, walled with probability 1/2,
+    hematocrit U[0.1, 0.5], rate log-uniform in [1e-5, 1e-3]."""
+    if box is None:
+        box = SERVING_BOXES[int(rng.integers(len(SERVING_BOXES)))]
+    if walled is None:
+        walled = bool(rng.random() < 0.5)
+    if hematocrit is None:
+        hematocrit = float(rng.uniform(0.1, 0.5))
+    if rate is None:
+        rate = float(10.0 ** rng.uniform(-5.0, -3.0))
+    if steps is None:
+        steps = int(rng.integers(2000, 10001))
+    steps = max(2, int(round(steps * step_scale / 2.0)) * 2)
+    nx, ny, nz = box
+    nu = 1.0 / 6.0
+    if walled:
+        geom = plane_channel(nx, ny, nz, body_force=(2.0 * nu * rate / (ny - 2), 0.0, 0.0))
+    else:
+        geom = periodic_box(nx, ny, nz, body_force_wave=(kolmogorov_amplitude(ny, rate, nu), 0.0, 0.0))
+    ncells = int(round(hematocrit * fluid_count(geom) / CELL_VOLUME))
+    cells = slot_lattice_cells(rng, geom, ncells, dense=hematocrit > 0.35)
+    info = dict(box=box, walled=walled, hematocrit=len(cells["pos"]) * CELL_VOLUME / fluid_count(geom),
+                rate=rate, steps=steps, ncells=len(cells["pos"]))
+    return geom, cells, params(precision=precision), steps, info
+
+
+def serving_stream(n, seed=SEED_BASE + 4, precision="f16", step_scale=1.0):
+    """The first n requests of the seeded serving stream."""
+    rng = np.random.default_rng(seed)
+    return [serving_request(rng, precision=precision, step_scale=step_scale) for _ in range(n)]

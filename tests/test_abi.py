@@ -45,10 +45,28 @@ def test_default_params_are_the_papers(lib):
 
 
 def test_struct_layouts_match_header(lib):
-    assert ctypes.sizeof(rbc.rbc_geometry) == 24 + 8 + 24
+    assert ctypes.sizeof(rbc.rbc_geometry) == 24 + 8 + 24 + 24
     assert ctypes.sizeof(rbc.rbc_cells) == 8 + 4 * 8
-    assert ctypes.sizeof(rbc.rbc_stats_t) == 8 * 10 + 8
+    assert ctypes.sizeof(rbc.rbc_stats_t) == 8 * 10 + 8 + 8
     assert rbc.rbc_params.stream.offset == ctypes.sizeof(rbc.rbc_params) - 8
+    # int precision, int rounding, uint64_t seed, void *stream close the struct
+    assert rbc.rbc_params.seed.offset == ctypes.sizeof(rbc.rbc_params) - 16
+    assert rbc.rbc_params.rounding.offset == rbc.rbc_params.seed.offset - 4
+    assert rbc.rbc_params.precision.offset == rbc.rbc_params.seed.offset - 8
+
+
+def test_reduced_precision_halves_population_bytes(lib):
+    g, c, p = wl.channel_workload()
+    Np = (64 * 64 * 256 + 63) // 64 * 64
+    s32 = rbc.rbc_workspace_size(g, c, p)
+    for prec in ("f16", "bf16"):
+        s16 = rbc.rbc_workspace_size(g, c, dict(p, precision=prec))
+        assert abs((s32 - s16) - 2 * 19 * 2 * Np) <= 2 * 256
+    with pytest.raises(rbc.RbcError) as e:
+        rbc.rbc_workspace_size(g, c, dict(p, precision=3))
+    assert e.value.code == rbc.RBC_EINVAL
+    with pytest.raises(rbc.RbcError):
+        rbc.rbc_workspace_size(g, c, dict(p, precision="f16", rounding=2))
 
 
 def test_workspace_size_scales_with_problem(lib):

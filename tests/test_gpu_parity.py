@@ -227,3 +227,23 @@ def test_full_size_channel_sampled_against_oracle():
     cells["vel"] = np.random.default_rng(2).normal(size=(len(cells["pos"]), 3)) * 1e-3
     r = _compare(geom, cells, params, 6)
     print("channel full size:", r)
+
+
+def test_autotuned_launch_shape_keeps_parity():
+    """The autotuner times the lattice pass's launch shapes on the live
+    solve; whatever it picks, the results stay those of the oracle (a node's
+    update does not depend on which CTA computes it)."""
+    geom, cells, params = wl.box_workload()
+    s = _solver(geom, cells, params)
+    rep = s.autotune(4)
+    assert rep["trials"] >= 2 and rep["ms_per_step"] <= rep["default_ms_per_step"]
+    s.step(6)
+    n = s.stats()["step"]
+    assert n == 4 * 2 * (rep["trials"] + 1) + 6
+    o = orc.Oracle(geom, cells, params)
+    o.step(n)
+    f = s.fields()
+    _, u_o, _ = o.fields()
+    assert rel_l2(f["u"], u_o) <= TOL
+    s.close()
+    o.close()

@@ -93,9 +93,10 @@ def test_neighbor_pairs_match_kdtree():
     assert len(ref) > 50 and np.array_equal(got, ref)
 
 
-def _gb_check(geom, cells, params, max_cells=None):
-    """Number of cell-cell and cell-wall pairs with a non-zero Gay-Berne
-    energy (via the oracle's pair) among the first max_cells cells."""
+def _gb_check(geom, cells, params, max_cells=None, level=0.0):
+    """Number of cell-cell and cell-wall pairs whose Gay-Berne energy (via the
+    oracle's pair) exceeds ``level`` among the first max_cells cells (level 0:
+    any interaction; level eps0: an overlap, reduced distance below 1)."""
     pos = cells["pos"]
     n = len(pos) if max_cells is None else min(max_cells, len(pos))
     Q = np.array([orc.quat_to_Q(q) for q in cells["quat"]])
@@ -114,7 +115,7 @@ def _gb_check(geom, cells, params, max_cells=None):
             if geom["periodic"][k]:
                 d[k] -= dims[k] * np.round(d[k] / dims[k])
         u, F, *_ = orc.gb_pair(d, A[i], A[j], smin, params["eps0"])
-        hits += u > 0
+        hits += u > level
     # walls: distance to the nearest solid node must exceed the wall range
     if geom["solid"] is not None:
         s = geom["solid"]
@@ -129,7 +130,7 @@ def _gb_check(geom, cells, params, max_cells=None):
                     if geom["periodic"][k]:
                         d[k] -= dims[k] * np.round(d[k] / dims[k])
                 u, *_ = orc.gb_pair(d, A[i], Aw, params["sigma_min_wall"], params["eps0"])
-                hits += u > 0
+                hits += u > level
     return hits
 
 
@@ -145,6 +146,22 @@ def test_channel_workload_cells_do_not_interact_initially():
     assert _gb_check(geom, cells, params, max_cells=3650) == 0
     # every centre stays clear of the walls
     assert cells["pos"][:, 1].min() >= 5.9 and cells["pos"][:, 1].max() <= 57.1
+
+
+def test_tube_workload_dense_and_without_overlaps():
+    """Radius 120 in 256^3: 11,582,464 fluid nodes, 51,846 cells at
+    hematocrit 0.45 of the lumen.  The hexagonal slot lattice is denser than
+    the Gay-Berne range (neighbours in a cross-section repel weakly at t = 0)
+    but no two cells and no cell and wall overlap: every reduced distance
+    exceeds 1 (energy below eps0).  Checked on the cells of the first 60
+    slot columns, which include the ones next to the wall."""
+    geom, cells, params = wl.tube_workload()
+    n = len(cells["pos"])
+    assert n == 51846 and wl.fluid_count(geom) == 11582464
+    assert abs(wl.tube_hematocrit(geom, n) - 0.45) < 1e-3
+    r = np.hypot(cells["pos"][:, 0] - 127.5, cells["pos"][:, 1] - 127.5)
+    assert r.max() <= 120 - 5.9
+    assert _gb_check(geom, cells, params, max_cells=4000, level=params["eps0"]) == 0
 
 
 def test_candidate_radii_bound_the_interaction_range():

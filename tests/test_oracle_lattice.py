@@ -184,3 +184,36 @@ def test_walls_conserve_mass():
     for _ in range(15):
         orc.lb_pass(dims, solid, f, None, np.full(N, 0.8))
     assert abs(f.sum() - m0) < 1e-12 * m0
+
+
+def _kolmogorov(L, A, steps):
+    from paper_1107_4889_gb300 import workloads as wl
+    geom = wl.periodic_box(1, L, 1, body_force_wave=(A, 0.0, 0.0))
+    o = orc.Oracle(geom, None, wl.params())
+    o.step(steps)
+    _, u, _ = o.fields()
+    b = o.budget()
+    o.close()
+    return u, b
+
+
+def test_kolmogorov_steady_state_and_work_rate():
+    """Force A sin(k y) x in a periodic box (k = 2 pi / L): the steady
+    Navier-Stokes flow is u_x = A / (nu k^2) sin(k y) with nu = (T - 1/2)/3;
+    the lattice error of this mode at tau = 1 falls faster than k^2 (1e-4 at
+    L = 16, 6e-6 at L = 32).  The work rate of the force, sum_x G(x).u(x),
+    is A^2 L / (2 nu k^2) there."""
+    nu = (1.0 - 0.5) / 3.0
+    A = 1e-6
+    errs = []
+    for L in (16, 32):
+        k = 2 * np.pi / L
+        U = A / (nu * k * k)
+        u, b = _kolmogorov(L, A, 30 * int(1.0 / (nu * k * k)))
+        prof = U * np.sin(k * np.arange(L))
+        err = np.abs(u[:, 0] - prof).max() / U
+        errs.append(err)
+        assert np.abs(u[:, 1:]).max() < 1e-9 * U
+        assert abs(b["power"] / (A * A * L / (2 * nu * k * k)) - 1.0) < 2 * err + 1e-6
+        assert abs(b["p_fluid"][0]) < 1e-9 * U * L
+    assert errs[0] < 3e-4 and errs[1] < errs[0] / 8.0
