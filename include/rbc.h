@@ -263,13 +263,21 @@ int rbc_neighbors_noalloc(const double *pos, int n, int nx, int ny, int nz, cons
  *
  * Not a step of the paper's method: it serves many rheology / vessel solves
  * (the use Sec. 4 puts the model to) on one GPU.  Requests of different box
- * sizes, hematocrits and drives are queued, admitted as device memory and
- * slots free up, and advanced concurrently, each on its own stream in ticks
- * of tick_steps steps captured as one CUDA graph (coupled steps followed by
- * the budget reduction, which accumulates the time averages on the device).
- * Device memory comes from one arena the caller lends: each admitted solve
- * takes rbc_workspace_size bytes of it (first fit) and returns them when it
- * finishes.  Results are the time-averaged budgets of each solve.
+ * sizes, hematocrits and drives are queued and admitted as device memory and
+ * slots free up (rbc_init runs on a worker thread).  Admitted solves of one
+ * class -- storage type, walls, cells, stress output, shape box -- form a
+ * pack that advances in ticks of tick_steps coupled steps captured as one
+ * CUDA graph: each kernel of the step is launched once for all members of
+ * the pack, over device tables of their arguments with per-solve block and
+ * batch offsets (the lattice pass is one persistent launch over all their
+ * row batches), followed by each member's budget reduction, which adds to
+ * its time averages on the device.  Members join and leave between ticks;
+ * the last (steps mod tick_steps) steps of a solve, and solves that cannot be packed
+ * (no cells, or rows not a multiple of 16 bytes), run on a stream of their
+ * own.  Device memory comes from one arena the caller lends: each admitted
+ * solve takes rbc_workspace_size bytes of it (first fit) and returns them
+ * when it finishes; each pack class takes a small table region.  Results are
+ * the time-averaged budgets of each solve.
  * ------------------------------------------------------------------------ */
 typedef struct rbc_server rbc_server;
 

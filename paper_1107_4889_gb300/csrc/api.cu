@@ -493,6 +493,9 @@ int capture_ticks(rbc_handle *h, int64_t steps, long long average_from, cudaGrap
 
 void advance_steps(rbc_handle *h, int64_t steps) { h->step += steps; }
 
+const Dev &handle_dev(const rbc_handle *h) { return h->d; }
+const Params &handle_params(const rbc_handle *h) { return h->P.p; }
+
 int read_accum(rbc_handle *h, double accum[8], int flags[8])
 {
     RBC_CU(cudaMemcpyAsync(accum, h->d.accum, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

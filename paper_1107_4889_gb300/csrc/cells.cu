@@ -22,6 +22,7 @@
 //             over the same list with atomics (Sec. 2.2, Eq.
 //             enhance-viscosity).
 #include <algorithm>
+#include <cstring>
 #include <utility>
 
 #include "internal.h"
@@ -94,9 +95,9 @@ struct BinArgs {
     double bs[3], a2[3];
 };
 
-__global__ void __launch_bounds__(kBinThreads) k_bin(BinArgs g)
+__device__ __forceinline__ void bin_body(const BinArgs &g, int blk)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blk * blockDim.x + threadIdx.x;
     if (i >= g.nc) return;
     double Rd[3];
     int b[3];
@@ -134,6 +135,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(BinArgs g)
     g.Af[6 * i + 5] = (float)S.yz;
 
 }
+
+__global__ void __launch_bounds__(kBinThreads) k_bin(BinArgs g) { bin_body(g, blockIdx.x); }
 
 // ---------------------------------------------------------------------------
 // k_gb
@@ -216,7 +219,7 @@ __device__ __forceinline__ bool gb_maybe_in_range(const float d[3], const float 
     return !(rho > cut);
 }
 
-__global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g)
+__device__ __forceinline__ void gb_body(const GbArgs &g, int blk)
 {
     __shared__ int s_cand[kGbWarps][kMaxNbr];
     __shared__ int s_sort[kGbWarps][kMaxNbr];
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g)
     __shared__ double s_res[kGbWarps * kGbQueue][6];
     __shared__ int s_clamped;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int i = blockIdx.x * kGbWarps + wid;
+    const int i = blk * kGbWarps + wid;
     if (threadIdx.x == 0) s_clamped = 0;
     int qn = 0;
     if (i < g.nc) {  // uniform across the warp
@@ -407,7 +410,7 @@ __global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g)
     for (int e = threadIdx.x; e < P; e += blockDim.x) {
         int c = 0;
         while (c + 1 < kGbWarps && s_qpre[c + 1] <= e) ++c;
-        const int ci = blockIdx.x * kGbWarps + c;
+        const int ci = blk * kGbWarps + c;
         const int v = s_q[c][e - s_qpre[c]];
         double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
         int clamped = 0;
@@ -446,6 +449,8 @@ __global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g)
     }
     if (threadIdx.x == 0 && s_clamped) atomicAdd(g.clamps, (unsigned long long)s_clamped);
 }
+
+__global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g) { gb_body(g, blockIdx.x); }
 
 // ---------------------------------------------------------------------------
 // Shape lists
@@ -534,11 +539,11 @@ __device__ __forceinline__ int find_row(const unsigned *words, int n, int t)
     return k0;
 }
 
-__global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc)
+__device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk)
 {
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * kWtWarps + warp;
+    const int i = blk * kWtWarps + warp;
     if (i >= nc) return;
     const int rows_cap = a.box_dim * a.box_dim;
     unsigned *srow = reinterpret_cast<unsigned *>(smem + (size_t)warp * a.box_pad);
@@ -722,6 +727,8 @@ __global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc)
         if (run > a.sp_cap) atomicOr(&a.flags[FLAG_OVERFLOW], OVF_BOX);
     }
 }
+
+__global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc) { weights_body(a, nc, blockIdx.x); }
 
 // ---------------------------------------------------------------------------
 // Sampling over the cell's shape list (one warp per cell):
@@ -993,10 +1000,10 @@ __device__ __forceinline__ bool rigid_update(const RigidArgs &a, int i, float Sf
 // warp goes straight from its own update to its own spread.
 // ---------------------------------------------------------------------------
 template <bool ALPHA>
-__global__ void __launch_bounds__(32 * kCellWarps) k_cells(ShapeArgs a, RigidArgs ra, int nc)
+__device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &ra, int nc, int blk)
 {
     const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kCellWarps + (threadIdx.x >> 5);
+    const int i = blk * kCellWarps + (threadIdx.x >> 5);
     if (i >= nc) return;
     const int n = a.sp_cnt[i];
     const float S = a.sp_S[i];
@@ -1027,6 +1034,12 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_cells(ShapeArgs a, RigidArg
             if (v[j].x > 0.f) atomicAdd(&a.theta[g[j]], 1.0f - powf(1.0f - v[j].x, a.kappa));
         }
     }
+}
+
+template <bool ALPHA>
+__global__ void __launch_bounds__(32 * kCellWarps) k_cells(ShapeArgs a, RigidArgs ra, int nc)
+{
+    cells_body<ALPHA>(a, ra, nc, blockIdx.x);
 }
 
 ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
@@ -1064,10 +1077,71 @@ ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
 
 }  // namespace
 
-void launch_bin(const Dev &d, const Params &p, cudaStream_t s)
+// ---------------------------------------------------------------------------
+// Packed launches: one launch of each per-cell kernel over the cells of
+// several solves (the request server's packs).  Block b belongs to the solve
+// i with start[i] <= b < start[i + 1] (found by binary search) and runs the
+// kernel body with the solve's arguments from the table and its local block
+// index.
+// ---------------------------------------------------------------------------
+struct CellPackEntry {
+    BinArgs bin;
+    GbArgs gb;
+    ShapeArgs shape[2];  // shape-list buffer 0 / 1
+    RigidArgs rigid;
+    int *bin_count;
+    int nbins;
+};
+
+__device__ __forceinline__ int cell_pack_find(const int *start, int n, int b)
 {
-    if (d.nc == 0) return;
-    cudaMemsetAsync(d.bin_count, 0, sizeof(int) * d.nbins, s);
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_binclear_packed(const CellPackEntry *tab, const int *start, int ninst)
+{
+    const int i = cell_pack_find(start, ninst, blockIdx.x);
+    const int k = (blockIdx.x - start[i]) * blockDim.x + threadIdx.x;
+    if (k < tab[i].nbins) tab[i].bin_count[k] = 0;
+}
+
+__global__ void __launch_bounds__(kBinThreads) k_bin_packed(const CellPackEntry *tab, const int *start, int ninst)
+{
+    const int i = cell_pack_find(start, ninst, blockIdx.x);
+    bin_body(tab[i].bin, blockIdx.x - start[i]);
+}
+
+__global__ void __launch_bounds__(32 * kGbWarps) k_gb_packed(const CellPackEntry *tab, const int *start, int ninst)
+{
+    const int i = cell_pack_find(start, ninst, blockIdx.x);
+    gb_body(tab[i].gb, blockIdx.x - start[i]);
+}
+
+__global__ void __launch_bounds__(32 * kWtWarps)
+    k_weights_packed(const CellPackEntry *tab, const int *start, int ninst, int buf)
+{
+    const int i = cell_pack_find(start, ninst, blockIdx.x);
+    weights_body(tab[i].shape[buf], tab[i].rigid.nc, blockIdx.x - start[i]);
+}
+
+template <bool ALPHA>
+__global__ void __launch_bounds__(32 * kCellWarps)
+    k_cells_packed(const CellPackEntry *tab, const int *start, int ninst, int buf)
+{
+    const int i = cell_pack_find(start, ninst, blockIdx.x);
+    cells_body<ALPHA>(tab[i].shape[buf], tab[i].rigid, tab[i].rigid.nc, blockIdx.x - start[i]);
+}
+
+static BinArgs bin_args(const Dev &d, const Params &p)
+{
     BinArgs g;
     g.R = d.R;
     g.q = d.q;
@@ -1085,12 +1159,18 @@ void launch_bin(const Dev &d, const Params &p, cudaStream_t s)
         g.bs[a] = d.bin_size[a];
         g.a2[a] = p.a2[a];
     }
-    launch_prio(k_bin, (d.nc + kBinThreads - 1) / kBinThreads, kBinThreads, 0, s, d.side_prio, g);
+    return g;
 }
 
-void launch_gb(const Dev &d, const Params &p, cudaStream_t s)
+void launch_bin(const Dev &d, const Params &p, cudaStream_t s)
 {
     if (d.nc == 0) return;
+    cudaMemsetAsync(d.bin_count, 0, sizeof(int) * d.nbins, s);
+    launch_prio(k_bin, (d.nc + kBinThreads - 1) / kBinThreads, kBinThreads, 0, s, d.side_prio, bin_args(d, p));
+}
+
+static GbArgs gb_args(const Dev &d, const Params &p)
+{
     GbArgs g;
     g.R = d.R;
     g.A = d.A;
@@ -1138,8 +1218,14 @@ void launch_gb(const Dev &d, const Params &p, cudaStream_t s)
         g.wnb[a] = d.wnb[a];
         g.wbs[a] = (float)d.wbin_size[a];
     }
+    return g;
+}
+
+void launch_gb(const Dev &d, const Params &p, cudaStream_t s)
+{
+    if (d.nc == 0) return;
     const int blocks = (d.nc + kGbWarps - 1) / kGbWarps;
-    launch_prio(k_gb, blocks, 32 * kGbWarps, 0, s, d.side_prio, g);
+    launch_prio(k_gb, blocks, 32 * kGbWarps, 0, s, d.side_prio, gb_args(d, p));
 }
 
 size_t cells_smem_bytes(const Params &p)
@@ -1205,6 +1291,67 @@ void launch_cells(const Dev &d, const Params &p, int buf, cudaStream_t s)
         k_cells<true><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc);
     else
         k_cells<false><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc);
+}
+
+
+// ---------------------------------------------------------------------------
+// Packs (host side)
+// ---------------------------------------------------------------------------
+size_t cell_pack_entry_bytes() { return sizeof(CellPackEntry); }
+
+int cell_pack_blocks(int nc, int nbins, int kind)
+{
+    switch (kind) {
+    case PACK_CLEAR: return (nbins + 255) / 256;
+    case PACK_BIN: return (nc + kBinThreads - 1) / kBinThreads;
+    case PACK_GB: return (nc + kGbWarps - 1) / kGbWarps;
+    case PACK_WEIGHTS: return (nc + kWtWarps - 1) / kWtWarps;
+    default: return (nc + kCellWarps - 1) / kCellWarps;
+    }
+}
+
+void fill_cell_pack_entry(const Dev &d, const Params &p, void *out)
+{
+    CellPackEntry e;
+    std::memset(&e, 0, sizeof e);
+    // the same argument structs the single-solve launches build
+    e.bin = bin_args(d, p);
+    e.gb = gb_args(d, p);
+    e.shape[0] = shape_args(d, p, 0);
+    e.shape[1] = shape_args(d, p, 1);
+    e.rigid = rigid_args(d, p);
+    e.bin_count = d.bin_count;
+    e.nbins = d.nbins;
+    std::memcpy(out, &e, sizeof e);
+}
+
+void launch_cells_packed(const CellPackDesc &k, int buf, bool alpha, cudaStream_t s)
+{
+    const CellPackEntry *tab = static_cast<const CellPackEntry *>(k.tab);
+    if (alpha)
+        k_cells_packed<true><<<k.blocks[PACK_CELLS], 32 * kCellWarps, 0, s>>>(tab, k.start[PACK_CELLS], k.ninst, buf);
+    else
+        k_cells_packed<false><<<k.blocks[PACK_CELLS], 32 * kCellWarps, 0, s>>>(tab, k.start[PACK_CELLS], k.ninst, buf);
+}
+
+void launch_bin_packed(const CellPackDesc &k, int prio, cudaStream_t s)
+{
+    const CellPackEntry *tab = static_cast<const CellPackEntry *>(k.tab);
+    launch_prio(k_binclear_packed, k.blocks[PACK_CLEAR], 256, 0, s, prio, tab, k.start[PACK_CLEAR], k.ninst);
+    launch_prio(k_bin_packed, k.blocks[PACK_BIN], kBinThreads, 0, s, prio, tab, k.start[PACK_BIN], k.ninst);
+}
+
+void launch_gb_packed(const CellPackDesc &k, int prio, cudaStream_t s)
+{
+    const CellPackEntry *tab = static_cast<const CellPackEntry *>(k.tab);
+    launch_prio(k_gb_packed, k.blocks[PACK_GB], 32 * kGbWarps, 0, s, prio, tab, k.start[PACK_GB], k.ninst);
+}
+
+void launch_weights_packed(const CellPackDesc &k, const Params &p, int buf, int prio, cudaStream_t s)
+{
+    const CellPackEntry *tab = static_cast<const CellPackEntry *>(k.tab);
+    launch_prio(k_weights_packed, k.blocks[PACK_WEIGHTS], 32 * kWtWarps, cells_smem_bytes(p), s, prio, tab,
+                k.start[PACK_WEIGHTS], k.ninst, buf);
 }
 
 }  // namespace rbc

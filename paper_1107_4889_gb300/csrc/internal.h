@@ -116,7 +116,39 @@ void launch_budget(const Dev &d, const Params &p, int parity, cudaStream_t s, bo
                    long long from = 0);
 int budget_blocks_for(int N);
 
+// Packs of solves of one class (request server): device tables of per-solve
+// kernel arguments; start[kind] (device, ninst + 1 ints) is the first block
+// of each solve in the packed launch of that kind, blocks[kind] the total.
+enum { PACK_CLEAR = 0, PACK_BIN = 1, PACK_GB = 2, PACK_WEIGHTS = 3, PACK_CELLS = 4, PACK_KINDS = 5 };
+struct CellPackDesc {
+    const void *tab;  // ninst CellPackEntry (cells.cu)
+    const int *start[PACK_KINDS];
+    int blocks[PACK_KINDS];
+    int ninst;
+};
+struct LbPackDesc {
+    const void *tab;     // ninst LbPackEntry (lb.cu)
+    const int *bstart;   // ninst + 1: first batch of each solve
+    int total, ninst;    // batches
+    int *work;           // 2 ints, zero between launches
+    int grid, stages, stage_bytes;
+    size_t smem;
+};
+
+// lb.cu (packs)
+size_t lb_pack_entry_bytes();
+bool fill_lb_pack_entry(const Dev &d, const Params &p, void *out, int *nbatches, int *stage_bytes);
+bool prepare_lb_pack(const Dev &d0, LbPackDesc &k);  // sets grid, stages, smem from stage_bytes, total
+void launch_lb_packed(const Dev &d0, const LbPackDesc &k, int parity, cudaStream_t s);
+
 // cells.cu
+size_t cell_pack_entry_bytes();
+int cell_pack_blocks(int nc, int nbins, int kind);
+void fill_cell_pack_entry(const Dev &d, const Params &p, void *out);
+void launch_cells_packed(const CellPackDesc &k, int buf, bool alpha, cudaStream_t s);
+void launch_bin_packed(const CellPackDesc &k, int prio, cudaStream_t s);
+void launch_gb_packed(const CellPackDesc &k, int prio, cudaStream_t s);
+void launch_weights_packed(const CellPackDesc &k, const Params &p, int buf, int prio, cudaStream_t s);
 void launch_bin(const Dev &d, const Params &p, cudaStream_t s);
 void launch_gb(const Dev &d, const Params &p, cudaStream_t s);
 void launch_weights(const Dev &d, const Params &p, int buf, cudaStream_t s);
@@ -127,6 +159,8 @@ void prepare_cells(const Params &p);
 // api.cu, for the request server (serve.cu)
 int capture_ticks(rbc_handle_t *h, int64_t steps, long long average_from, cudaGraphExec_t *out);
 void advance_steps(rbc_handle_t *h, int64_t steps);
+const Dev &handle_dev(const rbc_handle_t *h);
+const Params &handle_params(const rbc_handle_t *h);
 int read_accum(rbc_handle_t *h, double accum[8], int flags[8]);
 void set_thread_error(const char *msg);
 

@@ -16,6 +16,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 #include "internal.h"
@@ -436,6 +438,105 @@ struct StageLayout {
     int stages;      // buffers in the ring (2 .. kMaxStages)
 };
 
+// Producer side of one batch (rows y0 .. y0 + nb - 1 at one z of the
+// lattice `a`): the warp issues the bulk copies of the staged planes into
+// `base` (population plane k, batch row b at (k * B + b) * nx elements; the
+// 4-byte planes after the 19 population planes), completing on `bar`.
+template <typename St, bool CELLS>
+__device__ __forceinline__ void produce_batch(const LbArgs &a, const StageLayout &L, int batch, unsigned char *base,
+                                              uint32_t bar, int lane)
+{
+    const int nx = a.nx, ny = a.ny, nz = a.nz, B = L.B;
+    const int nyb = (ny + B - 1) / B;
+    const int z = batch / nyb, y0 = (batch - z * nyb) * B;
+    const int nb = min(B, ny - y0);
+    const St *src = static_cast<const St *>(a.src);
+    const uint32_t prow_bytes = (uint32_t)nx * (uint32_t)sizeof(St), frow_bytes = (uint32_t)nx * 4u;
+    if (lane == 0)
+        mbar_expect_tx(bar, (uint32_t)(kQ * nb) * prow_bytes + (uint32_t)((L.planes - kQ) * nb) * frow_bytes);
+    __syncwarp();
+    St *pst = reinterpret_cast<St *>(base);
+    float *fst = reinterpret_cast<float *>(base + L.pop_bytes);
+    for (int k = lane; k < L.planes; k += 32) {
+        if (k < kQ) {
+            // the upstream rows y - c_y are contiguous in plane k except
+            // where they wrap in y: one copy, or two
+            St *dst = pst + (size_t)k * B * nx;
+            const int zs = wrapm(z - cz(k), nz);
+            const St *plane = src + (long long)k * a.Np + (long long)zs * ny * nx;
+            const int ys = y0 - cy(k);  // first upstream row, may be -1 or run past ny
+            int b = 0;
+            while (b < nb) {
+                const int yr = wrapm(ys + b, ny);
+                const int run = min(nb - b, ny - yr);
+                bulk_g2s(smem_addr(dst + (size_t)b * nx), plane + (long long)yr * nx, (uint32_t)run * prow_bytes,
+                         bar);
+                b += run;
+            }
+        } else {
+            float *dst = fst + (size_t)(k - kQ) * B * nx;
+            const long long off = ((long long)z * ny + y0) * nx;
+            const float *fsrc;
+            if (CELLS && k < kQ + 3)
+                fsrc = a.G + (long long)(k - kQ) * a.Np + off;
+            else if (CELLS && k == kQ + 3)
+                fsrc = a.th + off;
+            else
+                fsrc = reinterpret_cast<const float *>(a.links) + off;
+            bulk_g2s(smem_addr(dst), fsrc, (uint32_t)nb * frow_bytes, bar);
+        }
+    }
+}
+
+// Consumer side of one batch: the 256 consumer threads take batch nodes
+// l = t, t + 256, ... as (row b, column x) = (l / nx, l % nx), advanced
+// without a division, and collide them from the staged rows.
+template <typename St, bool WALLS, bool CELLS, bool SIGMA>
+__device__ __forceinline__ void consume_batch(const LbArgs &a, const StageLayout &L, int batch,
+                                              const unsigned char *base, unsigned long long step, int x_first,
+                                              int b_first, int x_step, int b_step)
+{
+    const int nx = a.nx, ny = a.ny, B = L.B;
+    const int nyb = (ny + B - 1) / B;
+    const int z = batch / nyb, y0 = (batch - z * nyb) * B;
+    const int nb = min(B, ny - y0);
+    const int plane_stride = B * nx;
+    const St *pst = reinterpret_cast<const St *>(base);
+    const float *fst = reinterpret_cast<const float *>(base + L.pop_bytes);
+    for (int b = b_first, x = x_first; b < nb;) {
+        const int y = y0 + b;
+        const uint32_t n = (uint32_t)((y + ny * z) * nx + x);
+        const int bx = b, xx = x;
+        x += x_step;
+        b += b_step;
+        if (x >= nx) {
+            x -= nx;
+            ++b;
+        }
+        const St *prow = pst + (size_t)bx * nx;
+        const float *frow = fst + (size_t)bx * nx;
+        const uint32_t lk =
+            WALLS ? reinterpret_cast<const uint32_t *>(frow)[(size_t)(CELLS ? 4 : 0) * plane_stride + xx] : 0u;
+        if (WALLS && (lk >> 31)) continue;
+        const int xm = xx == 0 ? nx - 1 : xx - 1, xp = xx == nx - 1 ? 0 : xx + 1;
+        float d[kQ];
+        for_speeds<0, kQ>([&](auto pc) {
+            constexpr int p = decltype(pc)::value;
+            const int xs = cx(p) == 0 ? xx : (cx(p) > 0 ? xm : xp);
+            d[p] = Pop<St>::template get<p>(prow[p * plane_stride + xs]);
+        });
+        float gx, gy, gz, T = a.tau0;
+        external_force(a, y, gx, gy, gz);
+        if (CELLS) {
+            gx += frow[0 * plane_stride + xx];
+            gy += frow[1 * plane_stride + xx];
+            gz += frow[2 * plane_stride + xx];
+            T += a.delta * frow[3 * plane_stride + xx];
+        }
+        collide_node<St, WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, n, xx, y, z, step);
+    }
+}
+
 template <typename St, bool WALLS, bool CELLS, bool SIGMA>
 __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout L, int nbatches)
 {
@@ -443,9 +544,7 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
     __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages];
     __shared__ int s_batch[kMaxStages];
     __shared__ unsigned long long s_step;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int B = L.B, ns = L.stages;
-    const int nyb = (ny + B - 1) / B;
+    const int ns = L.stages;
     if (threadIdx.x == 0) {
         for (int k = 0; k < ns; ++k) {
             mbar_init(smem_addr(&full[k]), 1);
@@ -459,16 +558,9 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
     if (threadIdx.x >= kStConsumers) {
         // Producer warp.  Batches are claimed from a global counter, so a CTA
         // that starts late (the SM was busy with another kernel) just does
-        // fewer of them.  A batch is rows y0 .. y0 + nb - 1 at one z.  Staged
-        // population plane k, batch row b sits at (k * B + b) * nx elements of
-        // the stage, the 4-byte planes after the 19 population planes.  For
-        // a speed p the upstream rows y - c_y are contiguous in plane p except
-        // where they wrap in y, so each plane needs one copy, or two.  The
-        // batch id goes to s_batch[stage] before the arrive that the
-        // consumers' wait acquires; -1 tells them to stop.
-        const St *src = static_cast<const St *>(a.src);
+        // fewer of them.  The batch id goes to s_batch[stage] before the
+        // arrive that the consumers' wait acquires; -1 tells them to stop.
         const int lane = threadIdx.x - kStConsumers;
-        const uint32_t prow_bytes = (uint32_t)nx * (uint32_t)sizeof(St), frow_bytes = (uint32_t)nx * 4u;
         int it = 0;
         bool ok = true;
         for (;; ++it) {
@@ -489,43 +581,8 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
                 }
                 break;
             }
-            const int z = batch / nyb, y0 = (batch - z * nyb) * B;
-            const int nb = min(B, ny - y0);
-            if (lane == 0) {
-                s_batch[stage] = batch;
-                mbar_expect_tx(bar, (uint32_t)(kQ * nb) * prow_bytes + (uint32_t)((L.planes - kQ) * nb) * frow_bytes);
-            }
-            __syncwarp();
-            unsigned char *base = smraw + (size_t)stage * L.stage_bytes;
-            St *pst = reinterpret_cast<St *>(base);
-            float *fst = reinterpret_cast<float *>(base + L.pop_bytes);
-            for (int k = lane; k < L.planes; k += 32) {
-                if (k < kQ) {
-                    St *dst = pst + (size_t)k * B * nx;
-                    const int zs = wrapm(z - cz(k), nz);
-                    const St *plane = src + (long long)k * a.Np + (long long)zs * ny * nx;
-                    const int ys = y0 - cy(k);  // first upstream row, may be -1 or run past ny
-                    int b = 0;
-                    while (b < nb) {
-                        const int yr = wrapm(ys + b, ny);
-                        const int run = min(nb - b, ny - yr);
-                        bulk_g2s(smem_addr(dst + (size_t)b * nx), plane + (long long)yr * nx,
-                                 (uint32_t)run * prow_bytes, bar);
-                        b += run;
-                    }
-                } else {
-                    float *dst = fst + (size_t)(k - kQ) * B * nx;
-                    const long long off = ((long long)z * ny + y0) * nx;
-                    const float *fsrc;
-                    if (CELLS && k < kQ + 3)
-                        fsrc = a.G + (long long)(k - kQ) * a.Np + off;
-                    else if (CELLS && k == kQ + 3)
-                        fsrc = a.th + off;
-                    else
-                        fsrc = reinterpret_cast<const float *>(a.links) + off;
-                    bulk_g2s(smem_addr(dst), fsrc, (uint32_t)nb * frow_bytes, bar);
-                }
-            }
+            if (lane == 0) s_batch[stage] = batch;
+            produce_batch<St, CELLS>(a, L, batch, smraw + (size_t)stage * L.stage_bytes, bar, lane);
         }
         if (!ok) {
             // let the copies still in flight land before the CTA's memory goes away
@@ -546,11 +603,10 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
         return;
     }
 
-    // consumer warps: thread t takes batch nodes l = t, t + 256, ... as
-    // (row b, column x) = (l / nx, l % nx), advanced without a division
+    // consumer warps
     const int lane = threadIdx.x & 31;
-    const int plane_stride = B * nx;
     const unsigned long long step = s_step;
+    const int nx = a.nx;
     const int x_first = threadIdx.x % nx, b_first = threadIdx.x / nx;
     const int x_step = kStConsumers % nx, b_step = kStConsumers / nx;
     for (int it = 0;; ++it) {
@@ -561,45 +617,134 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
         }
         const int batch = s_batch[stage];
         if (batch < 0) break;
-        const unsigned char *base = smraw + (size_t)stage * L.stage_bytes;
-        const St *pst = reinterpret_cast<const St *>(base);
-        const float *fst = reinterpret_cast<const float *>(base + L.pop_bytes);
-        const int z = batch / nyb, y0 = (batch - z * nyb) * B;
-        const int nb = min(B, ny - y0);
-        for (int b = b_first, x = x_first; b < nb;) {
-            const int y = y0 + b;
-            const uint32_t n = (uint32_t)((y + ny * z) * nx + x);
-            const int bx = b, xx = x;
-            x += x_step;
-            b += b_step;
-            if (x >= nx) {
-                x -= nx;
-                ++b;
-            }
-            const St *prow = pst + (size_t)bx * nx;
-            const float *frow = fst + (size_t)bx * nx;
-            const uint32_t lk =
-                WALLS ? reinterpret_cast<const uint32_t *>(frow)[(size_t)(CELLS ? 4 : 0) * plane_stride + xx] : 0u;
-            if (WALLS && (lk >> 31)) continue;
-            const int xm = xx == 0 ? nx - 1 : xx - 1, xp = xx == nx - 1 ? 0 : xx + 1;
-            float d[kQ];
-            for_speeds<0, kQ>([&](auto pc) {
-                constexpr int p = decltype(pc)::value;
-                const int xs = cx(p) == 0 ? xx : (cx(p) > 0 ? xm : xp);
-                d[p] = Pop<St>::template get<p>(prow[p * plane_stride + xs]);
-            });
-            float gx, gy, gz, T = a.tau0;
-            external_force(a, y, gx, gy, gz);
-            if (CELLS) {
-                gx += frow[0 * plane_stride + xx];
-                gy += frow[1 * plane_stride + xx];
-                gz += frow[2 * plane_stride + xx];
-                T += a.delta * frow[3 * plane_stride + xx];
-            }
-            collide_node<St, WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, n, xx, y, z, step);
-        }
+        consume_batch<St, WALLS, CELLS, SIGMA>(a, L, batch, smraw + (size_t)stage * L.stage_bytes, step, x_first,
+                                               b_first, x_step, b_step);
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&empty[stage]));  // this warp is done with the stage
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Packed lattice pass: one persistent launch over the lattices of several
+// solves of one class (storage type, walls, cells, stress).  The solves'
+// batches are numbered consecutively (bstart[i] = first batch of solve i);
+// a producer that claims batch g finds its solve by binary search, copies
+// the solve's arguments, layout and pass count into the stage's slot of
+// shared memory and stages the rows as above; the consumers collide from
+// that slot.  Stages are `stage_bytes` (the largest layout of the pack).
+// The last CTA out resets the counters and advances every solve's pass
+// counter.  `parity` swaps source and destination populations.
+// ---------------------------------------------------------------------------
+struct LbPackEntry {
+    LbArgs a;  // populations of parity 0: src = pops[0], dst = pops[1]
+    StageLayout L;
+};
+
+__device__ __forceinline__ int pack_find(const int *start, int n, int g)
+{
+    int lo = 0, hi = n - 1;  // largest i with start[i] <= g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename St, bool WALLS, bool CELLS, bool SIGMA>
+__global__ void __launch_bounds__(kStThreads)
+    k_lb_staged_packed(const LbPackEntry *__restrict__ tab, const int *__restrict__ bstart, int ninst, int total,
+                       int parity, int *work, int ns, int stage_bytes)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages];
+    __shared__ int s_batch[kMaxStages];
+    __shared__ LbPackEntry s_ent[kMaxStages];
+    __shared__ unsigned long long s_step[kMaxStages];
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < ns; ++k) {
+            mbar_init(smem_addr(&full[k]), 1);
+            mbar_init(smem_addr(&empty[k]), kStConsumers / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (threadIdx.x >= kStConsumers) {
+        const int lane = threadIdx.x - kStConsumers;
+        int it = 0;
+        bool ok = true;
+        for (;; ++it) {
+            const int stage = it % ns;
+            if (it >= ns && !mbar_wait(smem_addr(&empty[stage]), (uint32_t)((it / ns - 1) & 1))) {
+                if (lane == 0) atomicOr(&tab[0].a.flags[FLAG_TIMEOUT], 1);
+                ok = false;
+                break;
+            }
+            int g = 0;
+            if (lane == 0) g = atomicAdd(&work[0], 1);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            const uint32_t bar = smem_addr(&full[stage]);
+            if (g >= total) {
+                if (lane == 0) {
+                    s_batch[stage] = -1;
+                    mbar_arrive(bar);
+                }
+                break;
+            }
+            const int inst = pack_find(bstart, ninst, g);
+            // copy the solve's entry into the stage's slot (the stage is free)
+            const int *srcw = reinterpret_cast<const int *>(&tab[inst]);
+            int *dstw = reinterpret_cast<int *>(&s_ent[stage]);
+            for (int w = lane; w < (int)(sizeof(LbPackEntry) / sizeof(int)); w += 32) dstw[w] = srcw[w];
+            if (lane == 0) {
+                s_batch[stage] = g - bstart[inst];
+                s_step[stage] = *tab[inst].a.step;
+            }
+            __syncwarp();
+            if (lane == 0 && parity) {
+                const void *t = s_ent[stage].a.src;
+                s_ent[stage].a.src = s_ent[stage].a.dst;
+                s_ent[stage].a.dst = const_cast<void *>(t);
+            }
+            __syncwarp();
+            produce_batch<St, CELLS>(s_ent[stage].a, s_ent[stage].L, s_batch[stage],
+                                     smraw + (size_t)stage * stage_bytes, bar, lane);
+        }
+        if (!ok) {
+            for (int j = it > ns ? it - ns : 0; j < it; ++j)
+                mbar_wait(smem_addr(&full[j % ns]), (uint32_t)((j / ns) & 1));
+        }
+        if (lane == 0) {
+            __threadfence();
+            if (atomicAdd(&work[1], 1) == (int)gridDim.x - 1) {
+                work[0] = 0;
+                work[1] = 0;
+                for (int k = 0; k < ninst; ++k) *tab[k].a.step += 1;
+                __threadfence();
+            }
+        }
+        return;
+    }
+
+    const int lane = threadIdx.x & 31;
+    for (int it = 0;; ++it) {
+        const int stage = it % ns;
+        if (!mbar_wait(smem_addr(&full[stage]), (uint32_t)((it / ns) & 1))) {
+            if (lane == 0) atomicOr(&tab[0].a.flags[FLAG_TIMEOUT], 1);
+            break;
+        }
+        const int batch = s_batch[stage];
+        if (batch < 0) break;
+        const LbArgs &a = s_ent[stage].a;
+        const int nx = a.nx;
+        consume_batch<St, WALLS, CELLS, SIGMA>(a, s_ent[stage].L, batch, smraw + (size_t)stage * stage_bytes,
+                                               s_step[stage], threadIdx.x % nx, threadIdx.x / nx, kStConsumers % nx,
+                                               kStConsumers / nx);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&empty[stage]));
     }
 }
 
@@ -901,7 +1046,7 @@ void set_lb_shape(Dev &d, int stages, int ctas_per_sm)
     d.lb_grid = (int)(slots > nbatches ? nbatches : slots);
 }
 
-void launch_lb(const Dev &d, const Params &p, int parity, cudaStream_t s)
+static LbArgs lb_args(const Dev &d, const Params &p, int parity)
 {
     LbArgs a;
     a.src = d.pops[parity];
@@ -932,8 +1077,87 @@ void launch_lb(const Dev &d, const Params &p, int parity, cudaStream_t s)
     a.key0 = (uint32_t)(d.seed & 0xffffffffull);
     a.key1 = (uint32_t)(d.seed >> 32);
     a.stochastic = d.stochastic;
+    return a;
+}
+
+void launch_lb(const Dev &d, const Params &p, int parity, cudaStream_t s)
+{
+    const LbArgs a = lb_args(d, p, parity);
     LaunchOp op{d, a, s};
     dispatch(d, op);
+}
+
+// ---------------------------------------------------------------------------
+// Packs of lattices (request server)
+// ---------------------------------------------------------------------------
+size_t lb_pack_entry_bytes() { return sizeof(LbPackEntry); }
+
+bool fill_lb_pack_entry(const Dev &d, const Params &p, void *out, int *nbatches, int *stage_bytes)
+{
+    if (!staged_ok(d)) return false;
+    LbPackEntry e;
+    std::memset(&e, 0, sizeof e);
+    e.a = lb_args(d, p, 0);
+    e.L = stage_layout(d);
+    e.L.stages = 0;  // the pack's ring depth applies
+    *nbatches = d.nz * ((d.ny + e.L.B - 1) / e.L.B);
+    *stage_bytes = e.L.stage_bytes;
+    std::memcpy(out, &e, sizeof e);
+    return true;
+}
+
+// ring depth and grid of a pack's launch: the deepest ring (up to
+// kMaxStages) of the pack's largest stage that fits, at most
+// kLbCtasWithCells CTAs per SM when cells run beside the pass
+struct PackPrepOp {
+    const Dev &d0;
+    LbPackDesc &k;
+    template <typename St, bool W, bool C, bool S_>
+    void run()
+    {
+        raise_smem_limit((const void *)k_lb_staged_packed<St, W, C, S_>, 200 * 1024);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        k.grid = 0;
+        for (int ns = kMaxStages; ns >= 2 && k.grid == 0; --ns) {
+            const size_t smem = (size_t)ns * k.stage_bytes;
+            if (smem > 200u * 1024u) continue;
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_staged_packed<St, W, C, S_>, kStThreads, smem);
+            if (d0.nc > 0 && per_sm > kLbCtasWithCells) per_sm = kLbCtasWithCells;
+            if (per_sm < 1) continue;
+            k.stages = ns;
+            k.smem = smem;
+            k.grid = std::min(sms * per_sm, k.total);
+        }
+    }
+};
+
+struct PackLaunchOp {
+    const LbPackDesc &k;
+    int parity;
+    cudaStream_t s;
+    template <typename St, bool W, bool C, bool S_>
+    void run()
+    {
+        k_lb_staged_packed<St, W, C, S_><<<k.grid, kStThreads, k.smem, s>>>(
+            static_cast<const LbPackEntry *>(k.tab), k.bstart, k.ninst, k.total, parity, k.work, k.stages,
+            k.stage_bytes);
+    }
+};
+
+bool prepare_lb_pack(const Dev &d0, LbPackDesc &k)
+{
+    PackPrepOp op{d0, k};
+    dispatch(d0, op);
+    return k.grid > 0;
+}
+
+void launch_lb_packed(const Dev &d0, const LbPackDesc &k, int parity, cudaStream_t s)
+{
+    PackLaunchOp op{k, parity, s};
+    dispatch(d0, op);
 }
 
 void launch_rho(const Dev &d, int parity, cudaStream_t s)

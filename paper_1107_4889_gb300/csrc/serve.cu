@@ -111,6 +111,23 @@ double seconds_since(std::chrono::steady_clock::time_point t0)
 
 }  // namespace
 
+// A pack: the solves of one class (storage type, walls, stress; all with
+// cells and a row-staged lattice pass) advanced together, each kernel of the
+// step launched once for all of them over device tables of their
+// arguments.  Members change only between ticks.
+struct Pack {
+    long long key = -1;
+    std::vector<std::unique_ptr<Active>> members, joining;
+    cudaStream_t st[3] = {nullptr, nullptr, nullptr};  // main, side (bins, Gay-Berne), side 2 (weights)
+    cudaEvent_t fork = nullptr, join1 = nullptr, join2 = nullptr, done[2] = {nullptr, nullptr};
+    cudaGraphExec_t pair = nullptr, budgets = nullptr;  // two packed steps; the members' budgets
+    int in_flight = 0, head = 0;  // ticks queued (at most 2) and the oldest one's event
+    size_t off = 0, bytes = 0;  // table region in the arena
+    rbc::CellPackDesc cd;
+    rbc::LbPackDesc ld;
+    std::vector<char> host;
+};
+
 struct rbc_server {
     char *base = nullptr;
     Arena arena;
@@ -130,6 +147,7 @@ struct rbc_server {
     std::deque<std::unique_ptr<Active>> to_init, ready;
     int pending = 0;
     bool stop = false;
+    std::vector<std::unique_ptr<Pack>> packs;
 };
 
 namespace {
@@ -229,7 +247,10 @@ void initialise(rbc_server *s, Active &a)
     p.stream = a.stream;
     int rc = rbc_init(&a.req->r.geom, &a.req->r.cells, &p, s->base + a.off, a.req->bytes, &a.h);
     const long long from = a.req->r.average_from;
-    if (rc == RBC_OK && a.total >= s->tick_steps) rc = rbc::capture_ticks(a.h, s->tick_steps, from, &a.tick);
+    // packable solves run their full ticks in a pack
+    const bool packable = rc == RBC_OK && rbc::handle_dev(a.h).nc > 0 && rbc::handle_dev(a.h).lb_grid > 0;
+    if (rc == RBC_OK && a.total >= s->tick_steps && !packable)
+        rc = rbc::capture_ticks(a.h, s->tick_steps, from, &a.tick);
     if (rc == RBC_OK && a.total % s->tick_steps) rc = rbc::capture_ticks(a.h, a.total % s->tick_steps, from, &a.last);
     for (int k = 0; rc == RBC_OK && k < kInFlight; ++k)
         if (cudaEventCreateWithFlags(&a.ev[k], cudaEventDisableTiming) != cudaSuccess) rc = RBC_ECUDA;
@@ -252,6 +273,233 @@ void worker_main(rbc_server *s)
         std::lock_guard<std::mutex> lock(s->mu);
         s->ready.push_back(std::move(a));
     }
+}
+
+// class of a solve: storage type, walls, cells, stress output, and the
+// shape-function box (the packed shape-list launch sizes its shared memory
+// for one box)
+long long pack_key(const rbc::Dev &d, const rbc::Params &p)
+{
+    return (((long long)p.box_dim * 65536 + p.sup_cap) * 4 + d.prec) * 8 + (d.walls ? 4 : 0) + (d.nc > 0 ? 2 : 0) +
+           (d.S ? 1 : 0);
+}
+
+bool packable(const Active &a) { return a.h && rbc::handle_dev(a.h).nc > 0 && rbc::handle_dev(a.h).lb_grid > 0; }
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+// Table region of a pack: per member one lattice and one cell entry, the
+// block / batch starts of every packed launch, and the lattice pass's two
+// work counters.
+size_t pack_bytes(int cap)
+{
+    return align256(cap * rbc::lb_pack_entry_bytes()) + align256(cap * rbc::cell_pack_entry_bytes()) +
+           (rbc::PACK_KINDS + 1) * align256((cap + 1) * sizeof(int)) + 256;
+}
+
+Pack *get_pack(rbc_server *s, long long key)
+{
+    for (auto &p : s->packs)
+        if (p->key == key) return p.get();
+    std::unique_ptr<Pack> p(new Pack());
+    p->key = key;
+    p->bytes = pack_bytes(s->max_active);
+    if (!s->arena.alloc(p->bytes, &p->off)) return nullptr;
+    bool ok = true;
+    for (auto &st : p->st) ok = ok && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t *e : {&p->fork, &p->join1, &p->join2, &p->done[0], &p->done[1]})
+        ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    // the lattice pass's work counters start at zero (the pass leaves them so)
+    const size_t work_off = p->off + p->bytes - 256;
+    ok = ok && cudaMemsetAsync(s->base + work_off, 0, 256, p->st[0]) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(p->st[0]) == cudaSuccess;
+    if (!ok) {
+        for (auto &st : p->st)
+            if (st) cudaStreamDestroy(st);
+        for (cudaEvent_t e : {p->fork, p->join1, p->join2, p->done[0], p->done[1]})
+            if (e) cudaEventDestroy(e);
+        s->arena.release(p->off, p->bytes);
+        return nullptr;
+    }
+    s->packs.push_back(std::move(p));
+    return s->packs.back().get();
+}
+
+// Rebuild a pack's tables and capture its two graphs: a pair of packed
+// steps (per step: the per-cell kernel, then the lattice pass beside the
+// next step's shape lists, cell list and Gay-Berne forces, as in a single
+// solve's step), launched tick_steps / 2 times per tick, and the members'
+// budget reductions into their time-average sums, launched once per tick.
+// Small graphs keep a membership change cheap.
+int rebuild_pack(rbc_server *s, Pack &pk)
+{
+    const int n = (int)pk.members.size();
+    if (pk.pair) cudaGraphExecDestroy(pk.pair);
+    if (pk.budgets) cudaGraphExecDestroy(pk.budgets);
+    pk.pair = pk.budgets = nullptr;
+    if (n == 0) return RBC_OK;
+    const size_t lbe = rbc::lb_pack_entry_bytes(), ce = rbc::cell_pack_entry_bytes();
+    const size_t cap = (size_t)s->max_active;
+    const size_t off_lb = 0, off_c = align256(cap * lbe), off_st = off_c + align256(cap * ce);
+    const size_t st_stride = align256((cap + 1) * sizeof(int));
+    pk.host.assign(pk.bytes - 256, 0);
+    std::vector<int> starts((rbc::PACK_KINDS + 1) * (n + 1), 0);
+    int *bstart = &starts[rbc::PACK_KINDS * (n + 1)];
+    int stage_bytes = 0;
+    for (int i = 0; i < n; ++i) {
+        const rbc::Dev &d = rbc::handle_dev(pk.members[i]->h);
+        const rbc::Params &p = rbc::handle_params(pk.members[i]->h);
+        int nb = 0, sb = 0;
+        if (!rbc::fill_lb_pack_entry(d, p, &pk.host[off_lb + i * lbe], &nb, &sb)) return RBC_EINVAL;
+        rbc::fill_cell_pack_entry(d, p, &pk.host[off_c + i * ce]);
+        bstart[i + 1] = bstart[i] + nb;
+        stage_bytes = std::max(stage_bytes, sb);
+        for (int k = 0; k < rbc::PACK_KINDS; ++k)
+            starts[k * (n + 1) + i + 1] = starts[k * (n + 1) + i] + rbc::cell_pack_blocks(d.nc, d.nbins, k);
+    }
+    for (int k = 0; k <= rbc::PACK_KINDS; ++k)
+        std::memcpy(&pk.host[off_st + k * st_stride], &starts[k * (n + 1)], (n + 1) * sizeof(int));
+    char *dev = s->base + pk.off;
+    if (cudaMemcpyAsync(dev, pk.host.data(), pk.host.size(), cudaMemcpyHostToDevice, pk.st[0]) != cudaSuccess)
+        return RBC_ECUDA;
+    pk.cd.tab = dev + off_c;
+    for (int k = 0; k < rbc::PACK_KINDS; ++k) {
+        pk.cd.start[k] = reinterpret_cast<const int *>(dev + off_st + k * st_stride);
+        pk.cd.blocks[k] = starts[k * (n + 1) + n];
+    }
+    pk.cd.ninst = n;
+    pk.ld.tab = dev + off_lb;
+    pk.ld.bstart = reinterpret_cast<const int *>(dev + off_st + rbc::PACK_KINDS * st_stride);
+    pk.ld.total = bstart[n];
+    pk.ld.ninst = n;
+    pk.ld.work = reinterpret_cast<int *>(dev + pk.bytes - 256);
+    pk.ld.stage_bytes = stage_bytes;
+    const rbc::Dev &d0 = rbc::handle_dev(pk.members[0]->h);
+    const rbc::Params &p0 = rbc::handle_params(pk.members[0]->h);
+    if (!rbc::prepare_lb_pack(d0, pk.ld)) return RBC_EINVAL;
+    const bool alpha = d0.S != nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(pk.st[0], cudaStreamCaptureModeThreadLocal) != cudaSuccess) return RBC_ECUDA;
+    for (int k = 0; k < 2; ++k) {
+        const int par = k & 1;
+        rbc::launch_cells_packed(pk.cd, par, alpha, pk.st[0]);
+        cudaEventRecord(pk.fork, pk.st[0]);
+        cudaStreamWaitEvent(pk.st[1], pk.fork, 0);
+        cudaStreamWaitEvent(pk.st[2], pk.fork, 0);
+        rbc::launch_weights_packed(pk.cd, p0, par ^ 1, d0.side_prio, pk.st[2]);
+        rbc::launch_bin_packed(pk.cd, d0.side_prio, pk.st[1]);
+        rbc::launch_gb_packed(pk.cd, d0.side_prio, pk.st[1]);
+        rbc::launch_lb_packed(d0, pk.ld, par, pk.st[0]);
+        cudaEventRecord(pk.join1, pk.st[1]);
+        cudaEventRecord(pk.join2, pk.st[2]);
+        cudaStreamWaitEvent(pk.st[0], pk.join1, 0);
+        cudaStreamWaitEvent(pk.st[0], pk.join2, 0);
+    }
+    if (cudaStreamEndCapture(pk.st[0], &g) != cudaSuccess) return RBC_ECUDA;
+    cudaError_t e = cudaGraphInstantiate(&pk.pair, g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return RBC_ECUDA;
+    if (cudaStreamBeginCapture(pk.st[0], cudaStreamCaptureModeThreadLocal) != cudaSuccess) return RBC_ECUDA;
+    for (auto &m : pk.members)
+        rbc::launch_budget(rbc::handle_dev(m->h), rbc::handle_params(m->h), 0, pk.st[0], true,
+                           m->req->r.average_from);
+    if (cudaStreamEndCapture(pk.st[0], &g) != cudaSuccess) return RBC_ECUDA;
+    e = cudaGraphInstantiate(&pk.budgets, g, 0);
+    cudaGraphDestroy(g);
+    return e == cudaSuccess ? RBC_OK : RBC_ECUDA;
+}
+
+// Queue one tick of the pack: tick_steps / 2 launches of the step pair,
+// the budgets, the tick's event.
+int launch_pack_tick(rbc_server *s, Pack &pk)
+{
+    bool ok = true;
+    for (int k = 0; ok && k < s->tick_steps / 2; ++k) ok = cudaGraphLaunch(pk.pair, pk.st[0]) == cudaSuccess;
+    ok = ok && cudaGraphLaunch(pk.budgets, pk.st[0]) == cudaSuccess;
+    ok = ok && cudaEventRecord(pk.done[(pk.head + pk.in_flight) % 2], pk.st[0]) == cudaSuccess;
+    if (!ok) return RBC_ECUDA;
+    pk.in_flight++;
+    for (auto &m : pk.members) {
+        m->launched += s->tick_steps;
+        rbc::advance_steps(m->h, s->tick_steps);
+    }
+    return RBC_OK;
+}
+
+void fail_pack(rbc_server *s, Pack &pk, int rc)
+{
+    for (auto &m : pk.members) {
+        m->status = rc;
+        finish(s, *m);
+    }
+    pk.members.clear();
+}
+
+// Retire the pack's completed ticks.  With no tick queued (a tick
+// boundary): retire finished members, hand members with fewer than a tick
+// of steps left to their own streams, take in joining solves, rebuild if
+// anything changed and queue the next tick.  With one tick queued, nobody
+// waiting to join and every member at least a tick from its end, queue the
+// following tick behind it so the device does not wait for the host.
+int progress_pack(rbc_server *s, Pack &pk)
+{
+    while (pk.in_flight > 0) {
+        const cudaError_t e = cudaEventQuery(pk.done[pk.head]);
+        if (e == cudaErrorNotReady) break;
+        if (e != cudaSuccess) {
+            pk.in_flight = 0;
+            fail_pack(s, pk, RBC_ECUDA);
+            return RBC_ECUDA;
+        }
+        pk.in_flight--;
+        pk.head = (pk.head + 1) % 2;
+    }
+    if (pk.in_flight == 1 && pk.joining.empty()) {
+        bool room = !pk.members.empty();
+        for (auto &m : pk.members) room = room && m->status == RBC_OK && m->total - m->launched >= s->tick_steps;
+        if (room) {
+            const int rc = launch_pack_tick(s, pk);
+            if (rc != RBC_OK) fail_pack(s, pk, rc);
+            return rc;
+        }
+    }
+    if (pk.in_flight > 0) return RBC_OK;
+    bool changed = false;
+    for (size_t i = 0; i < pk.members.size();) {
+        Active &a = *pk.members[i];
+        if (a.status != RBC_OK || a.launched >= a.total) {
+            finish(s, a);
+        } else if (a.total - a.launched < s->tick_steps) {
+            a.status = launch_tick(a, s->tick_steps);  // the remainder, on the solve's own stream
+            s->active.push_back(std::move(pk.members[i]));
+        } else {
+            ++i;
+            continue;
+        }
+        pk.members.erase(pk.members.begin() + (long)i);
+        changed = true;
+    }
+    for (auto &a : pk.joining) pk.members.push_back(std::move(a));
+    if (!pk.joining.empty()) changed = true;
+    pk.joining.clear();
+    if (pk.members.empty()) return RBC_OK;
+    if (changed || !pk.pair) {
+        const int rc = rebuild_pack(s, pk);
+        if (rc != RBC_OK) {
+            fail_pack(s, pk, rc);
+            return rc;
+        }
+    }
+    const int rc = launch_pack_tick(s, pk);
+    if (rc != RBC_OK) fail_pack(s, pk, rc);
+    return rc;
+}
+
+int pack_count(const rbc_server *s)
+{
+    int n = 0;
+    for (auto &p : s->packs) n += (int)(p->members.size() + p->joining.size());
+    return n;
 }
 
 }  // namespace
@@ -367,7 +615,13 @@ int rbc_server_poll(rbc_server *s, int *active, int *queued)
             ++i;
         }
     }
-    // solves the worker has initialised start their first ticks
+    // packs advance between their ticks
+    for (auto &pk : s->packs) {
+        const int rc = progress_pack(s, *pk);
+        if (rc != RBC_OK) err = rc;
+    }
+    // solves the worker has initialised join a pack (from its next tick) or
+    // start their own ticks
     std::deque<std::unique_ptr<Active>> ready;
     {
         std::lock_guard<std::mutex> lock(s->mu);
@@ -375,6 +629,16 @@ int rbc_server_poll(rbc_server *s, int *active, int *queued)
         s->pending -= (int)ready.size();
     }
     for (auto &a : ready) {
+        if (a->status == RBC_OK && packable(*a) && a->total >= s->tick_steps) {
+            Pack *pk = get_pack(s, pack_key(rbc::handle_dev(a->h), rbc::handle_params(a->h)));
+            if (pk) {
+                pk->joining.push_back(std::move(a));
+                if (pk->in_flight == 0) progress_pack(s, *pk);
+                continue;
+            }
+            // no room for a pack's tables: this solve runs on its own
+            a->status = rbc::capture_ticks(a->h, s->tick_steps, a->req->r.average_from, &a->tick);
+        }
         for (int k = 0; a->status == RBC_OK && k < kInFlight && a->launched < a->total; ++k)
             a->status = launch_tick(*a, s->tick_steps);
         if (a->status != RBC_OK) {
@@ -391,7 +655,7 @@ int rbc_server_poll(rbc_server *s, int *active, int *queued)
     }
     int looked = 0;
     for (auto it = s->queue.begin(); it != s->queue.end() && looked < kLookahead;) {
-        if ((int)s->active.size() + pending >= s->max_active || s->free_streams.empty()) break;
+        if ((int)s->active.size() + pack_count(s) + pending >= s->max_active || s->free_streams.empty()) break;
         size_t off = 0;
         if (s->arena.alloc((*it)->bytes, &off)) {
             std::unique_ptr<Owned> o = std::move(*it);
@@ -403,7 +667,7 @@ int rbc_server_poll(rbc_server *s, int *active, int *queued)
             ++looked;
         }
     }
-    if (active) *active = (int)s->active.size() + pending;
+    if (active) *active = (int)s->active.size() + pack_count(s) + pending;
     if (queued) *queued = (int)s->queue.size();
     return err;
 }
@@ -439,6 +703,23 @@ void rbc_server_free(rbc_server *s)
     s->to_init.clear();
     for (auto &a : s->active) release(s, *a);
     s->active.clear();
+    for (auto &pk : s->packs) {
+        for (cudaEvent_t e : pk->done)
+            if (e) cudaEventSynchronize(e);
+        for (auto &a : pk->members) release(s, *a);
+        for (auto &a : pk->joining) release(s, *a);
+        if (pk->pair) cudaGraphExecDestroy(pk->pair);
+        if (pk->budgets) cudaGraphExecDestroy(pk->budgets);
+        for (auto &st : pk->st)
+            if (st) {
+                cudaStreamSynchronize(st);
+                cudaStreamDestroy(st);
+            }
+        for (cudaEvent_t e : {pk->fork, pk->join1, pk->join2, pk->done[0], pk->done[1]})
+            if (e) cudaEventDestroy(e);
+        s->arena.release(pk->off, pk->bytes);
+    }
+    s->packs.clear();
     for (cudaStream_t st : s->streams) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
