@@ -815,6 +815,9 @@ struct orc_state {
     int *have_cache;
     double *Fm, *Tm, *ut, *wt, *TS, *J, *L;
     long step, clamps;
+    unsigned char *node_type; /* NULL: no open boundaries */
+    double in_c[2], in_r, in_umax;
+    double *fprev;
     int storage, stochastic;
     unsigned long long seed;
 };
@@ -852,6 +855,16 @@ orc_state *orc_create(const orc_config *c)
     s->rc = c->r_cut;
     s->rcw = c->r_cut_wall;
     s->storage = c->storage;
+    s->node_type = NULL;
+    if (c->node_type) {
+        s->node_type = (unsigned char *)malloc((size_t)s->N);
+        memcpy(s->node_type, c->node_type, (size_t)s->N);
+        s->fprev = (double *)calloc((size_t)NQ * s->N, sizeof(double));
+    }
+    s->in_c[0] = c->inlet_center[0];
+    s->in_c[1] = c->inlet_center[1];
+    s->in_r = c->inlet_radius;
+    s->in_umax = c->inlet_umax;
     s->stochastic = c->stochastic;
     s->seed = c->seed;
 
@@ -918,6 +931,8 @@ orc_state *orc_create(const orc_config *c)
 void orc_destroy(orc_state *s)
 {
     if (!s) return;
+    free(s->node_type);
+    free(s->fprev);
     free(s->solid);
     free(s->f);
     free(s->rho);
@@ -1025,6 +1040,104 @@ static void external_force(const orc_state *s, long n, double g[3])
     for (int a = 0; a < 3; a++) g[a] = s->gext[a] + s->gwave[a] * sw;
 }
 
+/* Equilibrium of Sec. 2.1 for density r and velocity v. */
+static double feq(int p, double r, const double v[3])
+{
+    const double c2 = 1.0 / 3.0;
+    double cu = CV[p][0] * v[0] + CV[p][1] * v[1] + CV[p][2] * v[2];
+    double uu = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    return weight(p) * r * (1.0 + cu / c2 + (cu * cu - c2 * uu) / (2.0 * c2 * c2));
+}
+
+/*
+ * Open boundaries.  The paper drives its vessels by an inlet velocity and an
+ * outlet pressure and cites, without giving, the boundary rules.  Reading:
+ * boundary nodes are not collided; after each pass their post-collision
+ * populations are set from the post-collision populations of the previous
+ * pass (fprev), so that every node of the pass reads only the previous state:
+ *   inlet node n:  f_p = f_p^eq(rho_d, u_in(x, y)), rho_d the density of the
+ *                  downstream neighbour n + z (the pressure floats at the
+ *                  inlet), u_in = u_max (1 - r^2/R^2) z;
+ *   outlet node n: f_p = f_p^eq(1, u_m) + [f_p(m) - f_p^eq(rho_m, u_m)],
+ *                  m = n - z the upstream neighbour with its density and
+ *                  velocity (rho = 1 with the neighbour's non-equilibrium
+ *                  part carried over).
+ * Their reported rho and u are the moments of the set populations, sigma 0.
+ */
+static void open_boundaries(orc_state *s)
+{
+    const int nx = s->nx, ny = s->ny, nz = s->nz;
+    const long N = s->N, nxy = (long)nx * ny;
+    for (long n = 0; n < N; n++) {
+        const int t = s->node_type[n];
+        if (t != ORC_NODE_INLET && t != ORC_NODE_OUTLET) continue;
+        const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / nxy);
+        double fb[NQ];
+        if (t == ORC_NODE_INLET) {
+            long d = node_of(nx, ny, nz, x, y, z + 1);
+            double rd = 0.0;
+            for (int p = 0; p < NQ; p++) rd += s->fprev[(long)p * N + d];
+            double dx = x - s->in_c[0], dy = y - s->in_c[1];
+            double r2 = (dx * dx + dy * dy) / (s->in_r * s->in_r);
+            double v[3] = {0.0, 0.0, r2 < 1.0 ? s->in_umax * (1.0 - r2) : 0.0};
+            for (int p = 0; p < NQ; p++) fb[p] = feq(p, rd, v);
+        } else {
+            long m = node_of(nx, ny, nz, x, y, z - 1);
+            double rm = 0.0, j[3] = {0.0, 0.0, 0.0};
+            for (int p = 0; p < NQ; p++) {
+                double fp = s->fprev[(long)p * N + m];
+                rm += fp;
+                for (int a = 0; a < 3; a++) j[a] += fp * CV[p][a];
+            }
+            double v[3] = {j[0] / rm, j[1] / rm, j[2] / rm};
+            for (int p = 0; p < NQ; p++) fb[p] = feq(p, 1.0, v) + (s->fprev[(long)p * N + m] - feq(p, rm, v));
+        }
+        double r = 0.0, jj[3] = {0.0, 0.0, 0.0};
+        for (int p = 0; p < NQ; p++) {
+            s->f[(long)p * N + n] = fb[p];
+            r += fb[p];
+            for (int a = 0; a < 3; a++) jj[a] += fb[p] * CV[p][a];
+        }
+        s->rho[n] = r;
+        for (int a = 0; a < 3; a++) s->U[3 * n + a] = jj[a] / r;
+        for (int k = 0; k < 6; k++) s->S[6 * n + k] = 0.0;
+    }
+}
+
+long orc_wall_shear(const orc_state *s, long *node, double *tau, long max)
+{
+    long cnt = 0;
+    for (int z = 0; z < s->nz; z++)
+        for (int y = 0; y < s->ny; y++)
+            for (int x = 0; x < s->nx; x++) {
+                long n = node_of(s->nx, s->ny, s->nz, x, y, z);
+                if (s->solid[n]) continue;
+                double nv[3] = {0.0, 0.0, 0.0};
+                int any = 0;
+                for (int p = 1; p < NQ; p++)
+                    if (s->solid[node_of(s->nx, s->ny, s->nz, x + CV[p][0], y + CV[p][1], z + CV[p][2])]) {
+                        any = 1;
+                        for (int a = 0; a < 3; a++) nv[a] -= CV[p][a];
+                    }
+                if (!any) continue;
+                double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+                if (cnt < max) {
+                    const double *sg = &s->S[6 * n];
+                    double S3[3][3] = {{sg[0], sg[3], sg[4]}, {sg[3], sg[1], sg[5]}, {sg[4], sg[5], sg[2]}};
+                    double t[3] = {0.0, 0.0, 0.0}, tn = 0.0;
+                    if (nn > 0.0)
+                        for (int a = 0; a < 3; a++) nv[a] /= nn;
+                    for (int a = 0; a < 3; a++)
+                        for (int b = 0; b < 3; b++) t[a] += S3[a][b] * nv[b];
+                    for (int a = 0; a < 3; a++) tn += t[a] * nv[a];
+                    node[cnt] = n;
+                    for (int a = 0; a < 3; a++) tau[3 * cnt + a] = t[a] - tn * nv[a];
+                }
+                cnt++;
+            }
+    return cnt;
+}
+
 void orc_step(orc_state *s, long nsteps)
 {
     const int nx = s->nx, ny = s->ny, nz = s->nz;
@@ -1116,7 +1229,9 @@ void orc_step(orc_state *s, long nsteps)
         for (int i = 0; i < nc; i++) shape_free(&sh[i]);
         free(sh);
         /* 7. lattice pass */
+        if (s->node_type) memcpy(s->fprev, s->f, sizeof(double) * NQ * (size_t)N);
         orc_lb_pass(nx, ny, nz, s->solid, s->f, s->G, s->tau, s->rho, s->U, s->S);
+        if (s->node_type) open_boundaries(s);
         /* 8. storage of the post-collision populations (reduced-precision
          * variants only) */
         store_populations(s->storage, s->stochastic, s->seed, s->step, N, s->solid, s->f);

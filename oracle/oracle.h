@@ -45,7 +45,17 @@ typedef struct {
     int stochastic;   /* 16-bit storage: 1 = stochastic rounding, 0 = to nearest */
     unsigned long long seed;  /* key of the stochastic rounding's random numbers */
     double body_force_wave[3];  /* amplitude of a force density A sin(2 pi y / ny) on fluid nodes */
+    /* open boundaries: node_type[N] (NULL = none) marks fluid nodes as
+     * ORC_NODE_INLET (velocity inlet: u = inlet_umax (1 - r^2 / R^2) along
+     * +z, r the distance of (x, y) from inlet_center, R = inlet_radius) or
+     * ORC_NODE_OUTLET (pressure outlet, rho = 1) */
+    const unsigned char *node_type;
+    double inlet_center[2], inlet_radius, inlet_umax;
 } orc_config;
+
+#define ORC_NODE_INTERIOR 0
+#define ORC_NODE_INLET 1
+#define ORC_NODE_OUTLET 2
 
 /* Population storage of the reduced-precision variants: FP64 (exact), or the
  * deviation from the lattice weight, scaled per direction, rounded to IEEE
@@ -132,6 +142,12 @@ void orc_populations(const orc_state *s, double *f);
 /* Replace the post-collision populations (then stored in the solver's
  * format), e.g. to start from a prescribed flow. */
 void orc_set_populations(orc_state *s, const double *f);
+/* Wall shear stress of the last lattice pass at every fluid node with a
+ * solid link neighbour: n = number of such nodes (returned), node[k] their
+ * indices, tau[3k..] the traction of the stress on the wall tangent plane,
+ * sigma n - (n.sigma n) n, with n the unit vector sum of the links into the
+ * fluid (minus the links to solid neighbours).  Writes up to max entries. */
+long orc_wall_shear(const orc_state *s, long *node, double *tau, long max);
 /* Velocities and weights in the order used above. */
 void orc_lattice(int *c, double *w);
 

@@ -48,6 +48,8 @@ class _Config(ctypes.Structure):
         ("storage", ctypes.c_int), ("stochastic", ctypes.c_int),
         ("seed", ctypes.c_ulonglong),
         ("body_force_wave", ctypes.c_double * 3),
+        ("node_type", _U8), ("inlet_center", ctypes.c_double * 2), ("inlet_radius", ctypes.c_double),
+        ("inlet_umax", ctypes.c_double),
     ]
 
 
@@ -117,6 +119,8 @@ def lib():
         L.orc_storage_scale.argtypes = [ctypes.c_int]
         L.orc_populations.argtypes = [ctypes.c_void_p, _D]
         L.orc_set_populations.argtypes = [ctypes.c_void_p, _D]
+        L.orc_wall_shear.restype = ctypes.c_long
+        L.orc_wall_shear.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_long), _D, ctypes.c_long]
         _lib = L
     return _lib
 
@@ -317,6 +321,13 @@ class Oracle:
         c.ncells = n
         c.pos, c.quat = _dp(self._pos), _dp(self._quat)
         c.vel, c.omega = _dp(self._vel), _dp(self._om)
+        nt = geometry.get("node_type")
+        self._nt = _u8(np.asarray(nt).reshape(-1)) if nt is not None else None
+        c.node_type = _u8p(self._nt)
+        ic = geometry.get("inlet_center", (0.0, 0.0))
+        c.inlet_center[0], c.inlet_center[1] = float(ic[0]), float(ic[1])
+        c.inlet_radius = float(geometry.get("inlet_radius", 1.0))
+        c.inlet_umax = float(geometry.get("inlet_umax", 0.0))
         c.storage = STORAGE[storage]
         c.stochastic = 1 if stochastic else 0
         c.seed = int(seed) & 0xffffffffffffffff
@@ -357,6 +368,14 @@ class Oracle:
         f = np.zeros(19 * self.N)
         lib().orc_populations(self._h, _dp(f))
         return f.reshape(19, self.N)
+
+    def wall_shear(self):
+        """(nodes, tau (n, 3)) of the wall-adjacent fluid nodes (orc_wall_shear)."""
+        cap = self.N
+        nodes = np.zeros(cap, dtype=np.int64)
+        tau = np.zeros(3 * cap)
+        n = lib().orc_wall_shear(self._h, nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(tau), cap)
+        return nodes[:n].copy(), tau[: 3 * n].reshape(n, 3).copy()
 
     def set_populations(self, f):
         f = _f64(f, (19 * self.N,))

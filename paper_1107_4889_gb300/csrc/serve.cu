@@ -102,6 +102,7 @@ struct Active {
     int head = 0, in_flight = 0;
     double t_admit = 0.0;
     int status = RBC_OK;
+    bool released = false;  // arena block returned
 };
 
 double seconds_since(std::chrono::steady_clock::time_point t0)
@@ -171,7 +172,8 @@ void release(rbc_server *s, Active &a)
     a.tick = a.last = nullptr;
     if (a.h) rbc_free(a.h);
     a.h = nullptr;
-    if (a.req) s->arena.release(a.off, a.req->bytes);
+    if (a.req && !a.released) s->arena.release(a.off, a.req->bytes);
+    a.released = true;
     if (a.stream_slot >= 0) s->free_streams.push_back(a.stream_slot);
     a.stream_slot = -1;
 }

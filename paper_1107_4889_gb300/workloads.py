@@ -86,6 +86,25 @@ def tube(n, radius, length=None, body_force=(0.0, 0.0, 0.0)):
                 body_force=tuple(float(b) for b in body_force))
 
 
+NODE_INLET, NODE_OUTLET = 1, 2
+
+
+def open_tube(n, length, radius, umax):
+    """Tube along z (axis at ((n-1)/2, (n-1)/2), nodes farther than
+    ``radius`` solid) with a velocity inlet on the plane z = 0 (Poiseuille
+    profile umax (1 - r^2/radius^2) along +z) and a pressure outlet on the
+    plane z = length - 1; the z index wraps, so the two planes are adjacent
+    and neither pulls from the other."""
+    g = tube(n, radius, length)
+    nt = np.zeros((length, n, n), dtype=np.uint8)
+    fluid = g["solid"] == 0
+    nt[0][fluid[0]] = NODE_INLET
+    nt[length - 1][fluid[length - 1]] = NODE_OUTLET
+    c = (n - 1) / 2.0
+    g.update(node_type=nt, inlet_center=(c, c), inlet_radius=float(radius), inlet_umax=float(umax))
+    return g
+
+
 def fluid_count(geom):
     N = geom["nx"] * geom["ny"] * geom["nz"]
     return N if geom["solid"] is None else int(N - int(np.count_nonzero(geom["solid"])))

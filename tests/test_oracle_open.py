@@ -1,0 +1,93 @@
+"""Pins of the oracle's open boundaries (velocity inlet, pressure outlet) and
+wall shear stress against Hagen-Poiseuille flow in a tube.
+
+Closed forms for steady flow in a tube of radius R: u_z(r) = U (1 - r^2/R^2),
+flux Q = pi R^2 U / 2, pressure gradient dp/dz = -4 mu U / R^2 (p = rho/3,
+mu = rho nu), wall shear stress mu 2 U / R.  The staircase wall moves the
+effective radius off the nominal one, so R is taken from the measured flux and
+centre velocity, R^2 = 2 Q / (pi U).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1107_4889_gb300 import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def tube_state():
+    n, L, R, U = 16, 40, 6.0, 0.02
+    geom = wl.open_tube(n, L, R, U)
+    o = orc.Oracle(geom, None, wl.params())
+    o.step(3000)
+    rho, u, _ = o.fields()
+    b0 = o.budget()
+    o.step(200)
+    rho2, u2, _ = o.fields()
+    b1 = o.budget()
+    nodes, tau = o.wall_shear()
+    o.close()
+    return dict(n=n, L=L, R=R, U=U, geom=geom, rho=rho.reshape(L, n, n), u=u.reshape(L, n, n, 3),
+                u2=u2.reshape(L, n, n, 3), b0=b0, b1=b1, nodes=nodes, tau=tau)
+
+
+def test_inlet_profile_and_steady_flux(tube_state):
+    t = tube_state
+    rho, u, L, n = t["rho"], t["u"], t["L"], t["n"]
+    fluid = t["geom"]["solid"][0] == 0
+    F = np.array([(rho[z] * u[z, :, :, 2])[fluid].sum() for z in range(L)])
+    # mass conservation: the same mass flux through every interior section
+    assert np.abs(F[1:-1] / F[L // 2] - 1.0).max() < 1e-4
+    # steady: nothing changes over 200 more steps, the mass is constant
+    assert np.abs(t["u2"] - u).max() < 1e-4 * t["U"]
+    assert abs(t["b1"]["mass"] / t["b0"]["mass"] - 1.0) < 1e-9
+    # the equilibrium inlet passes the prescribed flux to within its first-order
+    # boundary error (measured 3.7 %)
+    assert abs(F[0] / F[L // 2] - 1.0) < 0.05
+    # fully developed Poiseuille profile in the middle, away from the
+    # staircase wall: u = Umax (1 - r^2/R^2) with R from the flux
+    c = (n - 1) / 2.0
+    yy, xx = np.mgrid[0:n, 0:n]
+    r2 = (xx - c) ** 2 + (yy - c) ** 2
+    um = u[L // 2, :, :, 2]
+    Umax, Q = um[fluid].max(), um[fluid].sum()
+    R2 = 2.0 * Q / (np.pi * Umax)
+    inner = fluid & (r2 < (t["R"] - 2.0) ** 2)
+    assert np.abs(um[inner] - Umax * (1.0 - r2[inner] / R2)).max() < 0.02 * Umax
+    assert np.abs(u[L // 2, :, :, :2]).max() < 1e-3 * t["U"]
+
+
+def test_pressure_gradient_is_hagen_poiseuille(tube_state):
+    t = tube_state
+    rho, u, L = t["rho"], t["u"], t["L"]
+    fluid = t["geom"]["solid"][0] == 0
+    zs = np.arange(L // 4, 3 * L // 4)
+    p = np.array([rho[z][fluid].mean() / 3.0 for z in zs])
+    dpdz = np.polyfit(zs, p, 1)[0]
+    Umax = u[L // 2, :, :, 2][fluid].max()
+    Q = u[L // 2, :, :, 2][fluid].sum()
+    R2 = 2.0 * Q / (np.pi * Umax)
+    nu = 1.0 / 6.0
+    assert abs(dpdz / (-4.0 * nu * Umax / R2) - 1.0) < 0.10  # measured 6.5 % (staircase wall)
+    # the outlet holds rho = 1
+    assert abs(rho[L - 1][fluid].mean() - 1.0) < 1e-9 + 1e-3 * abs(dpdz) * L
+
+
+def test_wall_shear_stress_of_poiseuille(tube_state):
+    t = tube_state
+    L, n = t["L"], t["n"]
+    z = t["nodes"] // (n * n)
+    sel = (z >= L // 4) & (z < 3 * L // 4)
+    wss = np.linalg.norm(t["tau"][sel], axis=1)
+    u = t["u"]
+    fluid = t["geom"]["solid"][0] == 0
+    Umax = u[L // 2, :, :, 2][fluid].max()
+    Q = u[L // 2, :, :, 2][fluid].sum()
+    R = np.sqrt(2.0 * Q / (np.pi * Umax))
+    nu = 1.0 / 6.0
+    # the traction is axial at a straight wall: the stress on the tangent
+    # plane points along z
+    assert np.abs(t["tau"][sel][:, 2]).mean() > 20 * np.abs(t["tau"][sel][:, :2]).mean()
+    # mean over the wall nodes against mu 2 U / R (the nodes sit half a
+    # lattice spacing inside the wall, where the shear is (R - 1/2)/R of it)
+    assert abs(wss.mean() / (nu * 2.0 * Umax / R) - 1.0) < 0.15
