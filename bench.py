@@ -52,6 +52,11 @@ def _workload(name, precision="f32"):
     elif name == "box32":
         g, c, p = wl.box_workload()
         desc = "periodic box 32^3, 32 RBC (H=0.098), G=1e-6"
+    elif name == "ybif":
+        g, c, p = wl.ybif_workload()
+        desc = (f"Y-bifurcation in 512^3 (parent r=60, daughters r=45 at +-35 deg), {wl.fluid_count(g)} fluid nodes "
+                f"(node list), {len(c['pos'])} RBC (H={len(c['pos']) * wl.CELL_VOLUME / wl.fluid_count(g):.2f} of the "
+                f"lumen, slot-limited), inlet Poiseuille u_max={g['inlet_umax']}, pressure outlets")
     elif name in ("box256", "box128"):
         L = int(name[3:])
         g = wl.periodic_box(L, body_force=(1e-6, 0.0, 0.0))
@@ -418,13 +423,64 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_wss_map(args):
+    """Time-averaged wall-shear-stress map of the workload (ybif by default)
+    with binary16 storage against the FP32 run of the same seed: --steps
+    coupled steps each, the stress sampled every 20 steps over the second
+    half; prints relative L2 and percentiles of the magnitude difference and
+    the MLUPS of both runs."""
+    import torch
+
+    from paper_1107_4889_gb300 import build as B
+    from paper_1107_4889_gb300.rbc import Solver
+
+    B.build()
+    torch.cuda.set_device(0)
+    name = args.workload if args.workload != "channel" else "ybif"
+    res = {}
+    for prec in ("f32", "f16"):
+        geom, cells, params, desc = _workload(name, prec)
+        nf = wl.fluid_count(geom)
+        s = Solver(geom, cells, params)
+        s.step(args.warmup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = 0
+        while done < args.steps:
+            k = min(20, args.steps - done)
+            s.step(k)
+            done += k
+            if done >= args.steps // 2:
+                s.wss_accumulate()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        nodes, tau, samples = s.wss()
+        st = s.stats()
+        s.close()
+        res[prec] = dict(mag=np.linalg.norm(tau[np.argsort(nodes)], axis=1), mlups=nf * args.steps / dt / 1e6,
+                         samples=samples, max_u=st["max_u"], desc=desc)
+    a, b = res["f16"]["mag"], res["f32"]["mag"]
+    rel = np.abs(a - b) / np.maximum(b, 1e-3 * b.max())
+    line = {"metric": "wall-shear-stress map, binary16 vs FP32", "workload": res["f32"]["desc"],
+            "steps": args.steps, "samples": res["f32"]["samples"], "wall_nodes": int(len(b)),
+            "rel_l2": float(np.linalg.norm(a - b) / np.linalg.norm(b)),
+            "rel_median": float(np.median(rel)), "rel_p99": float(np.percentile(rel, 99)),
+            "mean_wss_f32": float(b.mean()), "mean_wss_f16": float(a.mean()),
+            "mlups_f32": res["f32"]["mlups"], "mlups_f16": res["f16"]["mlups"],
+            "max_u": [res["f32"]["max_u"], res["f16"]["max_u"]]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["channel", "box32", "tube", "box256", "box128"], default="channel")
+    ap.add_argument("--workload", choices=["channel", "box32", "tube", "box256", "box128", "ybif"],
+                    default="channel")
+    ap.add_argument("--wss-map", action="store_true",
+                    help="wall-shear-stress map of the workload, binary16 against FP32")
     ap.add_argument("--no-cells", action="store_true", help="drop the workload's cells (lattice pass alone)")
     ap.add_argument("--precision", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -440,6 +496,9 @@ def main():
     args = ap.parse_args()
     if args.serve:
         run_serve(args)
+        return
+    if args.wss_map:
+        run_wss_map(args)
         return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

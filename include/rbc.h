@@ -51,14 +51,31 @@ typedef struct rbc_handle rbc_handle;
  * 1 = solid node, NULL = all fluid; copied at init.  The external force
  * density at a fluid node (x, y, z) is body_force + body_force_wave *
  * sin(2 pi y / ny) (lattice units): a uniform drive, plus the Kolmogorov
- * profile that sustains a shear flow in a fully periodic box. */
+ * profile that sustains a shear flow in a fully periodic box.
+ * Open boundaries (the paper drives vessels by an inlet velocity and an
+ * outlet pressure, Sec. 4, citing the rules without giving them):
+ * node_type (host, nx*ny*nz bytes, NULL = none; copied) marks fluid nodes
+ * RBC_NODE_INLET or RBC_NODE_OUTLET.  Boundary nodes are not collided; each
+ * pass sets their populations from the previous pass: an inlet node takes
+ * f_eq(rho of its neighbour at z + 1, u_in) with u_in = inlet_umax (1 -
+ * r^2 / inlet_radius^2) along +z, r the distance of (x, y) from
+ * inlet_center; an outlet node takes f_eq(1, u_m) plus the non-equilibrium
+ * part of its neighbour m at z - 1.  The neighbour is the node straight
+ * across if fluid, else the first fluid one of x - 1, x + 1, y - 1, y + 1 on
+ * that plane (oblique vessels).  Cells must stay clear of them. */
 typedef struct {
     int nx, ny, nz;
     int periodic[3];
     const uint8_t *solid;
     double body_force[3];
     double body_force_wave[3];
+    const uint8_t *node_type;
+    double inlet_center[2], inlet_radius, inlet_umax;
 } rbc_geometry;
+
+#define RBC_NODE_INTERIOR 0
+#define RBC_NODE_INLET 1
+#define RBC_NODE_OUTLET 2
 
 /* Initial cell state (Sec. 2.2: Gamma_i = (R_i, Q_i, V_i, Omega_i)).  Host
  * arrays, copied at init: pos 3n (inside the box), quat 4n (need not be
@@ -102,6 +119,10 @@ typedef struct {
  *                       RBC_ROUND_NEAREST (ties to even, IEEE) is biased by
  *                       percents in slow steady flows [stochastic]
  *   seed                key of the stochastic rounding [0]
+ *   node_list           lattice pass over a list of the fluid nodes (one
+ *                       thread each, no work on solid nodes) instead of whole
+ *                       staged rows: 1 always, -1 never, 0 when fewer than
+ *                       half the nodes are fluid (sparse vessel geometries)
  *   stream              cudaStream_t the library works on (NULL: one it
  *                       creates and owns). */
 typedef struct {
@@ -121,6 +142,7 @@ typedef struct {
     int precision;
     int rounding;
     uint64_t seed;
+    int node_list;
     void *stream;
 } rbc_params;
 
@@ -225,6 +247,21 @@ typedef struct {
     int trials;                  /* shapes timed */
 } rbc_tune_report;
 int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out);
+
+/* Wall shear stress (the quantity Sec. 4 maps in the coronary geometry).
+ * At every fluid node with a solid link neighbour the wall normal n is the
+ * unit sum of its links that stay in the fluid (minus those into the
+ * wall), and the wall shear stress is the traction of the stress on the
+ * tangent plane, sigma n - (n . sigma n) n, with the sigma of Eq.
+ * stresstensorLB (requires walls, and cells with alpha_tt != 0 or open
+ * boundaries, for sigma to be computed).  rbc_wss_accumulate enqueues on the
+ * handle's stream the addition of the current value to per-node sums;
+ * rbc_wss synchronises and copies the node indices (node[k]) and the
+ * time-averaged vectors (tau[3k..]) of up to max nodes, returning their
+ * number in *n and the number of samples in *samples.  RBC_EINVAL without
+ * walls or stress. */
+int rbc_wss_accumulate(rbc_handle *h);
+int rbc_wss(rbc_handle *h, int64_t *node, double *tau, int64_t max, int64_t *n, int64_t *samples);
 
 /* Kernel launches one rbc_step(h, 1) enqueues. */
 int rbc_launches_per_step(const rbc_handle *h);

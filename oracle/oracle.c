@@ -1056,17 +1056,33 @@ static double feq(int p, double r, const double v[3])
  * populations are set from the post-collision populations of the previous
  * pass (fprev), so that every node of the pass reads only the previous state:
  *   inlet node n:  f_p = f_p^eq(rho_d, u_in(x, y)), rho_d the density of the
- *                  downstream neighbour n + z (the pressure floats at the
- *                  inlet), u_in = u_max (1 - r^2/R^2) z;
+ *                  downstream neighbour (bc_neighbour on z + 1; 1 if there
+ *                  is none; the pressure floats at the inlet),
+ *                  u_in = u_max (1 - r^2/R^2) z;
  *   outlet node n: f_p = f_p^eq(1, u_m) + [f_p(m) - f_p^eq(rho_m, u_m)],
- *                  m = n - z the upstream neighbour with its density and
- *                  velocity (rho = 1 with the neighbour's non-equilibrium
- *                  part carried over).
+ *                  m the upstream neighbour (bc_neighbour on z - 1) with its
+ *                  density and velocity (rho = 1 with the neighbour's
+ *                  non-equilibrium part carried over); f^eq(1, 0) if there
+ *                  is none.
  * Their reported rho and u are the moments of the set populations, sigma 0.
  */
+/* The neighbour a boundary node takes its state from, on the plane dz = +1
+ * (inlet) or -1 (outlet): the node straight across if it is fluid, else the
+ * first fluid one of (x-1, y), (x+1, y), (x, y-1), (x, y+1) on that plane
+ * (a tilted vessel meets the plane obliquely); -1 if none is. */
+static long bc_neighbour(const orc_state *s, int x, int y, int z, int dz)
+{
+    static const int off[5][2] = {{0, 0}, {-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+    for (int k = 0; k < 5; k++) {
+        long m = node_of(s->nx, s->ny, s->nz, x + off[k][0], y + off[k][1], z + dz);
+        if (!is_solid(s->solid, m)) return m;
+    }
+    return -1;
+}
+
 static void open_boundaries(orc_state *s)
 {
-    const int nx = s->nx, ny = s->ny, nz = s->nz;
+    const int nx = s->nx, ny = s->ny;
     const long N = s->N, nxy = (long)nx * ny;
     for (long n = 0; n < N; n++) {
         const int t = s->node_type[n];
@@ -1074,23 +1090,29 @@ static void open_boundaries(orc_state *s)
         const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / nxy);
         double fb[NQ];
         if (t == ORC_NODE_INLET) {
-            long d = node_of(nx, ny, nz, x, y, z + 1);
-            double rd = 0.0;
-            for (int p = 0; p < NQ; p++) rd += s->fprev[(long)p * N + d];
+            long d = bc_neighbour(s, x, y, z, 1);
+            double rd = d < 0 ? 1.0 : 0.0;
+            if (d >= 0)
+                for (int p = 0; p < NQ; p++) rd += s->fprev[(long)p * N + d];
             double dx = x - s->in_c[0], dy = y - s->in_c[1];
             double r2 = (dx * dx + dy * dy) / (s->in_r * s->in_r);
             double v[3] = {0.0, 0.0, r2 < 1.0 ? s->in_umax * (1.0 - r2) : 0.0};
             for (int p = 0; p < NQ; p++) fb[p] = feq(p, rd, v);
         } else {
-            long m = node_of(nx, ny, nz, x, y, z - 1);
-            double rm = 0.0, j[3] = {0.0, 0.0, 0.0};
-            for (int p = 0; p < NQ; p++) {
-                double fp = s->fprev[(long)p * N + m];
-                rm += fp;
-                for (int a = 0; a < 3; a++) j[a] += fp * CV[p][a];
+            long m = bc_neighbour(s, x, y, z, -1);
+            if (m < 0) {
+                const double zero[3] = {0.0, 0.0, 0.0};
+                for (int p = 0; p < NQ; p++) fb[p] = feq(p, 1.0, zero);
+            } else {
+                double rm = 0.0, j[3] = {0.0, 0.0, 0.0};
+                for (int p = 0; p < NQ; p++) {
+                    double fp = s->fprev[(long)p * N + m];
+                    rm += fp;
+                    for (int a = 0; a < 3; a++) j[a] += fp * CV[p][a];
+                }
+                double v[3] = {j[0] / rm, j[1] / rm, j[2] / rm};
+                for (int p = 0; p < NQ; p++) fb[p] = feq(p, 1.0, v) + (s->fprev[(long)p * N + m] - feq(p, rm, v));
             }
-            double v[3] = {j[0] / rm, j[1] / rm, j[2] / rm};
-            for (int p = 0; p < NQ; p++) fb[p] = feq(p, 1.0, v) + (s->fprev[(long)p * N + m] - feq(p, rm, v));
         }
         double r = 0.0, jj[3] = {0.0, 0.0, 0.0};
         for (int p = 0; p < NQ; p++) {

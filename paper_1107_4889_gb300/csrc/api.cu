@@ -32,6 +32,12 @@ struct Problem {
     long long Np;
     int per[3];
     bool any_solid;
+    bool has_bc;       // open-boundary nodes
+    bool need_links;   // link words: walls or open boundaries
+    bool use_list;     // node-list lattice pass
+    bool want_sigma;   // stress output (cells with alpha != 0, or open boundaries)
+    int nfluid;
+    int nwss;          // wall-adjacent fluid nodes (wall shear stress)
     int nc;
     int prec, stochastic;
     unsigned long long seed;
@@ -89,13 +95,26 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     if (19LL * P.Np >= (1LL << 32)) return fail(err, RBC_EINVAL, "lattice too large (19 * nodes must stay below 2^32)");
     for (int a = 0; a < 3; ++a) P.per[a] = g->periodic[a] ? 1 : 0;
     P.any_solid = false;
+    P.nfluid = (int)N;
     if (g->solid) {
-        for (long long n = 0; n < N; ++n)
-            if (g->solid[n]) {
-                P.any_solid = true;
-                break;
-            }
+        long long ns = 0;
+        for (long long n = 0; n < N; ++n) ns += g->solid[n] ? 1 : 0;
+        P.any_solid = ns > 0;
+        P.nfluid = (int)(N - ns);
     }
+    P.has_bc = false;
+    if (g->node_type) {
+        for (long long n = 0; n < N; ++n) {
+            const int t = g->node_type[n];
+            if (t != RBC_NODE_INTERIOR && t != RBC_NODE_INLET && t != RBC_NODE_OUTLET)
+                return fail(err, RBC_EINVAL, "node_type must be RBC_NODE_INTERIOR, _INLET or _OUTLET");
+            if (t == RBC_NODE_INTERIOR) continue;
+            if (g->solid && g->solid[n]) return fail(err, RBC_EINVAL, "an open-boundary node is solid");
+            P.has_bc = true;
+        }
+        if (P.has_bc && !(g->inlet_radius > 0.0)) return fail(err, RBC_EINVAL, "inlet_radius must be positive");
+    }
+    P.need_links = P.any_solid || P.has_bc;
     // a non-periodic axis must be closed by solid end planes (indices wrap)
     const int dims[3] = {g->nx, g->ny, g->nz};
     for (int a = 0; a < 3; ++a) {
@@ -131,6 +150,8 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
         return fail(err, RBC_EINVAL, "precision must be RBC_PREC_F32, RBC_PREC_F16 or RBC_PREC_BF16");
     if (q.rounding != RBC_ROUND_STOCHASTIC && q.rounding != RBC_ROUND_NEAREST)
         return fail(err, RBC_EINVAL, "rounding must be RBC_ROUND_STOCHASTIC or RBC_ROUND_NEAREST");
+    if (q.node_list < -1 || q.node_list > 1) return fail(err, RBC_EINVAL, "node_list must be -1, 0 or 1");
+    P.use_list = q.node_list == 1 || (q.node_list == 0 && 2LL * P.nfluid < N);
     P.prec = q.precision;
     P.stochastic = q.rounding == RBC_ROUND_STOCHASTIC ? 1 : 0;
     P.seed = (unsigned long long)q.seed;
@@ -141,6 +162,10 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
 
     Params &p = P.p;
     p.wave = 0;
+    p.in_c[0] = (float)g->inlet_center[0];
+    p.in_c[1] = (float)g->inlet_center[1];
+    p.in_ir2 = P.has_bc ? (float)(1.0 / (g->inlet_radius * g->inlet_radius)) : 0.0f;
+    p.in_umax = (float)g->inlet_umax;
     for (int a = 0; a < 3; ++a) {
         if (!std::isfinite(g->body_force[a]) || !std::isfinite(g->body_force_wave[a]))
             return fail(err, RBC_EINVAL, "non-finite body force");
@@ -229,20 +254,22 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     P.wall_start.assign(P.nwbins + 1, 0);
     P.wall_xyz.clear();
     if (P.any_solid && nc > 0) {
+        // solid nodes with a fluid link neighbour: marked from the fluid side
+        std::vector<uint8_t> wet((size_t)N, 0);
+        for (int z = 0; z < P.nz; ++z)
+            for (int y = 0; y < P.ny; ++y)
+                for (int x = 0; x < P.nx; ++x) {
+                    if (g->solid[(long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z)]) continue;
+                    for (int p = 1; p < kQ; ++p) {
+                        const long long m = node(P, x + cx(p), y + cy(p), z + cz(p));
+                        if (g->solid[m]) wet[m] = 1;
+                    }
+                }
         std::vector<int> xyz, bins;
         for (int z = 0; z < P.nz; ++z)
             for (int y = 0; y < P.ny; ++y)
                 for (int x = 0; x < P.nx; ++x) {
-                    if (!g->solid[(long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z)]) continue;
-                    bool wet = false;
-                    for (int dz = -1; dz <= 1 && !wet; ++dz)
-                        for (int dy = -1; dy <= 1 && !wet; ++dy)
-                            for (int dx = -1; dx <= 1 && !wet; ++dx) {
-                                const int m = std::abs(dx) + std::abs(dy) + std::abs(dz);
-                                if (m == 0 || m == 3) continue;
-                                if (!g->solid[node(P, x + dx, y + dy, z + dz)]) wet = true;
-                            }
-                    if (!wet) continue;
+                    if (!wet[(long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z)]) continue;
                     const int X[3] = {x, y, z};
                     int b[3];
                     for (int a = 0; a < 3; ++a)
@@ -262,6 +289,20 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
             for (int a = 0; a < 3; ++a) P.wall_xyz[3 * at + a] = xyz[3 * w + a];
         }
     }
+    P.want_sigma = (nc > 0 && q.alpha_tt != 0.0) || P.has_bc;
+    P.nwss = 0;
+    if (P.any_solid && P.want_sigma) {
+        for (int z = 0; z < P.nz; ++z)
+            for (int y = 0; y < P.ny; ++y)
+                for (int x = 0; x < P.nx; ++x) {
+                    if (g->solid[(long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z)]) continue;
+                    for (int p = 1; p < kQ; ++p)
+                        if (g->solid[node(P, x + cx(p), y + cy(p), z + cz(p))]) {
+                            P.nwss++;
+                            break;
+                        }
+                }
+    }
     P.budget_blocks = budget_blocks_for(P.N);
     return RBC_OK;
 }
@@ -276,19 +317,25 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.nz = P.nz;
     d.N = P.N;
     d.Np = P.Np;
-    d.walls = P.any_solid ? 1 : 0;
+    d.walls = P.need_links ? 1 : 0;
     d.prec = P.prec;
     d.stochastic = P.stochastic;
     d.seed = P.seed;
     d.pops[0] = cv.take<uint8_t>(19 * Np * (size_t)pop_bytes(P.prec));
     d.pops[1] = cv.take<uint8_t>(19 * Np * (size_t)pop_bytes(P.prec));
     d.U = cv.take<float>(3 * Np);
-    d.S = (P.nc > 0 && q->alpha_tt != 0.0) ? cv.take<float>(6 * Np) : nullptr;
+    d.S = P.want_sigma ? cv.take<float>(6 * Np) : nullptr;
     d.G = P.nc > 0 ? cv.take<float>(3 * Np) : nullptr;
     d.theta = P.nc > 0 ? cv.take<float>(Np) : nullptr;
     d.rho = cv.take<float>(Np);
     d.solid = P.any_solid ? cv.take<uint8_t>(Np) : nullptr;
-    d.links = P.any_solid ? cv.take<uint32_t>(Np) : nullptr;
+    d.links = P.need_links ? cv.take<uint32_t>(Np) : nullptr;
+    d.nfluid = P.nfluid;
+    d.fluid_list = P.use_list ? cv.take<uint32_t>((size_t)std::max(P.nfluid, 1)) : nullptr;
+    d.nwss = P.nwss;
+    d.wss_node = cv.take<int>((size_t)std::max(P.nwss, 1));
+    d.wss_n = cv.take<float>(3 * (size_t)std::max(P.nwss, 1));
+    d.wss_acc = cv.take<double>(3 * (size_t)std::max(P.nwss, 1));
     const size_t n = (size_t)std::max(P.nc, 1);
     d.nc = P.nc;
     d.R = cv.take<double>(3 * n);
@@ -376,6 +423,7 @@ struct rbc_handle {
     cudaEvent_t ev_dummy[3] = {nullptr, nullptr, nullptr}, fork_ev = nullptr, join_ev = nullptr;
     cudaEvent_t join2_ev = nullptr;
     int64_t step = 0;
+    int64_t wss_samples = 0;
     int timing_cap = 0, timing_used = 0;
     std::vector<cudaEvent_t> ev;  // 3 per timed step: before the cell kernel, after it, after the lattice pass
     std::string err;
@@ -596,20 +644,58 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
         if (d.solid) {
             RBC_CU(cudaMemsetAsync(d.solid, 0, Np, s));
             RBC_CU(cudaMemcpyAsync(d.solid, geom->solid, (size_t)P.N, cudaMemcpyHostToDevice, s));
-            // per-node link mask in the library's velocity ordering: bit p set
-            // when the downstream node x + c_p is solid, bit 31 when x is solid
-            // (set from the solid nodes: node m = s - c_p has x + c_p = s)
+        }
+        std::vector<uint32_t> flist;
+        std::vector<int> wnode;
+        std::vector<float> wnrm;
+        if (d.links) {
+            // per-node link word in the library's velocity ordering: bit p set
+            // when the downstream node x + c_p is solid (fluid nodes), bit 29 /
+            // 30 for inlet / outlet nodes, bit 31 when x is solid
             links.assign((size_t)P.N, 0u);
             for (int z = 0; z < P.nz; ++z)
                 for (int y = 0; y < P.ny; ++y) {
                     const long long row = (long long)P.nx * ((long long)y + (long long)P.ny * z);
                     for (int x = 0; x < P.nx; ++x) {
-                        if (!geom->solid[row + x]) continue;
-                        links[row + x] |= 1u << 31;
-                        for (int p = 1; p < kQ; ++p) links[node(P, x - cx(p), y - cy(p), z - cz(p))] |= 1u << p;
+                        const long long n = row + x;
+                        if (geom->solid && geom->solid[n]) {
+                            links[n] = 1u << 31;
+                            continue;
+                        }
+                        uint32_t m = 0u;
+                        float nv[3] = {0.f, 0.f, 0.f};
+                        if (geom->solid)
+                            for (int p = 1; p < kQ; ++p)
+                                if (geom->solid[node(P, x + cx(p), y + cy(p), z + cz(p))]) {
+                                    m |= 1u << p;
+                                    nv[0] -= (float)cx(p);
+                                    nv[1] -= (float)cy(p);
+                                    nv[2] -= (float)cz(p);
+                                }
+                        if (geom->node_type && geom->node_type[n] == RBC_NODE_INLET) m |= 1u << 29;
+                        if (geom->node_type && geom->node_type[n] == RBC_NODE_OUTLET) m |= 1u << 30;
+                        links[n] = m;
+                        if ((m & 0x7FFFEu) && P.nwss > 0) {
+                            const float nn = std::sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+                            wnode.push_back((int)n);
+                            for (int a = 0; a < 3; ++a) wnrm.push_back(nn > 0.f ? nv[a] / nn : 0.f);
+                        }
                     }
                 }
             RBC_CU(cudaMemcpyAsync(d.links, links.data(), links.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        }
+        if (d.fluid_list) {
+            flist.reserve((size_t)P.nfluid);
+            for (long long n = 0; n < (long long)P.N; ++n)
+                if (!(geom->solid && geom->solid[n])) flist.push_back((uint32_t)n);
+            RBC_CU(cudaMemcpyAsync(d.fluid_list, flist.data(), flist.size() * sizeof(uint32_t),
+                                   cudaMemcpyHostToDevice, s));
+        }
+        if (d.nwss > 0) {
+            if ((int)wnode.size() != d.nwss) return fail(&h->err, RBC_EINVAL, "wall node count mismatch");
+            RBC_CU(cudaMemcpyAsync(d.wss_node, wnode.data(), wnode.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+            RBC_CU(cudaMemcpyAsync(d.wss_n, wnrm.data(), wnrm.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+            RBC_CU(cudaMemsetAsync(d.wss_acc, 0, 3 * sizeof(double) * (size_t)d.nwss, s));
         }
         RBC_CU(cudaMemsetAsync(d.flags, 0, 8 * sizeof(int), s));
         RBC_CU(cudaMemsetAsync(d.lb_work, 0, 2 * sizeof(int), s));
@@ -951,6 +1037,38 @@ int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out)
     rc = recapture_steps(h);
     if (out) *out = rep;
     return rc;
+}
+
+int rbc_wss_accumulate(rbc_handle *h)
+{
+    if (!h) return fail(nullptr, RBC_EINVAL, "handle is NULL");
+    if (h->d.nwss <= 0 || !h->d.S) return fail(&h->err, RBC_EINVAL, "no wall nodes or no stress output");
+    launch_wss(h->d, h->stream);
+    RBC_CU(cudaGetLastError());
+    h->wss_samples++;
+    return RBC_OK;
+}
+
+int rbc_wss(rbc_handle *h, int64_t *node, double *tau, int64_t max, int64_t *n, int64_t *samples)
+{
+    if (!h || !n || !samples || (max > 0 && (!node || !tau)))
+        return fail(h ? &h->err : nullptr, RBC_EINVAL, "NULL argument");
+    if (h->d.nwss <= 0 || !h->d.S) return fail(&h->err, RBC_EINVAL, "no wall nodes or no stress output");
+    const size_t nw = (size_t)h->d.nwss;
+    std::vector<int> idx(nw);
+    std::vector<double> acc(3 * nw);
+    RBC_CU(cudaMemcpyAsync(idx.data(), h->d.wss_node, nw * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    RBC_CU(cudaMemcpyAsync(acc.data(), h->d.wss_acc, 3 * nw * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    RBC_CU(cudaStreamSynchronize(h->stream));
+    const double inv = h->wss_samples > 0 ? 1.0 / (double)h->wss_samples : 0.0;
+    const size_t k = std::min(nw, (size_t)std::max<int64_t>(max, 0));
+    for (size_t i = 0; i < k; ++i) {
+        node[i] = idx[i];
+        for (int a = 0; a < 3; ++a) tau[3 * i + a] = acc[3 * i + a] * inv;
+    }
+    *n = (int64_t)nw;
+    *samples = h->wss_samples;
+    return RBC_OK;
 }
 
 int rbc_launches_per_step(const rbc_handle *h)

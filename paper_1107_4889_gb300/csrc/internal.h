@@ -39,7 +39,16 @@ struct Dev {
     float *theta;       // 1 plane: sum of smoothed characteristic functions (zeroed by the pass)
     float *rho;         // 1 plane: density for field output
     uint8_t *solid;     // N bytes or null
-    uint32_t *links;    // N words or null: bit p (1..18) = node + c_p is solid, bit 31 = node is solid
+    uint32_t *links;    // N words or null: bit p (1..18) = node + c_p is solid, bit 29 = inlet node,
+                        // bit 30 = outlet node, bit 31 = node is solid
+    uint32_t *fluid_list;  // node-list pass: the fluid nodes in lattice order, or null
+    int nfluid;
+    // wall shear stress: wall-adjacent fluid nodes, unit normals into the
+    // fluid (3 floats each), time sums of the tangential traction
+    int nwss;
+    int *wss_node;
+    float *wss_n;
+    double *wss_acc;
     // cells (SoA FP64)
     int nc;
     double *R, *q, *V, *Om;  // 3n, 4n, 3n, 3n
@@ -88,6 +97,7 @@ struct Params {
     float gext[3];
     float gwave[3];  // amplitude of the force profile sin(2 pi y / ny)
     int wave;        // gwave != 0
+    float in_c[2], in_ir2, in_umax;  // inlet profile: centre, 1 / radius^2, peak velocity
     float tau0, delta, kappa, alpha;
     float mach2;
     float xi[3];
@@ -112,6 +122,7 @@ int lb_shapes(const Dev &d, int *stages, int *ctas_per_sm, int max);  // staged-
 void set_lb_shape(Dev &d, int stages, int ctas_per_sm);
 void launch_lb(const Dev &d, const Params &p, int parity, cudaStream_t s);
 void launch_rho(const Dev &d, int parity, cudaStream_t s);
+void launch_wss(const Dev &d, cudaStream_t s);
 void launch_budget(const Dev &d, const Params &p, int parity, cudaStream_t s, bool accumulate = false,
                    long long from = 0);
 int budget_blocks_for(int N);

@@ -49,6 +49,7 @@ struct LbArgs {
     float gx0, gy0, gz0, tau0, delta, mach2;
     float wx, wy, wz;  // amplitude of the external force profile sin(2 pi y / ny)
     int wave;
+    float in_cx, in_cy, in_ir2, in_umax;  // inlet profile
     uint32_t key0, key1;  // seed of the stochastic rounding
     int stochastic;
 };
@@ -285,6 +286,108 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
     }
 }
 
+// Open-boundary node n = (x, y, z) (bit 29 of its link word: inlet, bit 30:
+// outlet), not collided: its populations are set from the previous pass
+// (the source buffer), as deviations from the weights,
+//   inlet:  d_p = f_p^eq(rho_d, u_in) - w_p, rho_d the density of the
+//           neighbour on z + 1 (bc_neighbour; 1 if none), u_in = u_max
+//           (1 - r^2/R^2) z;
+//   outlet: d_p = d_p(m) - w_p drho_m (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u^2),
+//           m the neighbour on z - 1 with density 1 + drho_m and velocity
+//           u, i.e. f^eq(1, u) plus the non-equilibrium part of m (d = 0,
+//           f^eq(1, 0), if none);
+// stored like any population (same rounding), with u their moments, sigma
+// 0, and G, theta cleared.
+// The neighbour a boundary node takes its state from, on the plane z + dz:
+// straight across if fluid, else the first fluid one of the links
+// (-1, 0, dz), (+1, 0, dz), (0, -1, dz), (0, +1, dz) (a tilted vessel meets
+// the plane obliquely); -1 if none is.  lk holds the node's solid links.
+__device__ __forceinline__ long long bc_neighbour(const LbArgs &a, int x, int y, int z, int dz, uint32_t lk)
+{
+    const int off[5][2] = {{0, 0}, {-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+    for (int k = 0; k < 5; ++k) {
+        int p = -1;
+        for (int q = 1; q < kQ; ++q)
+            if (cx(q) == off[k][0] && cy(q) == off[k][1] && cz(q) == dz) p = q;
+        if (p < 0 || ((lk >> p) & 1u)) continue;
+        return (long long)wrapm(x + off[k][0], a.nx) +
+               (long long)a.nx * (wrapm(y + off[k][1], a.ny) + (long long)a.ny * wrapm(z + dz, a.nz));
+    }
+    return -1;
+}
+
+template <typename St, bool CELLS, bool SIGMA>
+__device__ __noinline__ void boundary_node(const LbArgs &a, uint32_t n, int x, int y, int z, uint32_t lk,
+                                           unsigned long long step)
+{
+    const uint32_t Np = (uint32_t)a.Np;
+    const St *src = static_cast<const St *>(a.src);
+    St *dst = static_cast<St *>(a.dst);
+    float d[kQ];
+    if (lk & (1u << 29)) {
+        const long long dl = bc_neighbour(a, x, y, z, 1, lk);
+        const uint32_t dn = (uint32_t)(dl < 0 ? 0 : dl);
+        float drho = 0.f;
+        if (dl >= 0)
+            for_speeds<0, kQ>([&](auto pc) {
+                constexpr int p = decltype(pc)::value;
+                drho += Pop<St>::template get<p>(src[(uint32_t)p * Np + dn]);
+            });
+        const float rx = (float)x - a.in_cx, ry = (float)y - a.in_cy;
+        const float r2 = (rx * rx + ry * ry) * a.in_ir2;
+        const float uz = r2 < 1.0f ? a.in_umax * (1.0f - r2) : 0.0f;
+        const float rho = 1.0f + drho;
+        for_speeds<0, kQ>([&](auto pc) {
+            constexpr int p = decltype(pc)::value;
+            const float cu = float(cz(p)) * uz;
+            d[p] = wq(p) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uz * uz));
+        });
+    } else {
+        const long long ml = bc_neighbour(a, x, y, z, -1, lk);
+        const uint32_t m = (uint32_t)(ml < 0 ? 0 : ml);
+        float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+        for_speeds<0, kQ>([&](auto pc) {
+            constexpr int p = decltype(pc)::value;
+            d[p] = ml < 0 ? 0.f : Pop<St>::template get<p>(src[(uint32_t)p * Np + m]);
+            drho += d[p];
+            jx += float(cx(p)) * d[p];
+            jy += float(cy(p)) * d[p];
+            jz += float(cz(p)) * d[p];
+        });
+        const float ir = 1.0f / (1.0f + drho);
+        const float ux = jx * ir, uy = jy * ir, uz = jz * ir, usq = ux * ux + uy * uy + uz * uz;
+        for_speeds<0, kQ>([&](auto pc) {
+            constexpr int p = decltype(pc)::value;
+            const float cu = float(cx(p)) * ux + float(cy(p)) * uy + float(cz(p)) * uz;
+            d[p] -= wq(p) * drho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * usq);
+        });
+    }
+    const bool sr = Pop<St>::kRounds && a.stochastic != 0;
+    uint4 rb = make_uint4(0u, 0u, 0u, 0u);
+    if (sr) rb = philox4x32_10(make_uint4(n, (uint32_t)step, (uint32_t)(step >> 32), 0u), a.key0, a.key1);
+    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    for_speeds<0, kQ>([&](auto pc) {
+        constexpr int p = decltype(pc)::value;
+        dst[(uint32_t)p * Np + n] = Pop<St>::template put<p>(d[p], sr, rb);
+        drho += d[p];
+        jx += float(cx(p)) * d[p];
+        jy += float(cy(p)) * d[p];
+        jz += float(cz(p)) * d[p];
+    });
+    const float ir = 1.0f / (1.0f + drho);
+    a.U[n] = jx * ir;
+    a.U[Np + n] = jy * ir;
+    a.U[2 * Np + n] = jz * ir;
+    if (SIGMA)
+        for (int k = 0; k < 6; ++k) a.S[(uint32_t)k * Np + n] = 0.f;
+    if (CELLS) {
+        a.G[n] = 0.f;
+        a.G[Np + n] = 0.f;
+        a.G[2 * Np + n] = 0.f;
+        a.th[n] = 0.f;
+    }
+}
+
 // External force density at row y: the uniform drive plus the Kolmogorov
 // profile A sin(2 pi y / ny).
 __device__ __forceinline__ void external_force(const LbArgs &a, int y, float &gx, float &gy, float &gz)
@@ -334,6 +437,10 @@ __device__ __forceinline__ void lb_node(const LbArgs &a, int n, unsigned long lo
         T += a.delta * a.th[n];
     }
     if (WALLS && (lk >> 31)) return;  // solid node: nothing to collide
+    if (WALLS && (lk & 0x60000000u)) {
+        boundary_node<St, CELLS, SIGMA>(a, (uint32_t)n, x, y, z, lk, step);
+        return;
+    }
     collide_node<St, WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, (uint32_t)n, x, y, z, step);
 }
 
@@ -347,6 +454,29 @@ __global__ void __launch_bounds__(kLbThreads) k_lb(LbArgs a)
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n < a.N) lb_node<St, WALLS, CELLS, SIGMA>(a, n, step);
     // the last block out advances the pass counter
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&a.work[1], 1) == (int)gridDim.x - 1) {
+            a.work[1] = 0;
+            *a.step = step + 1;
+            __threadfence();
+        }
+    }
+}
+
+// Node-list pass: one thread per fluid node of a sorted list (sparse vessel
+// geometries, where whole rows would be mostly solid); the pull, collision
+// and stores are those of the one-thread-per-node pass.
+template <typename St, bool WALLS, bool CELLS, bool SIGMA>
+__global__ void __launch_bounds__(kLbThreads) k_lb_list(LbArgs a, const uint32_t *__restrict__ list, int nf)
+{
+    __shared__ unsigned long long s_step;
+    if (threadIdx.x == 0) s_step = *a.step;
+    __syncthreads();
+    const unsigned long long step = s_step;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nf) lb_node<St, WALLS, CELLS, SIGMA>(a, (int)list[t], step);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -518,6 +648,10 @@ __device__ __forceinline__ void consume_batch(const LbArgs &a, const StageLayout
         const uint32_t lk =
             WALLS ? reinterpret_cast<const uint32_t *>(frow)[(size_t)(CELLS ? 4 : 0) * plane_stride + xx] : 0u;
         if (WALLS && (lk >> 31)) continue;
+        if (WALLS && (lk & 0x60000000u)) {
+            boundary_node<St, CELLS, SIGMA>(a, n, xx, y, z, lk, step);
+            continue;
+        }
         const int xm = xx == 0 ? nx - 1 : xx - 1, xp = xx == nx - 1 ? 0 : xx + 1;
         float d[kQ];
         for_speeds<0, kQ>([&](auto pc) {
@@ -947,7 +1081,7 @@ struct PrepareOp {
     void run()
     {
         d.lb_grid = 0;
-        if (!staged_ok(d)) return;
+        if (d.fluid_list || !staged_ok(d)) return;
         StageLayout L = stage_layout(d);
         const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
         int dev = 0, sms = 0;
@@ -981,7 +1115,10 @@ struct LaunchOp {
     template <typename St, bool W, bool C, bool S_>
     void run()
     {
-        if (d.lb_grid > 0) {
+        if (d.fluid_list) {
+            const int g = (d.nfluid + kLbThreads - 1) / kLbThreads;
+            if (g > 0) k_lb_list<St, W, C, S_><<<g, kLbThreads, 0, s>>>(a, d.fluid_list, d.nfluid);
+        } else if (d.lb_grid > 0) {
             StageLayout L = stage_layout(d);
             L.stages = d.lb_stages;
             const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
@@ -1074,6 +1211,10 @@ static LbArgs lb_args(const Dev &d, const Params &p, int parity)
     a.wy = p.gwave[1];
     a.wz = p.gwave[2];
     a.wave = p.wave;
+    a.in_cx = p.in_c[0];
+    a.in_cy = p.in_c[1];
+    a.in_ir2 = p.in_ir2;
+    a.in_umax = p.in_umax;
     a.key0 = (uint32_t)(d.seed & 0xffffffffull);
     a.key1 = (uint32_t)(d.seed >> 32);
     a.stochastic = d.stochastic;
@@ -1169,6 +1310,31 @@ void launch_rho(const Dev &d, int parity, cudaStream_t s)
         k_rho<__nv_bfloat16><<<g, 256, 0, s>>>(d.pops[parity], d.solid, d.rho, d.N, d.Np);
     else
         k_rho<float><<<g, 256, 0, s>>>(d.pops[parity], d.solid, d.rho, d.N, d.Np);
+}
+
+// Wall shear stress: the traction sigma n of the last pass's stress on the
+// wall's tangent plane, t - (t.n) n, added to the node's time sums.
+__global__ void k_wss(const float *__restrict__ S, long long Np, const int *__restrict__ node,
+                      const float *__restrict__ nrm, double *__restrict__ acc, int nw)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nw) return;
+    const long long n = node[k];
+    const float sxx = S[n], syy = S[Np + n], szz = S[2 * Np + n];
+    const float sxy = S[3 * Np + n], sxz = S[4 * Np + n], syz = S[5 * Np + n];
+    const float nx = nrm[3 * k], ny = nrm[3 * k + 1], nz = nrm[3 * k + 2];
+    const float tx = sxx * nx + sxy * ny + sxz * nz;
+    const float ty = sxy * nx + syy * ny + syz * nz;
+    const float tz = sxz * nx + syz * ny + szz * nz;
+    const float tn = tx * nx + ty * ny + tz * nz;
+    acc[3 * k] += (double)(tx - tn * nx);
+    acc[3 * k + 1] += (double)(ty - tn * ny);
+    acc[3 * k + 2] += (double)(tz - tn * nz);
+}
+
+void launch_wss(const Dev &d, cudaStream_t s)
+{
+    if (d.nwss > 0 && d.S) k_wss<<<(d.nwss + 255) / 256, 256, 0, s>>>(d.S, d.Np, d.wss_node, d.wss_n, d.wss_acc, d.nwss);
 }
 
 int budget_blocks_for(int N)

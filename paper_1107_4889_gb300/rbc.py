@@ -32,7 +32,9 @@ _U8 = ctypes.POINTER(ctypes.c_uint8)
 class rbc_geometry(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("periodic", ctypes.c_int * 3), ("solid", _U8), ("body_force", ctypes.c_double * 3),
-                ("body_force_wave", ctypes.c_double * 3)]
+                ("body_force_wave", ctypes.c_double * 3), ("node_type", _U8),
+                ("inlet_center", ctypes.c_double * 2), ("inlet_radius", ctypes.c_double),
+                ("inlet_umax", ctypes.c_double)]
 
 
 class rbc_cells(ctypes.Structure):
@@ -50,7 +52,7 @@ class rbc_params(ctypes.Structure):
                 ("r_cut_wall", ctypes.c_double), ("mach_max", ctypes.c_double),
                 ("bin_capacity", ctypes.c_int), ("max_neighbors", ctypes.c_int),
                 ("precision", ctypes.c_int), ("rounding", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+                ("seed", ctypes.c_uint64), ("node_list", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 #: rbc_params.precision / rounding values (include/rbc.h)
@@ -86,7 +88,7 @@ class rbc_tune_report(ctypes.Structure):
 #: symbols include/rbc.h declares
 EXPORTS = ["rbc_default_params", "rbc_workspace_size", "rbc_init", "rbc_step", "rbc_fields",
            "rbc_stats", "rbc_cell_diag", "rbc_neighbors", "rbc_set_timing", "rbc_kernel_times",
-           "rbc_autotune", "rbc_launches_per_step", "rbc_neighbors_noalloc", "rbc_server_create", "rbc_server_submit",
+           "rbc_autotune", "rbc_wss_accumulate", "rbc_wss", "rbc_launches_per_step", "rbc_neighbors_noalloc", "rbc_server_create", "rbc_server_submit",
            "rbc_server_poll", "rbc_server_results", "rbc_server_clock", "rbc_server_free", "rbc_free",
            "rbc_last_error"]
 
@@ -124,6 +126,10 @@ def load(path: str = LIB_PATH):
     L.rbc_launches_per_step.argtypes = [ctypes.c_void_p]
     L.rbc_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, P(rbc_tune_report)]
     L.rbc_autotune.restype = ctypes.c_int
+    L.rbc_wss_accumulate.argtypes = [ctypes.c_void_p]
+    L.rbc_wss_accumulate.restype = ctypes.c_int
+    L.rbc_wss.argtypes = [ctypes.c_void_p, _I64, _D, ctypes.c_int64, _I64, _I64]
+    L.rbc_wss.restype = ctypes.c_int
     L.rbc_neighbors_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         _I, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.c_void_p]
@@ -178,6 +184,13 @@ class _Inputs:
         solid = geometry.get("solid")
         self.solid = None if solid is None else np.ascontiguousarray(np.asarray(solid, np.uint8).reshape(-1))
         g.solid = None if self.solid is None else self.solid.ctypes.data_as(_U8)
+        nt = geometry.get("node_type")
+        self.node_type = None if nt is None else np.ascontiguousarray(np.asarray(nt, np.uint8).reshape(-1))
+        g.node_type = None if self.node_type is None else self.node_type.ctypes.data_as(_U8)
+        ic = geometry.get("inlet_center", (0.0, 0.0))
+        g.inlet_center[0], g.inlet_center[1] = float(ic[0]), float(ic[1])
+        g.inlet_radius = float(geometry.get("inlet_radius", 1.0))
+        g.inlet_umax = float(geometry.get("inlet_umax", 0.0))
         self.geom = g
         c = rbc_cells()
         n = 0 if cells is None else int(np.asarray(cells["pos"]).shape[0])
@@ -198,7 +211,7 @@ class _Inputs:
                 arr = getattr(p, k)
                 for a in range(3):
                     arr[a] = float(v[a])
-            elif k in ("bin_capacity", "max_neighbors"):
+            elif k in ("bin_capacity", "max_neighbors", "node_list"):
                 setattr(p, k, int(v))
             elif k == "precision":
                 p.precision = PRECISION[v] if isinstance(v, str) else int(v)
@@ -300,6 +313,20 @@ def rbc_autotune(h, steps_per_trial: int = 20):
                 default_ms_per_step=r.default_ms_per_step, trials=r.trials)
 
 
+def rbc_wss_accumulate(h):
+    _check(load().rbc_wss_accumulate(h), h)
+
+
+def rbc_wss(h, max_nodes: int):
+    node = np.zeros(max(max_nodes, 1), dtype=np.int64)
+    tau = np.zeros(3 * max(max_nodes, 1))
+    n, samples = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().rbc_wss(h, node.ctypes.data_as(_I64), _dp(tau), int(max_nodes), ctypes.byref(n),
+                          ctypes.byref(samples)), h)
+    k = min(n.value, max_nodes)
+    return node[:k].copy(), tau[: 3 * k].reshape(k, 3).copy(), int(samples.value)
+
+
 def rbc_launches_per_step(h) -> int:
     return int(load().rbc_launches_per_step(h))
 
@@ -372,6 +399,13 @@ class Solver:
 
     def autotune(self, steps_per_trial=20):
         return rbc_autotune(self.handle, steps_per_trial)
+
+    def wss_accumulate(self):
+        rbc_wss_accumulate(self.handle)
+
+    def wss(self):
+        """(nodes, time-averaged wall shear stress vectors (n, 3), samples)."""
+        return rbc_wss(self.handle, self.N)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -105,6 +105,91 @@ def open_tube(n, length, radius, umax):
     return g
 
 
+def y_bifurcation(n, r_parent, r_daughter, angle_deg=35.0, z_split=None, umax=0.02, nz=None):
+    """Y-shaped vessel in an n x n x nz box: a parent tube of radius r_parent
+    along z from the inlet plane z = 0 to the branch point ((n-1)/2, (n-1)/2,
+    z_split), two daughter tubes of radius r_daughter leaving it at
+    +-angle_deg from the z axis in the x-z plane up to the outlet plane
+    z = nz - 1, and a sphere of radius r_parent joining them.  Velocity inlet
+    (Poiseuille profile of peak umax in the parent) on z = 0, pressure outlets
+    on z = nz - 1; solid elsewhere."""
+    nz = n if nz is None else nz
+    z_split = nz // 2 if z_split is None else z_split
+    c = (n - 1) / 2.0
+    th = math.radians(angle_deg)
+    y, x = np.mgrid[0:n, 0:n].astype(np.float64)
+    dx, dy = x - c, y - c
+    rr = dx * dx + dy * dy
+    fluid = np.zeros((nz, n, n), dtype=bool)
+    for zi in range(nz):  # one plane at a time
+        dz = zi - z_split
+        f = rr + dz * dz < r_parent ** 2
+        if zi <= z_split:
+            f |= rr < r_parent ** 2
+        for sgn in (-1.0, 1.0):
+            t = dx * sgn * math.sin(th) + dz * math.cos(th)
+            f |= (t >= 0.0) & (rr + dz * dz - t * t < r_daughter ** 2)
+        fluid[zi] = f
+    solid = (~fluid).astype(np.uint8)
+    nt = np.zeros((nz, n, n), dtype=np.uint8)
+    nt[0][fluid[0]] = NODE_INLET
+    nt[nz - 1][fluid[nz - 1]] = NODE_OUTLET
+    return dict(nx=n, ny=n, nz=nz, periodic=(0, 0, 1), solid=solid, body_force=(0.0, 0.0, 0.0),
+                node_type=nt, inlet_center=(c, c), inlet_radius=float(r_parent), inlet_umax=float(umax),
+                branch=dict(z_split=z_split, angle=angle_deg, r_parent=r_parent, r_daughter=r_daughter))
+
+
+def y_bifurcation_cells(rng, geom, hematocrit, wall_clearance=6.0, end_clearance=20.0, pitch=8.3, zpitch=3.3,
+                        tilt_max_deg=1.5):
+    """Cells in the slots of the tube workload's lattice (hexagonal of pitch
+    ``pitch`` across, ``zpitch`` along z; short axis along z) that lie inside
+    the Y at least ``wall_clearance`` from its walls and ``end_clearance``
+    from the inlet and outlet planes; as many as give ``hematocrit`` of the
+    lumen, or all slots if fewer."""
+    n, nz = geom["nx"], geom["nz"]
+    b = geom["branch"]
+    c = (n - 1) / 2.0
+    th = math.radians(b["angle"])
+    dy = pitch * math.sqrt(3.0) / 2.0
+    pts = []
+    k = int(math.ceil(n / pitch)) + 1
+    for zz in np.arange(end_clearance, nz - 1 - end_clearance, zpitch):
+        for i, yy in enumerate(np.arange(0.0, n, dy)):
+            xs = np.arange(-k, k + 1) * pitch + c + 0.5 * pitch * (i % 2)
+            xs = xs[(xs >= 0) & (xs < n)]
+            px, py = xs - c, yy - c
+            pz = zz - b["z_split"]
+            m = np.full(xs.shape, -np.inf)
+            if zz <= b["z_split"]:
+                m = np.maximum(m, b["r_parent"] - np.hypot(px, py))
+            m = np.maximum(m, b["r_parent"] - np.sqrt(px * px + py * py + pz * pz))
+            for sgn in (-1.0, 1.0):
+                ax = (sgn * math.sin(th), 0.0, math.cos(th))
+                t = px * ax[0] + py * ax[1] + pz * ax[2]
+                d = np.sqrt(np.maximum(px * px + py * py + pz * pz - t * t, 0.0))
+                m = np.maximum(m, np.where(t >= 0.0, b["r_daughter"] - d, -np.inf))
+            for x in xs[m >= wall_clearance]:
+                pts.append((x, yy, zz))
+    pts = np.array(pts).reshape(-1, 3)
+    want = int(round(hematocrit * fluid_count(geom) / CELL_VOLUME))
+    ncell = min(want, len(pts))
+    pick = np.sort(rng.choice(len(pts), size=ncell, replace=False))
+    pos = pts[pick] + (rng.random((ncell, 3)) * 2.0 - 1.0) * np.array([0.04, 0.04, 0.03])
+    quat = tilted_quaternions(rng, ncell, np.array([1.0, 0.0, 0.0, 0.0]), math.radians(tilt_max_deg))
+    return cells_dict(pos, quat)
+
+
+def ybif_workload(n=512, r_parent=60.0, r_daughter=45.0, angle_deg=35.0, hematocrit=0.40, umax=0.02,
+                  seed=SEED_BASE + 5, **pover):
+    """The vascular workload: Y-bifurcation in n^3 (parent radius 60,
+    daughters radius 45 at +-35 degrees), velocity inlet / pressure outlets,
+    cells at up to ``hematocrit`` of the lumen (slot-limited)."""
+    rng = np.random.default_rng(seed)
+    geom = y_bifurcation(n, r_parent, r_daughter, angle_deg, umax=umax)
+    cells = y_bifurcation_cells(rng, geom, hematocrit)
+    return geom, cells, params(**pover)
+
+
 def fluid_count(geom):
     N = geom["nx"] * geom["ny"] * geom["nz"]
     return N if geom["solid"] is None else int(N - int(np.count_nonzero(geom["solid"])))

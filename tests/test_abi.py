@@ -45,12 +45,14 @@ def test_default_params_are_the_papers(lib):
 
 
 def test_struct_layouts_match_header(lib):
-    assert ctypes.sizeof(rbc.rbc_geometry) == 24 + 8 + 24 + 24
+    # nx..periodic, solid, body_force, body_force_wave, node_type, inlet_center, inlet_radius, inlet_umax
+    assert ctypes.sizeof(rbc.rbc_geometry) == 24 + 8 + 24 + 24 + 8 + 16 + 8 + 8
     assert ctypes.sizeof(rbc.rbc_cells) == 8 + 4 * 8
     assert ctypes.sizeof(rbc.rbc_stats_t) == 8 * 10 + 8 + 8
     assert rbc.rbc_params.stream.offset == ctypes.sizeof(rbc.rbc_params) - 8
-    # int precision, int rounding, uint64_t seed, void *stream close the struct
-    assert rbc.rbc_params.seed.offset == ctypes.sizeof(rbc.rbc_params) - 16
+    # int precision, int rounding, uint64_t seed, int node_list, void *stream close the struct
+    assert rbc.rbc_params.node_list.offset == rbc.rbc_params.stream.offset - 8
+    assert rbc.rbc_params.seed.offset == rbc.rbc_params.node_list.offset - 8
     assert rbc.rbc_params.rounding.offset == rbc.rbc_params.seed.offset - 4
     assert rbc.rbc_params.precision.offset == rbc.rbc_params.seed.offset - 8
 
@@ -103,3 +105,23 @@ def test_missing_library_fails_loudly(tmp_path):
     with pytest.raises(RuntimeError):
         mod.load(str(tmp_path / "librbc.so"))
     importlib.reload(rbc)
+
+
+def test_open_boundary_validation(lib):
+    g = wl.open_tube(16, 24, 6.0, 0.01)
+    p = wl.params()
+    dense = rbc.rbc_workspace_size(g, None, dict(p, node_list=-1))
+    # the node-list pass adds one index per fluid node (chosen automatically
+    # here: fewer than half the nodes are fluid)
+    nl = rbc.rbc_workspace_size(g, None, dict(p, node_list=1))
+    assert nl > dense and rbc.rbc_workspace_size(g, None, p) == nl
+    bad = dict(g, node_type=np.full_like(g["node_type"], 3))
+    with pytest.raises(rbc.RbcError):
+        rbc.rbc_workspace_size(bad, None, p)
+    bad = dict(g, inlet_radius=0.0)
+    with pytest.raises(rbc.RbcError):
+        rbc.rbc_workspace_size(bad, None, p)
+    bad_nt = g["node_type"].copy()
+    bad_nt[0, 0, 0] = 1  # a solid corner node marked as inlet
+    with pytest.raises(rbc.RbcError):
+        rbc.rbc_workspace_size(dict(g, node_type=bad_nt), None, p)

@@ -91,3 +91,25 @@ def test_wall_shear_stress_of_poiseuille(tube_state):
     # mean over the wall nodes against mu 2 U / R (the nodes sit half a
     # lattice spacing inside the wall, where the shear is (R - 1/2)/R of it)
     assert abs(wss.mean() / (nu * 2.0 * Umax / R) - 1.0) < 0.15
+
+
+def test_y_bifurcation_splits_the_flux_evenly():
+    """32^3 Y (parent radius 6, daughters 4.5 at +-35 degrees): the oblique
+    outlet planes take their state from the nearest fluid node behind them,
+    the flow stays finite, and at a steady state the mirror-symmetric
+    daughters carry equal mass fluxes whose sum is the parent's."""
+    g = wl.y_bifurcation(32, 6.0, 4.5, 35.0, umax=0.02)
+    o = orc.Oracle(g, None, wl.params())
+    o.step(700)
+    rho, u, _ = o.fields()
+    o.close()
+    n = 32
+    rho, u = rho.reshape(n, n, n), u.reshape(n, n, n, 3)
+    assert np.isfinite(u).all()
+    fl = g["solid"] == 0
+    mz = rho * u[..., 2] * fl
+    parent = mz[8].sum()
+    half = n // 2
+    left, right = mz[26][:, :half].sum(), mz[26][:, half:].sum()
+    assert parent > 0 and abs(left / right - 1.0) < 1e-6
+    assert abs((left + right) / parent - 1.0) < 2e-2
