@@ -469,6 +469,7 @@ struct ShapeArgs {
     int nx, ny, nz;
     long long Np;
     float two_over_xi[3], xi[3], kappa, alpha;
+    int kappa_i;  // kappa when it is a whole number 1..64 (integer power), else 0
     int box_dim, sup_cap;
     int box_pad;  // shared words per warp of k_weights: 2 box_dim^2 row words + sup_cap weights
 };
@@ -743,8 +744,11 @@ __global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc) 
 constexpr int kCellWarps = 4;
 constexpr int kIlp = 4;  // list entries per lane in flight
 
+// Sums over the entries part, part + parts, ... (in units of 32) of cell
+// i's list: this warp's share when `parts` warps sample one cell.
 template <bool ALPHA>
-__device__ __forceinline__ void sample_sums(const ShapeArgs &a, int i, int n, float S, float (&acc)[9])
+__device__ __forceinline__ void sample_sums(const ShapeArgs &a, int i, int n, float S, float (&acc)[9], int part,
+                                            int parts)
 {
     const int lane = threadIdx.x & 31;
     for (int k = 0; k < 9; ++k) acc[k] = 0.f;
@@ -758,13 +762,13 @@ __device__ __forceinline__ void sample_sums(const ShapeArgs &a, int i, int n, fl
     const float4 *val = a.sp_val + (size_t)i * a.sp_cap;
     // kIlp independent entries per lane in flight: the list and U loads of
     // all of them issue before any sum uses them
-    for (int e0 = lane; e0 < n; e0 += 32 * kIlp) {
+    for (int e0 = lane + 32 * part; e0 < n; e0 += 32 * parts * kIlp) {
         int2 ix[kIlp];
         float4 v[kIlp];
         float u[kIlp][3];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
-            const int e = e0 + 32 * j;
+            const int e = e0 + 32 * parts * j;
             ix[j] = e < n ? idx[e] : make_int2(gc, 0);
             v[j] = e < n ? val[e] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -999,29 +1003,67 @@ __device__ __forceinline__ bool rigid_update(const RigidArgs &a, int i, float Sf
 // A cell's spread writes only G and theta, which no sampling reads, so each
 // warp goes straight from its own update to its own spread.
 // ---------------------------------------------------------------------------
+// (1 - w)^kappa of Eq. enhance-viscosity: by squaring for a whole-number
+// kappa (the paper's 20: five multiplications), powf otherwise
+__device__ __forceinline__ float pow_kappa(float x, const ShapeArgs &a)
+{
+    if (a.kappa_i <= 0) return powf(x, a.kappa);
+    float r = 1.0f, b = x;
+    for (int e = a.kappa_i; e > 0; e >>= 1) {
+        if (e & 1) r *= b;
+        b *= b;
+    }
+    return r;
+}
+
+// Two warps per cell (kCellWarps / 2 cells per block): both sample half of
+// the cell's list, the first adds the halves (fixed order) and runs the
+// rigid update, both spread half of the list.
+constexpr int kCellsPerBlock = kCellWarps / 2;
+
 template <bool ALPHA>
 __device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &ra, int nc, int blk)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = blk * kCellWarps + (threadIdx.x >> 5);
-    if (i >= nc) return;
-    const int n = a.sp_cnt[i];
-    const float S = a.sp_S[i];
+    __shared__ float s_part[kCellsPerBlock][9];
+    __shared__ float s_jl[kCellsPerBlock][7];  // J / S, L / 2S, go
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, pair = w >> 1, half = w & 1;
+    const int i = blk * kCellsPerBlock + pair;
+    const bool valid = i < nc;
+    const int n = valid ? a.sp_cnt[i] : 0;
+    const float S = valid ? a.sp_S[i] : 0.f;
     float sums[9];
-    sample_sums<ALPHA>(a, i, n, S, sums);
-    float J[3], L[3];
-    if (!rigid_update(ra, i, S, sums, J, L) || n == 0) return;
-    const float iS = 1.0f / S;
-    const float Jx = J[0] * iS, Jy = J[1] * iS, Jz = J[2] * iS;
-    const float Lx = 0.5f * L[0] * iS, Ly = 0.5f * L[1] * iS, Lz = 0.5f * L[2] * iS;
+    if (valid)
+        sample_sums<ALPHA>(a, i, n, S, sums, half, 2);
+    else
+        for (int k = 0; k < 9; ++k) sums[k] = 0.f;
+    if (half == 1 && lane < 9) s_part[pair][lane] = pick(sums, lane);
+    __syncthreads();
+    if (half == 0 && valid) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) sums[k] += s_part[pair][k];
+        float J[3], L[3];
+        const bool go = rigid_update(ra, i, S, sums, J, L) && n > 0;
+        if (lane == 0) {
+            const float iS = go ? 1.0f / S : 0.f;
+            for (int d = 0; d < 3; ++d) {
+                s_jl[pair][d] = J[d] * iS;
+                s_jl[pair][3 + d] = 0.5f * L[d] * iS;
+            }
+            s_jl[pair][6] = go ? 1.f : 0.f;
+        }
+    }
+    __syncthreads();
+    if (!valid || s_jl[pair][6] == 0.f) return;
+    const float Jx = s_jl[pair][0], Jy = s_jl[pair][1], Jz = s_jl[pair][2];
+    const float Lx = s_jl[pair][3], Ly = s_jl[pair][4], Lz = s_jl[pair][5];
     const int2 *idx = a.sp_idx + (size_t)i * a.sp_cap;
     const float4 *val = a.sp_val + (size_t)i * a.sp_cap;
-    for (int e0 = lane; e0 < n; e0 += 32 * kIlp) {
+    for (int e0 = lane + 32 * half; e0 < n; e0 += 64 * kIlp) {
         int g[kIlp];
         float4 v[kIlp];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
-            const int e = e0 + 32 * j;
+            const int e = e0 + 64 * j;
             g[j] = e < n ? idx[e].x : -1;
             v[j] = e < n ? val[e] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -1031,7 +1073,7 @@ __device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &
             atomicAdd(&a.G[g[j]], -Jx * v[j].x + (Ly * v[j].w - Lz * v[j].z));
             atomicAdd(&a.G[a.Np + g[j]], -Jy * v[j].x + (Lz * v[j].y - Lx * v[j].w));
             atomicAdd(&a.G[2 * a.Np + g[j]], -Jz * v[j].x + (Lx * v[j].z - Ly * v[j].y));
-            if (v[j].x > 0.f) atomicAdd(&a.theta[g[j]], 1.0f - powf(1.0f - v[j].x, a.kappa));
+            if (v[j].x > 0.f) atomicAdd(&a.theta[g[j]], 1.0f - pow_kappa(1.0f - v[j].x, a));
         }
     }
 }
@@ -1071,6 +1113,7 @@ ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
     a.box_pad = 2 * p.box_dim * p.box_dim + p.sup_cap;
     a.sup_cap = p.sup_cap;
     a.kappa = p.kappa;
+    a.kappa_i = (p.kappa >= 1.0f && p.kappa <= 64.0f && p.kappa == floorf(p.kappa)) ? (int)p.kappa : 0;
     a.alpha = p.alpha;
     return a;
 }
@@ -1286,7 +1329,7 @@ void launch_cells(const Dev &d, const Params &p, int buf, cudaStream_t s)
     if (d.nc == 0) return;
     const ShapeArgs a = shape_args(d, p, buf);
     const RigidArgs r = rigid_args(d, p);
-    const int blocks = (d.nc + kCellWarps - 1) / kCellWarps;
+    const int blocks = (d.nc + kCellsPerBlock - 1) / kCellsPerBlock;
     if (d.S != nullptr)
         k_cells<true><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc);
     else
@@ -1306,7 +1349,7 @@ int cell_pack_blocks(int nc, int nbins, int kind)
     case PACK_BIN: return (nc + kBinThreads - 1) / kBinThreads;
     case PACK_GB: return (nc + kGbWarps - 1) / kGbWarps;
     case PACK_WEIGHTS: return (nc + kWtWarps - 1) / kWtWarps;
-    default: return (nc + kCellWarps - 1) / kCellWarps;
+    default: return (nc + kCellsPerBlock - 1) / kCellsPerBlock;
     }
 }
 

@@ -247,3 +247,10 @@ def test_autotuned_launch_shape_keeps_parity():
     assert rel_l2(f["u"], u_o) <= TOL
     s.close()
     o.close()
+
+
+def test_non_integer_kappa():
+    """kappa = 19.5 takes the general power of Eq. enhance-viscosity (the
+    paper's 20 is computed by squaring)."""
+    geom, cells, params = wl.box_workload(n=24, ncells=6, seed=9)
+    _compare(geom, cells, dict(params, kappa=19.5), 40)
