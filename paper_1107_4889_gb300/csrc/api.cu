@@ -323,10 +323,9 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.seed = P.seed;
     d.pops[0] = cv.take<uint8_t>(19 * Np * (size_t)pop_bytes(P.prec));
     d.pops[1] = cv.take<uint8_t>(19 * Np * (size_t)pop_bytes(P.prec));
-    d.U = cv.take<float>(3 * Np);
-    d.S = P.want_sigma ? cv.take<float>(6 * Np) : nullptr;
-    d.G = P.nc > 0 ? cv.take<float>(3 * Np) : nullptr;
-    d.theta = P.nc > 0 ? cv.take<float>(Np) : nullptr;
+    d.U = cv.take<float4>(Np);
+    d.S = P.want_sigma ? cv.take<float4>(2 * Np) : nullptr;
+    d.G = P.nc > 0 ? cv.take<float4>(Np) : nullptr;
     d.rho = cv.take<float>(Np);
     d.solid = P.any_solid ? cv.take<uint8_t>(Np) : nullptr;
     d.links = P.need_links ? cv.take<uint32_t>(Np) : nullptr;
@@ -635,10 +634,9 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
         // (zero bits are a zero deviation in every storage format)
         RBC_CU(cudaMemsetAsync(d.pops[0], 0, 19 * Np * pop_bytes(d.prec), s));
         RBC_CU(cudaMemsetAsync(d.pops[1], 0, 19 * Np * pop_bytes(d.prec), s));
-        RBC_CU(cudaMemsetAsync(d.U, 0, 3 * Np * sizeof(float), s));
-        if (d.S) RBC_CU(cudaMemsetAsync(d.S, 0, 6 * Np * sizeof(float), s));
-        if (d.G) RBC_CU(cudaMemsetAsync(d.G, 0, 3 * Np * sizeof(float), s));
-        if (d.theta) RBC_CU(cudaMemsetAsync(d.theta, 0, Np * sizeof(float), s));
+        RBC_CU(cudaMemsetAsync(d.U, 0, Np * sizeof(float4), s));
+        if (d.S) RBC_CU(cudaMemsetAsync(d.S, 0, 2 * Np * sizeof(float4), s));
+        if (d.G) RBC_CU(cudaMemsetAsync(d.G, 0, Np * sizeof(float4), s));
         RBC_CU(cudaMemsetAsync(d.rho, 0, Np * sizeof(float), s));
         std::vector<uint32_t> links;
         if (d.solid) {
@@ -824,11 +822,14 @@ int rbc_fields(rbc_handle *h, double *rho, double *u, double *cells_state)
         for (size_t k = 0; k < N; ++k) rho[k] = (solid && solid[k]) ? 0.0 : 1.0 + (double)r[k];
     }
     if (u) {
-        std::vector<float> U(3 * Np);
-        RBC_CU(cudaMemcpyAsync(U.data(), d.U, 3 * Np * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        std::vector<float4> U(Np);
+        RBC_CU(cudaMemcpyAsync(U.data(), d.U, Np * sizeof(float4), cudaMemcpyDeviceToHost, h->stream));
         RBC_CU(cudaStreamSynchronize(h->stream));
-        for (size_t k = 0; k < N; ++k)
-            for (int a = 0; a < 3; ++a) u[3 * k + a] = U[a * Np + k];
+        for (size_t k = 0; k < N; ++k) {
+            u[3 * k] = U[k].x;
+            u[3 * k + 1] = U[k].y;
+            u[3 * k + 2] = U[k].z;
+        }
     }
     if (cells_state && d.nc > 0) {
         const size_t n = (size_t)d.nc;

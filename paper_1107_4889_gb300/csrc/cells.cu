@@ -459,8 +459,8 @@ struct ShapeArgs {
     float *hdr;
     const double *R, *q;
     const uint8_t *solid;
-    const float *U, *S;
-    float *G, *theta;
+    const float4 *U, *S;  // node-major velocity, stress (2 per node)
+    float4 *G;            // node-major force density and hematocrit sum
     int2 *sp_idx;
     float4 *sp_val;
     int *sp_cnt, *flags;
@@ -755,7 +755,8 @@ __device__ __forceinline__ void sample_sums(const ShapeArgs &a, int i, int n, fl
     if (n == 0) return;
     const float *hd = &a.hdr[kHdrWords * i];
     const int gc = reinterpret_cast<const int *>(hd)[18];
-    const float uc0 = a.U[gc], uc1 = a.U[a.Np + gc], uc2 = a.U[2 * a.Np + gc];
+    const float4 uc = a.U[gc];
+    const float uc0 = uc.x, uc1 = uc.y, uc2 = uc.z;
     const float b0 = hd[9], b1 = hd[10], b2 = hd[11];
     const float thr = 1e-24f * S * S;
     const int2 *idx = a.sp_idx + (size_t)i * a.sp_cap;
@@ -774,10 +775,10 @@ __device__ __forceinline__ void sample_sums(const ShapeArgs &a, int i, int n, fl
         }
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
-            const int g = ix[j].x;
-            u[j][0] = a.U[g];
-            u[j][1] = a.U[a.Np + g];
-            u[j][2] = a.U[2 * a.Np + g];
+            const float4 u4 = a.U[ix[j].x];
+            u[j][0] = u4.x;
+            u[j][1] = u4.y;
+            u[j][2] = u4.z;
         }
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
@@ -796,8 +797,17 @@ __device__ __forceinline__ void sample_sums(const ShapeArgs &a, int i, int n, fl
             for (int j = 0; j < kIlp; ++j) {
                 const int g = ix[j].x;
                 on[j] = v[j].x > 0.f && v[j].y * v[j].y + v[j].z * v[j].z + v[j].w * v[j].w > thr;
-#pragma unroll
-                for (int c = 0; c < 6; ++c) sg[j][c] = on[j] ? a.S[c * a.Np + g] : 0.f;
+                float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+                if (on[j]) {
+                    s0 = a.S[2 * (long long)g];
+                    s1 = a.S[2 * (long long)g + 1];
+                }
+                sg[j][0] = s0.x;
+                sg[j][1] = s0.y;
+                sg[j][2] = s0.z;
+                sg[j][3] = s0.w;
+                sg[j][4] = s1.x;
+                sg[j][5] = s1.y;
             }
 #pragma unroll
             for (int j = 0; j < kIlp; ++j) {
@@ -1070,10 +1080,11 @@ __device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             if (g[j] < 0) continue;
-            atomicAdd(&a.G[g[j]], -Jx * v[j].x + (Ly * v[j].w - Lz * v[j].z));
-            atomicAdd(&a.G[a.Np + g[j]], -Jy * v[j].x + (Lz * v[j].y - Lx * v[j].w));
-            atomicAdd(&a.G[2 * a.Np + g[j]], -Jz * v[j].x + (Lx * v[j].z - Ly * v[j].y));
-            if (v[j].x > 0.f) atomicAdd(&a.theta[g[j]], 1.0f - pow_kappa(1.0f - v[j].x, a));
+            // one vector atomic per entry: (G_x, G_y, G_z, theta)
+            atomicAdd(&a.G[g[j]], make_float4(-Jx * v[j].x + (Ly * v[j].w - Lz * v[j].z),
+                                              -Jy * v[j].x + (Lz * v[j].y - Lx * v[j].w),
+                                              -Jz * v[j].x + (Lx * v[j].z - Ly * v[j].y),
+                                              v[j].x > 0.f ? 1.0f - pow_kappa(1.0f - v[j].x, a) : 0.f));
         }
     }
 }
@@ -1094,7 +1105,6 @@ ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
     a.U = d.U;
     a.S = d.S;
     a.G = d.G;
-    a.theta = d.theta;
     a.sp_idx = d.sp_idx[buf];
     a.sp_val = d.sp_val[buf];
     a.sp_cnt = d.sp_cnt[buf];

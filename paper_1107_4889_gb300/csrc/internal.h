@@ -33,10 +33,12 @@ struct Dev {
     int prec, stochastic;
     unsigned long long seed;  // key of the stochastic rounding's random numbers
     void *pops[2];
-    float *U;           // 3 planes: velocity of the last lattice pass
-    float *S;           // 6 planes (xx yy zz xy xz yz): stress of the last pass, or null
-    float *G;           // 3 planes: force density accumulated by the cells (zeroed by the pass)
-    float *theta;       // 1 plane: sum of smoothed characteristic functions (zeroed by the pass)
+    // node-major vectors, so that the per-cell gathers and the spread take
+    // one access per node
+    float4 *U;          // Np: velocity of the last lattice pass (x, y, z, 0)
+    float4 *S;          // 2 Np: stress of the last pass, (xx yy zz xy) (xz yz 0 0), or null
+    float4 *G;          // Np: force density (x, y, z) and sum of smoothed characteristic
+                        // functions (w), accumulated by the cells, zeroed by the pass
     float *rho;         // 1 plane: density for field output
     uint8_t *solid;     // N bytes or null
     uint32_t *links;    // N words or null: bit p (1..18) = node + c_p is solid, bit 29 = inlet node,

@@ -40,7 +40,7 @@ struct LbArgs {
     const void *src;  // populations of the previous pass (storage type St)
     void *dst;
     const uint32_t *links;
-    float *G, *th, *U, *S;
+    float4 *G, *U, *S;  // node-major: force density + hematocrit sum, velocity, stress (2 per node)
     int *flags;
     int *work;                 // [0] next batch, [1] CTAs done; zero at launch, reset by the last CTA
     unsigned long long *step;  // passes done: the counter of the rounding's random numbers
@@ -197,12 +197,7 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
     // element offsets fit 32 bits: the host keeps 19 Np below 2^32
     const uint32_t Np = (uint32_t)a.Np;
     St *dst = static_cast<St *>(a.dst);
-    if (CELLS) {
-        a.G[n] = 0.f;
-        a.G[Np + n] = 0.f;
-        a.G[2 * Np + n] = 0.f;
-        a.th[n] = 0.f;
-    }
+    if (CELLS) a.G[n] = make_float4(0.f, 0.f, 0.f, 0.f);
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int p = 0; p < kQ; ++p) {
@@ -262,16 +257,10 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
             }
         }
     });
-    a.U[n] = ux;
-    a.U[Np + n] = uy;
-    a.U[2 * Np + n] = uz;
+    a.U[n] = make_float4(ux, uy, uz, 0.f);
     if (SIGMA) {
-        a.S[n] = -ff * pxx;
-        a.S[Np + n] = -ff * pyy;
-        a.S[2 * Np + n] = -ff * pzz;
-        a.S[3 * Np + n] = -ff * pxy;
-        a.S[4 * Np + n] = -ff * pxz;
-        a.S[5 * Np + n] = -ff * pyz;
+        a.S[2 * n] = make_float4(-ff * pxx, -ff * pyy, -ff * pzz, -ff * pxy);
+        a.S[2 * n + 1] = make_float4(-ff * pxz, -ff * pyz, 0.f, 0.f);
     }
     if (!(rho > 0.0f) || !(usq <= a.mach2)) atomicOr(&a.flags[FLAG_UNSTABLE], 1);
     if (WALLS && (lk & 0x7FFFEu)) {  // nodes next to a wall only
@@ -375,17 +364,12 @@ __device__ __noinline__ void boundary_node(const LbArgs &a, uint32_t n, int x, i
         jz += float(cz(p)) * d[p];
     });
     const float ir = 1.0f / (1.0f + drho);
-    a.U[n] = jx * ir;
-    a.U[Np + n] = jy * ir;
-    a.U[2 * Np + n] = jz * ir;
-    if (SIGMA)
-        for (int k = 0; k < 6; ++k) a.S[(uint32_t)k * Np + n] = 0.f;
-    if (CELLS) {
-        a.G[n] = 0.f;
-        a.G[Np + n] = 0.f;
-        a.G[2 * Np + n] = 0.f;
-        a.th[n] = 0.f;
+    a.U[n] = make_float4(jx * ir, jy * ir, jz * ir, 0.f);
+    if (SIGMA) {
+        a.S[2 * n] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a.S[2 * n + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    if (CELLS) a.G[n] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // External force density at row y: the uniform drive plus the Kolmogorov
@@ -431,10 +415,11 @@ __device__ __forceinline__ void lb_node(const LbArgs &a, int n, unsigned long lo
     float gx, gy, gz, T = a.tau0;
     external_force(a, y, gx, gy, gz);
     if (CELLS) {
-        gx += a.G[n];
-        gy += a.G[a.Np + n];
-        gz += a.G[2 * a.Np + n];
-        T += a.delta * a.th[n];
+        const float4 g4 = a.G[n];
+        gx += g4.x;
+        gy += g4.y;
+        gz += g4.z;
+        T += a.delta * g4.w;
     }
     if (WALLS && (lk >> 31)) return;  // solid node: nothing to collide
     if (WALLS && (lk & 0x60000000u)) {
@@ -603,17 +588,15 @@ __device__ __forceinline__ void produce_batch(const LbArgs &a, const StageLayout
                          bar);
                 b += run;
             }
-        } else {
+        } else if (CELLS && k == kQ) {
+            // G and the hematocrit sum: one float4 per node, B rows of nx
+            const long long off = ((long long)z * ny + y0) * nx;
+            bulk_g2s(smem_addr(fst), a.G + off, (uint32_t)nb * 4u * frow_bytes, bar);
+        } else if (!(CELLS && k < kQ + 4)) {
+            // the link words after the cell planes
             float *dst = fst + (size_t)(k - kQ) * B * nx;
             const long long off = ((long long)z * ny + y0) * nx;
-            const float *fsrc;
-            if (CELLS && k < kQ + 3)
-                fsrc = a.G + (long long)(k - kQ) * a.Np + off;
-            else if (CELLS && k == kQ + 3)
-                fsrc = a.th + off;
-            else
-                fsrc = reinterpret_cast<const float *>(a.links) + off;
-            bulk_g2s(smem_addr(dst), fsrc, (uint32_t)nb * frow_bytes, bar);
+            bulk_g2s(smem_addr(dst), reinterpret_cast<const float *>(a.links) + off, (uint32_t)nb * frow_bytes, bar);
         }
     }
 }
@@ -662,10 +645,11 @@ __device__ __forceinline__ void consume_batch(const LbArgs &a, const StageLayout
         float gx, gy, gz, T = a.tau0;
         external_force(a, y, gx, gy, gz);
         if (CELLS) {
-            gx += frow[0 * plane_stride + xx];
-            gy += frow[1 * plane_stride + xx];
-            gz += frow[2 * plane_stride + xx];
-            T += a.delta * frow[3 * plane_stride + xx];
+            const float4 g4 = reinterpret_cast<const float4 *>(fst)[(size_t)bx * nx + xx];
+            gx += g4.x;
+            gy += g4.y;
+            gz += g4.z;
+            T += a.delta * g4.w;
         }
         collide_node<St, WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, n, xx, y, z, step);
     }
@@ -914,7 +898,7 @@ struct ForceArgs {
 
 template <typename St>
 __global__ void __launch_bounds__(kBudThreads)
-k_budget_nodes(const void *__restrict__ pops_v, const float *__restrict__ U,
+k_budget_nodes(const void *__restrict__ pops_v, const float4 *__restrict__ U,
                const uint8_t *__restrict__ solid, double *__restrict__ part, int N, long long Np, ForceArgs fa)
 {
     const St *pops = static_cast<const St *>(pops_v);
@@ -934,7 +918,8 @@ k_budget_nodes(const void *__restrict__ pops_v, const float *__restrict__ U,
         px += jx;
         py += jy;
         pz += jz;
-        const float ux = U[n], uy = U[Np + n], uz = U[2 * Np + n];
+        const float4 u4 = U[n];
+        const float ux = u4.x, uy = u4.y, uz = u4.z;
         const float u2 = ux * ux + uy * uy + uz * uz;
         if (!(u2 == u2) || !(s == s)) nan += 1.0;
         else if (u2 > umax) umax = u2;
@@ -1190,7 +1175,6 @@ static LbArgs lb_args(const Dev &d, const Params &p, int parity)
     a.dst = d.pops[parity ^ 1];
     a.links = d.links;
     a.G = d.G;
-    a.th = d.theta;
     a.U = d.U;
     a.S = d.S;
     a.flags = d.flags;
@@ -1314,14 +1298,14 @@ void launch_rho(const Dev &d, int parity, cudaStream_t s)
 
 // Wall shear stress: the traction sigma n of the last pass's stress on the
 // wall's tangent plane, t - (t.n) n, added to the node's time sums.
-__global__ void k_wss(const float *__restrict__ S, long long Np, const int *__restrict__ node,
+__global__ void k_wss(const float4 *__restrict__ S, long long Np, const int *__restrict__ node,
                       const float *__restrict__ nrm, double *__restrict__ acc, int nw)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nw) return;
     const long long n = node[k];
-    const float sxx = S[n], syy = S[Np + n], szz = S[2 * Np + n];
-    const float sxy = S[3 * Np + n], sxz = S[4 * Np + n], syz = S[5 * Np + n];
+    const float4 s0 = S[2 * n], s1 = S[2 * n + 1];
+    const float sxx = s0.x, syy = s0.y, szz = s0.z, sxy = s0.w, sxz = s1.x, syz = s1.y;
     const float nx = nrm[3 * k], ny = nrm[3 * k + 1], nz = nrm[3 * k + 2];
     const float tx = sxx * nx + sxy * ny + sxz * nz;
     const float ty = sxy * nx + syy * ny + syz * nz;
