@@ -254,6 +254,9 @@ def run_ours(args):
 
     s = Solver(geom, cells, params)
     s.step(args.warmup)
+    # the launch shape of the lattice pass (ring depth, CTAs per SM) picked
+    # by timing real steps of this solve
+    tune = s.autotune(args.tune_steps) if args.tune_steps > 0 else None
     torch.cuda.synchronize()
     st = s.stats()
 
@@ -327,7 +330,10 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": f"inputs larger than L2: per-step working set "
                          f"{ws_bytes / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB",
-                   "steps_per_s": args.steps / (ms_max * 1e-3)},
+                   "steps_per_s": args.steps / (ms_max * 1e-3),
+                   "lattice_launch": None if tune is None else
+                   {"stages": tune["stages"], "ctas_per_sm": tune["ctas_per_sm"],
+                    "lattice_first": tune["lattice_first"], "autotuned": True}},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
         "budget": {"mass_drift_rel": (st2["mass"] - st["mass"]) / st["mass"], "max_u": st2["max_u"],
                    "gb_clamps": st2["gb_clamps"]},
@@ -484,6 +490,8 @@ def main():
     ap.add_argument("--no-cells", action="store_true", help="drop the workload's cells (lattice pass alone)")
     ap.add_argument("--precision", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune-steps", type=int, default=50,
+                    help="steps per launch shape the autotuner times during warm-up (0: no tuning)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--reference-budget", type=float, default=60.0)
     ap.add_argument("--serve", action="store_true", help="batched-serving benchmark instead of the step benchmark")

@@ -237,14 +237,17 @@ int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2]);
  * runtime picks the shape from a cost model (fewest idle CTA slots in the
  * last wave; at most 2 CTAs per SM when cells run beside the pass).
  * rbc_autotune times every shape that fits (ring depth 2..4 x 1..4 CTAs per
- * SM) over steps_per_trial coupled steps after as many warm-up steps, keeps
- * the fastest and re-captures the step graphs.  The trial steps are ordinary
+ * SM), each in both graph orders of the step (the cell-list, Gay-Berne and
+ * shape-list kernels launched before the lattice pass, so that they overlap
+ * it, or after it), over steps_per_trial coupled steps after as many
+ * warm-up steps, keeps the fastest and re-captures the step graphs.  The trial steps are ordinary
  * steps of the solve (the state advances).  Synchronises.  out may be NULL. */
 typedef struct {
     int stages, ctas_per_sm;     /* chosen shape (0, 0: the one-thread-per-node pass, nothing to tune) */
     double ms_per_step;          /* its time per coupled step */
     double default_ms_per_step;  /* time per step of the cost model's shape */
     int trials;                  /* shapes timed */
+    int lattice_first;           /* chosen order: 1 = lattice pass before the side kernels */
 } rbc_tune_report;
 int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out);
 

@@ -424,6 +424,7 @@ struct rbc_handle {
     int64_t step = 0;
     int64_t wss_samples = 0;
     int timing_cap = 0, timing_used = 0;
+    bool lb_first = false;  // graph order of the step: lattice pass before the side kernels
     std::vector<cudaEvent_t> ev;  // 3 per timed step: before the cell kernel, after it, after the lattice pass
     std::string err;
     int device = 0;
@@ -485,6 +486,14 @@ static void body_prologue(rbc_handle *h, int)
 // Gay-Berne forces, and its shape headers and shape lists (into buffer
 // parity ^ 1); they read only the poses and write nothing the lattice pass
 // reads.  The step ends when all three streams have.
+static void launch_side(rbc_handle *h, int parity)
+{
+    if (h->d.nc <= 0) return;
+    launch_weights(h->d, h->P.p, parity ^ 1, h->side2);
+    launch_bin(h->d, h->P.p, h->side);
+    launch_gb(h->d, h->P.p, h->side);
+}
+
 static void body_step(rbc_handle *h, int parity)
 {
     const bool cells = h->d.nc > 0;
@@ -496,14 +505,14 @@ static void body_step(rbc_handle *h, int parity)
         cudaStreamWaitEvent(h->side, h->fork_ev, 0);
         cudaStreamWaitEvent(h->side2, h->fork_ev, 0);
     }
-    // the side kernels go into the graph first: their blocks are then
-    // dispatched before the persistent lattice pass fills the SMs
-    if (cells) {
-        launch_weights(h->d, h->P.p, parity ^ 1, h->side2);
-        launch_bin(h->d, h->P.p, h->side);
-        launch_gb(h->d, h->P.p, h->side);
-    }
+    // Default order: the side kernels go into the graph first, so their
+    // blocks are dispatched before the persistent lattice pass fills the
+    // SMs and the two overlap.  The autotuner also tries the lattice pass
+    // first (it then runs nearly alone and the side kernels mostly after
+    // it); which is faster depends on how much cell work there is.
+    if (!h->lb_first) launch_side(h, parity);
     launch_lb(h->d, h->P.p, parity, h->stream);
+    if (h->lb_first) launch_side(h, parity);
     cudaEventRecordWithFlags(h->ev_dummy[2], h->stream, cudaEventRecordExternal);
     if (cells) {
         cudaEventRecord(h->join_ev, h->side);
@@ -1006,10 +1015,12 @@ int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out)
     if (rc != RBC_OK) return rc;
     int stages[16], ctas[16];
     const int n = lb_shapes(h->d, stages, ctas, 16);
+    const bool order0 = h->lb_first;
     double best = rep.default_ms_per_step;
     int best_k = -1;
-    for (int k = 0; k < n; ++k) {
-        set_lb_shape(h->d, stages[k], ctas[k]);
+    for (int k = 0; k < 2 * n; ++k) {
+        set_lb_shape(h->d, stages[k % n], ctas[k % n]);
+        h->lb_first = k >= n;
         rc = recapture_steps(h);
         double ms = 0.0;
         if (rc == RBC_OK) rc = time_steps(h, steps_per_trial, &ms);
@@ -1021,19 +1032,22 @@ int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out)
         }
     }
     if (best_k >= 0) {
-        set_lb_shape(h->d, stages[best_k], ctas[best_k]);
-        rep.stages = stages[best_k];
-        rep.ctas_per_sm = ctas[best_k];
+        set_lb_shape(h->d, stages[best_k % n], ctas[best_k % n]);
+        h->lb_first = best_k >= n;
+        rep.stages = stages[best_k % n];
+        rep.ctas_per_sm = ctas[best_k % n];
     } else {
         h->d.lb_stages = st0;
         h->d.lb_grid = grid0;
         h->d.lb_smem = smem0;
+        h->lb_first = order0;
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         rep.stages = st0;
         rep.ctas_per_sm = (grid0 + sms - 1) / sms;
     }
+    rep.lattice_first = h->lb_first ? 1 : 0;
     rep.ms_per_step = best;
     rc = recapture_steps(h);
     if (out) *out = rep;
