@@ -925,6 +925,13 @@ int rbc_set_timing(rbc_handle *h, int capacity)
 {
     if (!h || capacity < 0) return fail(h ? &h->err : nullptr, RBC_EINVAL, "bad argument");
     RBC_CU(cudaStreamSynchronize(h->stream));
+    // the step graphs' event nodes may still name events of the previous
+    // timing: point them back at the dummies before those events go
+    for (int par = 0; par < 2; ++par) {
+        if (!h->g_step[par]) continue;
+        for (int e = 0; e < 3; ++e)
+            RBC_CU(cudaGraphExecEventRecordNodeSetEvent(h->g_step[par], h->ev_node[par][e], h->ev_dummy[e]));
+    }
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     h->ev.clear();
     h->timing_cap = 0;

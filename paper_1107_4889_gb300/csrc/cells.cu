@@ -1089,8 +1089,13 @@ __device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &
     }
 }
 
+// At most 72 registers so that 7 blocks fit an SM: the kernel waits on
+// memory and wants the warps (at 80 registers, 6 blocks per SM ran 3,650
+// cells as two full waves and a last one of a single block).
+constexpr int kCellBlocksPerSm = 7;
+
 template <bool ALPHA>
-__global__ void __launch_bounds__(32 * kCellWarps) k_cells(ShapeArgs a, RigidArgs ra, int nc)
+__global__ void __launch_bounds__(32 * kCellWarps, kCellBlocksPerSm) k_cells(ShapeArgs a, RigidArgs ra, int nc)
 {
     cells_body<ALPHA>(a, ra, nc, blockIdx.x);
 }

@@ -181,8 +181,11 @@ __device__ __forceinline__ void for_speeds(F &&f)
 //        force-density G, Guo's factor of the scheme Eq. vel comes from)
 //   d* = d - (d - d_eq)/T + Df                                (Eq. lbe_discrete)
 //   sigma = -(1 - 1/2T) sum c c (d - d_eq)                    (Eq. stresstensorLB)
-// Stores d* (in the storage format; `step` counts the stochastic rounding's
-// random numbers), u, sigma, clears the node's G and theta, raises the
+// Stores d* (in the storage format, with streaming stores: a population is
+// written once and read once per pass, and evicting it first keeps u, sigma,
+// G and the shape lists in L2 for the per-cell kernel; `step` counts the
+// stochastic rounding's random numbers), u, sigma, clears the node's G and
+// theta, raises the
 // stability flag, and at walls writes the reflected populations (halfway
 // bounce-back): a population heading into a solid neighbour m comes back to
 // this node in the opposite direction next pass, so it is stored in m's slot
@@ -233,7 +236,7 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
         if constexpr (p == 0) {
             const float A = wq(0) * (drho - 1.5f * rho * usq);
             const float C = -1.5f * ff * wq(0) * gu;
-            dst[n] = Pop<St>::template put<0>(omc * d[0] + (om * A + C), sr, rb);
+            __stcs(&dst[n], Pop<St>::template put<0>(omc * d[0] + (om * A + C), sr, rb));
         } else if constexpr (p < q) {
             const float cu = float(cx(p)) * ux + float(cy(p)) * uy + float(cz(p)) * uz;
             const float cg = float(cx(p)) * gx + float(cy(p)) * gy + float(cz(p)) * gz;
@@ -244,8 +247,8 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
             const float C = fw * (4.5f * cg * cu - 1.5f * gu);
             const float D = 3.0f * fw * cg;
             const float P = om * A + C, M = om * B + D;
-            dst[(uint32_t)p * Np + n] = Pop<St>::template put<p>(omc * d[p] + (P + M), sr, rb);
-            dst[(uint32_t)q * Np + n] = Pop<St>::template put<q>(omc * d[q] + (P - M), sr, rb);
+            __stcs(&dst[(uint32_t)p * Np + n], Pop<St>::template put<p>(omc * d[p] + (P + M), sr, rb));
+            __stcs(&dst[(uint32_t)q * Np + n], Pop<St>::template put<q>(omc * d[q] + (P - M), sr, rb));
             if (SIGMA) {
                 const float ne = (d[p] + d[q]) - 2.0f * A;
                 if (cx(p)) pxx += ne;
@@ -526,6 +529,25 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
+// L2 policy for data touched once per pass: evicted first
+__device__ __forceinline__ uint64_t l2_evict_first()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// bulk_g2s with an L2 cache policy
+__device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar,
+                                              uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+        : "memory");
+}
+
 // Wait for phase `parity` of the mbarrier, for at most kWaitCycles; false on
 // timeout (the caller raises the timeout flag).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
@@ -572,6 +594,7 @@ __device__ __forceinline__ void produce_batch(const LbArgs &a, const StageLayout
     __syncwarp();
     St *pst = reinterpret_cast<St *>(base);
     float *fst = reinterpret_cast<float *>(base + L.pop_bytes);
+    const uint64_t once = l2_evict_first();
     for (int k = lane; k < L.planes; k += 32) {
         if (k < kQ) {
             // the upstream rows y - c_y are contiguous in plane k except
@@ -584,8 +607,8 @@ __device__ __forceinline__ void produce_batch(const LbArgs &a, const StageLayout
             while (b < nb) {
                 const int yr = wrapm(ys + b, ny);
                 const int run = min(nb - b, ny - yr);
-                bulk_g2s(smem_addr(dst + (size_t)b * nx), plane + (long long)yr * nx, (uint32_t)run * prow_bytes,
-                         bar);
+                bulk_g2s_hint(smem_addr(dst + (size_t)b * nx), plane + (long long)yr * nx,
+                              (uint32_t)run * prow_bytes, bar, once);
                 b += run;
             }
         } else if (CELLS && k == kQ) {

@@ -255,3 +255,29 @@ def test_non_integer_kappa():
     paper's 20 is computed by squaring)."""
     geom, cells, params = wl.box_workload(n=24, ncells=6, seed=9)
     _compare(geom, cells, dict(params, kappa=19.5), 40)
+
+
+def test_kernel_timing_on_and_off():
+    """Per-launch timing through the graphs' event nodes: counts one timed
+    launch per step up to the capacity; turning it off (capacity 0) and on
+    again leaves the step graphs usable; the results stay the oracle's."""
+    geom, cells, params = wl.box_workload(n=24, ncells=6, seed=9)
+    s = _solver(geom, cells, params)
+    s.set_timing(4)
+    s.step(6)
+    ms, cnt = s.kernel_times()
+    assert list(cnt) == [4, 4] and ms[0] > 0 and ms[1] > 0
+    s.set_timing(0)
+    s.step(3)
+    s.set_timing(2)
+    s.step(3)
+    ms, cnt = s.kernel_times()
+    assert list(cnt) == [2, 2]
+    s.set_timing(0)
+    s.step(2)
+    o = orc.Oracle(geom, cells, params)
+    o.step(14)
+    _, u_o, _ = o.fields()
+    assert rel_l2(s.fields()["u"], u_o) <= TOL
+    s.close()
+    o.close()
