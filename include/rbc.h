@@ -223,7 +223,10 @@ int rbc_neighbors(rbc_handle *h, int *counts, int *lists, int max_per_cell);
 /* Kernel timing.  rbc_set_timing(h, capacity) makes the next `capacity`
  * steps record CUDA events inside the step graph on the handle's stream:
  * before and after the per-cell kernel and after the lattice pass (capacity
- * 0 turns it off).  rbc_kernel_times synchronises and returns for k = 0 (the
+ * 0 turns it off).  Timed steps run a second pair of step graphs with those
+ * event-record nodes (captured at the first call with capacity > 0); a node
+ * between two kernels delays the second by a few microseconds, so untimed
+ * steps run graphs without them.  Synchronises.  rbc_kernel_times synchronises and returns for k = 0 (the
  * lattice pass, which runs alongside the next step's cell list, Gay-Berne
  * forces and shape lists) and k = 1 (the per-cell kernel: sampling, rigid
  * update and spreading) the summed milliseconds ms[k] and the number of

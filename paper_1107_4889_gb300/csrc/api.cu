@@ -415,9 +415,15 @@ struct rbc_handle {
     // g_pro: cell list + Gay-Berne of the initial poses (run once at init);
     // g_step[parity]: the per-cell kernel, then the lattice pass on the main
     // stream alongside the next step's cell list, Gay-Berne forces and shape
-    // lists on two side streams (they touch disjoint data), joined at the end
-    cudaGraphExec_t g_pro = nullptr, g_step[2] = {nullptr, nullptr};
+    // lists on two side streams (they touch disjoint data), joined at the end;
+    // g_timed[parity]: the same with three event-record nodes (before and
+    // after the per-cell kernel, after the lattice pass), captured when kernel
+    // timing is first turned on.  An event-record node between two kernels
+    // delays the second by several microseconds, so untimed steps run
+    // graphs without them.
+    cudaGraphExec_t g_pro = nullptr, g_step[2] = {nullptr, nullptr}, g_timed[2] = {nullptr, nullptr};
     cudaGraph_t src[3] = {nullptr, nullptr, nullptr};  // kept: exec updates name their nodes
+    cudaGraph_t src_timed[2] = {nullptr, nullptr};
     cudaGraphNode_t ev_node[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     cudaEvent_t ev_dummy[3] = {nullptr, nullptr, nullptr}, fork_ev = nullptr, join_ev = nullptr;
     cudaEvent_t join2_ev = nullptr;
@@ -470,6 +476,28 @@ static int capture(rbc_handle *h, void (*body)(rbc_handle *, int), int arg, cuda
     return RBC_OK;
 }
 
+static void body_step(rbc_handle *h, int parity);
+static thread_local bool g_capture_timed = false;  // body_step: add the timing event nodes
+
+// (Re-)capture the two step graphs: plain, or timed (with the event nodes,
+// whose handles go to ev_node).
+static int capture_steps(rbc_handle *h, bool timed)
+{
+    cudaGraphExec_t *ex = timed ? h->g_timed : h->g_step;
+    cudaGraph_t *src = timed ? h->src_timed : h->src;
+    g_capture_timed = timed;
+    int r = RBC_OK;
+    for (int par = 0; par < 2 && r == RBC_OK; ++par) {
+        if (ex[par]) cudaGraphExecDestroy(ex[par]);
+        if (src[par]) cudaGraphDestroy(src[par]);
+        ex[par] = nullptr;
+        src[par] = nullptr;
+        r = capture(h, body_step, par, &ex[par], timed ? h->ev_node[par] : nullptr, &src[par]);
+    }
+    g_capture_timed = false;
+    return r;
+}
+
 // Cell list, Gay-Berne forces and shape lists of the initial poses (the
 // shape lists of step k live in buffer k & 1).
 static void body_prologue(rbc_handle *h, int)
@@ -497,9 +525,10 @@ static void launch_side(rbc_handle *h, int parity)
 static void body_step(rbc_handle *h, int parity)
 {
     const bool cells = h->d.nc > 0;
-    cudaEventRecordWithFlags(h->ev_dummy[0], h->stream, cudaEventRecordExternal);
+    const bool timed = g_capture_timed;
+    if (timed) cudaEventRecordWithFlags(h->ev_dummy[0], h->stream, cudaEventRecordExternal);
     launch_cells(h->d, h->P.p, parity, h->stream);
-    cudaEventRecordWithFlags(h->ev_dummy[1], h->stream, cudaEventRecordExternal);
+    if (timed) cudaEventRecordWithFlags(h->ev_dummy[1], h->stream, cudaEventRecordExternal);
     if (cells) {
         cudaEventRecord(h->fork_ev, h->stream);
         cudaStreamWaitEvent(h->side, h->fork_ev, 0);
@@ -513,7 +542,7 @@ static void body_step(rbc_handle *h, int parity)
     if (!h->lb_first) launch_side(h, parity);
     launch_lb(h->d, h->P.p, parity, h->stream);
     if (h->lb_first) launch_side(h, parity);
-    cudaEventRecordWithFlags(h->ev_dummy[2], h->stream, cudaEventRecordExternal);
+    if (timed) cudaEventRecordWithFlags(h->ev_dummy[2], h->stream, cudaEventRecordExternal);
     if (cells) {
         cudaEventRecord(h->join_ev, h->side);
         cudaEventRecord(h->join2_ev, h->side2);
@@ -764,8 +793,8 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
             int r = capture(h, body_prologue, 0, &h->g_pro, nullptr, &h->src[2]);
             if (r != RBC_OK) return r;
         }
-        for (int par = 0; par < 2; ++par) {
-            int r = capture(h, body_step, par, &h->g_step[par], h->ev_node[par], &h->src[par]);
+        {
+            int r = capture_steps(h, false);
             if (r != RBC_OK) return r;
         }
         // cell list and Gay-Berne forces of the initial poses
@@ -804,13 +833,16 @@ int rbc_step(rbc_handle *h, int64_t n)
     for (int64_t k = 0; k < n; ++k) {
         const int par = (int)(h->step & 1);
         const bool timed = h->timing_used < h->timing_cap;
-        // each timed launch records into its own three events
-        for (int e = 0; e < 3; ++e)
-            RBC_CU(cudaGraphExecEventRecordNodeSetEvent(h->g_step[par], h->ev_node[par][e],
-                                                        timed ? h->ev[3 * (size_t)h->timing_used + e]
-                                                              : h->ev_dummy[e]));
-        RBC_CU(cudaGraphLaunch(h->g_step[par], h->stream));
-        if (timed) h->timing_used++;
+        if (timed) {
+            // each timed launch records into its own three events
+            for (int e = 0; e < 3; ++e)
+                RBC_CU(cudaGraphExecEventRecordNodeSetEvent(h->g_timed[par], h->ev_node[par][e],
+                                                            h->ev[3 * (size_t)h->timing_used + e]));
+            RBC_CU(cudaGraphLaunch(h->g_timed[par], h->stream));
+            h->timing_used++;
+        } else {
+            RBC_CU(cudaGraphLaunch(h->g_step[par], h->stream));
+        }
         h->step++;
     }
     return RBC_OK;
@@ -925,12 +957,12 @@ int rbc_set_timing(rbc_handle *h, int capacity)
 {
     if (!h || capacity < 0) return fail(h ? &h->err : nullptr, RBC_EINVAL, "bad argument");
     RBC_CU(cudaStreamSynchronize(h->stream));
-    // the step graphs' event nodes may still name events of the previous
+    // the timed graphs' event nodes may still name events of the previous
     // timing: point them back at the dummies before those events go
     for (int par = 0; par < 2; ++par) {
-        if (!h->g_step[par]) continue;
+        if (!h->g_timed[par]) continue;
         for (int e = 0; e < 3; ++e)
-            RBC_CU(cudaGraphExecEventRecordNodeSetEvent(h->g_step[par], h->ev_node[par][e], h->ev_dummy[e]));
+            RBC_CU(cudaGraphExecEventRecordNodeSetEvent(h->g_timed[par], h->ev_node[par][e], h->ev_dummy[e]));
     }
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     h->ev.clear();
@@ -940,6 +972,10 @@ int rbc_set_timing(rbc_handle *h, int capacity)
         cudaEvent_t e;
         RBC_CU(cudaEventCreate(&e));
         h->ev.push_back(e);
+    }
+    if (capacity > 0 && !h->g_timed[0]) {
+        int r = capture_steps(h, true);
+        if (r != RBC_OK) return r;
     }
     h->timing_cap = capacity;
     return RBC_OK;
@@ -967,19 +1003,14 @@ int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2])
     return RBC_OK;
 }
 
-// Re-capture both step graphs (after a change of launch shape).
+// Re-capture the step graphs (after a change of launch shape), the timed
+// ones too if they exist.
 static int recapture_steps(rbc_handle *h)
 {
     RBC_CU(cudaStreamSynchronize(h->stream));
-    for (int par = 0; par < 2; ++par) {
-        if (h->g_step[par]) cudaGraphExecDestroy(h->g_step[par]);
-        if (h->src[par]) cudaGraphDestroy(h->src[par]);
-        h->g_step[par] = nullptr;
-        h->src[par] = nullptr;
-        int r = capture(h, body_step, par, &h->g_step[par], h->ev_node[par], &h->src[par]);
-        if (r != RBC_OK) return r;
-    }
-    return RBC_OK;
+    int r = capture_steps(h, false);
+    if (r == RBC_OK && h->g_timed[0]) r = capture_steps(h, true);
+    return r;
 }
 
 // ms per coupled step over n steps after n warm-up steps (CUDA events on the
@@ -1104,8 +1135,11 @@ void rbc_free(rbc_handle *h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->g_pro) cudaGraphExecDestroy(h->g_pro);
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
         if (h->g_step[k]) cudaGraphExecDestroy(h->g_step[k]);
+        if (h->g_timed[k]) cudaGraphExecDestroy(h->g_timed[k]);
+        if (h->src_timed[k]) cudaGraphDestroy(h->src_timed[k]);
+    }
     for (int k = 0; k < 3; ++k)
         if (h->src[k]) cudaGraphDestroy(h->src[k]);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);

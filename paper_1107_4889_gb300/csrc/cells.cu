@@ -471,7 +471,7 @@ struct ShapeArgs {
     float two_over_xi[3], xi[3], kappa, alpha;
     int kappa_i;  // kappa when it is a whole number 1..64 (integer power), else 0
     int box_dim, sup_cap;
-    int box_pad;  // shared words per warp of k_weights: 2 box_dim^2 row words + sup_cap weights
+    int box_pad;  // shared words per warp of k_weights (weights_words)
 };
 
 // ---------------------------------------------------------------------------
@@ -486,17 +486,26 @@ struct ShapeArgs {
 // Weights w = prod_b phi(2 y_b / xi_b), y = Q^T (x - R) (Sec. 2.2), 0 at
 // solid nodes, vanish outside the parallelepiped |y_b| < xi_b.  Per box row
 // (i1, i2) the kernel solves the three slab constraints for the row's
-// support interval along x (widened by 1e-3: nodes outside evaluate to 0),
-// evaluates w only there into a compact array, and visits per row the
-// union of its own support widened by one node and the supports of its
-// four neighbour rows: every node where w or its central difference D w can
-// be non-zero.  The list holds those where one is, in lattice order (z, y,
+// support interval along x (widened by 1e-3: nodes outside evaluate to 0)
+// and evaluates w only there, one lane per support node, into a compact
+// array (a row index per item replaces a search).  Per row it then visits
+// the union of its own support widened by one node and the supports of its
+// four neighbour rows -- every node where w or its central difference D w
+// can be non-zero -- one lane per row walking x with w(x - 1), w(x), w(x + 1)
+// in registers.  The list holds every visited node, in lattice order (z, y,
 // x), with the lattice index, box coordinates (i0 | i1 << 10 | i2 << 20), w
-// and D w; S is the sum of w over fluid nodes.
-// Shared memory per warp: row words (support lo | hi << 8 | first item
-// << 16), visit words (same layout) and the compact weights.
+// and D w (all four zero at the few visited nodes where they vanish); S is
+// the sum of w over fluid nodes.
+// Shared memory per warp (weights_words): row words (support lo | hi << 8 |
+// first item << 16), visit words (same layout), the compact weights and the
+// row of every support item (16 bits).
 // ---------------------------------------------------------------------------
 constexpr int kWtWarps = 4;
+
+int weights_words(const Params &p)
+{
+    return 2 * p.box_dim * p.box_dim + p.sup_cap + (p.sup_cap + 1) / 2;
+}
 
 // support interval [lo, hi] of box row (i1, i2) along x; lo > hi if empty
 __device__ __forceinline__ void support_row(const float Q[9], const float bs[3], const float t[3], int n0, int i1,
@@ -529,17 +538,6 @@ __device__ __forceinline__ void support_row(const float Q[9], const float bs[3],
     hi = (int)fminf(floorf(fhi + 1e-3f), (float)(n0 - 1));
 }
 
-// largest k in [0, n) with (words[k] >> 16) <= t (the item's row)
-__device__ __forceinline__ int find_row(const unsigned *words, int n, int t)
-{
-    int k0 = 0, k1 = n - 1;
-    while (k0 < k1) {
-        const int mid = (k0 + k1 + 1) >> 1;
-        if ((int)(words[mid] >> 16) <= t) k0 = mid; else k1 = mid - 1;
-    }
-    return k0;
-}
-
 __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk)
 {
     extern __shared__ float smem[];
@@ -550,6 +548,7 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
     unsigned *srow = reinterpret_cast<unsigned *>(smem + (size_t)warp * a.box_pad);
     unsigned *vrow = srow + rows_cap;
     float *wc = reinterpret_cast<float *>(vrow + rows_cap);
+    uint16_t *srowof = reinterpret_cast<uint16_t *>(wc + a.sup_cap);
     const float qm = lane < 4 ? (float)a.q[4 * i + lane] : 0.f;
     float qf[4], Q[9];
 #pragma unroll
@@ -606,7 +605,10 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
                 const int v = __shfl_up_sync(0xffffffffu, incl, off);
                 if (lane >= off) incl += v;
             }
-            if (r < nrows) srow[r] = (slo <= shi ? (unsigned)(slo | (shi << 8)) : 0xFFu) | ((unsigned)(stot + incl - len) << 16);
+            const int first = stot + incl - len;
+            if (r < nrows) srow[r] = (slo <= shi ? (unsigned)(slo | (shi << 8)) : 0xFFu) | ((unsigned)first << 16);
+            if (first + len <= a.sup_cap)
+                for (int k = 0; k < len; ++k) srowof[first + k] = (uint16_t)r;
             stot += __shfl_sync(0xffffffffu, incl, 31);
         }
         if (stot > a.sup_cap) ok = false;
@@ -662,7 +664,7 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
     const int nxy = a.nx * a.ny;
     float part = 0.f;
     for (int t = lane; t < stot; t += 32) {
-        const int r = find_row(srow, nrows, t);
+        const int r = srowof[t];
         const unsigned word = srow[r];
         const int i0 = (int)(word & 0xFFu) + (t - (int)(word >> 16));
         const int i2 = (int)(((float)r + 0.5f) * inv1), i1 = r - i2 * n1;
@@ -677,42 +679,41 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
         part += w;
     }
     __syncwarp();
-    // w at (x, row r) from the compact array; 0 outside the row's support
-    auto W = [&](int r, int x) -> float {
-        const unsigned word = srow[r];
+    // w at column x of the row with support word `word` (0xFF: empty); 0
+    // outside the row's support
+    auto W = [&](unsigned word, int x) -> float {
         const int slo = (int)(word & 0xFFu), shi = (int)((word >> 8) & 0xFFu);
         return (x >= slo && x <= shi) ? wc[(int)(word >> 16) + x - slo] : 0.f;
     };
-    // 4. the visit items
+    // 4. the visit items, one lane per row: the row's words and those of its
+    //    four neighbour rows are read once, w(x - 1), w(x), w(x + 1) slide
     int2 *sp_idx = a.sp_idx + (size_t)i * a.sp_cap;
     float4 *sp_val = a.sp_val + (size_t)i * a.sp_cap;
-    int run = 0;
-    for (int ub = 0; ub < vtot; ub += 32) {
-        const int u = ub + lane;
-        bool live = false;
-        float w0 = 0.f, Dx = 0.f, Dy = 0.f, Dz = 0.f;
-        int g = 0, pk = 0;
-        if (u < vtot) {
-            const int r = find_row(vrow, nrows, u);
-            const unsigned word = vrow[r];
-            const int i0 = (int)(word & 0xFFu) + (u - (int)(word >> 16));
-            const int i2 = (int)(((float)r + 0.5f) * inv1), i1 = r - i2 * n1;
-            w0 = W(r, i0);
-            Dx = 0.5f * (W(r, i0 + 1) - W(r, i0 - 1));
-            Dy = 0.5f * ((i1 + 1 < n1 ? W(r + 1, i0) : 0.f) - (i1 > 0 ? W(r - 1, i0) : 0.f));
-            Dz = 0.5f * ((i2 + 1 < n2 ? W(r + n1, i0) : 0.f) - (i2 > 0 ? W(r - n1, i0) : 0.f));
-            live = w0 != 0.f || Dx != 0.f || Dy != 0.f || Dz != 0.f;
-            g = wrap1(o[0] + i0, a.nx) + a.nx * wrap1(o[1] + i1, a.ny) + nxy * wrap1(o[2] + i2, a.nz);
-            pk = i0 | (i1 << 10) | (i2 << 20);
+    for (int rb = 0; rb < nrows; rb += 32) {
+        const int r = rb + lane;
+        const unsigned vw = r < nrows ? vrow[r] : 0xFFu;
+        const int vlo = (int)(vw & 0xFFu), vhi = (int)((vw >> 8) & 0xFFu);
+        if (vlo > vhi) continue;
+        const int i2 = (int)(((float)r + 0.5f) * inv1), i1 = r - i2 * n1;
+        const unsigned own = srow[r];
+        const unsigned ym = i1 > 0 ? srow[r - 1] : 0xFFu, yp = i1 + 1 < n1 ? srow[r + 1] : 0xFFu;
+        const unsigned zm = i2 > 0 ? srow[r - n1] : 0xFFu, zp = i2 + 1 < n2 ? srow[r + n1] : 0xFFu;
+        const int rowbase = a.nx * (wrap1(o[1] + i1, a.ny) + a.ny * wrap1(o[2] + i2, a.nz));
+        const int pkr = (i1 << 10) | (i2 << 20);
+        int pos = (int)(vw >> 16);
+        float wl = W(own, vlo - 1), wm = W(own, vlo);
+        for (int x = vlo; x <= vhi; ++x, ++pos) {
+            const float wr = W(own, x + 1);
+            if (pos < a.sp_cap) {
+                sp_idx[pos] = make_int2(wrap1(o[0] + x, a.nx) + rowbase, x | pkr);
+                sp_val[pos] = make_float4(wm, 0.5f * (wr - wl), 0.5f * (W(yp, x) - W(ym, x)),
+                                          0.5f * (W(zp, x) - W(zm, x)));
+            }
+            wl = wm;
+            wm = wr;
         }
-        const unsigned mk = __ballot_sync(0xffffffffu, live);
-        const int pos = run + __popc(mk & ((1u << lane) - 1u));
-        if (live && pos < a.sp_cap) {
-            sp_idx[pos] = make_int2(g, pk);
-            sp_val[pos] = make_float4(w0, Dx, Dy, Dz);
-        }
-        run += __popc(mk);
     }
+    const int run = vtot;
     for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
     if (lane == 0) {
         for (int k = 0; k < 9; ++k) h[k] = Q[k];
@@ -1125,7 +1126,7 @@ ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
         a.xi[k] = p.xi[k];
     }
     a.box_dim = p.box_dim;
-    a.box_pad = 2 * p.box_dim * p.box_dim + p.sup_cap;
+    a.box_pad = weights_words(p);
     a.sup_cap = p.sup_cap;
     a.kappa = p.kappa;
     a.kappa_i = (p.kappa >= 1.0f && p.kappa <= 64.0f && p.kappa == floorf(p.kappa)) ? (int)p.kappa : 0;
@@ -1286,10 +1287,7 @@ void launch_gb(const Dev &d, const Params &p, cudaStream_t s)
     launch_prio(k_gb, blocks, 32 * kGbWarps, 0, s, d.side_prio, gb_args(d, p));
 }
 
-size_t cells_smem_bytes(const Params &p)
-{
-    return kWtWarps * (2 * (size_t)p.box_dim * p.box_dim + p.sup_cap) * sizeof(float);
-}
+size_t cells_smem_bytes(const Params &p) { return kWtWarps * (size_t)weights_words(p) * sizeof(float); }
 
 void prepare_cells(const Params &p)
 {
