@@ -278,7 +278,9 @@ __device__ __forceinline__ void gb_body(const GbArgs &g, int blk)
                         if (s_pre[wid][mid] <= t) k0 = mid; else k1 = mid - 1;
                     }
                     j = g.bin_cells[s_key[wid][k0] * g.cap + (t - s_pre[wid][k0])];
-                    if (j != i) {
+                    // a slot holds a cell index only if this step's binning
+                    // wrote it; the range test keeps anything else out
+                    if (j != i && (unsigned)j < (unsigned)g.nc) {
                         float df[3] = {Rif[0] - g.Rf[3 * j], Rif[1] - g.Rf[3 * j + 1], Rif[2] - g.Rf[3 * j + 2]};
                         min_image_f(df, g.per, g.Lf);
                         const float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
