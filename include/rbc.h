@@ -243,7 +243,10 @@ int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2]);
  * SM), each in both graph orders of the step (the cell-list, Gay-Berne and
  * shape-list kernels launched before the lattice pass, so that they overlap
  * it, or after it), over steps_per_trial coupled steps after as many
- * warm-up steps, keeps the fastest and re-captures the step graphs.  The trial steps are ordinary
+ * warm-up steps, keeps the fastest, then with it times bounded grids of the
+ * shape-list and Gay-Berne kernels (2-4 blocks per SM, grid-stride over the
+ * cells) against one block per group of cells, and re-captures the step
+ * graphs.  The trial steps are ordinary
  * steps of the solve (the state advances).  Synchronises.  out may be NULL. */
 typedef struct {
     int stages, ctas_per_sm;     /* chosen shape (0, 0: the one-thread-per-node pass, nothing to tune) */
@@ -251,6 +254,8 @@ typedef struct {
     double default_ms_per_step;  /* time per step of the cost model's shape */
     int trials;                  /* shapes timed */
     int lattice_first;           /* chosen order: 1 = lattice pass before the side kernels */
+    int wt_blocks_per_sm;        /* grid of the shape-list kernel, blocks per SM (0: one per 4 cells) */
+    int gb_blocks_per_sm;        /* grid of the Gay-Berne kernel, blocks per SM (0: one per 8 cells) */
 } rbc_tune_report;
 int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out);
 

@@ -1043,6 +1043,12 @@ int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out)
     if (h->timing_used < h->timing_cap) return fail(&h->err, RBC_EINVAL, "kernel timing is active");
     const int st0 = h->d.lb_stages, grid0 = h->d.lb_grid;
     const size_t smem0 = h->d.lb_smem;
+    if (h->d.wt_grid != 0 || h->d.gb_grid != 0) {
+        // the lattice shapes are timed with one block per group of cells
+        h->d.wt_grid = h->d.gb_grid = 0;
+        const int r = recapture_steps(h);
+        if (r != RBC_OK) return r;
+    }
     if (grid0 <= 0) {
         int rc = time_steps(h, steps_per_trial, &rep.ms_per_step);
         rep.default_ms_per_step = rep.ms_per_step;
@@ -1086,6 +1092,35 @@ int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out)
         rep.ctas_per_sm = (grid0 + sms - 1) / sms;
     }
     rep.lattice_first = h->lb_first ? 1 : 0;
+    // then the grids of the shape-list and Gay-Berne kernels (blocks per
+    // SM; 0: one block per group of cells), with that shape and order: a
+    // bounded grid leaves the kernels room on every SM beside each other
+    // and beside the lattice pass
+    if (h->d.nc > 0) {
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int side[][2] = {{2, 2}, {3, 2}, {2, 3}, {3, 3}, {4, 2}};
+        int bw = 0, bg = 0;
+        for (const auto &c : side) {
+            h->d.wt_grid = c[0] * sms;
+            h->d.gb_grid = c[1] * sms;
+            rc = recapture_steps(h);
+            double ms = 0.0;
+            if (rc == RBC_OK) rc = time_steps(h, steps_per_trial, &ms);
+            if (rc != RBC_OK) return rc;
+            rep.trials++;
+            if (ms < best) {
+                best = ms;
+                bw = c[0];
+                bg = c[1];
+            }
+        }
+        h->d.wt_grid = bw * sms;
+        h->d.gb_grid = bg * sms;
+        rep.wt_blocks_per_sm = bw;
+        rep.gb_blocks_per_sm = bg;
+    }
     rep.ms_per_step = best;
     rc = recapture_steps(h);
     if (out) *out = rep;

@@ -452,7 +452,16 @@ __device__ __forceinline__ void gb_body(const GbArgs &g, int blk)
     if (threadIdx.x == 0 && s_clamped) atomicAdd(g.clamps, (unsigned long long)s_clamped);
 }
 
-__global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g) { gb_body(g, blockIdx.x); }
+// Grid-stride over the groups of kGbWarps cells: a grid smaller than the
+// group count leaves room on the SMs for the kernels running beside it.
+__global__ void __launch_bounds__(32 * kGbWarps) k_gb(GbArgs g)
+{
+    const int groups = (g.nc + kGbWarps - 1) / kGbWarps;
+    for (int b = blockIdx.x; b < groups; b += gridDim.x) {
+        gb_body(g, b);
+        __syncthreads();  // the next group reuses the block's shared memory
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Shape lists
@@ -732,7 +741,15 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
     }
 }
 
-__global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc) { weights_body(a, nc, blockIdx.x); }
+// Grid-stride over the groups of kWtWarps cells (see k_gb).
+__global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc)
+{
+    const int groups = (nc + kWtWarps - 1) / kWtWarps;
+    for (int b = blockIdx.x; b < groups; b += gridDim.x) {
+        weights_body(a, nc, b);
+        __syncwarp();  // the warp's next cell reuses its shared memory
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Sampling over the cell's shape list (one warp per cell):
@@ -876,11 +893,14 @@ struct RigidArgs {
 // q has unit norm (rbc_init normalises it, every step renormalises), so
 // |q + dq|^2 - 1 = e = 2 q.dq + dq.dq and the renormalised q is
 // (q + dq)(1 + s), s = -e/2 + 3e^2/8.
-// Returns false, with no update, when the cell has no valid shape box or
-// S = 0; J and L are then undefined.
+// J and L are handed to `publish` as soon as they exist, before the
+// sub-rotations (which only the stored state needs).  Returns false, with
+// no update and without calling publish, when the cell has no valid shape
+// box or S = 0.
 
+template <typename Publish>
 __device__ __forceinline__ bool rigid_update(const RigidArgs &a, int i, float Sf, const float (&sums)[9],
-                                             float (&J)[3], float (&Lm)[3])
+                                             Publish &&publish)
 {
     const int lane = threadIdx.x & 31;
     const int ok = reinterpret_cast<const int *>(a.hdr)[kHdrWords * i + 19];
@@ -925,7 +945,7 @@ __device__ __forceinline__ bool rigid_update(const RigidArgs &a, int i, float Sf
         TS[d] = a.alpha * sums[6 + d] * iS;
         Tl[d] = Tm[d] + TS[d];
     }
-    float dV[3], dW[3], Lb[3];
+    float dV[3], dW[3], Lb[3], J[3], Lm[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const float Fc = Fm[d] + a.gT * a.M * ut[d];
@@ -941,6 +961,7 @@ __device__ __forceinline__ bool rigid_update(const RigidArgs &a, int i, float Sf
     for (int d = 0; d < 3; ++d)
         Lm[d] = Q[3 * d] * Lb[0] + Q[3 * d + 1] * Lb[1] + Q[3 * d + 2] * Lb[2] +
                 b * ((a.eR - 1.0f) * Tm[d] + a.eR * TS[d]);
+    publish(J, Lm);
     // step 4 in increments: dq accumulates q r - q, dW the momentum turns
     float Wf[3] = {W0[0] + dW[0], W0[1] + dW[1], W0[2] + dW[2]};
     float dq[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1030,9 +1051,30 @@ __device__ __forceinline__ float pow_kappa(float x, const ShapeArgs &a)
 }
 
 // Two warps per cell (kCellWarps / 2 cells per block): both sample half of
-// the cell's list, the first adds the halves (fixed order) and runs the
-// rigid update, both spread half of the list.
+// the cell's list; the first adds the halves (fixed order), computes the
+// impulses J, L, hands them to the second through shared memory and a named
+// barrier of the pair, and finishes the rigid update (the sub-rotations and
+// the stored state) while the second spreads over the whole list.
 constexpr int kCellsPerBlock = kCellWarps / 2;
+
+// Named barriers 1 and 2 (one per pair of warps; 0 is __syncthreads).  The
+// ids are immediates: a barrier id held in a register makes the compiler
+// reserve all 16 barriers of the block, which cut the blocks per SM.
+static_assert(kCellsPerBlock == 2, "one named barrier per cell of the block");
+__device__ __forceinline__ void pair_arrive(int pair)
+{
+    if (pair == 0)
+        asm volatile("bar.arrive 1, 64;" ::: "memory");
+    else
+        asm volatile("bar.arrive 2, 64;" ::: "memory");
+}
+__device__ __forceinline__ void pair_sync(int pair)
+{
+    if (pair == 0)
+        asm volatile("bar.sync 1, 64;" ::: "memory");
+    else
+        asm volatile("bar.sync 2, 64;" ::: "memory");
+}
 
 template <bool ALPHA>
 __device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &ra, int nc, int blk)
@@ -1051,32 +1093,45 @@ __device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &
         for (int k = 0; k < 9; ++k) sums[k] = 0.f;
     if (half == 1 && lane < 9) s_part[pair][lane] = pick(sums, lane);
     __syncthreads();
-    if (half == 0 && valid) {
+    if (!valid) return;  // uniform across the pair: neither warp takes the pair barrier
+    if (half == 0) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) sums[k] += s_part[pair][k];
-        float J[3], L[3];
-        const bool go = rigid_update(ra, i, S, sums, J, L) && n > 0;
-        if (lane == 0) {
-            const float iS = go ? 1.0f / S : 0.f;
-            for (int d = 0; d < 3; ++d) {
-                s_jl[pair][d] = J[d] * iS;
-                s_jl[pair][3 + d] = 0.5f * L[d] * iS;
+        bool published = false;
+        auto publish = [&](const float (&J)[3], const float (&L)[3]) {
+            if (lane == 0) {
+                const bool go = n > 0;
+                const float iS = go ? 1.0f / S : 0.f;
+                for (int d = 0; d < 3; ++d) {
+                    s_jl[pair][d] = J[d] * iS;
+                    s_jl[pair][3 + d] = 0.5f * L[d] * iS;
+                }
+                s_jl[pair][6] = go ? 1.f : 0.f;
             }
-            s_jl[pair][6] = go ? 1.f : 0.f;
+            __syncwarp();
+            pair_arrive(pair);
+            published = true;
+        };
+        rigid_update(ra, i, S, sums, publish);
+        if (!published) {
+            if (lane == 0) s_jl[pair][6] = 0.f;
+            __syncwarp();
+            pair_arrive(pair);
         }
+        return;
     }
-    __syncthreads();
-    if (!valid || s_jl[pair][6] == 0.f) return;
+    pair_sync(pair);
+    if (s_jl[pair][6] == 0.f) return;
     const float Jx = s_jl[pair][0], Jy = s_jl[pair][1], Jz = s_jl[pair][2];
     const float Lx = s_jl[pair][3], Ly = s_jl[pair][4], Lz = s_jl[pair][5];
     const int2 *idx = a.sp_idx + (size_t)i * a.sp_cap;
     const float4 *val = a.sp_val + (size_t)i * a.sp_cap;
-    for (int e0 = lane + 32 * half; e0 < n; e0 += 64 * kIlp) {
+    for (int e0 = lane; e0 < n; e0 += 32 * kIlp) {
         int g[kIlp];
         float4 v[kIlp];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
-            const int e = e0 + 64 * j;
+            const int e = e0 + 32 * j;
             g[j] = e < n ? idx[e].x : -1;
             v[j] = e < n ? val[e] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -1285,7 +1340,8 @@ static GbArgs gb_args(const Dev &d, const Params &p)
 void launch_gb(const Dev &d, const Params &p, cudaStream_t s)
 {
     if (d.nc == 0) return;
-    const int blocks = (d.nc + kGbWarps - 1) / kGbWarps;
+    const int groups = (d.nc + kGbWarps - 1) / kGbWarps;
+    const int blocks = d.gb_grid > 0 && d.gb_grid < groups ? d.gb_grid : groups;
     launch_prio(k_gb, blocks, 32 * kGbWarps, 0, s, d.side_prio, gb_args(d, p));
 }
 
@@ -1300,8 +1356,9 @@ void prepare_cells(const Params &p)
 void launch_weights(const Dev &d, const Params &p, int buf, cudaStream_t s)
 {
     if (d.nc == 0) return;
-    launch_prio(k_weights, (d.nc + kWtWarps - 1) / kWtWarps, 32 * kWtWarps, cells_smem_bytes(p), s, d.side_prio,
-                shape_args(d, p, buf), d.nc);
+    const int groups = (d.nc + kWtWarps - 1) / kWtWarps;
+    const int blocks = d.wt_grid > 0 && d.wt_grid < groups ? d.wt_grid : groups;
+    launch_prio(k_weights, blocks, 32 * kWtWarps, cells_smem_bytes(p), s, d.side_prio, shape_args(d, p, buf), d.nc);
 }
 
 static RigidArgs rigid_args(const Dev &d, const Params &p)

@@ -92,6 +92,7 @@ struct Dev {
     int *lb_work;  // lattice-pass batch counter and finished-CTA count (zero between launches)
     unsigned long long *lb_step;  // lattice passes done (advanced by the pass itself)
     int side_prio;  // launch priority of the side-stream kernels (the device's highest)
+    int wt_grid = 0, gb_grid = 0;  // blocks of the shape-list and Gay-Berne launches (0: one per group)
     size_t lb_smem;
 };
 
