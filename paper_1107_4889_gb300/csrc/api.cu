@@ -72,12 +72,40 @@ int fail(std::string *err, int code, const std::string &msg)
     return code;
 }
 
+// node index of (x, y, z), each coordinate at most one step outside the
+// lattice (periodic wrap)
 inline long long node(const Problem &P, int x, int y, int z)
 {
-    x = (x % P.nx + P.nx) % P.nx;
-    y = (y % P.ny + P.ny) % P.ny;
-    z = (z % P.nz + P.nz) % P.nz;
+    x = x < 0 ? x + P.nx : (x >= P.nx ? x - P.nx : x);
+    y = y < 0 ? y + P.ny : (y >= P.ny ? y - P.ny : y);
+    z = z < 0 ? z + P.nz : (z >= P.nz ? z - P.nz : z);
     return (long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z);
+}
+
+// near[n] = 1 when a solid node lies in the 3x3x3 cube around n (periodic
+// wrap), by three one-axis passes; a node with near[n] = 0 has no solid link
+// neighbour, so the host loops over link neighbours skip it.
+std::vector<uint8_t> near_solid(const Problem &P, const uint8_t *solid)
+{
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const long long sx = 1, sy = nx, sz = (long long)nx * ny, N = sz * nz;
+    std::vector<uint8_t> a(solid, solid + N), b((size_t)N);
+    // one pass: b = a | a shifted by +-1 along the axis of length n, stride st
+    auto pass = [&](int n, long long st) {
+        for (long long base = 0; base < N; base += st * n)  // blocks of n planes
+            for (long long off = 0; off < st; ++off)
+                for (int c = 0; c < n; ++c) {
+                    const long long i = base + off + c * st;
+                    const long long lo = base + off + (c > 0 ? c - 1 : n - 1) * st;
+                    const long long hi = base + off + (c < n - 1 ? c + 1 : 0) * st;
+                    b[i] = a[i] | a[lo] | a[hi];
+                }
+        a.swap(b);
+    };
+    pass(nx, sx);
+    pass(ny, sy);
+    pass(nz, sz);
+    return a;
 }
 
 int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Problem &P, std::string *err)
@@ -256,10 +284,12 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     if (P.any_solid && nc > 0) {
         // solid nodes with a fluid link neighbour: marked from the fluid side
         std::vector<uint8_t> wet((size_t)N, 0);
+        const std::vector<uint8_t> near = near_solid(P, g->solid);
         for (int z = 0; z < P.nz; ++z)
             for (int y = 0; y < P.ny; ++y)
                 for (int x = 0; x < P.nx; ++x) {
-                    if (g->solid[(long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z)]) continue;
+                    const long long n = (long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z);
+                    if (g->solid[n] || !near[n]) continue;
                     for (int p = 1; p < kQ; ++p) {
                         const long long m = node(P, x + cx(p), y + cy(p), z + cz(p));
                         if (g->solid[m]) wet[m] = 1;
@@ -292,10 +322,12 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     P.want_sigma = (nc > 0 && q.alpha_tt != 0.0) || P.has_bc;
     P.nwss = 0;
     if (P.any_solid && P.want_sigma) {
+        const std::vector<uint8_t> near = near_solid(P, g->solid);
         for (int z = 0; z < P.nz; ++z)
             for (int y = 0; y < P.ny; ++y)
                 for (int x = 0; x < P.nx; ++x) {
-                    if (g->solid[(long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z)]) continue;
+                    const long long n = (long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z);
+                    if (g->solid[n] || !near[n]) continue;
                     for (int p = 1; p < kQ; ++p)
                         if (g->solid[node(P, x + cx(p), y + cy(p), z + cz(p))]) {
                             P.nwss++;
@@ -689,6 +721,8 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
             // when the downstream node x + c_p is solid (fluid nodes), bit 29 /
             // 30 for inlet / outlet nodes, bit 31 when x is solid
             links.assign((size_t)P.N, 0u);
+            std::vector<uint8_t> near;
+            if (geom->solid) near = near_solid(P, geom->solid);
             for (int z = 0; z < P.nz; ++z)
                 for (int y = 0; y < P.ny; ++y) {
                     const long long row = (long long)P.nx * ((long long)y + (long long)P.ny * z);
@@ -700,7 +734,7 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
                         }
                         uint32_t m = 0u;
                         float nv[3] = {0.f, 0.f, 0.f};
-                        if (geom->solid)
+                        if (geom->solid && near[n])
                             for (int p = 1; p < kQ; ++p)
                                 if (geom->solid[node(P, x + cx(p), y + cy(p), z + cz(p))]) {
                                     m |= 1u << p;
