@@ -95,25 +95,24 @@ struct BinArgs {
     double bs[3], a2[3];
 };
 
+// One thread per cell.  Its loads come first and the bin's slot, returned by
+// the atomic, is used last, so that the FP64 shape tensor is computed while
+// the atomic is in flight.
 __device__ __forceinline__ void bin_body(const BinArgs &g, int blk)
 {
     const int i = blk * blockDim.x + threadIdx.x;
     if (i >= g.nc) return;
-    double Rd[3];
+    double Rd[3], qq[4];
+    for (int a = 0; a < 3; ++a) Rd[a] = g.R[3 * i + a];
+    for (int k = 0; k < 4; ++k) qq[k] = g.q[4 * i + k];
     int b[3];
     for (int a = 0; a < 3; ++a) {
-        Rd[a] = g.R[3 * i + a];
         int k = (int)floor(Rd[a] / g.bs[a]);
         b[a] = k < 0 ? 0 : (k >= g.nb[a] ? g.nb[a] - 1 : k);
     }
     const int bin = b[0] + g.nb[0] * (b[1] + g.nb[1] * b[2]);
-    g.cell_bin[i] = bin;
     const int slot = atomicAdd(&g.bin_count[bin], 1);
-    if (slot < g.cap)
-        g.bin_cells[bin * g.cap + slot] = i;
-    else
-        atomicOr(&g.flags[FLAG_OVERFLOW], OVF_BIN);
-    double qq[4] = {g.q[4 * i], g.q[4 * i + 1], g.q[4 * i + 2], g.q[4 * i + 3]};
+    g.cell_bin[i] = bin;
     const double in = 1.0 / sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
     for (int k = 0; k < 4; ++k) qq[k] *= in;
     double Q[9];
@@ -133,7 +132,10 @@ __device__ __forceinline__ void bin_body(const BinArgs &g, int blk)
     g.Af[6 * i + 3] = (float)S.xy;
     g.Af[6 * i + 4] = (float)S.xz;
     g.Af[6 * i + 5] = (float)S.yz;
-
+    if (slot < g.cap)
+        g.bin_cells[bin * g.cap + slot] = i;
+    else
+        atomicOr(&g.flags[FLAG_OVERFLOW], OVF_BIN);
 }
 
 __global__ void __launch_bounds__(kBinThreads) k_bin(BinArgs g) { bin_body(g, blockIdx.x); }
