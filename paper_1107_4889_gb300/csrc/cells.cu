@@ -15,7 +15,7 @@
 //             weights on its box staged in shared memory, written out as
 //             the cell's shape list (node, w, D w) with the normalisation S;
 //             built for the next pose while the lattice pass runs.
-//   k_cells   one warp per cell: the fields sampled over the shape list
+//   k_cells   two warps per cell: the fields sampled over the shape list
 //             (Eqs. vel, vort, pheno_torque_diss), the rigid-body update
 //             (App. A) with the hydrodynamic impulses, and the reaction
 //             force density and smoothed characteristic function added
@@ -1030,14 +1030,14 @@ __device__ __forceinline__ bool rigid_update(const RigidArgs &a, int i, float Sf
 
 
 // ---------------------------------------------------------------------------
-// k_cells: the per-cell part of the coupled step, one warp per cell.
+// k_cells: the per-cell part of the coupled step, two warps per cell.
 //   1. sample the fields over the cell's shape list (sample_sums);
 //   2. the rigid-body update and the hydrodynamic impulses J, L (App. A);
 //   3. spread (h = 1) over the same list: G += -J delta + 1/2 L x D delta
 //      (delta = w / S) and theta += 1 - (1 - w)^kappa where w > 0 (Sec.
 //      2.2, Eq. enhance-viscosity), with atomics.
-// A cell's spread writes only G and theta, which no sampling reads, so each
-// warp goes straight from its own update to its own spread.
+// A cell's spread writes only G and theta, which no sampling reads, so the
+// spreading warp starts as soon as its cell's J and L exist.
 // ---------------------------------------------------------------------------
 // (1 - w)^kappa of Eq. enhance-viscosity: by squaring for a whole-number
 // kappa (the paper's 20: five multiplications), powf otherwise
