@@ -488,7 +488,7 @@ def run_wss_map(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20000)
@@ -512,7 +512,11 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=48)
     ap.add_argument("--serve-tick", type=int, default=100)
     ap.add_argument("--serve-arena-gb", type=float, default=64.0)
-    args = ap.parse_args()
+    return ap.parse_args(argv)
+
+
+def main():
+    args = parse_args()
     if args.serve:
         run_serve(args)
         return
