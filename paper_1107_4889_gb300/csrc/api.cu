@@ -539,13 +539,8 @@ static void body_prologue(rbc_handle *h, int)
     launch_weights(h->d, h->P.p, 0, h->stream);
 }
 
-// One coupled step.  Main stream: the per-cell kernel (sample the fields
-// with this pose's shape lists, the rigid update to the new poses, spread
-// the impulses with the same lists), then the lattice pass.  As soon as the
-// new poses exist, two side streams build the next step's cell list and
-// Gay-Berne forces, and its shape headers and shape lists (into buffer
-// parity ^ 1); they read only the poses and write nothing the lattice pass
-// reads.  The step ends when all three streams have.
+// The side work of a step: the next step's shape lists on one side stream,
+// its cell list and Gay-Berne forces on the other.
 static void launch_side(rbc_handle *h, int parity)
 {
     if (h->d.nc <= 0) return;
@@ -554,6 +549,13 @@ static void launch_side(rbc_handle *h, int parity)
     launch_gb(h->d, h->P.p, h->side);
 }
 
+// One coupled step.  Main stream: the per-cell kernel (sample the fields
+// with this pose's shape lists, the rigid update to the new poses, spread
+// the impulses with the same lists), then the lattice pass.  As soon as the
+// new poses exist, two side streams build the next step's cell list and
+// Gay-Berne forces, and its shape headers and shape lists (into buffer
+// parity ^ 1); they read only the poses and write nothing the lattice pass
+// reads.  The step ends when all three streams have.
 static void body_step(rbc_handle *h, int parity)
 {
     const bool cells = h->d.nc > 0;
