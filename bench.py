@@ -239,13 +239,14 @@ def run_ours(args):
     from paper_1107_4889_gb300.rbc import Solver
 
     ws, rank, local = _dist()
+    # the device first, so that NCCL binds each rank's communicator to its own GPU
+    torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     if rank == 0:
         B.build()
     _barrier(ws)
-    torch.cuda.set_device(local)
     geom, cells, params, desc = _workload(args.workload, args.precision)
     if args.no_cells and cells is not None:
         cells, desc = None, desc + ", cells removed"

@@ -298,11 +298,13 @@ int rbc_launches_per_step(const rbc_handle *h);
  * RBC_NOALLOC_SCRATCH_INTS ints that every GPU loading the library holds
  * until the process exits; boxes whose grid needs more return RBC_EINVAL.
  * All calls share that array, so calls that overlap on the GPU race and
- * must be serialised.  The first call on a device looks up the array's
- * address (cudaGetSymbolAddress) with that device current: make it before
- * any stream capture.  Synchronises the stream; RBC_ENOMEM when a bin holds
- * more than 32 cells or a list exceeds max_per_cell; rbc_last_error(NULL)
- * describes failures. */
+ * must be serialised.  Every call looks up the array's address
+ * (cudaGetSymbolAddress) on the current device, clears the counts it uses,
+ * and ends by copying a flag back and synchronising the stream: never call
+ * it on a stream that is being captured into a CUDA graph.  RBC_EINVAL for
+ * a box whose grid of bins no smaller than r_cut needs more scratch than
+ * the array holds; RBC_ENOMEM when a bin holds more than 32 cells or a list
+ * exceeds max_per_cell; rbc_last_error(NULL) describes failures. */
 int rbc_neighbors_noalloc(const double *pos, int n, int nx, int ny, int nz, const int periodic[3],
                           double r_cut, int *counts, int *lists, int max_per_cell, void *stream);
 

@@ -10,10 +10,11 @@
  *
  * Every function follows the paper's steps in the paper's order, in FP64,
  * single-threaded, with no blocking or fusion.  Where the paper is garbled or
- * silent the reading taken is named in the comment (the same readings are
- * listed in the design notes of the repository).  Pins: every function here
- * is checked by the -m "not gpu" tests against closed forms, invariants or
- * brute force (see tests/test_oracle_*.py).
+ * silent the reading taken is stated in the comment of the function that
+ * takes it.  Pins: every function here is checked by the -m "not gpu" tests
+ * against closed forms, invariants or brute force (tests/test_oracle_*.py);
+ * the per-cell sums of the Gay-Berne forces and torques, the wall-particle
+ * set and the frame of the angular impulse by tests/test_oracle_mechanics.py.
  *
  * One coupled step (readings "explicit coupling" and "velocity-Verlet caching"):
  *   1. shapes of every cell at the current pose (Sec. 2.2);

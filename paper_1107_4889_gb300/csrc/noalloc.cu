@@ -14,15 +14,17 @@
 // The array is RBC_NOALLOC_SCRATCH_INTS ints (4 MiB) and stays resident on
 // every device that loads this library, until the process exits.  Every call
 // shares it: calls that overlap on the GPU (on different streams, or from
-// different threads) race on it and must be serialised by the caller.  The
-// first call on a device looks up the array's device address with
-// cudaGetSymbolAddress while that device is current; make that first call
-// before any stream capture.
+// different threads) race on it and must be serialised by the caller.  Each
+// call looks up the array's device address with cudaGetSymbolAddress while
+// the caller's device is current (a host-side name of a __device__ array is
+// not a device address), so the address stays right after the context is
+// torn down and re-created.  A call copies the overflow flag back and
+// synchronises its stream, so it must never be made on a stream that is
+// being captured into a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "../../include/rbc.h"
@@ -33,16 +35,12 @@ void set_thread_error(const std::string &msg);  // api.cu: rbc_last_error(NULL)
 
 namespace {
 
-constexpr int kMaxDevices = 64;
 constexpr int kBinCap = 32;    // cells per bin
 constexpr int kWarps = 4;      // cells per CTA of the list kernel
 constexpr int kMaxList = 128;  // partners kept per cell
 
 // [0] overflow flag, [1 .. nbins] bin counts, then nbins * kBinCap slots
 static __device__ __align__(256) int g_scratch[RBC_NOALLOC_SCRATCH_INTS];
-
-int *g_scratch_addr[kMaxDevices] = {nullptr};
-std::mutex g_setup_mutex;
 
 int fail(int code, const std::string &msg)
 {
@@ -169,31 +167,30 @@ extern "C" int rbc_neighbors_noalloc(const double *pos, int n, int nx, int ny, i
     if (n > 0 && (!pos || !counts || !lists)) return fail(RBC_EINVAL, "NULL buffer");
     Grid g;
     const int dims[3] = {nx, ny, nz};
+    const std::string too_big = "the cell-list grid of this box exceeds the static scratch (" +
+                                std::to_string(RBC_NOALLOC_SCRATCH_INTS) + " ints)";
+    // Bins per axis, checked in floating point before any integer cast: a
+    // tiny r_cut would overflow the int, and the product of three large
+    // axes the 64-bit count.  Each axis stays below the scratch size
+    // (2^20), so the product of three fits 64 bits.
     long long nbins = 1;
     for (int a = 0; a < 3; ++a) {
         g.per[a] = periodic[a] ? 1 : 0;
         if (g.per[a] && 2.0 * r_cut >= dims[a]) return fail(RBC_EINVAL, "r_cut must be below half the box");
-        g.nb[a] = std::max(1, (int)std::floor(dims[a] / r_cut));
+        const double per_axis = std::floor(dims[a] / r_cut);
+        if (!(per_axis < (double)RBC_NOALLOC_SCRATCH_INTS)) return fail(RBC_EINVAL, too_big);
+        g.nb[a] = std::max(1, (int)per_axis);
         g.bs[a] = (double)dims[a] / g.nb[a];
         g.L[a] = dims[a];
         nbins *= g.nb[a];
+        if (1 + nbins * (1 + kBinCap) > RBC_NOALLOC_SCRATCH_INTS) return fail(RBC_EINVAL, too_big);
     }
     g.rc2 = r_cut * r_cut;
-    if (1 + nbins * (1 + kBinCap) > RBC_NOALLOC_SCRATCH_INTS)
-        return fail(RBC_EINVAL, "the cell-list grid of this box exceeds the static scratch (" +
-                                    std::to_string(RBC_NOALLOC_SCRATCH_INTS) + " ints)");
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return fail(RBC_ECUDA, "no CUDA device");
-    {
-        std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_addr[dev]) {
-            void *p = nullptr;
-            const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-            if (e != cudaSuccess) return fail(RBC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_scratch_addr[dev] = static_cast<int *>(p);
-        }
-    }
-    int *scratch = g_scratch_addr[dev];
+    // the device address of the static array in the current context
+    void *addr = nullptr;
+    const cudaError_t ea = cudaGetSymbolAddress(&addr, g_scratch);
+    if (ea != cudaSuccess) return fail(RBC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(ea));
+    int *scratch = static_cast<int *>(addr);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the flag and the bin counts must start at zero; slots are written before read
     cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int) * (size_t)(1 + nbins), s);
