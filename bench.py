@@ -248,6 +248,9 @@ def run_ours(args):
         B.build()
     _barrier(ws)
     geom, cells, params, desc = _workload(args.workload, args.precision)
+    if args.node_list:
+        params = dict(params, node_list=args.node_list)
+        desc += ", node-list pass" if args.node_list > 0 else ", row-staged pass"
     if args.no_cells and cells is not None:
         cells, desc = None, desc + ", cells removed"
     nf = wl.fluid_count(geom)
@@ -503,6 +506,8 @@ def parse_args(argv=None):
     ap.add_argument("--wss-map", action="store_true",
                     help="wall-shear-stress map of the workload, binary16 against FP32")
     ap.add_argument("--no-cells", action="store_true", help="drop the workload's cells (lattice pass alone)")
+    ap.add_argument("--node-list", type=int, default=0, choices=[-1, 0, 1],
+                    help="lattice pass over a fluid-node list (1), whole rows (-1), or the library's choice (0)")
     ap.add_argument("--precision", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune-steps", type=int, default=50,
