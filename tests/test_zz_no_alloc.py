@@ -50,8 +50,10 @@ def _geometry(dims, periodic):
 
 def _case(seed, dims, periodic, n):
     rng = np.random.default_rng(seed)
-    lo = np.array([0.0, 0.0 if periodic[1] else 1.0, 0.0])
-    hi = np.array(dims, float) - np.array([0.0, 0.0 if periodic[1] else 2.0, 0.0])
+    # walled along y: centres at least 6 from the wall planes (beyond the
+    # Gay-Berne range of a wall particle), all three bin rows still used
+    lo = np.array([0.0, 0.0 if periodic[1] else 6.0, 0.0])
+    hi = np.array(dims, float) - np.array([0.0, 0.0 if periodic[1] else 7.0, 0.0])
     pos = lo + rng.random((n, 3)) * (hi - lo)
     for a in range(3):
         pos[pos[:, a] >= dims[a], a] -= dims[a]
