@@ -119,10 +119,23 @@ typedef struct {
  *                       RBC_ROUND_NEAREST (ties to even, IEEE) is biased by
  *                       percents in slow steady flows [stochastic]
  *   seed                key of the stochastic rounding [0]
- *   node_list           lattice pass over a list of the fluid nodes (one
- *                       thread each, no work on solid nodes) instead of whole
- *                       staged rows: 1 always, -1 never, 0 when fewer than
- *                       half the nodes are fluid (sparse vessel geometries)
+ *   node_list           dense layout only: lattice pass over a list of the
+ *                       fluid nodes (one thread each, no work on solid nodes)
+ *                       instead of whole staged rows: 1 always, -1 never, 0
+ *                       when fewer than half the nodes are fluid
+ *   layout              storage of the lattice fields [RBC_LAYOUT_AUTO]:
+ *                       RBC_LAYOUT_DENSE keeps every node; RBC_LAYOUT_COMPACT
+ *                       keeps, per lattice row (y, z), only the span of x
+ *                       that a fluid node can reach through a link (the
+ *                       hull of the fluid nodes of the nine neighbouring rows
+ *                       widened by one, rounded out to 8 entries, or the
+ *                       whole row when it wraps along x), in lattice order,
+ *                       so the memory and the lattice pass's traffic follow
+ *                       the fluid nodes of vessel geometries; requires solid
+ *                       nodes and nx <= 32760 (RBC_EINVAL otherwise).
+ *                       RBC_LAYOUT_AUTO takes the compact layout for lattices
+ *                       with solid nodes where it stores at most 90 % of the
+ *                       nodes.  The request server packs dense solves only.
  *   stream              cudaStream_t the library works on (NULL: one it
  *                       creates and owns). */
 typedef struct {
@@ -143,8 +156,13 @@ typedef struct {
     int rounding;
     uint64_t seed;
     int node_list;
+    int layout;
     void *stream;
 } rbc_params;
+
+#define RBC_LAYOUT_AUTO 0
+#define RBC_LAYOUT_DENSE 1
+#define RBC_LAYOUT_COMPACT 2
 
 #define RBC_PREC_F32 0
 #define RBC_PREC_F16 1
@@ -276,6 +294,19 @@ int rbc_wss(rbc_handle *h, int64_t *node, double *tau, int64_t max, int64_t *n, 
 
 /* Kernel launches one rbc_step(h, 1) enqueues. */
 int rbc_launches_per_step(const rbc_handle *h);
+
+/* Storage layout of the handle's lattice fields (see rbc_params.layout):
+ * *compact = 1 for the compact layout, *entries = stored entries per field
+ * (lattice nodes when dense), *fluid = fluid nodes.  Any pointer may be
+ * NULL. */
+int rbc_layout(const rbc_handle *h, int *compact, int64_t *entries, int64_t *fluid);
+
+/* The library's fluid-node indexing: the lattice index x + nx (y + ny z) of
+ * every fluid node in the order of its storage entries, read back from the
+ * device's row table and link words (compact) or node flags (dense).  Up to
+ * max indices go to nodes (host); *count receives the number of fluid nodes.
+ * Synchronises. */
+int rbc_fluid_nodes(rbc_handle *h, int64_t *nodes, int64_t max, int64_t *count);
 
 /* Size of the static device scratch of rbc_neighbors_noalloc, in ints
  * (4 MiB). */

@@ -1351,6 +1351,20 @@ void orc_budget(const orc_state *s, double *out)
     out[7] = W;
 }
 
+/* Fluid nodes in canonical lattice order: n = x + nx (y + ny z) ascending,
+ * i.e. z-major, then y, then x (the indexing a sparse store of the fluid
+ * nodes keeps). */
+long orc_fluid_nodes(const orc_state *s, long *nodes, long max)
+{
+    long k = 0;
+    for (long n = 0; n < s->N; n++) {
+        if (s->solid[n]) continue;
+        if (k < max) nodes[k] = n;
+        k++;
+    }
+    return k;
+}
+
 long orc_neighbor_pairs(const orc_state *s, int *pairs, long max)
 {
     long np = 0;

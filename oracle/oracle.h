@@ -88,6 +88,9 @@ long orc_clamps(const orc_state *s);
 /* Cell pairs i<j with |R_ij|^2 < r_cut^2 at the current positions, by brute
  * force; writes up to max pairs (2 ints each), returns the number found. */
 long orc_neighbor_pairs(const orc_state *s, int *pairs, long max);
+/* Fluid nodes in canonical lattice order (n = x + nx (y + ny z)
+ * ascending); writes up to max, returns the number of fluid nodes. */
+long orc_fluid_nodes(const orc_state *s, long *nodes, long max);
 /* Overwrite the fluid outputs the next step samples (sampling pins). */
 void orc_set_sampled_fields(orc_state *s, const double *u, const double *sigma);
 

@@ -89,6 +89,8 @@ def lib():
         L.orc_neighbor_pairs.restype = ctypes.c_long
         L.orc_neighbor_pairs.argtypes = [ctypes.c_void_p, _I, ctypes.c_long]
         L.orc_set_sampled_fields.argtypes = [ctypes.c_void_p, _D, _D]
+        L.orc_fluid_nodes.restype = ctypes.c_long
+        L.orc_fluid_nodes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_long), ctypes.c_long]
         L.orc_peskin.restype = ctypes.c_double
         L.orc_peskin.argtypes = [ctypes.c_double]
         L.orc_quat_to_Q.argtypes = [_D, _D]
@@ -404,6 +406,12 @@ class Oracle:
         out = np.zeros(8)
         lib().orc_budget(self._h, _dp(out))
         return dict(mass=out[0], p_fluid=out[1:4].copy(), p_cells=out[4:7].copy(), power=out[7])
+
+    def fluid_nodes(self):
+        """Lattice indices of the fluid nodes in canonical order (orc_fluid_nodes)."""
+        out = np.zeros(self.N, dtype=np.int64)
+        n = lib().orc_fluid_nodes(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), self.N)
+        return out[:n].copy()
 
     def neighbor_pairs(self):
         cap = max(16, self.n * 64)

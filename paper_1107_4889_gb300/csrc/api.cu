@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -49,6 +50,11 @@ struct Problem {
     std::vector<int> wall_start, wall_xyz;
     int nw;
     int budget_blocks;
+    // compact layout (Dev in internal.h)
+    bool compact = false;
+    int M = 0;
+    std::vector<int4> rows, batches;
+    int stage_bytes = 0;
 };
 
 struct Carver {
@@ -106,6 +112,126 @@ std::vector<uint8_t> near_solid(const Problem &P, const uint8_t *solid)
     pass(ny, sy);
     pass(nz, sz);
     return a;
+}
+
+inline int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// Row table and batches of the compact layout (Dev in internal.h).
+// fl / fh: x-range of the fluid nodes of every row (y, z).  A row's span is
+// the hull of the fluid ranges of the nine rows (y + dy, z + dz), |dy|,
+// |dz| <= 1, widened by one node -- it holds every node a fluid node of the
+// row or its neighbours reaches through a link -- rounded out to multiples
+// of 8 entries; when that hull wraps around x (a neighbour row has fluid at
+// x = 0 or nx - 1) the span is the whole row.  Batches of the lattice pass:
+// runs of consecutive rows with fluid at one z whose common window (their
+// fluid x-range widened by one, rounded out to 8, or the whole row when it
+// wraps) times the rows fits in a stage of at most stage_cap bytes
+// (node_bytes staged per window entry); a non-wrapping row wider than that
+// is cut along x.  Returns false when a wrapping row does not fit.
+bool build_compact(Problem &P, const uint8_t *solid, int node_bytes)
+{
+    const int nx = P.nx, ny = P.ny, nz = P.nz, nrows = ny * nz;
+    const int full = (nx + 7) / 8 * 8;
+    std::vector<int> fl((size_t)nrows, -1), fh((size_t)nrows, -1);
+    bool any_wrap = false;
+    for (int r = 0; r < nrows; ++r) {
+        const uint8_t *row = solid + (size_t)r * nx;
+        int x = 0;
+        while (x < nx && row[x]) ++x;
+        if (x == nx) continue;
+        fl[r] = x;
+        x = nx - 1;
+        while (row[x]) --x;
+        fh[r] = x;
+        any_wrap |= fl[r] == 0 || fh[r] == nx - 1;
+    }
+    P.rows.assign((size_t)nrows, make_int4(0, 0, 0, 0xFFFF));
+    long long off = 0;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y) {
+            int hlo = nx, hhi = -1;
+            bool wraps = false;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int r2 = wrapi(y + dy, ny) + ny * wrapi(z + dz, nz);
+                    if (fh[r2] < 0) continue;
+                    wraps |= fl[r2] == 0 || fh[r2] == nx - 1;
+                    hlo = std::min(hlo, fl[r2] - 1);
+                    hhi = std::max(hhi, fh[r2] + 1);
+                }
+            int slo = 0, shi = 0;
+            if (hhi >= 0) {
+                slo = wraps ? 0 : hlo / 8 * 8;
+                shi = wraps ? full : (hhi + 1 + 7) / 8 * 8;
+            }
+            const int r = y + ny * z;
+            const int fr = fh[r] >= 0 ? (fl[r] | (fh[r] << 16)) : 0xFFFF;
+            P.rows[r] = make_int4((int)std::min(off, (long long)INT32_MAX), slo, shi, fr);
+            off += shi - slo;
+        }
+    if (off >= (1LL << 31) - 64) return false;
+    P.M = (int)off;
+    // batches
+    const int stage_cap = std::max(24 * 1024, any_wrap ? full * node_bytes : 0);
+    if (stage_cap > 96 * 1024) return false;
+    const int cap = stage_cap / node_bytes;  // window entries per stage
+    auto window = [&](int c0, int c1, int &X0, int &W) {
+        if (c0 == 0 || c1 == nx - 1) {
+            X0 = 0;
+            W = full;
+        } else {
+            X0 = (c0 - 1) / 8 * 8;
+            W = (c1 + 2 + 7) / 8 * 8 - X0;
+        }
+    };
+    auto push = [&](int z, int y0, int nb, int c0, int c1, int X0, int W) {
+        P.batches.push_back(make_int4(z, y0 | (nb << 20), c0 | (c1 << 16), X0 | (W << 16)));
+    };
+    P.batches.clear();
+    int most = 0;
+    for (int z = 0; z < nz; ++z) {
+        int y = 0;
+        while (y < ny) {
+            const int r = y + ny * z;
+            if (fh[r] < 0) {
+                ++y;
+                continue;
+            }
+            int c0 = fl[r], c1 = fh[r], X0, W;
+            window(c0, c1, X0, W);
+            if (W > cap) {
+                const int L = (cap - 16) / 8 * 8;
+                if (c0 == 0 || c1 == nx - 1 || L < 8) return false;
+                for (int a0 = c0; a0 <= c1; a0 += L) {
+                    const int a1 = std::min(c1, a0 + L - 1);
+                    window(a0, a1, X0, W);
+                    push(z, y, 1, a0, a1, X0, W);
+                    most = std::max(most, W);
+                }
+                ++y;
+                continue;
+            }
+            int nb = 1;
+            while (y + nb < ny && nb < 2047) {
+                const int r2 = y + nb + ny * z;
+                if (fh[r2] < 0) break;
+                const int d0 = std::min(c0, fl[r2]), d1 = std::max(c1, fh[r2]);
+                int X0b, Wb;
+                window(d0, d1, X0b, Wb);
+                if ((nb + 1) * Wb > cap) break;
+                c0 = d0;
+                c1 = d1;
+                X0 = X0b;
+                W = Wb;
+                ++nb;
+            }
+            push(z, y, nb, c0, c1, X0, W);
+            most = std::max(most, nb * W);
+            y += nb;
+        }
+    }
+    P.stage_bytes = (most * node_bytes + 127) / 128 * 128;
+    return true;
 }
 
 int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Problem &P, std::string *err)
@@ -179,6 +305,8 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     if (q.rounding != RBC_ROUND_STOCHASTIC && q.rounding != RBC_ROUND_NEAREST)
         return fail(err, RBC_EINVAL, "rounding must be RBC_ROUND_STOCHASTIC or RBC_ROUND_NEAREST");
     if (q.node_list < -1 || q.node_list > 1) return fail(err, RBC_EINVAL, "node_list must be -1, 0 or 1");
+    if (q.layout < RBC_LAYOUT_AUTO || q.layout > RBC_LAYOUT_COMPACT)
+        return fail(err, RBC_EINVAL, "layout must be RBC_LAYOUT_AUTO, RBC_LAYOUT_DENSE or RBC_LAYOUT_COMPACT");
     P.use_list = q.node_list == 1 || (q.node_list == 0 && 2LL * P.nfluid < N);
     P.prec = q.precision;
     P.stochastic = q.rounding == RBC_ROUND_STOCHASTIC ? 1 : 0;
@@ -336,6 +464,27 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
                 }
     }
     P.budget_blocks = budget_blocks_for(P.N);
+    // storage layout
+    P.compact = false;
+    P.rows.clear();
+    P.batches.clear();
+    if (q.layout != RBC_LAYOUT_DENSE && P.any_solid && P.nx <= 32760 && P.ny < (1 << 20)) {
+        const int node_bytes = kQ * pop_bytes(P.prec) + (nc > 0 ? 16 : 0) + 4;
+        const bool ok = build_compact(P, g->solid, node_bytes);
+        if (ok && (q.layout == RBC_LAYOUT_COMPACT || (long long)P.M * 10 <= (long long)N * 9)) {
+            P.compact = true;
+            P.use_list = false;
+            P.need_links = true;
+            P.Np = ((long long)P.M + 1 + 63) / 64 * 64;
+        }
+        if (!P.compact) {
+            P.rows.clear();
+            P.batches.clear();
+        }
+    }
+    if (q.layout == RBC_LAYOUT_COMPACT && !P.compact)
+        return fail(err, RBC_EINVAL, "the compact layout needs solid nodes, nx <= 32760 and rows that fit a stage");
+    if (19LL * P.Np >= (1LL << 32)) return fail(err, RBC_EINVAL, "lattice too large (19 * entries must stay below 2^32)");
     return RBC_OK;
 }
 
@@ -359,10 +508,18 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.S = P.want_sigma ? cv.take<float4>(2 * Np) : nullptr;
     d.G = P.nc > 0 ? cv.take<float4>(Np) : nullptr;
     d.rho = cv.take<float>(Np);
-    d.solid = P.any_solid ? cv.take<uint8_t>(Np) : nullptr;
+    // node flags stay dense (the shape lists test every node of a cell's box)
+    d.solid = P.any_solid ? cv.take<uint8_t>(((size_t)P.N + 63) / 64 * 64) : nullptr;
     d.links = P.need_links ? cv.take<uint32_t>(Np) : nullptr;
     d.nfluid = P.nfluid;
     d.fluid_list = P.use_list ? cv.take<uint32_t>((size_t)std::max(P.nfluid, 1)) : nullptr;
+    d.compact = P.compact ? 1 : 0;
+    d.M = P.compact ? P.M : P.N;
+    d.zero_entry = P.compact ? P.M : 0;
+    d.rows = P.compact ? cv.take<int4>((size_t)P.ny * P.nz) : nullptr;
+    d.nbatches = P.compact ? (int)P.batches.size() : 0;
+    d.lb_batches = P.compact ? cv.take<int4>((size_t)std::max(d.nbatches, 1)) : nullptr;
+    d.lb_stage_bytes = P.compact ? P.stage_bytes : 0;
     d.nwss = P.nwss;
     d.wss_node = cv.take<int>((size_t)std::max(P.nwss, 1));
     d.wss_n = cv.take<float>(3 * (size_t)std::max(P.nwss, 1));
@@ -467,6 +624,7 @@ struct rbc_handle {
     std::string err;
     int device = 0;
     std::vector<uint8_t> solid_host;
+    std::vector<long long> wss_dense;  // compact layout: lattice index of every wall-shear node
 };
 
 #define RBC_CU(call)                                                                                \
@@ -711,14 +869,51 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
         if (d.G) RBC_CU(cudaMemsetAsync(d.G, 0, Np * sizeof(float4), s));
         RBC_CU(cudaMemsetAsync(d.rho, 0, Np * sizeof(float), s));
         std::vector<uint32_t> links;
-        if (d.solid) {
-            RBC_CU(cudaMemsetAsync(d.solid, 0, Np, s));
-            RBC_CU(cudaMemcpyAsync(d.solid, geom->solid, (size_t)P.N, cudaMemcpyHostToDevice, s));
-        }
+        if (d.solid) RBC_CU(cudaMemcpyAsync(d.solid, geom->solid, (size_t)P.N, cudaMemcpyHostToDevice, s));
         std::vector<uint32_t> flist;
         std::vector<int> wnode;
         std::vector<float> wnrm;
-        if (d.links) {
+        if (d.compact) {
+            // link words of the stored entries (bit 31: solid node, or an
+            // entry past the end of a whole row); wall-shear nodes in
+            // storage order with their lattice indices kept on the host
+            links.assign(Np, 1u << 31);
+            const std::vector<uint8_t> near = near_solid(P, geom->solid);
+            for (int z = 0; z < P.nz; ++z)
+                for (int y = 0; y < P.ny; ++y) {
+                    const int4 rt = P.rows[(size_t)y + (size_t)P.ny * z];
+                    const long long row = (long long)P.nx * ((long long)y + (long long)P.ny * z);
+                    for (int x = rt.y; x < std::min(rt.z, P.nx); ++x) {
+                        const long long n = row + x;
+                        const size_t c = (size_t)rt.x + (size_t)(x - rt.y);
+                        if (geom->solid[n]) continue;
+                        uint32_t m = 0u;
+                        float nv[3] = {0.f, 0.f, 0.f};
+                        if (near[n])
+                            for (int p = 1; p < kQ; ++p)
+                                if (geom->solid[node(P, x + cx(p), y + cy(p), z + cz(p))]) {
+                                    m |= 1u << p;
+                                    nv[0] -= (float)cx(p);
+                                    nv[1] -= (float)cy(p);
+                                    nv[2] -= (float)cz(p);
+                                }
+                        if (geom->node_type && geom->node_type[n] == RBC_NODE_INLET) m |= 1u << 29;
+                        if (geom->node_type && geom->node_type[n] == RBC_NODE_OUTLET) m |= 1u << 30;
+                        links[c] = m;
+                        if ((m & 0x7FFFEu) && P.nwss > 0) {
+                            const float nn = std::sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+                            wnode.push_back((int)c);
+                            h->wss_dense.push_back(n);
+                            for (int a = 0; a < 3; ++a) wnrm.push_back(nn > 0.f ? nv[a] / nn : 0.f);
+                        }
+                    }
+                }
+            RBC_CU(cudaMemcpyAsync(d.links, links.data(), links.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+            RBC_CU(cudaMemcpyAsync(const_cast<int4 *>(d.rows), P.rows.data(), P.rows.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, s));
+            RBC_CU(cudaMemcpyAsync(const_cast<int4 *>(d.lb_batches), P.batches.data(), P.batches.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, s));
+        } else if (d.links) {
             // per-node link word in the library's velocity ordering: bit p set
             // when the downstream node x + c_p is solid (fluid nodes), bit 29 /
             // 30 for inlet / outlet nodes, bit 31 when x is solid
@@ -890,22 +1085,43 @@ int rbc_fields(rbc_handle *h, double *rho, double *u, double *cells_state)
     const Dev &d = h->d;
     const size_t N = (size_t)d.N, Np = (size_t)d.Np;
     const int par = (int)(h->step & 1);
+    const uint8_t *solid = h->P.any_solid ? h->solid_host.data() : nullptr;
+    // storage entry of lattice node k, or -1 for a solid node (compact:
+    // nodes outside every row's span are solid)
+    std::vector<long long> ent;
+    if (d.compact) {
+        ent.assign(N, -1);
+        for (size_t r = 0; r < h->P.rows.size(); ++r) {
+            const int4 rt = h->P.rows[r];
+            for (int x = rt.y; x < std::min(rt.z, d.nx); ++x) {
+                const size_t k = (size_t)d.nx * r + (size_t)x;
+                if (!solid[k]) ent[k] = (long long)rt.x + (x - rt.y);
+            }
+        }
+    }
     if (rho) {
         launch_rho(d, par, h->stream);
-        std::vector<float> r(N);
-        RBC_CU(cudaMemcpyAsync(r.data(), d.rho, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        const size_t nr = d.compact ? (size_t)d.M : N;
+        std::vector<float> r(nr);
+        RBC_CU(cudaMemcpyAsync(r.data(), d.rho, nr * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
         RBC_CU(cudaStreamSynchronize(h->stream));
-        const uint8_t *solid = h->P.any_solid ? h->solid_host.data() : nullptr;
-        for (size_t k = 0; k < N; ++k) rho[k] = (solid && solid[k]) ? 0.0 : 1.0 + (double)r[k];
+        for (size_t k = 0; k < N; ++k) {
+            if (d.compact)
+                rho[k] = ent[k] < 0 ? 0.0 : 1.0 + (double)r[(size_t)ent[k]];
+            else
+                rho[k] = (solid && solid[k]) ? 0.0 : 1.0 + (double)r[k];
+        }
     }
     if (u) {
         std::vector<float4> U(Np);
         RBC_CU(cudaMemcpyAsync(U.data(), d.U, Np * sizeof(float4), cudaMemcpyDeviceToHost, h->stream));
         RBC_CU(cudaStreamSynchronize(h->stream));
         for (size_t k = 0; k < N; ++k) {
-            u[3 * k] = U[k].x;
-            u[3 * k + 1] = U[k].y;
-            u[3 * k + 2] = U[k].z;
+            const long long e = d.compact ? ent[k] : (long long)k;
+            const float4 v = e < 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : U[(size_t)e];
+            u[3 * k] = v.x;
+            u[3 * k + 1] = v.y;
+            u[3 * k + 2] = v.z;
         }
     }
     if (cells_state && d.nc > 0) {
@@ -1187,7 +1403,7 @@ int rbc_wss(rbc_handle *h, int64_t *node, double *tau, int64_t max, int64_t *n, 
     const double inv = h->wss_samples > 0 ? 1.0 / (double)h->wss_samples : 0.0;
     const size_t k = std::min(nw, (size_t)std::max<int64_t>(max, 0));
     for (size_t i = 0; i < k; ++i) {
-        node[i] = idx[i];
+        node[i] = h->d.compact ? h->wss_dense[i] : idx[i];
         for (int a = 0; a < 3; ++a) tau[3 * i + a] = acc[3 * i + a] * inv;
     }
     *n = (int64_t)nw;
@@ -1199,6 +1415,55 @@ int rbc_launches_per_step(const rbc_handle *h)
 {
     if (!h) return 0;
     return 1 + (h->d.nc > 0 ? 4 : 0);  // cells, bin, gb, weights; the bin-count clear is a memset node
+}
+
+int rbc_layout(const rbc_handle *h, int *compact, int64_t *entries, int64_t *fluid)
+{
+    if (!h) return fail(nullptr, RBC_EINVAL, "handle is NULL");
+    if (compact) *compact = h->d.compact;
+    if (entries) *entries = h->d.compact ? h->d.M : h->d.N;
+    if (fluid) *fluid = h->P.nfluid;
+    return RBC_OK;
+}
+
+int rbc_fluid_nodes(rbc_handle *h, int64_t *nodes, int64_t max, int64_t *count)
+{
+    if (!h || !count || (max > 0 && !nodes)) return fail(h ? &h->err : nullptr, RBC_EINVAL, "NULL argument");
+    const Dev &d = h->d;
+    int64_t k = 0;
+    auto put = [&](int64_t n) {
+        if (k < max) nodes[k] = n;
+        ++k;
+    };
+    if (d.compact) {
+        // walk the device's own row table and link words in storage order
+        std::vector<int4> rows((size_t)d.ny * d.nz);
+        std::vector<uint32_t> links((size_t)d.M);
+        RBC_CU(cudaMemcpyAsync(rows.data(), d.rows, rows.size() * sizeof(int4), cudaMemcpyDeviceToHost, h->stream));
+        RBC_CU(cudaMemcpyAsync(links.data(), d.links, links.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                               h->stream));
+        RBC_CU(cudaStreamSynchronize(h->stream));
+        std::vector<std::pair<int64_t, int64_t>> order;  // (entry, node) of the fluid entries
+        for (size_t r = 0; r < rows.size(); ++r)
+            for (int x = rows[r].y; x < rows[r].z; ++x) {
+                const int64_t c = (int64_t)rows[r].x + (x - rows[r].y);
+                if (c < 0 || c >= d.M) return fail(&h->err, RBC_EINVAL, "row table outside the storage");
+                if (x < d.nx && !(links[(size_t)c] >> 31)) order.emplace_back(c, (int64_t)d.nx * (int64_t)r + x);
+            }
+        std::sort(order.begin(), order.end());
+        for (const auto &e : order) put(e.second);
+    } else if (d.links) {
+        std::vector<uint32_t> links((size_t)d.N);
+        RBC_CU(cudaMemcpyAsync(links.data(), d.links, links.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                               h->stream));
+        RBC_CU(cudaStreamSynchronize(h->stream));
+        for (int64_t n = 0; n < d.N; ++n)
+            if (!(links[(size_t)n] >> 31)) put(n);
+    } else {
+        for (int64_t n = 0; n < d.N; ++n) put(n);
+    }
+    *count = k;
+    return RBC_OK;
 }
 
 void rbc_free(rbc_handle *h)

@@ -485,6 +485,8 @@ struct ShapeArgs {
     int kappa_i;  // kappa when it is a whole number 1..64 (integer power), else 0
     int box_dim, sup_cap;
     int box_pad;  // shared words per warp of k_weights (weights_words)
+    const int4 *rows;  // compact layout: row table (offset, s_lo, s_hi, fluid range); null when dense
+    int zero_entry;    // compact layout: the entry nothing writes (u = sigma = 0)
 };
 
 // ---------------------------------------------------------------------------
@@ -711,14 +713,26 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
         const unsigned own = srow[r];
         const unsigned ym = i1 > 0 ? srow[r - 1] : 0xFFu, yp = i1 + 1 < n1 ? srow[r + 1] : 0xFFu;
         const unsigned zm = i2 > 0 ? srow[r - n1] : 0xFFu, zp = i2 + 1 < n2 ? srow[r + n1] : 0xFFu;
-        const int rowbase = a.nx * (wrap1(o[1] + i1, a.ny) + a.ny * wrap1(o[2] + i2, a.nz));
+        // storage entry of column xw of this lattice row: dense, the node
+        // index; compact, the row's offset + xw - s_lo inside the row's span
+        // (every visited node is there: it lies within one node of a fluid
+        // support node), the zero entry otherwise
+        const int lrow = wrap1(o[1] + i1, a.ny) + a.ny * wrap1(o[2] + i2, a.nz);
+        int ebase = a.nx * lrow, elo = 0, ehi = a.nx;
+        if (a.rows) {
+            const int4 rt = a.rows[lrow];
+            ebase = rt.x - rt.y;
+            elo = rt.y;
+            ehi = rt.z;
+        }
         const int pkr = (i1 << 10) | (i2 << 20);
         int pos = (int)(vw >> 16);
         float wl = W(own, vlo - 1), wm = W(own, vlo);
         for (int x = vlo; x <= vhi; ++x, ++pos) {
             const float wr = W(own, x + 1);
             if (pos < a.sp_cap) {
-                sp_idx[pos] = make_int2(wrap1(o[0] + x, a.nx) + rowbase, x | pkr);
+                const int xw = wrap1(o[0] + x, a.nx);
+                sp_idx[pos] = make_int2(xw >= elo && xw < ehi ? ebase + xw : a.zero_entry, x | pkr);
                 sp_val[pos] = make_float4(wm, 0.5f * (wr - wl), 0.5f * (W(yp, x) - W(ym, x)),
                                           0.5f * (W(zp, x) - W(zm, x)));
             }
@@ -735,7 +749,12 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
             hi_[12 + ax] = o[ax];
             hi_[15 + ax] = nn[ax];
         }
-        hi_[18] = cc[0] + a.nx * (cc[1] + a.ny * cc[2]);
+        int centre = cc[0] + a.nx * (cc[1] + a.ny * cc[2]);
+        if (a.rows) {
+            const int4 rt = a.rows[cc[1] + a.ny * cc[2]];
+            centre = cc[0] >= rt.y && cc[0] < rt.z ? rt.x + cc[0] - rt.y : a.zero_entry;
+        }
+        hi_[18] = centre;
         hi_[19] = 1;
         a.sp_cnt[i] = min(run, a.sp_cap);
         a.sp_S[i] = part;
@@ -1190,6 +1209,8 @@ ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
     a.kappa = p.kappa;
     a.kappa_i = (p.kappa >= 1.0f && p.kappa <= 64.0f && p.kappa == floorf(p.kappa)) ? (int)p.kappa : 0;
     a.alpha = p.alpha;
+    a.rows = d.compact ? d.rows : nullptr;
+    a.zero_entry = d.zero_entry;
     return a;
 }
 

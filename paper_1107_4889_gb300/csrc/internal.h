@@ -45,6 +45,21 @@ struct Dev {
                         // bit 30 = outlet node, bit 31 = node is solid
     uint32_t *fluid_list;  // node-list pass: the fluid nodes in lattice order, or null
     int nfluid;
+    // Compact layout (walled lattices with solid rows or row segments).  Only
+    // the entries of each lattice row (y, z) that a fluid node can reach
+    // through a link are stored: the row's span [s_lo, s_hi) of x, the hull
+    // of the fluid nodes of the nine rows (y + dy, z + dz) widened by one
+    // node, rounded out to multiples of 8, or the whole row when that hull
+    // wraps around x.  rows[y + ny z] = (offset of the row's first entry,
+    // s_lo, s_hi, fluid x-range lo | hi << 16; lo > hi for a row without
+    // fluid).  Every field array then holds M entries in lattice order plus
+    // one entry `zero_entry` = M that nothing writes (a node without storage
+    // reads u = 0 there).  Dense layout: entry = lattice node, rows null.
+    int compact;
+    int M, zero_entry;
+    const int4 *rows;
+    const int4 *lb_batches;  // compact lattice pass: (z, y0 | nb << 20, C0 | C1 << 16, X0 | W << 16)
+    int nbatches;
     // wall shear stress: wall-adjacent fluid nodes, unit normals into the
     // fluid (3 floats each), time sums of the tangential traction
     int nwss;
@@ -94,6 +109,7 @@ struct Dev {
     int side_prio;  // launch priority of the side-stream kernels (the device's highest)
     int wt_grid = 0, gb_grid = 0;  // blocks of the shape-list and Gay-Berne launches (0: one per group)
     size_t lb_smem;
+    int lb_stage_bytes;  // compact lattice pass: bytes of one stage (its largest batch)
 };
 
 struct Params {

@@ -40,6 +40,7 @@ struct LbArgs {
     const void *src;  // populations of the previous pass (storage type St)
     void *dst;
     const uint32_t *links;
+    const int4 *rows;  // compact layout: row table (internal.h), else null
     float4 *G, *U, *S;  // node-major: force density + hematocrit sum, velocity, stress (2 per node)
     int *flags;
     int *work;                 // [0] next batch, [1] CTAs done; zero at launch, reset by the last CTA
@@ -53,6 +54,20 @@ struct LbArgs {
     uint32_t key0, key1;  // seed of the stochastic rounding
     int stochastic;
 };
+
+// Storage entry of the lattice node (x, y, z) (wrapped coordinates): the node
+// itself in the dense layout; in the compact layout the offset of its row
+// plus x - s_lo.  Only nodes inside a row's span are ever addressed: the
+// fluid nodes, and the nodes a fluid node reaches through one link.
+template <bool COMPACT>
+__device__ __forceinline__ uint32_t entry_of(const LbArgs &a, int x, int y, int z)
+{
+    if (COMPACT) {
+        const int4 rt = a.rows[y + a.ny * z];
+        return (uint32_t)(rt.x + x - rt.y);
+    }
+    return (uint32_t)x + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
+}
 
 // ---------------------------------------------------------------------------
 // Population storage.  FP32 keeps d_p itself.  The 16-bit formats keep
@@ -192,9 +207,11 @@ __device__ __forceinline__ void for_speeds(F &&f)
 // of that direction, from which this node pulls.  Each (slot, solid node)
 // pair has exactly one writer; opposite speeds share a weight, so the stored
 // value is copied as it is.
-template <typename St, bool WALLS, bool CELLS, bool SIGMA>
+// n is the node's storage entry; nd its lattice index (x + nx (y + ny z)),
+// which keys the rounding's random numbers in either layout.
+template <typename St, bool WALLS, bool CELLS, bool SIGMA, bool COMPACT = false>
 __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], uint32_t lk, float gx, float gy,
-                                             float gz, float T, uint32_t n, int x, int y, int z,
+                                             float gz, float T, uint32_t n, uint32_t nd, int x, int y, int z,
                                              unsigned long long step)
 {
     // element offsets fit 32 bits: the host keeps 19 Np below 2^32
@@ -221,7 +238,7 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
     const float gu = gx * ux + gy * uy + gz * uz;
     const bool sr = Pop<St>::kRounds && a.stochastic != 0;
     uint4 rb = make_uint4(0u, 0u, 0u, 0u);
-    if (sr) rb = philox4x32_10(make_uint4(n, (uint32_t)step, (uint32_t)(step >> 32), 0u), a.key0, a.key1);
+    if (sr) rb = philox4x32_10(make_uint4(nd, (uint32_t)step, (uint32_t)(step >> 32), 0u), a.key0, a.key1);
     // A speed p and its opposite q share |c.u|, |c.G| and the weight, so
     //   d_eq(p, q) = A +- B,  A = w [drho + rho (4.5 (c.u)^2 - 1.5 u^2)],
     //                         B = 3 w rho c.u,
@@ -267,13 +284,12 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
     }
     if (!(rho > 0.0f) || !(usq <= a.mach2)) atomicOr(&a.flags[FLAG_UNSTABLE], 1);
     if (WALLS && (lk & 0x7FFFEu)) {  // nodes next to a wall only
-        const int nxy = a.nx * a.ny;
 #pragma unroll 1
         for (int p = 1; p < kQ; ++p) {
             if (!((lk >> p) & 1u)) continue;
             const int xd = wrapm(x + cx(p), a.nx), yd = wrapm(y + cy(p), a.ny), zd = wrapm(z + cz(p), a.nz);
             // read back this thread's own store of d*_p
-            dst[(uint32_t)kOppTab[p] * Np + (uint32_t)(xd + a.nx * yd + nxy * zd)] = dst[(uint32_t)p * Np + n];
+            dst[(uint32_t)kOppTab[p] * Np + entry_of<COMPACT>(a, xd, yd, zd)] = dst[(uint32_t)p * Np + n];
         }
     }
 }
@@ -294,6 +310,8 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
 // straight across if fluid, else the first fluid one of the links
 // (-1, 0, dz), (+1, 0, dz), (0, -1, dz), (0, +1, dz) (a tilted vessel meets
 // the plane obliquely); -1 if none is.  lk holds the node's solid links.
+// The result is the neighbour's storage entry.
+template <bool COMPACT>
 __device__ __forceinline__ long long bc_neighbour(const LbArgs &a, int x, int y, int z, int dz, uint32_t lk)
 {
     const int off[5][2] = {{0, 0}, {-1, 0}, {1, 0}, {0, -1}, {0, 1}};
@@ -302,22 +320,22 @@ __device__ __forceinline__ long long bc_neighbour(const LbArgs &a, int x, int y,
         for (int q = 1; q < kQ; ++q)
             if (cx(q) == off[k][0] && cy(q) == off[k][1] && cz(q) == dz) p = q;
         if (p < 0 || ((lk >> p) & 1u)) continue;
-        return (long long)wrapm(x + off[k][0], a.nx) +
-               (long long)a.nx * (wrapm(y + off[k][1], a.ny) + (long long)a.ny * wrapm(z + dz, a.nz));
+        return (long long)entry_of<COMPACT>(a, wrapm(x + off[k][0], a.nx), wrapm(y + off[k][1], a.ny),
+                                            wrapm(z + dz, a.nz));
     }
     return -1;
 }
 
-template <typename St, bool CELLS, bool SIGMA>
-__device__ __noinline__ void boundary_node(const LbArgs &a, uint32_t n, int x, int y, int z, uint32_t lk,
-                                           unsigned long long step)
+template <typename St, bool CELLS, bool SIGMA, bool COMPACT = false>
+__device__ __noinline__ void boundary_node(const LbArgs &a, uint32_t n, uint32_t nd, int x, int y, int z,
+                                           uint32_t lk, unsigned long long step)
 {
     const uint32_t Np = (uint32_t)a.Np;
     const St *src = static_cast<const St *>(a.src);
     St *dst = static_cast<St *>(a.dst);
     float d[kQ];
     if (lk & (1u << 29)) {
-        const long long dl = bc_neighbour(a, x, y, z, 1, lk);
+        const long long dl = bc_neighbour<COMPACT>(a, x, y, z, 1, lk);
         const uint32_t dn = (uint32_t)(dl < 0 ? 0 : dl);
         float drho = 0.f;
         if (dl >= 0)
@@ -335,7 +353,7 @@ __device__ __noinline__ void boundary_node(const LbArgs &a, uint32_t n, int x, i
             d[p] = wq(p) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uz * uz));
         });
     } else {
-        const long long ml = bc_neighbour(a, x, y, z, -1, lk);
+        const long long ml = bc_neighbour<COMPACT>(a, x, y, z, -1, lk);
         const uint32_t m = (uint32_t)(ml < 0 ? 0 : ml);
         float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
         for_speeds<0, kQ>([&](auto pc) {
@@ -356,7 +374,7 @@ __device__ __noinline__ void boundary_node(const LbArgs &a, uint32_t n, int x, i
     }
     const bool sr = Pop<St>::kRounds && a.stochastic != 0;
     uint4 rb = make_uint4(0u, 0u, 0u, 0u);
-    if (sr) rb = philox4x32_10(make_uint4(n, (uint32_t)step, (uint32_t)(step >> 32), 0u), a.key0, a.key1);
+    if (sr) rb = philox4x32_10(make_uint4(nd, (uint32_t)step, (uint32_t)(step >> 32), 0u), a.key0, a.key1);
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
     for_speeds<0, kQ>([&](auto pc) {
         constexpr int p = decltype(pc)::value;
@@ -426,10 +444,10 @@ __device__ __forceinline__ void lb_node(const LbArgs &a, int n, unsigned long lo
     }
     if (WALLS && (lk >> 31)) return;  // solid node: nothing to collide
     if (WALLS && (lk & 0x60000000u)) {
-        boundary_node<St, CELLS, SIGMA>(a, (uint32_t)n, x, y, z, lk, step);
+        boundary_node<St, CELLS, SIGMA>(a, (uint32_t)n, (uint32_t)n, x, y, z, lk, step);
         return;
     }
-    collide_node<St, WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, (uint32_t)n, x, y, z, step);
+    collide_node<St, WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, (uint32_t)n, (uint32_t)n, x, y, z, step);
 }
 
 template <typename St, bool WALLS, bool CELLS, bool SIGMA>
@@ -655,7 +673,7 @@ __device__ __forceinline__ void consume_batch(const LbArgs &a, const StageLayout
             WALLS ? reinterpret_cast<const uint32_t *>(frow)[(size_t)(CELLS ? 4 : 0) * plane_stride + xx] : 0u;
         if (WALLS && (lk >> 31)) continue;
         if (WALLS && (lk & 0x60000000u)) {
-            boundary_node<St, CELLS, SIGMA>(a, n, xx, y, z, lk, step);
+            boundary_node<St, CELLS, SIGMA>(a, n, n, xx, y, z, lk, step);
             continue;
         }
         const int xm = xx == 0 ? nx - 1 : xx - 1, xp = xx == nx - 1 ? 0 : xx + 1;
@@ -674,7 +692,7 @@ __device__ __forceinline__ void consume_batch(const LbArgs &a, const StageLayout
             gz += g4.z;
             T += a.delta * g4.w;
         }
-        collide_node<St, WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, n, xx, y, z, step);
+        collide_node<St, WALLS, CELLS, SIGMA>(a, d, lk, gx, gy, gz, T, n, n, xx, y, z, step);
     }
 }
 
@@ -762,6 +780,227 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
                                                b_first, x_step, b_step);
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&empty[stage]));  // this warp is done with the stage
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Compact lattice pass (walled lattices in the compact layout).  The same
+// persistent producer / consumer pipeline as the row-staged pass, over a
+// table of batches built at set-up: a batch is nb consecutive rows
+// y0 .. y0 + nb - 1 at one z that all hold fluid, the x-range [C0, C1] of
+// their fluid nodes (the union of the rows' ranges; a row wider than a stage
+// is cut into several batches), and the staged window [X0, X0 + W) =
+// [C0 - 1, C1 + 1] rounded out to multiples of 8 entries (the whole row when
+// the row wraps along x).  Rows without fluid are never visited: their
+// entries are only the targets of the bounce-back writes of their fluid
+// neighbours.  For every speed p the producer copies, per batch row, the
+// part of the upstream row (y - c_y, z - c_z) that lies in both the window
+// and that row's span (one bulk copy each; span and window ends are
+// multiples of 8 entries, so every copy starts and ends on a 16-byte
+// boundary), plus the batch rows' own G / theta and link words.  Stage
+// layout: [19][nb][W] populations, [nb][W] float4 G, [nb][W] link words;
+// window column x sits at x - X0.  The consumers collide the fluid nodes of
+// [C0, C1] x rows; a node pulls only from upstream entries inside the
+// upstream row's span (every node one link away from a fluid node is
+// stored), so the parts of the window outside a span are never read.
+// ---------------------------------------------------------------------------
+template <typename St, bool CELLS>
+__device__ __forceinline__ uint32_t compact_copy(const LbArgs &a, int4 bd, int j, unsigned char *base,
+                                                 const void *&gsrc, uint32_t &sdst)
+{
+    const int z = bd.x, y0 = bd.y & 0xFFFFF, nb = (int)((uint32_t)bd.y >> 20);
+    const int X0 = bd.w & 0xFFFF, W = (int)((uint32_t)bd.w >> 16);
+    const int k = j / nb, b = j - k * nb;
+    int r;
+    size_t esz;
+    const char *g;
+    unsigned char *sb;
+    const size_t pop_bytes = (size_t)kQ * nb * W * sizeof(St);
+    if (k < kQ) {
+        r = wrapm(y0 + b - cy(k), a.ny) + a.ny * wrapm(z - cz(k), a.nz);
+        esz = sizeof(St);
+        g = static_cast<const char *>(a.src) + (size_t)k * (size_t)a.Np * sizeof(St);
+        sb = base + (size_t)(k * nb + b) * W * sizeof(St);
+    } else if (CELLS && k == kQ) {
+        r = y0 + b + a.ny * z;
+        esz = sizeof(float4);
+        g = reinterpret_cast<const char *>(a.G);
+        sb = base + pop_bytes + (size_t)b * W * sizeof(float4);
+    } else {
+        r = y0 + b + a.ny * z;
+        esz = sizeof(uint32_t);
+        g = reinterpret_cast<const char *>(a.links);
+        sb = base + pop_bytes + (CELLS ? (size_t)nb * W * sizeof(float4) : 0) + (size_t)b * W * sizeof(uint32_t);
+    }
+    const int4 rt = a.rows[r];
+    const int lo = max(X0, rt.y), hi = min(X0 + W, rt.z);
+    if (hi <= lo) return 0u;
+    gsrc = g + (size_t)(rt.x + lo - rt.y) * esz;
+    sdst = smem_addr(sb + (size_t)(lo - X0) * esz);
+    return (uint32_t)((size_t)(hi - lo) * esz);
+}
+
+template <typename St, bool CELLS>
+__device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, unsigned char *base, uint32_t bar, int lane)
+{
+    const int nb = (int)((uint32_t)bd.y >> 20);
+    const int ncopies = (kQ + (CELLS ? 1 : 0) + 1) * nb;
+    uint32_t bytes = 0;
+    for (int j = lane; j < ncopies; j += 32) {
+        const void *g;
+        uint32_t sd;
+        bytes += compact_copy<St, CELLS>(a, bd, j, base, g, sd);
+    }
+    bytes = __reduce_add_sync(0xffffffffu, bytes);
+    if (lane == 0) mbar_expect_tx(bar, bytes);
+    __syncwarp();
+    const uint64_t once = l2_evict_first();
+    for (int j = lane; j < ncopies; j += 32) {
+        const void *g = nullptr;
+        uint32_t sd = 0;
+        const uint32_t nbytes = compact_copy<St, CELLS>(a, bd, j, base, g, sd);
+        if (nbytes == 0) continue;
+        if (j < kQ * nb)
+            bulk_g2s_hint(sd, g, nbytes, bar, once);
+        else
+            bulk_g2s(sd, g, nbytes, bar);
+    }
+}
+
+template <typename St, bool CELLS, bool SIGMA>
+__device__ __forceinline__ void consume_compact(const LbArgs &a, int4 bd, const unsigned char *base,
+                                                unsigned long long step)
+{
+    const int nx = a.nx, ny = a.ny;
+    const int z = bd.x, y0 = bd.y & 0xFFFFF, nb = (int)((uint32_t)bd.y >> 20);
+    const int C0 = bd.z & 0xFFFF, C1 = (int)((uint32_t)bd.z >> 16);
+    const int X0 = bd.w & 0xFFFF, W = (int)((uint32_t)bd.w >> 16);
+    const int Wc = C1 - C0 + 1, total = nb * Wc;
+    const size_t pop_bytes = (size_t)kQ * nb * W * sizeof(St);
+    const St *pst = reinterpret_cast<const St *>(base);
+    const float4 *gst = reinterpret_cast<const float4 *>(base + pop_bytes);
+    const uint32_t *lst =
+        reinterpret_cast<const uint32_t *>(base + pop_bytes + (CELLS ? (size_t)nb * W * sizeof(float4) : 0));
+    const int t = (int)threadIdx.x;
+    const int db = kStConsumers / Wc, dx = kStConsumers - db * Wc;
+    int b = t / Wc, xo = t - b * Wc;
+    for (int l = t; l < total; l += kStConsumers) {
+        const int bb = b, x = C0 + xo;
+        xo += dx;
+        b += db;
+        if (xo >= Wc) {
+            xo -= Wc;
+            ++b;
+        }
+        const int y = y0 + bb;
+        const int4 rt = a.rows[y + ny * z];
+        if (x < (rt.w & 0xFFFF) || x > (int)((uint32_t)rt.w >> 16)) continue;
+        const int sx = bb * W + x - X0;
+        const uint32_t lk = lst[sx];
+        if (lk >> 31) continue;
+        const uint32_t n = (uint32_t)(rt.x + x - rt.y);
+        const uint32_t nd = (uint32_t)x + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
+        if (lk & 0x60000000u) {
+            boundary_node<St, CELLS, SIGMA, true>(a, n, nd, x, y, z, lk, step);
+            continue;
+        }
+        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        float d[kQ];
+        for_speeds<0, kQ>([&](auto pc) {
+            constexpr int p = decltype(pc)::value;
+            const int xs = cx(p) == 0 ? x : (cx(p) > 0 ? xm : xp);
+            d[p] = Pop<St>::template get<p>(pst[(p * nb + bb) * W + xs - X0]);
+        });
+        float gx, gy, gz, T = a.tau0;
+        external_force(a, y, gx, gy, gz);
+        if (CELLS) {
+            const float4 g4 = gst[sx];
+            gx += g4.x;
+            gy += g4.y;
+            gz += g4.z;
+            T += a.delta * g4.w;
+        }
+        collide_node<St, true, CELLS, SIGMA, true>(a, d, lk, gx, gy, gz, T, n, nd, x, y, z, step);
+    }
+}
+
+// at least two CTAs per SM: the pass and the side kernels share the SMs
+template <typename St, bool CELLS, bool SIGMA>
+__global__ void __launch_bounds__(kStThreads, 2)
+    k_lb_compact(LbArgs a, const int4 *__restrict__ batches, int nbatches, int ns, int stage_bytes)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages];
+    __shared__ int4 s_desc[kMaxStages];
+    __shared__ unsigned long long s_step;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < ns; ++k) {
+            mbar_init(smem_addr(&full[k]), 1);
+            mbar_init(smem_addr(&empty[k]), kStConsumers / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_step = *a.step;
+    }
+    __syncthreads();
+
+    if (threadIdx.x >= kStConsumers) {
+        // producer warp: claims batches from the global counter (see
+        // k_lb_staged); s_desc[stage].x = -1 tells the consumers to stop
+        const int lane = threadIdx.x - kStConsumers;
+        int it = 0;
+        bool ok = true;
+        for (;; ++it) {
+            const int stage = it % ns;
+            if (it >= ns && !mbar_wait(smem_addr(&empty[stage]), (uint32_t)((it / ns - 1) & 1))) {
+                if (lane == 0) atomicOr(&a.flags[FLAG_TIMEOUT], 1);
+                ok = false;
+                break;
+            }
+            int batch = 0;
+            if (lane == 0) batch = atomicAdd(&a.work[0], 1);
+            batch = __shfl_sync(0xffffffffu, batch, 0);
+            const uint32_t bar = smem_addr(&full[stage]);
+            if (batch >= nbatches) {
+                if (lane == 0) {
+                    s_desc[stage] = make_int4(-1, 0, 0, 0);
+                    mbar_arrive(bar);
+                }
+                break;
+            }
+            const int4 bd = batches[batch];
+            if (lane == 0) s_desc[stage] = bd;
+            produce_compact<St, CELLS>(a, bd, smraw + (size_t)stage * stage_bytes, bar, lane);
+        }
+        if (!ok) {
+            // let the copies still in flight land before the CTA's memory goes away
+            for (int j = it > ns ? it - ns : 0; j < it; ++j)
+                mbar_wait(smem_addr(&full[j % ns]), (uint32_t)((j / ns) & 1));
+        }
+        if (lane == 0) {
+            __threadfence();
+            if (atomicAdd(&a.work[1], 1) == (int)gridDim.x - 1) {
+                a.work[0] = 0;
+                a.work[1] = 0;
+                *a.step = s_step + 1;
+                __threadfence();
+            }
+        }
+        return;
+    }
+
+    const int lane = threadIdx.x & 31;
+    const unsigned long long step = s_step;
+    for (int it = 0;; ++it) {
+        const int stage = it % ns;
+        if (!mbar_wait(smem_addr(&full[stage]), (uint32_t)((it / ns) & 1))) {
+            if (lane == 0) atomicOr(&a.flags[FLAG_TIMEOUT], 1);
+            break;
+        }
+        const int4 bd = s_desc[stage];
+        if (bd.x < 0) break;
+        consume_compact<St, CELLS, SIGMA>(a, bd, smraw + (size_t)stage * stage_bytes, step);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&empty[stage]));
     }
 }
 
@@ -889,13 +1128,15 @@ __global__ void __launch_bounds__(kStThreads)
     }
 }
 
+// One entry per thread; non-fluid entries (solid byte, or link bit 31 in the
+// compact layout) report 0.
 template <typename St>
 __global__ void k_rho(const void *__restrict__ pops_v, const uint8_t *__restrict__ solid,
-                      float *__restrict__ rho, int N, long long Np)
+                      const uint32_t *__restrict__ links, float *__restrict__ rho, int N, long long Np)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    if (solid && solid[n]) {
+    if ((solid && solid[n]) || (links && (links[n] >> 31))) {
         rho[n] = 0.f;
         return;
     }
@@ -950,6 +1191,65 @@ k_budget_nodes(const void *__restrict__ pops_v, const float4 *__restrict__ U,
         const double sw = sinpi(2.0 * (double)((n / fa.nx) % fa.ny) / (double)fa.ny);
         work += ((double)fa.g[0] + (double)fa.w[0] * sw) * ux + ((double)fa.g[1] + (double)fa.w[1] * sw) * uy +
                 ((double)fa.g[2] + (double)fa.w[2] * sw) * uz;
+    }
+    __shared__ double sh[7][kBudThreads];
+    sh[0][threadIdx.x] = m;
+    sh[1][threadIdx.x] = px;
+    sh[2][threadIdx.x] = py;
+    sh[3][threadIdx.x] = pz;
+    sh[4][threadIdx.x] = umax;
+    sh[5][threadIdx.x] = nan;
+    sh[6][threadIdx.x] = work;
+    __syncthreads();
+    for (int w = kBudThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            for (int k = 0; k < 7; ++k) {
+                if (k == 4)
+                    sh[k][threadIdx.x] = fmax(sh[k][threadIdx.x], sh[k][threadIdx.x + w]);
+                else
+                    sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 7) part[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// The same partial sums in the compact layout: blocks take rows (y, z) in
+// turn and their threads the row's entries; an entry is fluid when bit 31
+// of its link word is clear.
+template <typename St>
+__global__ void __launch_bounds__(kBudThreads)
+k_budget_rows(const void *__restrict__ pops_v, const float4 *__restrict__ U, const uint32_t *__restrict__ links,
+              const int4 *__restrict__ rows, double *__restrict__ part, int nrows, long long Np, ForceArgs fa)
+{
+    const St *pops = static_cast<const St *>(pops_v);
+    double m = 0.0, px = 0.0, py = 0.0, pz = 0.0, umax = 0.0, nan = 0.0, work = 0.0;
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int4 rt = rows[r];
+        const double sw = sinpi(2.0 * (double)(r % fa.ny) / (double)fa.ny);
+        for (int c = rt.x + (int)threadIdx.x; c < rt.x + rt.z - rt.y; c += blockDim.x) {
+            if (links[c] >> 31) continue;
+            float sacc = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+            for_speeds<0, kQ>([&](auto pc) {
+                constexpr int p = decltype(pc)::value;
+                const float v = Pop<St>::template get<p>(pops[(long long)p * Np + c]);
+                sacc += v;
+                if (cx(p)) jx += cx(p) > 0 ? v : -v;
+                if (cy(p)) jy += cy(p) > 0 ? v : -v;
+                if (cz(p)) jz += cz(p) > 0 ? v : -v;
+            });
+            m += 1.0 + (double)sacc;
+            px += jx;
+            py += jy;
+            pz += jz;
+            const float4 u4 = U[c];
+            const float u2 = u4.x * u4.x + u4.y * u4.y + u4.z * u4.z;
+            if (!(u2 == u2) || !(sacc == sacc)) nan += 1.0;
+            else if (u2 > umax) umax = u2;
+            work += ((double)fa.g[0] + (double)fa.w[0] * sw) * u4.x + ((double)fa.g[1] + (double)fa.w[1] * sw) * u4.y +
+                    ((double)fa.g[2] + (double)fa.w[2] * sw) * u4.z;
+        }
     }
     __shared__ double sh[7][kBudThreads];
     sh[0][threadIdx.x] = m;
@@ -1040,6 +1340,7 @@ StageLayout stage_layout(const Dev &d)
 
 bool staged_ok(const Dev &d)
 {
+    if (d.compact) return false;  // the compact pass has its own batches
     if ((d.nx * pop_bytes(d.prec)) % 16 != 0) return false;  // rows must be whole 16-byte units
     const StageLayout L = stage_layout(d);
     return 2u * (unsigned)L.stage_bytes <= 200u * 1024u;
@@ -1089,6 +1390,12 @@ struct PrepareOp {
     void run()
     {
         d.lb_grid = 0;
+        if constexpr (W) {
+            if (d.compact) {
+                prepare_compact<St, C, S_>();
+                return;
+            }
+        }
         if (d.fluid_list || !staged_ok(d)) return;
         StageLayout L = stage_layout(d);
         const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
@@ -1114,6 +1421,32 @@ struct PrepareOp {
             }
         }
     }
+    // compact pass: the same rule over its batch table and stage size
+    template <typename St, bool C, bool S_>
+    void prepare_compact()
+    {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        raise_smem_limit((const void *)k_lb_compact<St, C, S_>, 200 * 1024);
+        long long best_cost = -1;
+        for (int ns = kMaxStages; ns >= 2; --ns) {
+            const size_t smem = (size_t)ns * d.lb_stage_bytes;
+            if (smem > 200u * 1024u) continue;
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_compact<St, C, S_>, kStThreads, smem);
+            if (d.nc > 0 && per_sm > kLbCtasWithCells) per_sm = kLbCtasWithCells;
+            if (per_sm < 1) continue;
+            const long long slots = (long long)sms * per_sm;
+            const long long cost = ((d.nbatches + slots - 1) / slots) * per_sm;
+            if (best_cost < 0 || cost < best_cost) {
+                best_cost = cost;
+                d.lb_stages = ns;
+                d.lb_smem = smem;
+                d.lb_grid = (int)(slots > d.nbatches ? d.nbatches : slots);
+            }
+        }
+    }
 };
 
 struct LaunchOp {
@@ -1123,6 +1456,14 @@ struct LaunchOp {
     template <typename St, bool W, bool C, bool S_>
     void run()
     {
+        if constexpr (W) {
+            if (d.compact) {
+                if (d.lb_grid > 0)
+                    k_lb_compact<St, C, S_><<<d.lb_grid, kStThreads, d.lb_smem, s>>>(a, d.lb_batches, d.nbatches,
+                                                                                     d.lb_stages, d.lb_stage_bytes);
+                return;
+            }
+        }
         if (d.fluid_list) {
             const int g = (d.nfluid + kLbThreads - 1) / kLbThreads;
             if (g > 0) k_lb_list<St, W, C, S_><<<g, kLbThreads, 0, s>>>(a, d.fluid_list, d.nfluid);
@@ -1153,14 +1494,24 @@ struct ShapesOp {
     void run()
     {
         n = 0;
-        if (!staged_ok(d)) return;
-        const StageLayout L = stage_layout(d);
-        raise_smem_limit((const void *)k_lb_staged<St, W, C, S_>, 200 * 1024);
+        const void *kern = (const void *)k_lb_staged<St, W, C, S_>;
+        int stage_bytes = 0;
+        if constexpr (W) {
+            if (d.compact) {
+                kern = (const void *)k_lb_compact<St, C, S_>;
+                stage_bytes = d.lb_stage_bytes;
+            }
+        }
+        if (!d.compact) {
+            if (!staged_ok(d)) return;
+            stage_bytes = stage_layout(d).stage_bytes;
+        }
+        raise_smem_limit(kern, 200 * 1024);
         for (int ns = 2; ns <= kMaxStages; ++ns) {
-            const size_t smem = (size_t)ns * L.stage_bytes;
+            const size_t smem = (size_t)ns * stage_bytes;
             if (smem > 200u * 1024u) continue;
             int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_staged<St, W, C, S_>, kStThreads, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kStThreads, smem);
             for (int c = 1; c <= per_sm && c <= 4 && n < max; ++c) {
                 stages[n] = ns;
                 ctas[n] = c;
@@ -1180,14 +1531,18 @@ int lb_shapes(const Dev &d, int *stages, int *ctas, int max)
 void set_lb_shape(Dev &d, int stages, int ctas_per_sm)
 {
     if (d.lb_grid <= 0) return;
-    const StageLayout L = stage_layout(d);
-    const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
+    int nbatches = d.nbatches, stage_bytes = d.lb_stage_bytes;
+    if (!d.compact) {
+        const StageLayout L = stage_layout(d);
+        nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
+        stage_bytes = L.stage_bytes;
+    }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long slots = (long long)sms * ctas_per_sm;
     d.lb_stages = stages;
-    d.lb_smem = (size_t)stages * L.stage_bytes;
+    d.lb_smem = (size_t)stages * stage_bytes;
     d.lb_grid = (int)(slots > nbatches ? nbatches : slots);
 }
 
@@ -1197,6 +1552,7 @@ static LbArgs lb_args(const Dev &d, const Params &p, int parity)
     a.src = d.pops[parity];
     a.dst = d.pops[parity ^ 1];
     a.links = d.links;
+    a.rows = d.rows;
     a.G = d.G;
     a.U = d.U;
     a.S = d.S;
@@ -1308,15 +1664,20 @@ void launch_lb_packed(const Dev &d0, const LbPackDesc &k, int parity, cudaStream
     dispatch(d0, op);
 }
 
+// Density of every entry (rho - 1; 0 at non-fluid entries): N lattice nodes,
+// or the M entries of the compact layout.
 void launch_rho(const Dev &d, int parity, cudaStream_t s)
 {
-    const int g = (d.N + 255) / 256;
+    const int n = d.compact ? d.M : d.N;
+    const int g = (n + 255) / 256;
+    const uint8_t *solid = d.compact ? nullptr : d.solid;
+    const uint32_t *links = d.compact ? d.links : nullptr;
     if (d.prec == PREC_F16)
-        k_rho<__half><<<g, 256, 0, s>>>(d.pops[parity], d.solid, d.rho, d.N, d.Np);
+        k_rho<__half><<<g, 256, 0, s>>>(d.pops[parity], solid, links, d.rho, n, d.Np);
     else if (d.prec == PREC_BF16)
-        k_rho<__nv_bfloat16><<<g, 256, 0, s>>>(d.pops[parity], d.solid, d.rho, d.N, d.Np);
+        k_rho<__nv_bfloat16><<<g, 256, 0, s>>>(d.pops[parity], solid, links, d.rho, n, d.Np);
     else
-        k_rho<float><<<g, 256, 0, s>>>(d.pops[parity], d.solid, d.rho, d.N, d.Np);
+        k_rho<float><<<g, 256, 0, s>>>(d.pops[parity], solid, links, d.rho, n, d.Np);
 }
 
 // Wall shear stress: the traction sigma n of the last pass's stress on the
@@ -1359,7 +1720,18 @@ void launch_budget(const Dev &d, const Params &p, int parity, cudaStream_t s, bo
     }
     fa.nx = d.nx;
     fa.ny = d.ny;
-    if (d.prec == PREC_F16)
+    if (d.compact) {
+        const int nrows = d.ny * d.nz;
+        if (d.prec == PREC_F16)
+            k_budget_rows<__half><<<d.budget_blocks, kBudThreads, 0, s>>>(d.pops[parity], d.U, d.links, d.rows,
+                                                                         d.budget_part, nrows, d.Np, fa);
+        else if (d.prec == PREC_BF16)
+            k_budget_rows<__nv_bfloat16><<<d.budget_blocks, kBudThreads, 0, s>>>(
+                d.pops[parity], d.U, d.links, d.rows, d.budget_part, nrows, d.Np, fa);
+        else
+            k_budget_rows<float><<<d.budget_blocks, kBudThreads, 0, s>>>(d.pops[parity], d.U, d.links, d.rows,
+                                                                        d.budget_part, nrows, d.Np, fa);
+    } else if (d.prec == PREC_F16)
         k_budget_nodes<__half><<<d.budget_blocks, kBudThreads, 0, s>>>(d.pops[parity], d.U, d.solid,
                                                                       d.budget_part, d.N, d.Np, fa);
     else if (d.prec == PREC_BF16)

@@ -250,7 +250,8 @@ void initialise(rbc_server *s, Active &a)
     int rc = rbc_init(&a.req->r.geom, &a.req->r.cells, &p, s->base + a.off, a.req->bytes, &a.h);
     const long long from = a.req->r.average_from;
     // packable solves run their full ticks in a pack
-    const bool packable = rc == RBC_OK && rbc::handle_dev(a.h).nc > 0 && rbc::handle_dev(a.h).lb_grid > 0;
+    const bool packable = rc == RBC_OK && rbc::handle_dev(a.h).nc > 0 && rbc::handle_dev(a.h).lb_grid > 0 &&
+                          !rbc::handle_dev(a.h).compact;
     if (rc == RBC_OK && a.total >= s->tick_steps && !packable)
         rc = rbc::capture_ticks(a.h, s->tick_steps, from, &a.tick);
     if (rc == RBC_OK && a.total % s->tick_steps) rc = rbc::capture_ticks(a.h, a.total % s->tick_steps, from, &a.last);
@@ -286,7 +287,11 @@ long long pack_key(const rbc::Dev &d, const rbc::Params &p)
            (d.S ? 1 : 0);
 }
 
-bool packable(const Active &a) { return a.h && rbc::handle_dev(a.h).nc > 0 && rbc::handle_dev(a.h).lb_grid > 0; }
+// packs hold dense lattices with cells (the packed lattice pass is row-staged)
+bool packable(const Active &a)
+{
+    return a.h && rbc::handle_dev(a.h).nc > 0 && rbc::handle_dev(a.h).lb_grid > 0 && !rbc::handle_dev(a.h).compact;
+}
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 

@@ -52,12 +52,14 @@ class rbc_params(ctypes.Structure):
                 ("r_cut_wall", ctypes.c_double), ("mach_max", ctypes.c_double),
                 ("bin_capacity", ctypes.c_int), ("max_neighbors", ctypes.c_int),
                 ("precision", ctypes.c_int), ("rounding", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("node_list", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("seed", ctypes.c_uint64), ("node_list", ctypes.c_int), ("layout", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 #: rbc_params.precision / rounding values (include/rbc.h)
 PRECISION = {"f32": 0, "f16": 1, "bf16": 2}
 ROUNDING = {"stochastic": 0, "nearest": 1}
+LAYOUT = {"auto": 0, "dense": 1, "compact": 2}
 
 
 class rbc_stats_t(ctypes.Structure):
@@ -90,7 +92,8 @@ class rbc_tune_report(ctypes.Structure):
 #: symbols include/rbc.h declares
 EXPORTS = ["rbc_default_params", "rbc_workspace_size", "rbc_init", "rbc_step", "rbc_fields",
            "rbc_stats", "rbc_cell_diag", "rbc_neighbors", "rbc_set_timing", "rbc_kernel_times",
-           "rbc_autotune", "rbc_wss_accumulate", "rbc_wss", "rbc_launches_per_step", "rbc_neighbors_noalloc", "rbc_server_create", "rbc_server_submit",
+           "rbc_autotune", "rbc_wss_accumulate", "rbc_wss", "rbc_launches_per_step", "rbc_layout", "rbc_fluid_nodes",
+           "rbc_neighbors_noalloc", "rbc_server_create", "rbc_server_submit",
            "rbc_server_poll", "rbc_server_results", "rbc_server_clock", "rbc_server_free", "rbc_free",
            "rbc_last_error"]
 
@@ -126,6 +129,10 @@ def load(path: str = LIB_PATH):
     L.rbc_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.rbc_kernel_times.argtypes = [ctypes.c_void_p, _D, _I64]
     L.rbc_launches_per_step.argtypes = [ctypes.c_void_p]
+    L.rbc_layout.argtypes = [ctypes.c_void_p, _I, _I64, _I64]
+    L.rbc_layout.restype = ctypes.c_int
+    L.rbc_fluid_nodes.argtypes = [ctypes.c_void_p, _I64, ctypes.c_int64, _I64]
+    L.rbc_fluid_nodes.restype = ctypes.c_int
     L.rbc_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, P(rbc_tune_report)]
     L.rbc_autotune.restype = ctypes.c_int
     L.rbc_wss_accumulate.argtypes = [ctypes.c_void_p]
@@ -215,6 +222,8 @@ class _Inputs:
                     arr[a] = float(v[a])
             elif k in ("bin_capacity", "max_neighbors", "node_list"):
                 setattr(p, k, int(v))
+            elif k == "layout":
+                p.layout = LAYOUT[v] if isinstance(v, str) else int(v)
             elif k == "precision":
                 p.precision = PRECISION[v] if isinstance(v, str) else int(v)
             elif k == "rounding":
@@ -335,6 +344,19 @@ def rbc_launches_per_step(h) -> int:
     return int(load().rbc_launches_per_step(h))
 
 
+def rbc_layout(h):
+    c, e, f = ctypes.c_int(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().rbc_layout(h, ctypes.byref(c), ctypes.byref(e), ctypes.byref(f)), h)
+    return dict(compact=bool(c.value), entries=int(e.value), fluid=int(f.value))
+
+
+def rbc_fluid_nodes(h, max_nodes: int):
+    nodes = np.zeros(max(max_nodes, 1), dtype=np.int64)
+    cnt = ctypes.c_int64(0)
+    _check(load().rbc_fluid_nodes(h, nodes.ctypes.data_as(_I64), int(max_nodes), ctypes.byref(cnt)), h)
+    return nodes[: min(cnt.value, max_nodes)].copy()
+
+
 def rbc_neighbors_noalloc(pos_ptr: int, n: int, dims, periodic, r_cut: float, counts_ptr: int, lists_ptr: int,
                           max_per_cell: int, stream: int | None):
     """Candidate-partner lists without device allocation (device pointers in
@@ -403,6 +425,13 @@ class Solver:
 
     def autotune(self, steps_per_trial=20):
         return rbc_autotune(self.handle, steps_per_trial)
+
+    def layout(self):
+        return rbc_layout(self.handle)
+
+    def fluid_nodes(self):
+        """Lattice indices of the fluid nodes in the library's storage order."""
+        return rbc_fluid_nodes(self.handle, self.N)
 
     def wss_accumulate(self):
         rbc_wss_accumulate(self.handle)

@@ -50,7 +50,8 @@ def test_struct_layouts_match_header(lib):
     assert ctypes.sizeof(rbc.rbc_cells) == 8 + 4 * 8
     assert ctypes.sizeof(rbc.rbc_stats_t) == 8 * 10 + 8 + 8
     assert rbc.rbc_params.stream.offset == ctypes.sizeof(rbc.rbc_params) - 8
-    # int precision, int rounding, uint64_t seed, int node_list, void *stream close the struct
+    # int precision, int rounding, uint64_t seed, int node_list, int layout, void *stream close the struct
+    assert rbc.rbc_params.layout.offset == rbc.rbc_params.stream.offset - 4
     assert rbc.rbc_params.node_list.offset == rbc.rbc_params.stream.offset - 8
     assert rbc.rbc_params.seed.offset == rbc.rbc_params.node_list.offset - 8
     assert rbc.rbc_params.rounding.offset == rbc.rbc_params.seed.offset - 4
@@ -110,11 +111,13 @@ def test_missing_library_fails_loudly(tmp_path):
 def test_open_boundary_validation(lib):
     g = wl.open_tube(16, 24, 6.0, 0.01)
     p = wl.params()
-    dense = rbc.rbc_workspace_size(g, None, dict(p, node_list=-1))
-    # the node-list pass adds one index per fluid node (chosen automatically
-    # here: fewer than half the nodes are fluid)
-    nl = rbc.rbc_workspace_size(g, None, dict(p, node_list=1))
-    assert nl > dense and rbc.rbc_workspace_size(g, None, p) == nl
+    dense = rbc.rbc_workspace_size(g, None, dict(p, node_list=-1, layout="dense"))
+    # in the dense layout the node-list pass adds one index per fluid node;
+    # the default layout of this sparse vessel is the compact one, smaller
+    # than both
+    nl = rbc.rbc_workspace_size(g, None, dict(p, node_list=1, layout="dense"))
+    assert nl > dense and rbc.rbc_workspace_size(g, None, dict(p, layout="dense")) == nl
+    assert rbc.rbc_workspace_size(g, None, p) < dense
     bad = dict(g, node_type=np.full_like(g["node_type"], 3))
     with pytest.raises(rbc.RbcError):
         rbc.rbc_workspace_size(bad, None, p)
@@ -145,3 +148,37 @@ def test_walled_setup_is_linear_time(lib):
     t0 = time.perf_counter()
     rbc.rbc_workspace_size(geom, cells, dict(alpha_tt=0.04))
     assert time.perf_counter() - t0 < 0.4
+
+
+def test_compact_layout_footprint_follows_the_fluid_nodes(lib):
+    """The 512^3 Y-bifurcation (6.67 M fluid nodes of 134 M) with binary16
+    populations: the dense layout needs ~18 GB, the compact one stores per
+    lattice row only the span its fluid nodes reach, so its workspace is
+    within 1.5x of the fluid nodes times the bytes of one stored entry
+    (populations 2 x 19 x 2, u 16, sigma 32, rho 4, links 4) plus one byte
+    of node flags per lattice node."""
+    geom = wl.y_bifurcation(512, 60.0, 45.0)
+    p = wl.params(precision="f16")
+    dense = rbc.rbc_workspace_size(geom, None, dict(p, layout="dense"))
+    compact = rbc.rbc_workspace_size(geom, None, dict(p, layout="compact"))
+    auto = rbc.rbc_workspace_size(geom, None, p)
+    nf = wl.fluid_count(geom)
+    N = 512 ** 3
+    per_entry = 2 * 19 * 2 + 16 + 32 + 4 + 4
+    assert dense > 15e9 and auto == compact
+    assert compact < 1.5 * nf * per_entry + N + 64e6, (compact, nf)
+    print(f"Y 512^3 binary16: dense {dense / 1e9:.2f} GB, compact {compact / 1e9:.2f} GB, {nf} fluid nodes")
+
+
+def test_layout_argument_checks(lib):
+    """An unknown layout, and the compact layout of a lattice without solid
+    nodes, are rejected on the host."""
+    with pytest.raises(rbc.RbcError) as e:
+        rbc.rbc_workspace_size(wl.periodic_box(16), None, wl.params(layout=5))
+    assert e.value.code == rbc.RBC_EINVAL
+    with pytest.raises(rbc.RbcError) as e:
+        rbc.rbc_workspace_size(wl.periodic_box(16), None, wl.params(layout="compact"))
+    assert e.value.code == rbc.RBC_EINVAL
+    # a tube: compact by default, and smaller
+    g = wl.tube(64, 28.0, length=32)
+    assert rbc.rbc_workspace_size(g, None, wl.params()) < 0.9 * rbc.rbc_workspace_size(g, None, wl.params(layout="dense"))
