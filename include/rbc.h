@@ -369,6 +369,12 @@ typedef struct {
     int64_t steps;         /* coupled steps to run (>= 1) */
     int64_t average_from;  /* samples (one per tick) at pass counts >= this are averaged */
     uint64_t tag;          /* caller's identifier, returned in the result */
+    /* Final state of the solve, written when it finishes successfully,
+     * before its result is queued (each may be NULL): out_rho[N], out_u[3N]
+     * and out_cells[13 n] as rbc_fields, out_diag[21 n] as rbc_cell_diag.
+     * Host buffers owned by the caller, who keeps them valid until the
+     * result has come out of rbc_server_results. */
+    double *out_rho, *out_u, *out_cells, *out_diag;
 } rbc_request;
 
 typedef struct {

@@ -202,6 +202,12 @@ void finish(rbc_server *s, Active &a)
             for (int k = 0; k < 3; ++k) res.mean_p_fluid[k] = acc[2 + k] / acc[1];
         }
         res.max_u = acc[5];
+        // the final state, where the caller asked for it (the solve's work
+        // has completed: its ticks are retired)
+        const rbc_request &r = a.req->r;
+        if (res.status == RBC_OK && (r.out_rho || r.out_u || r.out_cells))
+            res.status = rbc_fields(a.h, r.out_rho, r.out_u, r.out_cells);
+        if (res.status == RBC_OK && r.out_diag) res.status = rbc_cell_diag(a.h, r.out_diag);
     }
     release(s, a);
     res.t_done = seconds_since(s->t0);

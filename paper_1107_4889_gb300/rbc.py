@@ -71,7 +71,8 @@ class rbc_stats_t(ctypes.Structure):
 
 class rbc_request(ctypes.Structure):
     _fields_ = [("geom", rbc_geometry), ("cells", rbc_cells), ("params", rbc_params),
-                ("steps", ctypes.c_int64), ("average_from", ctypes.c_int64), ("tag", ctypes.c_uint64)]
+                ("steps", ctypes.c_int64), ("average_from", ctypes.c_int64), ("tag", ctypes.c_uint64),
+                ("out_rho", _D), ("out_u", _D), ("out_cells", _D), ("out_diag", _D)]
 
 
 class rbc_result(ctypes.Structure):
@@ -464,11 +465,17 @@ def rbc_server_create(arena_ptr: int, arena_bytes: int, max_active: int, tick_st
     return h
 
 
-def rbc_server_submit(srv, geometry, cells, params, steps: int, average_from: int = 0, tag: int = 0):
+def rbc_server_submit(srv, geometry, cells, params, steps: int, average_from: int = 0, tag: int = 0, out=None):
+    """Queue a request.  ``out``: optional dict of float64 numpy buffers
+    (rho (N,), u (N, 3), cells (n, 13), diag (n, 21)) the server fills with
+    the final state; the caller keeps them alive until the result is out."""
     ins = _Inputs(geometry, cells, params, None)
     r = rbc_request()
     r.geom, r.cells, r.params = ins.geom, ins.cells, ins.params
     r.steps, r.average_from, r.tag = int(steps), int(average_from), int(tag)
+    if out:
+        r.out_rho, r.out_u = _dp(out.get("rho")), _dp(out.get("u"))
+        r.out_cells, r.out_diag = _dp(out.get("cells")), _dp(out.get("diag"))
     _check(load().rbc_server_submit(srv, ctypes.byref(r)))  # inputs are copied by the server
 
 
@@ -516,18 +523,40 @@ class Server:
             raise RuntimeError("the RBC server needs a CUDA GPU")
         load()
         self.device = torch.device("cuda" if device is None else device)
+        self._out = {}  # tag -> result buffers the server fills when the solve finishes
         with torch.cuda.device(self.device):
             self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.device)
             self.handle = rbc_server_create(self.arena.data_ptr(), int(arena_bytes), max_active, tick_steps)
 
-    def submit(self, geometry, cells, params, steps, average_from=0, tag=0):
-        rbc_server_submit(self.handle, geometry, cells, params, steps, average_from, tag)
+    def submit(self, geometry, cells, params, steps, average_from=0, tag=0, fields=False):
+        """Queue a solve.  fields=True: its result carries the final rho,
+        u, cell state and per-cell diagnostics (rbc_fields /
+        rbc_cell_diag layout), read back when it finishes."""
+        out = None
+        if fields:
+            N = int(geometry["nx"]) * int(geometry["ny"]) * int(geometry["nz"])
+            n = 0 if cells is None else int(np.asarray(cells["pos"]).shape[0])
+            out = dict(rho=np.zeros(N), u=np.zeros((N, 3)), cells=np.zeros((max(n, 1), 13)),
+                       diag=np.zeros((max(n, 1), 21)), n=n)
+            self._out[int(tag)] = out
+        rbc_server_submit(self.handle, geometry, cells, params, steps, average_from, tag, out)
 
     def poll(self):
         return rbc_server_poll(self.handle)
 
     def results(self, max_results=256):
-        return rbc_server_results(self.handle, max_results)
+        res = rbc_server_results(self.handle, max_results)
+        for r in res:
+            out = self._out.pop(r["tag"], None)
+            if out is None:
+                continue
+            n = out["n"]
+            cs, dg = out["cells"][:n], out["diag"][:n]
+            r["fields"] = dict(rho=out["rho"], u=out["u"], pos=cs[:, 0:3], quat=cs[:, 3:7], vel=cs[:, 7:10],
+                               omega=cs[:, 10:13])
+            r["diag"] = dict(F_mech=dg[:, 0:3], tau_mech=dg[:, 3:6], u_s=dg[:, 6:9], omega_s=dg[:, 9:12],
+                             T_S=dg[:, 12:15], J=dg[:, 15:18], L=dg[:, 18:21])
+        return res
 
     def clock(self):
         return rbc_server_clock(self.handle)
