@@ -1,17 +1,21 @@
 """Benchmark of the coupled LB + rigid-RBC time step on GB300.
 
-Default workload: the walled plane channel 64 x 64 x 256 (solid planes
-y = 0, 63; periodic x, z) with 3,650 cells (hematocrit 0.35), driven by a
-force density of 5.376e-7 along x, FP32 populations.  One step is one full
-coupled step: cell list + Gay-Berne forces, per-cell sampling + rigid update +
-spreading, and the fused lattice pass.
+Default workload: the largest single-GPU configuration, a straight tube of
+radius 120 in a 256^3 box (11,582,464 fluid nodes, periodic along z) with
+51,846 cells (hematocrit 0.45 of the lumen), driven by the axial force
+density that gives a wall shear rate of 1e-4 in plain plasma, FP32
+populations in the compact layout.  One step is one full coupled step: cell
+list + Gay-Berne forces, per-cell sampling + rigid update + spreading, and
+the fused lattice pass.
 
 Prints one JSON line (rank 0): value = fluid-node updates per second over all
 ranks (MLUPS) from CUDA events around K graph-launched steps, with live
 per-kernel event timing of the lattice pass for the roofline, nvidia-smi clock
 samples taken during the timed region, the end-to-end figure through the
 public API with host buffers (init from host arrays, K steps, fields read
-back), and the FP64 oracle timed on a bounded sample on the host.
+back; the init time beside it), the FP64 oracle timed on a bounded sample on
+the host, and (``serving``) the batched request server on the serving mix at
+full step counts against the plain FP32 single-instance path.
 
 ``--impl reference`` times the oracle (plain FP64 CPU implementation) on the
 same workload and prints the same line with ``"impl": "reference"``.
@@ -66,6 +70,10 @@ def _workload(name, precision="f32"):
         g, c, p = wl.tube_workload()
         desc = (f"tube r=120 in 256^3, {len(c['pos'])} RBC (H={wl.tube_hematocrit(g, len(c['pos'])):.2f} "
                 f"of the lumen), G_z={g['body_force'][2]:.3e}")
+    elif name == "tube_slab":
+        g, c, p = wl.tube_slab()
+        desc = (f"slab of the tube: r=120 in 256x256x{g['nz']} (periodic z), {len(c['pos'])} RBC, "
+                f"G_z={g['body_force'][2]:.3e}")
     else:
         raise SystemExit(f"unknown workload {name}")
     p = dict(p, precision=precision)
@@ -193,6 +201,15 @@ def _algorithmic_bytes_per_node(geom, params, has_cells=True):
     return b
 
 
+def _cpu_sample(name, precision):
+    """The bounded sample of a workload the oracle is timed on: the whole
+    workload, except for the tube, whose oracle step takes about a minute
+    (and whose cell-wall search is brute force over 193,000 wall particles
+    per cell): there a 20-plane slab of it, the same cross-section, drive
+    and cell density."""
+    return _workload("tube_slab" if name == "tube" else name, precision)
+
+
 def _oracle_rate(geom, cells, params, budget_s):
     """Run the FP64 oracle for about budget_s seconds; returns (MLUPS, steps, seconds)."""
     from oracle import oracle as orc
@@ -218,14 +235,15 @@ def run_reference(args):
         return
     geom, cells, params, desc = _workload(args.workload, args.precision)
     nf = wl.fluid_count(geom)
-    rate, steps, dt = _oracle_rate(geom, cells, params, args.reference_budget)
+    sg, sc, sp, sdesc = _cpu_sample(args.workload, args.precision)
+    rate, steps, dt = _oracle_rate(sg, sc, sp, args.reference_budget)
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps * nf / wl.fluid_count(sg),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": desc, "fluid_nodes": nf, "cells": 0 if cells is None else len(cells["pos"])},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{steps} coupled steps of the full workload ({dt:.1f} s), "
+                         "sample": f"{steps} coupled steps of {sdesc} ({dt:.1f} s), "
                                    f"capped by a {args.reference_budget:.0f} s budget"},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -300,23 +318,30 @@ def run_ours(args):
     ms_max = _barrier_and_max(ms, ws)
     value = nf * args.steps * ws / (ms_max * 1e-3) / 1e6
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers; the set-up
+    # (rbc_init: host tables, uploads, graph capture, the first cell list)
+    # is timed on its own as well
     _barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s2 = Solver(geom, cells, params)
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
     s2.step(args.steps)
     f = s2.fields()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    layout = s2.layout()
     s2.close()
     e2e_s = _barrier_and_max(e2e_s, ws)
+    init_s = _barrier_and_max(init_s, ws)
     n = 0 if cells is None else len(cells["pos"])
     h2d = (0 if geom["solid"] is None else N) + n * (3 + 4 + 3 + 3) * 8
     d2h = N * 8 + N * 3 * 8 + n * 13 * 8
     e2e = {"value": nf * args.steps * ws / e2e_s / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-           "note": "job = init from host arrays + K steps + fields read back"}
+           "init_s": init_s, "steps_s": e2e_s - init_s,
+           "note": "job = init from host arrays (init_s) + K steps + fields read back"}
     assert np.isfinite(f["u"]).all()
 
     if rank != 0:
@@ -333,9 +358,13 @@ def run_ours(args):
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        rate, csteps, cdt = _oracle_rate(geom, cells, params, args.cpu_budget)
+        sg, sc, sp, sdesc = _cpu_sample(args.workload, args.precision)
+        rate, csteps, cdt = _oracle_rate(sg, sc, sp, args.cpu_budget)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{csteps} coupled steps of the same workload ({cdt:.1f} s, one core)"}
+               "sample": f"{csteps} coupled steps of {sdesc} ({cdt:.1f} s, one core)"}
+    serving = None
+    if ws == 1 and not args.no_serve:
+        serving = serve_measure(args)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -343,6 +372,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "f32" else f"f32 ({args.precision} storage)", "data": "synthetic",
         "config": {"workload": desc, "nodes": N, "fluid_nodes": nf, "cells": n,
+                   "layout": "compact" if layout["compact"] else "dense", "stored_entries": layout["entries"],
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": f"inputs larger than L2: per-step working set "
                          f"{ws_bytes / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB",
@@ -355,11 +385,26 @@ def run_ours(args):
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
         "budget": {"mass_drift_rel": (st2["mass"] - st["mass"]) / st["mass"], "max_u": st2["max_u"],
                    "gb_clamps": st2["gb_clamps"]},
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
 
 
 def run_serve(args):
+    """The serving measurement alone, as its own JSON line."""
+    import torch
+
+    from paper_1107_4889_gb300 import build as B
+
+    B.build()
+    torch.cuda.set_device(0)
+    line = serve_measure(args)
+    line = {"metric": "batched serving solves/s (binary16, continuous batching)", "value": line["solves_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic", **line}
+    print(json.dumps(line), flush=True)
+
+
+def serve_measure(args):
     """Batched serving of the request stream: solves/s and p50/p99
     time-to-result of the binary16 request server (continuous batching,
     Poisson arrivals at 0.8 of its measured capacity) against the plain FP32
@@ -368,11 +413,8 @@ def run_serve(args):
     binary16 against FP32."""
     import torch
 
-    from paper_1107_4889_gb300 import build as B
     from paper_1107_4889_gb300.rbc import Server, Solver
 
-    B.build()
-    torch.cuda.set_device(0)
     reqs16 = wl.serving_stream(args.serve_requests, precision="f16", step_scale=args.serve_step_scale)
     n = len(reqs16)
 
@@ -428,12 +470,12 @@ def run_serve(args):
     ttr = np.array([r["t_done"] - r["t_submit"] for r in res_ol])
     errs = [abs(res_cl[k]["mean_power"] / p32[k] - 1.0) for k in range(nseq)]
     fluid = [wl.fluid_count(g) * steps for g, c, p, steps, i in reqs16]
-    line = {
-        "metric": "batched serving solves/s (binary16, continuous batching)", "value": capacity, "unit": "solves/s",
-        "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+    return {
+        "solves_per_s": capacity,
         "config": {"workload": f"{n} requests: boxes {list(wl.SERVING_BOXES)}, periodic (Kolmogorov drive) or walled "
                                f"(uniform drive), hematocrit U[0.1,0.5] (slot-limited), shear rate logU[1e-5,1e-3], "
-                               f"steps U[2000,10000] x {args.serve_step_scale}",
+                               f"steps U[2000,10000] x {args.serve_step_scale}, binary16 populations",
+                   "requests": n, "steps_total": int(sum(st for _, _, _, st, _ in reqs16)),
                    "slots": args.serve_slots, "tick_steps": args.serve_tick},
         "fp32_single_instance": {"value": seq_rate, "unit": "solves/s", "requests": nseq},
         "speedup_vs_fp32_single": capacity / seq_rate,
@@ -444,6 +486,71 @@ def run_serve(args):
                                     "within_1pct": int(np.sum(np.array(errs) < 0.01)), "of": nseq},
         "failed": int(sum(r["status"] != 0 for r in res_cl + res_ol)),
     }
+
+
+def run_stats(args):
+    """Long-run statistics of the channel workload (64 x 64 x 256, 3,650
+    cells, hematocrit 0.35): eta_rel = P_0 / P_H (time-averaged work rate of
+    the uniform drive without and with cells, i.e. the flow rate ratio
+    Q_0 / Q_H) and the near-wall hematocrit profile (cell centres in 1-lu
+    bins of y, time-averaged, as the local volume fraction V_cell count /
+    (n_x n_z)), each with FP32 and with binary16 populations; samples every
+    100 steps over the second half of --steps."""
+    import torch
+
+    from paper_1107_4889_gb300 import build as B
+    from paper_1107_4889_gb300.rbc import Solver
+
+    B.build()
+    torch.cuda.set_device(0)
+    every = 100
+    res = {}
+    for prec in ("f32", "f16"):
+        out = {}
+        for with_cells in (False, True):
+            geom, cells, params, desc = _workload("channel", prec)
+            s = Solver(geom, cells if with_cells else None, params)
+            powers, done = [], 0
+            t0 = time.perf_counter()
+            while done < args.steps:
+                s.step(every)
+                done += every
+                if done > args.steps // 2:
+                    powers.append(s.stats()["power"])
+                    if with_cells:
+                        s.profile_accumulate(1)
+            out["P_H" if with_cells else "P_0"] = float(np.mean(powers))
+            if with_cells:
+                prof = s.profile()[0]
+                out["profile"] = prof * wl.CELL_VOLUME / (geom["nx"] * geom["nz"])
+                out["samples"] = len(powers)
+            out["s_" + ("H" if with_cells else "0")] = time.perf_counter() - t0
+            s.close()
+        out["eta_rel"] = out["P_0"] / out["P_H"]
+        res[prec] = out
+    a, b = res["f32"], res["f16"]
+    ny = len(a["profile"])
+    core = a["profile"][ny // 4: 3 * ny // 4].mean()
+
+    def cfl(prof):
+        # distance from the wall plane y = 0.5 to the first bin whose local
+        # hematocrit reaches half the core value, averaged over both walls
+        d = []
+        for side in (prof, prof[::-1]):
+            k = int(np.argmax(side >= 0.5 * core))
+            d.append(k - 0.5)
+        return float(np.mean(d))
+
+    line = {"metric": "channel long-run statistics, binary16 vs FP32", "workload": desc,
+            "steps": args.steps, "samples": a["samples"], "sample_every": every,
+            "eta_rel": {"f32": a["eta_rel"], "f16": b["eta_rel"], "rel_diff": b["eta_rel"] / a["eta_rel"] - 1.0},
+            "near_wall_hematocrit": {"f32": [round(float(v), 4) for v in a["profile"][:12]],
+                                     "f16": [round(float(v), 4) for v in b["profile"][:12]],
+                                     "core_mean_f32": float(core),
+                                     "profile_l1_rel": float(np.abs(b["profile"] - a["profile"]).sum() /
+                                                             a["profile"].sum())},
+            "cell_free_layer_lu": {"f32": cfl(a["profile"]), "f16": cfl(b["profile"])},
+            "seconds": {k: res[k]["s_0"] + res[k]["s_H"] for k in res}}
     print(json.dumps(line), flush=True)
 
 
@@ -498,13 +605,15 @@ def run_wss_map(args):
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["channel", "box32", "tube", "box256", "box128", "ybif"],
-                    default="channel")
+    ap.add_argument("--workload", choices=["channel", "box32", "tube", "tube_slab", "box256", "box128", "ybif"],
+                    default="tube")
     ap.add_argument("--wss-map", action="store_true",
                     help="wall-shear-stress map of the workload, binary16 against FP32")
+    ap.add_argument("--stats", action="store_true",
+                    help="relative viscosity and near-wall hematocrit of the channel, binary16 against FP32")
     ap.add_argument("--no-cells", action="store_true", help="drop the workload's cells (lattice pass alone)")
     ap.add_argument("--node-list", type=int, default=0, choices=[-1, 0, 1],
                     help="lattice pass over a fluid-node list (1), whole rows (-1), or the library's choice (0)")
@@ -515,9 +624,10 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--reference-budget", type=float, default=60.0)
     ap.add_argument("--serve", action="store_true", help="batched-serving benchmark instead of the step benchmark")
-    ap.add_argument("--serve-requests", type=int, default=200)
-    ap.add_argument("--serve-step-scale", type=float, default=0.1)
-    ap.add_argument("--serve-baseline-requests", type=int, default=60)
+    ap.add_argument("--no-serve", action="store_true", help="leave the serving measurement out of the step line")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-step-scale", type=float, default=1.0)
+    ap.add_argument("--serve-baseline-requests", type=int, default=8)
     ap.add_argument("--serve-slots", type=int, default=48)
     ap.add_argument("--serve-tick", type=int, default=100)
     ap.add_argument("--serve-arena-gb", type=float, default=64.0)
@@ -531,6 +641,9 @@ def main():
         return
     if args.wss_map:
         run_wss_map(args)
+        return
+    if args.stats:
+        run_stats(args)
         return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -292,6 +292,33 @@ int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out);
 int rbc_wss_accumulate(rbc_handle *h);
 int rbc_wss(rbc_handle *h, int64_t *node, double *tau, int64_t max, int64_t *n, int64_t *samples);
 
+/* Failure detection of the staged lattice passes (the paper has no
+ * counterpart).  Their producer / consumer pipeline waits on shared-memory
+ * barriers, each wait bounded: past the bound the waiting warp raises a
+ * timeout flag and leaves, the producer first waiting (with the default
+ * bound) for every copy it has issued, so the kernel always returns and the
+ * context stays usable; the next synchronising call (rbc_stats,
+ * rbc_fields) returns RBC_ETIMEOUT.  rbc_set_wait_limit sets the bound in
+ * clock64 cycles (0: the default, about 2 s) and, for tests of this path,
+ * starve_batch >= 0 names a batch whose copies the producer never issues,
+ * so that the consumers waiting for it run out of time (-1: none); the step
+ * graphs are re-captured.  RBC_EINVAL when the solve's lattice pass is not
+ * a staged one. */
+int rbc_set_wait_limit(rbc_handle *h, int64_t cycles, int starve_batch);
+
+/* Cell-centre profile: the near-wall hematocrit and cell-free layer that
+ * Sec. 4 reports for vessels.  rbc_profile_accumulate enqueues on the
+ * handle's stream the addition of the current cell centres to a histogram
+ * of 1-lattice-unit bins along `axis` (0 x, 1 y, 2 z; bin k counts centres
+ * with k <= R_axis < k + 1), as FP64 whole numbers (exact, independent of
+ * order); a call with another axis first clears it.  rbc_profile
+ * synchronises and copies the n_axis bins to counts[nbins] (nbins >= the box
+ * along the axis, the rest zeroed) with the axis (-1: never accumulated)
+ * and the number of samples; the time-averaged count of bin k is
+ * counts[k] / samples.  RBC_EINVAL without cells. */
+int rbc_profile_accumulate(rbc_handle *h, int axis);
+int rbc_profile(rbc_handle *h, double *counts, int nbins, int *axis, int64_t *samples);
+
 /* Kernel launches one rbc_step(h, 1) enqueues. */
 int rbc_launches_per_step(const rbc_handle *h);
 

@@ -54,6 +54,7 @@ struct Problem {
     bool compact = false;
     int M = 0;
     std::vector<int4> rows, batches;
+    std::vector<int2> bx, pool;  // per batch (pool offset, bytes); per batch row nine copy descriptors
     int stage_bytes = 0;
 };
 
@@ -127,9 +128,16 @@ inline int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 // fluid x-range widened by one, rounded out to 8, or the whole row when it
 // wraps) times the rows fits in a stage of at most stage_cap bytes
 // (node_bytes staged per window entry); a non-wrapping row wider than that
-// is cut along x.  Returns false when a wrapping row does not fit.
-bool build_compact(Problem &P, const uint8_t *solid, int node_bytes)
+// is cut along x.  Copy descriptors: for every batch row and each of its
+// nine upstream rows (y + dy, z + dz), the part of that row's span inside
+// the window -- first entry, window offset, entry count -- and per batch the
+// total bytes its copies bring (esz bytes per population entry of the three
+// or one speeds pulled from that row, plus G / theta (cells) and the link
+// word from the row itself).  Returns false when a wrapping row does not
+// fit.
+bool build_compact(Problem &P, const uint8_t *solid, int esz, bool cells)
 {
+    const int node_bytes = kQ * esz + (cells ? 16 : 0) + 4;
     const int nx = P.nx, ny = P.ny, nz = P.nz, nrows = ny * nz;
     const int full = (nx + 7) / 8 * 8;
     std::vector<int> fl((size_t)nrows, -1), fh((size_t)nrows, -1);
@@ -231,6 +239,26 @@ bool build_compact(Problem &P, const uint8_t *solid, int node_bytes)
         }
     }
     P.stage_bytes = (most * node_bytes + 127) / 128 * 128;
+    // copy descriptors
+    P.bx.clear();
+    P.pool.clear();
+    for (const int4 &bd : P.batches) {
+        const int z = bd.x, y0 = bd.y & 0xFFFFF, nb = (int)((uint32_t)bd.y >> 20);
+        const int X0 = bd.w & 0xFFFF, W = (int)((uint32_t)bd.w >> 16);
+        long long bytes = 0;
+        const int first = (int)P.pool.size();
+        for (int b = 0; b < nb; ++b)
+            for (int u = 0; u < 9; ++u) {
+                const int dy = u % 3 - 1, dz = u / 3 - 1;
+                const int4 rt = P.rows[(size_t)wrapi(y0 + b + dy, ny) + (size_t)ny * wrapi(z + dz, nz)];
+                const int lo = std::max(X0, rt.y), hi = std::min(X0 + W, rt.z);
+                const int cnt = std::max(0, hi - lo);
+                P.pool.push_back(cnt > 0 ? make_int2(rt.x + lo - rt.y, (lo - X0) | (cnt << 16)) : make_int2(0, 0));
+                const int planes = (dy == 0 || dz == 0) ? 3 : 1;
+                bytes += (long long)cnt * (esz * planes + (u == 4 ? (cells ? 16 : 0) + 4 : 0));
+            }
+        P.bx.push_back(make_int2(first, (int)bytes));
+    }
     return true;
 }
 
@@ -469,8 +497,7 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     P.rows.clear();
     P.batches.clear();
     if (q.layout != RBC_LAYOUT_DENSE && P.any_solid && P.nx <= 32760 && P.ny < (1 << 20)) {
-        const int node_bytes = kQ * pop_bytes(P.prec) + (nc > 0 ? 16 : 0) + 4;
-        const bool ok = build_compact(P, g->solid, node_bytes);
+        const bool ok = build_compact(P, g->solid, pop_bytes(P.prec), nc > 0);
         if (ok && (q.layout == RBC_LAYOUT_COMPACT || (long long)P.M * 10 <= (long long)N * 9)) {
             P.compact = true;
             P.use_list = false;
@@ -480,6 +507,8 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
         if (!P.compact) {
             P.rows.clear();
             P.batches.clear();
+            P.bx.clear();
+            P.pool.clear();
         }
     }
     if (q.layout == RBC_LAYOUT_COMPACT && !P.compact)
@@ -519,6 +548,8 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.rows = P.compact ? cv.take<int4>((size_t)P.ny * P.nz) : nullptr;
     d.nbatches = P.compact ? (int)P.batches.size() : 0;
     d.lb_batches = P.compact ? cv.take<int4>((size_t)std::max(d.nbatches, 1)) : nullptr;
+    d.lb_bx = P.compact ? cv.take<int2>((size_t)std::max(d.nbatches, 1)) : nullptr;
+    d.lb_pool = P.compact ? cv.take<int2>(std::max(P.pool.size(), (size_t)1)) : nullptr;
     d.lb_stage_bytes = P.compact ? P.stage_bytes : 0;
     d.nwss = P.nwss;
     d.wss_node = cv.take<int>((size_t)std::max(P.nwss, 1));
@@ -573,6 +604,7 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.budget_part = cv.take<double>(8 * (size_t)P.budget_blocks);
     d.budget_out = cv.take<double>(16);
     d.accum = cv.take<double>(8);
+    d.profile = cv.take<double>((size_t)std::max(P.nx, std::max(P.ny, P.nz)));
     return (cv.off + 255) & ~size_t(255);
 }
 
@@ -618,6 +650,8 @@ struct rbc_handle {
     cudaEvent_t join2_ev = nullptr;
     int64_t step = 0;
     int64_t wss_samples = 0;
+    int64_t profile_samples = 0;
+    int profile_axis = -1;
     int timing_cap = 0, timing_used = 0;
     bool lb_first = false;  // graph order of the step: lattice pass before the side kernels
     std::vector<cudaEvent_t> ev;  // 3 per timed step: before the cell kernel, after it, after the lattice pass
@@ -913,6 +947,10 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
                                    cudaMemcpyHostToDevice, s));
             RBC_CU(cudaMemcpyAsync(const_cast<int4 *>(d.lb_batches), P.batches.data(), P.batches.size() * sizeof(int4),
                                    cudaMemcpyHostToDevice, s));
+            RBC_CU(cudaMemcpyAsync(const_cast<int2 *>(d.lb_bx), P.bx.data(), P.bx.size() * sizeof(int2),
+                                   cudaMemcpyHostToDevice, s));
+            RBC_CU(cudaMemcpyAsync(const_cast<int2 *>(d.lb_pool), P.pool.data(), P.pool.size() * sizeof(int2),
+                                   cudaMemcpyHostToDevice, s));
         } else if (d.links) {
             // per-node link word in the library's velocity ordering: bit p set
             // when the downstream node x + c_p is solid (fluid nodes), bit 29 /
@@ -968,6 +1006,7 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
         RBC_CU(cudaMemsetAsync(d.lb_work, 0, 2 * sizeof(int), s));
         RBC_CU(cudaMemsetAsync(d.lb_step, 0, sizeof(unsigned long long), s));
         RBC_CU(cudaMemsetAsync(d.accum, 0, 8 * sizeof(double), s));
+        RBC_CU(cudaMemsetAsync(d.profile, 0, sizeof(double) * (size_t)std::max(P.nx, std::max(P.ny, P.nz)), s));
         RBC_CU(cudaMemsetAsync(d.clamps, 0, sizeof(unsigned long long), s));
         const int n = P.nc;
         if (n > 0) {
@@ -1054,6 +1093,7 @@ static int check_flags(rbc_handle *h)
                         ((flags[FLAG_OVERFLOW] & OVF_NBR) ? " neighbour list" : "") +
                         ((flags[FLAG_OVERFLOW] & OVF_BOX) ? " shape box" : ""));
     if (flags[FLAG_UNSTABLE]) return fail(&h->err, RBC_EUNSTABLE, "NaN or |u| above the Mach guard");
+    if (flags[FLAG_TIMEOUT]) return fail(&h->err, RBC_ETIMEOUT, "a bounded wait of the lattice pass ran out");
     return RBC_OK;
 }
 
@@ -1171,6 +1211,7 @@ int rbc_stats(rbc_handle *h, rbc_stats_t *out)
     out->power = b[9];
     if (out->overflow) return fail(&h->err, RBC_ENOMEM, "a device capacity was exceeded");
     if (out->unstable) return fail(&h->err, RBC_EUNSTABLE, "NaN or |u| above the Mach guard");
+    if (flags[FLAG_TIMEOUT]) return fail(&h->err, RBC_ETIMEOUT, "a bounded wait of the lattice pass ran out");
     return RBC_OK;
 }
 
@@ -1386,6 +1427,49 @@ int rbc_wss_accumulate(rbc_handle *h)
     launch_wss(h->d, h->stream);
     RBC_CU(cudaGetLastError());
     h->wss_samples++;
+    return RBC_OK;
+}
+
+int rbc_set_wait_limit(rbc_handle *h, int64_t cycles, int starve_batch)
+{
+    if (!h || cycles < 0 || starve_batch < -1) return fail(h ? &h->err : nullptr, RBC_EINVAL, "bad argument");
+    if (h->d.lb_grid <= 0) return fail(&h->err, RBC_EINVAL, "the lattice pass of this solve is not staged");
+    h->d.wait_cycles = cycles;
+    h->d.starve_batch = starve_batch;
+    return recapture_steps(h);
+}
+
+int rbc_profile_accumulate(rbc_handle *h, int axis)
+{
+    if (!h) return fail(nullptr, RBC_EINVAL, "handle is NULL");
+    if (axis < 0 || axis > 2) return fail(&h->err, RBC_EINVAL, "axis must be 0, 1 or 2");
+    if (h->d.nc <= 0) return fail(&h->err, RBC_EINVAL, "no cells");
+    if (axis != h->profile_axis) {
+        const int nb = std::max(h->d.nx, std::max(h->d.ny, h->d.nz));
+        RBC_CU(cudaMemsetAsync(h->d.profile, 0, sizeof(double) * (size_t)nb, h->stream));
+        h->profile_axis = axis;
+        h->profile_samples = 0;
+    }
+    launch_profile(h->d, axis, h->stream);
+    RBC_CU(cudaGetLastError());
+    h->profile_samples++;
+    return RBC_OK;
+}
+
+int rbc_profile(rbc_handle *h, double *counts, int nbins, int *axis, int64_t *samples)
+{
+    if (!h || !counts || !axis || !samples) return fail(h ? &h->err : nullptr, RBC_EINVAL, "NULL argument");
+    *axis = h->profile_axis;
+    *samples = h->profile_samples;
+    if (h->profile_axis < 0) {
+        for (int k = 0; k < nbins; ++k) counts[k] = 0.0;
+        return RBC_OK;
+    }
+    const int n = h->profile_axis == 0 ? h->d.nx : (h->profile_axis == 1 ? h->d.ny : h->d.nz);
+    if (nbins < n) return fail(&h->err, RBC_EINVAL, "nbins is smaller than the box along the axis");
+    RBC_CU(cudaMemcpyAsync(counts, h->d.profile, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, h->stream));
+    RBC_CU(cudaStreamSynchronize(h->stream));
+    for (int k = n; k < nbins; ++k) counts[k] = 0.0;
     return RBC_OK;
 }
 

@@ -1301,6 +1301,26 @@ static BinArgs bin_args(const Dev &d, const Params &p)
     return g;
 }
 
+// Cell-centre profile along one axis: every cell adds 1 to the 1-lattice-
+// unit bin floor(R_axis) of its centre (positions live in [0, n_axis)).
+// FP64 atomics of whole numbers: the sums are exact and independent of
+// their order.
+__global__ void k_profile(const double *__restrict__ R, int nc, int axis, int nbins, double *__restrict__ prof)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const double r = R[3 * i + axis];
+    if (!(r >= 0.0 && r < (double)nbins)) return;  // non-finite or outside: not counted
+    atomicAdd(&prof[(int)r], 1.0);
+}
+
+void launch_profile(const Dev &d, int axis, cudaStream_t s)
+{
+    if (d.nc <= 0) return;
+    const int nbins = axis == 0 ? d.nx : (axis == 1 ? d.ny : d.nz);
+    k_profile<<<(d.nc + 255) / 256, 256, 0, s>>>(d.R, d.nc, axis, nbins, d.profile);
+}
+
 void launch_bin(const Dev &d, const Params &p, cudaStream_t s)
 {
     if (d.nc == 0) return;

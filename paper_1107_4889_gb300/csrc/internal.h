@@ -59,6 +59,8 @@ struct Dev {
     int M, zero_entry;
     const int4 *rows;
     const int4 *lb_batches;  // compact lattice pass: (z, y0 | nb << 20, C0 | C1 << 16, X0 | W << 16)
+    const int2 *lb_bx;       // per batch: (first copy descriptor in lb_pool, bytes of its copies)
+    const int2 *lb_pool;     // per batch row, 9 copy descriptors (first entry, window offset | count << 16)
     int nbatches;
     // wall shear stress: wall-adjacent fluid nodes, unit normals into the
     // fluid (3 floats each), time sums of the tangential traction
@@ -101,6 +103,7 @@ struct Dev {
     double *budget_part;            // budget_blocks * 8
     double *budget_out;             // 16: mass, p_fluid(3), max|u|, NaN count, p_cells(3), work rate
     double *accum;                  // 8: time-average sums of a served solve (k_budget_final)
+    double *profile;                // max(nx, ny, nz): cell-centre counts per 1-lu bin (k_profile)
     int budget_blocks;
     // lattice pass launch: grid of the row-staged kernel (0: one thread per node)
     int lb_grid, lb_stages;
@@ -110,6 +113,8 @@ struct Dev {
     int wt_grid = 0, gb_grid = 0;  // blocks of the shape-list and Gay-Berne launches (0: one per group)
     size_t lb_smem;
     int lb_stage_bytes;  // compact lattice pass: bytes of one stage (its largest batch)
+    long long wait_cycles = 0;  // bound of the staged passes' mbarrier waits (0: the default, ~2 s)
+    int starve_batch = -1;      // fault injection: a batch the staged passes never fill (-1: none)
 };
 
 struct Params {
@@ -180,6 +185,7 @@ void launch_bin_packed(const CellPackDesc &k, int prio, cudaStream_t s);
 void launch_gb_packed(const CellPackDesc &k, int prio, cudaStream_t s);
 void launch_weights_packed(const CellPackDesc &k, const Params &p, int buf, int prio, cudaStream_t s);
 void launch_bin(const Dev &d, const Params &p, cudaStream_t s);
+void launch_profile(const Dev &d, int axis, cudaStream_t s);
 void launch_gb(const Dev &d, const Params &p, cudaStream_t s);
 void launch_weights(const Dev &d, const Params &p, int buf, cudaStream_t s);
 void launch_cells(const Dev &d, const Params &p, int buf, cudaStream_t s);

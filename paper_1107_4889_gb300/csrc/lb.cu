@@ -41,6 +41,7 @@ struct LbArgs {
     void *dst;
     const uint32_t *links;
     const int4 *rows;  // compact layout: row table (internal.h), else null
+    const int2 *pool;  // compact lattice pass: per batch row, nine copy descriptors (produce_compact)
     float4 *G, *U, *S;  // node-major: force density + hematocrit sum, velocity, stress (2 per node)
     int *flags;
     int *work;                 // [0] next batch, [1] CTAs done; zero at launch, reset by the last CTA
@@ -53,6 +54,8 @@ struct LbArgs {
     float in_cx, in_cy, in_ir2, in_umax;  // inlet profile
     uint32_t key0, key1;  // seed of the stochastic rounding
     int stochastic;
+    long long wait_cycles;  // bound of the pipeline's mbarrier waits (clock64 cycles)
+    int starve_batch;       // fault injection: this batch's copies are never issued (-1: none)
 };
 
 // Storage entry of the lattice node (x, y, z) (wrapped coordinates): the node
@@ -566,9 +569,9 @@ __device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void *src, uin
         : "memory");
 }
 
-// Wait for phase `parity` of the mbarrier, for at most kWaitCycles; false on
-// timeout (the caller raises the timeout flag).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// Wait for phase `parity` of the mbarrier, for at most `limit` cycles; false
+// on timeout (the caller raises the timeout flag).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = kWaitCycles)
 {
     const long long t0 = clock64();
     while (true) {
@@ -581,7 +584,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -722,9 +725,10 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
         const int lane = threadIdx.x - kStConsumers;
         int it = 0;
         bool ok = true;
+        unsigned issued = 0;  // stages whose last fill has copies issued
         for (;; ++it) {
             const int stage = it % ns;
-            if (it >= ns && !mbar_wait(smem_addr(&empty[stage]), (uint32_t)((it / ns - 1) & 1))) {
+            if (it >= ns && !mbar_wait(smem_addr(&empty[stage]), (uint32_t)((it / ns - 1) & 1), a.wait_cycles)) {
                 if (lane == 0) atomicOr(&a.flags[FLAG_TIMEOUT], 1);
                 ok = false;
                 break;
@@ -741,12 +745,18 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
                 break;
             }
             if (lane == 0) s_batch[stage] = batch;
+            if (batch == a.starve_batch) {  // fault injection: the stage never fills
+                issued &= ~(1u << stage);
+                continue;
+            }
+            issued |= 1u << stage;
             produce_batch<St, CELLS>(a, L, batch, smraw + (size_t)stage * L.stage_bytes, bar, lane);
         }
         if (!ok) {
-            // let the copies still in flight land before the CTA's memory goes away
+            // let the copies still in flight land before the CTA's memory
+            // goes away (with the full bound, whatever the pipeline's)
             for (int j = it > ns ? it - ns : 0; j < it; ++j)
-                mbar_wait(smem_addr(&full[j % ns]), (uint32_t)((j / ns) & 1));
+                if ((issued >> (j % ns)) & 1u) mbar_wait(smem_addr(&full[j % ns]), (uint32_t)((j / ns) & 1));
         }
         // the last CTA out resets the counters for the next launch and
         // advances the pass counter (every CTA read it before its barrier)
@@ -770,7 +780,7 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
     const int x_step = kStConsumers % nx, b_step = kStConsumers / nx;
     for (int it = 0;; ++it) {
         const int stage = it % ns;
-        if (!mbar_wait(smem_addr(&full[stage]), (uint32_t)((it / ns) & 1))) {
+        if (!mbar_wait(smem_addr(&full[stage]), (uint32_t)((it / ns) & 1), a.wait_cycles)) {
             if (lane == 0) atomicOr(&a.flags[FLAG_TIMEOUT], 1);
             break;
         }
@@ -804,66 +814,48 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
 // upstream row's span (every node one link away from a fluid node is
 // stored), so the parts of the window outside a span are never read.
 // ---------------------------------------------------------------------------
+// Producer side of one compact batch.  The set-up precomputed, for every
+// batch row b and each of its nine upstream rows u = (dy + 1) + 3 (dz + 1)
+// (the row (y + dy, z + dz) that the speeds with c_y = -dy, c_z = -dz pull
+// from), the part of that row's span inside the window: its first entry and
+// (offset in the window | entry count << 16); and per batch the pool offset
+// of these descriptors and the bytes of all its copies.  Lane j takes
+// descriptor j and copies that part of each of its speeds' planes (and, for
+// the batch row's own row u = 4, of G / theta and the link words), so the
+// warp issues a batch with one coalesced load and no dependent lookups.
 template <typename St, bool CELLS>
-__device__ __forceinline__ uint32_t compact_copy(const LbArgs &a, int4 bd, int j, unsigned char *base,
-                                                 const void *&gsrc, uint32_t &sdst)
-{
-    const int z = bd.x, y0 = bd.y & 0xFFFFF, nb = (int)((uint32_t)bd.y >> 20);
-    const int X0 = bd.w & 0xFFFF, W = (int)((uint32_t)bd.w >> 16);
-    const int k = j / nb, b = j - k * nb;
-    int r;
-    size_t esz;
-    const char *g;
-    unsigned char *sb;
-    const size_t pop_bytes = (size_t)kQ * nb * W * sizeof(St);
-    if (k < kQ) {
-        r = wrapm(y0 + b - cy(k), a.ny) + a.ny * wrapm(z - cz(k), a.nz);
-        esz = sizeof(St);
-        g = static_cast<const char *>(a.src) + (size_t)k * (size_t)a.Np * sizeof(St);
-        sb = base + (size_t)(k * nb + b) * W * sizeof(St);
-    } else if (CELLS && k == kQ) {
-        r = y0 + b + a.ny * z;
-        esz = sizeof(float4);
-        g = reinterpret_cast<const char *>(a.G);
-        sb = base + pop_bytes + (size_t)b * W * sizeof(float4);
-    } else {
-        r = y0 + b + a.ny * z;
-        esz = sizeof(uint32_t);
-        g = reinterpret_cast<const char *>(a.links);
-        sb = base + pop_bytes + (CELLS ? (size_t)nb * W * sizeof(float4) : 0) + (size_t)b * W * sizeof(uint32_t);
-    }
-    const int4 rt = a.rows[r];
-    const int lo = max(X0, rt.y), hi = min(X0 + W, rt.z);
-    if (hi <= lo) return 0u;
-    gsrc = g + (size_t)(rt.x + lo - rt.y) * esz;
-    sdst = smem_addr(sb + (size_t)(lo - X0) * esz);
-    return (uint32_t)((size_t)(hi - lo) * esz);
-}
-
-template <typename St, bool CELLS>
-__device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, unsigned char *base, uint32_t bar, int lane)
+__device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, int2 bx, unsigned char *base,
+                                                uint32_t bar, int lane)
 {
     const int nb = (int)((uint32_t)bd.y >> 20);
-    const int ncopies = (kQ + (CELLS ? 1 : 0) + 1) * nb;
-    uint32_t bytes = 0;
-    for (int j = lane; j < ncopies; j += 32) {
-        const void *g;
-        uint32_t sd;
-        bytes += compact_copy<St, CELLS>(a, bd, j, base, g, sd);
-    }
-    bytes = __reduce_add_sync(0xffffffffu, bytes);
-    if (lane == 0) mbar_expect_tx(bar, bytes);
+    const int W = (int)((uint32_t)bd.w >> 16);
+    if (lane == 0) mbar_expect_tx(bar, (uint32_t)bx.y);
     __syncwarp();
     const uint64_t once = l2_evict_first();
-    for (int j = lane; j < ncopies; j += 32) {
-        const void *g = nullptr;
-        uint32_t sd = 0;
-        const uint32_t nbytes = compact_copy<St, CELLS>(a, bd, j, base, g, sd);
-        if (nbytes == 0) continue;
-        if (j < kQ * nb)
-            bulk_g2s_hint(sd, g, nbytes, bar, once);
-        else
-            bulk_g2s(sd, g, nbytes, bar);
+    const size_t pop_bytes = (size_t)kQ * nb * W * sizeof(St);
+    for (int j = lane; j < 9 * nb; j += 32) {
+        const int2 e = a.pool[bx.x + j];
+        const int count = (int)((uint32_t)e.y >> 16);
+        if (count == 0) continue;
+        const int at = e.y & 0xFFFF;  // window offset of the first entry
+        const int b = j / 9, u = j - 9 * b;
+        const int dy = u % 3 - 1, dz = u / 3 - 1;
+        const uint32_t bar_ = bar;
+        for_speeds<0, kQ>([&](auto pc) {
+            constexpr int p = decltype(pc)::value;
+            if (cy(p) != -dy || cz(p) != -dz) return;
+            const St *g = static_cast<const St *>(a.src) + (size_t)p * (size_t)a.Np + (size_t)e.x;
+            bulk_g2s_hint(smem_addr(base + ((size_t)(p * nb + b) * W + at) * sizeof(St)), g,
+                          (uint32_t)(count * (int)sizeof(St)), bar_, once);
+        });
+        if (u == 4) {
+            if (CELLS)
+                bulk_g2s(smem_addr(base + pop_bytes + ((size_t)b * W + at) * sizeof(float4)), a.G + e.x,
+                         (uint32_t)(count * (int)sizeof(float4)), bar_);
+            bulk_g2s(smem_addr(base + pop_bytes + (CELLS ? (size_t)nb * W * sizeof(float4) : 0) +
+                               ((size_t)b * W + at) * sizeof(uint32_t)),
+                     a.links + e.x, (uint32_t)(count * (int)sizeof(uint32_t)), bar_);
+        }
     }
 }
 
@@ -927,7 +919,8 @@ __device__ __forceinline__ void consume_compact(const LbArgs &a, int4 bd, const 
 // at least two CTAs per SM: the pass and the side kernels share the SMs
 template <typename St, bool CELLS, bool SIGMA>
 __global__ void __launch_bounds__(kStThreads, 2)
-    k_lb_compact(LbArgs a, const int4 *__restrict__ batches, int nbatches, int ns, int stage_bytes)
+    k_lb_compact(LbArgs a, const int4 *__restrict__ batches, const int2 *__restrict__ bxs, int nbatches, int ns,
+                 int stage_bytes)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages];
@@ -945,20 +938,30 @@ __global__ void __launch_bounds__(kStThreads, 2)
 
     if (threadIdx.x >= kStConsumers) {
         // producer warp: claims batches from the global counter (see
-        // k_lb_staged); s_desc[stage].x = -1 tells the consumers to stop
+        // k_lb_staged), each one a batch ahead so that the atomic and the
+        // batch's descriptor loads overlap the wait for a free stage;
+        // s_desc[stage].x = -1 tells the consumers to stop
         const int lane = threadIdx.x - kStConsumers;
         int it = 0;
         bool ok = true;
+        unsigned issued = 0;  // stages whose last fill has copies issued
+        int next = 0;
+        if (lane == 0) next = atomicAdd(&a.work[0], 1);
         for (;; ++it) {
             const int stage = it % ns;
-            if (it >= ns && !mbar_wait(smem_addr(&empty[stage]), (uint32_t)((it / ns - 1) & 1))) {
+            const int batch = __shfl_sync(0xffffffffu, next, 0);
+            int4 bd = make_int4(-1, 0, 0, 0);
+            int2 bx = make_int2(0, 0);
+            if (batch < nbatches) {
+                if (lane == 0) next = atomicAdd(&a.work[0], 1);
+                bd = batches[batch];
+                bx = bxs[batch];
+            }
+            if (it >= ns && !mbar_wait(smem_addr(&empty[stage]), (uint32_t)((it / ns - 1) & 1), a.wait_cycles)) {
                 if (lane == 0) atomicOr(&a.flags[FLAG_TIMEOUT], 1);
                 ok = false;
                 break;
             }
-            int batch = 0;
-            if (lane == 0) batch = atomicAdd(&a.work[0], 1);
-            batch = __shfl_sync(0xffffffffu, batch, 0);
             const uint32_t bar = smem_addr(&full[stage]);
             if (batch >= nbatches) {
                 if (lane == 0) {
@@ -967,14 +970,19 @@ __global__ void __launch_bounds__(kStThreads, 2)
                 }
                 break;
             }
-            const int4 bd = batches[batch];
             if (lane == 0) s_desc[stage] = bd;
-            produce_compact<St, CELLS>(a, bd, smraw + (size_t)stage * stage_bytes, bar, lane);
+            if (batch == a.starve_batch) {  // fault injection: the stage never fills
+                issued &= ~(1u << stage);
+                continue;
+            }
+            issued |= 1u << stage;
+            produce_compact<St, CELLS>(a, bd, bx, smraw + (size_t)stage * stage_bytes, bar, lane);
         }
         if (!ok) {
-            // let the copies still in flight land before the CTA's memory goes away
+            // let the copies still in flight land before the CTA's memory
+            // goes away (with the full bound, whatever the pipeline's)
             for (int j = it > ns ? it - ns : 0; j < it; ++j)
-                mbar_wait(smem_addr(&full[j % ns]), (uint32_t)((j / ns) & 1));
+                if ((issued >> (j % ns)) & 1u) mbar_wait(smem_addr(&full[j % ns]), (uint32_t)((j / ns) & 1));
         }
         if (lane == 0) {
             __threadfence();
@@ -992,7 +1000,7 @@ __global__ void __launch_bounds__(kStThreads, 2)
     const unsigned long long step = s_step;
     for (int it = 0;; ++it) {
         const int stage = it % ns;
-        if (!mbar_wait(smem_addr(&full[stage]), (uint32_t)((it / ns) & 1))) {
+        if (!mbar_wait(smem_addr(&full[stage]), (uint32_t)((it / ns) & 1), a.wait_cycles)) {
             if (lane == 0) atomicOr(&a.flags[FLAG_TIMEOUT], 1);
             break;
         }
@@ -1459,8 +1467,8 @@ struct LaunchOp {
         if constexpr (W) {
             if (d.compact) {
                 if (d.lb_grid > 0)
-                    k_lb_compact<St, C, S_><<<d.lb_grid, kStThreads, d.lb_smem, s>>>(a, d.lb_batches, d.nbatches,
-                                                                                     d.lb_stages, d.lb_stage_bytes);
+                    k_lb_compact<St, C, S_><<<d.lb_grid, kStThreads, d.lb_smem, s>>>(
+                        a, d.lb_batches, d.lb_bx, d.nbatches, d.lb_stages, d.lb_stage_bytes);
                 return;
             }
         }
@@ -1553,6 +1561,7 @@ static LbArgs lb_args(const Dev &d, const Params &p, int parity)
     a.dst = d.pops[parity ^ 1];
     a.links = d.links;
     a.rows = d.rows;
+    a.pool = d.lb_pool;
     a.G = d.G;
     a.U = d.U;
     a.S = d.S;
@@ -1581,6 +1590,8 @@ static LbArgs lb_args(const Dev &d, const Params &p, int parity)
     a.key0 = (uint32_t)(d.seed & 0xffffffffull);
     a.key1 = (uint32_t)(d.seed >> 32);
     a.stochastic = d.stochastic;
+    a.wait_cycles = d.wait_cycles > 0 ? d.wait_cycles : kWaitCycles;
+    a.starve_batch = d.starve_batch;
     return a;
 }
 

@@ -94,6 +94,7 @@ class rbc_tune_report(ctypes.Structure):
 EXPORTS = ["rbc_default_params", "rbc_workspace_size", "rbc_init", "rbc_step", "rbc_fields",
            "rbc_stats", "rbc_cell_diag", "rbc_neighbors", "rbc_set_timing", "rbc_kernel_times",
            "rbc_autotune", "rbc_wss_accumulate", "rbc_wss", "rbc_launches_per_step", "rbc_layout", "rbc_fluid_nodes",
+           "rbc_profile_accumulate", "rbc_profile", "rbc_set_wait_limit",
            "rbc_neighbors_noalloc", "rbc_server_create", "rbc_server_submit",
            "rbc_server_poll", "rbc_server_results", "rbc_server_clock", "rbc_server_free", "rbc_free",
            "rbc_last_error"]
@@ -130,6 +131,12 @@ def load(path: str = LIB_PATH):
     L.rbc_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.rbc_kernel_times.argtypes = [ctypes.c_void_p, _D, _I64]
     L.rbc_launches_per_step.argtypes = [ctypes.c_void_p]
+    L.rbc_set_wait_limit.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
+    L.rbc_set_wait_limit.restype = ctypes.c_int
+    L.rbc_profile_accumulate.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.rbc_profile_accumulate.restype = ctypes.c_int
+    L.rbc_profile.argtypes = [ctypes.c_void_p, _D, ctypes.c_int, _I, _I64]
+    L.rbc_profile.restype = ctypes.c_int
     L.rbc_layout.argtypes = [ctypes.c_void_p, _I, _I64, _I64]
     L.rbc_layout.restype = ctypes.c_int
     L.rbc_fluid_nodes.argtypes = [ctypes.c_void_p, _I64, ctypes.c_int64, _I64]
@@ -345,6 +352,21 @@ def rbc_launches_per_step(h) -> int:
     return int(load().rbc_launches_per_step(h))
 
 
+def rbc_set_wait_limit(h, cycles: int, starve_batch: int = -1):
+    _check(load().rbc_set_wait_limit(h, int(cycles), int(starve_batch)), h)
+
+
+def rbc_profile_accumulate(h, axis: int = 1):
+    _check(load().rbc_profile_accumulate(h, int(axis)), h)
+
+
+def rbc_profile(h, nbins: int):
+    counts = np.zeros(max(nbins, 1))
+    axis, samples = ctypes.c_int(-1), ctypes.c_int64(0)
+    _check(load().rbc_profile(h, _dp(counts), int(nbins), ctypes.byref(axis), ctypes.byref(samples)), h)
+    return counts[:nbins], int(axis.value), int(samples.value)
+
+
 def rbc_layout(h):
     c, e, f = ctypes.c_int(0), ctypes.c_int64(0), ctypes.c_int64(0)
     _check(load().rbc_layout(h, ctypes.byref(c), ctypes.byref(e), ctypes.byref(f)), h)
@@ -388,7 +410,8 @@ class Solver:
             raise RuntimeError("the RBC solver needs a CUDA GPU")
         load()
         self.device = torch.device("cuda" if device is None else device)
-        self.N = int(geometry["nx"]) * int(geometry["ny"]) * int(geometry["nz"])
+        self.dims = (int(geometry["nx"]), int(geometry["ny"]), int(geometry["nz"]))
+        self.N = self.dims[0] * self.dims[1] * self.dims[2]
         self.n = 0 if cells is None else int(np.asarray(cells["pos"]).shape[0])
         with torch.cuda.device(self.device):
             # a stream of its own: the legacy default stream cannot be
@@ -429,6 +452,18 @@ class Solver:
 
     def layout(self):
         return rbc_layout(self.handle)
+
+    def set_wait_limit(self, cycles, starve_batch=-1):
+        rbc_set_wait_limit(self.handle, cycles, starve_batch)
+
+    def profile_accumulate(self, axis=1):
+        rbc_profile_accumulate(self.handle, axis)
+
+    def profile(self):
+        """(time-averaged cell-centre count per 1-lu bin, axis, samples)."""
+        counts, axis, samples = rbc_profile(self.handle, max(self.dims))
+        n = self.dims[axis] if axis >= 0 else 0
+        return (counts[:n] / max(samples, 1)), axis, samples
 
     def fluid_nodes(self):
         """Lattice indices of the fluid nodes in the library's storage order."""

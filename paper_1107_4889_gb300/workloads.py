@@ -377,6 +377,21 @@ def tube_workload(n=256, radius=120.0, ncells=51846, body_force=None, seed=SEED_
     return geom, cells_dict(pos, quat), params(**pover)
 
 
+def tube_slab(nz=20, **kw):
+    """A slab of the tube workload: its cross-section (radius 120 in 256 x
+    256, the same drive) over nz planes, periodic along z, with the cells
+    of the slot layers whose centres lie below nz - 1.65 (the first six at
+    nz = 20, each layer's slots as in the full tube; the layers across the
+    periodic seam stay more than a face-to-face contact apart).  The same
+    geometry and cell density at 1/12.8 of the size: a bounded sample of
+    the tube for timing the oracle."""
+    geom, cells, params = tube_workload(**kw)
+    keep = cells["pos"][:, 2] < nz - 1.65
+    slab = tube(geom["nx"], 120.0 if "radius" not in kw else kw["radius"], length=nz,
+                body_force=geom["body_force"])
+    return slab, cells_dict(cells["pos"][keep], cells["quat"][keep]), params
+
+
 def tube_hematocrit(geom, ncells, semi_axes=(4.0, 4.0, 1.5)):
     """Cell volume fraction of the fluid nodes (the lumen)."""
     a = semi_axes
