@@ -1092,8 +1092,9 @@ static int check_flags(rbc_handle *h)
                     std::string("capacity exceeded:") + ((flags[FLAG_OVERFLOW] & OVF_BIN) ? " cell-list bin" : "") +
                         ((flags[FLAG_OVERFLOW] & OVF_NBR) ? " neighbour list" : "") +
                         ((flags[FLAG_OVERFLOW] & OVF_BOX) ? " shape box" : ""));
-    if (flags[FLAG_UNSTABLE]) return fail(&h->err, RBC_EUNSTABLE, "NaN or |u| above the Mach guard");
+    // a timed-out pass leaves part of the lattice unupdated: report the cause
     if (flags[FLAG_TIMEOUT]) return fail(&h->err, RBC_ETIMEOUT, "a bounded wait of the lattice pass ran out");
+    if (flags[FLAG_UNSTABLE]) return fail(&h->err, RBC_EUNSTABLE, "NaN or |u| above the Mach guard");
     return RBC_OK;
 }
 
@@ -1209,9 +1210,9 @@ int rbc_stats(rbc_handle *h, rbc_stats_t *out)
     out->unstable = flags[FLAG_UNSTABLE] != 0 || b[5] > 0.0;
     out->overflow = flags[FLAG_OVERFLOW];
     out->power = b[9];
+    if (flags[FLAG_TIMEOUT]) return fail(&h->err, RBC_ETIMEOUT, "a bounded wait of the lattice pass ran out");
     if (out->overflow) return fail(&h->err, RBC_ENOMEM, "a device capacity was exceeded");
     if (out->unstable) return fail(&h->err, RBC_EUNSTABLE, "NaN or |u| above the Mach guard");
-    if (flags[FLAG_TIMEOUT]) return fail(&h->err, RBC_ETIMEOUT, "a bounded wait of the lattice pass ran out");
     return RBC_OK;
 }
 
