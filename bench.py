@@ -554,6 +554,73 @@ def run_stats(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mobility(args):
+    """The mobility test of Sec. 3: one cell (M = 10, I = 1000, no viscosity
+    contrast) in a 60^3 periodic box of quiescent fluid, pushed by a constant
+    external force (the counter-force spread uniformly over the fluid keeps
+    the total momentum at zero) or turned by a constant external torque.
+    The terminal velocity (angular velocity), averaged over the last third
+    of the run, over the push is the mobility mu; against the bare mobility
+    1 / (M gamma_T) (1 / (I gamma_R)) it is a line whose intercept at
+    infinite friction is the mesh-induced mobility the paper reports
+    (1 / (M gamma_T^mesh) = 6.6 frontal, 10.3 side-wise; gamma_R^mesh =
+    1/44 about the smallest radius, 1/38 about the largest).  Frontal: push
+    along the short axis; side-wise: along a long axis."""
+    import torch
+
+    from paper_1107_4889_gb300 import build as B
+    from paper_1107_4889_gb300.rbc import Solver
+
+    B.build()
+    torch.cuda.set_device(0)
+    L, steps = 60, args.steps
+    N = L ** 3
+    gammas = [0.05, 0.1, 0.2, 0.4, 0.8]
+    base = dict(delta=0.0, alpha_tt=0.0)
+    out = {}
+    cases = {"frontal": ("force", 2), "side": ("force", 0), "spin_smallest_radius": ("torque", 2),
+             "spin_largest_radius": ("torque", 0)}
+    for name, (kind, axis) in cases.items():
+        rows = []
+        for g in gammas:
+            push = np.zeros(3)
+            push[axis] = 1e-5 if kind == "force" else 1e-3
+            cells = wl.cells_dict(np.array([[30.2, 29.7, 30.4]]), np.array([[1.0, 0.0, 0.0, 0.0]]))
+            cells["force_ext" if kind == "force" else "torque_ext"] = push[None, :]
+            geom = wl.periodic_box(L, body_force=tuple(-push / N) if kind == "force" else (0.0, 0.0, 0.0))
+            p = wl.params(**base, gamma_T=g, gamma_R=g)
+            s = Solver(geom, cells, p)
+            vals = []
+            done, chunk = 0, 100
+            while done < steps:
+                s.step(chunk)
+                done += chunk
+                if done > 2 * steps // 3:
+                    f = s.fields(rho=False, u=False)
+                    vals.append(f["vel"][0, axis] if kind == "force" else f["omega"][0, axis])
+            s.close()
+            mu = float(np.mean(vals)) / push[axis]
+            bare = 1.0 / ((p["mass"] if kind == "force" else p["inertia"][axis]) * g)
+            rows.append((g, bare, mu))
+        bare = np.array([r[1] for r in rows])
+        mu = np.array([r[2] for r in rows])
+        slope, icpt = np.polyfit(bare, mu, 1)
+        out[name] = {"gamma": gammas, "mu": [float(m) for m in mu], "bare_mobility": [float(b) for b in bare],
+                     "slope": float(slope), "intercept_mesh_mobility": float(icpt)}
+        if kind == "force":
+            out[name]["gamma_mesh"] = float(1.0 / (p["mass"] * icpt))
+            out[name]["a_T_mesh"] = float(1.0 / icpt / (6 * np.pi / 6.0))
+        else:
+            gm = 1.0 / (p["inertia"][axis] * icpt)
+            out[name]["gamma_R_mesh"] = float(gm)
+            out[name]["a_R_mesh"] = float((p["inertia"][axis] * gm / (8 * np.pi / 6.0)) ** (1.0 / 3.0))
+    line = {"metric": "mobility of one cell vs friction (Sec. 3 mobility test)",
+            "workload": f"one cell, 60^3 periodic box, M=10, I=1000, delta=0, {steps} steps per point",
+            "paper": {"frontal": 6.6, "side": 10.3, "gamma_R_mesh_smallest": 1 / 44, "gamma_R_mesh_largest": 1 / 38},
+            **out}
+    print(json.dumps(line), flush=True)
+
+
 def run_wss_map(args):
     """Time-averaged wall-shear-stress map of the workload (ybif by default)
     with binary16 storage against the FP32 run of the same seed: --steps
@@ -612,6 +679,7 @@ def parse_args(argv=None):
                     default="tube")
     ap.add_argument("--wss-map", action="store_true",
                     help="wall-shear-stress map of the workload, binary16 against FP32")
+    ap.add_argument("--mobility", action="store_true", help="mobility of one cell against the friction rates")
     ap.add_argument("--stats", action="store_true",
                     help="relative viscosity and near-wall hematocrit of the channel, binary16 against FP32")
     ap.add_argument("--no-cells", action="store_true", help="drop the workload's cells (lattice pass alone)")
@@ -644,6 +712,9 @@ def main():
         return
     if args.stats:
         run_stats(args)
+        return
+    if args.mobility:
+        run_mobility(args)
         return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

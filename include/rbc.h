@@ -79,13 +79,20 @@ typedef struct {
 
 /* Initial cell state (Sec. 2.2: Gamma_i = (R_i, Q_i, V_i, Omega_i)).  Host
  * arrays, copied at init: pos 3n (inside the box), quat 4n (need not be
- * normalised), vel 3n or NULL (zero), omega_body 3n or NULL (zero). */
+ * normalised), vel 3n or NULL (zero), omega_body 3n or NULL (zero).
+ * force_ext, torque_ext: 3n each or NULL (zero), a constant external force
+ * and torque (lab frame) on every cell, as the mobility tests of Sec. 3
+ * push a single cell; they act like the Gay-Berne forces (they enter the
+ * combined force and torque of App. A and are not part of the impulse
+ * returned to the fluid) and are reported with them in rbc_cell_diag. */
 typedef struct {
     int n;
     const double *pos;
     const double *quat;
     const double *vel;
     const double *omega_body;
+    const double *force_ext;
+    const double *torque_ext;
 } rbc_cells;
 
 /* Model parameters (paper values in brackets; rbc_default_params fills them).
@@ -224,8 +231,8 @@ int rbc_fields(rbc_handle *h, double *rho, double *u, double *cells_state);
 /* Compute the budgets on the device and copy them to *out (synchronising). */
 int rbc_stats(rbc_handle *h, rbc_stats_t *out);
 
-/* Per cell 21 doubles of the last step: F_mech(3) tau_mech(3) (Gay-Berne,
- * lab frame), u~(3) omega~(3) (Eqs. vel, vort), T^S(3) (Eq.
+/* Per cell 21 doubles of the last step: F_mech(3) tau_mech(3) (Gay-Berne
+ * plus any external force and torque, lab frame), u~(3) omega~(3) (Eqs. vel, vort), T^S(3) (Eq.
  * pheno_torque_diss), J(3) L(3) (hydrodynamic linear and lab angular impulse
  * returned to the fluid).  Host buffer; synchronises. */
 int rbc_cell_diag(rbc_handle *h, double *out);
@@ -291,6 +298,24 @@ int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out);
  * walls or stress. */
 int rbc_wss_accumulate(rbc_handle *h);
 int rbc_wss(rbc_handle *h, int64_t *node, double *tau, int64_t max, int64_t *n, int64_t *samples);
+
+/* Checkpoint and resume (the paper has no counterpart).  A checkpoint
+ * holds what the next step reads: the populations of the last pass, its
+ * velocity and stress fields, the cell state (R, q, V, Omega in FP64, the
+ * cached-step flags), the step count, the pass counter that keys the
+ * stochastic rounding and the clamp count; the cell list, the Gay-Berne
+ * forces and the shape lists are rebuilt from the poses on load.
+ * rbc_checkpoint_size gives its bytes; rbc_save synchronises and writes it
+ * to a caller-owned host buffer; rbc_load restores it into a handle
+ * initialised with the same problem (geometry, cells count, parameters,
+ * storage and layout; RBC_EINVAL otherwise) and synchronises.  A resumed
+ * run continues as the saved one would: bit for bit without cells, and with
+ * cells up to the rounding order of the spreading's float atomics.  The
+ * time averages of the server, of the wall shear stress and of the
+ * cell-centre profile start again. */
+int rbc_checkpoint_size(const rbc_handle *h, size_t *bytes);
+int rbc_save(rbc_handle *h, void *buf, size_t bytes);
+int rbc_load(rbc_handle *h, const void *buf, size_t bytes);
 
 /* Failure detection of the staged lattice passes (the paper has no
  * counterpart).  Their producer / consumer pipeline waits on shared-memory

@@ -815,6 +815,7 @@ struct orc_state {
     double *R, *Q, *V, *Om, *Fc, *Tc;
     int *have_cache;
     double *Fm, *Tm, *ut, *wt, *TS, *J, *L;
+    double *Fext, *Text; /* external force and torque per cell (lab), 3n each */
     long step, clamps;
     unsigned char *node_type; /* NULL: no open boundaries */
     double in_c[2], in_r, in_umax;
@@ -918,6 +919,12 @@ orc_state *orc_create(const orc_config *c)
     s->TS = dalloc(3 * nc);
     s->J = dalloc(3 * nc);
     s->L = dalloc(3 * nc);
+    s->Fext = dalloc(3 * nc);
+    s->Text = dalloc(3 * nc);
+    for (int k = 0; k < 3 * nc; k++) {
+        if (c->force_ext) s->Fext[k] = c->force_ext[k];
+        if (c->torque_ext) s->Text[k] = c->torque_ext[k];
+    }
     for (int i = 0; i < nc; i++) {
         for (int a = 0; a < 3; a++) {
             s->R[3 * i + a] = c->pos[3 * i + a];
@@ -957,6 +964,8 @@ void orc_destroy(orc_state *s)
     free(s->TS);
     free(s->J);
     free(s->L);
+    free(s->Fext);
+    free(s->Text);
     free(s);
 }
 
@@ -983,13 +992,20 @@ static double dist2(const double d[3])
 }
 
 /* Gay-Berne forces and torques (lab frame) on every cell: all cell pairs and
- * all cell-wall-particle pairs inside the candidate radii, by brute force. */
+ * all cell-wall-particle pairs inside the candidate radii, by brute force.
+ * A constant external force and torque on a cell (the push of the mobility
+ * tests of Sec. 3) is counted with them: like the Gay-Berne forces it is a
+ * non-hydrodynamic force, so it enters the combined force and torque of
+ * App. A and not the impulse the cell returns to the fluid. */
 static void mechanical_forces(orc_state *s)
 {
     int nc = s->nc;
     double *A = dalloc(9 * nc);
     for (int i = 0; i < nc; i++) shape_matrix(&s->Q[9 * i], s->a, &A[9 * i]);
-    for (int k = 0; k < 3 * nc; k++) s->Fm[k] = s->Tm[k] = 0.0;
+    for (int k = 0; k < 3 * nc; k++) {
+        s->Fm[k] = s->Fext[k];
+        s->Tm[k] = s->Text[k];
+    }
     double smin_cc = sqrt(2.0 * (2.0 * pow(fmin(s->a[0], fmin(s->a[1], s->a[2])), 2.0)));
     for (int i = 0; i < nc; i++)
         for (int j = i + 1; j < nc; j++) {

@@ -51,6 +51,9 @@ typedef struct {
      * ORC_NODE_OUTLET (pressure outlet, rho = 1) */
     const unsigned char *node_type;
     double inlet_center[2], inlet_radius, inlet_umax;
+    /* constant external force and torque on every cell (lab frame, 3n each,
+     * or NULL): the push of the mobility tests of Sec. 3 */
+    const double *force_ext, *torque_ext;
 } orc_config;
 
 #define ORC_NODE_INTERIOR 0

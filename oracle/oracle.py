@@ -49,7 +49,7 @@ class _Config(ctypes.Structure):
         ("seed", ctypes.c_ulonglong),
         ("body_force_wave", ctypes.c_double * 3),
         ("node_type", _U8), ("inlet_center", ctypes.c_double * 2), ("inlet_radius", ctypes.c_double),
-        ("inlet_umax", ctypes.c_double),
+        ("inlet_umax", ctypes.c_double), ("force_ext", _D), ("torque_ext", _D),
     ]
 
 
@@ -306,6 +306,8 @@ class Oracle:
         self._quat = _f64(cells["quat"], (4 * n,)) if n else np.zeros(4)
         self._vel = _f64(cells.get("vel"), (3 * n,)) if n and cells.get("vel") is not None else None
         self._om = _f64(cells.get("omega"), (3 * n,)) if n and cells.get("omega") is not None else None
+        self._fext = _f64(cells.get("force_ext"), (3 * n,)) if n and cells.get("force_ext") is not None else None
+        self._text = _f64(cells.get("torque_ext"), (3 * n,)) if n and cells.get("torque_ext") is not None else None
         c = _Config()
         c.nx, c.ny, c.nz = nx, ny, nz
         for a in range(3):
@@ -323,6 +325,7 @@ class Oracle:
         c.ncells = n
         c.pos, c.quat = _dp(self._pos), _dp(self._quat)
         c.vel, c.omega = _dp(self._vel), _dp(self._om)
+        c.force_ext, c.torque_ext = _dp(self._fext), _dp(self._text)
         nt = geometry.get("node_type")
         self._nt = _u8(np.asarray(nt).reshape(-1)) if nt is not None else None
         c.node_type = _u8p(self._nt)

@@ -56,6 +56,7 @@ struct Problem {
     std::vector<int4> rows, batches;
     std::vector<int2> bx, pool;  // per batch (pool offset, bytes); per batch row nine copy descriptors
     int stage_bytes = 0;
+    bool has_ext = false;  // cells carry an external force or torque
 };
 
 struct Carver {
@@ -220,7 +221,7 @@ bool build_compact(Problem &P, const uint8_t *solid, int esz, bool cells)
                 continue;
             }
             int nb = 1;
-            while (y + nb < ny && nb < 2047) {
+            while (y + nb < ny && nb < 16) {  // at most 16 rows (the pass stages their row bases)
                 const int r2 = y + nb + ny * z;
                 if (fh[r2] < 0) break;
                 const int d0 = std::min(c0, fl[r2]), d1 = std::max(c1, fh[r2]);
@@ -343,6 +344,11 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     if (nc < 0) return fail(err, RBC_EINVAL, "negative cell count");
     if (nc > 0 && (!c->pos || !c->quat)) return fail(err, RBC_EINVAL, "cell positions and quaternions are required");
     P.nc = nc;
+    P.has_ext = nc > 0 && (c->force_ext || c->torque_ext);
+    if (P.has_ext)
+        for (int k = 0; k < 3 * nc; ++k)
+            if ((c->force_ext && !std::isfinite(c->force_ext[k])) || (c->torque_ext && !std::isfinite(c->torque_ext[k])))
+                return fail(err, RBC_EINVAL, "non-finite external force or torque");
 
     Params &p = P.p;
     p.wave = 0;
@@ -566,6 +572,7 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.Af = cv.take<float>(6 * n);
     d.Fm = cv.take<double>(3 * n);
     d.Tm = cv.take<double>(3 * n);
+    d.ext = P.has_ext ? cv.take<double>(6 * n) : nullptr;
     d.have = cv.take<int>(n);
     d.diag = cv.take<double>(21 * n);
     d.hdr = cv.take<float>(kHdrWords * n);
@@ -1033,6 +1040,15 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
             RBC_CU(cudaMemcpyAsync(d.q, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice, s));
             RBC_CU(cudaMemcpyAsync(d.V, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice, s));
             RBC_CU(cudaMemcpyAsync(d.Om, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+            if (d.ext) {
+                std::vector<double> E(6 * (size_t)n, 0.0);
+                for (int i = 0; i < n; ++i)
+                    for (int a = 0; a < 3; ++a) {
+                        if (cells->force_ext) E[6 * i + a] = cells->force_ext[3 * i + a];
+                        if (cells->torque_ext) E[6 * i + 3 + a] = cells->torque_ext[3 * i + a];
+                    }
+                RBC_CU(cudaMemcpyAsync(d.ext, E.data(), E.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+            }
             RBC_CU(cudaMemsetAsync(d.have, 0, sizeof(int) * n, s));
             RBC_CU(cudaMemsetAsync(d.diag, 0, sizeof(double) * 21 * n, s));
             RBC_CU(cudaMemsetAsync(d.Fm, 0, sizeof(double) * 3 * n, s));
@@ -1428,6 +1444,129 @@ int rbc_wss_accumulate(rbc_handle *h)
     launch_wss(h->d, h->stream);
     RBC_CU(cudaGetLastError());
     h->wss_samples++;
+    return RBC_OK;
+}
+
+// Checkpoint: a header of 16 int64 words, then the populations of the
+// current parity, u, sigma (if stored) and the cell state R, q, V, Omega
+// (FP64) and the cached-step flags.
+namespace {
+constexpr int64_t kCkptMagic = 0x3154504b43434252LL;  // "RBCCKPT1"
+constexpr int kCkptWords = 16;
+
+size_t ckpt_bytes(const rbc_handle *h)
+{
+    const Dev &d = h->d;
+    const size_t Np = (size_t)d.Np, n = (size_t)d.nc;
+    return kCkptWords * 8 + 19 * Np * (size_t)pop_bytes(d.prec) + Np * sizeof(float4) +
+           (d.S ? 2 * Np * sizeof(float4) : 0) + n * (3 + 4 + 3 + 3) * sizeof(double) + n * sizeof(int);
+}
+
+void ckpt_header(const rbc_handle *h, int64_t w[kCkptWords])
+{
+    const Dev &d = h->d;
+    for (int k = 0; k < kCkptWords; ++k) w[k] = 0;
+    w[0] = kCkptMagic;
+    w[1] = d.nx;
+    w[2] = d.ny;
+    w[3] = d.nz;
+    w[4] = d.nc;
+    w[5] = d.prec;
+    w[6] = d.compact;
+    w[7] = d.Np;
+    w[8] = d.S ? 1 : 0;
+    w[9] = (int64_t)ckpt_bytes(h);
+}
+}  // namespace
+
+int rbc_checkpoint_size(const rbc_handle *h, size_t *bytes)
+{
+    if (!h || !bytes) return fail(nullptr, RBC_EINVAL, "NULL argument");
+    *bytes = ckpt_bytes(h);
+    return RBC_OK;
+}
+
+int rbc_save(rbc_handle *h, void *buf, size_t bytes)
+{
+    if (!h || !buf) return fail(h ? &h->err : nullptr, RBC_EINVAL, "NULL argument");
+    if (bytes < ckpt_bytes(h)) return fail(&h->err, RBC_EINVAL, "checkpoint buffer too small");
+    const Dev &d = h->d;
+    int64_t w[kCkptWords];
+    ckpt_header(h, w);
+    unsigned long long lb_step = 0, clamps = 0;
+    RBC_CU(cudaMemcpyAsync(&lb_step, d.lb_step, sizeof lb_step, cudaMemcpyDeviceToHost, h->stream));
+    RBC_CU(cudaMemcpyAsync(&clamps, d.clamps, sizeof clamps, cudaMemcpyDeviceToHost, h->stream));
+    char *o = static_cast<char *>(buf) + kCkptWords * 8;
+    const size_t Np = (size_t)d.Np, n = (size_t)d.nc;
+    auto take = [&](const void *src, size_t nb) -> cudaError_t {
+        const cudaError_t e = cudaMemcpyAsync(o, src, nb, cudaMemcpyDeviceToHost, h->stream);
+        o += nb;
+        return e;
+    };
+    RBC_CU(take(d.pops[h->step & 1], 19 * Np * (size_t)pop_bytes(d.prec)));
+    RBC_CU(take(d.U, Np * sizeof(float4)));
+    if (d.S) RBC_CU(take(d.S, 2 * Np * sizeof(float4)));
+    if (n) {
+        RBC_CU(take(d.R, 3 * n * sizeof(double)));
+        RBC_CU(take(d.q, 4 * n * sizeof(double)));
+        RBC_CU(take(d.V, 3 * n * sizeof(double)));
+        RBC_CU(take(d.Om, 3 * n * sizeof(double)));
+        RBC_CU(take(d.have, n * sizeof(int)));
+    }
+    RBC_CU(cudaStreamSynchronize(h->stream));
+    w[10] = h->step;
+    w[11] = (int64_t)lb_step;
+    w[12] = (int64_t)clamps;
+    std::memcpy(buf, w, sizeof w);
+    return check_flags(h);
+}
+
+int rbc_load(rbc_handle *h, const void *buf, size_t bytes)
+{
+    if (!h || !buf) return fail(h ? &h->err : nullptr, RBC_EINVAL, "NULL argument");
+    int64_t w[kCkptWords], mine[kCkptWords];
+    if (bytes < sizeof w) return fail(&h->err, RBC_EINVAL, "checkpoint too short");
+    std::memcpy(w, buf, sizeof w);
+    ckpt_header(h, mine);
+    for (int k = 0; k < 10; ++k)
+        if (w[k] != mine[k])
+            return fail(&h->err, RBC_EINVAL, "checkpoint of another problem (lattice, cells, storage or layout)");
+    if (bytes < ckpt_bytes(h)) return fail(&h->err, RBC_EINVAL, "checkpoint too short");
+    Dev &d = h->d;
+    RBC_CU(cudaStreamSynchronize(h->stream));
+    h->step = w[10];
+    const unsigned long long lb_step = (unsigned long long)w[11], clamps = (unsigned long long)w[12];
+    const char *o = static_cast<const char *>(buf) + kCkptWords * 8;
+    const size_t Np = (size_t)d.Np, n = (size_t)d.nc;
+    auto put = [&](void *dst, size_t nb) -> cudaError_t {
+        const cudaError_t e = cudaMemcpyAsync(dst, o, nb, cudaMemcpyHostToDevice, h->stream);
+        o += nb;
+        return e;
+    };
+    RBC_CU(put(d.pops[h->step & 1], 19 * Np * (size_t)pop_bytes(d.prec)));
+    RBC_CU(put(d.U, Np * sizeof(float4)));
+    if (d.S) RBC_CU(put(d.S, 2 * Np * sizeof(float4)));
+    if (n) {
+        RBC_CU(put(d.R, 3 * n * sizeof(double)));
+        RBC_CU(put(d.q, 4 * n * sizeof(double)));
+        RBC_CU(put(d.V, 3 * n * sizeof(double)));
+        RBC_CU(put(d.Om, 3 * n * sizeof(double)));
+        RBC_CU(put(d.have, n * sizeof(int)));
+    }
+    RBC_CU(cudaMemcpyAsync(d.lb_step, &lb_step, sizeof lb_step, cudaMemcpyHostToDevice, h->stream));
+    RBC_CU(cudaMemcpyAsync(d.clamps, &clamps, sizeof clamps, cudaMemcpyHostToDevice, h->stream));
+    // between steps the spread force density is zero; the cell list, the
+    // Gay-Berne forces and the shape lists of the restored poses are rebuilt
+    // (the shape lists of step k live in buffer k & 1)
+    if (d.G) RBC_CU(cudaMemsetAsync(d.G, 0, Np * sizeof(float4), h->stream));
+    RBC_CU(cudaMemsetAsync(d.flags, 0, 8 * sizeof(int), h->stream));
+    if (n) {
+        launch_bin(d, h->P.p, h->stream);
+        launch_gb(d, h->P.p, h->stream);
+        launch_weights(d, h->P.p, (int)(h->step & 1), h->stream);
+    }
+    RBC_CU(cudaStreamSynchronize(h->stream));
+    RBC_CU(cudaGetLastError());
     return RBC_OK;
 }
 

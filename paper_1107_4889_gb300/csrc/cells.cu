@@ -150,6 +150,7 @@ struct GbArgs {
     const int *wall_start, *wall_xyz;
     int *nbr, *nbr_count;
     double *Fm, *Tm;
+    const double *ext;  // 6n external force and torque (lab), or null
     int *flags;
     unsigned long long *clamps;
     int nc, cap, maxn, nb[3], per[3];
@@ -442,9 +443,10 @@ __device__ __forceinline__ void gb_body(const GbArgs &g, int blk)
         if (clamped) atomicAdd(&s_clamped, clamped);
     }
     __syncthreads();
-    // 5. every cell sums its own entries in queue order (deterministic)
+    // 5. every cell sums its own entries in queue order (deterministic),
+    //    starting from its external force and torque
     if (i < g.nc && lane < 6) {
-        double acc = 0.0;
+        double acc = g.ext ? g.ext[6 * i + lane] : 0.0;
         for (int e = s_qpre[wid]; e < s_qpre[wid + 1]; ++e) acc += s_res[e][lane];
         if (lane < 3)
             g.Fm[3 * i + lane] = acc;
@@ -1342,6 +1344,7 @@ static GbArgs gb_args(const Dev &d, const Params &p)
     g.nbr_count = d.nbr_count;
     g.Fm = d.Fm;
     g.Tm = d.Tm;
+    g.ext = d.ext;
     g.flags = d.flags;
     g.clamps = d.clamps;
     g.nc = d.nc;

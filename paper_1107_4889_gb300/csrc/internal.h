@@ -73,7 +73,8 @@ struct Dev {
     double *R, *q, *V, *Om;  // 3n, 4n, 3n, 3n
     double *A;               // 6n shape tensors (xx yy zz xy xz yz)
     float *Rf, *Af;          // 3n, 6n FP32 copies of positions and shape tensors (prefilters)
-    double *Fm, *Tm;         // 3n GB force, 3n GB torque (lab)
+    double *Fm, *Tm;         // 3n GB force, 3n GB torque (lab), external force and torque included
+    double *ext;             // 6n external force (3) and torque (3) per cell (lab), or null
     int *have;               // n: cached combined force exists (not the first step)
     double *diag;            // 21n per-cell diagnostics of the last step
     float *hdr;              // kHdrWords per cell: shape header built by k_bin

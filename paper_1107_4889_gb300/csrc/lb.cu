@@ -29,11 +29,6 @@ namespace {
 
 constexpr int kLbThreads = 256;
 
-// opposite speeds for run-time indices
-__constant__ int kOppTab[kQ] = {opp(0),  opp(1),  opp(2),  opp(3),  opp(4),  opp(5),  opp(6),
-                                opp(7),  opp(8),  opp(9),  opp(10), opp(11), opp(12), opp(13),
-                                opp(14), opp(15), opp(16), opp(17), opp(18)};
-
 __device__ __forceinline__ int wrapm(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 struct LbArgs {
@@ -70,6 +65,17 @@ __device__ __forceinline__ uint32_t entry_of(const LbArgs &a, int x, int y, int 
         return (uint32_t)(rt.x + x - rt.y);
     }
     return (uint32_t)x + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
+}
+
+// Storage entry of the neighbour x + c_p of node (x, y, z): arithmetic in the
+// dense layout; in the compact layout from the row base of (y + c_y, z + c_z)
+// in rb (the node's nine neighbour-row bases), with x + c_x wrapped.
+template <int P, bool COMPACT>
+__device__ __forceinline__ uint32_t ghost_entry(const LbArgs &a, int x, int y, int z, const int *rb)
+{
+    const int xd = wrapm(x + cx(P), a.nx);
+    if (COMPACT) return (uint32_t)(rb[(cy(P) + 1) + 3 * (cz(P) + 1)] + xd);
+    return entry_of<false>(a, xd, wrapm(y + cy(P), a.ny), wrapm(z + cz(P), a.nz));
 }
 
 // ---------------------------------------------------------------------------
@@ -209,13 +215,16 @@ __device__ __forceinline__ void for_speeds(F &&f)
 // this node in the opposite direction next pass, so it is stored in m's slot
 // of that direction, from which this node pulls.  Each (slot, solid node)
 // pair has exactly one writer; opposite speeds share a weight, so the stored
-// value is copied as it is.
+// value is written as it is, from the register that holds it, together with
+// the node's own store of the pair.
 // n is the node's storage entry; nd its lattice index (x + nx (y + ny z)),
-// which keys the rounding's random numbers in either layout.
+// which keys the rounding's random numbers in either layout.  rb (compact
+// layout only): the nine row bases of the node's row neighbourhood, entry of
+// (x', y + dy, z + dz) = rb[(dy + 1) + 3 (dz + 1)] + x'.
 template <typename St, bool WALLS, bool CELLS, bool SIGMA, bool COMPACT = false>
 __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], uint32_t lk, float gx, float gy,
                                              float gz, float T, uint32_t n, uint32_t nd, int x, int y, int z,
-                                             unsigned long long step)
+                                             unsigned long long step, const int *rb = nullptr)
 {
     // element offsets fit 32 bits: the host keeps 19 Np below 2^32
     const uint32_t Np = (uint32_t)a.Np;
@@ -240,8 +249,8 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
     const float usq = ux * ux + uy * uy + uz * uz;
     const float gu = gx * ux + gy * uy + gz * uz;
     const bool sr = Pop<St>::kRounds && a.stochastic != 0;
-    uint4 rb = make_uint4(0u, 0u, 0u, 0u);
-    if (sr) rb = philox4x32_10(make_uint4(nd, (uint32_t)step, (uint32_t)(step >> 32), 0u), a.key0, a.key1);
+    uint4 rbits = make_uint4(0u, 0u, 0u, 0u);
+    if (sr) rbits = philox4x32_10(make_uint4(nd, (uint32_t)step, (uint32_t)(step >> 32), 0u), a.key0, a.key1);
     // A speed p and its opposite q share |c.u|, |c.G| and the weight, so
     //   d_eq(p, q) = A +- B,  A = w [drho + rho (4.5 (c.u)^2 - 1.5 u^2)],
     //                         B = 3 w rho c.u,
@@ -256,7 +265,7 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
         if constexpr (p == 0) {
             const float A = wq(0) * (drho - 1.5f * rho * usq);
             const float C = -1.5f * ff * wq(0) * gu;
-            __stcs(&dst[n], Pop<St>::template put<0>(omc * d[0] + (om * A + C), sr, rb));
+            __stcs(&dst[n], Pop<St>::template put<0>(omc * d[0] + (om * A + C), sr, rbits));
         } else if constexpr (p < q) {
             const float cu = float(cx(p)) * ux + float(cy(p)) * uy + float(cz(p)) * uz;
             const float cg = float(cx(p)) * gx + float(cy(p)) * gy + float(cz(p)) * gz;
@@ -267,8 +276,16 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
             const float C = fw * (4.5f * cg * cu - 1.5f * gu);
             const float D = 3.0f * fw * cg;
             const float P = om * A + C, M = om * B + D;
-            __stcs(&dst[(uint32_t)p * Np + n], Pop<St>::template put<p>(omc * d[p] + (P + M), sr, rb));
-            __stcs(&dst[(uint32_t)q * Np + n], Pop<St>::template put<q>(omc * d[q] + (P - M), sr, rb));
+            const St vp = Pop<St>::template put<p>(omc * d[p] + (P + M), sr, rbits);
+            const St vq = Pop<St>::template put<q>(omc * d[q] + (P - M), sr, rbits);
+            __stcs(&dst[(uint32_t)p * Np + n], vp);
+            __stcs(&dst[(uint32_t)q * Np + n], vq);
+            if (WALLS) {
+                // the solid neighbour x + c_p pulls nothing: its slot of q is
+                // this node's next-pass population q (and likewise for q)
+                if ((lk >> p) & 1u) dst[(uint32_t)q * Np + ghost_entry<p, COMPACT>(a, x, y, z, rb)] = vp;
+                if ((lk >> q) & 1u) dst[(uint32_t)p * Np + ghost_entry<q, COMPACT>(a, x, y, z, rb)] = vq;
+            }
             if (SIGMA) {
                 const float ne = (d[p] + d[q]) - 2.0f * A;
                 if (cx(p)) pxx += ne;
@@ -286,15 +303,6 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
         a.S[2 * n + 1] = make_float4(-ff * pxz, -ff * pyz, 0.f, 0.f);
     }
     if (!(rho > 0.0f) || !(usq <= a.mach2)) atomicOr(&a.flags[FLAG_UNSTABLE], 1);
-    if (WALLS && (lk & 0x7FFFEu)) {  // nodes next to a wall only
-#pragma unroll 1
-        for (int p = 1; p < kQ; ++p) {
-            if (!((lk >> p) & 1u)) continue;
-            const int xd = wrapm(x + cx(p), a.nx), yd = wrapm(y + cy(p), a.ny), zd = wrapm(z + cz(p), a.nz);
-            // read back this thread's own store of d*_p
-            dst[(uint32_t)kOppTab[p] * Np + entry_of<COMPACT>(a, xd, yd, zd)] = dst[(uint32_t)p * Np + n];
-        }
-    }
 }
 
 // Open-boundary node n = (x, y, z) (bit 29 of its link word: inlet, bit 30:
@@ -823,12 +831,26 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
 // descriptor j and copies that part of each of its speeds' planes (and, for
 // the batch row's own row u = 4, of G / theta and the link words), so the
 // warp issues a batch with one coalesced load and no dependent lookups.
+constexpr int kMaxBatchRows = 16;  // rows of one compact batch (the set-up keeps to it)
+
+// rbs[b][u]: base of upstream row u of batch row b (entry of x' in that row =
+// base + x'), rbs[b][9]: the batch row's fluid x-range; written before the
+// stage's arrive, read by the consumers.
 template <typename St, bool CELLS>
 __device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, int2 bx, unsigned char *base,
-                                                uint32_t bar, int lane)
+                                                uint32_t bar, int lane, int (*rbs)[10])
 {
     const int nb = (int)((uint32_t)bd.y >> 20);
     const int W = (int)((uint32_t)bd.w >> 16);
+    const int z = bd.x, y0 = bd.y & 0xFFFFF, X0 = bd.w & 0xFFFF;
+    for (int j = lane; j < 9 * nb; j += 32) {
+        const int2 e = a.pool[bx.x + j];
+        const int count = (int)((uint32_t)e.y >> 16), at = e.y & 0xFFFF;
+        const int b = j / 9, u = j - 9 * b;
+        rbs[b][u] = count > 0 ? e.x - at - X0 : 0;
+        if (u == 4) rbs[b][9] = a.rows[y0 + b + a.ny * z].w;
+    }
+    __syncwarp();
     if (lane == 0) mbar_expect_tx(bar, (uint32_t)bx.y);
     __syncwarp();
     const uint64_t once = l2_evict_first();
@@ -861,7 +883,7 @@ __device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, int2 b
 
 template <typename St, bool CELLS, bool SIGMA>
 __device__ __forceinline__ void consume_compact(const LbArgs &a, int4 bd, const unsigned char *base,
-                                                unsigned long long step)
+                                                unsigned long long step, const int (*rbs)[10])
 {
     const int nx = a.nx, ny = a.ny;
     const int z = bd.x, y0 = bd.y & 0xFFFFF, nb = (int)((uint32_t)bd.y >> 20);
@@ -885,12 +907,13 @@ __device__ __forceinline__ void consume_compact(const LbArgs &a, int4 bd, const 
             ++b;
         }
         const int y = y0 + bb;
-        const int4 rt = a.rows[y + ny * z];
-        if (x < (rt.w & 0xFFFF) || x > (int)((uint32_t)rt.w >> 16)) continue;
+        const int *rb = rbs[bb];
+        const int fr = rb[9];
+        if (x < (fr & 0xFFFF) || x > (int)((uint32_t)fr >> 16)) continue;
         const int sx = bb * W + x - X0;
         const uint32_t lk = lst[sx];
         if (lk >> 31) continue;
-        const uint32_t n = (uint32_t)(rt.x + x - rt.y);
+        const uint32_t n = (uint32_t)(rb[4] + x);
         const uint32_t nd = (uint32_t)x + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
         if (lk & 0x60000000u) {
             boundary_node<St, CELLS, SIGMA, true>(a, n, nd, x, y, z, lk, step);
@@ -912,7 +935,7 @@ __device__ __forceinline__ void consume_compact(const LbArgs &a, int4 bd, const 
             gz += g4.z;
             T += a.delta * g4.w;
         }
-        collide_node<St, true, CELLS, SIGMA, true>(a, d, lk, gx, gy, gz, T, n, nd, x, y, z, step);
+        collide_node<St, true, CELLS, SIGMA, true>(a, d, lk, gx, gy, gz, T, n, nd, x, y, z, step, rb);
     }
 }
 
@@ -925,6 +948,7 @@ __global__ void __launch_bounds__(kStThreads, 2)
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages];
     __shared__ int4 s_desc[kMaxStages];
+    __shared__ int s_rb[kMaxStages][kMaxBatchRows][10];
     __shared__ unsigned long long s_step;
     if (threadIdx.x == 0) {
         for (int k = 0; k < ns; ++k) {
@@ -976,7 +1000,7 @@ __global__ void __launch_bounds__(kStThreads, 2)
                 continue;
             }
             issued |= 1u << stage;
-            produce_compact<St, CELLS>(a, bd, bx, smraw + (size_t)stage * stage_bytes, bar, lane);
+            produce_compact<St, CELLS>(a, bd, bx, smraw + (size_t)stage * stage_bytes, bar, lane, s_rb[stage]);
         }
         if (!ok) {
             // let the copies still in flight land before the CTA's memory
@@ -1006,7 +1030,7 @@ __global__ void __launch_bounds__(kStThreads, 2)
         }
         const int4 bd = s_desc[stage];
         if (bd.x < 0) break;
-        consume_compact<St, CELLS, SIGMA>(a, bd, smraw + (size_t)stage * stage_bytes, step);
+        consume_compact<St, CELLS, SIGMA>(a, bd, smraw + (size_t)stage * stage_bytes, step, s_rb[stage]);
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&empty[stage]));
     }

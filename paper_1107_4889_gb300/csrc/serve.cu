@@ -42,7 +42,7 @@ constexpr int kInFlight = 2;    // ticks per solve queued on its stream
 struct Owned {
     rbc_request r;
     std::vector<uint8_t> solid;
-    std::vector<double> pos, quat, vel, om;
+    std::vector<double> pos, quat, vel, om, fext, text;
     double t_submit = 0.0;
     size_t bytes = 0;
 };
@@ -579,6 +579,14 @@ int rbc_server_submit(rbc_server *s, const rbc_request *r)
         if (r->cells.vel) {
             o->vel.assign(r->cells.vel, r->cells.vel + 3 * (size_t)n);
             o->r.cells.vel = o->vel.data();
+        }
+        if (r->cells.force_ext) {
+            o->fext.assign(r->cells.force_ext, r->cells.force_ext + 3 * (size_t)n);
+            o->r.cells.force_ext = o->fext.data();
+        }
+        if (r->cells.torque_ext) {
+            o->text.assign(r->cells.torque_ext, r->cells.torque_ext + 3 * (size_t)n);
+            o->r.cells.torque_ext = o->text.data();
         }
         if (r->cells.omega_body) {
             o->om.assign(r->cells.omega_body, r->cells.omega_body + 3 * (size_t)n);

@@ -38,7 +38,8 @@ class rbc_geometry(ctypes.Structure):
 
 
 class rbc_cells(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int), ("pos", _D), ("quat", _D), ("vel", _D), ("omega_body", _D)]
+    _fields_ = [("n", ctypes.c_int), ("pos", _D), ("quat", _D), ("vel", _D), ("omega_body", _D),
+                ("force_ext", _D), ("torque_ext", _D)]
 
 
 class rbc_params(ctypes.Structure):
@@ -95,6 +96,7 @@ EXPORTS = ["rbc_default_params", "rbc_workspace_size", "rbc_init", "rbc_step", "
            "rbc_stats", "rbc_cell_diag", "rbc_neighbors", "rbc_set_timing", "rbc_kernel_times",
            "rbc_autotune", "rbc_wss_accumulate", "rbc_wss", "rbc_launches_per_step", "rbc_layout", "rbc_fluid_nodes",
            "rbc_profile_accumulate", "rbc_profile", "rbc_set_wait_limit",
+           "rbc_checkpoint_size", "rbc_save", "rbc_load",
            "rbc_neighbors_noalloc", "rbc_server_create", "rbc_server_submit",
            "rbc_server_poll", "rbc_server_results", "rbc_server_clock", "rbc_server_free", "rbc_free",
            "rbc_last_error"]
@@ -131,6 +133,11 @@ def load(path: str = LIB_PATH):
     L.rbc_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.rbc_kernel_times.argtypes = [ctypes.c_void_p, _D, _I64]
     L.rbc_launches_per_step.argtypes = [ctypes.c_void_p]
+    L.rbc_checkpoint_size.argtypes = [ctypes.c_void_p, P(ctypes.c_size_t)]
+    L.rbc_save.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+    L.rbc_load.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+    for name in ("rbc_checkpoint_size", "rbc_save", "rbc_load"):
+        getattr(L, name).restype = ctypes.c_int
     L.rbc_set_wait_limit.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
     L.rbc_set_wait_limit.restype = ctypes.c_int
     L.rbc_profile_accumulate.argtypes = [ctypes.c_void_p, ctypes.c_int]
@@ -220,6 +227,10 @@ class _Inputs:
             self.vel = None if v is None else np.ascontiguousarray(np.asarray(v, np.float64).reshape(n, 3))
             self.om = None if w is None else np.ascontiguousarray(np.asarray(w, np.float64).reshape(n, 3))
             c.pos, c.quat, c.vel, c.omega_body = _dp(self.pos), _dp(self.quat), _dp(self.vel), _dp(self.om)
+            fe, te = cells.get("force_ext"), cells.get("torque_ext")
+            self.fext = None if fe is None else np.ascontiguousarray(np.asarray(fe, np.float64).reshape(n, 3))
+            self.text = None if te is None else np.ascontiguousarray(np.asarray(te, np.float64).reshape(n, 3))
+            c.force_ext, c.torque_ext = _dp(self.fext), _dp(self.text)
         self.cells = c
         p = rbc_params()
         load().rbc_default_params(ctypes.byref(p))
@@ -352,6 +363,20 @@ def rbc_launches_per_step(h) -> int:
     return int(load().rbc_launches_per_step(h))
 
 
+def rbc_save(h) -> bytes:
+    """The handle's checkpoint (rbc_checkpoint_size bytes) as a bytes object."""
+    nb = ctypes.c_size_t(0)
+    _check(load().rbc_checkpoint_size(h, ctypes.byref(nb)), h)
+    buf = ctypes.create_string_buffer(nb.value)
+    _check(load().rbc_save(h, buf, nb.value), h)
+    return buf.raw
+
+
+def rbc_load(h, data: bytes):
+    buf = ctypes.create_string_buffer(data, len(data))
+    _check(load().rbc_load(h, buf, len(data)), h)
+
+
 def rbc_set_wait_limit(h, cycles: int, starve_batch: int = -1):
     _check(load().rbc_set_wait_limit(h, int(cycles), int(starve_batch)), h)
 
@@ -452,6 +477,12 @@ class Solver:
 
     def layout(self):
         return rbc_layout(self.handle)
+
+    def save(self) -> bytes:
+        return rbc_save(self.handle)
+
+    def load(self, data: bytes):
+        rbc_load(self.handle, data)
 
     def set_wait_limit(self, cycles, starve_batch=-1):
         rbc_set_wait_limit(self.handle, cycles, starve_batch)

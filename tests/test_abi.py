@@ -47,7 +47,7 @@ def test_default_params_are_the_papers(lib):
 def test_struct_layouts_match_header(lib):
     # nx..periodic, solid, body_force, body_force_wave, node_type, inlet_center, inlet_radius, inlet_umax
     assert ctypes.sizeof(rbc.rbc_geometry) == 24 + 8 + 24 + 24 + 8 + 16 + 8 + 8
-    assert ctypes.sizeof(rbc.rbc_cells) == 8 + 4 * 8
+    assert ctypes.sizeof(rbc.rbc_cells) == 8 + 6 * 8  # n, pos, quat, vel, omega_body, force_ext, torque_ext
     assert ctypes.sizeof(rbc.rbc_stats_t) == 8 * 10 + 8 + 8
     assert rbc.rbc_params.stream.offset == ctypes.sizeof(rbc.rbc_params) - 8
     # int precision, int rounding, uint64_t seed, int node_list, int layout, void *stream close the struct

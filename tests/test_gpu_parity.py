@@ -331,3 +331,16 @@ def test_kernel_timing_on_and_off():
     assert rel_l2(s.fields()["u"], u_o) <= TOL
     s.close()
     o.close()
+
+
+def test_external_force_and_torque_on_cells():
+    """Cells pushed by constant external forces and torques (the mobility
+    tests of Sec. 3), the counter-force spread uniformly over the fluid."""
+    geom, cells, params = wl.box_workload(n=24, ncells=4, body_force=(0, 0, 0), seed=14)
+    rng = np.random.default_rng(15)
+    F = rng.normal(size=(4, 3)) * 1e-4
+    cells["force_ext"] = F
+    cells["torque_ext"] = rng.normal(size=(4, 3)) * 5e-3
+    geom["body_force"] = tuple(-F.sum(axis=0) / 24 ** 3)
+    r = _compare(geom, cells, params, 60)
+    print("external push:", r)
