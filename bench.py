@@ -266,6 +266,9 @@ def run_ours(args):
         B.build()
     _barrier(ws)
     geom, cells, params, desc = _workload(args.workload, args.precision)
+    if args.layout != "auto":
+        params = dict(params, layout=args.layout)
+        desc += f", {args.layout} layout"
     if args.node_list:
         params = dict(params, node_list=args.node_list)
         desc += ", node-list pass" if args.node_list > 0 else ", row-staged pass"
@@ -683,6 +686,8 @@ def parse_args(argv=None):
     ap.add_argument("--stats", action="store_true",
                     help="relative viscosity and near-wall hematocrit of the channel, binary16 against FP32")
     ap.add_argument("--no-cells", action="store_true", help="drop the workload's cells (lattice pass alone)")
+    ap.add_argument("--layout", choices=["auto", "dense", "compact"], default="auto",
+                    help="storage layout of the lattice fields (auto: compact for sparse walled lattices)")
     ap.add_argument("--node-list", type=int, default=0, choices=[-1, 0, 1],
                     help="lattice pass over a fluid-node list (1), whole rows (-1), or the library's choice (0)")
     ap.add_argument("--precision", choices=["f32", "f16", "bf16"], default="f32")
