@@ -580,6 +580,9 @@ def run_mobility(args):
     N = L ** 3
     gammas = [0.05, 0.1, 0.2, 0.4, 0.8]
     base = dict(delta=0.0, alpha_tt=0.0)
+    if args.mobility_xi_half:
+        # the alternative reading of the shape-function radii: xi = a / 2
+        base["xi"] = tuple(0.5 * a for a in wl.PAPER_PARAMS["semi_axes"])
     out = {}
     cases = {"frontal": ("force", 2), "side": ("force", 0), "spin_smallest_radius": ("torque", 2),
              "spin_largest_radius": ("torque", 0)}
@@ -618,7 +621,8 @@ def run_mobility(args):
             out[name]["gamma_R_mesh"] = float(gm)
             out[name]["a_R_mesh"] = float((p["inertia"][axis] * gm / (8 * np.pi / 6.0)) ** (1.0 / 3.0))
     line = {"metric": "mobility of one cell vs friction (Sec. 3 mobility test)",
-            "workload": f"one cell, 60^3 periodic box, M=10, I=1000, delta=0, {steps} steps per point",
+            "workload": f"one cell, 60^3 periodic box, M=10, I=1000, delta=0, xi={tuple(base.get('xi', wl.PAPER_PARAMS['xi']))}, "
+                        f"{steps} steps per point",
             "paper": {"frontal": 6.6, "side": 10.3, "gamma_R_mesh_smallest": 1 / 44, "gamma_R_mesh_largest": 1 / 38},
             **out}
     print(json.dumps(line), flush=True)
@@ -683,6 +687,7 @@ def parse_args(argv=None):
     ap.add_argument("--wss-map", action="store_true",
                     help="wall-shear-stress map of the workload, binary16 against FP32")
     ap.add_argument("--mobility", action="store_true", help="mobility of one cell against the friction rates")
+    ap.add_argument("--mobility-xi-half", action="store_true", help="mobility test with xi = semi-axes / 2")
     ap.add_argument("--stats", action="store_true",
                     help="relative viscosity and near-wall hematocrit of the channel, binary16 against FP32")
     ap.add_argument("--no-cells", action="store_true", help="drop the workload's cells (lattice pass alone)")

@@ -198,11 +198,53 @@ bool build_compact(Problem &P, const uint8_t *solid, int esz, bool cells)
     };
     P.batches.clear();
     int most = 0;
+    // a row whose fluid nodes form runs separated by wide solid gaps (a
+    // vessel that branched) is taken one run at a time, so that neither the
+    // copies nor the consumer threads cover the gap
+    const int kGap = 24;
+    auto runs_of = [&](int r, std::vector<std::pair<int, int>> &runs) {
+        runs.clear();
+        const uint8_t *row = solid + (size_t)r * nx;
+        int x = fl[r];
+        while (x <= fh[r]) {
+            int e = x;
+            while (e + 1 <= fh[r] && !row[e + 1]) ++e;
+            if (!runs.empty() && x - runs.back().second - 1 < kGap)
+                runs.back().second = e;
+            else
+                runs.emplace_back(x, e);
+            x = e + 1;
+            while (x <= fh[r] && row[x]) ++x;
+        }
+    };
+    std::vector<std::pair<int, int>> runs;
     for (int z = 0; z < nz; ++z) {
         int y = 0;
         while (y < ny) {
             const int r = y + ny * z;
             if (fh[r] < 0) {
+                ++y;
+                continue;
+            }
+            runs_of(r, runs);
+            if (runs.size() > 1 && fl[r] > 0 && fh[r] < nx - 1) {
+                for (const auto &run : runs) {
+                    int X0r, Wr;
+                    window(run.first, run.second, X0r, Wr);
+                    if (Wr > cap) {
+                        const int L = (cap - 16) / 8 * 8;
+                        if (L < 8) return false;
+                        for (int a0 = run.first; a0 <= run.second; a0 += L) {
+                            const int a1 = std::min(run.second, a0 + L - 1);
+                            window(a0, a1, X0r, Wr);
+                            push(z, y, 1, a0, a1, X0r, Wr);
+                            most = std::max(most, Wr);
+                        }
+                    } else {
+                        push(z, y, 1, run.first, run.second, X0r, Wr);
+                        most = std::max(most, Wr);
+                    }
+                }
                 ++y;
                 continue;
             }
@@ -224,6 +266,8 @@ bool build_compact(Problem &P, const uint8_t *solid, int esz, bool cells)
             while (y + nb < ny && nb < 16) {  // at most 16 rows (the pass stages their row bases)
                 const int r2 = y + nb + ny * z;
                 if (fh[r2] < 0) break;
+                runs_of(r2, runs);
+                if (runs.size() > 1 && fl[r2] > 0 && fh[r2] < nx - 1) break;
                 const int d0 = std::min(c0, fl[r2]), d1 = std::max(c1, fh[r2]);
                 int X0b, Wb;
                 window(d0, d1, X0b, Wb);

@@ -939,9 +939,15 @@ __device__ __forceinline__ void consume_compact(const LbArgs &a, int4 bd, const 
     }
 }
 
-// at least two CTAs per SM: the pass and the side kernels share the SMs
+// Registers bounded so that the side kernels of the step find room beside
+// the pass on every SM: 72 per thread for FP32 populations (the row-staged
+// pass's count), 96 for the 16-bit ones (their decode and stochastic
+// rounding need more)
+template <typename St>
+constexpr int compact_min_blocks() { return sizeof(St) == 4 ? 3 : 2; }
+
 template <typename St, bool CELLS, bool SIGMA>
-__global__ void __launch_bounds__(kStThreads, 2)
+__global__ void __launch_bounds__(kStThreads, compact_min_blocks<St>())
     k_lb_compact(LbArgs a, const int4 *__restrict__ batches, const int2 *__restrict__ bxs, int nbatches, int ns,
                  int stage_bytes)
 {
