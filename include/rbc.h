@@ -270,8 +270,10 @@ int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2]);
  * it, or after it), over steps_per_trial coupled steps after as many
  * warm-up steps, keeps the fastest, then with it times bounded grids of the
  * shape-list and Gay-Berne kernels (2-4 blocks per SM, grid-stride over the
- * cells) against one block per group of cells, and re-captures the step
- * graphs.  The trial steps are ordinary
+ * cells) against one block per group of cells, then the particle-bin edge
+ * (the candidate radius times 1, 1.25, 1.5 or 2: coarser grids scan fewer,
+ * fuller bins; a grid that overflows a bin is dropped), and re-captures the
+ * step graphs.  The trial steps are ordinary
  * steps of the solve (the state advances).  Synchronises.  out may be NULL. */
 typedef struct {
     int stages, ctas_per_sm;     /* chosen shape (0, 0: the one-thread-per-node pass, nothing to tune) */
@@ -281,6 +283,7 @@ typedef struct {
     int lattice_first;           /* chosen order: 1 = lattice pass before the side kernels */
     int wt_blocks_per_sm;        /* grid of the shape-list kernel, blocks per SM (0: one per 4 cells) */
     int gb_blocks_per_sm;        /* grid of the Gay-Berne kernel, blocks per SM (0: one per 8 cells) */
+    double bin_scale;            /* chosen edge of the particle bins over the candidate radius (>= 1) */
 } rbc_tune_report;
 int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out);
 

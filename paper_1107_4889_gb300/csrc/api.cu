@@ -1394,6 +1394,7 @@ int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out)
     if (!h || steps_per_trial < 1) return fail(h ? &h->err : nullptr, RBC_EINVAL, "bad argument");
     rbc_tune_report rep;
     std::memset(&rep, 0, sizeof rep);
+    rep.bin_scale = 1.0;
     if (h->timing_used < h->timing_cap) return fail(&h->err, RBC_EINVAL, "kernel timing is active");
     const int st0 = h->d.lb_stages, grid0 = h->d.lb_grid;
     const size_t smem0 = h->d.lb_smem;
@@ -1474,6 +1475,52 @@ int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out)
         h->d.gb_grid = bg * sms;
         rep.wt_blocks_per_sm = bw;
         rep.gb_blocks_per_sm = bg;
+        // then the particle bins: edges of r_cut x {1, 1.25, 1.5, 2}
+        // (coarser grids scan fewer, fuller bins); the arrays hold the finest
+        // grid, and a trial that overflows a bin is dropped
+        const int dims[3] = {h->d.nx, h->d.ny, h->d.nz};
+        const double bin_min = std::sqrt(std::max(h->P.p.rc2, h->P.p.rcw2));
+        int nb0[3];
+        double bs0[3];
+        for (int a = 0; a < 3; ++a) {
+            nb0[a] = h->d.nb[a];
+            bs0[a] = h->d.bin_size[a];
+        }
+        double best_scale = 1.0;
+        int best_nb[3] = {nb0[0], nb0[1], nb0[2]};
+        for (const double scale : {1.25, 1.5, 2.0}) {
+            int nbt[3];
+            for (int a = 0; a < 3; ++a) nbt[a] = std::max(1, (int)std::floor(dims[a] / (bin_min * scale)));
+            if (nbt[0] == best_nb[0] && nbt[1] == best_nb[1] && nbt[2] == best_nb[2]) continue;
+            for (int a = 0; a < 3; ++a) {
+                h->d.nb[a] = nbt[a];
+                h->d.bin_size[a] = (double)dims[a] / nbt[a];
+            }
+            h->d.nbins = nbt[0] * nbt[1] * nbt[2];
+            rc = recapture_steps(h);
+            double ms = 0.0;
+            if (rc == RBC_OK) rc = time_steps(h, steps_per_trial, &ms);
+            if (rc != RBC_OK) return rc;
+            rep.trials++;
+            int flags[8];
+            RBC_CU(cudaMemcpy(flags, h->d.flags, sizeof flags, cudaMemcpyDeviceToHost));
+            if (flags[FLAG_OVERFLOW] & (OVF_BIN | OVF_NBR)) {
+                flags[FLAG_OVERFLOW] &= ~(OVF_BIN | OVF_NBR);
+                RBC_CU(cudaMemcpy(h->d.flags, flags, sizeof flags, cudaMemcpyHostToDevice));
+                continue;  // this grid overflowed a bin: not a candidate
+            }
+            if (ms < best) {
+                best = ms;
+                best_scale = scale;
+                for (int a = 0; a < 3; ++a) best_nb[a] = nbt[a];
+            }
+        }
+        for (int a = 0; a < 3; ++a) {
+            h->d.nb[a] = best_nb[a];
+            h->d.bin_size[a] = best_scale == 1.0 ? bs0[a] : (double)dims[a] / best_nb[a];
+        }
+        h->d.nbins = best_nb[0] * best_nb[1] * best_nb[2];
+        rep.bin_scale = best_scale;
     }
     rep.ms_per_step = best;
     rc = recapture_steps(h);

@@ -832,51 +832,91 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
 // the batch row's own row u = 4, of G / theta and the link words), so the
 // warp issues a batch with one coalesced load and no dependent lookups.
 constexpr int kMaxBatchRows = 16;  // rows of one compact batch (the set-up keeps to it)
+constexpr int kDescPerLane = (9 * kMaxBatchRows + 31) / 32;
 
-// rbs[b][u]: base of upstream row u of batch row b (entry of x' in that row =
-// base + x'), rbs[b][9]: the batch row's fluid x-range; written before the
-// stage's arrive, read by the consumers.
+// The producer's copy of one batch: its record, the copy descriptors of its
+// batch rows (descriptor j = lane + 32 k in e[k]) and the fluid range of
+// each batch row (fr[k], for the lanes holding u = 4).  Loaded one batch
+// ahead, so that the loads overlap the consumers' work on earlier stages.
+struct CompactBatch {
+    int batch;
+    int4 bd;
+    int2 bx;
+    int2 e[kDescPerLane];
+    int fr[kDescPerLane];
+};
+
+__device__ __forceinline__ void load_compact_batch(const LbArgs &a, const int4 *__restrict__ batches,
+                                                   const int2 *__restrict__ bxs, int batch, int nbatches,
+                                                   int lane, CompactBatch &cb)
+{
+    cb.batch = batch;
+    if (batch >= nbatches) return;
+    cb.bd = batches[batch];
+    cb.bx = bxs[batch];
+    const int nb = (int)((uint32_t)cb.bd.y >> 20);
+    const int z = cb.bd.x, y0 = cb.bd.y & 0xFFFFF;
+#pragma unroll
+    for (int k = 0; k < kDescPerLane; ++k) {
+        const int j = lane + 32 * k;
+        cb.e[k] = make_int2(0, 0);
+        cb.fr[k] = 0;
+        if (j < 9 * nb) {
+            cb.e[k] = a.pool[cb.bx.x + j];
+            const int b = j / 9;
+            if (j - 9 * b == 4) cb.fr[k] = a.rows[y0 + b + a.ny * z].w;
+        }
+    }
+}
+
+// Producer side of one compact batch (descriptors already in registers):
+// rbs[b][u] = base of upstream row u of batch row b (entry of x' in that
+// row = base + x'), rbs[b][9] = the batch row's fluid x-range, written before
+// the stage's arrive; then the bulk copies.
 template <typename St, bool CELLS>
-__device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, int2 bx, unsigned char *base,
+__device__ __forceinline__ void produce_compact(const LbArgs &a, const CompactBatch &cb, unsigned char *base,
                                                 uint32_t bar, int lane, int (*rbs)[10])
 {
-    const int nb = (int)((uint32_t)bd.y >> 20);
-    const int W = (int)((uint32_t)bd.w >> 16);
-    const int z = bd.x, y0 = bd.y & 0xFFFFF, X0 = bd.w & 0xFFFF;
-    for (int j = lane; j < 9 * nb; j += 32) {
-        const int2 e = a.pool[bx.x + j];
-        const int count = (int)((uint32_t)e.y >> 16), at = e.y & 0xFFFF;
+    const int nb = (int)((uint32_t)cb.bd.y >> 20);
+    const int W = (int)((uint32_t)cb.bd.w >> 16);
+    const int X0 = cb.bd.w & 0xFFFF;
+#pragma unroll
+    for (int k = 0; k < kDescPerLane; ++k) {
+        const int j = lane + 32 * k;
+        if (j >= 9 * nb) continue;
+        const int count = (int)((uint32_t)cb.e[k].y >> 16), at = cb.e[k].y & 0xFFFF;
         const int b = j / 9, u = j - 9 * b;
-        rbs[b][u] = count > 0 ? e.x - at - X0 : 0;
-        if (u == 4) rbs[b][9] = a.rows[y0 + b + a.ny * z].w;
+        rbs[b][u] = count > 0 ? cb.e[k].x - at - X0 : 0;
+        if (u == 4) rbs[b][9] = cb.fr[k];
     }
     __syncwarp();
-    if (lane == 0) mbar_expect_tx(bar, (uint32_t)bx.y);
+    if (lane == 0) mbar_expect_tx(bar, (uint32_t)cb.bx.y);
     __syncwarp();
     const uint64_t once = l2_evict_first();
     const size_t pop_bytes = (size_t)kQ * nb * W * sizeof(St);
-    for (int j = lane; j < 9 * nb; j += 32) {
-        const int2 e = a.pool[bx.x + j];
+#pragma unroll
+    for (int k = 0; k < kDescPerLane; ++k) {
+        const int j = lane + 32 * k;
+        const int2 e = cb.e[k];
         const int count = (int)((uint32_t)e.y >> 16);
-        if (count == 0) continue;
+        if (j >= 9 * nb || count == 0) continue;
         const int at = e.y & 0xFFFF;  // window offset of the first entry
         const int b = j / 9, u = j - 9 * b;
         const int dy = u % 3 - 1, dz = u / 3 - 1;
-        const uint32_t bar_ = bar;
         for_speeds<0, kQ>([&](auto pc) {
             constexpr int p = decltype(pc)::value;
             if (cy(p) != -dy || cz(p) != -dz) return;
             const St *g = static_cast<const St *>(a.src) + (size_t)p * (size_t)a.Np + (size_t)e.x;
             bulk_g2s_hint(smem_addr(base + ((size_t)(p * nb + b) * W + at) * sizeof(St)), g,
-                          (uint32_t)(count * (int)sizeof(St)), bar_, once);
+                          (uint32_t)(count * (int)sizeof(St)), bar, once);
         });
         if (u == 4) {
             if (CELLS)
                 bulk_g2s(smem_addr(base + pop_bytes + ((size_t)b * W + at) * sizeof(float4)), a.G + e.x,
-                         (uint32_t)(count * (int)sizeof(float4)), bar_);
+                         (uint32_t)(count * (int)sizeof(float4)), bar);
             bulk_g2s(smem_addr(base + pop_bytes + (CELLS ? (size_t)nb * W * sizeof(float4) : 0) +
                                ((size_t)b * W + at) * sizeof(uint32_t)),
-                     a.links + e.x, (uint32_t)(count * (int)sizeof(uint32_t)), bar_);
+                     a.links + e.x, (uint32_t)(count * (int)sizeof(uint32_t)), bar);
         }
     }
 }
@@ -975,38 +1015,39 @@ __global__ void __launch_bounds__(kStThreads, compact_min_blocks<St>())
         int it = 0;
         bool ok = true;
         unsigned issued = 0;  // stages whose last fill has copies issued
+        // software pipeline: the current batch's record and descriptors are
+        // in registers when its stage frees up; the next one is claimed and
+        // loaded right after the current one's copies are issued
         int next = 0;
         if (lane == 0) next = atomicAdd(&a.work[0], 1);
+        CompactBatch cur;
+        load_compact_batch(a, batches, bxs, __shfl_sync(0xffffffffu, next, 0), nbatches, lane, cur);
+        if (lane == 0 && cur.batch < nbatches) next = atomicAdd(&a.work[0], 1);
         for (;; ++it) {
             const int stage = it % ns;
-            const int batch = __shfl_sync(0xffffffffu, next, 0);
-            int4 bd = make_int4(-1, 0, 0, 0);
-            int2 bx = make_int2(0, 0);
-            if (batch < nbatches) {
-                if (lane == 0) next = atomicAdd(&a.work[0], 1);
-                bd = batches[batch];
-                bx = bxs[batch];
-            }
             if (it >= ns && !mbar_wait(smem_addr(&empty[stage]), (uint32_t)((it / ns - 1) & 1), a.wait_cycles)) {
                 if (lane == 0) atomicOr(&a.flags[FLAG_TIMEOUT], 1);
                 ok = false;
                 break;
             }
             const uint32_t bar = smem_addr(&full[stage]);
-            if (batch >= nbatches) {
+            if (cur.batch >= nbatches) {
                 if (lane == 0) {
                     s_desc[stage] = make_int4(-1, 0, 0, 0);
                     mbar_arrive(bar);
                 }
                 break;
             }
-            if (lane == 0) s_desc[stage] = bd;
-            if (batch == a.starve_batch) {  // fault injection: the stage never fills
+            if (lane == 0) s_desc[stage] = cur.bd;
+            if (cur.batch == a.starve_batch) {  // fault injection: the stage never fills
                 issued &= ~(1u << stage);
-                continue;
+            } else {
+                issued |= 1u << stage;
+                produce_compact<St, CELLS>(a, cur, smraw + (size_t)stage * stage_bytes, bar, lane, s_rb[stage]);
             }
-            issued |= 1u << stage;
-            produce_compact<St, CELLS>(a, bd, bx, smraw + (size_t)stage * stage_bytes, bar, lane, s_rb[stage]);
+            const int nb_ = __shfl_sync(0xffffffffu, next, 0);
+            load_compact_batch(a, batches, bxs, nb_, nbatches, lane, cur);
+            if (lane == 0 && cur.batch < nbatches) next = atomicAdd(&a.work[0], 1);
         }
         if (!ok) {
             // let the copies still in flight land before the CTA's memory
@@ -1253,41 +1294,50 @@ k_budget_nodes(const void *__restrict__ pops_v, const float4 *__restrict__ U,
     if (threadIdx.x < 7) part[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// The same partial sums in the compact layout: blocks take rows (y, z) in
-// turn and their threads the row's entries; an entry is fluid when bit 31
-// of its link word is clear.
+// The same partial sums in the compact layout, one thread per stored entry
+// (grid-stride, coalesced); an entry is fluid when bit 31 of its link word
+// is clear.  The row of an entry -- its y, for the sin(2 pi y / ny) drive --
+// is found by binary search over the row offsets, only when that drive is
+// on.
 template <typename St>
 __global__ void __launch_bounds__(kBudThreads)
-k_budget_rows(const void *__restrict__ pops_v, const float4 *__restrict__ U, const uint32_t *__restrict__ links,
-              const int4 *__restrict__ rows, double *__restrict__ part, int nrows, long long Np, ForceArgs fa)
+k_budget_entries(const void *__restrict__ pops_v, const float4 *__restrict__ U, const uint32_t *__restrict__ links,
+                 const int4 *__restrict__ rows, double *__restrict__ part, int nrows, int M, long long Np,
+                 ForceArgs fa)
 {
     const St *pops = static_cast<const St *>(pops_v);
+    const bool wave = fa.w[0] != 0.f || fa.w[1] != 0.f || fa.w[2] != 0.f;
     double m = 0.0, px = 0.0, py = 0.0, pz = 0.0, umax = 0.0, nan = 0.0, work = 0.0;
-    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
-        const int4 rt = rows[r];
-        const double sw = sinpi(2.0 * (double)(r % fa.ny) / (double)fa.ny);
-        for (int c = rt.x + (int)threadIdx.x; c < rt.x + rt.z - rt.y; c += blockDim.x) {
-            if (links[c] >> 31) continue;
-            float sacc = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-            for_speeds<0, kQ>([&](auto pc) {
-                constexpr int p = decltype(pc)::value;
-                const float v = Pop<St>::template get<p>(pops[(long long)p * Np + c]);
-                sacc += v;
-                if (cx(p)) jx += cx(p) > 0 ? v : -v;
-                if (cy(p)) jy += cy(p) > 0 ? v : -v;
-                if (cz(p)) jz += cz(p) > 0 ? v : -v;
-            });
-            m += 1.0 + (double)sacc;
-            px += jx;
-            py += jy;
-            pz += jz;
-            const float4 u4 = U[c];
-            const float u2 = u4.x * u4.x + u4.y * u4.y + u4.z * u4.z;
-            if (!(u2 == u2) || !(sacc == sacc)) nan += 1.0;
-            else if (u2 > umax) umax = u2;
-            work += ((double)fa.g[0] + (double)fa.w[0] * sw) * u4.x + ((double)fa.g[1] + (double)fa.w[1] * sw) * u4.y +
-                    ((double)fa.g[2] + (double)fa.w[2] * sw) * u4.z;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
+        if (links[c] >> 31) continue;
+        float sacc = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+        for_speeds<0, kQ>([&](auto pc) {
+            constexpr int p = decltype(pc)::value;
+            const float v = Pop<St>::template get<p>(pops[(long long)p * Np + c]);
+            sacc += v;
+            if (cx(p)) jx += cx(p) > 0 ? v : -v;
+            if (cy(p)) jy += cy(p) > 0 ? v : -v;
+            if (cz(p)) jz += cz(p) > 0 ? v : -v;
+        });
+        m += 1.0 + (double)sacc;
+        px += jx;
+        py += jy;
+        pz += jz;
+        const float4 u4 = U[c];
+        const float u2 = u4.x * u4.x + u4.y * u4.y + u4.z * u4.z;
+        if (!(u2 == u2) || !(sacc == sacc)) nan += 1.0;
+        else if (u2 > umax) umax = u2;
+        double sw = 0.0;
+        if (wave) {
+            int lo = 0, hi = nrows - 1;  // last row whose first entry is <= c
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (rows[mid].x <= c) lo = mid; else hi = mid - 1;
+            }
+            sw = sinpi(2.0 * (double)(lo % fa.ny) / (double)fa.ny);
         }
+        work += ((double)fa.g[0] + (double)fa.w[0] * sw) * u4.x + ((double)fa.g[1] + (double)fa.w[1] * sw) * u4.y +
+                ((double)fa.g[2] + (double)fa.w[2] * sw) * u4.z;
     }
     __shared__ double sh[7][kBudThreads];
     sh[0][threadIdx.x] = m;
@@ -1764,14 +1814,14 @@ void launch_budget(const Dev &d, const Params &p, int parity, cudaStream_t s, bo
     if (d.compact) {
         const int nrows = d.ny * d.nz;
         if (d.prec == PREC_F16)
-            k_budget_rows<__half><<<d.budget_blocks, kBudThreads, 0, s>>>(d.pops[parity], d.U, d.links, d.rows,
-                                                                         d.budget_part, nrows, d.Np, fa);
+            k_budget_entries<__half><<<d.budget_blocks, kBudThreads, 0, s>>>(
+                d.pops[parity], d.U, d.links, d.rows, d.budget_part, nrows, d.M, d.Np, fa);
         else if (d.prec == PREC_BF16)
-            k_budget_rows<__nv_bfloat16><<<d.budget_blocks, kBudThreads, 0, s>>>(
-                d.pops[parity], d.U, d.links, d.rows, d.budget_part, nrows, d.Np, fa);
+            k_budget_entries<__nv_bfloat16><<<d.budget_blocks, kBudThreads, 0, s>>>(
+                d.pops[parity], d.U, d.links, d.rows, d.budget_part, nrows, d.M, d.Np, fa);
         else
-            k_budget_rows<float><<<d.budget_blocks, kBudThreads, 0, s>>>(d.pops[parity], d.U, d.links, d.rows,
-                                                                        d.budget_part, nrows, d.Np, fa);
+            k_budget_entries<float><<<d.budget_blocks, kBudThreads, 0, s>>>(
+                d.pops[parity], d.U, d.links, d.rows, d.budget_part, nrows, d.M, d.Np, fa);
     } else if (d.prec == PREC_F16)
         k_budget_nodes<__half><<<d.budget_blocks, kBudThreads, 0, s>>>(d.pops[parity], d.U, d.solid,
                                                                       d.budget_part, d.N, d.Np, fa);
