@@ -140,7 +140,10 @@ bool build_compact(Problem &P, const uint8_t *solid, int esz, bool cells)
 {
     const int node_bytes = kQ * esz + (cells ? 16 : 0) + 4;
     const int nx = P.nx, ny = P.ny, nz = P.nz, nrows = ny * nz;
-    const int full = (nx + 7) / 8 * 8;
+    // spans and windows start and end on whole 32-byte sectors of the
+    // population planes: 8 FP32 or 16 two-byte entries
+    const int A = 32 / esz;
+    const int full = (nx + A - 1) / A * A;
     std::vector<int> fl((size_t)nrows, -1), fh((size_t)nrows, -1);
     bool any_wrap = false;
     for (int r = 0; r < nrows; ++r) {
@@ -170,8 +173,8 @@ bool build_compact(Problem &P, const uint8_t *solid, int esz, bool cells)
                 }
             int slo = 0, shi = 0;
             if (hhi >= 0) {
-                slo = wraps ? 0 : hlo / 8 * 8;
-                shi = wraps ? full : (hhi + 1 + 7) / 8 * 8;
+                slo = wraps ? 0 : hlo / A * A;
+                shi = wraps ? full : (hhi + 1 + A - 1) / A * A;
             }
             const int r = y + ny * z;
             const int fr = fh[r] >= 0 ? (fl[r] | (fh[r] << 16)) : 0xFFFF;
@@ -189,8 +192,8 @@ bool build_compact(Problem &P, const uint8_t *solid, int esz, bool cells)
             X0 = 0;
             W = full;
         } else {
-            X0 = (c0 - 1) / 8 * 8;
-            W = (c1 + 2 + 7) / 8 * 8 - X0;
+            X0 = (c0 - 1) / A * A;
+            W = (c1 + 2 + A - 1) / A * A - X0;
         }
     };
     auto push = [&](int z, int y0, int nb, int c0, int c1, int X0, int W) {
@@ -232,8 +235,8 @@ bool build_compact(Problem &P, const uint8_t *solid, int esz, bool cells)
                     int X0r, Wr;
                     window(run.first, run.second, X0r, Wr);
                     if (Wr > cap) {
-                        const int L = (cap - 16) / 8 * 8;
-                        if (L < 8) return false;
+                        const int L = (cap - 2 * A) / A * A;
+                        if (L < A) return false;
                         for (int a0 = run.first; a0 <= run.second; a0 += L) {
                             const int a1 = std::min(run.second, a0 + L - 1);
                             window(a0, a1, X0r, Wr);
@@ -251,8 +254,8 @@ bool build_compact(Problem &P, const uint8_t *solid, int esz, bool cells)
             int c0 = fl[r], c1 = fh[r], X0, W;
             window(c0, c1, X0, W);
             if (W > cap) {
-                const int L = (cap - 16) / 8 * 8;
-                if (c0 == 0 || c1 == nx - 1 || L < 8) return false;
+                const int L = (cap - 2 * A) / A * A;
+                if (c0 == 0 || c1 == nx - 1 || L < A) return false;
                 for (int a0 = c0; a0 <= c1; a0 += L) {
                     const int a1 = std::min(c1, a0 + L - 1);
                     window(a0, a1, X0, W);

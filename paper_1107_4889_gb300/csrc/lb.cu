@@ -929,27 +929,29 @@ __device__ __forceinline__ void consume_compact(const LbArgs &a, int4 bd, const 
     const int z = bd.x, y0 = bd.y & 0xFFFFF, nb = (int)((uint32_t)bd.y >> 20);
     const int C0 = bd.z & 0xFFFF, C1 = (int)((uint32_t)bd.z >> 16);
     const int X0 = bd.w & 0xFFFF, W = (int)((uint32_t)bd.w >> 16);
-    const int Wc = C1 - C0 + 1, total = nb * Wc;
+    // threads run over the whole window from its sector-aligned start X0, so
+    // that a warp's stores cover whole 32-byte sectors of each plane
+    const int total = nb * W;
     const size_t pop_bytes = (size_t)kQ * nb * W * sizeof(St);
     const St *pst = reinterpret_cast<const St *>(base);
     const float4 *gst = reinterpret_cast<const float4 *>(base + pop_bytes);
     const uint32_t *lst =
         reinterpret_cast<const uint32_t *>(base + pop_bytes + (CELLS ? (size_t)nb * W * sizeof(float4) : 0));
     const int t = (int)threadIdx.x;
-    const int db = kStConsumers / Wc, dx = kStConsumers - db * Wc;
-    int b = t / Wc, xo = t - b * Wc;
+    const int db = kStConsumers / W, dx = kStConsumers - db * W;
+    int b = t / W, xo = t - b * W;
     for (int l = t; l < total; l += kStConsumers) {
-        const int bb = b, x = C0 + xo;
+        const int bb = b, x = X0 + xo;
         xo += dx;
         b += db;
-        if (xo >= Wc) {
-            xo -= Wc;
+        if (xo >= W) {
+            xo -= W;
             ++b;
         }
         const int y = y0 + bb;
         const int *rb = rbs[bb];
         const int fr = rb[9];
-        if (x < (fr & 0xFFFF) || x > (int)((uint32_t)fr >> 16)) continue;
+        if (x < max(C0, fr & 0xFFFF) || x > min(C1, (int)((uint32_t)fr >> 16))) continue;
         const int sx = bb * W + x - X0;
         const uint32_t lk = lst[sx];
         if (lk >> 31) continue;
