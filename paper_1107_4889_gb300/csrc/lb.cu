@@ -832,91 +832,51 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
 // the batch row's own row u = 4, of G / theta and the link words), so the
 // warp issues a batch with one coalesced load and no dependent lookups.
 constexpr int kMaxBatchRows = 16;  // rows of one compact batch (the set-up keeps to it)
-constexpr int kDescPerLane = (9 * kMaxBatchRows + 31) / 32;
 
-// The producer's copy of one batch: its record, the copy descriptors of its
-// batch rows (descriptor j = lane + 32 k in e[k]) and the fluid range of
-// each batch row (fr[k], for the lanes holding u = 4).  Loaded one batch
-// ahead, so that the loads overlap the consumers' work on earlier stages.
-struct CompactBatch {
-    int batch;
-    int4 bd;
-    int2 bx;
-    int2 e[kDescPerLane];
-    int fr[kDescPerLane];
-};
-
-__device__ __forceinline__ void load_compact_batch(const LbArgs &a, const int4 *__restrict__ batches,
-                                                   const int2 *__restrict__ bxs, int batch, int nbatches,
-                                                   int lane, CompactBatch &cb)
-{
-    cb.batch = batch;
-    if (batch >= nbatches) return;
-    cb.bd = batches[batch];
-    cb.bx = bxs[batch];
-    const int nb = (int)((uint32_t)cb.bd.y >> 20);
-    const int z = cb.bd.x, y0 = cb.bd.y & 0xFFFFF;
-#pragma unroll
-    for (int k = 0; k < kDescPerLane; ++k) {
-        const int j = lane + 32 * k;
-        cb.e[k] = make_int2(0, 0);
-        cb.fr[k] = 0;
-        if (j < 9 * nb) {
-            cb.e[k] = a.pool[cb.bx.x + j];
-            const int b = j / 9;
-            if (j - 9 * b == 4) cb.fr[k] = a.rows[y0 + b + a.ny * z].w;
-        }
-    }
-}
-
-// Producer side of one compact batch (descriptors already in registers):
-// rbs[b][u] = base of upstream row u of batch row b (entry of x' in that
-// row = base + x'), rbs[b][9] = the batch row's fluid x-range, written before
-// the stage's arrive; then the bulk copies.
+// rbs[b][u]: base of upstream row u of batch row b (entry of x' in that row =
+// base + x'), rbs[b][9]: the batch row's fluid x-range; written before the
+// stage's arrive, read by the consumers.
 template <typename St, bool CELLS>
-__device__ __forceinline__ void produce_compact(const LbArgs &a, const CompactBatch &cb, unsigned char *base,
+__device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, int2 bx, unsigned char *base,
                                                 uint32_t bar, int lane, int (*rbs)[10])
 {
-    const int nb = (int)((uint32_t)cb.bd.y >> 20);
-    const int W = (int)((uint32_t)cb.bd.w >> 16);
-    const int X0 = cb.bd.w & 0xFFFF;
-#pragma unroll
-    for (int k = 0; k < kDescPerLane; ++k) {
-        const int j = lane + 32 * k;
-        if (j >= 9 * nb) continue;
-        const int count = (int)((uint32_t)cb.e[k].y >> 16), at = cb.e[k].y & 0xFFFF;
+    const int nb = (int)((uint32_t)bd.y >> 20);
+    const int W = (int)((uint32_t)bd.w >> 16);
+    const int z = bd.x, y0 = bd.y & 0xFFFFF, X0 = bd.w & 0xFFFF;
+    for (int j = lane; j < 9 * nb; j += 32) {
+        const int2 e = a.pool[bx.x + j];
+        const int count = (int)((uint32_t)e.y >> 16), at = e.y & 0xFFFF;
         const int b = j / 9, u = j - 9 * b;
-        rbs[b][u] = count > 0 ? cb.e[k].x - at - X0 : 0;
-        if (u == 4) rbs[b][9] = cb.fr[k];
+        rbs[b][u] = count > 0 ? e.x - at - X0 : 0;
+        if (u == 4) rbs[b][9] = a.rows[y0 + b + a.ny * z].w;
     }
     __syncwarp();
-    if (lane == 0) mbar_expect_tx(bar, (uint32_t)cb.bx.y);
+    if (lane == 0) mbar_expect_tx(bar, (uint32_t)bx.y);
     __syncwarp();
     const uint64_t once = l2_evict_first();
     const size_t pop_bytes = (size_t)kQ * nb * W * sizeof(St);
-#pragma unroll
-    for (int k = 0; k < kDescPerLane; ++k) {
-        const int j = lane + 32 * k;
-        const int2 e = cb.e[k];
+    for (int j = lane; j < 9 * nb; j += 32) {
+        const int2 e = a.pool[bx.x + j];
         const int count = (int)((uint32_t)e.y >> 16);
-        if (j >= 9 * nb || count == 0) continue;
+        if (count == 0) continue;
         const int at = e.y & 0xFFFF;  // window offset of the first entry
         const int b = j / 9, u = j - 9 * b;
         const int dy = u % 3 - 1, dz = u / 3 - 1;
+        const uint32_t bar_ = bar;
         for_speeds<0, kQ>([&](auto pc) {
             constexpr int p = decltype(pc)::value;
             if (cy(p) != -dy || cz(p) != -dz) return;
             const St *g = static_cast<const St *>(a.src) + (size_t)p * (size_t)a.Np + (size_t)e.x;
             bulk_g2s_hint(smem_addr(base + ((size_t)(p * nb + b) * W + at) * sizeof(St)), g,
-                          (uint32_t)(count * (int)sizeof(St)), bar, once);
+                          (uint32_t)(count * (int)sizeof(St)), bar_, once);
         });
         if (u == 4) {
             if (CELLS)
                 bulk_g2s(smem_addr(base + pop_bytes + ((size_t)b * W + at) * sizeof(float4)), a.G + e.x,
-                         (uint32_t)(count * (int)sizeof(float4)), bar);
+                         (uint32_t)(count * (int)sizeof(float4)), bar_);
             bulk_g2s(smem_addr(base + pop_bytes + (CELLS ? (size_t)nb * W * sizeof(float4) : 0) +
                                ((size_t)b * W + at) * sizeof(uint32_t)),
-                     a.links + e.x, (uint32_t)(count * (int)sizeof(uint32_t)), bar);
+                     a.links + e.x, (uint32_t)(count * (int)sizeof(uint32_t)), bar_);
         }
     }
 }
@@ -1017,39 +977,38 @@ __global__ void __launch_bounds__(kStThreads, compact_min_blocks<St>())
         int it = 0;
         bool ok = true;
         unsigned issued = 0;  // stages whose last fill has copies issued
-        // software pipeline: the current batch's record and descriptors are
-        // in registers when its stage frees up; the next one is claimed and
-        // loaded right after the current one's copies are issued
         int next = 0;
         if (lane == 0) next = atomicAdd(&a.work[0], 1);
-        CompactBatch cur;
-        load_compact_batch(a, batches, bxs, __shfl_sync(0xffffffffu, next, 0), nbatches, lane, cur);
-        if (lane == 0 && cur.batch < nbatches) next = atomicAdd(&a.work[0], 1);
         for (;; ++it) {
             const int stage = it % ns;
+            const int batch = __shfl_sync(0xffffffffu, next, 0);
+            int4 bd = make_int4(-1, 0, 0, 0);
+            int2 bx = make_int2(0, 0);
+            if (batch < nbatches) {
+                if (lane == 0) next = atomicAdd(&a.work[0], 1);
+                bd = batches[batch];
+                bx = bxs[batch];
+            }
             if (it >= ns && !mbar_wait(smem_addr(&empty[stage]), (uint32_t)((it / ns - 1) & 1), a.wait_cycles)) {
                 if (lane == 0) atomicOr(&a.flags[FLAG_TIMEOUT], 1);
                 ok = false;
                 break;
             }
             const uint32_t bar = smem_addr(&full[stage]);
-            if (cur.batch >= nbatches) {
+            if (batch >= nbatches) {
                 if (lane == 0) {
                     s_desc[stage] = make_int4(-1, 0, 0, 0);
                     mbar_arrive(bar);
                 }
                 break;
             }
-            if (lane == 0) s_desc[stage] = cur.bd;
-            if (cur.batch == a.starve_batch) {  // fault injection: the stage never fills
+            if (lane == 0) s_desc[stage] = bd;
+            if (batch == a.starve_batch) {  // fault injection: the stage never fills
                 issued &= ~(1u << stage);
-            } else {
-                issued |= 1u << stage;
-                produce_compact<St, CELLS>(a, cur, smraw + (size_t)stage * stage_bytes, bar, lane, s_rb[stage]);
+                continue;
             }
-            const int nb_ = __shfl_sync(0xffffffffu, next, 0);
-            load_compact_batch(a, batches, bxs, nb_, nbatches, lane, cur);
-            if (lane == 0 && cur.batch < nbatches) next = atomicAdd(&a.work[0], 1);
+            issued |= 1u << stage;
+            produce_compact<St, CELLS>(a, bd, bx, smraw + (size_t)stage * stage_bytes, bar, lane, s_rb[stage]);
         }
         if (!ok) {
             // let the copies still in flight land before the CTA's memory
@@ -1519,7 +1478,7 @@ struct PrepareOp {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         raise_smem_limit((const void *)k_lb_compact<St, C, S_>, 200 * 1024);
-        long long best_cost = -1;
+        int best_per_sm = 0;
         for (int ns = kMaxStages; ns >= 2; --ns) {
             const size_t smem = (size_t)ns * d.lb_stage_bytes;
             if (smem > 200u * 1024u) continue;
@@ -1527,10 +1486,12 @@ struct PrepareOp {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_compact<St, C, S_>, kStThreads, smem);
             if (d.nc > 0 && per_sm > kLbCtasWithCells) per_sm = kLbCtasWithCells;
             if (per_sm < 1) continue;
+            // many more batches than CTA slots: the last wave costs little,
+            // while CTAs per SM hide the copies' latency; take the most CTAs
+            // per SM, then the deepest ring (the autotuner times the others)
             const long long slots = (long long)sms * per_sm;
-            const long long cost = ((d.nbatches + slots - 1) / slots) * per_sm;
-            if (best_cost < 0 || cost < best_cost) {
-                best_cost = cost;
+            if (per_sm > best_per_sm) {
+                best_per_sm = per_sm;
                 d.lb_stages = ns;
                 d.lb_smem = smem;
                 d.lb_grid = (int)(slots > d.nbatches ? d.nbatches : slots);
