@@ -833,22 +833,47 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
 // warp issues a batch with one coalesced load and no dependent lookups.
 constexpr int kMaxBatchRows = 16;  // rows of one compact batch (the set-up keeps to it)
 
+__device__ __forceinline__ void cp_async_4(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The producer's own copy of one batch's copy descriptors (pd[j], j < 9 nb)
+// and of its rows' fluid x-ranges (pfr[b]): asynchronous copies, so that
+// they are in flight while the producer waits for a free stage and hold no
+// registers meanwhile.  The caller waits for them (cp_async_wait_all, then
+// __syncwarp: pfr[b] is read by another lane than the one that copied it).
+__device__ __forceinline__ void load_descs(const LbArgs &a, int4 bd, int2 bx, int lane, int2 *pd, int *pfr)
+{
+    const int nb = (int)((uint32_t)bd.y >> 20);
+    const int z = bd.x, y0 = bd.y & 0xFFFFF;
+    for (int j = lane; j < 9 * nb; j += 32) cp_async_8(smem_addr(&pd[j]), a.pool + bx.x + j);
+    if (lane < nb) cp_async_4(smem_addr(&pfr[lane]), &a.rows[y0 + lane + a.ny * z].w);
+    cp_async_commit();
+}
+
 // rbs[b][u]: base of upstream row u of batch row b (entry of x' in that row =
 // base + x'), rbs[b][9]: the batch row's fluid x-range; written before the
 // stage's arrive, read by the consumers.
 template <typename St, bool CELLS>
-__device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, int2 bx, unsigned char *base,
-                                                uint32_t bar, int lane, int (*rbs)[10])
+__device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, int2 bx, const int2 *pd, const int *pfr,
+                                                unsigned char *base, uint32_t bar, int lane, int (*rbs)[10])
 {
     const int nb = (int)((uint32_t)bd.y >> 20);
     const int W = (int)((uint32_t)bd.w >> 16);
-    const int z = bd.x, y0 = bd.y & 0xFFFFF, X0 = bd.w & 0xFFFF;
+    const int X0 = bd.w & 0xFFFF;
     for (int j = lane; j < 9 * nb; j += 32) {
-        const int2 e = a.pool[bx.x + j];
+        const int2 e = pd[j];
         const int count = (int)((uint32_t)e.y >> 16), at = e.y & 0xFFFF;
         const int b = j / 9, u = j - 9 * b;
         rbs[b][u] = count > 0 ? e.x - at - X0 : 0;
-        if (u == 4) rbs[b][9] = a.rows[y0 + b + a.ny * z].w;
+        if (u == 4) rbs[b][9] = pfr[b];
     }
     __syncwarp();
     if (lane == 0) mbar_expect_tx(bar, (uint32_t)bx.y);
@@ -856,7 +881,7 @@ __device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, int2 b
     const uint64_t once = l2_evict_first();
     const size_t pop_bytes = (size_t)kQ * nb * W * sizeof(St);
     for (int j = lane; j < 9 * nb; j += 32) {
-        const int2 e = a.pool[bx.x + j];
+        const int2 e = pd[j];
         const int count = (int)((uint32_t)e.y >> 16);
         if (count == 0) continue;
         const int at = e.y & 0xFFFF;  // window offset of the first entry
@@ -897,9 +922,13 @@ __device__ __forceinline__ void consume_compact(const LbArgs &a, int4 bd, const 
     const float4 *gst = reinterpret_cast<const float4 *>(base + pop_bytes);
     const uint32_t *lst =
         reinterpret_cast<const uint32_t *>(base + pop_bytes + (CELLS ? (size_t)nb * W * sizeof(float4) : 0));
+    // (t, 256) -> (row, column) of the window without an integer division:
+    // floor((t + 1/2) / W) in FP32 is exact for t <= 256 (a quotient that is
+    // a whole number k is hit as k + 1/(2W), never rounded below k)
     const int t = (int)threadIdx.x;
-    const int db = kStConsumers / W, dx = kStConsumers - db * W;
-    int b = t / W, xo = t - b * W;
+    const float iW = 1.0f / (float)W;
+    const int db = (int)(((float)kStConsumers + 0.5f) * iW), dx = kStConsumers - db * W;
+    int b = (int)(((float)t + 0.5f) * iW), xo = t - b * W;
     for (int l = t; l < total; l += kStConsumers) {
         const int bb = b, x = X0 + xo;
         xo += dx;
@@ -957,6 +986,8 @@ __global__ void __launch_bounds__(kStThreads, compact_min_blocks<St>())
     __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages];
     __shared__ int4 s_desc[kMaxStages];
     __shared__ int s_rb[kMaxStages][kMaxBatchRows][10];
+    __shared__ __align__(8) int2 s_pd[9 * kMaxBatchRows];
+    __shared__ int s_pfr[kMaxBatchRows];
     __shared__ unsigned long long s_step;
     if (threadIdx.x == 0) {
         for (int k = 0; k < ns; ++k) {
@@ -970,26 +1001,42 @@ __global__ void __launch_bounds__(kStThreads, compact_min_blocks<St>())
 
     if (threadIdx.x >= kStConsumers) {
         // producer warp: claims batches from the global counter (see
-        // k_lb_staged), each one a batch ahead so that the atomic and the
-        // batch's descriptor loads overlap the wait for a free stage;
-        // s_desc[stage].x = -1 tells the consumers to stop
+        // k_lb_staged) two ahead.  While the stage for batch i is still in
+        // use it starts the copy of batch i's descriptors (its record came
+        // in the round before), loads batch i + 1's record (claimed the
+        // round before) and claims batch i + 2, so that all of it is in
+        // flight during the wait and the bulk copies start as soon as the
+        // stage is free; s_desc[stage].x = -1 tells the consumers to stop.
         const int lane = threadIdx.x - kStConsumers;
         int it = 0;
         bool ok = true;
         unsigned issued = 0;  // stages whose last fill has copies issued
-        int next = 0;
-        if (lane == 0) next = atomicAdd(&a.work[0], 1);
+        int claim = 0;
+        if (lane == 0) claim = atomicAdd(&a.work[0], 1);
+        int batch = __shfl_sync(0xffffffffu, claim, 0);
+        int4 bd = make_int4(-1, 0, 0, 0);
+        int2 bx = make_int2(0, 0);
+        if (batch < nbatches) {
+            bd = batches[batch];
+            bx = bxs[batch];
+            if (lane == 0) claim = atomicAdd(&a.work[0], 1);
+        }
         for (;; ++it) {
             const int stage = it % ns;
-            const int batch = __shfl_sync(0xffffffffu, next, 0);
-            int4 bd = make_int4(-1, 0, 0, 0);
-            int2 bx = make_int2(0, 0);
-            if (batch < nbatches) {
-                if (lane == 0) next = atomicAdd(&a.work[0], 1);
-                bd = batches[batch];
-                bx = bxs[batch];
+            if (batch < nbatches) load_descs(a, bd, bx, lane, s_pd, s_pfr);
+            const int nbatch = __shfl_sync(0xffffffffu, claim, 0);
+            int4 nbd = make_int4(-1, 0, 0, 0);
+            int2 nbx = make_int2(0, 0);
+            if (batch < nbatches && nbatch < nbatches) {
+                nbd = batches[nbatch];
+                nbx = bxs[nbatch];
+                if (lane == 0) claim = atomicAdd(&a.work[0], 1);
             }
-            if (it >= ns && !mbar_wait(smem_addr(&empty[stage]), (uint32_t)((it / ns - 1) & 1), a.wait_cycles)) {
+            const bool freed =
+                it < ns || mbar_wait(smem_addr(&empty[stage]), (uint32_t)((it / ns - 1) & 1), a.wait_cycles);
+            cp_async_wait_all();
+            __syncwarp();
+            if (!freed) {
                 if (lane == 0) atomicOr(&a.flags[FLAG_TIMEOUT], 1);
                 ok = false;
                 break;
@@ -1005,10 +1052,15 @@ __global__ void __launch_bounds__(kStThreads, compact_min_blocks<St>())
             if (lane == 0) s_desc[stage] = bd;
             if (batch == a.starve_batch) {  // fault injection: the stage never fills
                 issued &= ~(1u << stage);
-                continue;
+            } else {
+                issued |= 1u << stage;
+                produce_compact<St, CELLS>(a, bd, bx, s_pd, s_pfr, smraw + (size_t)stage * stage_bytes, bar,
+                                           lane, s_rb[stage]);
             }
-            issued |= 1u << stage;
-            produce_compact<St, CELLS>(a, bd, bx, smraw + (size_t)stage * stage_bytes, bar, lane, s_rb[stage]);
+            __syncwarp();  // every lane has read s_pd / s_pfr before the next copy into them
+            batch = nbatch < nbatches ? nbatch : nbatches;
+            bd = nbd;
+            bx = nbx;
         }
         if (!ok) {
             // let the copies still in flight land before the CTA's memory
