@@ -49,7 +49,7 @@ L2_BYTES = 129e6
 PREC_NAME = {"f32": "FP32", "f16": "binary16 (stochastic rounding)", "bf16": "bfloat16 (stochastic rounding)"}
 
 
-def _workload(name, precision="f32"):
+def _workload(name, precision="f32", planes=20):
     if name == "channel":
         g, c, p = wl.channel_workload()
         desc = "walled channel 64x64x256, 3650 RBC (H=0.35), G=5.376e-7"
@@ -71,7 +71,7 @@ def _workload(name, precision="f32"):
         desc = (f"tube r=120 in 256^3, {len(c['pos'])} RBC (H={wl.tube_hematocrit(g, len(c['pos'])):.2f} "
                 f"of the lumen), G_z={g['body_force'][2]:.3e}")
     elif name == "tube_slab":
-        g, c, p = wl.tube_slab()
+        g, c, p = wl.tube_slab(nz=planes)
         desc = (f"slab of the tube: r=120 in 256x256x{g['nz']} (periodic z), {len(c['pos'])} RBC, "
                 f"G_z={g['body_force'][2]:.3e}")
     else:
@@ -233,7 +233,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    geom, cells, params, desc = _workload(args.workload, args.precision)
+    geom, cells, params, desc = _workload(args.workload, args.precision, args.planes)
     nf = wl.fluid_count(geom)
     sg, sc, sp, sdesc = _cpu_sample(args.workload, args.precision)
     rate, steps, dt = _oracle_rate(sg, sc, sp, args.reference_budget)
@@ -265,7 +265,7 @@ def run_ours(args):
     if rank == 0:
         B.build()
     _barrier(ws)
-    geom, cells, params, desc = _workload(args.workload, args.precision)
+    geom, cells, params, desc = _workload(args.workload, args.precision, args.planes)
     if args.layout != "auto":
         params = dict(params, layout=args.layout)
         desc += f", {args.layout} layout"
@@ -691,6 +691,7 @@ def parse_args(argv=None):
     ap.add_argument("--mobility-xi-half", action="store_true", help="mobility test with xi = semi-axes / 2")
     ap.add_argument("--stats", action="store_true",
                     help="relative viscosity and near-wall hematocrit of the channel, binary16 against FP32")
+    ap.add_argument("--planes", type=int, default=20, help="planes of the tube_slab workload")
     ap.add_argument("--no-cells", action="store_true", help="drop the workload's cells (lattice pass alone)")
     ap.add_argument("--layout", choices=["auto", "dense", "compact"], default="auto",
                     help="storage layout of the lattice fields (auto: compact for sparse walled lattices)")

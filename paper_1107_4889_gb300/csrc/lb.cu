@@ -827,11 +827,27 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
 // (the row (y + dy, z + dz) that the speeds with c_y = -dy, c_z = -dz pull
 // from), the part of that row's span inside the window: its first entry and
 // (offset in the window | entry count << 16); and per batch the pool offset
-// of these descriptors and the bytes of all its copies.  Lane j takes
-// descriptor j and copies that part of each of its speeds' planes (and, for
-// the batch row's own row u = 4, of G / theta and the link words), so the
-// warp issues a batch with one coalesced load and no dependent lookups.
+// of these descriptors and the bytes of all its copies.  The lanes take the
+// batch's copies one each (speed plane k of batch row b reads descriptor
+// u(k) of that row; G / theta and the link words read u = 4), so a batch
+// row's 20 or 21 copies go out in one pass of the warp.
 constexpr int kMaxBatchRows = 16;  // rows of one compact batch (the set-up keeps to it)
+
+// Upstream row of speed p among the nine (dy, dz) rows of a compact batch
+// row, u = (dy + 1) + 3 (dz + 1) with (dy, dz) = (-c_y, -c_z), for a
+// run-time p: four bits per speed in two 64-bit constants.
+__host__ __device__ constexpr uint64_t upstream_bits(int first, int count)
+{
+    uint64_t v = 0;
+    for (int p = first; p < first + count && p < kQ; ++p)
+        v |= (uint64_t)((1 - cy(p)) + 3 * (1 - cz(p))) << (4 * (p - first));
+    return v;
+}
+__device__ __forceinline__ int upstream_row(int p)
+{
+    constexpr uint64_t lo = upstream_bits(0, 16), hi = upstream_bits(16, 16);
+    return (int)((p < 16 ? lo >> (4 * p) : hi >> (4 * (p - 16))) & 0xFu);
+}
 
 __device__ __forceinline__ void cp_async_4(uint32_t dst, const void *src)
 {
@@ -878,30 +894,30 @@ __device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, int2 b
     __syncwarp();
     if (lane == 0) mbar_expect_tx(bar, (uint32_t)bx.y);
     __syncwarp();
+    // one copy per lane: copy k of batch row b is speed plane k (k < 19),
+    // whose upstream row is u = (1 - c_y) + 3 (1 - c_z), then G / theta
+    // and the link words of the row itself (u = 4)
+    constexpr int kCopies = kQ + (CELLS ? 2 : 1);
     const uint64_t once = l2_evict_first();
     const size_t pop_bytes = (size_t)kQ * nb * W * sizeof(St);
-    for (int j = lane; j < 9 * nb; j += 32) {
-        const int2 e = pd[j];
+    for (int j = lane; j < kCopies * nb; j += 32) {
+        const int b = j / kCopies, k = j - b * kCopies;
+        const int u = k < kQ ? upstream_row(k) : 4;
+        const int2 e = pd[9 * b + u];
         const int count = (int)((uint32_t)e.y >> 16);
         if (count == 0) continue;
         const int at = e.y & 0xFFFF;  // window offset of the first entry
-        const int b = j / 9, u = j - 9 * b;
-        const int dy = u % 3 - 1, dz = u / 3 - 1;
-        const uint32_t bar_ = bar;
-        for_speeds<0, kQ>([&](auto pc) {
-            constexpr int p = decltype(pc)::value;
-            if (cy(p) != -dy || cz(p) != -dz) return;
-            const St *g = static_cast<const St *>(a.src) + (size_t)p * (size_t)a.Np + (size_t)e.x;
-            bulk_g2s_hint(smem_addr(base + ((size_t)(p * nb + b) * W + at) * sizeof(St)), g,
-                          (uint32_t)(count * (int)sizeof(St)), bar_, once);
-        });
-        if (u == 4) {
-            if (CELLS)
-                bulk_g2s(smem_addr(base + pop_bytes + ((size_t)b * W + at) * sizeof(float4)), a.G + e.x,
-                         (uint32_t)(count * (int)sizeof(float4)), bar_);
+        if (k < kQ) {
+            const St *g = static_cast<const St *>(a.src) + (size_t)k * (size_t)a.Np + (size_t)e.x;
+            bulk_g2s_hint(smem_addr(base + ((size_t)(k * nb + b) * W + at) * sizeof(St)), g,
+                          (uint32_t)(count * (int)sizeof(St)), bar, once);
+        } else if (CELLS && k == kQ) {
+            bulk_g2s(smem_addr(base + pop_bytes + ((size_t)b * W + at) * sizeof(float4)), a.G + e.x,
+                     (uint32_t)(count * (int)sizeof(float4)), bar);
+        } else {
             bulk_g2s(smem_addr(base + pop_bytes + (CELLS ? (size_t)nb * W * sizeof(float4) : 0) +
                                ((size_t)b * W + at) * sizeof(uint32_t)),
-                     a.links + e.x, (uint32_t)(count * (int)sizeof(uint32_t)), bar_);
+                     a.links + e.x, (uint32_t)(count * (int)sizeof(uint32_t)), bar);
         }
     }
 }
