@@ -46,10 +46,14 @@ UNIT = "MLUPS"
 L2_BYTES = 129e6
 
 
-PREC_NAME = {"f32": "FP32", "f16": "binary16 (stochastic rounding)", "bf16": "bfloat16 (stochastic rounding)"}
+PREC_NAME = {"f32": "FP32", "f16": "binary16", "bf16": "bfloat16"}
 
 
-def _workload(name, precision="f32", planes=20):
+def _prec_name(precision, rounding="stochastic"):
+    return PREC_NAME[precision] + ("" if precision == "f32" else f" ({rounding} rounding)")
+
+
+def _workload(name, precision="f32", planes=20, rounding="stochastic"):
     if name == "channel":
         g, c, p = wl.channel_workload()
         desc = "walled channel 64x64x256, 3650 RBC (H=0.35), G=5.376e-7"
@@ -77,7 +81,9 @@ def _workload(name, precision="f32", planes=20):
     else:
         raise SystemExit(f"unknown workload {name}")
     p = dict(p, precision=precision)
-    return g, c, p, f"{desc}, {PREC_NAME[precision]} populations"
+    if precision != "f32":
+        p["rounding"] = rounding
+    return g, c, p, f"{desc}, {_prec_name(precision, rounding)} populations"
 
 
 def _dist():
@@ -233,7 +239,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    geom, cells, params, desc = _workload(args.workload, args.precision, args.planes)
+    geom, cells, params, desc = _workload(args.workload, args.precision, args.planes, args.rounding)
     nf = wl.fluid_count(geom)
     sg, sc, sp, sdesc = _cpu_sample(args.workload, args.precision)
     rate, steps, dt = _oracle_rate(sg, sc, sp, args.reference_budget)
@@ -265,7 +271,7 @@ def run_ours(args):
     if rank == 0:
         B.build()
     _barrier(ws)
-    geom, cells, params, desc = _workload(args.workload, args.precision, args.planes)
+    geom, cells, params, desc = _workload(args.workload, args.precision, args.planes, args.rounding)
     if args.layout != "auto":
         params = dict(params, layout=args.layout)
         desc += f", {args.layout} layout"
@@ -512,7 +518,7 @@ def run_stats(args):
     for prec in ("f32", "f16"):
         out = {}
         for with_cells in (False, True):
-            geom, cells, params, desc = _workload("channel", prec)
+            geom, cells, params, desc = _workload("channel", prec, rounding=args.rounding)
             s = Solver(geom, cells if with_cells else None, params)
             powers, done = [], 0
             t0 = time.perf_counter()
@@ -545,7 +551,7 @@ def run_stats(args):
             d.append(k - 0.5)
         return float(np.mean(d))
 
-    line = {"metric": "channel long-run statistics, binary16 vs FP32", "workload": desc,
+    line = {"metric": f"channel long-run statistics, {_prec_name('f16', args.rounding)} vs FP32", "workload": desc,
             "steps": args.steps, "samples": a["samples"], "sample_every": every,
             "eta_rel": {"f32": a["eta_rel"], "f16": b["eta_rel"], "rel_diff": b["eta_rel"] / a["eta_rel"] - 1.0},
             "near_wall_hematocrit": {"f32": [round(float(v), 4) for v in a["profile"][:12]],
@@ -698,6 +704,8 @@ def parse_args(argv=None):
     ap.add_argument("--node-list", type=int, default=0, choices=[-1, 0, 1],
                     help="lattice pass over a fluid-node list (1), whole rows (-1), or the library's choice (0)")
     ap.add_argument("--precision", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--rounding", choices=["stochastic", "nearest"], default="stochastic",
+                    help="rounding of the 16-bit population stores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune-steps", type=int, default=50,
                     help="steps per launch shape the autotuner times during warm-up (0: no tuning)")

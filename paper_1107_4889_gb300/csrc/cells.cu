@@ -155,6 +155,7 @@ struct GbArgs {
     unsigned long long *clamps;
     int nc, cap, maxn, nb[3], per[3];
     double L[3], rc2, rcw2, smin, smin_w, rw2, eps0, rho_floor, rho_cut;
+    double ismin, ismin_w;  // 1 / sigma_min (cell pairs, cell-wall pairs)
     float rho_cut_f;  // FP32 prefilter bound (rho_cut with a safety margin)
     float rc_lo2, rc_hi2, rcw2_f, Lf[3];  // FP32 candidate band around r_cut, wall radius
     int wnb[3];                           // wall-particle grid
@@ -409,36 +410,40 @@ __device__ __forceinline__ void gb_body(const GbArgs &g, int blk)
         for (int c = 0; c < kGbWarps; ++c) s_qpre[c + 1] += s_qpre[c];
     }
     __syncthreads();
-    // 4. the block's queue, all lanes busy: one FP64 Gay-Berne pair each
-    //    (Sec. 2.5, App. B); cells and wall particles alike
+    // 4. the block's queue, all lanes busy: one Gay-Berne pair each (Sec.
+    //    2.5, App. B), cells and wall particles alike: the geometry up to
+    //    rho in FP64, the force law in FP32 (gb_pair_mixed); step 5 sums
+    //    the pairs per cell in FP64
     const int P = s_qpre[kGbWarps];
     for (int e = threadIdx.x; e < P; e += blockDim.x) {
         int c = 0;
         while (c + 1 < kGbWarps && s_qpre[c + 1] <= e) ++c;
         const int ci = blk * kGbWarps + c;
         const int v = s_q[c][e - s_qpre[c]];
-        double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+        float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
         int clamped = 0;
         const double *ai = &g.A[6 * ci];
         const Sym3 Ai{ai[0], ai[1], ai[2], ai[3], ai[4], ai[5]};
+        const float *aif = &g.Af[6 * ci];
+        const float Ai_f[6] = {aif[0], aif[1], aif[2], aif[3], aif[4], aif[5]};
         if (v >= 0) {
             double d[3] = {__dsub_rn(g.R[3 * ci], g.R[3 * v]), __dsub_rn(g.R[3 * ci + 1], g.R[3 * v + 1]),
                            __dsub_rn(g.R[3 * ci + 2], g.R[3 * v + 2])};
             min_image(d, g.per, g.L);
             const double *aj = &g.A[6 * v];
             const Sym3 Aj{aj[0], aj[1], aj[2], aj[3], aj[4], aj[5]};
-            gb_pair(d, Ai, Aj, g.smin, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
+            gb_pair_mixed(d, Ai, Aj, Ai_f, g.smin, g.ismin, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
         } else {
             const int w = -1 - v;
             double d[3] = {g.R[3 * ci] - (double)g.wall_xyz[3 * w], g.R[3 * ci + 1] - (double)g.wall_xyz[3 * w + 1],
                            g.R[3 * ci + 2] - (double)g.wall_xyz[3 * w + 2]};
             min_image(d, g.per, g.L);
             const Sym3 Aw{g.rw2, g.rw2, g.rw2, 0.0, 0.0, 0.0};
-            gb_pair(d, Ai, Aw, g.smin_w, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
+            gb_pair_mixed(d, Ai, Aw, Ai_f, g.smin_w, g.ismin_w, g.eps0, g.rho_floor, g.rho_cut, F, T, clamped);
         }
         for (int a = 0; a < 3; ++a) {
-            s_res[e][a] = F[a];
-            s_res[e][3 + a] = T[a];
+            s_res[e][a] = (double)F[a];
+            s_res[e][3 + a] = (double)T[a];
         }
         if (clamped) atomicAdd(&s_clamped, clamped);
     }
@@ -702,15 +707,23 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
         const int slo = (int)(word & 0xFFu), shi = (int)((word >> 8) & 0xFFu);
         return (x >= slo && x <= shi) ? wc[(int)(word >> 16) + x - slo] : 0.f;
     };
-    // 4. the visit items, one lane per row: the row's words and those of its
-    //    four neighbour rows are read once, w(x - 1), w(x), w(x + 1) slide
+    // 4. the visit items, one lane per item, so that consecutive lanes write
+    //    consecutive list entries: the item's row is reached by walking
+    //    forward from the row of the previous round's last item (rows are in
+    //    item order; a row without items has the next row's first item)
     int2 *sp_idx = a.sp_idx + (size_t)i * a.sp_cap;
     float4 *sp_val = a.sp_val + (size_t)i * a.sp_cap;
-    for (int rb = 0; rb < nrows; rb += 32) {
-        const int r = rb + lane;
-        const unsigned vw = r < nrows ? vrow[r] : 0xFFu;
-        const int vlo = (int)(vw & 0xFFu), vhi = (int)((vw >> 8) & 0xFFu);
-        if (vlo > vhi) continue;
+    const int vcount = min(vtot, a.sp_cap);
+    int rstart = 0;
+    for (int t0 = 0; t0 < vcount; t0 += 32) {
+        const int t = t0 + lane;
+        int r = rstart;
+        if (t < vcount)
+            while (r + 1 < nrows && (int)(vrow[r + 1] >> 16) <= t) ++r;
+        rstart = __shfl_sync(0xffffffffu, r, 31);
+        if (t >= vcount) continue;
+        const unsigned vw = vrow[r];
+        const int x = (int)(vw & 0xFFu) + (t - (int)(vw >> 16));
         const int i2 = (int)(((float)r + 0.5f) * inv1), i1 = r - i2 * n1;
         const unsigned own = srow[r];
         const unsigned ym = i1 > 0 ? srow[r - 1] : 0xFFu, yp = i1 + 1 < n1 ? srow[r + 1] : 0xFFu;
@@ -722,25 +735,15 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
         const int lrow = wrap1(o[1] + i1, a.ny) + a.ny * wrap1(o[2] + i2, a.nz);
         int ebase = a.nx * lrow, elo = 0, ehi = a.nx;
         if (a.rows) {
-            const int4 rt = a.rows[lrow];
+            const int4 rt = __ldg(&a.rows[lrow]);
             ebase = rt.x - rt.y;
             elo = rt.y;
             ehi = rt.z;
         }
-        const int pkr = (i1 << 10) | (i2 << 20);
-        int pos = (int)(vw >> 16);
-        float wl = W(own, vlo - 1), wm = W(own, vlo);
-        for (int x = vlo; x <= vhi; ++x, ++pos) {
-            const float wr = W(own, x + 1);
-            if (pos < a.sp_cap) {
-                const int xw = wrap1(o[0] + x, a.nx);
-                sp_idx[pos] = make_int2(xw >= elo && xw < ehi ? ebase + xw : a.zero_entry, x | pkr);
-                sp_val[pos] = make_float4(wm, 0.5f * (wr - wl), 0.5f * (W(yp, x) - W(ym, x)),
-                                          0.5f * (W(zp, x) - W(zm, x)));
-            }
-            wl = wm;
-            wm = wr;
-        }
+        const int xw = wrap1(o[0] + x, a.nx);
+        sp_idx[t] = make_int2(xw >= elo && xw < ehi ? ebase + xw : a.zero_entry, x | (i1 << 10) | (i2 << 20));
+        sp_val[t] = make_float4(W(own, x), 0.5f * (W(own, x + 1) - W(own, x - 1)), 0.5f * (W(yp, x) - W(ym, x)),
+                                0.5f * (W(zp, x) - W(zm, x)));
     }
     const int run = vtot;
     for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
@@ -1365,6 +1368,8 @@ static GbArgs gb_args(const Dev &d, const Params &p)
     g.rho_floor = p.rho_floor;
     g.rho_cut = p.rho_cut;
     g.rho_cut_f = (float)(p.rho_cut * 1.001 + 1e-3);
+    g.ismin = 1.0 / p.smin_cc;
+    g.ismin_w = 1.0 / p.smin_w;
     g.Rf = d.Rf;
     g.Af = d.Af;
     // FP32 positions carry ~1e-7 relative error: outside a band of
