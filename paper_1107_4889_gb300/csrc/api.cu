@@ -587,7 +587,8 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.pops[0] = cv.take<uint8_t>(19 * Np * (size_t)pop_bytes(P.prec));
     d.pops[1] = cv.take<uint8_t>(19 * Np * (size_t)pop_bytes(P.prec));
     d.U = cv.take<float4>(Np);
-    d.S = P.want_sigma ? cv.take<float4>(2 * Np) : nullptr;
+    d.S = P.want_sigma ? cv.take<float4>(Np) : nullptr;
+    d.Syz = P.want_sigma ? cv.take<float>(Np) : nullptr;
     d.G = P.nc > 0 ? cv.take<float4>(Np) : nullptr;
     d.rho = cv.take<float>(Np);
     // node flags stay dense (the shape lists test every node of a cell's box)
@@ -953,7 +954,8 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
         RBC_CU(cudaMemsetAsync(d.pops[0], 0, 19 * Np * pop_bytes(d.prec), s));
         RBC_CU(cudaMemsetAsync(d.pops[1], 0, 19 * Np * pop_bytes(d.prec), s));
         RBC_CU(cudaMemsetAsync(d.U, 0, Np * sizeof(float4), s));
-        if (d.S) RBC_CU(cudaMemsetAsync(d.S, 0, 2 * Np * sizeof(float4), s));
+        if (d.S) RBC_CU(cudaMemsetAsync(d.S, 0, Np * sizeof(float4), s));
+        if (d.Syz) RBC_CU(cudaMemsetAsync(d.Syz, 0, Np * sizeof(float), s));
         if (d.G) RBC_CU(cudaMemsetAsync(d.G, 0, Np * sizeof(float4), s));
         RBC_CU(cudaMemsetAsync(d.rho, 0, Np * sizeof(float), s));
         std::vector<uint32_t> links;
@@ -1553,7 +1555,8 @@ size_t ckpt_bytes(const rbc_handle *h)
     const Dev &d = h->d;
     const size_t Np = (size_t)d.Np, n = (size_t)d.nc;
     return kCkptWords * 8 + 19 * Np * (size_t)pop_bytes(d.prec) + Np * sizeof(float4) +
-           (d.S ? 2 * Np * sizeof(float4) : 0) + n * (3 + 4 + 3 + 3) * sizeof(double) + n * sizeof(int);
+           (d.S ? Np * (sizeof(float4) + sizeof(float)) : 0) + n * (3 + 4 + 3 + 3) * sizeof(double) +
+           n * sizeof(int);
 }
 
 void ckpt_header(const rbc_handle *h, int64_t w[kCkptWords])
@@ -1599,7 +1602,8 @@ int rbc_save(rbc_handle *h, void *buf, size_t bytes)
     };
     RBC_CU(take(d.pops[h->step & 1], 19 * Np * (size_t)pop_bytes(d.prec)));
     RBC_CU(take(d.U, Np * sizeof(float4)));
-    if (d.S) RBC_CU(take(d.S, 2 * Np * sizeof(float4)));
+    if (d.S) RBC_CU(take(d.S, Np * sizeof(float4)));
+    if (d.Syz) RBC_CU(take(d.Syz, Np * sizeof(float)));
     if (n) {
         RBC_CU(take(d.R, 3 * n * sizeof(double)));
         RBC_CU(take(d.q, 4 * n * sizeof(double)));
@@ -1639,7 +1643,8 @@ int rbc_load(rbc_handle *h, const void *buf, size_t bytes)
     };
     RBC_CU(put(d.pops[h->step & 1], 19 * Np * (size_t)pop_bytes(d.prec)));
     RBC_CU(put(d.U, Np * sizeof(float4)));
-    if (d.S) RBC_CU(put(d.S, 2 * Np * sizeof(float4)));
+    if (d.S) RBC_CU(put(d.S, Np * sizeof(float4)));
+    if (d.Syz) RBC_CU(put(d.Syz, Np * sizeof(float)));
     if (n) {
         RBC_CU(put(d.R, 3 * n * sizeof(double)));
         RBC_CU(put(d.q, 4 * n * sizeof(double)));

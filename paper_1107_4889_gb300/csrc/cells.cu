@@ -479,7 +479,8 @@ struct ShapeArgs {
     float *hdr;
     const double *R, *q;
     const uint8_t *solid;
-    const float4 *U, *S;  // node-major velocity, stress (2 per node)
+    const float4 *U, *S;  // node-major velocity (+ stress xz in w), stress xx yy zz xy
+    const float *Syz;     // node-major stress yz
     float4 *G;            // node-major force density and hematocrit sum
     int2 *sp_idx;
     float4 *sp_val;
@@ -812,7 +813,7 @@ __device__ __forceinline__ void sample_sums(const ShapeArgs &a, int i, int n, fl
     for (int e0 = lane + 32 * part; e0 < n; e0 += 32 * parts * kIlp) {
         int2 ix[kIlp];
         float4 v[kIlp];
-        float u[kIlp][3];
+        float u[kIlp][3], sxz[kIlp];  // u and, in U.w, the stress xz
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             const int e = e0 + 32 * parts * j;
@@ -825,6 +826,7 @@ __device__ __forceinline__ void sample_sums(const ShapeArgs &a, int i, int n, fl
             u[j][0] = u4.x;
             u[j][1] = u4.y;
             u[j][2] = u4.z;
+            sxz[j] = u4.w;
         }
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
@@ -843,17 +845,18 @@ __device__ __forceinline__ void sample_sums(const ShapeArgs &a, int i, int n, fl
             for (int j = 0; j < kIlp; ++j) {
                 const int g = ix[j].x;
                 on[j] = v[j].x > 0.f && v[j].y * v[j].y + v[j].z * v[j].z + v[j].w * v[j].w > thr;
-                float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+                float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f);
+                float syz = 0.f;
                 if (on[j]) {
-                    s0 = a.S[2 * (long long)g];
-                    s1 = a.S[2 * (long long)g + 1];
+                    s0 = a.S[g];
+                    syz = a.Syz[g];
                 }
                 sg[j][0] = s0.x;
                 sg[j][1] = s0.y;
                 sg[j][2] = s0.z;
                 sg[j][3] = s0.w;
-                sg[j][4] = s1.x;
-                sg[j][5] = s1.y;
+                sg[j][4] = sxz[j];
+                sg[j][5] = syz;
             }
 #pragma unroll
             for (int j = 0; j < kIlp; ++j) {
@@ -1193,6 +1196,7 @@ ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
     a.solid = d.solid;
     a.U = d.U;
     a.S = d.S;
+    a.Syz = d.Syz;
     a.G = d.G;
     a.sp_idx = d.sp_idx[buf];
     a.sp_val = d.sp_val[buf];

@@ -36,7 +36,8 @@ struct Dev {
     // node-major vectors, so that the per-cell gathers and the spread take
     // one access per node
     float4 *U;          // Np: velocity of the last lattice pass (x, y, z, 0)
-    float4 *S;          // 2 Np: stress of the last pass, (xx yy zz xy) (xz yz 0 0), or null
+    float4 *S;          // Np: stress of the last pass, (xx yy zz xy) (its xz sits in U.w), or null
+    float *Syz;         // Np: stress yz of the last pass, or null
     float4 *G;          // Np: force density (x, y, z) and sum of smoothed characteristic
                         // functions (w), accumulated by the cells, zeroed by the pass
     float *rho;         // 1 plane: density for field output

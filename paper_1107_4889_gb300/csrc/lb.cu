@@ -37,7 +37,8 @@ struct LbArgs {
     const uint32_t *links;
     const int4 *rows;  // compact layout: row table (internal.h), else null
     const int2 *pool;  // compact lattice pass: per batch row, nine copy descriptors (produce_compact)
-    float4 *G, *U, *S;  // node-major: force density + hematocrit sum, velocity, stress (2 per node)
+    float4 *G, *U, *S;  // node-major: force density + hematocrit sum, velocity (+ stress xz), stress xx yy zz xy
+    float *Syz;         // node-major: stress yz
     int *flags;
     int *work;                 // [0] next batch, [1] CTAs done; zero at launch, reset by the last CTA
     unsigned long long *step;  // passes done: the counter of the rounding's random numbers
@@ -297,10 +298,12 @@ __device__ __forceinline__ void collide_node(const LbArgs &a, float (&d)[kQ], ui
             }
         }
     });
-    a.U[n] = make_float4(ux, uy, uz, 0.f);
+    // the stress's six components ride in U.w (xz), S (xx yy zz xy) and Syz:
+    // 36 bytes per node
+    a.U[n] = make_float4(ux, uy, uz, SIGMA ? -ff * pxz : 0.f);
     if (SIGMA) {
-        a.S[2 * n] = make_float4(-ff * pxx, -ff * pyy, -ff * pzz, -ff * pxy);
-        a.S[2 * n + 1] = make_float4(-ff * pxz, -ff * pyz, 0.f, 0.f);
+        a.S[n] = make_float4(-ff * pxx, -ff * pyy, -ff * pzz, -ff * pxy);
+        a.Syz[n] = -ff * pyz;
     }
     if (!(rho > 0.0f) || !(usq <= a.mach2)) atomicOr(&a.flags[FLAG_UNSTABLE], 1);
 }
@@ -398,8 +401,8 @@ __device__ __noinline__ void boundary_node(const LbArgs &a, uint32_t n, uint32_t
     const float ir = 1.0f / (1.0f + drho);
     a.U[n] = make_float4(jx * ir, jy * ir, jz * ir, 0.f);
     if (SIGMA) {
-        a.S[2 * n] = make_float4(0.f, 0.f, 0.f, 0.f);
-        a.S[2 * n + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a.S[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a.Syz[n] = 0.f;
     }
     if (CELLS) a.G[n] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
@@ -1676,6 +1679,7 @@ static LbArgs lb_args(const Dev &d, const Params &p, int parity)
     a.G = d.G;
     a.U = d.U;
     a.S = d.S;
+    a.Syz = d.Syz;
     a.flags = d.flags;
     a.work = d.lb_work;
     a.step = d.lb_step;
@@ -1804,14 +1808,14 @@ void launch_rho(const Dev &d, int parity, cudaStream_t s)
 
 // Wall shear stress: the traction sigma n of the last pass's stress on the
 // wall's tangent plane, t - (t.n) n, added to the node's time sums.
-__global__ void k_wss(const float4 *__restrict__ S, long long Np, const int *__restrict__ node,
-                      const float *__restrict__ nrm, double *__restrict__ acc, int nw)
+__global__ void k_wss(const float4 *__restrict__ S, const float4 *__restrict__ U, const float *__restrict__ Syz,
+                      const int *__restrict__ node, const float *__restrict__ nrm, double *__restrict__ acc, int nw)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nw) return;
     const long long n = node[k];
-    const float4 s0 = S[2 * n], s1 = S[2 * n + 1];
-    const float sxx = s0.x, syy = s0.y, szz = s0.z, sxy = s0.w, sxz = s1.x, syz = s1.y;
+    const float4 s0 = S[n];
+    const float sxx = s0.x, syy = s0.y, szz = s0.z, sxy = s0.w, sxz = U[n].w, syz = Syz[n];
     const float nx = nrm[3 * k], ny = nrm[3 * k + 1], nz = nrm[3 * k + 2];
     const float tx = sxx * nx + sxy * ny + sxz * nz;
     const float ty = sxy * nx + syy * ny + syz * nz;
@@ -1824,7 +1828,8 @@ __global__ void k_wss(const float4 *__restrict__ S, long long Np, const int *__r
 
 void launch_wss(const Dev &d, cudaStream_t s)
 {
-    if (d.nwss > 0 && d.S) k_wss<<<(d.nwss + 255) / 256, 256, 0, s>>>(d.S, d.Np, d.wss_node, d.wss_n, d.wss_acc, d.nwss);
+    if (d.nwss > 0 && d.S)
+        k_wss<<<(d.nwss + 255) / 256, 256, 0, s>>>(d.S, d.U, d.Syz, d.wss_node, d.wss_n, d.wss_acc, d.nwss);
 }
 
 int budget_blocks_for(int N)

@@ -155,7 +155,7 @@ def test_compact_layout_footprint_follows_the_fluid_nodes(lib):
     populations: the dense layout needs ~18 GB, the compact one stores per
     lattice row only the span its fluid nodes reach, so its workspace is
     within 1.5x of the fluid nodes times the bytes of one stored entry
-    (populations 2 x 19 x 2, u 16, sigma 32, rho 4, links 4) plus one byte
+    (populations 2 x 19 x 2, u 16, sigma 20, rho 4, links 4) plus one byte
     of node flags per lattice node."""
     geom = wl.y_bifurcation(512, 60.0, 45.0)
     p = wl.params(precision="f16")
@@ -164,7 +164,7 @@ def test_compact_layout_footprint_follows_the_fluid_nodes(lib):
     auto = rbc.rbc_workspace_size(geom, None, p)
     nf = wl.fluid_count(geom)
     N = 512 ** 3
-    per_entry = 2 * 19 * 2 + 16 + 32 + 4 + 4
+    per_entry = 2 * 19 * 2 + 16 + 20 + 4 + 4
     assert dense > 15e9 and auto == compact
     assert compact < 1.5 * nf * per_entry + N + 64e6, (compact, nf)
     print(f"Y 512^3 binary16: dense {dense / 1e9:.2f} GB, compact {compact / 1e9:.2f} GB, {nf} fluid nodes")
