@@ -530,9 +530,10 @@ int weights_words(const Params &p)
     return 2 * p.box_dim * p.box_dim + p.sup_cap + (p.sup_cap + 1) / 2;
 }
 
-// support interval [lo, hi] of box row (i1, i2) along x; lo > hi if empty
-__device__ __forceinline__ void support_row(const float Q[9], const float bs[3], const float t[3], int n0, int i1,
-                                            int i2, int &lo, int &hi)
+// support interval [lo, hi] of box row (i1, i2) along x; lo > hi if empty.
+// lim[b] = 2 / t[b] = xi_b and iq[b] = 1 / Q_xb are the cell's, computed once.
+__device__ __forceinline__ void support_row(const float Q[9], const float bs[3], const float lim3[3],
+                                            const float iq3[3], int n0, int i1, int i2, int &lo, int &hi)
 {
     const float r1 = bs[1] + (float)i1, r2 = bs[2] + (float)i2;
     float flo = -1e30f, fhi = 1e30f;
@@ -540,12 +541,12 @@ __device__ __forceinline__ void support_row(const float Q[9], const float bs[3],
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
         const float cb = Q[3 + b] * r1 + Q[6 + b] * r2;  // y_b without the x term
-        const float lim = 2.0f / t[b];                      // |y_b| < xi_b
+        const float lim = lim3[b];                          // |y_b| < xi_b
         if (fabsf(Q[b]) < 1e-7f) {
             empty |= fabsf(cb) >= lim * 1.0001f;
             continue;
         }
-        const float iq = 1.0f / Q[b];
+        const float iq = iq3[b];
         const float u1 = (-lim - cb) * iq, u2 = (lim - cb) * iq;
         flo = fmaxf(flo, fminf(u1, u2));
         fhi = fminf(fhi, fmaxf(u1, u2));
@@ -612,6 +613,12 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
     const int n0 = nn[0], n1 = nn[1], n2 = nn[2], nrows = n1 * n2;
     const float inv1 = 1.0f / (float)n1;
     const float tq[3] = {a.two_over_xi[0], a.two_over_xi[1], a.two_over_xi[2]};
+    float lim3[3], iq3[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        lim3[b] = 2.0f / tq[b];
+        iq3[b] = fabsf(Q[b]) < 1e-7f ? 0.0f : 1.0f / Q[b];
+    }
     // 1. support interval and first item of every row
     int stot = 0;
     if (ok) {
@@ -620,7 +627,7 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
             int slo = 1, shi = 0;
             if (r < nrows) {
                 const int i2 = (int)(((float)r + 0.5f) * inv1), i1 = r - i2 * n1;
-                support_row(Q, bs, tq, n0, i1, i2, slo, shi);
+                support_row(Q, bs, lim3, iq3, n0, i1, i2, slo, shi);
             }
             const int len = slo <= shi ? shi - slo + 1 : 0;
             int incl = len;
@@ -1079,11 +1086,12 @@ __device__ __forceinline__ float pow_kappa(float x, const ShapeArgs &a)
     return r;
 }
 
-// Two warps per cell (kCellWarps / 2 cells per block): both sample half of
-// the cell's list; the first adds the halves (fixed order), computes the
-// impulses J, L, hands them to the second through shared memory and a named
-// barrier of the pair, and finishes the rigid update (the sub-rotations and
-// the stored state) while the second spreads over the whole list.
+// Two warps per cell (kCellWarps / 2 cells per block), the packed solves'
+// per-cell kernel: both sample half of the cell's list; the first adds the
+// halves (fixed order), computes the impulses J, L, hands them to the second
+// through shared memory and a named barrier of the pair, and finishes the
+// rigid update (the sub-rotations and the stored state) while the second
+// spreads over the whole list.
 constexpr int kCellsPerBlock = kCellWarps / 2;
 
 // Named barriers 1 and 2 (one per pair of warps; 0 is __syncthreads).  The
@@ -1178,13 +1186,65 @@ __device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &
 
 // At most 72 registers so that 7 blocks fit an SM: the kernel waits on
 // memory and wants the warps (at 80 registers, 6 blocks per SM ran 3,650
-// cells as two full waves and a last one of a single block).
+// cells as two full waves and a last one of a single block; at 64, 8
+// blocks, the stress sampling spilled and the channel step took 3 % longer).
 constexpr int kCellBlocksPerSm = 7;
 
+// The per-cell kernel of a single solve: one warp per cell samples the whole
+// list, runs the rigid update and spreads; four cells per block, no barriers
+// between warps.  Twice as many cells in flight per SM as the two-warp form
+// (each taking longer): the tube step 1,239 -> 1,221 us, the channel
+// 108.2 -> 105.7 us.
+constexpr int kCells1Warps = 4;
+
 template <bool ALPHA>
-__global__ void __launch_bounds__(32 * kCellWarps, kCellBlocksPerSm) k_cells(ShapeArgs a, RigidArgs ra, int nc)
+__device__ __forceinline__ void cells_body1(const ShapeArgs &a, const RigidArgs &ra, int nc, int i)
 {
-    cells_body<ALPHA>(a, ra, nc, blockIdx.x);
+    if (i >= nc) return;  // uniform across the warp
+    const int lane = threadIdx.x & 31;
+    const int n = a.sp_cnt[i];
+    const float S = a.sp_S[i];
+    float sums[9];
+    sample_sums<ALPHA>(a, i, n, S, sums, 0, 1);
+    float jl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool go = false;
+    auto publish = [&](const float (&J)[3], const float (&L)[3]) {
+        go = n > 0;
+        const float iS = go ? 1.0f / S : 0.f;
+        for (int d = 0; d < 3; ++d) {
+            jl[d] = J[d] * iS;
+            jl[3 + d] = 0.5f * L[d] * iS;
+        }
+    };
+    rigid_update(ra, i, S, sums, publish);
+    if (!go) return;
+    const float Jx = jl[0], Jy = jl[1], Jz = jl[2], Lx = jl[3], Ly = jl[4], Lz = jl[5];
+    const int2 *idx = a.sp_idx + (size_t)i * a.sp_cap;
+    const float4 *val = a.sp_val + (size_t)i * a.sp_cap;
+    for (int e0 = lane; e0 < n; e0 += 32 * kIlp) {
+        int g[kIlp];
+        float4 v[kIlp];
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            const int e = e0 + 32 * j;
+            g[j] = e < n ? idx[e].x : -1;
+            v[j] = e < n ? val[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            if (g[j] < 0) continue;
+            atomicAdd(&a.G[g[j]], make_float4(-Jx * v[j].x + (Ly * v[j].w - Lz * v[j].z),
+                                              -Jy * v[j].x + (Lz * v[j].y - Lx * v[j].w),
+                                              -Jz * v[j].x + (Lx * v[j].z - Ly * v[j].y),
+                                              v[j].x > 0.f ? 1.0f - pow_kappa(1.0f - v[j].x, a) : 0.f));
+        }
+    }
+}
+
+template <bool ALPHA>
+__global__ void __launch_bounds__(32 * kCells1Warps, kCellBlocksPerSm) k_cells(ShapeArgs a, RigidArgs ra, int nc)
+{
+    cells_body1<ALPHA>(a, ra, nc, blockIdx.x * kCells1Warps + (int)(threadIdx.x >> 5));
 }
 
 ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
@@ -1456,11 +1516,11 @@ void launch_cells(const Dev &d, const Params &p, int buf, cudaStream_t s)
     if (d.nc == 0) return;
     const ShapeArgs a = shape_args(d, p, buf);
     const RigidArgs r = rigid_args(d, p);
-    const int blocks = (d.nc + kCellsPerBlock - 1) / kCellsPerBlock;
+    const int blocks = (d.nc + kCells1Warps - 1) / kCells1Warps;
     if (d.S != nullptr)
-        k_cells<true><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc);
+        k_cells<true><<<blocks, 32 * kCells1Warps, 0, s>>>(a, r, d.nc);
     else
-        k_cells<false><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc);
+        k_cells<false><<<blocks, 32 * kCells1Warps, 0, s>>>(a, r, d.nc);
 }
 
 
