@@ -795,7 +795,6 @@ __global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc)
 // pheno_torque_diss).  Lane partial sums, then a fixed shuffle tree: every
 // lane ends with the 9 sums.
 // ---------------------------------------------------------------------------
-constexpr int kCellWarps = 4;
 constexpr int kIlp = 4;  // list entries per lane in flight
 
 // Sums over the entries part, part + parts, ... (in units of 32) of cell
@@ -1064,14 +1063,14 @@ __device__ __forceinline__ bool rigid_update(const RigidArgs &a, int i, float Sf
 
 
 // ---------------------------------------------------------------------------
-// k_cells: the per-cell part of the coupled step, two warps per cell.
+// k_cells: the per-cell part of the coupled step, one warp per cell.
 //   1. sample the fields over the cell's shape list (sample_sums);
 //   2. the rigid-body update and the hydrodynamic impulses J, L (App. A);
 //   3. spread (h = 1) over the same list: G += -J delta + 1/2 L x D delta
 //      (delta = w / S) and theta += 1 - (1 - w)^kappa where w > 0 (Sec.
 //      2.2, Eq. enhance-viscosity), with atomics.
 // A cell's spread writes only G and theta, which no sampling reads, so the
-// spreading warp starts as soon as its cell's J and L exist.
+// cells of the kernel need no order among themselves.
 // ---------------------------------------------------------------------------
 // (1 - w)^kappa of Eq. enhance-viscosity: by squaring for a whole-number
 // kappa (the paper's 20: five multiplications), powf otherwise
@@ -1086,119 +1085,22 @@ __device__ __forceinline__ float pow_kappa(float x, const ShapeArgs &a)
     return r;
 }
 
-// Two warps per cell (kCellWarps / 2 cells per block), the packed solves'
-// per-cell kernel: both sample half of the cell's list; the first adds the
-// halves (fixed order), computes the impulses J, L, hands them to the second
-// through shared memory and a named barrier of the pair, and finishes the
-// rigid update (the sub-rotations and the stored state) while the second
-// spreads over the whole list.
-constexpr int kCellsPerBlock = kCellWarps / 2;
-
-// Named barriers 1 and 2 (one per pair of warps; 0 is __syncthreads).  The
-// ids are immediates: a barrier id held in a register makes the compiler
-// reserve all 16 barriers of the block, which cut the blocks per SM.
-static_assert(kCellsPerBlock == 2, "one named barrier per cell of the block");
-__device__ __forceinline__ void pair_arrive(int pair)
-{
-    if (pair == 0)
-        asm volatile("bar.arrive 1, 64;" ::: "memory");
-    else
-        asm volatile("bar.arrive 2, 64;" ::: "memory");
-}
-__device__ __forceinline__ void pair_sync(int pair)
-{
-    if (pair == 0)
-        asm volatile("bar.sync 1, 64;" ::: "memory");
-    else
-        asm volatile("bar.sync 2, 64;" ::: "memory");
-}
-
-template <bool ALPHA>
-__device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &ra, int nc, int blk)
-{
-    __shared__ float s_part[kCellsPerBlock][9];
-    __shared__ float s_jl[kCellsPerBlock][7];  // J / S, L / 2S, go
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, pair = w >> 1, half = w & 1;
-    const int i = blk * kCellsPerBlock + pair;
-    const bool valid = i < nc;
-    const int n = valid ? a.sp_cnt[i] : 0;
-    const float S = valid ? a.sp_S[i] : 0.f;
-    float sums[9];
-    if (valid)
-        sample_sums<ALPHA>(a, i, n, S, sums, half, 2);
-    else
-        for (int k = 0; k < 9; ++k) sums[k] = 0.f;
-    if (half == 1 && lane < 9) s_part[pair][lane] = pick(sums, lane);
-    __syncthreads();
-    if (!valid) return;  // uniform across the pair: neither warp takes the pair barrier
-    if (half == 0) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) sums[k] += s_part[pair][k];
-        bool published = false;
-        auto publish = [&](const float (&J)[3], const float (&L)[3]) {
-            if (lane == 0) {
-                const bool go = n > 0;
-                const float iS = go ? 1.0f / S : 0.f;
-                for (int d = 0; d < 3; ++d) {
-                    s_jl[pair][d] = J[d] * iS;
-                    s_jl[pair][3 + d] = 0.5f * L[d] * iS;
-                }
-                s_jl[pair][6] = go ? 1.f : 0.f;
-            }
-            __syncwarp();
-            pair_arrive(pair);
-            published = true;
-        };
-        rigid_update(ra, i, S, sums, publish);
-        if (!published) {
-            if (lane == 0) s_jl[pair][6] = 0.f;
-            __syncwarp();
-            pair_arrive(pair);
-        }
-        return;
-    }
-    pair_sync(pair);
-    if (s_jl[pair][6] == 0.f) return;
-    const float Jx = s_jl[pair][0], Jy = s_jl[pair][1], Jz = s_jl[pair][2];
-    const float Lx = s_jl[pair][3], Ly = s_jl[pair][4], Lz = s_jl[pair][5];
-    const int2 *idx = a.sp_idx + (size_t)i * a.sp_cap;
-    const float4 *val = a.sp_val + (size_t)i * a.sp_cap;
-    for (int e0 = lane; e0 < n; e0 += 32 * kIlp) {
-        int g[kIlp];
-        float4 v[kIlp];
-#pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            const int e = e0 + 32 * j;
-            g[j] = e < n ? idx[e].x : -1;
-            v[j] = e < n ? val[e] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            if (g[j] < 0) continue;
-            // one vector atomic per entry: (G_x, G_y, G_z, theta)
-            atomicAdd(&a.G[g[j]], make_float4(-Jx * v[j].x + (Ly * v[j].w - Lz * v[j].z),
-                                              -Jy * v[j].x + (Lz * v[j].y - Lx * v[j].w),
-                                              -Jz * v[j].x + (Lx * v[j].z - Ly * v[j].y),
-                                              v[j].x > 0.f ? 1.0f - pow_kappa(1.0f - v[j].x, a) : 0.f));
-        }
-    }
-}
-
 // At most 72 registers so that 7 blocks fit an SM: the kernel waits on
 // memory and wants the warps (at 80 registers, 6 blocks per SM ran 3,650
 // cells as two full waves and a last one of a single block; at 64, 8
 // blocks, the stress sampling spilled and the channel step took 3 % longer).
 constexpr int kCellBlocksPerSm = 7;
 
-// The per-cell kernel of a single solve: one warp per cell samples the whole
-// list, runs the rigid update and spreads; four cells per block, no barriers
-// between warps.  Twice as many cells in flight per SM as the two-warp form
-// (each taking longer): the tube step 1,239 -> 1,221 us, the channel
-// 108.2 -> 105.7 us.
-constexpr int kCells1Warps = 4;
+// One warp per cell samples the whole list, runs the rigid update and
+// spreads; four cells per block, no barriers between warps (the single-solve
+// and the packed kernels alike).  Twice as many cells in flight per SM as a
+// two-warp form (each cell taking longer) that split the sampling and handed
+// J and L from a rigid-update warp to a spreading warp: the tube step
+// 1,239 -> 1,221 us, the channel 108.2 -> 105.7 us.
+constexpr int kCellWarps = 4;
 
 template <bool ALPHA>
-__device__ __forceinline__ void cells_body1(const ShapeArgs &a, const RigidArgs &ra, int nc, int i)
+__device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &ra, int nc, int i)
 {
     if (i >= nc) return;  // uniform across the warp
     const int lane = threadIdx.x & 31;
@@ -1242,9 +1144,9 @@ __device__ __forceinline__ void cells_body1(const ShapeArgs &a, const RigidArgs 
 }
 
 template <bool ALPHA>
-__global__ void __launch_bounds__(32 * kCells1Warps, kCellBlocksPerSm) k_cells(ShapeArgs a, RigidArgs ra, int nc)
+__global__ void __launch_bounds__(32 * kCellWarps, kCellBlocksPerSm) k_cells(ShapeArgs a, RigidArgs ra, int nc)
 {
-    cells_body1<ALPHA>(a, ra, nc, blockIdx.x * kCells1Warps + (int)(threadIdx.x >> 5));
+    cells_body<ALPHA>(a, ra, nc, blockIdx.x * kCellWarps + (int)(threadIdx.x >> 5));
 }
 
 ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
@@ -1341,11 +1243,12 @@ __global__ void __launch_bounds__(32 * kWtWarps)
 }
 
 template <bool ALPHA>
-__global__ void __launch_bounds__(32 * kCellWarps)
+__global__ void __launch_bounds__(32 * kCellWarps, kCellBlocksPerSm)
     k_cells_packed(const CellPackEntry *tab, const int *start, int ninst, int buf)
 {
     const int i = cell_pack_find(start, ninst, blockIdx.x);
-    cells_body<ALPHA>(tab[i].shape[buf], tab[i].rigid, tab[i].rigid.nc, blockIdx.x - start[i]);
+    cells_body<ALPHA>(tab[i].shape[buf], tab[i].rigid, tab[i].rigid.nc,
+                       (blockIdx.x - start[i]) * kCellWarps + (int)(threadIdx.x >> 5));
 }
 
 static BinArgs bin_args(const Dev &d, const Params &p)
@@ -1516,11 +1419,11 @@ void launch_cells(const Dev &d, const Params &p, int buf, cudaStream_t s)
     if (d.nc == 0) return;
     const ShapeArgs a = shape_args(d, p, buf);
     const RigidArgs r = rigid_args(d, p);
-    const int blocks = (d.nc + kCells1Warps - 1) / kCells1Warps;
+    const int blocks = (d.nc + kCellWarps - 1) / kCellWarps;
     if (d.S != nullptr)
-        k_cells<true><<<blocks, 32 * kCells1Warps, 0, s>>>(a, r, d.nc);
+        k_cells<true><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc);
     else
-        k_cells<false><<<blocks, 32 * kCells1Warps, 0, s>>>(a, r, d.nc);
+        k_cells<false><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc);
 }
 
 
@@ -1536,7 +1439,7 @@ int cell_pack_blocks(int nc, int nbins, int kind)
     case PACK_BIN: return (nc + kBinThreads - 1) / kBinThreads;
     case PACK_GB: return (nc + kGbWarps - 1) / kGbWarps;
     case PACK_WEIGHTS: return (nc + kWtWarps - 1) / kWtWarps;
-    default: return (nc + kCellsPerBlock - 1) / kCellsPerBlock;
+    default: return (nc + kCellWarps - 1) / kCellWarps;
     }
 }
 
