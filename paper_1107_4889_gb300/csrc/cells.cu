@@ -33,7 +33,7 @@ namespace rbc {
 namespace {
 
 constexpr int kBinThreads = 32;  // FP64-bound: spread the warps over all SMs
-constexpr int kGbWarps = 8;   // cells per block of the Gay-Berne kernel
+constexpr int kGbWarps = 4;   // cells per block of the Gay-Berne kernel
 constexpr int kGbQueue = 64;  // partners per cell (cells and wall particles) that may interact
 constexpr int kMaxNbr = 128;
 
@@ -1123,17 +1123,20 @@ __device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &
     const float Jx = jl[0], Jy = jl[1], Jz = jl[2], Lx = jl[3], Ly = jl[4], Lz = jl[5];
     const int2 *idx = a.sp_idx + (size_t)i * a.sp_cap;
     const float4 *val = a.sp_val + (size_t)i * a.sp_cap;
-    for (int e0 = lane; e0 < n; e0 += 32 * kIlp) {
-        int g[kIlp];
-        float4 v[kIlp];
+    // few values are live in the spread: twice the sampling's entries in
+    // flight (tube step 1,221 -> 1,206 us, channel 105.5 -> 103.6 us)
+    constexpr int kIlpSpread = 2 * kIlp;
+    for (int e0 = lane; e0 < n; e0 += 32 * kIlpSpread) {
+        int g[kIlpSpread];
+        float4 v[kIlpSpread];
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
+        for (int j = 0; j < kIlpSpread; ++j) {
             const int e = e0 + 32 * j;
             g[j] = e < n ? idx[e].x : -1;
             v[j] = e < n ? val[e] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
+        for (int j = 0; j < kIlpSpread; ++j) {
             if (g[j] < 0) continue;
             atomicAdd(&a.G[g[j]], make_float4(-Jx * v[j].x + (Ly * v[j].w - Lz * v[j].z),
                                               -Jy * v[j].x + (Lz * v[j].y - Lx * v[j].w),
@@ -1243,7 +1246,10 @@ __global__ void __launch_bounds__(32 * kWtWarps)
 }
 
 template <bool ALPHA>
-__global__ void __launch_bounds__(32 * kCellWarps, kCellBlocksPerSm)
+// The packed kernel reads each solve's arguments from the pack table: at
+// the single-solve kernel's 72 registers it spilled 172 bytes; bounded at 5
+// blocks per SM it does not (serving 4.75 -> 4.81 solves/s)
+__global__ void __launch_bounds__(32 * kCellWarps, 5)
     k_cells_packed(const CellPackEntry *tab, const int *start, int ninst, int buf)
 {
     const int i = cell_pack_find(start, ninst, blockIdx.x);
