@@ -391,7 +391,7 @@ def run_ours(args):
                     "lattice_first": tune["lattice_first"],
                     "shape_list_blocks_per_sm": tune["wt_blocks_per_sm"],
                     "gay_berne_blocks_per_sm": tune["gb_blocks_per_sm"], "particle_bin_scale": tune["bin_scale"],
-                    "autotuned": True}},
+                    "spread_split": tune["split_spread"], "autotuned": True}},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
         "budget": {"mass_drift_rel": (st2["mass"] - st["mass"]) / st["mass"], "max_u": st2["max_u"],
                    "gb_clamps": st2["gb_clamps"]},

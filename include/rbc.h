@@ -270,7 +270,11 @@ int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2]);
  * it, or after it), over steps_per_trial coupled steps after as many
  * warm-up steps, keeps the fastest, then with it times bounded grids of the
  * shape-list and Gay-Berne kernels (2-4 blocks per SM, grid-stride over the
- * cells) against one block per group of cells, then the particle-bin edge
+ * cells) against one block per group of cells, then the step with the
+ * spread of the cells' impulses split off the per-cell kernel into a kernel
+ * of its own (the next step's cell-side kernels then start beside the
+ * spread, which only the lattice pass waits for) in both graph orders, then
+ * the particle-bin edge
  * (the candidate radius times 1, 1.25, 1.5 or 2: coarser grids scan fewer,
  * fuller bins; a grid that overflows a bin is dropped), and re-captures the
  * step graphs.  The trial steps are ordinary
@@ -282,8 +286,9 @@ typedef struct {
     int trials;                  /* shapes timed */
     int lattice_first;           /* chosen order: 1 = lattice pass before the side kernels */
     int wt_blocks_per_sm;        /* grid of the shape-list kernel, blocks per SM (0: one per 4 cells) */
-    int gb_blocks_per_sm;        /* grid of the Gay-Berne kernel, blocks per SM (0: one per 8 cells) */
+    int gb_blocks_per_sm;        /* grid of the Gay-Berne kernel, blocks per SM (0: one per 4 cells) */
     double bin_scale;            /* chosen edge of the particle bins over the candidate radius (>= 1) */
+    int split_spread;            /* 1: the spread runs as a kernel of its own beside the side kernels */
 } rbc_tune_report;
 int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out);
 

@@ -623,6 +623,7 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.ext = P.has_ext ? cv.take<double>(6 * n) : nullptr;
     d.have = cv.take<int>(n);
     d.diag = cv.take<double>(21 * n);
+    d.jl = cv.take<float>(8 * n);
     d.hdr = cv.take<float>(kHdrWords * n);
     d.sp_cap = P.nc > 0 ? P.p.box_max : 1;
     for (int b = 0; b < 2; ++b) {
@@ -709,6 +710,7 @@ struct rbc_handle {
     int profile_axis = -1;
     int timing_cap = 0, timing_used = 0;
     bool lb_first = false;  // graph order of the step: lattice pass before the side kernels
+    bool split = false;     // the spread as a kernel of its own, beside the side kernels
     std::vector<cudaEvent_t> ev;  // 3 per timed step: before the cell kernel, after it, after the lattice pass
     std::string err;
     int device = 0;
@@ -798,18 +800,19 @@ static void launch_side(rbc_handle *h, int parity)
 
 // One coupled step.  Main stream: the per-cell kernel (sample the fields
 // with this pose's shape lists, the rigid update to the new poses, spread
-// the impulses with the same lists), then the lattice pass.  As soon as the
-// new poses exist, two side streams build the next step's cell list and
-// Gay-Berne forces, and its shape headers and shape lists (into buffer
-// parity ^ 1); they read only the poses and write nothing the lattice pass
-// reads.  The step ends when all three streams have.
+// the impulses with the same lists; or, split, the spread as a kernel of its
+// own after it), then the lattice pass.  As soon as the new poses exist, two
+// side streams build the next step's cell list and Gay-Berne forces, and its
+// shape headers and shape lists (into buffer parity ^ 1); they read only the
+// poses and write nothing the spread or the lattice pass reads.  The step
+// ends when all three streams have.
 static void body_step(rbc_handle *h, int parity)
 {
     const bool cells = h->d.nc > 0;
     const bool timed = g_capture_timed;
     if (timed) cudaEventRecordWithFlags(h->ev_dummy[0], h->stream, cudaEventRecordExternal);
-    launch_cells(h->d, h->P.p, parity, h->stream);
-    if (timed) cudaEventRecordWithFlags(h->ev_dummy[1], h->stream, cudaEventRecordExternal);
+    const bool split = cells && h->split;
+    launch_cells(h->d, h->P.p, parity, h->stream, split);
     if (cells) {
         cudaEventRecord(h->fork_ev, h->stream);
         cudaStreamWaitEvent(h->side, h->fork_ev, 0);
@@ -819,8 +822,13 @@ static void body_step(rbc_handle *h, int parity)
     // blocks are dispatched before the persistent lattice pass fills the
     // SMs and the two overlap.  The autotuner also tries the lattice pass
     // first (it then runs nearly alone and the side kernels mostly after
-    // it); which is faster depends on how much cell work there is.
+    // it); which is faster depends on how much cell work there is.  With
+    // the spread split off the per-cell kernel, the side kernels (which
+    // need only the new poses) start beside it and only the lattice pass
+    // waits for it.
     if (!h->lb_first) launch_side(h, parity);
+    if (split) launch_spread(h->d, h->P.p, parity, h->stream);
+    if (timed) cudaEventRecordWithFlags(h->ev_dummy[1], h->stream, cudaEventRecordExternal);
     launch_lb(h->d, h->P.p, parity, h->stream);
     if (h->lb_first) launch_side(h, parity);
     if (timed) cudaEventRecordWithFlags(h->ev_dummy[2], h->stream, cudaEventRecordExternal);
@@ -1403,9 +1411,11 @@ int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out)
     if (h->timing_used < h->timing_cap) return fail(&h->err, RBC_EINVAL, "kernel timing is active");
     const int st0 = h->d.lb_stages, grid0 = h->d.lb_grid;
     const size_t smem0 = h->d.lb_smem;
-    if (h->d.wt_grid != 0 || h->d.gb_grid != 0) {
-        // the lattice shapes are timed with one block per group of cells
+    if (h->d.wt_grid != 0 || h->d.gb_grid != 0 || h->split) {
+        // the lattice shapes are timed with one block per group of cells and
+        // the spread in the per-cell kernel
         h->d.wt_grid = h->d.gb_grid = 0;
+        h->split = false;
         const int r = recapture_steps(h);
         if (r != RBC_OK) return r;
     }
@@ -1451,6 +1461,30 @@ int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out)
         rep.stages = st0;
         rep.ctas_per_sm = (grid0 + sms - 1) / sms;
     }
+    // then, with that shape, the spread split off the per-cell kernel, in
+    // both graph orders
+    if (h->d.nc > 0) {
+        const bool order1 = h->lb_first;
+        bool best_order = order1;
+        bool split_wins = false;
+        for (int k = 0; k < 2; ++k) {
+            h->split = true;
+            h->lb_first = k == 1;
+            rc = recapture_steps(h);
+            double ms = 0.0;
+            if (rc == RBC_OK) rc = time_steps(h, steps_per_trial, &ms);
+            if (rc != RBC_OK) return rc;
+            rep.trials++;
+            if (ms < best) {
+                best = ms;
+                best_order = h->lb_first;
+                split_wins = true;
+            }
+        }
+        h->split = split_wins;
+        h->lb_first = split_wins ? best_order : order1;
+    }
+    rep.split_spread = h->split ? 1 : 0;
     rep.lattice_first = h->lb_first ? 1 : 0;
     // then the grids of the shape-list and Gay-Berne kernels (blocks per
     // SM; 0: one block per group of cells), with that shape and order: a
@@ -1737,7 +1771,9 @@ int rbc_wss(rbc_handle *h, int64_t *node, double *tau, int64_t max, int64_t *n, 
 int rbc_launches_per_step(const rbc_handle *h)
 {
     if (!h) return 0;
-    return 1 + (h->d.nc > 0 ? 4 : 0);  // cells, bin, gb, weights; the bin-count clear is a memset node
+    // lattice pass; cells, bin, gb, weights (+ the spread when split); the
+    // bin-count clear is a memset node
+    return 1 + (h->d.nc > 0 ? (h->split ? 5 : 4) : 0);
 }
 
 int rbc_layout(const rbc_handle *h, int *compact, int64_t *entries, int64_t *fluid)

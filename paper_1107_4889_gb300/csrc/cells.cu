@@ -1099,27 +1099,9 @@ constexpr int kCellBlocksPerSm = 7;
 // 1,239 -> 1,221 us, the channel 108.2 -> 105.7 us.
 constexpr int kCellWarps = 4;
 
-template <bool ALPHA>
-__device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &ra, int nc, int i)
+// Spread (step 3) of cell i over its list, with J / S and L / 2S in jl.
+__device__ __forceinline__ void spread_list(const ShapeArgs &a, int i, int n, int lane, const float (&jl)[6])
 {
-    if (i >= nc) return;  // uniform across the warp
-    const int lane = threadIdx.x & 31;
-    const int n = a.sp_cnt[i];
-    const float S = a.sp_S[i];
-    float sums[9];
-    sample_sums<ALPHA>(a, i, n, S, sums, 0, 1);
-    float jl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    bool go = false;
-    auto publish = [&](const float (&J)[3], const float (&L)[3]) {
-        go = n > 0;
-        const float iS = go ? 1.0f / S : 0.f;
-        for (int d = 0; d < 3; ++d) {
-            jl[d] = J[d] * iS;
-            jl[3 + d] = 0.5f * L[d] * iS;
-        }
-    };
-    rigid_update(ra, i, S, sums, publish);
-    if (!go) return;
     const float Jx = jl[0], Jy = jl[1], Jz = jl[2], Lx = jl[3], Ly = jl[4], Lz = jl[5];
     const int2 *idx = a.sp_idx + (size_t)i * a.sp_cap;
     const float4 *val = a.sp_val + (size_t)i * a.sp_cap;
@@ -1146,10 +1128,52 @@ __device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &
     }
 }
 
-template <bool ALPHA>
-__global__ void __launch_bounds__(32 * kCellWarps, kCellBlocksPerSm) k_cells(ShapeArgs a, RigidArgs ra, int nc)
+// Steps 1 and 2 of cell i, then step 3 here (SPREAD) or, for k_spread,
+// J / S, L / 2S and the go flag to jl_out[8 i ..].
+template <bool ALPHA, bool SPREAD = true>
+__device__ __forceinline__ void cells_body(const ShapeArgs &a, const RigidArgs &ra, int nc, int i,
+                                           float *jl_out = nullptr)
 {
-    cells_body<ALPHA>(a, ra, nc, blockIdx.x * kCellWarps + (int)(threadIdx.x >> 5));
+    if (i >= nc) return;  // uniform across the warp
+    const int lane = threadIdx.x & 31;
+    const int n = a.sp_cnt[i];
+    const float S = a.sp_S[i];
+    float sums[9];
+    sample_sums<ALPHA>(a, i, n, S, sums, 0, 1);
+    float jl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool go = false;
+    auto publish = [&](const float (&J)[3], const float (&L)[3]) {
+        go = n > 0;
+        const float iS = go ? 1.0f / S : 0.f;
+        for (int d = 0; d < 3; ++d) {
+            jl[d] = J[d] * iS;
+            jl[3 + d] = 0.5f * L[d] * iS;
+        }
+    };
+    rigid_update(ra, i, S, sums, publish);
+    if (!SPREAD) {
+        if (lane < 6) jl_out[8 * i + lane] = pick(jl, lane);
+        if (lane == 6) jl_out[8 * i + 6] = go ? 1.f : 0.f;
+        return;
+    }
+    if (go) spread_list(a, i, n, lane, jl);
+}
+
+template <bool ALPHA, bool SPREAD>
+__global__ void __launch_bounds__(32 * kCellWarps, kCellBlocksPerSm) k_cells(ShapeArgs a, RigidArgs ra, int nc,
+                                                                             float *jl)
+{
+    cells_body<ALPHA, SPREAD>(a, ra, nc, blockIdx.x * kCellWarps + (int)(threadIdx.x >> 5), jl);
+}
+
+// The spread as a kernel of its own: only the lattice pass waits for it,
+// the next step's cell list, Gay-Berne forces and shape lists run beside it.
+__global__ void __launch_bounds__(32 * kCellWarps) k_spread(ShapeArgs a, const float *__restrict__ jl, int nc)
+{
+    const int i = blockIdx.x * kCellWarps + (int)(threadIdx.x >> 5);
+    if (i >= nc || jl[8 * i + 6] == 0.f) return;
+    const float v[6] = {jl[8 * i], jl[8 * i + 1], jl[8 * i + 2], jl[8 * i + 3], jl[8 * i + 4], jl[8 * i + 5]};
+    spread_list(a, i, a.sp_cnt[i], (int)(threadIdx.x & 31), v);
 }
 
 ShapeArgs shape_args(const Dev &d, const Params &p, int buf)
@@ -1420,16 +1444,29 @@ static RigidArgs rigid_args(const Dev &d, const Params &p)
     return a;
 }
 
-void launch_cells(const Dev &d, const Params &p, int buf, cudaStream_t s)
+void launch_cells(const Dev &d, const Params &p, int buf, cudaStream_t s, bool split)
 {
     if (d.nc == 0) return;
     const ShapeArgs a = shape_args(d, p, buf);
     const RigidArgs r = rigid_args(d, p);
     const int blocks = (d.nc + kCellWarps - 1) / kCellWarps;
-    if (d.S != nullptr)
-        k_cells<true><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc);
-    else
-        k_cells<false><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc);
+    if (d.S != nullptr) {
+        if (split)
+            k_cells<true, false><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc, d.jl);
+        else
+            k_cells<true, true><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc, d.jl);
+    } else {
+        if (split)
+            k_cells<false, false><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc, d.jl);
+        else
+            k_cells<false, true><<<blocks, 32 * kCellWarps, 0, s>>>(a, r, d.nc, d.jl);
+    }
+}
+
+void launch_spread(const Dev &d, const Params &p, int buf, cudaStream_t s)
+{
+    if (d.nc == 0) return;
+    k_spread<<<(d.nc + kCellWarps - 1) / kCellWarps, 32 * kCellWarps, 0, s>>>(shape_args(d, p, buf), d.jl, d.nc);
 }
 
 

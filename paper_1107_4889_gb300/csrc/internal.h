@@ -78,6 +78,7 @@ struct Dev {
     double *ext;             // 6n external force (3) and torque (3) per cell (lab), or null
     int *have;               // n: cached combined force exists (not the first step)
     double *diag;            // 21n per-cell diagnostics of the last step
+    float *jl;               // 8n: J / S, L / 2S and a go flag of the step, from k_cells to k_spread
     float *hdr;              // kHdrWords per cell: shape header built by k_bin
     // shape lists written by k_weights, two buffers (step parity): per cell
     // up to sp_cap entries (lattice node, packed box coordinates) and
@@ -190,7 +191,10 @@ void launch_bin(const Dev &d, const Params &p, cudaStream_t s);
 void launch_profile(const Dev &d, int axis, cudaStream_t s);
 void launch_gb(const Dev &d, const Params &p, cudaStream_t s);
 void launch_weights(const Dev &d, const Params &p, int buf, cudaStream_t s);
-void launch_cells(const Dev &d, const Params &p, int buf, cudaStream_t s);
+// split: the per-cell kernel stops after the rigid update (J, L to d.jl)
+// and launch_spread spreads them
+void launch_cells(const Dev &d, const Params &p, int buf, cudaStream_t s, bool split = false);
+void launch_spread(const Dev &d, const Params &p, int buf, cudaStream_t s);
 size_t cells_smem_bytes(const Params &p);
 void prepare_cells(const Params &p);
 

@@ -88,7 +88,7 @@ class rbc_tune_report(ctypes.Structure):
     _fields_ = [("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("ms_per_step", ctypes.c_double),
                 ("default_ms_per_step", ctypes.c_double), ("trials", ctypes.c_int),
                 ("lattice_first", ctypes.c_int), ("wt_blocks_per_sm", ctypes.c_int),
-                ("gb_blocks_per_sm", ctypes.c_int), ("bin_scale", ctypes.c_double)]
+                ("gb_blocks_per_sm", ctypes.c_int), ("bin_scale", ctypes.c_double), ("split_spread", ctypes.c_int)]
 
 
 #: symbols include/rbc.h declares
@@ -342,7 +342,7 @@ def rbc_autotune(h, steps_per_trial: int = 20):
     return dict(stages=r.stages, ctas_per_sm=r.ctas_per_sm, ms_per_step=r.ms_per_step,
                 default_ms_per_step=r.default_ms_per_step, trials=r.trials,
                 lattice_first=bool(r.lattice_first), wt_blocks_per_sm=r.wt_blocks_per_sm,
-                gb_blocks_per_sm=r.gb_blocks_per_sm, bin_scale=r.bin_scale)
+                gb_blocks_per_sm=r.gb_blocks_per_sm, bin_scale=r.bin_scale, split_spread=bool(r.split_spread))
 
 
 def rbc_wss_accumulate(h):
