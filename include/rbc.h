@@ -268,13 +268,13 @@ int rbc_kernel_times(rbc_handle *h, double ms[2], int64_t count[2]);
  * SM), each in both graph orders of the step (the cell-list, Gay-Berne and
  * shape-list kernels launched before the lattice pass, so that they overlap
  * it, or after it), over steps_per_trial coupled steps after as many
- * warm-up steps, keeps the fastest, then with it times bounded grids of the
- * shape-list and Gay-Berne kernels (2-4 blocks per SM, grid-stride over the
- * cells) against one block per group of cells, then the step with the
- * spread of the cells' impulses split off the per-cell kernel into a kernel
- * of its own (the next step's cell-side kernels then start beside the
- * spread, which only the lattice pass waits for) in both graph orders, then
- * the particle-bin edge
+ * warm-up steps, keeps the fastest, then with it times jointly the schedule
+ * of the cell-side kernels: the spread of the cells' impulses in the
+ * per-cell kernel or split off it into a kernel of its own (the next step's
+ * cell-side kernels then start beside the spread, which only the lattice
+ * pass waits for), both graph orders, and bounded grids of the shape-list
+ * and Gay-Berne kernels (2-4 blocks per SM, grid-stride over the cells)
+ * against one block per group of cells; then the particle-bin edge
  * (the candidate radius times 1, 1.25, 1.5 or 2: coarser grids scan fewer,
  * fuller bins; a grid that overflows a bin is dropped), and re-captures the
  * step graphs.  The trial steps are ordinary

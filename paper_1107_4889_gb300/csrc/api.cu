@@ -1461,57 +1461,48 @@ int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out)
         rep.stages = st0;
         rep.ctas_per_sm = (grid0 + sms - 1) / sms;
     }
-    // then, with that shape, the spread split off the per-cell kernel, in
-    // both graph orders
-    if (h->d.nc > 0) {
-        const bool order1 = h->lb_first;
-        bool best_order = order1;
-        bool split_wins = false;
-        for (int k = 0; k < 2; ++k) {
-            h->split = true;
-            h->lb_first = k == 1;
-            rc = recapture_steps(h);
-            double ms = 0.0;
-            if (rc == RBC_OK) rc = time_steps(h, steps_per_trial, &ms);
-            if (rc != RBC_OK) return rc;
-            rep.trials++;
-            if (ms < best) {
-                best = ms;
-                best_order = h->lb_first;
-                split_wins = true;
-            }
-        }
-        h->split = split_wins;
-        h->lb_first = split_wins ? best_order : order1;
-    }
-    rep.split_spread = h->split ? 1 : 0;
     rep.lattice_first = h->lb_first ? 1 : 0;
-    // then the grids of the shape-list and Gay-Berne kernels (blocks per
-    // SM; 0: one block per group of cells), with that shape and order: a
-    // bounded grid leaves the kernels room on every SM beside each other
-    // and beside the lattice pass
+    // then, with that shape, the schedule of the cell-side kernels, jointly:
+    // the spread in the per-cell kernel or split off it (the side kernels
+    // then start beside it), both graph orders, and the grids of the
+    // shape-list and Gay-Berne kernels (blocks per SM; 0: one block per
+    // group of cells; a bounded grid leaves room on every SM beside each
+    // other and beside the spread and the lattice pass)
     if (h->d.nc > 0) {
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int side[][2] = {{2, 2}, {3, 2}, {2, 3}, {3, 3}, {4, 2}};
+        const int side[][2] = {{0, 0}, {2, 2}, {3, 2}, {2, 3}, {3, 3}, {4, 2}};
+        const bool order1 = h->lb_first;
+        bool bsplit = false, border = order1;
         int bw = 0, bg = 0;
-        for (const auto &c : side) {
-            h->d.wt_grid = c[0] * sms;
-            h->d.gb_grid = c[1] * sms;
-            rc = recapture_steps(h);
-            double ms = 0.0;
-            if (rc == RBC_OK) rc = time_steps(h, steps_per_trial, &ms);
-            if (rc != RBC_OK) return rc;
-            rep.trials++;
-            if (ms < best) {
-                best = ms;
-                bw = c[0];
-                bg = c[1];
-            }
-        }
+        for (int sp = 0; sp < 2; ++sp)
+            for (int ord = 0; ord < 2; ++ord)
+                for (const auto &c : side) {
+                    if (!sp && (ord == 1) == order1 && c[0] == 0 && c[1] == 0) continue;  // timed above
+                    h->split = sp == 1;
+                    h->lb_first = ord == 1;
+                    h->d.wt_grid = c[0] * sms;
+                    h->d.gb_grid = c[1] * sms;
+                    rc = recapture_steps(h);
+                    double ms = 0.0;
+                    if (rc == RBC_OK) rc = time_steps(h, steps_per_trial, &ms);
+                    if (rc != RBC_OK) return rc;
+                    rep.trials++;
+                    if (ms < best) {
+                        best = ms;
+                        bsplit = h->split;
+                        border = h->lb_first;
+                        bw = c[0];
+                        bg = c[1];
+                    }
+                }
+        h->split = bsplit;
+        h->lb_first = border;
         h->d.wt_grid = bw * sms;
         h->d.gb_grid = bg * sms;
+        rep.split_spread = bsplit ? 1 : 0;
+        rep.lattice_first = border ? 1 : 0;
         rep.wt_blocks_per_sm = bw;
         rep.gb_blocks_per_sm = bg;
         // then the particle bins: edges of r_cut x {1, 1.25, 1.5, 2}
