@@ -520,14 +520,15 @@ struct ShapeArgs {
 // and D w (all four zero at the few visited nodes where they vanish); S is
 // the sum of w over fluid nodes.
 // Shared memory per warp (weights_words): row words (support lo | hi << 8 |
-// first item << 16), visit words (same layout), the compact weights and the
+// first item << 16), visit words (same layout), the rows that have visit
+// items (row | first item << 16, in row order), the compact weights and the
 // row of every support item (16 bits).
 // ---------------------------------------------------------------------------
 constexpr int kWtWarps = 4;
 
 int weights_words(const Params &p)
 {
-    return 2 * p.box_dim * p.box_dim + p.sup_cap + (p.sup_cap + 1) / 2;
+    return 3 * p.box_dim * p.box_dim + p.sup_cap + (p.sup_cap + 1) / 2;
 }
 
 // support interval [lo, hi] of box row (i1, i2) along x; lo > hi if empty.
@@ -571,7 +572,8 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
     const int rows_cap = a.box_dim * a.box_dim;
     unsigned *srow = reinterpret_cast<unsigned *>(smem + (size_t)warp * a.box_pad);
     unsigned *vrow = srow + rows_cap;
-    float *wc = reinterpret_cast<float *>(vrow + rows_cap);
+    unsigned *vne = vrow + rows_cap;
+    float *wc = reinterpret_cast<float *>(vne + rows_cap);
     uint16_t *srowof = reinterpret_cast<uint16_t *>(wc + a.sup_cap);
     const float qm = lane < 4 ? (float)a.q[4 * i + lane] : 0.f;
     float qf[4], Q[9];
@@ -656,8 +658,10 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
         return;
     }
     __syncwarp();
-    // 2. visit interval and first item of every row
-    int vtot = 0;
+    // 2. visit interval and first item of every row, and the list of the
+    //    rows that have visit items (many box rows miss the cell)
+    int vtot = 0, nne = 0;
+    const unsigned lt = (1u << lane) - 1u;
     for (int rb = 0; rb < nrows; rb += 32) {
         const int r = rb + lane;
         int vlo = 1 << 20, vhi = -1;
@@ -688,6 +692,9 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
             if (lane >= off) incl += v;
         }
         if (r < nrows) vrow[r] = (len > 0 ? (unsigned)(vlo | (vhi << 8)) : 0xFFu) | ((unsigned)(vtot + incl - len) << 16);
+        const unsigned ne = __ballot_sync(0xffffffffu, len > 0);
+        if (len > 0) vne[nne + __popc(ne & lt)] = (unsigned)r | ((unsigned)(vtot + incl - len) << 16);
+        nne += __popc(ne);
         vtot += __shfl_sync(0xffffffffu, incl, 31);
     }
     // 3. weights over the support items
@@ -716,20 +723,23 @@ __device__ __forceinline__ void weights_body(const ShapeArgs &a, int nc, int blk
         return (x >= slo && x <= shi) ? wc[(int)(word >> 16) + x - slo] : 0.f;
     };
     // 4. the visit items, one lane per item, so that consecutive lanes write
-    //    consecutive list entries: the item's row is reached by walking
-    //    forward from the row of the previous round's last item (rows are in
-    //    item order; a row without items has the next row's first item)
+    //    consecutive list entries: the item's row is reached by walking the
+    //    list of rows with items forward from the row of the previous
+    //    round's last item.  This phase is 57 % of the kernel's instructions
+    //    (per item five support words, seven weight lookups and the storage
+    //    entry)
     int2 *sp_idx = a.sp_idx + (size_t)i * a.sp_cap;
     float4 *sp_val = a.sp_val + (size_t)i * a.sp_cap;
     const int vcount = min(vtot, a.sp_cap);
-    int rstart = 0;
+    int kstart = 0;
     for (int t0 = 0; t0 < vcount; t0 += 32) {
         const int t = t0 + lane;
-        int r = rstart;
+        int k = kstart;
         if (t < vcount)
-            while (r + 1 < nrows && (int)(vrow[r + 1] >> 16) <= t) ++r;
-        rstart = __shfl_sync(0xffffffffu, r, 31);
+            while (k + 1 < nne && (int)(vne[k + 1] >> 16) <= t) ++k;
+        kstart = __shfl_sync(0xffffffffu, k, 31);
         if (t >= vcount) continue;
+        const int r = (int)(vne[k] & 0xFFFFu);
         const unsigned vw = vrow[r];
         const int x = (int)(vw & 0xFFu) + (t - (int)(vw >> 16));
         const int i2 = (int)(((float)r + 0.5f) * inv1), i1 = r - i2 * n1;
