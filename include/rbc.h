@@ -292,6 +292,16 @@ typedef struct {
 } rbc_tune_report;
 int rbc_autotune(rbc_handle *h, int steps_per_trial, rbc_tune_report *out);
 
+/* Step schedule set by hand (what rbc_autotune chooses besides the launch
+ * shapes): split_spread != 0 runs the spread of the cells' impulses as a
+ * kernel of its own, which the next step's cell-list, Gay-Berne and
+ * shape-list kernels run beside (no effect without cells); lattice_first
+ * != 0 captures the lattice pass before those kernels in the step graph.
+ * Either schedule computes the same step (up to the order of the spread's
+ * float atomics).  Re-captures the step graphs.  RBC_EINVAL while kernel
+ * timing is active. */
+int rbc_set_schedule(rbc_handle *h, int split_spread, int lattice_first);
+
 /* Wall shear stress (the quantity Sec. 4 maps in the coronary geometry).
  * At every fluid node with a solid link neighbour the wall normal n is the
  * unit sum of its links that stay in the fluid (minus those into the

@@ -1759,6 +1759,15 @@ int rbc_wss(rbc_handle *h, int64_t *node, double *tau, int64_t max, int64_t *n, 
     return RBC_OK;
 }
 
+int rbc_set_schedule(rbc_handle *h, int split_spread, int lattice_first)
+{
+    if (!h) return fail(nullptr, RBC_EINVAL, "handle is NULL");
+    if (h->timing_used < h->timing_cap) return fail(&h->err, RBC_EINVAL, "kernel timing is active");
+    h->split = split_spread != 0 && h->d.nc > 0;
+    h->lb_first = lattice_first != 0;
+    return recapture_steps(h);
+}
+
 int rbc_launches_per_step(const rbc_handle *h)
 {
     if (!h) return 0;

@@ -94,7 +94,7 @@ class rbc_tune_report(ctypes.Structure):
 #: symbols include/rbc.h declares
 EXPORTS = ["rbc_default_params", "rbc_workspace_size", "rbc_init", "rbc_step", "rbc_fields",
            "rbc_stats", "rbc_cell_diag", "rbc_neighbors", "rbc_set_timing", "rbc_kernel_times",
-           "rbc_autotune", "rbc_wss_accumulate", "rbc_wss", "rbc_launches_per_step", "rbc_layout", "rbc_fluid_nodes",
+           "rbc_autotune", "rbc_set_schedule", "rbc_wss_accumulate", "rbc_wss", "rbc_launches_per_step", "rbc_layout", "rbc_fluid_nodes",
            "rbc_profile_accumulate", "rbc_profile", "rbc_set_wait_limit",
            "rbc_checkpoint_size", "rbc_save", "rbc_load",
            "rbc_neighbors_noalloc", "rbc_server_create", "rbc_server_submit",
@@ -149,6 +149,8 @@ def load(path: str = LIB_PATH):
     L.rbc_fluid_nodes.argtypes = [ctypes.c_void_p, _I64, ctypes.c_int64, _I64]
     L.rbc_fluid_nodes.restype = ctypes.c_int
     L.rbc_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, P(rbc_tune_report)]
+    L.rbc_set_schedule.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    L.rbc_set_schedule.restype = ctypes.c_int
     L.rbc_autotune.restype = ctypes.c_int
     L.rbc_wss_accumulate.argtypes = [ctypes.c_void_p]
     L.rbc_wss_accumulate.restype = ctypes.c_int
@@ -345,6 +347,10 @@ def rbc_autotune(h, steps_per_trial: int = 20):
                 gb_blocks_per_sm=r.gb_blocks_per_sm, bin_scale=r.bin_scale, split_spread=bool(r.split_spread))
 
 
+def rbc_set_schedule(h, split_spread: bool, lattice_first: bool):
+    _check(load().rbc_set_schedule(h, int(bool(split_spread)), int(bool(lattice_first))), h)
+
+
 def rbc_wss_accumulate(h):
     _check(load().rbc_wss_accumulate(h), h)
 
@@ -474,6 +480,9 @@ class Solver:
 
     def autotune(self, steps_per_trial=20):
         return rbc_autotune(self.handle, steps_per_trial)
+
+    def set_schedule(self, split_spread=False, lattice_first=False):
+        rbc_set_schedule(self.handle, split_spread, lattice_first)
 
     def layout(self):
         return rbc_layout(self.handle)

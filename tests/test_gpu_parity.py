@@ -58,12 +58,15 @@ def _rotational_floors(do, params, steps):
             "angle": steps * grad}
 
 
-def _compare(geom, cells, params, steps, tol=TOL, check_cells=True, floors=True):
+def _compare(geom, cells, params, steps, tol=TOL, check_cells=True, floors=True, schedule=None):
     """Run both for `steps` and compare.  floors=False judges the rotational
     quantities on their own largest value alone (for flows whose gradients
-    lift them far above the FP32 noise)."""
+    lift them far above the FP32 noise).  schedule: (split_spread,
+    lattice_first) set on the solver before its steps."""
     o = orc.Oracle(geom, cells, params)
     s = _solver(geom, cells, params)
+    if schedule is not None:
+        s.set_schedule(*schedule)
     o.step(steps)
     s.step(steps)
     rho_o, u_o, _ = o.fields()
@@ -300,6 +303,19 @@ def test_autotuned_launch_shape_keeps_parity():
     assert rel_l2(f["u"], u_o) <= TOL
     s.close()
     o.close()
+
+
+@pytest.mark.parametrize("lattice_first", [False, True])
+def test_split_spread_schedule_matches_oracle(lattice_first):
+    """The spread as a kernel of its own, the next step's cell-side kernels
+    beside it, in either graph order: the coupled walled channel stays at
+    the oracle's results (the schedule moves no arithmetic, only the order
+    of the spread's atomics)."""
+    geom, cells, params = wl.channel_workload(nx=24, ny=28, nz=32, ncells=12, body_force=(5e-6, 0, 0), seed=33)
+    rng = np.random.default_rng(5)
+    cells["vel"] = rng.normal(size=(12, 3)) * 3e-3
+    r = _compare(geom, cells, params, 80, schedule=(True, lattice_first))
+    print("split spread:", r)
 
 
 def test_non_integer_kappa():
