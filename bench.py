@@ -28,6 +28,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import subprocess
@@ -564,6 +565,84 @@ def run_stats(args):
     print(json.dumps(line), flush=True)
 
 
+def run_tank_treading(args):
+    """The tank-treading test of Sec. 3 (E2), in a Kolmogorov flow: one cell
+    at a plane where the plasma velocity u_x = U sin(2 pi y / n) vanishes
+    and its shear rate is largest (the paper shears with Lees-Edwards
+    boundaries, which it only cites; near that plane the flow is simple shear
+    to within the curvature of the profile over the cell, cos(2 pi a / n) =
+    0.92 for a = 4 in n = 64).  The cell starts with its short (symmetry)
+    axis in the shear plane, 10 degrees off the gradient direction.  For each
+    coefficient alpha of the elongational torque (Eq. pheno_torque_diss) the
+    short axis' angle phi in the shear plane is sampled; the cell tumbles if
+    phi advances by more than a quarter turn over the second half of the
+    run, else it holds a fixed inclination, reported as the angle of its
+    long axis in the shear plane to the flow direction (mean over the last
+    quarter).  The paper finds the transition at alpha = 0.063 with an
+    inclination of about 40 degrees (20-35 degrees in a bounded slab)."""
+    import torch
+
+    from paper_1107_4889_gb300 import build as B
+    from paper_1107_4889_gb300.rbc import RbcError, Solver
+
+    B.build()
+    torch.cuda.set_device(0)
+    n, rate, steps, every = 64, 1e-3, args.steps, 200
+    # the paper's range, then up to where the elongational torque can match
+    # the vorticity-driven one (gamma_R I omega~ under the App. A integrator)
+    alphas = [0.0, 0.04, 0.063, 0.1, 1.0, 10.0, 30.0, 100.0, 300.0, 1000.0]
+    nu = (wl.PAPER_PARAMS["tau0"] - 0.5) / 3.0
+    geom = wl.periodic_box(n, body_force_wave=(wl.kolmogorov_amplitude(n, rate, nu), 0.0, 0.0))
+    # short axis in the shear plane at 80 degrees from the flow: body z to lab
+    # x (a quarter turn about y), then 80 degrees about z
+    a, b = math.radians(80.0) / 2, math.pi / 4
+    q0 = np.array([[math.cos(a) * math.cos(b), -math.sin(a) * math.sin(b), math.cos(a) * math.sin(b),
+                    math.sin(a) * math.cos(b)]])
+    rows = []
+    for alpha in alphas:
+        cells = wl.cells_dict(np.array([[n / 2 + 0.2, n / 2, n / 2 + 0.3]]), q0)
+        p = wl.params(alpha_tt=alpha)
+        s = Solver(geom, cells, p)
+        phis, ratios, done = [], [], 0
+        try:
+            while done < steps:
+                s.step(every)
+                done += every
+                w, x, y, z = s.fields(rho=False, u=False)["quat"][0]
+                e = np.array([2 * (x * z + w * y), 2 * (y * z - w * x), 1 - 2 * (x * x + y * y)])  # lab short axis
+                phis.append(math.atan2(e[1], e[0]))
+                if done > steps // 2:
+                    dg = s.cell_diag()
+                    # elongational torque against the vorticity-driven one,
+                    # gamma_R I omega~ (z: the vorticity axis)
+                    ratios.append(abs(dg["T_S"][0, 2]) /
+                                  max(p["gamma_R"] * p["inertia"][2] * abs(dg["omega_s"][0, 2]), 1e-30))
+        except RbcError as err:
+            # a strong elongational torque, spread back as force density,
+            # drives the lattice past the Mach guard
+            rows.append({"alpha": alpha, "unstable_at_step": done, "error": str(err)[:60]})
+            s.close()
+            continue
+        s.close()
+        phi = np.unwrap(np.array(phis))
+        half = len(phi) // 2
+        turn = float(phi[-1] - phi[half])
+        tumbling = abs(turn) > math.pi / 2
+        # long axis in the shear plane: perpendicular to the short axis
+        incl = np.degrees(np.angle(np.exp(2j * (phi[3 * len(phi) // 4:] - math.pi / 2))) / 2.0)
+        rows.append({"alpha": alpha, "tumbling": bool(tumbling),
+                     "turns_second_half": turn / (2 * math.pi),
+                     "inclination_deg": None if tumbling else float(np.mean(np.abs(incl))),
+                     "torque_ratio_TS_over_vorticity": float(np.mean(ratios))})
+    steady = [r["alpha"] for r in rows if r.get("tumbling") is False]
+    line = {"metric": "tank-treading test (Sec. 3): tumbling or fixed inclination vs alpha",
+            "workload": f"one cell, {n}^3 periodic box, Kolmogorov flow with peak shear rate {rate}, cell at its "
+                        f"zero-velocity plane, {steps} steps per alpha",
+            "paper": {"transition_alpha": 0.063, "inclination_deg": 40, "bounded_slab_deg": [20, 35]},
+            "transition_alpha": min(steady) if steady else None, "runs": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_mobility(args):
     """The mobility test of Sec. 3: one cell (M = 10, I = 1000, no viscosity
     contrast) in a 60^3 periodic box of quiescent fluid, pushed by a constant
@@ -695,6 +774,8 @@ def parse_args(argv=None):
                     help="wall-shear-stress map of the workload, binary16 against FP32")
     ap.add_argument("--mobility", action="store_true", help="mobility of one cell against the friction rates")
     ap.add_argument("--mobility-xi-half", action="store_true", help="mobility test with xi = semi-axes / 2")
+    ap.add_argument("--tank-treading", action="store_true",
+                    help="tank-treading test: tumbling or fixed inclination of one cell in shear vs alpha")
     ap.add_argument("--stats", action="store_true",
                     help="relative viscosity and near-wall hematocrit of the channel, binary16 against FP32")
     ap.add_argument("--planes", type=int, default=20, help="planes of the tube_slab workload")
@@ -732,6 +813,9 @@ def main():
         return
     if args.stats:
         run_stats(args)
+        return
+    if args.tank_treading:
+        run_tank_treading(args)
         return
     if args.mobility:
         run_mobility(args)
