@@ -2,25 +2,27 @@
 //
 //   k_bin     one thread per cell: cell-list bin and slot (FP64 position / bin
 //             size) and the shape tensor A = Q S^2 Q^T.
-//   k_gb      one warp per cell: the 27 surrounding bins are scanned by the
-//             lanes with the exact FP64 distance test (no fused multiply-add),
-//             passing partners are compacted with a ballot and ranked into a
-//             list sorted by partner index; the lanes then evaluate the
-//             Gay-Berne pairs and the wall particles (Sec. 2.5, App. B).  A
+//   k_gb      one warp per cell, four cells per block: the 27 surrounding
+//             bins are scanned by the lanes with the exact FP64 distance
+//             test (no fused multiply-add), passing partners are compacted
+//             with a ballot and ranked into a list sorted by partner index;
+//             the block's threads then evaluate the queued Gay-Berne pairs
+//             and wall particles one each (Sec. 2.5, App. B; the geometry and
+//             u'(rho) in FP64, the force and torque vectors in FP32).  A
 //             conservative FP32 reduced-distance test skips pairs that are
-//             certainly outside the range, so FP64 runs only for pairs that
-//             interact.  Each pair is evaluated from both sides: every cell
-//             sums its own force in a fixed order, without atomics.
+//             certainly outside the range.  Each pair is evaluated from both
+//             sides: every cell sums its own force in FP64 in a fixed order,
+//             without atomics.
 //   k_weights one warp per cell: the cell's shape header and the shape-function
 //             weights on its box staged in shared memory, written out as
 //             the cell's shape list (node, w, D w) with the normalisation S;
 //             built for the next pose while the lattice pass runs.
-//   k_cells   two warps per cell: the fields sampled over the shape list
+//   k_cells   one warp per cell: the fields sampled over the shape list
 //             (Eqs. vel, vort, pheno_torque_diss), the rigid-body update
 //             (App. A) with the hydrodynamic impulses, and the reaction
 //             force density and smoothed characteristic function added
 //             over the same list with atomics (Sec. 2.2, Eq.
-//             enhance-viscosity).
+//             enhance-viscosity); or, split, the last part as k_spread.
 #include <algorithm>
 #include <cstring>
 #include <utility>
