@@ -57,6 +57,7 @@ struct Problem {
     std::vector<int2> bx, pool;  // per batch (pool offset, bytes); per batch row nine copy descriptors
     int stage_bytes = 0;
     bool has_ext = false;  // cells carry an external force or torque
+    std::vector<uint8_t> near;  // near_solid of the mask (host set-up only; released after rbc_init)
 };
 
 struct Carver {
@@ -96,21 +97,30 @@ inline long long node(const Problem &P, int x, int y, int z)
 std::vector<uint8_t> near_solid(const Problem &P, const uint8_t *solid)
 {
     const int nx = P.nx, ny = P.ny, nz = P.nz;
-    const long long sx = 1, sy = nx, sz = (long long)nx * ny, N = sz * nz;
+    const long long sy = nx, sz = (long long)nx * ny, N = sz * nz;
     std::vector<uint8_t> a(solid, solid + N), b((size_t)N);
-    // one pass: b = a | a shifted by +-1 along the axis of length n, stride st
+    // along x: each row on its own (the ends wrap)
+    for (long long r = 0; r < N; r += nx) {
+        const uint8_t *in = &a[(size_t)r];
+        uint8_t *out = &b[(size_t)r];
+        out[0] = in[0] | in[1 % nx] | in[nx - 1];
+        for (int x = 1; x < nx - 1; ++x) out[x] = in[x - 1] | in[x] | in[x + 1];
+        if (nx > 1) out[nx - 1] = in[nx - 2] | in[nx - 1] | in[0];
+    }
+    a.swap(b);
+    // along y and z: whole contiguous lines (of nx, or nx ny, bytes) at a
+    // time, the line before and the line after (periodic)
     auto pass = [&](int n, long long st) {
-        for (long long base = 0; base < N; base += st * n)  // blocks of n planes
-            for (long long off = 0; off < st; ++off)
-                for (int c = 0; c < n; ++c) {
-                    const long long i = base + off + c * st;
-                    const long long lo = base + off + (c > 0 ? c - 1 : n - 1) * st;
-                    const long long hi = base + off + (c < n - 1 ? c + 1 : 0) * st;
-                    b[i] = a[i] | a[lo] | a[hi];
-                }
+        for (long long base = 0; base < N; base += st * n)  // blocks of n lines
+            for (int c = 0; c < n; ++c) {
+                const uint8_t *cur = &a[(size_t)(base + c * st)];
+                const uint8_t *lo = &a[(size_t)(base + (c > 0 ? c - 1 : n - 1) * st)];
+                const uint8_t *hi = &a[(size_t)(base + (c < n - 1 ? c + 1 : 0) * st)];
+                uint8_t *out = &b[(size_t)(base + c * st)];
+                for (long long k = 0; k < st; ++k) out[k] = cur[k] | lo[k] | hi[k];
+            }
         a.swap(b);
     };
-    pass(nx, sx);
     pass(ny, sy);
     pass(nz, sz);
     return a;
@@ -486,6 +496,12 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     P.bin_cap = q.bin_capacity > 0 ? q.bin_capacity : 32;
     P.max_nbr = q.max_neighbors > 0 ? std::min(q.max_neighbors, 128) : 64;
 
+    // nodes within one node of a solid node: computed once, for the wall
+    // particles, the wall-shear nodes and (rbc_init) the link words
+    P.want_sigma = (nc > 0 && q.alpha_tt != 0.0) || P.has_bc;
+    P.near.clear();
+    if (P.any_solid) P.near = near_solid(P, g->solid);
+    const std::vector<uint8_t> &near = P.near;
     // wall particles: solid nodes with a fluid node among their 18 links
     P.nw = 0;
     P.wall_start.assign(P.nwbins + 1, 0);
@@ -493,7 +509,6 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
     if (P.any_solid && nc > 0) {
         // solid nodes with a fluid link neighbour: marked from the fluid side
         std::vector<uint8_t> wet((size_t)N, 0);
-        const std::vector<uint8_t> near = near_solid(P, g->solid);
         for (int z = 0; z < P.nz; ++z)
             for (int y = 0; y < P.ny; ++y)
                 for (int x = 0; x < P.nx; ++x) {
@@ -528,10 +543,8 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
             for (int a = 0; a < 3; ++a) P.wall_xyz[3 * at + a] = xyz[3 * w + a];
         }
     }
-    P.want_sigma = (nc > 0 && q.alpha_tt != 0.0) || P.has_bc;
     P.nwss = 0;
     if (P.any_solid && P.want_sigma) {
-        const std::vector<uint8_t> near = near_solid(P, g->solid);
         for (int z = 0; z < P.nz; ++z)
             for (int y = 0; y < P.ny; ++y)
                 for (int x = 0; x < P.nx; ++x) {
@@ -976,7 +989,7 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
             // entry past the end of a whole row); wall-shear nodes in
             // storage order with their lattice indices kept on the host
             links.assign(Np, 1u << 31);
-            const std::vector<uint8_t> near = near_solid(P, geom->solid);
+            const std::vector<uint8_t> &near = P.near;
             for (int z = 0; z < P.nz; ++z)
                 for (int y = 0; y < P.ny; ++y) {
                     const int4 rt = P.rows[(size_t)y + (size_t)P.ny * z];
@@ -987,7 +1000,7 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
                         if (geom->solid[n]) continue;
                         uint32_t m = 0u;
                         float nv[3] = {0.f, 0.f, 0.f};
-                        if (near[n])
+                        if (!near.empty() && near[n])
                             for (int p = 1; p < kQ; ++p)
                                 if (geom->solid[node(P, x + cx(p), y + cy(p), z + cz(p))]) {
                                     m |= 1u << p;
@@ -1020,8 +1033,7 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
             // when the downstream node x + c_p is solid (fluid nodes), bit 29 /
             // 30 for inlet / outlet nodes, bit 31 when x is solid
             links.assign((size_t)P.N, 0u);
-            std::vector<uint8_t> near;
-            if (geom->solid) near = near_solid(P, geom->solid);
+            const std::vector<uint8_t> &near = P.near;
             for (int z = 0; z < P.nz; ++z)
                 for (int y = 0; y < P.ny; ++y) {
                     const long long row = (long long)P.nx * ((long long)y + (long long)P.ny * z);
@@ -1033,7 +1045,7 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
                         }
                         uint32_t m = 0u;
                         float nv[3] = {0.f, 0.f, 0.f};
-                        if (geom->solid && near[n])
+                        if (!near.empty() && near[n])
                             for (int p = 1; p < kQ; ++p)
                                 if (geom->solid[node(P, x + cx(p), y + cy(p), z + cz(p))]) {
                                     m |= 1u << p;
@@ -1053,6 +1065,7 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
                 }
             RBC_CU(cudaMemcpyAsync(d.links, links.data(), links.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
         }
+        std::vector<uint8_t>().swap(h->P.near);  // the set-up's last use of it
         if (d.fluid_list) {
             flist.reserve((size_t)P.nfluid);
             for (long long n = 0; n < (long long)P.N; ++n)
