@@ -116,85 +116,5 @@ __host__ __device__ inline Sym3 shape_tensor(const double Q[9], const double a2[
     return A;
 }
 
-__device__ __forceinline__ void sym_apply(const Sym3 &A, const double v[3], double r[3])
-{
-    r[0] = A.xx * v[0] + A.xy * v[1] + A.xz * v[2];
-    r[1] = A.xy * v[0] + A.yy * v[1] + A.yz * v[2];
-    r[2] = A.xz * v[0] + A.yz * v[1] + A.zz * v[2];
-}
-
-// ---------------------------------------------------------------------------
-// Gay-Berne pair (Sec. 2.5, App. B), d = R_i - R_j: the force on i and the
-// lab-frame torque on i; returns true if the pair is inside the range.
-//   kappa = (A_i + A_j)^-1 d, phi = (d.kappa) / (2 R^2), sigma = phi^-1/2,
-//   rho = (R - sigma + sigma_min) / sigma_min, range rho <= 2^(1/6),
-//   F_i = -u'(rho)/sigma_min d^ - (du/dphi / R^2) (kappa - (kappa.d^) d^),
-//   du/dphi = u'(rho) sigma^3 / (2 sigma_min),
-//   tau_i = (-A_i kappa) x f_kappa, f_kappa = -(du/dphi / R^2) kappa.
-// rho below rho_floor is evaluated at rho_floor and counted.
-// ---------------------------------------------------------------------------
-// Precision: the geometry -- kappa, R, phi, sigma, rho -- and u'(rho) in
-// FP64, so the range test and the clamp count are exact and the two
-// differences of nearly equal numbers (the gap R - sigma, and u'(rho) near
-// the minimum of the potential) keep FP64 accuracy; the force and torque
-// vectors in FP32 from them (relative error ~1e-7).  F and T are this pair's
-// contribution; the caller sums them per cell in FP64.  Ai_f: A_i in FP32
-// (xx yy zz xy xz yz); ismin = 1 / sigma_min.
-__device__ inline bool gb_pair_mixed(const double d[3], const Sym3 &Ai, const Sym3 &Aj, const float Ai_f[6],
-                                     double smin, double ismin, double eps0, double rho_floor, double rho_cut,
-                                     float F[3], float T[3], int &clamped)
-{
-    Sym3 H{Ai.xx + Aj.xx, Ai.yy + Aj.yy, Ai.zz + Aj.zz, Ai.xy + Aj.xy, Ai.xz + Aj.xz, Ai.yz + Aj.yz};
-    const double cxx = H.yy * H.zz - H.yz * H.yz;
-    const double cyy = H.xx * H.zz - H.xz * H.xz;
-    const double czz = H.xx * H.yy - H.xy * H.xy;
-    const double cxy = H.xz * H.yz - H.xy * H.zz;
-    const double cxz = H.xy * H.yz - H.xz * H.yy;
-    const double cyz = H.xy * H.xz - H.xx * H.yz;
-    const double idet = 1.0 / (H.xx * cxx + H.xy * cxy + H.xz * cxz);
-    double k[3];
-    k[0] = (cxx * d[0] + cxy * d[1] + cxz * d[2]) * idet;
-    k[1] = (cxy * d[0] + cyy * d[1] + cyz * d[2]) * idet;
-    k[2] = (cxz * d[0] + cyz * d[1] + czz * d[2]) * idet;
-    const double R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    const double R = sqrt(R2);
-    const double phi = 0.5 * (d[0] * k[0] + d[1] * k[1] + d[2] * k[2]) / R2;
-    const double sigma = 1.0 / sqrt(phi);
-    double rho = (R - sigma + smin) / smin;
-    if (rho > rho_cut) return false;
-    if (rho < rho_floor) {
-        rho = rho_floor;
-        clamped++;
-    }
-    // u'(rho) in FP64 too: 2 rho^-13 - rho^-7 cancels near the minimum of
-    // the potential
-    const double ir = 1.0 / rho;
-    const double ir2 = ir * ir;
-    const double ir6 = ir2 * ir2 * ir2;
-    const double ir7 = ir6 * ir;
-    const double ir13 = ir6 * ir7;
-    const double dud = -24.0 * eps0 * (2.0 * ir13 - ir7);  // du/drho
-    const float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
-    const float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
-    const float Rf = (float)R, R2f = (float)R2;
-    const float dudR = (float)(dud * ismin);
-    const float dudphi = (float)(dud * sigma * sigma * sigma * (0.5 * ismin));
-    const float iR = 1.0f / Rf;
-    const float kR = (kf[0] * df[0] + kf[1] * df[1] + kf[2] * df[2]) * iR;
-    const float g = dudphi / R2f;
-    float fk[3];
-    for (int a = 0; a < 3; ++a) {
-        F[a] = -dudR * df[a] * iR - g * (kf[a] - kR * df[a] * iR);
-        fk[a] = -g * kf[a];
-    }
-    const float Ak[3] = {Ai_f[0] * kf[0] + Ai_f[3] * kf[1] + Ai_f[4] * kf[2],
-                         Ai_f[3] * kf[0] + Ai_f[1] * kf[1] + Ai_f[5] * kf[2],
-                         Ai_f[4] * kf[0] + Ai_f[5] * kf[1] + Ai_f[2] * kf[2]};
-    // (-A_i kappa) x f_kappa
-    T[0] = -(Ak[1] * fk[2] - Ak[2] * fk[1]);
-    T[1] = -(Ak[2] * fk[0] - Ak[0] * fk[2]);
-    T[2] = -(Ak[0] * fk[1] - Ak[1] * fk[0]);
-    return true;
-}
 
 }  // namespace rbc
