@@ -53,8 +53,8 @@ struct Problem {
     // compact layout (Dev in internal.h)
     bool compact = false;
     int M = 0;
-    std::vector<int4> rows, batches;
-    std::vector<int2> bx, pool;  // per batch (pool offset, bytes); per batch row nine copy descriptors
+    std::vector<int4> rows, batches;  // batches: (first descriptor, segments | entries << 8, bytes, 0)
+    std::vector<int2> pool;           // kSegDescs copy descriptors per batch segment
     int stage_bytes = 0;
     bool has_ext = false;  // cells carry an external force or torque
     std::vector<uint8_t> near;  // near_solid of the mask (host set-up only; released after rbc_init)
@@ -132,20 +132,23 @@ inline int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 // fl / fh: x-range of the fluid nodes of every row (y, z).  A row's span is
 // the hull of the fluid ranges of the nine rows (y + dy, z + dz), |dy|,
 // |dz| <= 1, widened by one node -- it holds every node a fluid node of the
-// row or its neighbours reaches through a link -- rounded out to multiples
-// of 8 entries; when that hull wraps around x (a neighbour row has fluid at
+// row or its neighbours reaches through a link -- rounded out to whole
+// 32-byte sectors of a population plane (A = 8 FP32 or 16 two-byte
+// entries); when that hull wraps around x (a neighbour row has fluid at
 // x = 0 or nx - 1) the span is the whole row.  Batches of the lattice pass:
-// runs of consecutive rows with fluid at one z whose common window (their
-// fluid x-range widened by one, rounded out to 8, or the whole row when it
-// wraps) times the rows fits in a stage of at most stage_cap bytes
-// (node_bytes staged per window entry); a non-wrapping row wider than that
-// is cut along x.  Copy descriptors: for every batch row and each of its
-// nine upstream rows (y + dy, z + dz), the part of that row's span inside
-// the window -- first entry, window offset, entry count -- and per batch the
-// total bytes its copies bring (esz bytes per population entry of the three
-// or one speeds pulled from that row, plus G / theta (cells) and the link
-// word from the row itself).  Returns false when a wrapping row does not
-// fit.
+// consecutive row segments -- a segment is a row's fluid x-range [c0, c1]
+// (or one run of a branched row, or a piece of a row) with its window
+// [X0, X0 + W), the range widened by one and rounded out to A entries, or the
+// whole row when it wraps -- whose windows together fill a stage of cap
+// entries (node_bytes staged per entry); the segment that overflows a stage
+// is cut there when the room left is worth a piece.  Per segment the pool
+// holds kSegDescs int2: for each of its nine upstream rows (y + dy, z + dz)
+// the part of that row's span inside the window (first entry, window offset,
+// entry count), the segment's (y, z), its range and window, and its offset
+// in the stage's planes; per batch the total bytes its copies bring (esz
+// bytes per population entry of the three or one speeds pulled from that
+// row, plus G / theta (cells) and the link word from the row itself).
+// Returns false when a wrapping row does not fit a stage.
 bool build_compact(Problem &P, const uint8_t *solid, int esz, bool cells)
 {
     const int node_bytes = kQ * esz + (cells ? 16 : 0) + 4;
@@ -193,10 +196,23 @@ bool build_compact(Problem &P, const uint8_t *solid, int esz, bool cells)
         }
     if (off >= (1LL << 31) - 64) return false;
     P.M = (int)off;
-    // batches
-    const int stage_cap = std::max(24 * 1024, any_wrap ? full * node_bytes : 0);
-    if (stage_cap > 96 * 1024) return false;
-    const int cap = stage_cap / node_bytes;  // window entries per stage
+    // batches: row segments in (z, y, x) order -- a row's fluid range, or
+    // each run of a branched row, or a piece of a row wider than a stage --
+    // packed into stages of cap window entries.  Entries per stage (measured
+    // on the 256^3 tube): FP32 populations 256 without cells (one node per
+    // consumer thread; lattice pass 449 us, against 473 with 512) and 512
+    // with cells (the autotuned step then runs the pass at one CTA of two
+    // stages per SM, leaving room for the cell kernels beside it: 1.198 ->
+    // 1.173 ms per step; 768: 1.276 ms); 16-bit populations 768 (1.212 ms
+    // with 512, 1.206 with 768, 1.359 with 1024).  When a stage holds more
+    // than one row, the segment that overflows it is cut there (its rest
+    // opens the next batch) unless it wraps around x or the room left is
+    // small; one-row FP32 stages take whole segments (cutting them filled the
+    // stages, 0.85 -> 0.98, but the windows' overlap at the cuts and the
+    // extra copies cost more: 449 -> 461 us).
+    const int per_stage = esz == 4 ? (cells ? 2 : 1) : 3;
+    const int cap = std::max(256 * per_stage, any_wrap ? full : 0);  // window entries per stage
+    if ((long long)cap * node_bytes > 96 * 1024) return false;
     auto window = [&](int c0, int c1, int &X0, int &W) {
         if (c0 == 0 || c1 == nx - 1) {
             X0 = 0;
@@ -206,16 +222,31 @@ bool build_compact(Problem &P, const uint8_t *solid, int esz, bool cells)
             W = (c1 + 2 + A - 1) / A * A - X0;
         }
     };
-    auto push = [&](int z, int y0, int nb, int c0, int c1, int X0, int W) {
-        P.batches.push_back(make_int4(z, y0 | (nb << 20), c0 | (c1 << 16), X0 | (W << 16)));
+    struct Seg {
+        int z, y, c0, c1;
     };
-    P.batches.clear();
-    int most = 0;
+    std::vector<Seg> segs;
+    bool fits = true;
+    auto add_seg = [&](int z, int y, int c0, int c1) {
+        int X0, W;
+        window(c0, c1, X0, W);
+        if (W <= cap) {
+            segs.push_back({z, y, c0, c1});
+            return;
+        }
+        const int L = (cap - 2 * A) / A * A;
+        if (c0 == 0 || c1 == nx - 1 || L < A) {
+            fits = false;
+            return;
+        }
+        for (int a0 = c0; a0 <= c1; a0 += L) segs.push_back({z, y, a0, std::min(c1, a0 + L - 1)});
+    };
     // a row whose fluid nodes form runs separated by wide solid gaps (a
     // vessel that branched) is taken one run at a time, so that neither the
     // copies nor the consumer threads cover the gap
     const int kGap = 24;
-    auto runs_of = [&](int r, std::vector<std::pair<int, int>> &runs) {
+    std::vector<std::pair<int, int>> runs;
+    auto runs_of = [&](int r) {
         runs.clear();
         const uint8_t *row = solid + (size_t)r * nx;
         int x = fl[r];
@@ -230,93 +261,67 @@ bool build_compact(Problem &P, const uint8_t *solid, int esz, bool cells)
             while (x <= fh[r] && row[x]) ++x;
         }
     };
-    std::vector<std::pair<int, int>> runs;
-    for (int z = 0; z < nz; ++z) {
-        int y = 0;
-        while (y < ny) {
+    for (int z = 0; z < nz && fits; ++z)
+        for (int y = 0; y < ny && fits; ++y) {
             const int r = y + ny * z;
-            if (fh[r] < 0) {
-                ++y;
-                continue;
-            }
-            runs_of(r, runs);
-            if (runs.size() > 1 && fl[r] > 0 && fh[r] < nx - 1) {
-                for (const auto &run : runs) {
-                    int X0r, Wr;
-                    window(run.first, run.second, X0r, Wr);
-                    if (Wr > cap) {
-                        const int L = (cap - 2 * A) / A * A;
-                        if (L < A) return false;
-                        for (int a0 = run.first; a0 <= run.second; a0 += L) {
-                            const int a1 = std::min(run.second, a0 + L - 1);
-                            window(a0, a1, X0r, Wr);
-                            push(z, y, 1, a0, a1, X0r, Wr);
-                            most = std::max(most, Wr);
-                        }
-                    } else {
-                        push(z, y, 1, run.first, run.second, X0r, Wr);
-                        most = std::max(most, Wr);
-                    }
-                }
-                ++y;
-                continue;
-            }
-            int c0 = fl[r], c1 = fh[r], X0, W;
-            window(c0, c1, X0, W);
-            if (W > cap) {
-                const int L = (cap - 2 * A) / A * A;
-                if (c0 == 0 || c1 == nx - 1 || L < A) return false;
-                for (int a0 = c0; a0 <= c1; a0 += L) {
-                    const int a1 = std::min(c1, a0 + L - 1);
-                    window(a0, a1, X0, W);
-                    push(z, y, 1, a0, a1, X0, W);
-                    most = std::max(most, W);
-                }
-                ++y;
-                continue;
-            }
-            int nb = 1;
-            while (y + nb < ny && nb < 16) {  // at most 16 rows (the pass stages their row bases)
-                const int r2 = y + nb + ny * z;
-                if (fh[r2] < 0) break;
-                runs_of(r2, runs);
-                if (runs.size() > 1 && fl[r2] > 0 && fh[r2] < nx - 1) break;
-                const int d0 = std::min(c0, fl[r2]), d1 = std::max(c1, fh[r2]);
-                int X0b, Wb;
-                window(d0, d1, X0b, Wb);
-                if ((nb + 1) * Wb > cap) break;
-                c0 = d0;
-                c1 = d1;
-                X0 = X0b;
-                W = Wb;
-                ++nb;
-            }
-            push(z, y, nb, c0, c1, X0, W);
-            most = std::max(most, nb * W);
-            y += nb;
+            if (fh[r] < 0) continue;
+            runs_of(r);
+            if (runs.size() > 1 && fl[r] > 0 && fh[r] < nx - 1)
+                for (const auto &run : runs) add_seg(z, y, run.first, run.second);
+            else
+                add_seg(z, y, fl[r], fh[r]);
         }
-    }
-    P.stage_bytes = (most * node_bytes + 127) / 128 * 128;
-    // copy descriptors
-    P.bx.clear();
+    if (!fits) return false;
+    // copy descriptors of one segment (kSegDescs int2 in the pool): for each
+    // of its nine upstream rows (y + dy, z + dz) the part of that row's span
+    // inside the window -- first entry, window offset | entry count << 16 --
+    // then (y, z), (c0 | c1 << 16, X0 | W << 16), (plane offset, 0)
+    P.batches.clear();
     P.pool.clear();
-    for (const int4 &bd : P.batches) {
-        const int z = bd.x, y0 = bd.y & 0xFFFFF, nb = (int)((uint32_t)bd.y >> 20);
-        const int X0 = bd.w & 0xFFFF, W = (int)((uint32_t)bd.w >> 16);
-        long long bytes = 0;
+    int most = 0;
+    const int kMinPiece = per_stage == 1 ? 1 << 30 : 4 * A;
+    size_t i = 0;
+    while (i < segs.size()) {
         const int first = (int)P.pool.size();
-        for (int b = 0; b < nb; ++b)
+        int nb = 0, total = 0;
+        long long bytes = 0;
+        auto emit = [&](const Seg &s, int c1, int X0, int W) {
             for (int u = 0; u < 9; ++u) {
                 const int dy = u % 3 - 1, dz = u / 3 - 1;
-                const int4 rt = P.rows[(size_t)wrapi(y0 + b + dy, ny) + (size_t)ny * wrapi(z + dz, nz)];
+                const int4 rt = P.rows[(size_t)wrapi(s.y + dy, ny) + (size_t)ny * wrapi(s.z + dz, nz)];
                 const int lo = std::max(X0, rt.y), hi = std::min(X0 + W, rt.z);
                 const int cnt = std::max(0, hi - lo);
                 P.pool.push_back(cnt > 0 ? make_int2(rt.x + lo - rt.y, (lo - X0) | (cnt << 16)) : make_int2(0, 0));
                 const int planes = (dy == 0 || dz == 0) ? 3 : 1;
                 bytes += (long long)cnt * (esz * planes + (u == 4 ? (cells ? 16 : 0) + 4 : 0));
             }
-        P.bx.push_back(make_int2(first, (int)bytes));
+            P.pool.push_back(make_int2(s.y, s.z));
+            P.pool.push_back(make_int2(s.c0 | (c1 << 16), X0 | (W << 16)));
+            P.pool.push_back(make_int2(total, 0));
+            total += W;
+            ++nb;
+        };
+        while (i < segs.size() && nb < kMaxSegs) {
+            Seg &s = segs[i];
+            int X0, W;
+            window(s.c0, s.c1, X0, W);
+            if (total + W <= cap) {
+                emit(s, s.c1, X0, W);
+                ++i;
+                continue;
+            }
+            const int R = cap - total;
+            const int a1 = X0 + R - 2;  // window(c0, a1) is [X0, X0 + R)
+            if (s.c0 > 0 && s.c1 < nx - 1 && R >= kMinPiece && a1 >= s.c0 && a1 < s.c1) {
+                emit(s, a1, X0, R);
+                s.c0 = a1 + 1;
+            }
+            break;
+        }
+        P.batches.push_back(make_int4(first, nb | (total << 8), (int)bytes, 0));
+        most = std::max(most, total);
     }
+    P.stage_bytes = (most * node_bytes + 127) / 128 * 128;
     return true;
 }
 
@@ -573,7 +578,6 @@ int analyse(const rbc_geometry *g, const rbc_cells *c, const rbc_params *pp, Pro
         if (!P.compact) {
             P.rows.clear();
             P.batches.clear();
-            P.bx.clear();
             P.pool.clear();
         }
     }
@@ -615,7 +619,6 @@ size_t carve(const Problem &P, const rbc_params *q, void *base, Dev &d)
     d.rows = P.compact ? cv.take<int4>((size_t)P.ny * P.nz) : nullptr;
     d.nbatches = P.compact ? (int)P.batches.size() : 0;
     d.lb_batches = P.compact ? cv.take<int4>((size_t)std::max(d.nbatches, 1)) : nullptr;
-    d.lb_bx = P.compact ? cv.take<int2>((size_t)std::max(d.nbatches, 1)) : nullptr;
     d.lb_pool = P.compact ? cv.take<int2>(std::max(P.pool.size(), (size_t)1)) : nullptr;
     d.lb_stage_bytes = P.compact ? P.stage_bytes : 0;
     d.nwss = P.nwss;
@@ -1023,8 +1026,6 @@ int rbc_init(const rbc_geometry *geom, const rbc_cells *cells, const rbc_params 
             RBC_CU(cudaMemcpyAsync(const_cast<int4 *>(d.rows), P.rows.data(), P.rows.size() * sizeof(int4),
                                    cudaMemcpyHostToDevice, s));
             RBC_CU(cudaMemcpyAsync(const_cast<int4 *>(d.lb_batches), P.batches.data(), P.batches.size() * sizeof(int4),
-                                   cudaMemcpyHostToDevice, s));
-            RBC_CU(cudaMemcpyAsync(const_cast<int2 *>(d.lb_bx), P.bx.data(), P.bx.size() * sizeof(int2),
                                    cudaMemcpyHostToDevice, s));
             RBC_CU(cudaMemcpyAsync(const_cast<int2 *>(d.lb_pool), P.pool.data(), P.pool.size() * sizeof(int2),
                                    cudaMemcpyHostToDevice, s));

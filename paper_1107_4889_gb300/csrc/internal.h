@@ -16,6 +16,12 @@ using rbc_handle_t = ::rbc_handle;
 // Q[9] body->lab, base[3] = box origin - R, origin[3], dims[3], centre node, ok.
 constexpr int kHdrWords = 20;
 
+// Compact lattice pass: at most kMaxSegs row segments per batch, each
+// described by kSegDescs int2 in the descriptor pool (nine upstream copies,
+// (y, z), (c0 | c1 << 16, X0 | W << 16), (offset in the stage's planes, 0)).
+constexpr int kMaxSegs = 16;
+constexpr int kSegDescs = 12;
+
 // Flags word indices (device int[8]).
 enum { FLAG_UNSTABLE = 0, FLAG_OVERFLOW = 1, FLAG_TIMEOUT = 2 };
 enum { OVF_BIN = 1, OVF_NBR = 2, OVF_BOX = 4 };
@@ -50,7 +56,7 @@ struct Dev {
     // the entries of each lattice row (y, z) that a fluid node can reach
     // through a link are stored: the row's span [s_lo, s_hi) of x, the hull
     // of the fluid nodes of the nine rows (y + dy, z + dz) widened by one
-    // node, rounded out to multiples of 8, or the whole row when that hull
+    // node, rounded out to whole 32-byte sectors, or the whole row when that hull
     // wraps around x.  rows[y + ny z] = (offset of the row's first entry,
     // s_lo, s_hi, fluid x-range lo | hi << 16; lo > hi for a row without
     // fluid).  Every field array then holds M entries in lattice order plus
@@ -59,9 +65,8 @@ struct Dev {
     int compact;
     int M, zero_entry;
     const int4 *rows;
-    const int4 *lb_batches;  // compact lattice pass: (z, y0 | nb << 20, C0 | C1 << 16, X0 | W << 16)
-    const int2 *lb_bx;       // per batch: (first copy descriptor in lb_pool, bytes of its copies)
-    const int2 *lb_pool;     // per batch row, 9 copy descriptors (first entry, window offset | count << 16)
+    const int4 *lb_batches;  // compact lattice pass: (first descriptor in lb_pool, segments | entries << 8, bytes, 0)
+    const int2 *lb_pool;     // per batch segment kSegDescs descriptors (nine upstream rows, position, window)
     int nbatches;
     // wall shear stress: wall-adjacent fluid nodes, unit normals into the
     // fluid (3 floats each), time sums of the tangential traction

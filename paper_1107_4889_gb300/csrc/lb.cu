@@ -807,35 +807,34 @@ __global__ void __launch_bounds__(kStThreads) k_lb_staged(LbArgs a, StageLayout 
 // ---------------------------------------------------------------------------
 // Compact lattice pass (walled lattices in the compact layout).  The same
 // persistent producer / consumer pipeline as the row-staged pass, over a
-// table of batches built at set-up: a batch is nb consecutive rows
-// y0 .. y0 + nb - 1 at one z that all hold fluid, the x-range [C0, C1] of
-// their fluid nodes (the union of the rows' ranges; a row wider than a stage
-// is cut into several batches), and the staged window [X0, X0 + W) =
-// [C0 - 1, C1 + 1] rounded out to multiples of 8 entries (the whole row when
-// the row wraps along x).  Rows without fluid are never visited: their
-// entries are only the targets of the bounce-back writes of their fluid
-// neighbours.  For every speed p the producer copies, per batch row, the
-// part of the upstream row (y - c_y, z - c_z) that lies in both the window
-// and that row's span (one bulk copy each; span and window ends are
-// multiples of 8 entries, so every copy starts and ends on a 16-byte
-// boundary), plus the batch rows' own G / theta and link words.  Stage
-// layout: [19][nb][W] populations, [nb][W] float4 G, [nb][W] link words;
-// window column x sits at x - X0.  The consumers collide the fluid nodes of
-// [C0, C1] x rows; a node pulls only from upstream entries inside the
-// upstream row's span (every node one link away from a fluid node is
-// stored), so the parts of the window outside a span are never read.
+// table of batches built at set-up.  A batch is up to kMaxSegs row segments
+// in lattice order: a segment is the fluid x-range [c0, c1] of one row (or
+// of one run of a branched row, or a piece of a row) with its staged window
+// [X0, X0 + W) = [c0 - 1, c1 + 1] rounded out to whole 32-byte sectors (the
+// whole row when the row wraps along x); the windows of a batch fill one
+// stage, the segment that overflows it being cut.  Rows without fluid are
+// never visited: their entries are only the targets of the bounce-back
+// writes of their fluid neighbours.  For every speed p the producer copies,
+// per segment, the part of the upstream row (y - c_y, z - c_z) that lies in
+// both the window and that row's span (one bulk copy each; span and window
+// ends are whole sectors, so every copy starts and ends on a 16-byte
+// boundary), plus the segment's own G / theta and link words.  Stage layout:
+// [19][E] populations, [E] float4 G, [E] link words, E the batch's window
+// entries; segment s's window column x sits at off_s + x - X0_s.  The
+// consumer threads run over the E entries and collide the fluid nodes among
+// them; a node pulls only from upstream entries inside the upstream row's
+// span (every node one link away from a fluid node is stored), so the parts
+// of a window outside a span are never read.
 // ---------------------------------------------------------------------------
 // Producer side of one compact batch.  The set-up precomputed, for every
-// batch row b and each of its nine upstream rows u = (dy + 1) + 3 (dz + 1)
+// segment s and each of its nine upstream rows u = (dy + 1) + 3 (dz + 1)
 // (the row (y + dy, z + dz) that the speeds with c_y = -dy, c_z = -dz pull
 // from), the part of that row's span inside the window: its first entry and
-// (offset in the window | entry count << 16); and per batch the pool offset
-// of these descriptors and the bytes of all its copies.  The lanes take the
-// batch's copies one each (speed plane k of batch row b reads descriptor
-// u(k) of that row; G / theta and the link words read u = 4), so a batch
-// row's 20 or 21 copies go out in one pass of the warp.
-constexpr int kMaxBatchRows = 16;  // rows of one compact batch (the set-up keeps to it)
-
+// (window offset | entry count << 16); and per batch the bytes of all its
+// copies.  The lanes take the batch's copies one each (speed plane k of
+// segment s reads descriptor u(k) of that segment; G / theta and the link
+// words read u = 4), so a segment's 20 or 21 copies go out in one pass of
+// the warp.
 // Upstream row of speed p among the nine (dy, dz) rows of a compact batch
 // row, u = (dy + 1) + 3 (dz + 1) with (dy, dz) = (-c_y, -c_z), for a
 // run-time p: four bits per speed in two 64-bit constants.
@@ -863,63 +862,74 @@ __device__ __forceinline__ void cp_async_8(uint32_t dst, const void *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// The producer's own copy of one batch's copy descriptors (pd[j], j < 9 nb)
-// and of its rows' fluid x-ranges (pfr[b]): asynchronous copies, so that
-// they are in flight while the producer waits for a free stage and hold no
-// registers meanwhile.  The caller waits for them (cp_async_wait_all, then
-// __syncwarp: pfr[b] is read by another lane than the one that copied it).
-__device__ __forceinline__ void load_descs(const LbArgs &a, int4 bd, int2 bx, int lane, int2 *pd, int *pfr)
+// The producer's own copy of one batch's descriptors (pd[j], j < kSegDescs
+// nb): asynchronous copies, so that they are in flight while the producer
+// waits for a free stage and hold no registers meanwhile.  The caller waits
+// for them (cp_async_wait_all, then __syncwarp: every lane reads entries
+// that other lanes copied).
+__device__ __forceinline__ void load_descs(const LbArgs &a, int4 bd, int lane, int2 *pd)
 {
-    const int nb = (int)((uint32_t)bd.y >> 20);
-    const int z = bd.x, y0 = bd.y & 0xFFFFF;
-    for (int j = lane; j < 9 * nb; j += 32) cp_async_8(smem_addr(&pd[j]), a.pool + bx.x + j);
-    if (lane < nb) cp_async_4(smem_addr(&pfr[lane]), &a.rows[y0 + lane + a.ny * z].w);
+    const int nd = kSegDescs * (bd.y & 0xFF);
+    for (int j = lane; j < nd; j += 32) cp_async_8(smem_addr(&pd[j]), a.pool + bd.x + j);
     cp_async_commit();
 }
 
-// rbs[b][u]: base of upstream row u of batch row b (entry of x' in that row =
-// base + x'), rbs[b][9]: the batch row's fluid x-range; written before the
-// stage's arrive, read by the consumers.
+// Per segment s of a stage, rbs[s][..]: [0..8] base of upstream row u
+// (entry of x' in that row = base + x'), [9] y, [10] z, [11] c0, [12] c1,
+// [13] X0, [14] off_s, [15] off_s + W_s; written before the stage's arrive,
+// read by the consumers.
+constexpr int kSegWords = 16;
 template <typename St, bool CELLS>
-__device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, int2 bx, const int2 *pd, const int *pfr,
-                                                unsigned char *base, uint32_t bar, int lane, int (*rbs)[10])
+__device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, const int2 *pd, unsigned char *base,
+                                                uint32_t bar, int lane, int (*rbs)[kSegWords])
 {
-    const int nb = (int)((uint32_t)bd.y >> 20);
-    const int W = (int)((uint32_t)bd.w >> 16);
-    const int X0 = bd.w & 0xFFFF;
-    for (int j = lane; j < 9 * nb; j += 32) {
+    const int nb = bd.y & 0xFF;
+    const int total = (int)((uint32_t)bd.y >> 8);
+    for (int j = lane; j < kSegDescs * nb; j += 32) {
         const int2 e = pd[j];
-        const int count = (int)((uint32_t)e.y >> 16), at = e.y & 0xFFFF;
-        const int b = j / 9, u = j - 9 * b;
-        rbs[b][u] = count > 0 ? e.x - at - X0 : 0;
-        if (u == 4) rbs[b][9] = pfr[b];
+        const int b = j / kSegDescs, u = j - kSegDescs * b;
+        int *rb = rbs[b];
+        if (u < 9) {
+            const int count = (int)((uint32_t)e.y >> 16), at = e.y & 0xFFFF;
+            rb[u] = count > 0 ? e.x - at - (pd[kSegDescs * b + 10].y & 0xFFFF) : 0;
+        } else if (u == 9) {
+            rb[9] = e.x;
+            rb[10] = e.y;
+        } else if (u == 10) {
+            rb[11] = e.x & 0xFFFF;
+            rb[12] = (int)((uint32_t)e.x >> 16);
+            rb[13] = e.y & 0xFFFF;
+        } else {
+            rb[14] = e.x;
+            rb[15] = e.x + (int)((uint32_t)pd[kSegDescs * b + 10].y >> 16);
+        }
     }
     __syncwarp();
-    if (lane == 0) mbar_expect_tx(bar, (uint32_t)bx.y);
+    if (lane == 0) mbar_expect_tx(bar, (uint32_t)bd.z);
     __syncwarp();
-    // one copy per lane: copy k of batch row b is speed plane k (k < 19),
+    // one copy per lane: copy k of segment s is speed plane k (k < 19),
     // whose upstream row is u = (1 - c_y) + 3 (1 - c_z), then G / theta
     // and the link words of the row itself (u = 4)
     constexpr int kCopies = kQ + (CELLS ? 2 : 1);
     const uint64_t once = l2_evict_first();
-    const size_t pop_bytes = (size_t)kQ * nb * W * sizeof(St);
+    const size_t pop_bytes = (size_t)kQ * total * sizeof(St);
     for (int j = lane; j < kCopies * nb; j += 32) {
         const int b = j / kCopies, k = j - b * kCopies;
         const int u = k < kQ ? upstream_row(k) : 4;
-        const int2 e = pd[9 * b + u];
+        const int2 e = pd[kSegDescs * b + u];
         const int count = (int)((uint32_t)e.y >> 16);
         if (count == 0) continue;
-        const int at = e.y & 0xFFFF;  // window offset of the first entry
+        const int at = pd[kSegDescs * b + 11].x + (e.y & 0xFFFF);  // stage column of the first entry
         if (k < kQ) {
             const St *g = static_cast<const St *>(a.src) + (size_t)k * (size_t)a.Np + (size_t)e.x;
-            bulk_g2s_hint(smem_addr(base + ((size_t)(k * nb + b) * W + at) * sizeof(St)), g,
+            bulk_g2s_hint(smem_addr(base + ((size_t)k * total + at) * sizeof(St)), g,
                           (uint32_t)(count * (int)sizeof(St)), bar, once);
         } else if (CELLS && k == kQ) {
-            bulk_g2s(smem_addr(base + pop_bytes + ((size_t)b * W + at) * sizeof(float4)), a.G + e.x,
+            bulk_g2s(smem_addr(base + pop_bytes + (size_t)at * sizeof(float4)), a.G + e.x,
                      (uint32_t)(count * (int)sizeof(float4)), bar);
         } else {
-            bulk_g2s(smem_addr(base + pop_bytes + (CELLS ? (size_t)nb * W * sizeof(float4) : 0) +
-                               ((size_t)b * W + at) * sizeof(uint32_t)),
+            bulk_g2s(smem_addr(base + pop_bytes + (CELLS ? (size_t)total * sizeof(float4) : 0) +
+                               (size_t)at * sizeof(uint32_t)),
                      a.links + e.x, (uint32_t)(count * (int)sizeof(uint32_t)), bar);
         }
     }
@@ -927,59 +937,46 @@ __device__ __forceinline__ void produce_compact(const LbArgs &a, int4 bd, int2 b
 
 template <typename St, bool CELLS, bool SIGMA>
 __device__ __forceinline__ void consume_compact(const LbArgs &a, int4 bd, const unsigned char *base,
-                                                unsigned long long step, const int (*rbs)[10])
+                                                unsigned long long step, const int (*rbs)[kSegWords])
 {
     const int nx = a.nx, ny = a.ny;
-    const int z = bd.x, y0 = bd.y & 0xFFFFF, nb = (int)((uint32_t)bd.y >> 20);
-    const int C0 = bd.z & 0xFFFF, C1 = (int)((uint32_t)bd.z >> 16);
-    const int X0 = bd.w & 0xFFFF, W = (int)((uint32_t)bd.w >> 16);
-    // threads run over the whole window from its sector-aligned start X0, so
-    // that a warp's stores cover whole 32-byte sectors of each plane
-    const int total = nb * W;
-    const size_t pop_bytes = (size_t)kQ * nb * W * sizeof(St);
+    // threads run over the batch's window entries, whose segments start on
+    // whole sectors, so that a warp's stores cover whole 32-byte sectors of
+    // each plane
+    const int total = (int)((uint32_t)bd.y >> 8);
+    const size_t pop_bytes = (size_t)kQ * total * sizeof(St);
     const St *pst = reinterpret_cast<const St *>(base);
     const float4 *gst = reinterpret_cast<const float4 *>(base + pop_bytes);
     const uint32_t *lst =
-        reinterpret_cast<const uint32_t *>(base + pop_bytes + (CELLS ? (size_t)nb * W * sizeof(float4) : 0));
-    // (t, 256) -> (row, column) of the window without an integer division:
-    // floor((t + 1/2) / W) in FP32 is exact for t <= 256 (a quotient that is
-    // a whole number k is hit as k + 1/(2W), never rounded below k)
-    const int t = (int)threadIdx.x;
-    const float iW = 1.0f / (float)W;
-    const int db = (int)(((float)kStConsumers + 0.5f) * iW), dx = kStConsumers - db * W;
-    int b = (int)(((float)t + 0.5f) * iW), xo = t - b * W;
-    for (int l = t; l < total; l += kStConsumers) {
-        const int bb = b, x = X0 + xo;
-        xo += dx;
-        b += db;
-        if (xo >= W) {
-            xo -= W;
-            ++b;
-        }
-        const int y = y0 + bb;
-        const int *rb = rbs[bb];
-        const int fr = rb[9];
-        if (x < max(C0, fr & 0xFFFF) || x > min(C1, (int)((uint32_t)fr >> 16))) continue;
-        const int sx = bb * W + x - X0;
-        const uint32_t lk = lst[sx];
+        reinterpret_cast<const uint32_t *>(base + pop_bytes + (CELLS ? (size_t)total * sizeof(float4) : 0));
+    int s = 0;
+    for (int l = (int)threadIdx.x; l < total; l += kStConsumers) {
+        while (l >= rbs[s][15]) ++s;  // the last segment ends at total
+        const int *rb = rbs[s];
+        const int x = rb[13] + l - rb[14];
+        if (x < rb[11] || x > rb[12]) continue;
+        const uint32_t lk = lst[l];
         if (lk >> 31) continue;
+        const int y = rb[9], z = rb[10];
         const uint32_t n = (uint32_t)(rb[4] + x);
         const uint32_t nd = (uint32_t)x + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
         if (lk & 0x60000000u) {
             boundary_node<St, CELLS, SIGMA, true>(a, n, nd, x, y, z, lk, step);
             continue;
         }
-        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        // window column of x - 1 / x + 1 relative to x (the neighbour across
+        // a periodic x boundary lies in the same whole-row window)
+        const int om = x == 0 ? nx - 1 : -1, op = x == nx - 1 ? 1 - nx : 1;
         float d[kQ];
         for_speeds<0, kQ>([&](auto pc) {
             constexpr int p = decltype(pc)::value;
-            const int xs = cx(p) == 0 ? x : (cx(p) > 0 ? xm : xp);
-            d[p] = Pop<St>::template get<p>(pst[(p * nb + bb) * W + xs - X0]);
+            const int o = cx(p) == 0 ? 0 : (cx(p) > 0 ? om : op);
+            d[p] = Pop<St>::template get<p>(pst[p * total + l + o]);
         });
         float gx, gy, gz, T = a.tau0;
         external_force(a, y, gx, gy, gz);
         if (CELLS) {
-            const float4 g4 = gst[sx];
+            const float4 g4 = gst[l];
             gx += g4.x;
             gy += g4.y;
             gz += g4.z;
@@ -998,15 +995,13 @@ constexpr int compact_min_blocks() { return sizeof(St) == 4 ? 3 : 2; }
 
 template <typename St, bool CELLS, bool SIGMA>
 __global__ void __launch_bounds__(kStThreads, compact_min_blocks<St>())
-    k_lb_compact(LbArgs a, const int4 *__restrict__ batches, const int2 *__restrict__ bxs, int nbatches, int ns,
-                 int stage_bytes)
+    k_lb_compact(LbArgs a, const int4 *__restrict__ batches, int nbatches, int ns, int stage_bytes)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages];
     __shared__ int4 s_desc[kMaxStages];
-    __shared__ int s_rb[kMaxStages][kMaxBatchRows][10];
-    __shared__ __align__(8) int2 s_pd[9 * kMaxBatchRows];
-    __shared__ int s_pfr[kMaxBatchRows];
+    __shared__ int s_rb[kMaxStages][kMaxSegs][kSegWords];
+    __shared__ __align__(8) int2 s_pd[kSegDescs * kMaxSegs];
     __shared__ unsigned long long s_step;
     if (threadIdx.x == 0) {
         for (int k = 0; k < ns; ++k) {
@@ -1034,21 +1029,17 @@ __global__ void __launch_bounds__(kStThreads, compact_min_blocks<St>())
         if (lane == 0) claim = atomicAdd(&a.work[0], 1);
         int batch = __shfl_sync(0xffffffffu, claim, 0);
         int4 bd = make_int4(-1, 0, 0, 0);
-        int2 bx = make_int2(0, 0);
         if (batch < nbatches) {
             bd = batches[batch];
-            bx = bxs[batch];
             if (lane == 0) claim = atomicAdd(&a.work[0], 1);
         }
         for (;; ++it) {
             const int stage = it % ns;
-            if (batch < nbatches) load_descs(a, bd, bx, lane, s_pd, s_pfr);
+            if (batch < nbatches) load_descs(a, bd, lane, s_pd);
             const int nbatch = __shfl_sync(0xffffffffu, claim, 0);
             int4 nbd = make_int4(-1, 0, 0, 0);
-            int2 nbx = make_int2(0, 0);
             if (batch < nbatches && nbatch < nbatches) {
                 nbd = batches[nbatch];
-                nbx = bxs[nbatch];
                 if (lane == 0) claim = atomicAdd(&a.work[0], 1);
             }
             const bool freed =
@@ -1073,13 +1064,12 @@ __global__ void __launch_bounds__(kStThreads, compact_min_blocks<St>())
                 issued &= ~(1u << stage);
             } else {
                 issued |= 1u << stage;
-                produce_compact<St, CELLS>(a, bd, bx, s_pd, s_pfr, smraw + (size_t)stage * stage_bytes, bar,
-                                           lane, s_rb[stage]);
+                produce_compact<St, CELLS>(a, bd, s_pd, smraw + (size_t)stage * stage_bytes, bar, lane,
+                                           s_rb[stage]);
             }
-            __syncwarp();  // every lane has read s_pd / s_pfr before the next copy into them
+            __syncwarp();  // every lane has read s_pd before the next copy into it
             batch = nbatch < nbatches ? nbatch : nbatches;
             bd = nbd;
-            bx = nbx;
         }
         if (!ok) {
             // let the copies still in flight land before the CTA's memory
@@ -1582,7 +1572,7 @@ struct LaunchOp {
             if (d.compact) {
                 if (d.lb_grid > 0)
                     k_lb_compact<St, C, S_><<<d.lb_grid, kStThreads, d.lb_smem, s>>>(
-                        a, d.lb_batches, d.lb_bx, d.nbatches, d.lb_stages, d.lb_stage_bytes);
+                        a, d.lb_batches, d.nbatches, d.lb_stages, d.lb_stage_bytes);
                 return;
             }
         }
