@@ -889,7 +889,12 @@ __global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc)
 // pheno_torque_diss).  Lane partial sums, then a fixed shuffle tree: every
 // lane ends with the 9 sums.
 // ---------------------------------------------------------------------------
-constexpr int kIlp = 4;  // list entries per lane in flight
+// List entries per lane in flight.  Each entry's u and stress gathers issue
+// together, after the list loads: two dependent memory round trips per
+// group instead of three (the stress had been gathered after the velocity
+// sums, only where Dw != 0): tube step 1.173 -> 1.159 ms.  Four entries need
+// 80 registers (six blocks per SM: 1.162 ms) or spill at 72 (1.208 ms).
+constexpr int kIlp = 3;
 
 // Sums over the entries part, part + parts, ... (in units of 32) of cell
 // i's list: this warp's share when `parts` warps sample one cell.
@@ -908,65 +913,47 @@ __device__ __forceinline__ void sample_sums(const ShapeArgs &a, int i, int n, fl
     const float thr = 1e-24f * S * S;
     const int2 *idx = a.sp_idx + (size_t)i * a.sp_cap;
     const float4 *val = a.sp_val + (size_t)i * a.sp_cap;
-    // kIlp independent entries per lane in flight: the list and U loads of
-    // all of them issue before any sum uses them
+    // kIlp independent entries per lane in flight: the list loads of all of
+    // them, then all their gathers (u, and the stress where the torque
+    // needs it), before any sum uses them
     for (int e0 = lane + 32 * part; e0 < n; e0 += 32 * parts * kIlp) {
         int2 ix[kIlp];
         float4 v[kIlp];
-        float u[kIlp][3], sxz[kIlp];  // u and, in U.w, the stress xz
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             const int e = e0 + 32 * parts * j;
             ix[j] = e < n ? idx[e] : make_int2(gc, 0);
             v[j] = e < n ? val[e] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        float4 u4[kIlp], s4[kIlp];
+        float syz[kIlp];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
-            const float4 u4 = a.U[ix[j].x];
-            u[j][0] = u4.x;
-            u[j][1] = u4.y;
-            u[j][2] = u4.z;
-            sxz[j] = u4.w;
+            const int g = ix[j].x;
+            u4[j] = a.U[g];
+            if (ALPHA) {
+                s4[j] = a.S[g];
+                syz[j] = a.Syz[g];
+            }
         }
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
-            acc[0] += v[j].x * u[j][0];
-            acc[1] += v[j].x * u[j][1];
-            acc[2] += v[j].x * u[j][2];
-            const float vx = u[j][0] - uc0, vy = u[j][1] - uc1, vz = u[j][2] - uc2;
+            acc[0] += v[j].x * u4[j].x;
+            acc[1] += v[j].x * u4[j].y;
+            acc[2] += v[j].x * u4[j].z;
+            const float vx = u4[j].x - uc0, vy = u4[j].y - uc1, vz = u4[j].z - uc2;
             acc[3] -= v[j].z * vz - v[j].w * vy;
             acc[4] -= v[j].w * vx - v[j].y * vz;
             acc[5] -= v[j].y * vy - v[j].z * vx;
-        }
-        if (ALPHA) {
-            float sg[kIlp][6];
-            bool on[kIlp];
-#pragma unroll
-            for (int j = 0; j < kIlp; ++j) {
-                const int g = ix[j].x;
-                on[j] = v[j].x > 0.f && v[j].y * v[j].y + v[j].z * v[j].z + v[j].w * v[j].w > thr;
-                float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f);
-                float syz = 0.f;
-                if (on[j]) {
-                    s0 = a.S[g];
-                    syz = a.Syz[g];
-                }
-                sg[j][0] = s0.x;
-                sg[j][1] = s0.y;
-                sg[j][2] = s0.z;
-                sg[j][3] = s0.w;
-                sg[j][4] = sxz[j];
-                sg[j][5] = syz;
-            }
-#pragma unroll
-            for (int j = 0; j < kIlp; ++j) {
-                if (!on[j]) continue;
-                const float inv = rsqrtf(v[j].y * v[j].y + v[j].z * v[j].z + v[j].w * v[j].w);
+            if (ALPHA) {
+                const float d2 = v[j].y * v[j].y + v[j].z * v[j].z + v[j].w * v[j].w;
+                if (!(v[j].x > 0.f && d2 > thr)) continue;
+                const float inv = rsqrtf(d2);
                 const float nx = v[j].y * inv, ny = v[j].z * inv, nz = v[j].w * inv;
-                // sigma components: xx, yy, zz, xy, xz, yz
-                const float tx = sg[j][0] * nx + sg[j][3] * ny + sg[j][4] * nz;
-                const float ty = sg[j][3] * nx + sg[j][1] * ny + sg[j][5] * nz;
-                const float tz = sg[j][4] * nx + sg[j][5] * ny + sg[j][2] * nz;
+                // sigma components: xx = s.x, yy = s.y, zz = s.z, xy = s.w, xz = u.w, yz
+                const float tx = s4[j].x * nx + s4[j].w * ny + u4[j].w * nz;
+                const float ty = s4[j].w * nx + s4[j].y * ny + syz[j] * nz;
+                const float tz = u4[j].w * nx + syz[j] * ny + s4[j].z * nz;
                 const int pk = ix[j].y;
                 const float r0 = b0 + (float)(pk & 1023), r1 = b1 + (float)((pk >> 10) & 1023),
                             r2 = b2 + (float)(pk >> 20);
@@ -1199,9 +1186,9 @@ __device__ __forceinline__ void spread_list(const ShapeArgs &a, int i, int n, in
     const float Jx = jl[0], Jy = jl[1], Jz = jl[2], Lx = jl[3], Ly = jl[4], Lz = jl[5];
     const int2 *idx = a.sp_idx + (size_t)i * a.sp_cap;
     const float4 *val = a.sp_val + (size_t)i * a.sp_cap;
-    // few values are live in the spread: twice the sampling's entries in
-    // flight (tube step 1,221 -> 1,206 us, channel 105.5 -> 103.6 us)
-    constexpr int kIlpSpread = 2 * kIlp;
+    // few values are live in the spread: eight entries per lane in flight
+    // (against four: tube step 1,221 -> 1,206 us, channel 105.5 -> 103.6 us)
+    constexpr int kIlpSpread = 8;
     for (int e0 = lane; e0 < n; e0 += 32 * kIlpSpread) {
         int g[kIlpSpread];
         float4 v[kIlpSpread];

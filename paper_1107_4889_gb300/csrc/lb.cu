@@ -1429,15 +1429,24 @@ k_budget_final(const double *__restrict__ part, int nblocks, const double *__res
 
 int pop_bytes(int prec) { return prec == PREC_F32 ? 4 : 2; }
 
-StageLayout stage_layout(const Dev &d)
+// Stage layout of the row-staged pass: about kStageBytes per stage, whole
+// rows, at most one y column of rows; a multiple of the rows that fill the
+// consumer threads when rows are short.  A single solve with 16-bit
+// populations stages at least 2 kStConsumers nodes (two per consumer
+// thread; the 64 x 64 x 256 channel with cells in binary16: 105.1 -> 101.3
+// us per coupled step, 102.8 with three per thread); the packed passes of
+// the request server (`packed`) keep about kStageBytes, since their small
+// lattices need the batches (48 mixed requests: 4.87 -> 4.38 solves/s with
+// two nodes per thread).
+StageLayout stage_layout(const Dev &d, bool packed)
 {
     StageLayout L;
     L.planes = kQ + (d.nc > 0 ? 4 : 0) + (d.walls ? 1 : 0);
     const int es = pop_bytes(d.prec);
     const int row_bytes = d.nx * (kQ * es + (L.planes - kQ) * 4);
-    // about kStageBytes per stage, whole rows, at most one y column of rows;
-    // a multiple of the rows that fill the consumer threads when rows are short
-    int B = kStageBytes / row_bytes;
+    int budget = kStageBytes;
+    if (es == 2 && !packed) budget = max(budget, 2 * kStConsumers * (row_bytes / d.nx));
+    int B = budget / row_bytes;
     B = B < 1 ? 1 : (B > d.ny ? d.ny : B);
     if (d.nx < kStConsumers && B * d.nx > kStConsumers)
         B -= B % (kStConsumers / d.nx > 0 ? kStConsumers / d.nx : 1);
@@ -1448,11 +1457,11 @@ StageLayout stage_layout(const Dev &d)
     return L;
 }
 
-bool staged_ok(const Dev &d)
+bool staged_ok(const Dev &d, bool packed)
 {
     if (d.compact) return false;  // the compact pass has its own batches
     if ((d.nx * pop_bytes(d.prec)) % 16 != 0) return false;  // rows must be whole 16-byte units
-    const StageLayout L = stage_layout(d);
+    const StageLayout L = stage_layout(d, packed);
     return 2u * (unsigned)L.stage_bytes <= 200u * 1024u;
 }
 
@@ -1506,8 +1515,8 @@ struct PrepareOp {
                 return;
             }
         }
-        if (d.fluid_list || !staged_ok(d)) return;
-        StageLayout L = stage_layout(d);
+        if (d.fluid_list || !staged_ok(d, false)) return;
+        StageLayout L = stage_layout(d, false);
         const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
@@ -1580,7 +1589,7 @@ struct LaunchOp {
             const int g = (d.nfluid + kLbThreads - 1) / kLbThreads;
             if (g > 0) k_lb_list<St, W, C, S_><<<g, kLbThreads, 0, s>>>(a, d.fluid_list, d.nfluid);
         } else if (d.lb_grid > 0) {
-            StageLayout L = stage_layout(d);
+            StageLayout L = stage_layout(d, false);
             L.stages = d.lb_stages;
             const int nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
             k_lb_staged<St, W, C, S_><<<d.lb_grid, kStThreads, d.lb_smem, s>>>(a, L, nbatches);
@@ -1615,8 +1624,8 @@ struct ShapesOp {
             }
         }
         if (!d.compact) {
-            if (!staged_ok(d)) return;
-            stage_bytes = stage_layout(d).stage_bytes;
+            if (!staged_ok(d, false)) return;
+            stage_bytes = stage_layout(d, false).stage_bytes;
         }
         raise_smem_limit(kern, 200 * 1024);
         for (int ns = 2; ns <= kMaxStages; ++ns) {
@@ -1645,7 +1654,7 @@ void set_lb_shape(Dev &d, int stages, int ctas_per_sm)
     if (d.lb_grid <= 0) return;
     int nbatches = d.nbatches, stage_bytes = d.lb_stage_bytes;
     if (!d.compact) {
-        const StageLayout L = stage_layout(d);
+        const StageLayout L = stage_layout(d, false);
         nbatches = d.nz * ((d.ny + L.B - 1) / L.B);
         stage_bytes = L.stage_bytes;
     }
@@ -1714,11 +1723,11 @@ size_t lb_pack_entry_bytes() { return sizeof(LbPackEntry); }
 
 bool fill_lb_pack_entry(const Dev &d, const Params &p, void *out, int *nbatches, int *stage_bytes)
 {
-    if (!staged_ok(d)) return false;
+    if (!staged_ok(d, true)) return false;
     LbPackEntry e;
     std::memset(&e, 0, sizeof e);
     e.a = lb_args(d, p, 0);
-    e.L = stage_layout(d);
+    e.L = stage_layout(d, true);
     e.L.stages = 0;  // the pack's ring depth applies
     *nbatches = d.nz * ((d.ny + e.L.B - 1) / e.L.B);
     *stage_bytes = e.L.stage_bytes;
