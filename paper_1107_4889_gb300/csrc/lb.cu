@@ -1432,12 +1432,15 @@ int pop_bytes(int prec) { return prec == PREC_F32 ? 4 : 2; }
 // Stage layout of the row-staged pass: about kStageBytes per stage, whole
 // rows, at most one y column of rows; a multiple of the rows that fill the
 // consumer threads when rows are short.  A single solve with 16-bit
-// populations stages at least 2 kStConsumers nodes (two per consumer
-// thread; the 64 x 64 x 256 channel with cells in binary16: 105.1 -> 101.3
-// us per coupled step, 102.8 with three per thread); the packed passes of
-// the request server (`packed`) keep about kStageBytes, since their small
-// lattices need the batches (48 mixed requests: 4.87 -> 4.38 solves/s with
-// two nodes per thread).
+// populations or with cells stages at least 2 kStConsumers nodes (two per
+// consumer thread) when that still leaves kWideMinBatches batches: the
+// 64 x 64 x 256 channel with cells, coupled step 97.9 -> 96.2 us in FP32,
+// 105.1 -> 101.3 us in binary16 (102.8 with three nodes per thread).  The
+// packed passes of the request server (`packed`) keep about kStageBytes,
+// since their small lattices need the batches (48 mixed requests: 4.87 ->
+// 4.38 solves/s with two nodes per thread).
+constexpr int kWideMinBatches = 1024;
+
 StageLayout stage_layout(const Dev &d, bool packed)
 {
     StageLayout L;
@@ -1445,7 +1448,11 @@ StageLayout stage_layout(const Dev &d, bool packed)
     const int es = pop_bytes(d.prec);
     const int row_bytes = d.nx * (kQ * es + (L.planes - kQ) * 4);
     int budget = kStageBytes;
-    if (es == 2 && !packed) budget = max(budget, 2 * kStConsumers * (row_bytes / d.nx));
+    if ((es == 2 || d.nc > 0) && !packed) {
+        const int wide = max(budget, 2 * kStConsumers * (row_bytes / d.nx));
+        const int Bw = max(1, min(wide / row_bytes, d.ny));
+        if ((long long)d.nz * ((d.ny + Bw - 1) / Bw) >= kWideMinBatches) budget = wide;
+    }
     int B = budget / row_bytes;
     B = B < 1 ? 1 : (B > d.ny ? d.ny : B);
     if (d.nx < kStConsumers && B * d.nx > kStConsumers)

@@ -109,6 +109,16 @@ def test_ragged_walled_lattice_storage(prec):
     assert r["J_emul"] <= 5 * TOL_EMULATED
 
 
+def test_full_size_channel_binary16_matches_emulating_oracle():
+    """The 64 x 64 x 256 channel with 3,650 cells in binary16: the row-staged
+    pass stages two nodes per consumer thread on a lattice this size; 4
+    steps against the oracle with the same storage step."""
+    geom, cells, params = wl.channel_workload()
+    r = _run(geom, cells, params, "f16", "stochastic", 4)
+    print("f16 full-size channel", r)
+    assert r["u_emul"] <= TOL_EMULATED and r["J_emul"] <= 5 * TOL_EMULATED
+
+
 def test_rest_state_and_uniform_force_storage():
     """A fluid at rest stays exactly at rest in every format; under a
     uniform force the mean velocity of pass n is (n + 1/2) G to within the
