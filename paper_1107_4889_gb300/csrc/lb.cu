@@ -1529,6 +1529,7 @@ struct PrepareOp {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         long long best_cost = -1;
+        int best_per_sm = 0;
         raise_smem_limit((const void *)k_lb_staged<St, W, C, S_>, 200 * 1024);
         for (int ns = kMaxStages; ns >= 2; --ns) {
             const size_t smem = (size_t)ns * L.stage_bytes;
@@ -1539,8 +1540,13 @@ struct PrepareOp {
             if (per_sm < 1) continue;
             const long long slots = (long long)sms * per_sm;
             const long long cost = ((nbatches + slots - 1) / slots) * per_sm;
-            if (best_cost < 0 || cost < best_cost) {
+            // on a tie, more CTAs per SM (their copies hide each other's
+            // latency): with 48 KB stages one CTA of four stages ties with
+            // two of two, and one CTA per SM left the channel's FP32 pass at
+            // 43.6 us alone
+            if (best_cost < 0 || cost < best_cost || (cost == best_cost && per_sm > best_per_sm)) {
                 best_cost = cost;
+                best_per_sm = per_sm;
                 d.lb_stages = ns;
                 d.lb_smem = smem;
                 d.lb_grid = (int)(slots > nbatches ? nbatches : slots);
