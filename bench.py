@@ -176,9 +176,11 @@ def _lb_source_hash():
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic(workload, precision="f32"):
-    """DRAM bytes per lattice-pass launch from the committed ncu summary, if
-    it was taken on the current kernel source; else None."""
+def _profiled_lb(workload, precision="f32"):
+    """From the committed ncu summary of the lattice pass, if it was taken on
+    the current kernel source: DRAM bytes per launch and the launch's time
+    alone (serialised under ncu, default launch shape, in us; None when the
+    summary gives none).  None when there is no current summary."""
     path = os.path.join(ROOT, "profiles", f"lb_pass_{workload}.md")
     if precision != "f32":
         path = os.path.join(ROOT, "profiles", f"lb_pass_{workload}_{precision}.md")
@@ -187,9 +189,18 @@ def _profiled_traffic(workload, precision="f32"):
     txt = open(path).read()
     m_hash = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", txt)
     m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    m_us = re.search(r"alone_us_per_launch:\s*([0-9.eE+]+)", txt)
     if not m_hash or not m_bytes or m_hash.group(1) != _lb_source_hash():
         return None
-    return float(m_bytes.group(1))
+    return {"traffic": float(m_bytes.group(1)), "alone_us": float(m_us.group(1)) if m_us else None,
+            "summary": os.path.relpath(path, ROOT)}
+
+
+def _profiled_traffic(workload, precision="f32"):
+    """DRAM bytes per lattice-pass launch from the committed ncu summary, if
+    it was taken on the current kernel source; else None."""
+    prof = _profiled_lb(workload, precision)
+    return prof["traffic"] if prof else None
 
 
 def _algorithmic_bytes_per_node(geom, params, has_cells=True):
@@ -360,11 +371,19 @@ def run_ours(args):
     bpn = _algorithmic_bytes_per_node(geom, params, n > 0)
     peak, peak_kind = _peaks()
     achieved = bpn * nf / (lb_ms * 1e-3) / 1e9
-    traffic = _profiled_traffic(args.workload, args.precision)
+    # the committed summaries profile the pass with cells
+    prof = _profiled_lb(args.workload, args.precision) if n > 0 else None
+    traffic = prof["traffic"] if prof else None
     roof = {"kernel": "lattice pass (k_lb)", "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_fluid_node": bpn,
             "lb_ms_per_launch": lb_ms, "cell_work_ms_per_step": kms[1] / max(kcount[1], 1)}
+    if prof and prof["alone_us"]:
+        # the same pass with nothing beside it (the step's live launch shares
+        # the SMs with the cell kernels that the graph runs next to it)
+        a_gbs = bpn * nf / (prof["alone_us"] * 1e-6) / 1e9
+        roof["alone"] = {"us_per_launch": prof["alone_us"], "achieved": a_gbs, "frac": a_gbs / peak,
+                         "how": f"serialised under ncu, default launch shape ({prof['summary']})"}
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:

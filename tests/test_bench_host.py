@@ -59,3 +59,20 @@ def test_profiled_traffic_follows_the_source_hash(tmp_path, monkeypatch):
     assert bench._profiled_traffic("tube") == pytest.approx(2719223808.0)
     assert bench._profiled_traffic("tube", "f16") is None
     assert bench._profiled_traffic("channel") is None
+    # the launch's time alone, when the summary gives it
+    assert bench._profiled_lb("tube")["alone_us"] is None
+    (prof / "lb_pass_channel.md").write_text(
+        f"source_sha256_16: {cur}\ndram_bytes_per_launch: 171991296\nalone_us_per_launch: 37.4\n")
+    got = bench._profiled_lb("channel")
+    assert got["traffic"] == pytest.approx(171991296.0) and got["alone_us"] == pytest.approx(37.4)
+    assert got["summary"] == os.path.join("profiles", "lb_pass_channel.md")
+
+
+def test_committed_lattice_summaries_are_current():
+    """Every committed summary of the lattice pass carries the hash of the
+    current kernel source (else the bench line reports no traffic), its DRAM
+    bytes and its time alone."""
+    for w, p in (("tube", "f32"), ("tube", "f16"), ("channel", "f32"), ("channel", "f16")):
+        got = bench._profiled_lb(w, p)
+        assert got is not None, (w, p)
+        assert got["traffic"] > 0 and got["alone_us"] > 0
