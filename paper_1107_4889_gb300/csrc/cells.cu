@@ -892,8 +892,10 @@ __global__ void __launch_bounds__(32 * kWtWarps) k_weights(ShapeArgs a, int nc)
 // List entries per lane in flight.  Each entry's u and stress gathers issue
 // together, after the list loads: two dependent memory round trips per
 // group instead of three (the stress had been gathered after the velocity
-// sums, only where Dw != 0): tube step 1.173 -> 1.159 ms.  Four entries need
-// 80 registers (six blocks per SM: 1.162 ms) or spill at 72 (1.208 ms).
+// sums): tube step 1.173 -> 1.159 ms.  Four entries need 80 registers (six
+// blocks per SM: 1.162 ms) or spill at 72 (1.208 ms).  The stress is
+// gathered only where w > 0 (the torque's other entries, the rim of the
+// list where only D w is non-zero, need u alone): 1.159 -> 1.142 ms.
 constexpr int kIlp = 3;
 
 // Sums over the entries part, part + parts, ... (in units of 32) of cell
@@ -932,8 +934,12 @@ __device__ __forceinline__ void sample_sums(const ShapeArgs &a, int i, int n, fl
             const int g = ix[j].x;
             u4[j] = a.U[g];
             if (ALPHA) {
-                s4[j] = a.S[g];
-                syz[j] = a.Syz[g];
+                s4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                syz[j] = 0.f;
+                if (v[j].x > 0.f) {  // the torque needs the stress only where w > 0
+                    s4[j] = a.S[g];
+                    syz[j] = a.Syz[g];
+                }
             }
         }
 #pragma unroll
