@@ -36,7 +36,7 @@ struct LbArgs {
     void *dst;
     const uint32_t *links;
     const int4 *rows;  // compact layout: row table (internal.h), else null
-    const int2 *pool;  // compact lattice pass: per batch row, nine copy descriptors (produce_compact)
+    const int2 *pool;  // compact lattice pass: per batch segment, kSegDescs descriptors (produce_compact)
     float4 *G, *U, *S;  // node-major: force density + hematocrit sum, velocity (+ stress xz), stress xx yy zz xy
     float *Syz;         // node-major: stress yz
     int *flags;
